@@ -1,0 +1,162 @@
+"""Exact transition operators on tiny lattices (test infrastructure).
+
+Builds, over all 2^N states of an L x L periodic lattice, the operators the
+paper's proofs are about (arXiv:1403.4674, Sec. 2.2 and App. A):
+
+  * ``step(d)``: one uniformised single-site step of domain d (App. A,
+    Eq. Glauber_TM with selection probability 1/n_d): site i of d flips with
+    probability a_c(i)/n_d, otherwise the state is kept (T_ii = 1 - sum);
+  * ``domain(d)`` = step(d)^k: the domain process T_(lambda_d)^{N_I}
+    (Eqs. 4-5);
+  * ``colour(c)``: the product over the domains of one colour (they commute,
+    Sec. 2.2);
+  * ``schedule(colours)``: T_SEQ(Lambda) for a colour sequence (Eq. 8);
+  * ``reference_step``: the textbook single-spin kernel over the whole lattice,
+    built from H(sigma') - H(sigma) directly (the N_D = 1 special case);
+  * ``real_flip_step(d)``: the *other* reading of "k events per visit"
+    (always one real flip, chosen proportionally to rate) -- a negative test.
+
+Operators act on column vectors of probabilities, p' = T p.  The acceptance
+table is the oracle's own (``oracle.rate_table``); ``quantised=True`` uses the
+fixed-point values A_c / 2^P that the sampler actually draws with.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import oracle as orc
+from .exact_ising import lattice_energy_all_states
+
+
+class Enumerator:
+    def __init__(self, L: int, Ld: int, k: int, beta: float, J: float = 1.0,
+                 h: float = 0.0, law: int = orc.RATE_METROPOLIS, quantised: bool = True):
+        if L * L > 20:
+            raise ValueError("state space too large to enumerate")
+        self.L, self.Ld, self.k = L, Ld, k
+        self.beta, self.J, self.h = beta, J, h
+        self.N = L * L
+        self.nd = Ld * Ld
+        self.Dx = L // Ld
+        self.S = 1 << self.N
+        idx = np.arange(self.S, dtype=np.int64)
+        self.bits = ((idx[:, None] >> np.arange(self.N)) & 1).astype(np.int64)
+        self.idx = idx
+        H, _ = lattice_energy_all_states(L, J, h)
+        self.H = H
+        w = np.exp(-beta * (H - H.min()))
+        self.pi = w / w.sum()
+        log2nd = int(round(np.log2(self.nd)))
+        a, A = orc.rate_table(J, beta, h, law, log2nd)
+        if quantised:
+            P = 63 - log2nd
+            self.acc = np.array([float(x) for x in A]) / float(2 ** P)
+        else:
+            self.acc = a
+        # class of every site in every state: c = 5*up + (number of up neighbours)
+        self.cls = np.zeros((self.S, self.N), dtype=np.int64)
+        for y in range(L):
+            for x in range(L):
+                i = y * L + x
+                nb = [((y - 1) % L) * L + x, ((y + 1) % L) * L + x,
+                      y * L + (x - 1) % L, y * L + (x + 1) % L]
+                q = sum(self.bits[:, j] for j in nb)
+                self.cls[:, i] = 5 * self.bits[:, i] + q
+
+    # -- geometry -----------------------------------------------------------
+    def domain_sites(self, d: int):
+        bx, by = d % self.Dx, d // self.Dx
+        return [(by * self.Ld + yy) * self.L + bx * self.Ld + xx
+                for yy in range(self.Ld) for xx in range(self.Ld)]
+
+    def domain_colour(self, d: int) -> int:
+        bx, by = d % self.Dx, d // self.Dx
+        return (bx & 1) | ((by & 1) << 1)
+
+    def domains_of_colour(self, c: int):
+        return [d for d in range(self.Dx * self.Dx) if self.domain_colour(d) == c]
+
+    # -- operators (functions p -> T p) ---------------------------------------
+    def _apply_rates(self, p: np.ndarray, sites, rates) -> np.ndarray:
+        out = p * (1.0 - sum(rates))
+        for i, r in zip(sites, rates):
+            out = out + (r * p)[self.idx ^ (1 << i)]
+        return out
+
+    def step(self, d: int, p: np.ndarray) -> np.ndarray:
+        sites = self.domain_sites(d)
+        rates = [self.acc[self.cls[:, i]] / self.nd for i in sites]
+        return self._apply_rates(p, sites, rates)
+
+    def domain(self, d: int, p: np.ndarray) -> np.ndarray:
+        for _ in range(self.k):
+            p = self.step(d, p)
+        return p
+
+    def colour(self, c: int, p: np.ndarray) -> np.ndarray:
+        for d in self.domains_of_colour(c):
+            p = self.domain(d, p)
+        return p
+
+    def schedule(self, colours, p: np.ndarray) -> np.ndarray:
+        for c in colours:
+            p = self.colour(c, p)
+        return p
+
+    def reference_step(self, p: np.ndarray, law: int = orc.RATE_METROPOLIS) -> np.ndarray:
+        """Textbook random-site kernel on the whole lattice from energy differences."""
+        sites = list(range(self.N))
+        rates = []
+        for i in sites:
+            dE = self.H[self.idx ^ (1 << i)] - self.H
+            if law == orc.RATE_METROPOLIS:
+                acc = np.minimum(1.0, np.exp(-self.beta * dE))
+            else:
+                acc = 1.0 / (1.0 + np.exp(self.beta * dE))
+            rates.append(acc / self.N)
+        return self._apply_rates(p, sites, rates)
+
+    def whole_lattice_step(self, p: np.ndarray) -> np.ndarray:
+        """One uniformised class-table step with the whole lattice as one domain."""
+        sites = list(range(self.N))
+        rates = [self.acc[self.cls[:, i]] / self.N for i in sites]
+        return self._apply_rates(p, sites, rates)
+
+    def real_flip_step(self, d: int, p: np.ndarray) -> np.ndarray:
+        """Negative test: exactly one real flip per step, chosen proportionally to rate."""
+        sites = self.domain_sites(d)
+        raw = [self.acc[self.cls[:, i]] for i in sites]
+        tot = sum(raw)
+        rates = [r / tot for r in raw]
+        return self._apply_rates(p, sites, rates)
+
+    # -- checks -----------------------------------------------------------------
+    def stationarity_error(self, op) -> float:
+        return float(np.max(np.abs(op(self.pi) - self.pi)) / np.max(self.pi))
+
+    def detailed_balance_error(self, op, n_probe: int = 4, seed: int = 0) -> float:
+        """max |<x, M D_pi y> - <y, M D_pi x>| / scale over random probes.
+
+        M D_pi is symmetric iff M_ij pi_j = M_ji pi_i (detailed balance).
+        """
+        rng = np.random.default_rng(seed)
+        worst = 0.0
+        for _ in range(n_probe):
+            x = rng.standard_normal(self.S)
+            y = rng.standard_normal(self.S)
+            a = float(x @ op(self.pi * y))
+            b = float(y @ op(self.pi * x))
+            scale = float(np.abs(x) @ op(self.pi * np.abs(y)))
+            worst = max(worst, abs(a - b) / scale)
+        return worst
+
+    def dense(self, op) -> np.ndarray:
+        """Dense matrix of an operator (only for very small state spaces)."""
+        if self.S > 4096:
+            raise ValueError("too large for a dense matrix")
+        M = np.zeros((self.S, self.S))
+        for j in range(self.S):
+            e = np.zeros(self.S)
+            e[j] = 1.0
+            M[:, j] = op(e)
+        return M

@@ -1,0 +1,456 @@
+/*
+ * kmc_oracle.c -- plain, slow, single-threaded CPU oracle for the
+ * sequential-update parallel kinetic Monte Carlo of Nilmeier & Marian,
+ * "A rigorous sequential update strategy for parallel kinetic Monte Carlo
+ * simulation" (arXiv:1403.4674).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file; only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline / reference arm do.  It shares no code, header,
+ * table or constant generator with the CUDA library: every definition below
+ * (Philox4x32-10, the rate table, the class index, the step protocol, the
+ * event hash) is written out here a second time, on purpose, from its
+ * published or stated definition.
+ *
+ * What it computes, in the paper's order:
+ *   - 2D periodic Ising energy, App. A (Eq. for beta*H, 2D line; both
+ *     factors read as configuration j), plus a field term -h*sum(sigma);
+ *   - the lattice cut into equal square domains (Sec. 2.2), coloured 2x2 so
+ *     that same-coloured domains share no halo (Sec. 2.2, "the order of
+ *     updates is not important");
+ *   - each domain process runs k steps with its halo frozen (Sec. 2.2,
+ *     Eqs. 4-5).  One step is the uniformised single-site kernel of App. A
+ *     (Eq. Glauber_TM): site i of the domain flips with probability
+ *     a_c(i)/n_d, otherwise the step is null (the diagonal T_ii).  The real
+ *     event is drawn the n-fold-way way (Sec. 2.1, R = sum of all rates):
+ *     classes c, counts n_c, cumulative rates, then a uniform member;
+ *   - colours visited in a schedule closed under reversal (Sec. 2.2,
+ *     Eqs. 9-10): the palindrome 0 1 2 3 3 2 1 0 by default;
+ *   - the clock: Erlang / Poisson variate of Sec. 2.1 (Eq. 2) as a sum of
+ *     -log(u), or its expectation N*tau_S;
+ *   - observables at schedule endpoints only (Sec. 2.3).
+ *
+ * Everything that steers the trajectory is integer: the rate table is held
+ * in fixed point, A_c = round(a_c * 2^P) with P = 63 - log2(n_d), so that a
+ * step's decision is an exact integer comparison.  Floating point only
+ * appears in the clock and in the final observables.
+ *
+ * Pins (tests/test_oracle_*.py): Philox against PyTorch's engine; the
+ * rate table against closed forms; the sampler against exact enumeration of
+ * the same chain, the beta = 0 closed form and the Erlang clock law; the
+ * long-run energy against Kaufman's exact finite lattice.
+ * Parity unpinned: the per-domain event hash (a fingerprint this build
+ * defines for CPU/GPU event-sequence parity, not a quantity of the paper)
+ * and the Philox counter layout (likewise a definition of this build).
+ *
+ * Build: gcc -O2 -std=gnu11 -ffp-contract=off -fPIC -shared -lm.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11).  Ten rounds of the 4x32 Philox S-box with the
+ * published multipliers and Weyl key increments.
+ * ---------------------------------------------------------------------- */
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u
+#define ORC_PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                       uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)ORC_PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)ORC_PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += ORC_PHILOX_W0;
+        k1 += ORC_PHILOX_W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Counter-word tags (top byte of counter word 3). */
+#define ORC_TAG_STEP 0u
+#define ORC_TAG_INIT 1u
+#define ORC_TAG_PERM 2u
+
+/* Rate laws, schedules, time modes, initial states. */
+#define ORC_RATE_METROPOLIS 0
+#define ORC_RATE_BARKER 1
+#define ORC_SCHED_PALINDROME 0
+#define ORC_SCHED_FIXED 1
+#define ORC_SCHED_RANDOM_PERM 2
+#define ORC_TIME_EXPONENTIAL 0
+#define ORC_TIME_EXPECTED 1
+#define ORC_INIT_RANDOM 0
+#define ORC_INIT_ALL_UP 1
+
+/* FNV-1a 64-bit offset basis and prime (Fowler, Noll, Vo), applied to
+ * whole 64-bit event words rather than bytes. */
+#define ORC_HASH_BASIS 0xcbf29ce484222325ull
+#define ORC_HASH_PRIME 0x00000100000001b3ull
+
+static int orc_log2(int v)
+{
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return ((1 << r) == v) ? r : -1;
+}
+
+/* ------------------------------------------------------------------------
+ * Rate table (App. A, Eq. Glauber_TM; Metropolis as the alternative law).
+ * Class c = 5*sp + q: sp = 1 for an up spin, q = number of up neighbours
+ * (0..4).  sigma = 2*sp - 1, neighbour sum = 2q - 4,
+ *   dE_c = 2*sigma*(J*(2q-4) + h),
+ *   Metropolis: a_c = 1 if dE_c <= 0 else exp(-beta*dE_c)
+ *   Barker:     a_c = 1 / (1 + exp(beta*dE_c))     (App. A, "Barker")
+ * a_c is the acceptance of the uniformised step; the physical rate is
+ * nu*a_c.  A_c = round-to-nearest-even(a_c * 2^P), P = 63 - log2(n_d).
+ * Returns 0, or -1 for an invalid argument.
+ * ---------------------------------------------------------------------- */
+int orc_rate_table(double J, double beta, double h, int law, int log2_nd,
+                   double a_out[10], uint64_t A_out[10])
+{
+    if (log2_nd < 0 || log2_nd > 12) return -1;
+    if (law != ORC_RATE_METROPOLIS && law != ORC_RATE_BARKER) return -1;
+    if (!(beta >= 0.0) || !isfinite(beta) || !isfinite(J) || !isfinite(h))
+        return -1;
+    int P = 63 - log2_nd;
+    for (int sp = 0; sp < 2; ++sp) {
+        for (int q = 0; q <= 4; ++q) {
+            int c = 5 * sp + q;
+            double sigma = sp ? 1.0 : -1.0;
+            double nsum = (double)(2 * q - 4);
+            double dE = 2.0 * sigma * (J * nsum + h);
+            double a;
+            if (law == ORC_RATE_METROPOLIS)
+                a = (dE <= 0.0) ? 1.0 : exp(-beta * dE);
+            else
+                a = 1.0 / (1.0 + exp(beta * dE));
+            a_out[c] = a;
+            A_out[c] = (uint64_t)nearbyint(ldexp(a, P));
+        }
+    }
+    return 0;
+}
+
+/* dE of class c, for tests and for the score. */
+double orc_class_dE(int c, double J, double h)
+{
+    int sp = c / 5, q = c % 5;
+    double sigma = sp ? 1.0 : -1.0;
+    return 2.0 * sigma * (J * (double)(2 * q - 4) + h);
+}
+
+/* ------------------------------------------------------------------------
+ * Initial state: iid +-1 from Philox, or all up.  Site i = y*L + x; block
+ * b = i / 128 uses counter {b_lo, b_hi, 0, TAG_INIT<<24}; the site is up
+ * iff bit (i mod 128) of the 128-bit output is set (word (i%128)/32,
+ * bit i%32).
+ * ---------------------------------------------------------------------- */
+void orc_init_spins(int8_t *s, int L, int init, uint64_t seed)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    int64_t N = (int64_t)L * L;
+    for (int64_t i = 0; i < N; ++i) {
+        if (init == ORC_INIT_ALL_UP) { s[i] = 1; continue; }
+        uint64_t b = (uint64_t)i / 128u;
+        uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), 0u,
+                           ORC_TAG_INIT << 24};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        int bit = (int)((w[(i % 128) / 32] >> (i % 32)) & 1u);
+        s[i] = bit ? 1 : -1;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Colour of domain (bx, by): (bx & 1) | ((by & 1) << 1).
+ * Colour sequence of schedule n (Sec. 2.2, Eqs. 9-10):
+ *   PALINDROME: 0 1 2 3 3 2 1 0 (its own reverse, so w(L) = w(reverse L));
+ *   FIXED:      0 1 2 3 (not closed under reversal: keeps pi stationary but
+ *               not detailed balance; kept as a negative test);
+ *   RANDOM_PERM: a uniform random order of the four colours per schedule,
+ *               Philox counter {0, 0, n_lo, n_hi | TAG_PERM<<24}; index =
+ *               floor(x * 24 / 2^64) with x = w0 | w1<<32, decoded as a
+ *               Lehmer code (most significant digit first).
+ * Returns the number of phases of one schedule.
+ * ---------------------------------------------------------------------- */
+int orc_schedule_colours(int schedule, uint64_t n, uint64_t seed, int out[8])
+{
+    if (schedule == ORC_SCHED_PALINDROME) {
+        static const int pal[8] = {0, 1, 2, 3, 3, 2, 1, 0};
+        memcpy(out, pal, sizeof pal);
+        return 8;
+    }
+    if (schedule == ORC_SCHED_FIXED) {
+        for (int i = 0; i < 4; ++i) out[i] = i;
+        return 4;
+    }
+    if (schedule == ORC_SCHED_RANDOM_PERM) {
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        uint32_t ctr[4] = {0u, 0u, (uint32_t)n,
+                           (uint32_t)((n >> 32) & 0xFFFFFFu) | (ORC_TAG_PERM << 24)};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        uint64_t x = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+        /* floor(x * 24 / 2^64), exact in 128-bit arithmetic */
+        unsigned __int128 prod = (unsigned __int128)x * 24u;
+        int idx = (int)(prod >> 64);
+        int pool[4] = {0, 1, 2, 3};
+        int left = 4;
+        static const int fact[4] = {6, 2, 1, 1};
+        for (int pos = 0; pos < 4; ++pos) {
+            int sel = idx / fact[pos];
+            idx %= fact[pos];
+            out[pos] = pool[sel];
+            for (int t = sel; t < left - 1; ++t) pool[t] = pool[t + 1];
+            --left;
+        }
+        return 4;
+    }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------
+ * One domain process (Sec. 2.2): domain d = by*Dx + bx of a replica, k
+ * uniformised steps with the halo frozen.
+ *
+ * Step j of global phase np uses Philox counter
+ *   {j, d, np_lo, (np_hi & 0xFFFFFF) | TAG_STEP<<24}, key = replica seed:
+ *   target = (w0 | w1<<32) >> 1, uniform on [0, n_d * 2^P) = [0, 2^63);
+ *   V      = ((w2 | w3<<32) >> 11) + 1, so v = V * 2^-53 is in (0, 1].
+ * With counts n_c and R' = sum_c n_c A_c (classes taken in order 0..9):
+ *   target >= R'  -> null step (the diagonal of Eq. Glauber_TM);
+ *   otherwise class c = the smallest c with target < C_c (C_c inclusive
+ *   cumulative sums), member index jj = (target - C_{c-1}) / A_c, and the
+ *   jj-th site of class c in row-major order flips.
+ * So P(site i flips) = A_c(i) / (n_d 2^P) exactly, the same single-site
+ * kernel as App. A with a_c quantised to P fractional bits.
+ *
+ * The event hash of the domain folds every real event as
+ *   H <- (H xor e) * FNV_PRIME,  e = np<<32 | j<<16 | i.
+ * Exponential clock: esum_d += -log(v) for every step (Sec. 2.1, the
+ * Poisson variate as a sum of negative logarithms).
+ * ---------------------------------------------------------------------- */
+static void orc_visit(int8_t *s, int L, int Ld, int bx, int by, int k,
+                      const uint64_t A[10], uint32_t key0, uint32_t key1,
+                      uint64_t np, uint32_t d, int time_mode,
+                      double *esum, uint64_t *hash, int64_t *flips,
+                      int64_t *steps)
+{
+    const int x0 = bx * Ld, y0 = by * Ld, nd = Ld * Ld;
+    /* frozen halo, collected before the domain process runs */
+    int8_t *top = (int8_t *)malloc((size_t)Ld);
+    int8_t *bot = (int8_t *)malloc((size_t)Ld);
+    int8_t *lft = (int8_t *)malloc((size_t)Ld);
+    int8_t *rgt = (int8_t *)malloc((size_t)Ld);
+    int *cls = (int *)malloc(sizeof(int) * (size_t)nd);
+    for (int x = 0; x < Ld; ++x) {
+        top[x] = s[(int64_t)((y0 - 1 + L) % L) * L + x0 + x];
+        bot[x] = s[(int64_t)((y0 + Ld) % L) * L + x0 + x];
+    }
+    for (int y = 0; y < Ld; ++y) {
+        lft[y] = s[(int64_t)(y0 + y) * L + (x0 - 1 + L) % L];
+        rgt[y] = s[(int64_t)(y0 + y) * L + (x0 + Ld) % L];
+    }
+#define SITE(xx, yy) s[(int64_t)(y0 + (yy)) * L + x0 + (xx)]
+    for (int j = 0; j < k; ++j) {
+        /* classes of every domain site, recomputed from scratch */
+        uint64_t n[10] = {0};
+        for (int y = 0; y < Ld; ++y) {
+            for (int x = 0; x < Ld; ++x) {
+                int sp = SITE(x, y) > 0;
+                int up = (y > 0) ? SITE(x, y - 1) : top[x];
+                int dn = (y < Ld - 1) ? SITE(x, y + 1) : bot[x];
+                int lf = (x > 0) ? SITE(x - 1, y) : lft[y];
+                int rt = (x < Ld - 1) ? SITE(x + 1, y) : rgt[y];
+                int q = (up > 0) + (dn > 0) + (lf > 0) + (rt > 0);
+                int c = 5 * sp + q;
+                cls[y * Ld + x] = c;
+                n[c] += 1;
+            }
+        }
+        uint64_t R = 0;
+        for (int c = 0; c < 10; ++c) R += n[c] * A[c];
+
+        uint32_t ctr[4] = {(uint32_t)j, d, (uint32_t)np,
+                           (uint32_t)((np >> 32) & 0xFFFFFFu) | (ORC_TAG_STEP << 24)};
+        uint32_t key[2] = {key0, key1};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        uint64_t target = ((uint64_t)w[0] | ((uint64_t)w[1] << 32)) >> 1;
+        uint64_t V = (((uint64_t)w[2] | ((uint64_t)w[3] << 32)) >> 11) + 1u;
+        if (time_mode == ORC_TIME_EXPONENTIAL)
+            *esum += -log(ldexp((double)V, -53));
+        *steps += 1;
+        if (target >= R) continue; /* null step */
+
+        uint64_t C = 0;
+        int c = 0;
+        for (c = 0; c < 10; ++c) {
+            uint64_t w_c = n[c] * A[c];
+            if (target < C + w_c) break;
+            C += w_c;
+        }
+        uint64_t jj = (target - C) / A[c];
+        int site = -1;
+        uint64_t seen = 0;
+        for (int i = 0; i < nd; ++i) {
+            if (cls[i] == c) {
+                if (seen == jj) { site = i; break; }
+                ++seen;
+            }
+        }
+        /* site >= 0 always: jj < n_c by construction */
+        int xs = site % Ld, ys = site / Ld;
+        SITE(xs, ys) = (int8_t)(-SITE(xs, ys));
+        *flips += 1;
+        uint64_t e = (np << 32) | ((uint64_t)j << 16) | (uint64_t)site;
+        *hash = (*hash ^ e) * ORC_HASH_PRIME;
+    }
+#undef SITE
+    free(top); free(bot); free(lft); free(rgt); free(cls);
+}
+
+/* ------------------------------------------------------------------------
+ * Observables at a schedule endpoint (Sec. 2.3; App. A energy):
+ *   bonds = sum over sites of s(x,y)*(s(x+1,y) + s(x,y+1)), periodic;
+ *   mag = sum s;  e = (-J*bonds - h*mag)/N;  m = mag/N;  A = e*m;
+ *   T = mean over domains of t_d, t_d = esum_d/Lambda (exponential) or
+ *   steps_d/Lambda (expected), Lambda = n_d*nu.
+ * out = {e, m, e*m, T}.
+ * ---------------------------------------------------------------------- */
+void orc_energy_mag(const int8_t *s, int L, int64_t *bonds, int64_t *mag)
+{
+    int64_t b = 0, m = 0;
+    for (int y = 0; y < L; ++y) {
+        for (int x = 0; x < L; ++x) {
+            int v = s[(int64_t)y * L + x];
+            int r = s[(int64_t)y * L + (x + 1) % L];
+            int u = s[(int64_t)((y + 1) % L) * L + x];
+            b += v * (r + u);
+            m += v;
+        }
+    }
+    *bonds = b;
+    *mag = m;
+}
+
+double orc_domain_time(int time_mode, double esum, int64_t steps, int nd,
+                       double nu)
+{
+    double lambda = (double)nd * nu;
+    if (time_mode == ORC_TIME_EXPONENTIAL) return esum / lambda;
+    return (double)steps / lambda;
+}
+
+static void orc_observe(const int8_t *s, int L, double J, double h,
+                        int time_mode, const double *esum,
+                        const int64_t *steps, int ND, int nd, double nu,
+                        double out[4])
+{
+    int64_t bonds, mag;
+    orc_energy_mag(s, L, &bonds, &mag);
+    double N = (double)L * (double)L;
+    double e = (-J * (double)bonds - h * (double)mag) / N;
+    double m = (double)mag / N;
+    double tsum = 0.0;
+    for (int d = 0; d < ND; ++d)
+        tsum += orc_domain_time(time_mode, esum[d], steps[d], nd, nu);
+    out[0] = e;
+    out[1] = m;
+    out[2] = e * m;
+    out[3] = tsum / (double)ND;
+}
+
+/* ------------------------------------------------------------------------
+ * Run n_sched schedules of one replica, starting at global schedule index
+ * sched_begin.  Per-domain state (esum, steps, hash, flips) is read and
+ * updated in place, indexed d = by*Dx + bx.  If obs_every > 0, after each
+ * local schedule n with (n+1) % obs_every == 0 the record
+ * {e, m, e*m, T} is written to obs[4*((n+1)/obs_every - 1)].
+ * Domains of one colour are visited in ascending d; the paper allows any
+ * order because they do not interact (Sec. 2.2).
+ * Returns 0, or -1 for an invalid configuration.
+ * ---------------------------------------------------------------------- */
+int orc_run_replica(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
+                    uint64_t seed, int schedule, int time_mode, double nu,
+                    double J, double h, int64_t sched_begin, int64_t n_sched,
+                    int obs_every, double *esum, int64_t *steps,
+                    uint64_t *hash, int64_t *flips, double *obs)
+{
+    if (L <= 0 || Ld <= 0 || L % Ld != 0) return -1;
+    int Dx = L / Ld;
+    if (Dx < 2 || (Dx & 1)) return -1;
+    if (orc_log2(Ld * Ld) < 0) return -1;
+    if (k < 0 || k > 65535) return -1;
+    const int ND = Dx * Dx, nd = Ld * Ld;
+    uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+    for (int64_t nl = 0; nl < n_sched; ++nl) {
+        uint64_t n = (uint64_t)(sched_begin + nl);
+        int col[8];
+        int nph = orc_schedule_colours(schedule, n, seed, col);
+        if (nph < 0) return -1;
+        for (int p = 0; p < nph; ++p) {
+            uint64_t np = n * (uint64_t)nph + (uint64_t)p;
+            for (int d = 0; d < ND; ++d) {
+                int bx = d % Dx, by = d / Dx;
+                int colour = (bx & 1) | ((by & 1) << 1);
+                if (colour != col[p]) continue;
+                orc_visit(s, L, Ld, bx, by, k, A, key0, key1, np,
+                          (uint32_t)d, time_mode, &esum[d], &hash[d],
+                          &flips[d], &steps[d]);
+            }
+        }
+        if (obs_every > 0 && obs != NULL && (nl + 1) % obs_every == 0) {
+            int64_t o = (nl + 1) / obs_every - 1;
+            orc_observe(s, L, J, h, time_mode, esum, steps, ND, nd, nu,
+                        &obs[4 * o]);
+        }
+    }
+    return 0;
+}
+
+uint64_t orc_hash_basis(void) { return ORC_HASH_BASIS; }
+
+/* ------------------------------------------------------------------------
+ * Many independent short runs for statistical tests: replica r uses seed
+ * seed0 + r, starts from s0 (copied), runs n_sched schedules and writes its
+ * final state to out[r*L*L ...].  Plain loop over orc_run_replica.
+ * ---------------------------------------------------------------------- */
+int orc_sample_final_states(const int8_t *s0, int L, int Ld, int k,
+                            const uint64_t A[10], uint64_t seed0,
+                            int64_t n_runs, int schedule, int64_t n_sched,
+                            int8_t *out)
+{
+    int Dx = (Ld > 0) ? L / Ld : 0;
+    int ND = Dx * Dx;
+    if (ND <= 0) return -1;
+    double *esum = (double *)calloc((size_t)ND, sizeof(double));
+    int64_t *steps = (int64_t *)calloc((size_t)ND, sizeof(int64_t));
+    uint64_t *hash = (uint64_t *)calloc((size_t)ND, sizeof(uint64_t));
+    int64_t *flips = (int64_t *)calloc((size_t)ND, sizeof(int64_t));
+    int rc = 0;
+    for (int64_t r = 0; r < n_runs && rc == 0; ++r) {
+        int8_t *s = out + r * (int64_t)L * L;
+        memcpy(s, s0, (size_t)L * L);
+        rc = orc_run_replica(s, L, Ld, k, A, seed0 + (uint64_t)r, schedule,
+                             ORC_TIME_EXPECTED, 1.0, 1.0, 0.0, 0, n_sched, 0,
+                             esum, steps, hash, flips, NULL);
+    }
+    free(esum); free(steps); free(hash); free(flips);
+    return rc;
+}

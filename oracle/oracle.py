@@ -1,0 +1,228 @@
+"""Python side of the CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import this module.  The product library never
+touches it.  ``build()`` compiles ``kmc_oracle.c`` with gcc into
+``oracle/liborc_kmc.so``; the wrappers below only marshal arguments.
+
+Everything here follows the C file's comments: the paper's App. A energy and
+single-site kernel, Sec. 2.2 domains/halo/schedule, Sec. 2.1 clock and
+Sec. 2.3 endpoint observables (arXiv:1403.4674).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "kmc_oracle.c")
+LIB = os.path.join(HERE, "liborc_kmc.so")
+
+RATE_METROPOLIS = 0
+RATE_BARKER = 1
+SCHED_PALINDROME = 0
+SCHED_FIXED = 1
+SCHED_RANDOM_PERM = 2
+TIME_EXPONENTIAL = 0
+TIME_EXPECTED = 1
+INIT_RANDOM = 0
+INIT_ALL_UP = 1
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, gcc, no FP contraction)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i8p = ctypes.POINTER(ctypes.c_int8)
+        L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_philox4x32_10.restype = None
+        L.orc_rate_table.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int, dp, u64p]
+        L.orc_rate_table.restype = ctypes.c_int
+        L.orc_class_dE.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_class_dE.restype = ctypes.c_double
+        L.orc_init_spins.argtypes = [i8p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
+        L.orc_init_spins.restype = None
+        L.orc_schedule_colours.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.POINTER(ctypes.c_int)]
+        L.orc_schedule_colours.restype = ctypes.c_int
+        L.orc_energy_mag.argtypes = [i8p, ctypes.c_int, i64p, i64p]
+        L.orc_energy_mag.restype = None
+        L.orc_domain_time.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                      ctypes.c_int, ctypes.c_double]
+        L.orc_domain_time.restype = ctypes.c_double
+        L.orc_run_replica.argtypes = [i8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p,
+                                      ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                      dp, i64p, u64p, i64p, dp]
+        L.orc_run_replica.restype = ctypes.c_int
+        L.orc_sample_final_states.argtypes = [i8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              u64p, ctypes.c_uint64, ctypes.c_int64,
+                                              ctypes.c_int, ctypes.c_int64, i8p]
+        L.orc_sample_final_states.restype = ctypes.c_int
+        L.orc_hash_basis.argtypes = []
+        L.orc_hash_basis.restype = ctypes.c_uint64
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
+                            _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def rate_table(J: float, beta: float, h: float, law: int, log2_nd: int):
+    """Returns (a[10] float64, A[10] uint64): App. A acceptance, fixed point."""
+    a = np.zeros(10, dtype=np.float64)
+    A = np.zeros(10, dtype=np.uint64)
+    rc = lib().orc_rate_table(J, beta, h, law, log2_nd, _ptr(a, ctypes.c_double),
+                              _ptr(A, ctypes.c_uint64))
+    if rc != 0:
+        raise ValueError("invalid rate-table arguments")
+    return a, A
+
+
+def class_dE(c: int, J: float, h: float) -> float:
+    return lib().orc_class_dE(c, J, h)
+
+
+def init_spins(L: int, init: int, seed: int) -> np.ndarray:
+    s = np.zeros(L * L, dtype=np.int8)
+    lib().orc_init_spins(_ptr(s, ctypes.c_int8), L, init, seed)
+    return s.reshape(L, L)
+
+
+def schedule_colours(schedule: int, n: int, seed: int):
+    out = (ctypes.c_int * 8)()
+    nph = lib().orc_schedule_colours(schedule, n, seed, out)
+    if nph < 0:
+        raise ValueError("bad schedule")
+    return [out[i] for i in range(nph)]
+
+
+def energy_mag(s: np.ndarray):
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    L = s.shape[0]
+    b = ctypes.c_int64()
+    m = ctypes.c_int64()
+    lib().orc_energy_mag(_ptr(s, ctypes.c_int8), L, ctypes.byref(b), ctypes.byref(m))
+    return b.value, m.value
+
+
+def sample_final_states(s0: np.ndarray, Ld: int, k: int, A: np.ndarray, seed0: int,
+                        n_runs: int, n_sched: int, schedule: int = SCHED_PALINDROME):
+    """Final states of n_runs independent runs (seeds seed0..seed0+n_runs-1) from s0."""
+    s0 = np.ascontiguousarray(s0, dtype=np.int8)
+    L = s0.shape[0]
+    A = np.ascontiguousarray(A, dtype=np.uint64)
+    out = np.zeros((n_runs, L, L), dtype=np.int8)
+    rc = lib().orc_sample_final_states(_ptr(s0, ctypes.c_int8), L, Ld, k,
+                                       _ptr(A, ctypes.c_uint64), seed0, n_runs, schedule,
+                                       n_sched, _ptr(out, ctypes.c_int8))
+    if rc != 0:
+        raise ValueError("oracle rejected the configuration")
+    return out
+
+
+@dataclass
+class Replica:
+    """One lattice replica and its per-domain counters (oracle side)."""
+    L: int
+    Ld: int
+    k: int
+    seed: int
+    beta: float
+    J: float = 1.0
+    h: float = 0.0
+    nu: float = 1.0
+    law: int = RATE_METROPOLIS
+    init: int = INIT_RANDOM
+    spins: np.ndarray = field(default=None)
+    esum: np.ndarray = field(default=None)
+    steps: np.ndarray = field(default=None)
+    hash: np.ndarray = field(default=None)
+    flips: np.ndarray = field(default=None)
+    sched_done: int = 0
+
+    def __post_init__(self):
+        if self.spins is None:
+            self.spins = init_spins(self.L, self.init, self.seed)
+        nD = (self.L // self.Ld) ** 2
+        self.esum = np.zeros(nD, dtype=np.float64)
+        self.steps = np.zeros(nD, dtype=np.int64)
+        self.hash = np.full(nD, lib().orc_hash_basis(), dtype=np.uint64)
+        self.flips = np.zeros(nD, dtype=np.int64)
+        log2nd = int(round(np.log2(self.Ld * self.Ld)))
+        self.a, self.A = rate_table(self.J, self.beta, self.h, self.law, log2nd)
+
+    @property
+    def n_domains(self) -> int:
+        return (self.L // self.Ld) ** 2
+
+    def run(self, n_sched: int, schedule: int = SCHED_PALINDROME,
+            time_mode: int = TIME_EXPONENTIAL, obs_every: int = 0) -> np.ndarray:
+        n_obs = n_sched // obs_every if obs_every > 0 else 0
+        obs = np.zeros((max(n_obs, 1), 4), dtype=np.float64)
+        s = np.ascontiguousarray(self.spins.reshape(-1))
+        A = np.ascontiguousarray(self.A)
+        rc = lib().orc_run_replica(
+            _ptr(s, ctypes.c_int8), self.L, self.Ld, self.k, _ptr(A, ctypes.c_uint64),
+            self.seed, schedule, time_mode, self.nu, self.J, self.h,
+            self.sched_done, n_sched, obs_every,
+            _ptr(self.esum, ctypes.c_double), _ptr(self.steps, ctypes.c_int64),
+            _ptr(self.hash, ctypes.c_uint64), _ptr(self.flips, ctypes.c_int64),
+            _ptr(obs, ctypes.c_double))
+        if rc != 0:
+            raise ValueError("oracle rejected the configuration")
+        self.spins = s.reshape(self.L, self.L)
+        self.sched_done += n_sched
+        return obs[:n_obs]
+
+    def domain_times(self, time_mode: int = TIME_EXPONENTIAL) -> np.ndarray:
+        nd = self.Ld * self.Ld
+        return np.array([lib().orc_domain_time(time_mode, float(self.esum[d]),
+                                               int(self.steps[d]), nd, self.nu)
+                         for d in range(self.n_domains)])
+
+    def observables(self, time_mode: int = TIME_EXPONENTIAL):
+        """(e, m, e*m, T) at the current state (Sec. 2.3 endpoint)."""
+        b, m = energy_mag(self.spins)
+        N = float(self.L * self.L)
+        e = (-self.J * float(b) - self.h * float(m)) / N
+        mm = float(m) / N
+        tsum = 0.0
+        for t in self.domain_times(time_mode):
+            tsum += float(t)
+        T = tsum / self.n_domains
+        return e, mm, e * mm, T
