@@ -1,0 +1,198 @@
+/*
+ * kmc.h -- C ABI of the GB300-native sequential-update parallel kinetic Monte
+ * Carlo library (Nilmeier & Marian, arXiv:1403.4674).
+ *
+ * The method (Sec. 2.2): the lattice is cut into equal domains; each domain
+ * process runs N_I (here k) steps with its halo frozen; domains are visited
+ * in a schedule whose reverse has the same weight (Eqs. 9-10), which makes
+ * the whole sweep obey detailed balance.  On the device, all domains of one
+ * colour run at once (Sec. 2.2: non-interacting domains may be updated
+ * simultaneously) and colours follow the palindrome 0 1 2 3 3 2 1 0.
+ *
+ * Model (App. A): 2D periodic Ising lattice, spins +-1,
+ *   H = -J sum_<ij> s_i s_j - h sum_i s_i,
+ * single-site uniformised step with acceptance a_c of the site's class
+ * c = 5*(s_i > 0) + (number of up neighbours), Metropolis or Barker
+ * (App. A, Eq. Glauber_TM).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers owned by the caller; the
+ *     library keeps them (non-owning) until kmc_destroy.  Other array
+ *     pointers are host pointers, read during the call only.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Work is enqueued asynchronously on it.
+ *   - Every call returns a kmc_status; on failure kmc_last_error(ctx)
+ *     describes it.  Argument errors return at once and leave the context
+ *     unchanged.  Device-side errors (a bounded wait that gave up, spins
+ *     that are not +-1) are raised by the next synchronising call
+ *     (kmc_sync, kmc_observables, kmc_domain_state, kmc_grad).
+ *   - One context per host thread; the library never falls back to the CPU.
+ *   - All device work uses the current CUDA device at kmc_create_lattice.
+ */
+#ifndef KMC_H
+#define KMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kmc_ctx kmc_ctx; /* opaque, library-owned */
+
+typedef enum {
+    KMC_OK = 0,
+    KMC_EINVAL = -1,       /* invalid argument or unsupported configuration */
+    KMC_ENOMEM = -2,       /* device or host allocation failed */
+    KMC_ECUDA = -3,        /* a CUDA runtime call failed */
+    KMC_ENOTBALANCED = -4, /* rate table violates detailed balance */
+    KMC_ETIMEOUT = -5,     /* a bounded device wait (phase barrier) gave up */
+    KMC_EDEVICE = -6       /* device error word set (e.g. a spin not +-1) */
+} kmc_status;
+
+enum { KMC_INIT_RANDOM = 0, KMC_INIT_ALL_UP = 1, KMC_INIT_KEEP = 2 };
+enum { KMC_RATE_METROPOLIS = 0, KMC_RATE_BARKER = 1 };
+enum {
+    KMC_SCHEDULE_PALINDROME = 0,  /* 0 1 2 3 3 2 1 0: its own reverse (Eq. 10) */
+    KMC_SCHEDULE_FIXED = 1,       /* 0 1 2 3: stationary, NOT reversible (tests) */
+    KMC_SCHEDULE_RANDOM_PERM = 2  /* uniform colour order per schedule (Eq. 10) */
+};
+enum { KMC_TIME_EXPONENTIAL = 0, KMC_TIME_EXPECTED = 1 };
+
+/*
+ * kmc_create_lattice -- bind a batch of replicas and initialise them.
+ * Sec. 2.2 (equal, fixed domains; halo = adjacent spins), App. A (lattice).
+ *   n_replicas  number of independent lattices (>= 1).
+ *   L[r]        host array: side of replica r; L[r] must be a multiple of
+ *               2*L_d (an even number of domains per side keeps the 2x2
+ *               colouring valid under periodic wrap).
+ *   L_d         domain side: 8, 16, 32 or 64 (n_d = L_d^2 sites).
+ *   k_steps     uniformised steps per domain visit (the paper's N_I),
+ *               1..65535.
+ *   init        KMC_INIT_RANDOM (iid +-1 from Philox4x32-10 keyed by the
+ *               replica seed), KMC_INIT_ALL_UP, or KMC_INIT_KEEP (use the
+ *               spins already in spins_dev; each byte must be +1 or -1).
+ *   seeds[r]    host array: 64-bit Philox key of replica r.
+ *   spins_dev   device int8 buffer, replicas concatenated, replica r at
+ *               offset sum_{q<r} L[q]^2, row-major (site (x, y) at y*L + x),
+ *               8-byte aligned.  Caller-owned; holds the state between calls.
+ *   stream      stream for the initialisation work.
+ * The whole bit-packed state must fit in on-chip shared memory of the
+ * device (about 34 MB on a GB300); larger batches return KMC_EINVAL.
+ * The rate table defaults to Metropolis at beta = 0.4, J = 1, h = 0,
+ * nu = 1 until kmc_set_rates is called.
+ */
+kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *L,
+                              int32_t L_d, int32_t k_steps, int32_t init,
+                              const uint64_t *seeds, int8_t *spins_dev, void *stream);
+
+/*
+ * kmc_set_rates -- acceptance table of App. A (Eq. Glauber_TM).
+ *   J           coupling (shared by all replicas).
+ *   beta[r], h[r]  host arrays: inverse temperature (>= 0) and field.
+ *   nu          rate prefactor (> 0); physical rate = nu * a_c.  It only
+ *               scales time: Lambda_d = n_d * nu per domain.
+ *   rate_law    KMC_RATE_METROPOLIS: a_c = min(1, exp(-beta dE_c));
+ *               KMC_RATE_BARKER:     a_c = 1 / (1 + exp(beta dE_c)),
+ *               dE_c = 2 s (J (2q - 4) + h) for class c = 5 (s>0) + q.
+ * The table is built on the host in FP64 and held in fixed point,
+ * A_c = round(a_c 2^P), P = 63 - log2(n_d), so that every trajectory
+ * decision on the device is an exact integer comparison.
+ */
+kmc_status kmc_set_rates(kmc_ctx *ctx, double J, const double *beta, const double *h,
+                         double nu, int32_t rate_law);
+
+/*
+ * kmc_set_rate_table -- user acceptance table a[r*10 + c] in (0, 1], checked
+ * against detailed balance (Eq. 4): a_c / a_cbar must equal exp(-beta dE_c)
+ * to 1e-12 relative, cbar = the same site after its flip.  Otherwise
+ * KMC_ENOTBALANCED and the previous table stays.
+ */
+kmc_status kmc_set_rate_table(kmc_ctx *ctx, double J, const double *beta, const double *h,
+                              double nu, const double *a);
+
+/*
+ * kmc_run_schedule -- run n_schedules colour schedules on every replica
+ * (Sec. 2.2, Eqs. 8-11).  One schedule visits every domain twice
+ * (PALINDROME) or once (FIXED, RANDOM_PERM); each visit is k uniformised
+ * steps with frozen halo.  The integer step counter of a replica advances by
+ * k * N_D per colour pass (Eq. 11).
+ *   time_mode   KMC_TIME_EXPONENTIAL: each step advances the domain clock by
+ *               Exp(Lambda_d) (Sec. 2.1, Erlang variate as a sum of -log u);
+ *               KMC_TIME_EXPECTED: by its mean 1/Lambda_d (the paper's
+ *               choice, Sec. 2.1).
+ *   obs_every   if > 0 and obs_dev != NULL, after every obs_every-th
+ *               schedule of this call the endpoint observables (Sec. 2.3)
+ *               of replica r go to obs_dev[(o*n_replicas + r)*4 + {0..3}] =
+ *               {e = E/N, m = M/N, e*m, T}, T = mean domain clock;
+ *               o = 0 .. n_schedules/obs_every - 1.  obs_dev is a caller
+ *               device buffer of at least that many doubles.
+ * Asynchronous; spins_dev holds the final state when the stream reaches
+ * the end of the call.
+ */
+kmc_status kmc_run_schedule(kmc_ctx *ctx, int64_t n_schedules, int32_t schedule,
+                            int32_t time_mode, int32_t obs_every, double *obs_dev,
+                            void *stream);
+
+/*
+ * kmc_observables -- synchronise and return the current endpoint observables
+ * per replica into host arrays of n_replicas entries (any may be NULL):
+ * E_per_site, m, t (mean domain clock, in the time mode of the last run),
+ * steps (uniformised steps so far, Eq. 11), flips (real events so far).
+ */
+kmc_status kmc_observables(kmc_ctx *ctx, double *E_per_site, double *m, double *t,
+                           int64_t *steps, int64_t *flips);
+
+/*
+ * kmc_grad -- likelihood-ratio score of the path so far, per replica:
+ * score_dev[r*2 + {0,1}] = d log P(path) / d{beta, h} of the uniformised
+ * jump chain (device buffer, caller-owned).  reset != 0 zeroes the accumulators after
+ * copying (a checkpointed segment boundary).  Accumulation is enabled by
+ * kmc_enable_grad.  Synchronising.
+ */
+kmc_status kmc_grad(kmc_ctx *ctx, double *score_dev, int32_t reset);
+
+/* Turn score accumulation on (enable != 0) or off for following runs. */
+kmc_status kmc_enable_grad(kmc_ctx *ctx, int32_t enable);
+
+/* Re-initialise spins from the seeds (init as in kmc_create_lattice), zero
+ * clocks, counters, scores and the schedule index.  Asynchronous. */
+kmc_status kmc_reset(kmc_ctx *ctx, int32_t init, void *stream);
+
+/* Wait for all work of the context and raise any device-side error. */
+kmc_status kmc_sync(kmc_ctx *ctx);
+
+/* Per-domain state for parity checks, host arrays of total-domain length,
+ * domains of replica r at offset sum_{q<r} (L[q]/L_d)^2, domain d = by*Dx + bx:
+ * event hash (FNV-1a over real events, see DESIGN), real-flip count and
+ * domain clock.  Any pointer may be NULL.  Synchronising. */
+kmc_status kmc_domain_state(kmc_ctx *ctx, uint64_t *hash, int64_t *flips, double *t);
+
+/* Fixed-point and FP64 acceptance table of replica r (host arrays of 10). */
+kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, uint64_t *A);
+
+/* Launch shape of the persistent kernel: ctas and warps per CTA (0 = the
+ * library's default).  Returns KMC_EINVAL if the shape cannot be
+ * co-resident or the state does not fit. */
+kmc_status kmc_set_launch(kmc_ctx *ctx, int32_t ctas, int32_t warps_per_cta);
+kmc_status kmc_get_launch(const kmc_ctx *ctx, int32_t *ctas, int32_t *warps_per_cta,
+                          int32_t *smem_bytes);
+
+/* Test hook for the bounded phase barrier: the next run's first barrier
+ * waits for `extra` arrivals that never come and gives up after limit_ns
+ * nanoseconds (KMC_ETIMEOUT at the next kmc_sync).  extra = 0 restores the
+ * normal barrier; limit_ns = 0 restores the default limit (2 s). */
+kmc_status kmc_debug_barrier(kmc_ctx *ctx, int32_t extra, int64_t limit_ns);
+
+/* Number of kernels this context launched so far (all kinds). */
+int64_t kmc_kernel_launches(const kmc_ctx *ctx);
+
+const char *kmc_last_error(const kmc_ctx *ctx);
+void kmc_destroy(kmc_ctx *ctx);
+int32_t kmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMC_H */

@@ -405,7 +405,9 @@ int orc_run_replica(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
         int nph = orc_schedule_colours(schedule, n, seed, col);
         if (nph < 0) return -1;
         for (int p = 0; p < nph; ++p) {
-            uint64_t np = n * (uint64_t)nph + (uint64_t)p;
+            /* eight phase slots per schedule index for every schedule kind,
+             * so that no two kinds ever share a Philox counter */
+            uint64_t np = n * 8u + (uint64_t)p;
             for (int d = 0; d < ND; ++d) {
                 int bx = d % Dx, by = d / Dx;
                 int colour = (bx & 1) | ((by & 1) << 1);

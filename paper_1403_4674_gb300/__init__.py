@@ -1,0 +1,17 @@
+"""GB300-native sequential-update parallel kinetic Monte Carlo.
+
+Nilmeier & Marian, "A rigorous sequential update strategy for parallel kinetic
+Monte Carlo simulation" (arXiv:1403.4674): coloured domains with frozen halos,
+a palindromic colour schedule that obeys detailed balance, uniformised
+rejection-free domain steps.  The compute path is the sm_103a library
+``libkmc_gb300.so`` behind the C ABI of ``include/kmc.h``; ``api`` is its thin
+Python binding.
+"""
+from .api import (KMC_INIT_ALL_UP, KMC_INIT_KEEP, KMC_INIT_RANDOM, KMC_RATE_BARKER,  # noqa: F401
+                  KMC_RATE_METROPOLIS, KMC_SCHEDULE_FIXED, KMC_SCHEDULE_PALINDROME,
+                  KMC_SCHEDULE_RANDOM_PERM, KMC_TIME_EXPECTED, KMC_TIME_EXPONENTIAL, Lattice,
+                  kmc_create_lattice, kmc_debug_barrier, kmc_destroy, kmc_domain_state,
+                  kmc_enable_grad, kmc_get_launch, kmc_get_rate_table, kmc_grad,
+                  kmc_kernel_launches, kmc_observables, kmc_reset, kmc_run_schedule,
+                  kmc_set_launch, kmc_set_rate_table, kmc_set_rates, kmc_sync, kmc_version)
+from ._lib import KmcError  # noqa: F401

@@ -1,0 +1,87 @@
+"""ctypes loader for libkmc_gb300.so (the C ABI of include/kmc.h).
+
+There is no CPU fallback: if the shared library is missing or cannot be
+loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+_LIB = None
+
+# kmc_status codes
+KMC_OK = 0
+KMC_EINVAL = -1
+KMC_ENOMEM = -2
+KMC_ECUDA = -3
+KMC_ENOTBALANCED = -4
+KMC_ETIMEOUT = -5
+KMC_EDEVICE = -6
+
+STATUS_NAMES = {0: "KMC_OK", -1: "KMC_EINVAL", -2: "KMC_ENOMEM", -3: "KMC_ECUDA",
+                -4: "KMC_ENOTBALANCED", -5: "KMC_ETIMEOUT", -6: "KMC_EDEVICE"}
+
+#: every symbol include/kmc.h declares
+EXPORTS = [
+    "kmc_create_lattice", "kmc_set_rates", "kmc_set_rate_table", "kmc_run_schedule",
+    "kmc_observables", "kmc_grad", "kmc_enable_grad", "kmc_reset", "kmc_sync",
+    "kmc_domain_state", "kmc_get_rate_table", "kmc_set_launch", "kmc_get_launch",
+    "kmc_debug_barrier", "kmc_kernel_launches", "kmc_last_error", "kmc_destroy", "kmc_version",
+]
+
+
+class KmcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load the library (building it first if allowed and needed)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError("libkmc_gb300.so is not built (%s); run python -m paper_1403_4674_gb300.build" % path)
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    P = ctypes.POINTER
+    L.kmc_create_lattice.argtypes = [P(vp), i32, P(i32), i32, i32, i32, P(u64), vp, vp]
+    L.kmc_set_rates.argtypes = [vp, dbl, P(dbl), P(dbl), dbl, i32]
+    L.kmc_set_rate_table.argtypes = [vp, dbl, P(dbl), P(dbl), dbl, P(dbl)]
+    L.kmc_run_schedule.argtypes = [vp, i64, i32, i32, i32, vp, vp]
+    L.kmc_observables.argtypes = [vp, P(dbl), P(dbl), P(dbl), P(i64), P(i64)]
+    L.kmc_grad.argtypes = [vp, vp, i32]
+    L.kmc_enable_grad.argtypes = [vp, i32]
+    L.kmc_reset.argtypes = [vp, i32, vp]
+    L.kmc_sync.argtypes = [vp]
+    L.kmc_domain_state.argtypes = [vp, P(u64), P(i64), P(dbl)]
+    L.kmc_get_rate_table.argtypes = [vp, i32, P(dbl), P(u64)]
+    L.kmc_set_launch.argtypes = [vp, i32, i32]
+    L.kmc_get_launch.argtypes = [vp, P(i32), P(i32), P(i32)]
+    L.kmc_debug_barrier.argtypes = [vp, i32, i64]
+    L.kmc_kernel_launches.argtypes = [vp]
+    L.kmc_kernel_launches.restype = i64
+    L.kmc_last_error.argtypes = [vp]
+    L.kmc_last_error.restype = ctypes.c_char_p
+    L.kmc_destroy.argtypes = [vp]
+    L.kmc_destroy.restype = None
+    L.kmc_version.argtypes = []
+    L.kmc_version.restype = i32
+    for name in EXPORTS:
+        fn = getattr(L, name)
+        if fn.restype is ctypes.c_int:  # default restype: kmc_status
+            fn.restype = ctypes.c_int
+    _LIB = L
+    return L

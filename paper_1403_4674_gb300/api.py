@@ -1,0 +1,244 @@
+"""Thin Python binding of the C ABI (include/kmc.h), same names.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+(libkmc_gb300.so).  PyTorch provides the device buffers and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from ._lib import KmcError, load
+
+KMC_INIT_RANDOM, KMC_INIT_ALL_UP, KMC_INIT_KEEP = 0, 1, 2
+KMC_RATE_METROPOLIS, KMC_RATE_BARKER = 0, 1
+KMC_SCHEDULE_PALINDROME, KMC_SCHEDULE_FIXED, KMC_SCHEDULE_RANDOM_PERM = 0, 1, 2
+KMC_TIME_EXPONENTIAL, KMC_TIME_EXPECTED = 0, 1
+
+_i32, _i64, _u64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+
+
+def _arr(values, ctype):
+    vals = list(values)
+    return (ctype * len(vals))(*vals)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _check(ctx, status: int):
+    if status != 0:
+        msg = load().kmc_last_error(ctx)
+        raise KmcError(status, msg.decode() if msg else "")
+
+
+def kmc_version() -> int:
+    return load().kmc_version()
+
+
+def kmc_create_lattice(L: Sequence[int], L_d: int, k_steps: int, init: int, seeds: Sequence[int],
+                       spins_dev: torch.Tensor, stream=None) -> ctypes.c_void_p:
+    lib = load()
+    if not torch.cuda.is_available():
+        raise KmcError(-3, "no CUDA device: the library has no CPU path")
+    if spins_dev.dtype != torch.int8 or not spins_dev.is_cuda or not spins_dev.is_contiguous():
+        raise KmcError(-1, "spins_dev must be a contiguous int8 CUDA tensor")
+    need = sum(int(x) * int(x) for x in L)
+    if spins_dev.numel() < need:
+        raise KmcError(-1, "spins_dev holds %d bytes, %d needed" % (spins_dev.numel(), need))
+    ctx = ctypes.c_void_p()
+    st = lib.kmc_create_lattice(ctypes.byref(ctx), len(L), _arr(L, _i32), L_d, k_steps, init,
+                                _arr(seeds, _u64), ctypes.c_void_p(spins_dev.data_ptr()),
+                                ctypes.c_void_p(_stream_handle(stream)))
+    if st != 0:
+        msg = lib.kmc_last_error(ctx).decode() if ctx.value else ""
+        if ctx.value:
+            lib.kmc_destroy(ctx)
+        raise KmcError(st, msg)
+    return ctx
+
+
+def kmc_set_rates(ctx, J: float, beta: Sequence[float], h: Sequence[float], nu: float, rate_law: int):
+    _check(ctx, load().kmc_set_rates(ctx, J, _arr(beta, _dbl), _arr(h, _dbl), nu, rate_law))
+
+
+def kmc_set_rate_table(ctx, J: float, beta, h, nu: float, a: np.ndarray):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    _check(ctx, load().kmc_set_rate_table(ctx, J, _arr(beta, _dbl), _arr(h, _dbl), nu,
+                                          a.ctypes.data_as(ctypes.POINTER(_dbl))))
+
+
+def kmc_run_schedule(ctx, n_schedules: int, schedule: int, time_mode: int, obs_every: int,
+                     obs_dev: Optional[torch.Tensor], stream=None):
+    ptr = ctypes.c_void_p(obs_dev.data_ptr()) if obs_dev is not None else ctypes.c_void_p()
+    if obs_dev is not None and (obs_dev.dtype != torch.float64 or not obs_dev.is_cuda):
+        raise KmcError(-1, "obs_dev must be a float64 CUDA tensor")
+    _check(ctx, load().kmc_run_schedule(ctx, n_schedules, schedule, time_mode, obs_every, ptr,
+                                        ctypes.c_void_p(_stream_handle(stream))))
+
+
+def kmc_observables(ctx, n_replicas: int):
+    e, m, t = ((_dbl * n_replicas)() for _ in range(3))
+    steps, flips = (_i64 * n_replicas)(), (_i64 * n_replicas)()
+    _check(ctx, load().kmc_observables(ctx, e, m, t, steps, flips))
+    return {"e": np.array(e[:]), "m": np.array(m[:]), "t": np.array(t[:]),
+            "steps": np.array(steps[:], dtype=np.int64), "flips": np.array(flips[:], dtype=np.int64)}
+
+
+def kmc_domain_state(ctx, n_domains: int):
+    hs, fl, tt = (_u64 * n_domains)(), (_i64 * n_domains)(), (_dbl * n_domains)()
+    _check(ctx, load().kmc_domain_state(ctx, hs, fl, tt))
+    return (np.array(hs[:], dtype=np.uint64), np.array(fl[:], dtype=np.int64),
+            np.array(tt[:], dtype=np.float64))
+
+
+def kmc_get_rate_table(ctx, replica: int):
+    a, A = (_dbl * 10)(), (_u64 * 10)()
+    _check(ctx, load().kmc_get_rate_table(ctx, replica, a, A))
+    return np.array(a[:]), np.array(A[:], dtype=np.uint64)
+
+
+def kmc_grad(ctx, score_dev: torch.Tensor, reset: int = 0):
+    if score_dev.dtype != torch.float64 or not score_dev.is_cuda:
+        raise KmcError(-1, "score_dev must be a float64 CUDA tensor")
+    _check(ctx, load().kmc_grad(ctx, ctypes.c_void_p(score_dev.data_ptr()), reset))
+
+
+def kmc_enable_grad(ctx, enable: bool):
+    _check(ctx, load().kmc_enable_grad(ctx, int(bool(enable))))
+
+
+def kmc_reset(ctx, init: int, stream=None):
+    _check(ctx, load().kmc_reset(ctx, init, ctypes.c_void_p(_stream_handle(stream))))
+
+
+def kmc_sync(ctx):
+    _check(ctx, load().kmc_sync(ctx))
+
+
+def kmc_set_launch(ctx, ctas: int, warps_per_cta: int):
+    _check(ctx, load().kmc_set_launch(ctx, ctas, warps_per_cta))
+
+
+def kmc_get_launch(ctx):
+    a, b, c = _i32(), _i32(), _i32()
+    _check(ctx, load().kmc_get_launch(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def kmc_debug_barrier(ctx, extra: int, limit_ns: int):
+    _check(ctx, load().kmc_debug_barrier(ctx, extra, limit_ns))
+
+
+def kmc_kernel_launches(ctx) -> int:
+    return load().kmc_kernel_launches(ctx)
+
+
+def kmc_destroy(ctx):
+    if ctx is not None and ctx.value:
+        load().kmc_destroy(ctx)
+
+
+class Lattice:
+    """A batch of replicas bound to one library context (convenience wrapper).
+
+    spins: int8 CUDA tensor, replicas concatenated row-major (allocated here
+    unless given).  Methods map one-to-one onto the C entry points.
+    """
+
+    def __init__(self, L: Sequence[int], L_d: int, k: int, seeds: Sequence[int],
+                 init: int = KMC_INIT_RANDOM, spins: Optional[torch.Tensor] = None, stream=None,
+                 device: Optional[torch.device] = None):
+        self.L = [int(x) for x in L]
+        self.L_d = int(L_d)
+        self.k = int(k)
+        self.seeds = [int(s) for s in seeds]
+        total = sum(x * x for x in self.L)
+        if spins is None:
+            dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+            spins = torch.empty(total, dtype=torch.int8, device=dev)
+        self.spins = spins
+        self.offsets = np.concatenate([[0], np.cumsum([x * x for x in self.L])]).astype(np.int64)
+        self.dom_offsets = np.concatenate([[0], np.cumsum([(x // self.L_d) ** 2 for x in self.L])]).astype(np.int64)
+        self.ctx = kmc_create_lattice(self.L, self.L_d, self.k, init, self.seeds, self.spins, stream)
+        self.grad_enabled = False
+
+    @property
+    def n_replicas(self) -> int:
+        return len(self.L)
+
+    @property
+    def n_domains(self) -> int:
+        return int(self.dom_offsets[-1])
+
+    def replica_spins(self, r: int) -> torch.Tensor:
+        a, b = int(self.offsets[r]), int(self.offsets[r + 1])
+        return self.spins[a:b].view(self.L[r], self.L[r])
+
+    def set_rates(self, beta, h=None, J: float = 1.0, nu: float = 1.0, law: int = KMC_RATE_METROPOLIS):
+        beta = np.broadcast_to(np.asarray(beta, dtype=np.float64), (self.n_replicas,))
+        h = np.zeros(self.n_replicas) if h is None else np.broadcast_to(np.asarray(h, dtype=np.float64), (self.n_replicas,))
+        self.J = J
+        kmc_set_rates(self.ctx, J, beta.tolist(), h.tolist(), nu, law)
+
+    def run(self, n_schedules: int, schedule: int = KMC_SCHEDULE_PALINDROME,
+            time_mode: int = KMC_TIME_EXPONENTIAL, obs_every: int = 0, stream=None) -> Optional[torch.Tensor]:
+        obs = None
+        if obs_every > 0 and n_schedules // obs_every > 0:
+            width = 6 if self.grad_enabled else 4
+            obs = torch.empty((n_schedules // obs_every, self.n_replicas, width), dtype=torch.float64,
+                              device=self.spins.device)
+        kmc_run_schedule(self.ctx, n_schedules, schedule, time_mode, obs_every, obs, stream)
+        return obs
+
+    def observables(self):
+        return kmc_observables(self.ctx, self.n_replicas)
+
+    def domain_state(self):
+        return kmc_domain_state(self.ctx, self.n_domains)
+
+    def rate_table(self, r: int = 0):
+        return kmc_get_rate_table(self.ctx, r)
+
+    def enable_grad(self, enable: bool = True):
+        kmc_enable_grad(self.ctx, enable)
+        self.grad_enabled = bool(enable)
+
+    def score(self, reset: bool = False) -> torch.Tensor:
+        out = torch.empty((self.n_replicas, 2), dtype=torch.float64, device=self.spins.device)
+        kmc_grad(self.ctx, out, int(reset))
+        return out
+
+    def reset(self, init: int = KMC_INIT_RANDOM, stream=None):
+        kmc_reset(self.ctx, init, stream)
+
+    def sync(self):
+        kmc_sync(self.ctx)
+
+    def set_launch(self, ctas: int, warps_per_cta: int):
+        kmc_set_launch(self.ctx, ctas, warps_per_cta)
+
+    def launch(self):
+        return kmc_get_launch(self.ctx)
+
+    def kernel_launches(self) -> int:
+        return kmc_kernel_launches(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            kmc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

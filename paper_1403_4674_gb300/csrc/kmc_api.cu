@@ -1,0 +1,809 @@
+// kmc_api.cu -- host side of the C ABI declared in include/kmc.h.
+//
+// Owns the library's device scratch (bit tiles, edges, per-domain counters,
+// work lists, rate tables, barrier counter, error word), validates
+// arguments, builds the fixed-point rate table on the host and enqueues the
+// kernels of kmc_kernels.cuh on the caller's stream.
+#include "kmc.h"
+#include "kmc_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace kmcdev;
+
+struct kmc_ctx {
+    int dev = 0;
+    int n_rep = 0;
+    int LD = 0;
+    int log2nd = 0;
+    int k = 1;
+    std::vector<int32_t> L, Dx;
+    std::vector<uint64_t> seed;
+    std::vector<uint32_t> dom_off;   // n_rep + 1
+    std::vector<uint64_t> site_off;  // n_rep
+    std::vector<uint64_t> blk_off;   // n_rep + 1
+    int n_dom = 0;
+    int8_t *spins = nullptr;
+    cudaStream_t stream = nullptr;
+
+    int32_t *d_L = nullptr, *d_Dx = nullptr;
+    uint32_t *d_dom_off = nullptr, *d_dom_rep = nullptr;
+    uint64_t *d_site_off = nullptr, *d_blk_off = nullptr, *d_seed = nullptr;
+    uint64_t *d_A = nullptr, *d_inv = nullptr;
+    double *d_grad = nullptr, *d_h = nullptr;
+    uint64_t *d_list[4] = {nullptr, nullptr, nullptr, nullptr};
+    int n_list[4] = {0, 0, 0, 0};
+    uint8_t *d_tiles = nullptr;
+    uint64_t *d_edges = nullptr, *d_dctr = nullptr;
+    unsigned *d_bar = nullptr;
+    int *d_err = nullptr;
+    unsigned long long *d_obs_acc = nullptr;
+    size_t obs_acc_words = 0;
+    void *d_tmp = nullptr; // n_dom * 24 bytes, host-facing staging
+
+    double J = 1.0, nu = 1.0;
+    std::vector<double> beta, h, a, gb, gh;
+    std::vector<uint64_t> A, inv;
+    int law = KMC_RATE_METROPOLIS;
+
+    int64_t sched_done = 0;
+    int64_t visits_done = 0;
+    int last_time_mode = KMC_TIME_EXPONENTIAL;
+    bool grad = false;
+
+    int sm_count = 0, smem_optin = 0;
+    int ctas = 0, wpb = 0, slots_per_warp = 0, slot_bytes = 0, smem_bytes = 0;
+    int64_t launches = 0;
+    int debug_extra = 0;
+    uint64_t bar_limit_ns = 2000000000ull;
+    std::string err;
+};
+
+namespace {
+
+const uint64_t DEFAULT_BAR_LIMIT_NS = 2000000000ull;
+
+kmc_status fail(kmc_ctx *c, kmc_status s, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), KMC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+int ld_index(int LD) { return LD == 8 ? 0 : LD == 16 ? 1 : LD == 32 ? 2 : LD == 64 ? 3 : -1; }
+
+// Acceptance table (App. A, Eq. Glauber_TM): FP64 a_c, fixed point A_c =
+// round(a_c 2^P), P = 63 - log2(n_d), reciprocal floor((2^64-1)/A_c) and the
+// score derivatives d log a_c / d beta, d log a_c / d h.
+void build_table(double J, double beta, double h, int law, int log2nd, double *a, uint64_t *A,
+                 uint64_t *inv, double *gb, double *gh)
+{
+    const int P = 63 - log2nd;
+    for (int c = 0; c < 10; ++c) {
+        const int up = c / 5, q = c % 5;
+        const double sigma = up ? 1.0 : -1.0;
+        const double dE = 2.0 * sigma * (J * (double)(2 * q - 4) + h);
+        double ac, dlb, dlh;
+        if (law == KMC_RATE_METROPOLIS) {
+            if (dE <= 0.0) {
+                ac = 1.0;
+                dlb = 0.0;
+                dlh = 0.0;
+            } else {
+                ac = std::exp(-beta * dE);
+                dlb = -dE;
+                dlh = -beta * 2.0 * sigma;
+            }
+        } else {
+            ac = 1.0 / (1.0 + std::exp(beta * dE));
+            dlb = -dE * (1.0 - ac);
+            dlh = -beta * 2.0 * sigma * (1.0 - ac);
+        }
+        a[c] = ac;
+        A[c] = (uint64_t)std::nearbyint(std::ldexp(ac, P));
+        inv[c] = A[c] ? (~0ull) / A[c] : 0ull;
+        gb[c] = dlb;
+        gh[c] = dlh;
+    }
+}
+
+template <typename T>
+kmc_status dev_alloc(kmc_ctx *c, T **p, size_t n)
+{
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) return fail(c, KMC_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    return KMC_OK;
+}
+
+template <typename T>
+kmc_status upload(kmc_ctx *c, T *dst, const T *src, size_t n, cudaStream_t s)
+{
+    CUDA_TRY(c, cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return KMC_OK;
+}
+
+using RunKernel = void (*)(const RunParams);
+
+RunKernel run_kernel_for(int LD, bool expo, bool grad)
+{
+#define KMC_PICK(LDV)                                                                       \
+    if (LD == LDV) {                                                                        \
+        if (expo) return grad ? run_kernel<LDV, true, true> : run_kernel<LDV, true, false>; \
+        return grad ? run_kernel<LDV, false, true> : run_kernel<LDV, false, false>;         \
+    }
+    KMC_PICK(8)
+    KMC_PICK(16)
+    KMC_PICK(32)
+    KMC_PICK(64)
+#undef KMC_PICK
+    return nullptr;
+}
+
+LayoutParams layout_params(kmc_ctx *c)
+{
+    LayoutParams P;
+    P.n_rep = c->n_rep;
+    P.n_dom = c->n_dom;
+    P.rep_L = c->d_L;
+    P.rep_Dx = c->d_Dx;
+    P.rep_dom_off = c->d_dom_off;
+    P.rep_site_off = c->d_site_off;
+    P.rep_blk_off = c->d_blk_off;
+    P.rep_seed = c->d_seed;
+    P.dom_rep = c->d_dom_rep;
+    P.spins = c->spins;
+    P.tiles = c->d_tiles;
+    P.edges = c->d_edges;
+    P.dctr = c->d_dctr;
+    P.err = c->d_err;
+    return P;
+}
+
+RunParams run_params(kmc_ctx *c)
+{
+    RunParams P;
+    std::memset(&P, 0, sizeof P);
+    P.n_rep = c->n_rep;
+    P.k = c->k;
+    P.rep_Dx = c->d_Dx;
+    P.rep_dom_off = c->d_dom_off;
+    P.rep_seed = c->d_seed;
+    P.rep_A = c->d_A;
+    P.rep_inv = c->d_inv;
+    P.rep_grad = c->d_grad;
+    for (int q = 0; q < 4; ++q) {
+        P.list[q] = c->d_list[q];
+        P.n_list[q] = c->n_list[q];
+    }
+    P.tiles = c->d_tiles;
+    P.dctr = c->d_dctr;
+    P.edges = c->d_edges;
+    P.bar_count = c->d_bar;
+    P.err = c->d_err;
+    P.bar_limit_ns = c->bar_limit_ns;
+    P.debug_extra = c->debug_extra;
+    P.total_warps = c->ctas * c->wpb;
+    P.slots_per_warp = c->slots_per_warp;
+    P.slot_bytes = c->slot_bytes;
+    P.lambda = (double)(c->LD * c->LD) * c->nu;
+    return P;
+}
+
+int grid_for(int n_items, int per_block)
+{
+    int g = (n_items + per_block - 1) / per_block;
+    return std::max(1, std::min(g, 65535));
+}
+
+kmc_status launch_pack(kmc_ctx *c, cudaStream_t s)
+{
+    LayoutParams P = layout_params(c);
+    const int blocks = grid_for(c->n_dom, 8);
+    switch (c->LD) {
+    case 8: pack_kernel<8><<<blocks, 256, 0, s>>>(P); break;
+    case 16: pack_kernel<16><<<blocks, 256, 0, s>>>(P); break;
+    case 32: pack_kernel<32><<<blocks, 256, 0, s>>>(P); break;
+    default: pack_kernel<64><<<blocks, 256, 0, s>>>(P); break;
+    }
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    return KMC_OK;
+}
+
+kmc_status launch_unpack(kmc_ctx *c, cudaStream_t s)
+{
+    LayoutParams P = layout_params(c);
+    const int blocks = grid_for(c->n_dom, 8);
+    switch (c->LD) {
+    case 8: unpack_kernel<8><<<blocks, 256, 0, s>>>(P); break;
+    case 16: unpack_kernel<16><<<blocks, 256, 0, s>>>(P); break;
+    case 32: unpack_kernel<32><<<blocks, 256, 0, s>>>(P); break;
+    default: unpack_kernel<64><<<blocks, 256, 0, s>>>(P); break;
+    }
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    return KMC_OK;
+}
+
+kmc_status launch_init(kmc_ctx *c, int init, cudaStream_t s)
+{
+    LayoutParams P = layout_params(c);
+    const uint64_t total = c->blk_off[c->n_rep];
+    const int blocks = (int)std::min<uint64_t>((total + 255) / 256, 65535);
+    init_spins_kernel<<<std::max(blocks, 1), 256, 0, s>>>(P, init);
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    return KMC_OK;
+}
+
+kmc_status launch_reset_counters(kmc_ctx *c, cudaStream_t s)
+{
+    reset_counters_kernel<<<grid_for(c->n_dom, 256), 256, 0, s>>>(c->d_dctr, c->n_dom);
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    return KMC_OK;
+}
+
+// Validate a launch shape: shared memory and co-residency.
+kmc_status check_shape(kmc_ctx *c, int ctas, int wpb, bool grad_variant, int *spw_out, int *slot_out,
+                       int *smem_out)
+{
+    if (ctas < 1 || wpb < 1 || wpb > 16) return fail(c, KMC_EINVAL, "launch shape %d x %d out of range", ctas, wpb);
+    const int W = ctas * wpb;
+    int spw = 0;
+    for (int q = 0; q < 4; ++q) spw += (c->n_list[q] + W - 1) / W;
+    const int tile = c->LD * c->LD / 8;
+    const int slot = ((tile + DCTR_WORDS * 8) + 15) / 16 * 16;
+    const size_t smem = (size_t)wpb * spw * slot;
+    if (smem > (size_t)c->smem_optin)
+        return fail(c, KMC_EINVAL, "state does not fit: %zu bytes of shared memory per CTA needed, %d available",
+                    smem, c->smem_optin);
+    for (int e = 0; e < 2; ++e) {
+        RunKernel kern = run_kernel_for(c->LD, e == 0, grad_variant);
+        CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int nb = 0;
+        CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)kern, wpb * 32, smem));
+        if ((int64_t)nb * c->sm_count < ctas)
+            return fail(c, KMC_EINVAL, "%d CTAs of %d warps cannot be co-resident (%d per SM)", ctas, wpb, nb);
+    }
+    *spw_out = spw;
+    *slot_out = slot;
+    *smem_out = (int)smem;
+    return KMC_OK;
+}
+
+kmc_status default_shape(kmc_ctx *c)
+{
+    int maxn = 0;
+    for (int q = 0; q < 4; ++q) maxn = std::max(maxn, c->n_list[q]);
+    const int want = std::min(maxn, c->sm_count * 16);
+    int wpb = std::max(1, std::min(16, (want + c->sm_count - 1) / c->sm_count));
+    std::string last;
+    for (; wpb >= 1; --wpb) {
+        const int ctas = std::min((want + wpb - 1) / wpb, c->sm_count);
+        int spw, slot, smem;
+        if (check_shape(c, ctas, wpb, c->grad, &spw, &slot, &smem) == KMC_OK &&
+            check_shape(c, ctas, wpb, !c->grad, &spw, &slot, &smem) == KMC_OK) {
+            c->ctas = ctas;
+            c->wpb = wpb;
+            c->slots_per_warp = spw;
+            c->slot_bytes = slot;
+            c->smem_bytes = smem;
+            return KMC_OK;
+        }
+        last = c->err;
+    }
+    return fail(c, KMC_EINVAL, "no valid launch shape: %s", last.c_str());
+}
+
+kmc_status upload_rates(kmc_ctx *c)
+{
+    std::vector<uint64_t> A16((size_t)c->n_rep * 16, 0), inv16((size_t)c->n_rep * 16, 0);
+    std::vector<double> g32((size_t)c->n_rep * 32, 0.0);
+    for (int r = 0; r < c->n_rep; ++r) {
+        for (int q = 0; q < 10; ++q) {
+            A16[(size_t)r * 16 + q] = c->A[(size_t)r * 10 + q];
+            inv16[(size_t)r * 16 + q] = c->inv[(size_t)r * 10 + q];
+            g32[(size_t)r * 32 + q] = c->a[(size_t)r * 10 + q];
+            g32[(size_t)r * 32 + 10 + q] = c->gb[(size_t)r * 10 + q];
+            g32[(size_t)r * 32 + 20 + q] = c->gh[(size_t)r * 10 + q];
+        }
+    }
+    // synchronous copies: the host vectors are temporaries
+    CUDA_TRY(c, cudaMemcpy(c->d_A, A16.data(), A16.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_inv, inv16.data(), inv16.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_grad, g32.data(), g32.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_h, c->h.data(), c->h.size() * 8, cudaMemcpyHostToDevice));
+    return KMC_OK;
+}
+
+kmc_status check_device_error(kmc_ctx *c)
+{
+    int e = 0;
+    CUDA_TRY(c, cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
+    if (e == 0) return KMC_OK;
+    int zero = 0;
+    CUDA_TRY(c, cudaMemcpy(c->d_err, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    if (e == ERR_TIMEOUT) return fail(c, KMC_ETIMEOUT, "a phase barrier gave up waiting (bounded wait)");
+    if (e == ERR_SPIN) return fail(c, KMC_EDEVICE, "spin buffer holds a byte that is not +1 or -1");
+    return fail(c, KMC_EDEVICE, "device error word %d", e);
+}
+
+kmc_status sync_ctx(kmc_ctx *c)
+{
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
+}
+
+void free_all(kmc_ctx *c)
+{
+    void **ptrs[] = {(void **)&c->d_L, (void **)&c->d_Dx, (void **)&c->d_dom_off, (void **)&c->d_dom_rep,
+                     (void **)&c->d_site_off, (void **)&c->d_blk_off, (void **)&c->d_seed, (void **)&c->d_A,
+                     (void **)&c->d_inv, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_list[0],
+                     (void **)&c->d_list[1], (void **)&c->d_list[2], (void **)&c->d_list[3],
+                     (void **)&c->d_tiles, (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_bar,
+                     (void **)&c->d_err, (void **)&c->d_obs_acc, (void **)&c->d_tmp};
+    for (void **p : ptrs) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    c->obs_acc_words = 0;
+}
+
+} // namespace
+
+extern "C" {
+
+int32_t kmc_version(void) { return 10000; }
+
+const char *kmc_last_error(const kmc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t kmc_kernel_launches(const kmc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *L, int32_t L_d,
+                              int32_t k_steps, int32_t init, const uint64_t *seeds, int8_t *spins_dev,
+                              void *stream)
+{
+    if (!out) return KMC_EINVAL;
+    *out = nullptr;
+    kmc_ctx *c = new (std::nothrow) kmc_ctx();
+    if (!c) return KMC_ENOMEM;
+    auto bail = [&](kmc_status s) {
+        free_all(c);
+        // keep the context so that kmc_last_error works; caller destroys it
+        *out = c;
+        return s;
+    };
+    if (n_replicas < 1 || !L || !seeds || !spins_dev)
+        return bail(fail(c, KMC_EINVAL, "n_replicas >= 1 and non-null L, seeds, spins_dev required"));
+    if (ld_index(L_d) < 0) return bail(fail(c, KMC_EINVAL, "L_d must be 8, 16, 32 or 64 (got %d)", L_d));
+    if (k_steps < 1 || k_steps > 65535) return bail(fail(c, KMC_EINVAL, "k_steps must be in 1..65535"));
+    if (init < KMC_INIT_RANDOM || init > KMC_INIT_KEEP) return bail(fail(c, KMC_EINVAL, "bad init mode"));
+    if (((uintptr_t)spins_dev) % 8 != 0) return bail(fail(c, KMC_EINVAL, "spins_dev must be 8-byte aligned"));
+    c->n_rep = n_replicas;
+    c->LD = L_d;
+    c->log2nd = 2 * (L_d == 8 ? 3 : L_d == 16 ? 4 : L_d == 32 ? 5 : 6);
+    c->k = k_steps;
+    c->spins = spins_dev;
+    c->stream = (cudaStream_t)stream;
+    c->L.assign(L, L + n_replicas);
+    c->seed.assign(seeds, seeds + n_replicas);
+    c->Dx.resize(n_replicas);
+    c->dom_off.assign(n_replicas + 1, 0);
+    c->site_off.assign(n_replicas, 0);
+    c->blk_off.assign(n_replicas + 1, 0);
+    uint64_t site = 0, ndom = 0, blk = 0;
+    for (int r = 0; r < n_replicas; ++r) {
+        const int Lr = L[r];
+        if (Lr < 2 * L_d || Lr % (2 * L_d) != 0 || Lr > 65536)
+            return bail(fail(c, KMC_EINVAL, "replica %d: L = %d must be a positive multiple of 2*L_d = %d", r, Lr, 2 * L_d));
+        c->Dx[r] = Lr / L_d;
+        c->site_off[r] = site;
+        c->dom_off[r] = (uint32_t)ndom;
+        c->blk_off[r] = blk;
+        site += (uint64_t)Lr * Lr;
+        ndom += (uint64_t)c->Dx[r] * c->Dx[r];
+        blk += (uint64_t)Lr * Lr / 128;
+    }
+    if (ndom >= (1ull << 31)) return bail(fail(c, KMC_EINVAL, "too many domains"));
+    c->dom_off[n_replicas] = (uint32_t)ndom;
+    c->blk_off[n_replicas] = blk;
+    c->n_dom = (int)ndom;
+
+    cudaError_t ce = cudaGetDevice(&c->dev);
+    if (ce != cudaSuccess) return bail(fail(c, KMC_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)));
+    ce = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
+    if (ce != cudaSuccess) return bail(fail(c, KMC_ECUDA, "device attributes: %s", cudaGetErrorString(ce)));
+    c->smem_optin -= 1024; // static shared memory of the kernel (barrier flag) and slack
+
+    // work lists per colour: entries (g << 32 | r), ascending g
+    std::vector<uint64_t> lists[4];
+    std::vector<uint32_t> dom_rep(ndom);
+    for (int r = 0; r < n_replicas; ++r) {
+        const int D = c->Dx[r];
+        for (int d = 0; d < D * D; ++d) {
+            const int bx = d % D, by = d / D;
+            const int colour = (bx & 1) | ((by & 1) << 1);
+            const uint64_t g = c->dom_off[r] + (uint64_t)d;
+            lists[colour].push_back((g << 32) | (uint64_t)r);
+            dom_rep[g] = (uint32_t)r;
+        }
+    }
+    for (int q = 0; q < 4; ++q) c->n_list[q] = (int)lists[q].size();
+
+    kmc_status s;
+    const size_t tile = (size_t)L_d * L_d / 8;
+#define ALLOC(p, n) if ((s = dev_alloc(c, &(p), (n))) != KMC_OK) return bail(s)
+    ALLOC(c->d_L, n_replicas);
+    ALLOC(c->d_Dx, n_replicas);
+    ALLOC(c->d_dom_off, n_replicas + 1);
+    ALLOC(c->d_dom_rep, ndom);
+    ALLOC(c->d_site_off, n_replicas);
+    ALLOC(c->d_blk_off, n_replicas + 1);
+    ALLOC(c->d_seed, n_replicas);
+    ALLOC(c->d_A, (size_t)n_replicas * 16);
+    ALLOC(c->d_inv, (size_t)n_replicas * 16);
+    ALLOC(c->d_grad, (size_t)n_replicas * 32);
+    ALLOC(c->d_h, n_replicas);
+    for (int q = 0; q < 4; ++q) ALLOC(c->d_list[q], lists[q].size());
+    ALLOC(c->d_tiles, ndom * tile);
+    ALLOC(c->d_edges, ndom * 4);
+    ALLOC(c->d_dctr, ndom * DCTR_WORDS);
+    ALLOC(c->d_bar, 1);
+    ALLOC(c->d_err, 1);
+    {
+        uint8_t *tmp = nullptr;
+        ALLOC(tmp, ndom * 24 + (size_t)n_replicas * 64);
+        c->d_tmp = tmp;
+    }
+#undef ALLOC
+    auto up = [&](auto *dst, const auto *src, size_t n) { return upload(c, dst, src, n, c->stream); };
+    if ((s = up(c->d_L, c->L.data(), n_replicas)) != KMC_OK ||
+        (s = up(c->d_Dx, c->Dx.data(), n_replicas)) != KMC_OK ||
+        (s = up(c->d_dom_off, c->dom_off.data(), n_replicas + 1)) != KMC_OK ||
+        (s = up(c->d_dom_rep, dom_rep.data(), ndom)) != KMC_OK ||
+        (s = up(c->d_site_off, c->site_off.data(), n_replicas)) != KMC_OK ||
+        (s = up(c->d_blk_off, c->blk_off.data(), n_replicas + 1)) != KMC_OK ||
+        (s = up(c->d_seed, c->seed.data(), n_replicas)) != KMC_OK)
+        return bail(s);
+    for (int q = 0; q < 4; ++q)
+        if (!lists[q].empty() && (s = up(c->d_list[q], lists[q].data(), lists[q].size())) != KMC_OK) return bail(s);
+    // the host vectors above are locals: make the copies complete before they go away
+    ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) return bail(fail(c, KMC_ECUDA, "upload: %s", cudaGetErrorString(ce)));
+    ce = cudaMemset(c->d_err, 0, sizeof(int));
+    if (ce != cudaSuccess) return bail(fail(c, KMC_ECUDA, "memset: %s", cudaGetErrorString(ce)));
+
+    // default rates: Metropolis, beta = 0.4, J = 1, h = 0, nu = 1
+    std::vector<double> b0(n_replicas, 0.4), h0(n_replicas, 0.0);
+    *out = c;
+    if ((s = kmc_set_rates(c, 1.0, b0.data(), h0.data(), 1.0, KMC_RATE_METROPOLIS)) != KMC_OK) return bail(s);
+    if ((s = default_shape(c)) != KMC_OK) return bail(s);
+    if ((s = kmc_reset(c, init, stream)) != KMC_OK) return bail(s);
+    return KMC_OK;
+}
+
+kmc_status kmc_reset(kmc_ctx *c, int32_t init, void *stream)
+{
+    if (!c) return KMC_EINVAL;
+    if (init < KMC_INIT_RANDOM || init > KMC_INIT_KEEP) return fail(c, KMC_EINVAL, "bad init mode");
+    c->stream = (cudaStream_t)stream;
+    kmc_status s;
+    if (init != KMC_INIT_KEEP && (s = launch_init(c, init, c->stream)) != KMC_OK) return s;
+    if ((s = launch_reset_counters(c, c->stream)) != KMC_OK) return s;
+    c->sched_done = 0;
+    c->visits_done = 0;
+    return KMC_OK;
+}
+
+kmc_status kmc_set_rates(kmc_ctx *c, double J, const double *beta, const double *h, double nu, int32_t rate_law)
+{
+    if (!c) return KMC_EINVAL;
+    if (!beta || !h) return fail(c, KMC_EINVAL, "beta and h arrays required");
+    if (rate_law != KMC_RATE_METROPOLIS && rate_law != KMC_RATE_BARKER) return fail(c, KMC_EINVAL, "bad rate law");
+    if (!std::isfinite(J) || !(nu > 0.0) || !std::isfinite(nu)) return fail(c, KMC_EINVAL, "J finite and nu > 0 required");
+    for (int r = 0; r < c->n_rep; ++r)
+        if (!(beta[r] >= 0.0) || !std::isfinite(beta[r]) || !std::isfinite(h[r]))
+            return fail(c, KMC_EINVAL, "replica %d: beta >= 0 and finite h required", r);
+    const size_t n = (size_t)c->n_rep * 10;
+    std::vector<double> a(n), gb(n), gh(n);
+    std::vector<uint64_t> A(n), inv(n);
+    for (int r = 0; r < c->n_rep; ++r)
+        build_table(J, beta[r], h[r], rate_law, c->log2nd, &a[r * 10], &A[r * 10], &inv[r * 10], &gb[r * 10], &gh[r * 10]);
+    c->J = J;
+    c->nu = nu;
+    c->law = rate_law;
+    c->beta.assign(beta, beta + c->n_rep);
+    c->h.assign(h, h + c->n_rep);
+    c->a = a;
+    c->A = A;
+    c->inv = inv;
+    c->gb = gb;
+    c->gh = gh;
+    return upload_rates(c);
+}
+
+kmc_status kmc_set_rate_table(kmc_ctx *c, double J, const double *beta, const double *h, double nu, const double *a)
+{
+    if (!c) return KMC_EINVAL;
+    if (!beta || !h || !a) return fail(c, KMC_EINVAL, "beta, h and a arrays required");
+    if (!std::isfinite(J) || !(nu > 0.0)) return fail(c, KMC_EINVAL, "J finite and nu > 0 required");
+    const int P = 63 - c->log2nd;
+    const size_t n = (size_t)c->n_rep * 10;
+    std::vector<double> av(a, a + n), gb(n, 0.0), gh(n, 0.0);
+    std::vector<uint64_t> A(n), inv(n);
+    for (int r = 0; r < c->n_rep; ++r) {
+        if (!(beta[r] >= 0.0) || !std::isfinite(h[r])) return fail(c, KMC_EINVAL, "replica %d: bad beta/h", r);
+        for (int q = 0; q < 10; ++q) {
+            const double ac = a[r * 10 + q];
+            if (!(ac > 0.0 && ac <= 1.0)) return fail(c, KMC_EINVAL, "replica %d class %d: a must be in (0, 1]", r, q);
+            const int up = q / 5, qq = q % 5;
+            const double sigma = up ? 1.0 : -1.0;
+            const double dE = 2.0 * sigma * (J * (double)(2 * qq - 4) + h[r]);
+            const int qbar = 5 * (1 - up) + qq;
+            const double ratio = ac / a[r * 10 + qbar];
+            const double want = std::exp(-beta[r] * dE);
+            if (std::fabs(ratio - want) > 1e-12 * want)
+                return fail(c, KMC_ENOTBALANCED,
+                            "replica %d class %d: a_c/a_cbar = %.17g but exp(-beta dE) = %.17g (detailed balance, Eq. 4)",
+                            r, q, ratio, want);
+            A[r * 10 + q] = (uint64_t)std::nearbyint(std::ldexp(ac, P));
+            inv[r * 10 + q] = A[r * 10 + q] ? (~0ull) / A[r * 10 + q] : 0ull;
+        }
+    }
+    c->J = J;
+    c->nu = nu;
+    c->beta.assign(beta, beta + c->n_rep);
+    c->h.assign(h, h + c->n_rep);
+    c->a = av;
+    c->A = A;
+    c->inv = inv;
+    c->gb = gb; // no closed-form derivatives for a user table
+    c->gh = gh;
+    return upload_rates(c);
+}
+
+kmc_status kmc_get_rate_table(const kmc_ctx *c, int32_t replica, double *a, uint64_t *A)
+{
+    if (!c || replica < 0 || replica >= c->n_rep) return KMC_EINVAL;
+    for (int q = 0; q < 10; ++q) {
+        if (a) a[q] = c->a[(size_t)replica * 10 + q];
+        if (A) A[q] = c->A[(size_t)replica * 10 + q];
+    }
+    return KMC_OK;
+}
+
+kmc_status kmc_set_launch(kmc_ctx *c, int32_t ctas, int32_t warps_per_cta)
+{
+    if (!c) return KMC_EINVAL;
+    if (ctas == 0 && warps_per_cta == 0) return default_shape(c);
+    int spw, slot, smem;
+    kmc_status s = check_shape(c, ctas, warps_per_cta, c->grad, &spw, &slot, &smem);
+    if (s != KMC_OK) return s;
+    c->ctas = ctas;
+    c->wpb = warps_per_cta;
+    c->slots_per_warp = spw;
+    c->slot_bytes = slot;
+    c->smem_bytes = smem;
+    return KMC_OK;
+}
+
+kmc_status kmc_get_launch(const kmc_ctx *c, int32_t *ctas, int32_t *wpb, int32_t *smem)
+{
+    if (!c) return KMC_EINVAL;
+    if (ctas) *ctas = c->ctas;
+    if (wpb) *wpb = c->wpb;
+    if (smem) *smem = c->smem_bytes;
+    return KMC_OK;
+}
+
+kmc_status kmc_debug_barrier(kmc_ctx *c, int32_t extra, int64_t limit_ns)
+{
+    if (!c || extra < 0 || limit_ns < 0) return KMC_EINVAL;
+    c->debug_extra = extra;
+    c->bar_limit_ns = limit_ns > 0 ? (uint64_t)limit_ns : DEFAULT_BAR_LIMIT_NS;
+    return KMC_OK;
+}
+
+kmc_status kmc_enable_grad(kmc_ctx *c, int32_t enable)
+{
+    if (!c) return KMC_EINVAL;
+    c->grad = enable != 0;
+    int spw, slot, smem;
+    kmc_status s = check_shape(c, c->ctas, c->wpb, c->grad, &spw, &slot, &smem);
+    if (s != KMC_OK) return s;
+    return KMC_OK;
+}
+
+kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, int32_t time_mode,
+                            int32_t obs_every, double *obs_dev, void *stream)
+{
+    if (!c) return KMC_EINVAL;
+    if (n_schedules < 0) return fail(c, KMC_EINVAL, "n_schedules must be >= 0");
+    if (schedule < KMC_SCHEDULE_PALINDROME || schedule > KMC_SCHEDULE_RANDOM_PERM)
+        return fail(c, KMC_EINVAL, "bad schedule kind");
+    if (time_mode != KMC_TIME_EXPONENTIAL && time_mode != KMC_TIME_EXPECTED) return fail(c, KMC_EINVAL, "bad time mode");
+    if (obs_every < 0) return fail(c, KMC_EINVAL, "obs_every must be >= 0");
+    if (c->sched_done + n_schedules >= (1ll << 52)) return fail(c, KMC_EINVAL, "schedule index overflow");
+    c->stream = (cudaStream_t)stream;
+    if (n_schedules == 0) return KMC_OK;
+    cudaStream_t s = c->stream;
+    kmc_status st;
+    const bool want_obs = obs_every > 0 && obs_dev != nullptr;
+    const int64_t n_obs = want_obs ? n_schedules / obs_every : 0;
+    if (want_obs && n_obs > 0) {
+        const size_t words = (size_t)n_obs * c->n_rep * OBS_WORDS;
+        if (words > c->obs_acc_words) {
+            if (c->d_obs_acc) cudaFree(c->d_obs_acc);
+            c->d_obs_acc = nullptr;
+            c->obs_acc_words = 0;
+            if ((st = dev_alloc(c, &c->d_obs_acc, words)) != KMC_OK) return st;
+            c->obs_acc_words = words;
+        }
+        CUDA_TRY(c, cudaMemsetAsync(c->d_obs_acc, 0, words * 8, s));
+    }
+    if ((st = launch_pack(c, s)) != KMC_OK) return st;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), s));
+    RunParams P = run_params(c);
+    P.schedule = schedule;
+    P.obs_every = want_obs ? obs_every : 0;
+    P.obs_acc = (want_obs && n_obs > 0) ? c->d_obs_acc : nullptr;
+    P.sched_begin = c->sched_done;
+    P.n_sched = n_schedules;
+    P.visits_before = c->visits_done;
+    RunKernel kern = run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad);
+    CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes));
+    void *args[] = {(void *)&P};
+    CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)kern, dim3(c->ctas), dim3(c->wpb * 32), args,
+                                            (size_t)c->smem_bytes, s));
+    ++c->launches;
+    if (want_obs && n_obs > 0) {
+        const int n_rec = (int)(n_obs * c->n_rep);
+        finalize_obs_kernel<<<grid_for(n_rec, 256), 256, 0, s>>>(c->d_obs_acc, n_rec, c->n_rep, c->d_L, c->d_Dx, c->J,
+                                                                  c->d_h, obs_dev, c->grad ? 6 : 4);
+        ++c->launches;
+        CUDA_TRY(c, cudaGetLastError());
+    }
+    if ((st = launch_unpack(c, s)) != KMC_OK) return st;
+    c->sched_done += n_schedules;
+    c->visits_done += n_schedules * (schedule == KMC_SCHEDULE_PALINDROME ? 2 : 1);
+    c->last_time_mode = time_mode;
+    return KMC_OK;
+}
+
+kmc_status kmc_sync(kmc_ctx *c)
+{
+    if (!c) return KMC_EINVAL;
+    return sync_ctx(c);
+}
+
+kmc_status kmc_observables(kmc_ctx *c, double *E_per_site, double *m, double *t, int64_t *steps, int64_t *flips)
+{
+    if (!c) return KMC_EINVAL;
+    kmc_status st;
+    cudaStream_t s = c->stream;
+    if ((st = launch_pack(c, s)) != KMC_OK) return st;
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(c->d_tmp);
+    const size_t words = (size_t)c->n_rep * OBS_WORDS;
+    if (words * 8 > (size_t)c->n_dom * 24) {
+        // staging too small for this many replicas: use the observation buffer
+        if (words > c->obs_acc_words) {
+            if (c->d_obs_acc) cudaFree(c->d_obs_acc);
+            c->d_obs_acc = nullptr;
+            c->obs_acc_words = 0;
+            if ((st = dev_alloc(c, &c->d_obs_acc, words)) != KMC_OK) return st;
+            c->obs_acc_words = words;
+        }
+        acc = c->d_obs_acc;
+    }
+    CUDA_TRY(c, cudaMemsetAsync(acc, 0, words * 8, s));
+    RunParams P = run_params(c);
+    const bool expo = c->last_time_mode == KMC_TIME_EXPONENTIAL;
+    const int blocks = grid_for(c->n_dom, 8);
+#define KMC_OBS(LDV)                                                                                         \
+    if (expo) observe_kernel<LDV, true><<<blocks, 256, 0, s>>>(P, c->d_dom_rep, c->n_dom, c->visits_done, acc); \
+    else observe_kernel<LDV, false><<<blocks, 256, 0, s>>>(P, c->d_dom_rep, c->n_dom, c->visits_done, acc);
+    switch (c->LD) {
+    case 8: KMC_OBS(8) break;
+    case 16: KMC_OBS(16) break;
+    case 32: KMC_OBS(32) break;
+    default: KMC_OBS(64) break;
+    }
+#undef KMC_OBS
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    std::vector<unsigned long long> h_acc(words);
+    CUDA_TRY(c, cudaMemcpyAsync(h_acc.data(), acc, words * 8, cudaMemcpyDeviceToHost, s));
+    if ((st = sync_ctx(c)) != KMC_OK) return st;
+    for (int r = 0; r < c->n_rep; ++r) {
+        const unsigned long long *a = &h_acc[(size_t)r * OBS_WORDS];
+        const double N = (double)c->L[r] * (double)c->L[r];
+        const double b = (double)(long long)a[0];
+        const double mg = (double)(long long)a[1];
+        double tsum;
+        std::memcpy(&tsum, &a[2], 8);
+        const double e = (-c->J * b - c->h[r] * mg) / N;
+        if (E_per_site) E_per_site[r] = e;
+        if (m) m[r] = mg / N;
+        if (t) t[r] = tsum / ((double)c->Dx[r] * c->Dx[r]);
+        if (steps) steps[r] = c->visits_done * (int64_t)c->k * (int64_t)c->Dx[r] * c->Dx[r];
+    }
+    if (flips) {
+        std::vector<int64_t> fl(c->n_dom);
+        std::vector<uint64_t> hs(c->n_dom);
+        std::vector<double> tt(c->n_dom);
+        if ((st = kmc_domain_state(c, hs.data(), fl.data(), tt.data())) != KMC_OK) return st;
+        for (int r = 0; r < c->n_rep; ++r) {
+            int64_t f = 0;
+            for (uint32_t g = c->dom_off[r]; g < c->dom_off[r + 1]; ++g) f += fl[g];
+            flips[r] = f;
+        }
+    }
+    return KMC_OK;
+}
+
+kmc_status kmc_domain_state(kmc_ctx *c, uint64_t *hash, int64_t *flips, double *t)
+{
+    if (!c) return KMC_EINVAL;
+    cudaStream_t s = c->stream;
+    uint64_t *dh = reinterpret_cast<uint64_t *>(c->d_tmp);
+    int64_t *df = reinterpret_cast<int64_t *>(dh + c->n_dom);
+    double *dt = reinterpret_cast<double *>(df + c->n_dom);
+    const int64_t steps = c->visits_done * (int64_t)c->k;
+    const double lambda = (double)(c->LD * c->LD) * c->nu;
+    if (c->last_time_mode == KMC_TIME_EXPONENTIAL)
+        domain_state_kernel<true><<<grid_for(c->n_dom, 256), 256, 0, s>>>(c->d_dctr, c->n_dom, steps, lambda, dh, df, dt);
+    else
+        domain_state_kernel<false><<<grid_for(c->n_dom, 256), 256, 0, s>>>(c->d_dctr, c->n_dom, steps, lambda, dh, df, dt);
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    const size_t n = (size_t)c->n_dom;
+    if (hash) CUDA_TRY(c, cudaMemcpyAsync(hash, dh, n * 8, cudaMemcpyDeviceToHost, s));
+    if (flips) CUDA_TRY(c, cudaMemcpyAsync(flips, df, n * 8, cudaMemcpyDeviceToHost, s));
+    if (t) CUDA_TRY(c, cudaMemcpyAsync(t, dt, n * 8, cudaMemcpyDeviceToHost, s));
+    return sync_ctx(c);
+}
+
+kmc_status kmc_grad(kmc_ctx *c, double *score_dev, int32_t reset)
+{
+    if (!c) return KMC_EINVAL;
+    if (!score_dev) return fail(c, KMC_EINVAL, "score_dev required");
+    score_reduce_kernel<<<grid_for(c->n_rep, 128), 128, 0, c->stream>>>(c->d_dctr, c->d_dom_off, c->n_rep, score_dev,
+                                                                          reset, c->d_dctr);
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    return sync_ctx(c);
+}
+
+void kmc_destroy(kmc_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+} // extern "C"

@@ -1,0 +1,43 @@
+"""The C-ABI library builds, loads and exports every entry point of include/kmc.h (no GPU needed)."""
+import ctypes
+import os
+import re
+
+from paper_1403_4674_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "kmc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kmc_[a-z_]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    build.build()
+    lib = ctypes.CDLL(build.LIB)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_null_context():
+    lib = _lib.load()
+    assert lib.kmc_version() >= 10000
+    assert lib.kmc_last_error(None) == b"null context"
+    assert lib.kmc_run_schedule(None, 1, 0, 0, 0, None, None) == _lib.KMC_EINVAL
+    assert lib.kmc_kernel_launches(None) == 0
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1403_4674_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                for bad in ("import oracle", "from oracle", "liborc", "kmc_oracle"):
+                    assert bad not in src, (f, bad)

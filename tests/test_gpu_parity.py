@@ -1,0 +1,106 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Bit-exact: spins, per-domain real-event counts and event-sequence hashes,
+e, m and e*m (integer sums, same FP64 formula and order).  Clocks: 1e-12
+relative (the device multiplies 64-bit mantissas where the oracle sums
+logarithms, Sec. 2.1; the decision path never reads the clock).
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import assert_parity, run_both
+from oracle import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def test_init_random_and_all_up_bit_exact():
+    import paper_1403_4674_gb300 as kmc
+    L = [64, 128, 48 * 2, 256]
+    seeds = [1, 2**40 + 3, 77, 2**63 - 5]
+    lat = kmc.Lattice(L, 16, 1, seeds, init=kmc.KMC_INIT_RANDOM)
+    for r, (Lr, s) in enumerate(zip(L, seeds)):
+        assert np.array_equal(lat.replica_spins(r).cpu().numpy(), orc.init_spins(Lr, orc.INIT_RANDOM, s))
+    lat.reset(kmc.KMC_INIT_ALL_UP)
+    lat.sync()
+    assert bool((lat.spins == 1).all())
+    lat.close()
+
+
+def test_config_64_T25_k1_1000_schedules():
+    """64^2, T=2.5, h=0, L_d=16, k=1, palindrome, 1000 schedules, FP64 clock."""
+    gpu, ref = run_both([64], 16, 1, [1], [1 / 2.5], [0.0], 1000, obs_every=10)
+    assert_parity(gpu, ref, 1)
+    assert gpu["obs"].shape == (100, 1, 4)
+
+
+@pytest.mark.parametrize("Ld", [8, 16, 32, 64])
+@pytest.mark.parametrize("k", [1, 3, 16, 40])
+def test_domain_sizes_and_step_counts(Ld, k):
+    L = 4 * Ld
+    gpu, ref = run_both([L], Ld, k, [1000 + Ld + k], [1 / 2.269], [0.01], 6, obs_every=2)
+    assert_parity(gpu, ref, 1)
+
+
+@pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
+@pytest.mark.parametrize("time_mode", [orc.TIME_EXPONENTIAL, orc.TIME_EXPECTED])
+@pytest.mark.parametrize("schedule", [orc.SCHED_PALINDROME, orc.SCHED_FIXED, orc.SCHED_RANDOM_PERM])
+def test_laws_time_modes_schedules(law, time_mode, schedule):
+    gpu, ref = run_both([64, 96], 16, 4, [11, 12], [0.5, 0.3], [0.2, -0.1], 9, law=law,
+                        time_mode=time_mode, schedule=schedule, obs_every=3, nu=0.75)
+    assert_parity(gpu, ref, 2)
+
+
+def test_uneven_batch_of_replicas():
+    L = [32, 48, 64, 80, 96, 128, 160, 256]
+    seeds = [int(s) for s in np.random.default_rng(5).integers(1, 2**62, size=len(L))]
+    beta = list(np.linspace(1 / 3.5, 1 / 1.5, len(L)))
+    h = list(np.linspace(-0.1, 0.1, len(L)))
+    gpu, ref = run_both(L, 8, 8, seeds, beta, h, 5, obs_every=1)
+    assert_parity(gpu, ref, len(L))
+
+
+def test_resume_across_calls_is_bit_exact():
+    gpu, ref = run_both([128], 32, 4, [99], [0.44], [0.0], 10, obs_every=2, chunks=[3, 5, 2])
+    assert_parity(gpu, ref, 1)
+
+
+def test_degenerate_rates():
+    # beta = 0: every step is a real event; beta = 8: almost every step is null
+    gpu, ref = run_both([64, 64], 16, 8, [3, 4], [0.0, 8.0], [0.0, 0.0], 5, init=orc.INIT_ALL_UP)
+    assert_parity(gpu, ref, 2)
+    assert gpu["flips"][:16].sum() == 16 * 2 * 8 * 5
+
+
+def test_minimum_lattice_two_domains_per_side():
+    gpu, ref = run_both([16, 32, 64, 128], 8, 5, [1, 2, 3, 4], [0.4] * 4, [0.05] * 4, 7)
+    assert_parity(gpu, ref, 4)
+    gpu, ref = run_both([128], 64, 5, [9], [0.4], [0.05], 7)
+    assert_parity(gpu, ref, 1)
+
+
+@pytest.mark.parametrize("launch", [(1, 1), (3, 2), (7, 16)])
+def test_launch_shape_does_not_change_results(launch):
+    gpu, ref = run_both([256], 16, 4, [2024], [0.42], [0.01], 4, obs_every=2, launch=launch)
+    assert_parity(gpu, ref, 1)
+
+
+@pytest.mark.parametrize("k", [1, 4, 16])
+def test_config_1024_k(k):
+    """1024^2, L_d=32, T=2.269 from random and all-up starts, k in {1,4,16}."""
+    for init in (orc.INIT_RANDOM, orc.INIT_ALL_UP):
+        gpu, ref = run_both([1024], 32, k, [7 + k], [1 / 2.269], [0.0], 2, init=init, obs_every=1)
+        assert_parity(gpu, ref, 1)
+
+
+def test_config_8192_one_schedule():
+    """8192^2 (67M sites), T=2.269, h=0.01, L_d=64, k=8: one full schedule vs the oracle."""
+    gpu, ref = run_both([8192], 64, 8, [8192], [1 / 2.269], [0.01], 1, obs_every=1)
+    assert_parity(gpu, ref, 1)
