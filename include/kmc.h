@@ -184,6 +184,13 @@ kmc_status kmc_get_launch(const kmc_ctx *ctx, int32_t *ctas, int32_t *warps_per_
  * normal barrier; limit_ns = 0 restores the default limit (2 s). */
 kmc_status kmc_debug_barrier(kmc_ctx *ctx, int32_t extra, int64_t limit_ns);
 
+/* Event timing of the persistent run kernel: with enable != 0 every
+ * kmc_run_schedule records a CUDA event pair around its run-kernel launch on
+ * the launch stream.  kmc_profile_read synchronises, returns the summed
+ * elapsed milliseconds and the number of timed launches, and clears them. */
+kmc_status kmc_profile(kmc_ctx *ctx, int32_t enable);
+kmc_status kmc_profile_read(kmc_ctx *ctx, double *run_kernel_ms, int64_t *run_kernel_launches);
+
 /* Number of kernels this context launched so far (all kinds). */
 int64_t kmc_kernel_launches(const kmc_ctx *ctx);
 

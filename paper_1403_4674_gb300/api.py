@@ -138,6 +138,16 @@ def kmc_debug_barrier(ctx, extra: int, limit_ns: int):
     _check(ctx, load().kmc_debug_barrier(ctx, extra, limit_ns))
 
 
+def kmc_profile(ctx, enable: bool):
+    _check(ctx, load().kmc_profile(ctx, int(bool(enable))))
+
+
+def kmc_profile_read(ctx):
+    ms, n = _dbl(), _i64()
+    _check(ctx, load().kmc_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
 def kmc_kernel_launches(ctx) -> int:
     return load().kmc_kernel_launches(ctx)
 
@@ -228,6 +238,13 @@ class Lattice:
 
     def launch(self):
         return kmc_get_launch(self.ctx)
+
+    def profile(self, enable: bool = True):
+        kmc_profile(self.ctx, enable)
+
+    def profile_read(self):
+        """(summed run-kernel milliseconds, timed launches) since the last read."""
+        return kmc_profile_read(self.ctx)
 
     def kernel_launches(self) -> int:
         return kmc_kernel_launches(self.ctx)

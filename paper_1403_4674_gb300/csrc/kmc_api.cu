@@ -64,6 +64,8 @@ struct kmc_ctx {
     int64_t launches = 0;
     int debug_extra = 0;
     uint64_t bar_limit_ns = 2000000000ull;
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
     std::string err;
 };
 
@@ -677,9 +679,19 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     RunKernel kern = run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad);
     CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes));
     void *args[] = {(void *)&P};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (c->prof) {
+        CUDA_TRY(c, cudaEventCreate(&ev0));
+        CUDA_TRY(c, cudaEventCreate(&ev1));
+        CUDA_TRY(c, cudaEventRecord(ev0, s));
+    }
     CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)kern, dim3(c->ctas), dim3(c->wpb * 32), args,
                                             (size_t)c->smem_bytes, s));
     ++c->launches;
+    if (c->prof) {
+        CUDA_TRY(c, cudaEventRecord(ev1, s));
+        c->prof_events.emplace_back(ev0, ev1);
+    }
     if (want_obs && n_obs > 0) {
         const int n_rec = (int)(n_obs * c->n_rep);
         finalize_obs_kernel<<<grid_for(n_rec, 256), 256, 0, s>>>(c->d_obs_acc, n_rec, c->n_rep, c->d_L, c->d_Dx, c->J,
@@ -798,10 +810,42 @@ kmc_status kmc_grad(kmc_ctx *c, double *score_dev, int32_t reset)
     return sync_ctx(c);
 }
 
+kmc_status kmc_profile(kmc_ctx *c, int32_t enable)
+{
+    if (!c) return KMC_EINVAL;
+    c->prof = enable != 0;
+    return KMC_OK;
+}
+
+kmc_status kmc_profile_read(kmc_ctx *c, double *run_kernel_ms, int64_t *run_kernel_launches)
+{
+    if (!c) return KMC_EINVAL;
+    double tot = 0.0;
+    int64_t n = 0;
+    for (auto &pr : c->prof_events) {
+        CUDA_TRY(c, cudaEventSynchronize(pr.second));
+        float ms = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, pr.first, pr.second));
+        tot += ms;
+        ++n;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    c->prof_events.clear();
+    if (run_kernel_ms) *run_kernel_ms = tot;
+    if (run_kernel_launches) *run_kernel_launches = n;
+    return KMC_OK;
+}
+
 void kmc_destroy(kmc_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    for (auto &pr : c->prof_events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    c->prof_events.clear();
     free_all(c);
     delete c;
 }
