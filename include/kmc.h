@@ -77,8 +77,10 @@ enum { KMC_TIME_EXPONENTIAL = 0, KMC_TIME_EXPECTED = 1 };
  *               offset sum_{q<r} L[q]^2, row-major (site (x, y) at y*L + x),
  *               8-byte aligned.  Caller-owned; holds the state between calls.
  *   stream      stream for the initialisation work.
- * The whole bit-packed state must fit in on-chip shared memory of the
- * device (about 34 MB on a GB300); larger batches return KMC_EINVAL.
+ * The whole bit-packed state (L^2/8 bytes per replica plus 112 bytes per
+ * domain) stays in on-chip shared memory during a run: up to 16 CTAs per
+ * replica in CLUSTER plans, all SMs in GRID plans (about 34 MB on a GB300);
+ * larger batches return KMC_EINVAL.
  * The rate table defaults to Metropolis at beta = 0.4, J = 1, h = 0,
  * nu = 1 until kmc_set_rates is called.
  */
@@ -171,17 +173,29 @@ kmc_status kmc_domain_state(kmc_ctx *ctx, uint64_t *hash, int64_t *flips, double
 /* Fixed-point and FP64 acceptance table of replica r (host arrays of 10). */
 kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, uint64_t *A);
 
-/* Launch shape of the persistent kernel: ctas and warps per CTA (0 = the
- * library's default).  Returns KMC_EINVAL if the shape cannot be
- * co-resident or the state does not fit. */
-kmc_status kmc_set_launch(kmc_ctx *ctx, int32_t ctas, int32_t warps_per_cta);
-kmc_status kmc_get_launch(const kmc_ctx *ctx, int32_t *ctas, int32_t *warps_per_cta,
-                          int32_t *smem_bytes);
+/* Launch plan of the persistent run kernel.
+ *   KMC_LAUNCH_AUTO: the library's choice (CLUSTER when every replica fits
+ *     one cluster of at most 16 CTAs, else GRID); size and warps ignored.
+ *   KMC_LAUNCH_CLUSTER: every replica resident in one thread-block cluster of
+ *     `size` CTAs (1, 2, 4, 8 or 16); halos exchanged through distributed
+ *     shared memory, colour phases separated by the hardware cluster barrier;
+ *     no device-wide synchronisation.
+ *   KMC_LAUNCH_GRID: one cooperative grid of `size` CTAs; halos through L2,
+ *     colour phases separated by a bounded grid barrier (kmc_debug_barrier).
+ * warps_per_cta: 1..16.  Returns KMC_EINVAL if the plan cannot be scheduled
+ * or the state does not fit in shared memory; the previous plan then stays.
+ * Results do not depend on the plan. */
+enum { KMC_LAUNCH_AUTO = 0, KMC_LAUNCH_CLUSTER = 1, KMC_LAUNCH_GRID = 2 };
+kmc_status kmc_set_launch(kmc_ctx *ctx, int32_t mode, int32_t size, int32_t warps_per_cta);
+/* Current plan: mode, size (cluster size or CTA count), CTAs, warps per CTA,
+ * dynamic shared memory per CTA.  Any pointer may be NULL. */
+kmc_status kmc_get_launch(const kmc_ctx *ctx, int32_t *mode, int32_t *size, int32_t *ctas,
+                          int32_t *warps_per_cta, int32_t *smem_bytes);
 
-/* Test hook for the bounded phase barrier: the next run's first barrier
- * waits for `extra` arrivals that never come and gives up after limit_ns
- * nanoseconds (KMC_ETIMEOUT at the next kmc_sync).  extra = 0 restores the
- * normal barrier; limit_ns = 0 restores the default limit (2 s). */
+/* Test hook for the bounded grid barrier (GRID plans): the next run's first
+ * barrier waits for `extra` arrivals that never come and gives up after
+ * limit_ns nanoseconds (KMC_ETIMEOUT at the next kmc_sync).  extra = 0
+ * restores the normal barrier; limit_ns = 0 restores the default (2 s). */
 kmc_status kmc_debug_barrier(kmc_ctx *ctx, int32_t extra, int64_t limit_ns);
 
 /* Event timing of the persistent run kernel: with enable != 0 every

@@ -68,8 +68,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmc_sync.argtypes = [vp]
     L.kmc_domain_state.argtypes = [vp, P(u64), P(i64), P(dbl)]
     L.kmc_get_rate_table.argtypes = [vp, i32, P(dbl), P(u64)]
-    L.kmc_set_launch.argtypes = [vp, i32, i32]
-    L.kmc_get_launch.argtypes = [vp, P(i32), P(i32), P(i32)]
+    L.kmc_set_launch.argtypes = [vp, i32, i32, i32]
+    L.kmc_get_launch.argtypes = [vp, P(i32), P(i32), P(i32), P(i32), P(i32)]
     L.kmc_debug_barrier.argtypes = [vp, i32, i64]
     L.kmc_profile.argtypes = [vp, i32]
     L.kmc_profile_read.argtypes = [vp, P(dbl), P(i64)]

@@ -17,6 +17,7 @@ KMC_INIT_RANDOM, KMC_INIT_ALL_UP, KMC_INIT_KEEP = 0, 1, 2
 KMC_RATE_METROPOLIS, KMC_RATE_BARKER = 0, 1
 KMC_SCHEDULE_PALINDROME, KMC_SCHEDULE_FIXED, KMC_SCHEDULE_RANDOM_PERM = 0, 1, 2
 KMC_TIME_EXPONENTIAL, KMC_TIME_EXPECTED = 0, 1
+KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID = 0, 1, 2
 
 _i32, _i64, _u64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
 
@@ -124,14 +125,15 @@ def kmc_sync(ctx):
     _check(ctx, load().kmc_sync(ctx))
 
 
-def kmc_set_launch(ctx, ctas: int, warps_per_cta: int):
-    _check(ctx, load().kmc_set_launch(ctx, ctas, warps_per_cta))
+def kmc_set_launch(ctx, mode: int, size: int, warps_per_cta: int):
+    _check(ctx, load().kmc_set_launch(ctx, mode, size, warps_per_cta))
 
 
 def kmc_get_launch(ctx):
-    a, b, c = _i32(), _i32(), _i32()
-    _check(ctx, load().kmc_get_launch(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return a.value, b.value, c.value
+    """(mode, size, ctas, warps_per_cta, smem_bytes) of the current plan."""
+    v = [_i32() for _ in range(5)]
+    _check(ctx, load().kmc_get_launch(ctx, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def kmc_debug_barrier(ctx, extra: int, limit_ns: int):
@@ -233,8 +235,8 @@ class Lattice:
     def sync(self):
         kmc_sync(self.ctx)
 
-    def set_launch(self, ctas: int, warps_per_cta: int):
-        kmc_set_launch(self.ctx, ctas, warps_per_cta)
+    def set_launch(self, mode: int = KMC_LAUNCH_AUTO, size: int = 0, warps_per_cta: int = 16):
+        kmc_set_launch(self.ctx, mode, size, warps_per_cta)
 
     def launch(self):
         return kmc_get_launch(self.ctx)

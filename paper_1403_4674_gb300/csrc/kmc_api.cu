@@ -1,8 +1,9 @@
 // kmc_api.cu -- host side of the C ABI declared in include/kmc.h.
 //
 // Owns the library's device scratch (bit tiles, edges, per-domain counters,
-// work lists, rate tables, barrier counter, error word), validates
-// arguments, builds the fixed-point rate table on the host and enqueues the
+// launch plan, rate tables, barrier counter, error word), validates
+// arguments, builds the fixed-point rate table on the host, plans which CTA
+// (and which thread-block cluster) owns which domain, and enqueues the
 // kernels of kmc_kernels.cuh on the caller's stream.
 #include "kmc.h"
 #include "kmc_kernels.cuh"
@@ -15,9 +16,26 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 using namespace kmcdev;
+
+namespace {
+
+// Host copy of a launch plan (see RunParams for the device arrays).
+struct Plan {
+    int mode = 0;     // KMC_LAUNCH_CLUSTER or KMC_LAUNCH_GRID
+    int cluster = 0;  // CTAs per cluster (CLUSTER mode)
+    int n_cta = 0;
+    int wpb = 0;
+    int max_rt = 0;
+    int max_slots = 0;
+    size_t smem = 0;
+    std::vector<uint32_t> cta_slot_off, cta_col_off, cta_rt_off, rt_rep, slot_g, slot_rt, slot_nb;
+};
+
+} // namespace
 
 struct kmc_ctx {
     int dev = 0;
@@ -30,6 +48,7 @@ struct kmc_ctx {
     std::vector<uint32_t> dom_off;   // n_rep + 1
     std::vector<uint64_t> site_off;  // n_rep
     std::vector<uint64_t> blk_off;   // n_rep + 1
+    std::vector<uint32_t> dom_rep;   // n_dom
     int n_dom = 0;
     int8_t *spins = nullptr;
     cudaStream_t stream = nullptr;
@@ -39,15 +58,16 @@ struct kmc_ctx {
     uint64_t *d_site_off = nullptr, *d_blk_off = nullptr, *d_seed = nullptr;
     uint64_t *d_A = nullptr, *d_inv = nullptr;
     double *d_grad = nullptr, *d_h = nullptr;
-    uint64_t *d_list[4] = {nullptr, nullptr, nullptr, nullptr};
-    int n_list[4] = {0, 0, 0, 0};
     uint8_t *d_tiles = nullptr;
     uint64_t *d_edges = nullptr, *d_dctr = nullptr;
     unsigned *d_bar = nullptr;
     int *d_err = nullptr;
     unsigned long long *d_obs_acc = nullptr;
     size_t obs_acc_words = 0;
-    void *d_tmp = nullptr; // n_dom * 24 bytes, host-facing staging
+    void *d_tmp = nullptr; // n_dom * 24 + n_rep * 64 bytes, host-facing staging
+    // device copy of the launch plan
+    uint32_t *d_plan = nullptr;
+    size_t plan_words = 0;
 
     double J = 1.0, nu = 1.0;
     std::vector<double> beta, h, a, gb, gh;
@@ -60,7 +80,7 @@ struct kmc_ctx {
     bool grad = false;
 
     int sm_count = 0, smem_optin = 0;
-    int ctas = 0, wpb = 0, slots_per_warp = 0, slot_bytes = 0, smem_bytes = 0;
+    Plan plan;
     int64_t launches = 0;
     int debug_extra = 0;
     uint64_t bar_limit_ns = 2000000000ull;
@@ -72,6 +92,7 @@ struct kmc_ctx {
 namespace {
 
 const uint64_t DEFAULT_BAR_LIMIT_NS = 2000000000ull;
+const int MAX_WPB = 16;
 
 kmc_status fail(kmc_ctx *c, kmc_status s, const char *fmt, ...)
 {
@@ -94,6 +115,11 @@ kmc_status fail(kmc_ctx *c, kmc_status s, const char *fmt, ...)
     } while (0)
 
 int ld_index(int LD) { return LD == 8 ? 0 : LD == 16 ? 1 : LD == 32 ? 2 : LD == 64 ? 3 : -1; }
+
+int slot_bytes_for(int LD)
+{
+    return LD == 8 ? slot_bytes<8>() : LD == 16 ? slot_bytes<16>() : LD == 32 ? slot_bytes<32>() : slot_bytes<64>();
+}
 
 // Acceptance table (App. A, Eq. Glauber_TM): FP64 a_c, fixed point A_c =
 // round(a_c 2^P), P = 63 - log2(n_d), reciprocal floor((2^64-1)/A_c) and the
@@ -139,27 +165,21 @@ kmc_status dev_alloc(kmc_ctx *c, T **p, size_t n)
     return KMC_OK;
 }
 
-template <typename T>
-kmc_status upload(kmc_ctx *c, T *dst, const T *src, size_t n, cudaStream_t s)
-{
-    CUDA_TRY(c, cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
-    return KMC_OK;
-}
-
 using RunKernel = void (*)(const RunParams);
 
-RunKernel run_kernel_for(int LD, bool expo, bool grad)
+RunKernel run_kernel_for(int LD, bool expo, bool grad, bool cluster)
 {
-#define KMC_PICK(LDV)                                                                       \
-    if (LD == LDV) {                                                                        \
-        if (expo) return grad ? run_kernel<LDV, true, true> : run_kernel<LDV, true, false>; \
-        return grad ? run_kernel<LDV, false, true> : run_kernel<LDV, false, false>;         \
-    }
+#define KMC_PICK2(LDV, E, G)                                                   \
+    if (LD == LDV && expo == E && grad == G)                                   \
+        return cluster ? run_kernel<LDV, E, G, true> : run_kernel<LDV, E, G, false>;
+#define KMC_PICK(LDV)                                                          \
+    KMC_PICK2(LDV, true, true) KMC_PICK2(LDV, true, false) KMC_PICK2(LDV, false, true) KMC_PICK2(LDV, false, false)
     KMC_PICK(8)
     KMC_PICK(16)
     KMC_PICK(32)
     KMC_PICK(64)
 #undef KMC_PICK
+#undef KMC_PICK2
     return nullptr;
 }
 
@@ -195,10 +215,19 @@ RunParams run_params(kmc_ctx *c)
     P.rep_A = c->d_A;
     P.rep_inv = c->d_inv;
     P.rep_grad = c->d_grad;
-    for (int q = 0; q < 4; ++q) {
-        P.list[q] = c->d_list[q];
-        P.n_list[q] = c->n_list[q];
-    }
+    const Plan &pl = c->plan;
+    uint32_t *base = c->d_plan;
+    size_t off = 0;
+    auto take = [&](size_t n) { uint32_t *p = base + off; off += n; return p; };
+    P.cta_slot_off = take(pl.cta_slot_off.size());
+    P.cta_col_off = take(pl.cta_col_off.size());
+    P.cta_rt_off = take(pl.cta_rt_off.size());
+    P.rt_rep = take(pl.rt_rep.size());
+    P.slot_g = take(pl.slot_g.size());
+    P.slot_rt = take(pl.slot_rt.size());
+    P.slot_nb = take(pl.slot_nb.size());
+    P.max_rt = pl.max_rt;
+    P.cluster = pl.mode == KMC_LAUNCH_CLUSTER ? pl.cluster : 0;
     P.tiles = c->d_tiles;
     P.dctr = c->d_dctr;
     P.edges = c->d_edges;
@@ -206,9 +235,6 @@ RunParams run_params(kmc_ctx *c)
     P.err = c->d_err;
     P.bar_limit_ns = c->bar_limit_ns;
     P.debug_extra = c->debug_extra;
-    P.total_warps = c->ctas * c->wpb;
-    P.slots_per_warp = c->slots_per_warp;
-    P.slot_bytes = c->slot_bytes;
     P.lambda = (double)(c->LD * c->LD) * c->nu;
     return P;
 }
@@ -217,6 +243,309 @@ int grid_for(int n_items, int per_block)
 {
     int g = (n_items + per_block - 1) / per_block;
     return std::max(1, std::min(g, 65535));
+}
+
+int domain_colour(const kmc_ctx *c, uint32_t g)
+{
+    const uint32_t r = c->dom_rep[g];
+    const uint32_t d = g - c->dom_off[r];
+    const int D = c->Dx[r];
+    return (int)((d % D) & 1u) | (int)(((d / D) & 1u) << 1);
+}
+
+uint32_t neighbour(const kmc_ctx *c, uint32_t g, int side)
+{
+    const uint32_t r = c->dom_rep[g];
+    const uint32_t d = g - c->dom_off[r];
+    const int D = c->Dx[r];
+    const int bx = (int)(d % D), by = (int)(d / D);
+    int nx = bx, ny = by;
+    if (side == EDGE_N) ny = (by + D - 1) % D;
+    else if (side == EDGE_S) ny = (by + 1) % D;
+    else if (side == EDGE_W) nx = (bx + D - 1) % D;
+    else nx = (bx + 1) % D;
+    return c->dom_off[r] + (uint32_t)(ny * D + nx);
+}
+
+// Fill per-CTA slot lists (colour-sorted), replica tables and neighbour refs
+// from an assignment domain -> CTA.
+void finish_plan(const kmc_ctx *c, Plan &pl, const std::vector<std::vector<uint32_t>> &cta_doms)
+{
+    const int slot_b = slot_bytes_for(c->LD);
+    pl.n_cta = (int)cta_doms.size();
+    pl.cta_slot_off.assign(1, 0);
+    pl.cta_col_off.clear();
+    pl.cta_rt_off.assign(1, 0);
+    pl.rt_rep.clear();
+    pl.slot_g.clear();
+    pl.slot_rt.clear();
+    pl.max_rt = 1;
+    pl.max_slots = 1;
+    std::vector<uint32_t> where_cta(c->n_dom, 0), where_slot(c->n_dom, 0);
+    for (int b = 0; b < pl.n_cta; ++b) {
+        std::vector<uint32_t> doms = cta_doms[b];
+        std::stable_sort(doms.begin(), doms.end(), [&](uint32_t x, uint32_t y) {
+            const int cx = domain_colour(c, x), cy = domain_colour(c, y);
+            return cx != cy ? cx < cy : x < y;
+        });
+        std::vector<uint32_t> reps;
+        for (uint32_t g : doms) reps.push_back(c->dom_rep[g]);
+        std::sort(reps.begin(), reps.end());
+        reps.erase(std::unique(reps.begin(), reps.end()), reps.end());
+        uint32_t colc[5] = {0, 0, 0, 0, 0};
+        for (size_t i = 0; i < doms.size(); ++i) {
+            const uint32_t g = doms[i];
+            colc[domain_colour(c, g) + 1]++;
+            const uint32_t rt = (uint32_t)(std::lower_bound(reps.begin(), reps.end(), c->dom_rep[g]) - reps.begin());
+            where_cta[g] = (uint32_t)b;
+            where_slot[g] = (uint32_t)i;
+            pl.slot_g.push_back(g);
+            pl.slot_rt.push_back(rt);
+        }
+        for (int q = 1; q < 5; ++q) colc[q] += colc[q - 1];
+        for (int q = 0; q < 5; ++q) pl.cta_col_off.push_back(colc[q]);
+        pl.cta_slot_off.push_back((uint32_t)pl.slot_g.size());
+        for (uint32_t r : reps) pl.rt_rep.push_back(r);
+        pl.cta_rt_off.push_back((uint32_t)pl.rt_rep.size());
+        pl.max_rt = std::max(pl.max_rt, (int)reps.size());
+        pl.max_slots = std::max(pl.max_slots, (int)doms.size());
+    }
+    pl.slot_nb.resize(pl.slot_g.size() * 4);
+    for (size_t s = 0; s < pl.slot_g.size(); ++s) {
+        const uint32_t g = pl.slot_g[s];
+        for (int side = 0; side < 4; ++side) {
+            const uint32_t gn = neighbour(c, g, side);
+            if (pl.mode == KMC_LAUNCH_CLUSTER) {
+                const uint32_t cta = where_cta[gn];
+                const uint32_t rank = cta % (uint32_t)pl.cluster;
+                pl.slot_nb[s * 4 + side] = (rank << 24) | where_slot[gn];
+            } else {
+                pl.slot_nb[s * 4 + side] = gn;
+            }
+        }
+    }
+    pl.smem = (size_t)pl.max_rt * RT_BYTES + (size_t)pl.max_slots * slot_b;
+}
+
+// CLUSTER plan: every replica inside one cluster of `C` CTAs; a replica with
+// n domains spreads over m = ceil(n/4 / (wpb*load)) CTAs (one visit per warp
+// and phase when load = 1); replicas that need one CTA share CTAs.
+kmc_status plan_cluster(kmc_ctx *c, int C, int wpb, int load, Plan &pl)
+{
+    pl = Plan();
+    pl.mode = KMC_LAUNCH_CLUSTER;
+    pl.cluster = C;
+    pl.wpb = wpb;
+    const int slot_b = slot_bytes_for(c->LD);
+    const int cap_per_colour = wpb * load;               // domains of one colour per CTA
+    std::vector<std::vector<uint32_t>> cta_doms;
+    std::vector<int> cta_fill;                           // per-colour domains in the CTA
+    std::vector<int> cta_nrep;
+    int cluster_base = -1;                               // first CTA of the open cluster
+    auto open_cluster = [&]() {
+        cluster_base = (int)cta_doms.size();
+        for (int q = 0; q < C; ++q) {
+            cta_doms.emplace_back();
+            cta_fill.push_back(0);
+            cta_nrep.push_back(0);
+        }
+    };
+    for (int r = 0; r < c->n_rep; ++r) {
+        const int n = c->Dx[r] * c->Dx[r];
+        const int per_colour = n / 4;
+        const int m = (per_colour + cap_per_colour - 1) / cap_per_colour;
+        if (m > C) return fail(c, KMC_EINVAL, "replica %d (%d domains) needs %d CTAs, more than a cluster of %d", r, n, m, C);
+        if ((size_t)RT_BYTES + (size_t)((n + m - 1) / m) * slot_b > (size_t)c->smem_optin)
+            return fail(c, KMC_EINVAL, "replica %d does not fit in the shared memory of %d CTAs", r, m);
+        std::vector<uint32_t> ctas;
+        if (m == 1) {
+            // first CTA of the open cluster with room (domains of all colours scale together)
+            int pick = -1;
+            if (cluster_base >= 0) {
+                for (int q = cluster_base; q < cluster_base + C; ++q) {
+                    const size_t smem_after = (size_t)(cta_nrep[q] + 1) * RT_BYTES +
+                                              (cta_doms[q].size() + (size_t)n) * slot_b;
+                    if (cta_fill[q] + per_colour <= cap_per_colour && smem_after <= (size_t)c->smem_optin) {
+                        pick = q;
+                        break;
+                    }
+                }
+            }
+            if (pick < 0) {
+                open_cluster();
+                pick = cluster_base;
+            }
+            ctas.push_back((uint32_t)pick);
+        } else {
+            // m empty CTAs at the end of the open cluster, else a new cluster
+            int start = -1;
+            if (cluster_base >= 0) {
+                int q = cluster_base + C;
+                while (q > cluster_base && cta_doms[q - 1].empty()) --q;
+                if (cluster_base + C - q >= m) start = q;
+            }
+            if (start < 0) {
+                open_cluster();
+                start = cluster_base;
+            }
+            for (int q = 0; q < m; ++q) ctas.push_back((uint32_t)(start + q));
+        }
+        // colour-balanced round robin over the replica's CTAs
+        int rr[4] = {0, 0, 0, 0};
+        for (int d = 0; d < n; ++d) {
+            const uint32_t g = c->dom_off[r] + (uint32_t)d;
+            const int col = domain_colour(c, g);
+            const uint32_t q = ctas[rr[col]++ % ctas.size()];
+            cta_doms[q].push_back(g);
+        }
+        for (uint32_t q : ctas) {
+            cta_fill[q] += (per_colour + (int)ctas.size() - 1) / (int)ctas.size();
+            cta_nrep[q] += 1;
+        }
+    }
+    finish_plan(c, pl, cta_doms);
+    if (pl.smem > (size_t)c->smem_optin)
+        return fail(c, KMC_EINVAL, "cluster plan needs %zu bytes of shared memory per CTA (%d available)", pl.smem,
+                    c->smem_optin);
+    return KMC_OK;
+}
+
+// GRID plan: each colour list (all replicas, ascending g) cut into n_cta contiguous chunks.
+kmc_status plan_grid(kmc_ctx *c, int n_cta, int wpb, Plan &pl)
+{
+    pl = Plan();
+    pl.mode = KMC_LAUNCH_GRID;
+    pl.cluster = 0;
+    pl.wpb = wpb;
+    std::vector<std::vector<uint32_t>> lists(4);
+    for (uint32_t g = 0; g < (uint32_t)c->n_dom; ++g) lists[domain_colour(c, g)].push_back(g);
+    std::vector<std::vector<uint32_t>> cta_doms(n_cta);
+    for (int q = 0; q < 4; ++q) {
+        const size_t n = lists[q].size();
+        for (int b = 0; b < n_cta; ++b) {
+            const size_t i0 = n * b / n_cta, i1 = n * (b + 1) / n_cta;
+            for (size_t i = i0; i < i1; ++i) cta_doms[b].push_back(lists[q][i]);
+        }
+    }
+    finish_plan(c, pl, cta_doms);
+    if (pl.smem > (size_t)c->smem_optin)
+        return fail(c, KMC_EINVAL, "grid plan needs %zu bytes of shared memory per CTA (%d available)", pl.smem,
+                    c->smem_optin);
+    return KMC_OK;
+}
+
+// Can this plan run?  Shared memory, cluster support and (GRID) co-residency.
+kmc_status check_plan(kmc_ctx *c, const Plan &pl)
+{
+    for (int e = 0; e < 2; ++e) {
+        for (int gv = 0; gv < 2; ++gv) {
+            RunKernel kern = run_kernel_for(c->LD, e == 0, gv == 1, pl.mode == KMC_LAUNCH_CLUSTER);
+            CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+            if (pl.mode == KMC_LAUNCH_CLUSTER) {
+                if (pl.cluster > 8)
+                    CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(pl.n_cta);
+                cfg.blockDim = dim3(pl.wpb * 32);
+                cfg.dynamicSmemBytes = pl.smem;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = pl.cluster;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int ncl = 0;
+                cudaError_t ce = cudaOccupancyMaxActiveClusters(&ncl, (const void *)kern, &cfg);
+                if (ce != cudaSuccess || ncl < 1) {
+                    cudaGetLastError();
+                    return fail(c, KMC_EINVAL, "clusters of %d CTAs x %d warps with %zu bytes cannot be scheduled (%s)",
+                                pl.cluster, pl.wpb, pl.smem, ce != cudaSuccess ? cudaGetErrorString(ce) : "0 active clusters");
+                }
+            } else {
+                int nb = 0;
+                CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)kern, pl.wpb * 32, pl.smem));
+                if ((int64_t)nb * c->sm_count < pl.n_cta)
+                    return fail(c, KMC_EINVAL, "%d CTAs of %d warps cannot be co-resident (%d per SM)", pl.n_cta, pl.wpb, nb);
+            }
+        }
+    }
+    return KMC_OK;
+}
+
+kmc_status install_plan(kmc_ctx *c, Plan &pl)
+{
+    kmc_status s = check_plan(c, pl);
+    if (s != KMC_OK) return s;
+    std::vector<uint32_t> flat;
+    for (auto *v : {&pl.cta_slot_off, &pl.cta_col_off, &pl.cta_rt_off, &pl.rt_rep, &pl.slot_g, &pl.slot_rt, &pl.slot_nb})
+        flat.insert(flat.end(), v->begin(), v->end());
+    if (flat.size() > c->plan_words) {
+        if (c->d_plan) cudaFree(c->d_plan);
+        c->d_plan = nullptr;
+        c->plan_words = 0;
+        if ((s = dev_alloc(c, &c->d_plan, flat.size())) != KMC_OK) return s;
+        c->plan_words = flat.size();
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_plan, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice));
+    c->plan = std::move(pl);
+    return KMC_OK;
+}
+
+// Default plan: clusters when every replica fits one (smallest power of two
+// that covers the largest replica at one visit per warp and phase, up to 16),
+// otherwise the cooperative grid.
+kmc_status default_plan(kmc_ctx *c)
+{
+    int need = 1;
+    for (int r = 0; r < c->n_rep; ++r) {
+        const int per_colour = c->Dx[r] * c->Dx[r] / 4;
+        need = std::max(need, (per_colour + MAX_WPB - 1) / MAX_WPB);
+    }
+    int C = 1;
+    while (C < need) C *= 2;
+    std::string why;
+    if (C <= 16) {
+        int total_pc = 0;
+        for (int r = 0; r < c->n_rep; ++r) total_pc += c->Dx[r] * c->Dx[r] / 4;
+        for (int cl = C; cl <= 16; cl *= 2) {
+            // domains of one colour per warp: keep the CTA count within one wave
+            int load = 1;
+            while (load < 64 && (int64_t)((total_pc + MAX_WPB * load - 1) / (MAX_WPB * load)) > (int64_t)c->sm_count)
+                ++load;
+            Plan pl;
+            if (plan_cluster(c, cl, MAX_WPB, load, pl) == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
+            why = c->err;
+        }
+    }
+    for (int wpb = MAX_WPB; wpb >= 4; wpb /= 2) {
+        Plan pl;
+        if (plan_grid(c, c->sm_count, wpb, pl) == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
+        why = c->err;
+    }
+    return fail(c, KMC_EINVAL, "no launch plan fits this batch: %s", why.c_str());
+}
+
+kmc_status upload_rates(kmc_ctx *c)
+{
+    std::vector<uint64_t> A16((size_t)c->n_rep * 16, 0), inv16((size_t)c->n_rep * 16, 0);
+    std::vector<double> g32((size_t)c->n_rep * 32, 0.0);
+    for (int r = 0; r < c->n_rep; ++r) {
+        for (int q = 0; q < 10; ++q) {
+            A16[(size_t)r * 16 + q] = c->A[(size_t)r * 10 + q];
+            inv16[(size_t)r * 16 + q] = c->inv[(size_t)r * 10 + q];
+            g32[(size_t)r * 32 + q] = c->a[(size_t)r * 10 + q];
+            g32[(size_t)r * 32 + 10 + q] = c->gb[(size_t)r * 10 + q];
+            g32[(size_t)r * 32 + 20 + q] = c->gh[(size_t)r * 10 + q];
+        }
+    }
+    // synchronous copies: the host vectors are temporaries and the tables may
+    // be read by work already queued on another stream
+    CUDA_TRY(c, cudaMemcpy(c->d_A, A16.data(), A16.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_inv, inv16.data(), inv16.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_grad, g32.data(), g32.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_h, c->h.data(), c->h.size() * 8, cudaMemcpyHostToDevice));
+    return KMC_OK;
 }
 
 kmc_status launch_pack(kmc_ctx *c, cudaStream_t s)
@@ -268,79 +597,6 @@ kmc_status launch_reset_counters(kmc_ctx *c, cudaStream_t s)
     return KMC_OK;
 }
 
-// Validate a launch shape: shared memory and co-residency.
-kmc_status check_shape(kmc_ctx *c, int ctas, int wpb, bool grad_variant, int *spw_out, int *slot_out,
-                       int *smem_out)
-{
-    if (ctas < 1 || wpb < 1 || wpb > 16) return fail(c, KMC_EINVAL, "launch shape %d x %d out of range", ctas, wpb);
-    const int W = ctas * wpb;
-    int spw = 0;
-    for (int q = 0; q < 4; ++q) spw += (c->n_list[q] + W - 1) / W;
-    const int tile = c->LD * c->LD / 8;
-    const int slot = ((tile + DCTR_WORDS * 8) + 15) / 16 * 16;
-    const size_t smem = (size_t)wpb * spw * slot;
-    if (smem > (size_t)c->smem_optin)
-        return fail(c, KMC_EINVAL, "state does not fit: %zu bytes of shared memory per CTA needed, %d available",
-                    smem, c->smem_optin);
-    for (int e = 0; e < 2; ++e) {
-        RunKernel kern = run_kernel_for(c->LD, e == 0, grad_variant);
-        CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int nb = 0;
-        CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)kern, wpb * 32, smem));
-        if ((int64_t)nb * c->sm_count < ctas)
-            return fail(c, KMC_EINVAL, "%d CTAs of %d warps cannot be co-resident (%d per SM)", ctas, wpb, nb);
-    }
-    *spw_out = spw;
-    *slot_out = slot;
-    *smem_out = (int)smem;
-    return KMC_OK;
-}
-
-kmc_status default_shape(kmc_ctx *c)
-{
-    int maxn = 0;
-    for (int q = 0; q < 4; ++q) maxn = std::max(maxn, c->n_list[q]);
-    const int want = std::min(maxn, c->sm_count * 16);
-    int wpb = std::max(1, std::min(16, (want + c->sm_count - 1) / c->sm_count));
-    std::string last;
-    for (; wpb >= 1; --wpb) {
-        const int ctas = std::min((want + wpb - 1) / wpb, c->sm_count);
-        int spw, slot, smem;
-        if (check_shape(c, ctas, wpb, c->grad, &spw, &slot, &smem) == KMC_OK &&
-            check_shape(c, ctas, wpb, !c->grad, &spw, &slot, &smem) == KMC_OK) {
-            c->ctas = ctas;
-            c->wpb = wpb;
-            c->slots_per_warp = spw;
-            c->slot_bytes = slot;
-            c->smem_bytes = smem;
-            return KMC_OK;
-        }
-        last = c->err;
-    }
-    return fail(c, KMC_EINVAL, "no valid launch shape: %s", last.c_str());
-}
-
-kmc_status upload_rates(kmc_ctx *c)
-{
-    std::vector<uint64_t> A16((size_t)c->n_rep * 16, 0), inv16((size_t)c->n_rep * 16, 0);
-    std::vector<double> g32((size_t)c->n_rep * 32, 0.0);
-    for (int r = 0; r < c->n_rep; ++r) {
-        for (int q = 0; q < 10; ++q) {
-            A16[(size_t)r * 16 + q] = c->A[(size_t)r * 10 + q];
-            inv16[(size_t)r * 16 + q] = c->inv[(size_t)r * 10 + q];
-            g32[(size_t)r * 32 + q] = c->a[(size_t)r * 10 + q];
-            g32[(size_t)r * 32 + 10 + q] = c->gb[(size_t)r * 10 + q];
-            g32[(size_t)r * 32 + 20 + q] = c->gh[(size_t)r * 10 + q];
-        }
-    }
-    // synchronous copies: the host vectors are temporaries
-    CUDA_TRY(c, cudaMemcpy(c->d_A, A16.data(), A16.size() * 8, cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(c->d_inv, inv16.data(), inv16.size() * 8, cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(c->d_grad, g32.data(), g32.size() * 8, cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(c->d_h, c->h.data(), c->h.size() * 8, cudaMemcpyHostToDevice));
-    return KMC_OK;
-}
-
 kmc_status check_device_error(kmc_ctx *c)
 {
     int e = 0;
@@ -363,22 +619,22 @@ void free_all(kmc_ctx *c)
 {
     void **ptrs[] = {(void **)&c->d_L, (void **)&c->d_Dx, (void **)&c->d_dom_off, (void **)&c->d_dom_rep,
                      (void **)&c->d_site_off, (void **)&c->d_blk_off, (void **)&c->d_seed, (void **)&c->d_A,
-                     (void **)&c->d_inv, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_list[0],
-                     (void **)&c->d_list[1], (void **)&c->d_list[2], (void **)&c->d_list[3],
-                     (void **)&c->d_tiles, (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_bar,
-                     (void **)&c->d_err, (void **)&c->d_obs_acc, (void **)&c->d_tmp};
+                     (void **)&c->d_inv, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_tiles,
+                     (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_bar, (void **)&c->d_err,
+                     (void **)&c->d_obs_acc, (void **)&c->d_tmp, (void **)&c->d_plan};
     for (void **p : ptrs) {
         if (*p) cudaFree(*p);
         *p = nullptr;
     }
     c->obs_acc_words = 0;
+    c->plan_words = 0;
 }
 
 } // namespace
 
 extern "C" {
 
-int32_t kmc_version(void) { return 10000; }
+int32_t kmc_version(void) { return 10100; }
 
 const char *kmc_last_error(const kmc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -394,7 +650,7 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     if (!c) return KMC_ENOMEM;
     auto bail = [&](kmc_status s) {
         free_all(c);
-        // keep the context so that kmc_last_error works; caller destroys it
+        // keep the context so that kmc_last_error works; the caller destroys it
         *out = c;
         return s;
     };
@@ -429,32 +685,20 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
         ndom += (uint64_t)c->Dx[r] * c->Dx[r];
         blk += (uint64_t)Lr * Lr / 128;
     }
-    if (ndom >= (1ull << 31)) return bail(fail(c, KMC_EINVAL, "too many domains"));
+    if (ndom >= (1ull << 24)) return bail(fail(c, KMC_EINVAL, "too many domains (%llu)", (unsigned long long)ndom));
     c->dom_off[n_replicas] = (uint32_t)ndom;
     c->blk_off[n_replicas] = blk;
     c->n_dom = (int)ndom;
+    c->dom_rep.resize(ndom);
+    for (int r = 0; r < n_replicas; ++r)
+        for (uint32_t g = c->dom_off[r]; g < c->dom_off[r + 1]; ++g) c->dom_rep[g] = (uint32_t)r;
 
     cudaError_t ce = cudaGetDevice(&c->dev);
     if (ce != cudaSuccess) return bail(fail(c, KMC_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)));
     ce = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
     if (ce != cudaSuccess) return bail(fail(c, KMC_ECUDA, "device attributes: %s", cudaGetErrorString(ce)));
-    c->smem_optin -= 1024; // static shared memory of the kernel (barrier flag) and slack
-
-    // work lists per colour: entries (g << 32 | r), ascending g
-    std::vector<uint64_t> lists[4];
-    std::vector<uint32_t> dom_rep(ndom);
-    for (int r = 0; r < n_replicas; ++r) {
-        const int D = c->Dx[r];
-        for (int d = 0; d < D * D; ++d) {
-            const int bx = d % D, by = d / D;
-            const int colour = (bx & 1) | ((by & 1) << 1);
-            const uint64_t g = c->dom_off[r] + (uint64_t)d;
-            lists[colour].push_back((g << 32) | (uint64_t)r);
-            dom_rep[g] = (uint32_t)r;
-        }
-    }
-    for (int q = 0; q < 4; ++q) c->n_list[q] = (int)lists[q].size();
+    c->smem_optin -= 1024; // static shared memory of the run kernel and slack
 
     kmc_status s;
     const size_t tile = (size_t)L_d * L_d / 8;
@@ -470,7 +714,6 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     ALLOC(c->d_inv, (size_t)n_replicas * 16);
     ALLOC(c->d_grad, (size_t)n_replicas * 32);
     ALLOC(c->d_h, n_replicas);
-    for (int q = 0; q < 4; ++q) ALLOC(c->d_list[q], lists[q].size());
     ALLOC(c->d_tiles, ndom * tile);
     ALLOC(c->d_edges, ndom * 4);
     ALLOC(c->d_dctr, ndom * DCTR_WORDS);
@@ -482,20 +725,19 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
         c->d_tmp = tmp;
     }
 #undef ALLOC
-    auto up = [&](auto *dst, const auto *src, size_t n) { return upload(c, dst, src, n, c->stream); };
-    if ((s = up(c->d_L, c->L.data(), n_replicas)) != KMC_OK ||
-        (s = up(c->d_Dx, c->Dx.data(), n_replicas)) != KMC_OK ||
-        (s = up(c->d_dom_off, c->dom_off.data(), n_replicas + 1)) != KMC_OK ||
-        (s = up(c->d_dom_rep, dom_rep.data(), ndom)) != KMC_OK ||
-        (s = up(c->d_site_off, c->site_off.data(), n_replicas)) != KMC_OK ||
-        (s = up(c->d_blk_off, c->blk_off.data(), n_replicas + 1)) != KMC_OK ||
-        (s = up(c->d_seed, c->seed.data(), n_replicas)) != KMC_OK)
-        return bail(s);
-    for (int q = 0; q < 4; ++q)
-        if (!lists[q].empty() && (s = up(c->d_list[q], lists[q].data(), lists[q].size())) != KMC_OK) return bail(s);
-    // the host vectors above are locals: make the copies complete before they go away
-    ce = cudaStreamSynchronize(c->stream);
-    if (ce != cudaSuccess) return bail(fail(c, KMC_ECUDA, "upload: %s", cudaGetErrorString(ce)));
+    struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
+        {c->d_L, c->L.data(), (size_t)n_replicas * 4},
+        {c->d_Dx, c->Dx.data(), (size_t)n_replicas * 4},
+        {c->d_dom_off, c->dom_off.data(), (size_t)(n_replicas + 1) * 4},
+        {c->d_dom_rep, c->dom_rep.data(), (size_t)ndom * 4},
+        {c->d_site_off, c->site_off.data(), (size_t)n_replicas * 8},
+        {c->d_blk_off, c->blk_off.data(), (size_t)(n_replicas + 1) * 8},
+        {c->d_seed, c->seed.data(), (size_t)n_replicas * 8},
+    };
+    for (const Up &u : ups) {
+        ce = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) return bail(fail(c, KMC_ECUDA, "upload: %s", cudaGetErrorString(ce)));
+    }
     ce = cudaMemset(c->d_err, 0, sizeof(int));
     if (ce != cudaSuccess) return bail(fail(c, KMC_ECUDA, "memset: %s", cudaGetErrorString(ce)));
 
@@ -503,7 +745,7 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     std::vector<double> b0(n_replicas, 0.4), h0(n_replicas, 0.0);
     *out = c;
     if ((s = kmc_set_rates(c, 1.0, b0.data(), h0.data(), 1.0, KMC_RATE_METROPOLIS)) != KMC_OK) return bail(s);
-    if ((s = default_shape(c)) != KMC_OK) return bail(s);
+    if ((s = default_plan(c)) != KMC_OK) return bail(s);
     if ((s = kmc_reset(c, init, stream)) != KMC_OK) return bail(s);
     return KMC_OK;
 }
@@ -598,27 +840,38 @@ kmc_status kmc_get_rate_table(const kmc_ctx *c, int32_t replica, double *a, uint
     return KMC_OK;
 }
 
-kmc_status kmc_set_launch(kmc_ctx *c, int32_t ctas, int32_t warps_per_cta)
+kmc_status kmc_set_launch(kmc_ctx *c, int32_t mode, int32_t size, int32_t warps_per_cta)
 {
     if (!c) return KMC_EINVAL;
-    if (ctas == 0 && warps_per_cta == 0) return default_shape(c);
-    int spw, slot, smem;
-    kmc_status s = check_shape(c, ctas, warps_per_cta, c->grad, &spw, &slot, &smem);
-    if (s != KMC_OK) return s;
-    c->ctas = ctas;
-    c->wpb = warps_per_cta;
-    c->slots_per_warp = spw;
-    c->slot_bytes = slot;
-    c->smem_bytes = smem;
-    return KMC_OK;
+    if (mode == KMC_LAUNCH_AUTO) return default_plan(c);
+    if (warps_per_cta < 1 || warps_per_cta > MAX_WPB) return fail(c, KMC_EINVAL, "warps_per_cta must be 1..%d", MAX_WPB);
+    Plan pl;
+    kmc_status s;
+    if (mode == KMC_LAUNCH_CLUSTER) {
+        if (size != 1 && size != 2 && size != 4 && size != 8 && size != 16)
+            return fail(c, KMC_EINVAL, "cluster size must be 1, 2, 4, 8 or 16");
+        int need = 1;
+        for (int r = 0; r < c->n_rep; ++r)
+            need = std::max(need, (c->Dx[r] * c->Dx[r] / 4 + warps_per_cta * size - 1) / (warps_per_cta * size));
+        if ((s = plan_cluster(c, size, warps_per_cta, need, pl)) != KMC_OK) return s;
+    } else if (mode == KMC_LAUNCH_GRID) {
+        if (size < 1) return fail(c, KMC_EINVAL, "grid needs >= 1 CTA");
+        if ((s = plan_grid(c, size, warps_per_cta, pl)) != KMC_OK) return s;
+    } else {
+        return fail(c, KMC_EINVAL, "bad launch mode %d", mode);
+    }
+    return install_plan(c, pl);
 }
 
-kmc_status kmc_get_launch(const kmc_ctx *c, int32_t *ctas, int32_t *wpb, int32_t *smem)
+kmc_status kmc_get_launch(const kmc_ctx *c, int32_t *mode, int32_t *size, int32_t *ctas, int32_t *warps_per_cta,
+                          int32_t *smem_bytes)
 {
     if (!c) return KMC_EINVAL;
-    if (ctas) *ctas = c->ctas;
-    if (wpb) *wpb = c->wpb;
-    if (smem) *smem = c->smem_bytes;
+    if (mode) *mode = c->plan.mode;
+    if (size) *size = c->plan.mode == KMC_LAUNCH_CLUSTER ? c->plan.cluster : c->plan.n_cta;
+    if (ctas) *ctas = c->plan.n_cta;
+    if (warps_per_cta) *warps_per_cta = c->plan.wpb;
+    if (smem_bytes) *smem_bytes = (int32_t)c->plan.smem;
     return KMC_OK;
 }
 
@@ -634,9 +887,6 @@ kmc_status kmc_enable_grad(kmc_ctx *c, int32_t enable)
 {
     if (!c) return KMC_EINVAL;
     c->grad = enable != 0;
-    int spw, slot, smem;
-    kmc_status s = check_shape(c, c->ctas, c->wpb, c->grad, &spw, &slot, &smem);
-    if (s != KMC_OK) return s;
     return KMC_OK;
 }
 
@@ -650,6 +900,8 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     if (time_mode != KMC_TIME_EXPONENTIAL && time_mode != KMC_TIME_EXPECTED) return fail(c, KMC_EINVAL, "bad time mode");
     if (obs_every < 0) return fail(c, KMC_EINVAL, "obs_every must be >= 0");
     if (c->sched_done + n_schedules >= (1ll << 52)) return fail(c, KMC_EINVAL, "schedule index overflow");
+    if (c->debug_extra > 0 && c->plan.mode != KMC_LAUNCH_GRID)
+        return fail(c, KMC_EINVAL, "the barrier test hook needs the GRID launch mode");
     c->stream = (cudaStream_t)stream;
     if (n_schedules == 0) return KMC_OK;
     cudaStream_t s = c->stream;
@@ -668,7 +920,6 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
         CUDA_TRY(c, cudaMemsetAsync(c->d_obs_acc, 0, words * 8, s));
     }
     if ((st = launch_pack(c, s)) != KMC_OK) return st;
-    CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), s));
     RunParams P = run_params(c);
     P.schedule = schedule;
     P.obs_every = want_obs ? obs_every : 0;
@@ -676,17 +927,34 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     P.sched_begin = c->sched_done;
     P.n_sched = n_schedules;
     P.visits_before = c->visits_done;
-    RunKernel kern = run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad);
-    CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes));
-    void *args[] = {(void *)&P};
+    const Plan &pl = c->plan;
+    const bool cluster = pl.mode == KMC_LAUNCH_CLUSTER;
+    RunKernel kern = run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad, cluster);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (c->prof) {
         CUDA_TRY(c, cudaEventCreate(&ev0));
         CUDA_TRY(c, cudaEventCreate(&ev1));
         CUDA_TRY(c, cudaEventRecord(ev0, s));
     }
-    CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)kern, dim3(c->ctas), dim3(c->wpb * 32), args,
-                                            (size_t)c->smem_bytes, s));
+    if (cluster) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(pl.n_cta);
+        cfg.blockDim = dim3(pl.wpb * 32);
+        cfg.dynamicSmemBytes = pl.smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = pl.cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CUDA_TRY(c, cudaLaunchKernelEx(&cfg, kern, P));
+    } else {
+        CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), s));
+        void *args[] = {(void *)&P};
+        CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)kern, dim3(pl.n_cta), dim3(pl.wpb * 32), args, pl.smem, s));
+    }
     ++c->launches;
     if (c->prof) {
         CUDA_TRY(c, cudaEventRecord(ev1, s));
@@ -720,17 +988,6 @@ kmc_status kmc_observables(kmc_ctx *c, double *E_per_site, double *m, double *t,
     if ((st = launch_pack(c, s)) != KMC_OK) return st;
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(c->d_tmp);
     const size_t words = (size_t)c->n_rep * OBS_WORDS;
-    if (words * 8 > (size_t)c->n_dom * 24) {
-        // staging too small for this many replicas: use the observation buffer
-        if (words > c->obs_acc_words) {
-            if (c->d_obs_acc) cudaFree(c->d_obs_acc);
-            c->d_obs_acc = nullptr;
-            c->obs_acc_words = 0;
-            if ((st = dev_alloc(c, &c->d_obs_acc, words)) != KMC_OK) return st;
-            c->obs_acc_words = words;
-        }
-        acc = c->d_obs_acc;
-    }
     CUDA_TRY(c, cudaMemsetAsync(acc, 0, words * 8, s));
     RunParams P = run_params(c);
     const bool expo = c->last_time_mode == KMC_TIME_EXPONENTIAL;
@@ -765,9 +1022,7 @@ kmc_status kmc_observables(kmc_ctx *c, double *E_per_site, double *m, double *t,
     }
     if (flips) {
         std::vector<int64_t> fl(c->n_dom);
-        std::vector<uint64_t> hs(c->n_dom);
-        std::vector<double> tt(c->n_dom);
-        if ((st = kmc_domain_state(c, hs.data(), fl.data(), tt.data())) != KMC_OK) return st;
+        if ((st = kmc_domain_state(c, nullptr, fl.data(), nullptr)) != KMC_OK) return st;
         for (int r = 0; r < c->n_rep; ++r) {
             int64_t f = 0;
             for (uint32_t g = c->dom_off[r]; g < c->dom_off[r + 1]; ++g) f += fl[g];

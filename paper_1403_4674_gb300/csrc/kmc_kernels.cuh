@@ -1,22 +1,28 @@
 // kmc_kernels.cuh -- sm_103a device code of the sequential-update parallel
 // kinetic Monte Carlo (Nilmeier & Marian, arXiv:1403.4674).
 //
-// Data layout (device):
+// Data layout (device memory, between launches):
 //   * caller spins: int8, replicas concatenated, row-major.
 //   * bit tiles: replica r, domain d = by*Dx + bx owns LD*LD bits, row y of
 //     the domain at bits [y*LD, (y+1)*LD) of the tile, bit x = column x,
-//     1 = spin up.  Tile bytes = LD*LD/8.
+//     1 = spin up.  Tile bytes = LD*LD/8.  Global domain id g = dom_off[r] + d.
 //   * edges[g*4 + {N,S,W,E}]: the domain's first row, last row, first column
 //     and last column as bit masks.  Column bit of row y is
 //     (y % RPL)*32 + y / RPL (RPL = rows per lane, 2 for LD = 64, else 1).
-//     Neighbours read their frozen halo (Sec. 2.2) from here.
-//   * per-domain counters (hash, flips, clock mantissa, clock exponent,
-//     score beta, score h) -- DCTR_WORDS words.
+//   * per-domain counters dctr[g*6 + ...]: event hash, real flips, clock
+//     mantissa, clock exponent, score d/dbeta, score d/dh.
 //
-// The run kernel is persistent and cooperative: every warp owns a fixed set
-// of domains; their tiles and counters stay in shared memory for the whole
-// launch, only the edges travel through L2 between colour phases, and a
-// bounded grid barrier separates phases of different colours.
+// The run kernel is persistent: every CTA owns a fixed set of domains (its
+// "slots") for the whole launch; their tiles, edges, counters and the rate
+// tables of their replicas live in shared memory.  Between colour phases the
+// only communication is the frozen halo (Sec. 2.2) -- the four edge words of
+// each neighbour:
+//   * CLUSTER mode: every replica is resident in one thread-block cluster
+//     (1..16 CTAs); halos are read from the owner CTA through distributed
+//     shared memory and phases are separated by the hardware cluster barrier;
+//   * GRID mode (a replica larger than a cluster can hold): one cooperative
+//     grid; halos go through L2 and phases are separated by a bounded grid
+//     barrier.
 #pragma once
 
 #include <cstdint>
@@ -35,8 +41,19 @@ constexpr int ERR_TIMEOUT = 1, ERR_SPIN = 2, ERR_INTERNAL = 3;
 constexpr int SCHED_PALINDROME = 0, SCHED_FIXED = 1, SCHED_RANDOM_PERM = 2;
 constexpr int OBS_WORDS = 5; // bonds, mag, clock sum, score beta sum, score h sum
 
+// Replica table staged in shared memory (bytes):
+//   [0,128) A[16] fixed-point acceptance, [128,256) inv[16] = floor((2^64-1)/A),
+//   [256,512) grad[32] = a[10], dlog a/dbeta[10], dlog a/dh[10],
+//   [512] seed, [520] dom_off, [524] Dx.
+constexpr int RT_BYTES = 528;
+constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524;
+// Slot: [tile][edges 32][counters 48][meta 32]; meta u32: g, replica, d, rt, nb[4].
+constexpr int SLOT_EXTRA = 32 + 48 + 32;
+constexpr int META_G = 0, META_R = 1, META_D = 2, META_RT = 3, META_NB = 4;
+
+template <int LD> __host__ __device__ constexpr int slot_bytes() { return ((LD * LD / 8 + SLOT_EXTRA) + 15) / 16 * 16; }
+
 struct RunParams {
-    // geometry and schedule
     int n_rep;
     int k;
     int schedule;
@@ -44,31 +61,34 @@ struct RunParams {
     int64_t sched_begin;
     int64_t n_sched;
     int64_t visits_before; // per-domain visits before this launch (clock mode EXPECTED)
-    // per replica
+    // per replica (global)
     const int32_t *rep_Dx;
     const uint32_t *rep_dom_off;
     const uint64_t *rep_seed;
     const uint64_t *rep_A;   // [n_rep][16]
     const uint64_t *rep_inv; // [n_rep][16]
-    const double *rep_grad;  // [n_rep][32]: a[0..9], dlog a/dbeta [10..19], /dh [20..29]
-    // work lists: colour c entries (g << 32 | replica)
-    const uint64_t *list[4];
-    int n_list[4];
+    const double *rep_grad;  // [n_rep][32]
+    // plan: per CTA slot ranges (colour-sorted), replica tables, neighbours
+    const uint32_t *cta_slot_off; // [n_cta + 1]
+    const uint32_t *cta_col_off;  // [n_cta][5], relative to the CTA's first slot
+    const uint32_t *cta_rt_off;   // [n_cta + 1]
+    const uint32_t *rt_rep;       // replica id of each staged table
+    const uint32_t *slot_g;       // global domain id of each slot
+    const uint32_t *slot_rt;      // local table index of each slot
+    const uint32_t *slot_nb;      // [n_slots][4]: GRID: neighbour g; CLUSTER: rank << 24 | local slot
+    int max_rt;                   // table capacity per CTA (uniform layout)
+    int cluster;                  // 0 = GRID mode, else cluster size
     // state
     uint8_t *tiles;
     uint64_t *dctr;
     uint64_t *edges;
     // observables scratch [n_obs][n_rep][OBS_WORDS]
     unsigned long long *obs_acc;
-    // barrier
+    // grid barrier
     unsigned *bar_count;
     int *err;
     uint64_t bar_limit_ns;
     int debug_extra;
-    // launch shape
-    int total_warps;
-    int slots_per_warp;
-    int slot_bytes;
     double lambda; // n_d * nu
 };
 
@@ -108,6 +128,27 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// distributed shared memory (thread-block clusters)
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t local_addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ uint64_t ld_dsmem(uint32_t addr)
+{
+    uint64_t v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Per-domain-size geometry.
@@ -123,7 +164,6 @@ template <int LD> struct Geo {
         typename std::conditional<LD == 32, uint32_t,
                                   typename std::conditional<LD == 16, uint16_t, uint8_t>::type>::type>::type;
     static constexpr row_t FULL = (LD >= 64) ? (row_t)~0ull : (row_t)((1ull << LD) - 1ull);
-    static __device__ __forceinline__ int colbit(int y) { return (y % RPL) * 32 + y / RPL; }
 };
 
 __device__ __forceinline__ int popc_row(uint32_t v) { return __popc(v); }
@@ -142,6 +182,18 @@ __device__ __forceinline__ int select_bit(uint64_t m, uint32_t rr)
     c = __popc(w & 0x3u);    if (rr >= c) { rr -= c; w >>= 2;  pos += 2; }
     if (rr >= (w & 1u)) pos += 1;
     return pos;
+}
+
+// Exclusive prefix over lanes of a small count v < 2^NBITS, from NBITS ballots
+// of its bit planes (no shuffle chain).
+template <int NBITS>
+__device__ __forceinline__ uint32_t excl_prefix_small(uint32_t v, int lane)
+{
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t s = 0;
+#pragma unroll
+    for (int b = 0; b < NBITS; ++b) s += (uint32_t)__popc(__ballot_sync(FULL_WARP, (v >> b) & 1u) & lt) << b;
+    return s;
 }
 
 // Normalised unsigned mantissa product for the exponential clock:
@@ -174,7 +226,8 @@ __device__ __forceinline__ double domain_time(bool expo, uint64_t M, int64_t E, 
 // ---------------------------------------------------------------------------
 // Row-plane state of one domain held by one warp: lane l holds rows
 // l*RPL .. l*RPL+RPL-1 (bit x = column x), plus the bit-sliced count of up
-// neighbours b2 b1 b0 of every site.
+// neighbours b2 b1 b0 of every site (App. A: the site's class is
+// 5*(spin up) + number of up neighbours).
 // ---------------------------------------------------------------------------
 template <int LD> struct Planes {
     using G = Geo<LD>;
@@ -265,66 +318,55 @@ __device__ __forceinline__ double warp_sum10(double v)
     return v;
 }
 
+// Per-domain counters, identical in every lane during a visit.
+struct Counters {
+    uint64_t H, flips, clkM;
+    int64_t clkE;
+    double sb, sh;
+};
+
 // ---------------------------------------------------------------------------
 // One domain visit (Sec. 2.2): nfused consecutive global phases of the same
-// colour, k uniformised steps each, halo frozen (read once from the edges).
-// Steps are drawn 32 at a time (lane i draws step base+i); null steps are
-// skipped with a ballot of (target >= R') since the state does not change
-// between real events.
+// colour, k uniformised steps each, with the halo hN/hS/hW/hE frozen.
+//
+// Step j of global phase np draws Philox {j, d, np_lo, np_hi} with the replica
+// seed: target = (w0 | w1<<32) >> 1 uniform on [0, n_d 2^P), V = (w2 | w3<<32)
+// >> 11 plus 1.  target >= R' = sum_c n_c A_c is a null step (the diagonal of
+// App. A Eq. Glauber_TM); otherwise class c = first class whose inclusive
+// cumulative rate exceeds target, member jj = (target - C_{c-1}) / A_c in
+// row-major order flips (the n-fold way's cumulative selection, Sec. 2.1).
+// Steps are drawn 32 at a time (lane i draws step base+i); runs of null steps
+// are skipped with one ballot since the state does not change between real
+// events.  rt: the replica table in shared memory.
 // ---------------------------------------------------------------------------
 template <int LD, bool EXPO, bool GRAD>
-__device__ __forceinline__ void visit_domain(const RunParams &P, uint8_t *slot, uint64_t g, uint32_t r, uint32_t d,
-                             uint64_t np0, int nfused, int lane)
+__device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const uint8_t *rt,
+                                           typename Geo<LD>::row_t hN, typename Geo<LD>::row_t hS,
+                                           uint64_t hW, uint64_t hE, uint32_t d, uint64_t np0,
+                                           int nfused, int k, int lane, int *err)
 {
     using G = Geo<LD>;
     using row_t = typename G::row_t;
-    using mem_t = typename G::mem_t;
-    const int Dx = __ldg(&P.rep_Dx[r]);
-    const uint64_t gbase = g - d;
-    const int bx = (int)(d % (uint32_t)Dx), by = (int)(d / (uint32_t)Dx);
-    const uint32_t dN = (uint32_t)(((by + Dx - 1) % Dx) * Dx + bx);
-    const uint32_t dS = (uint32_t)(((by + 1) % Dx) * Dx + bx);
-    const uint32_t dW = (uint32_t)(by * Dx + (bx + Dx - 1) % Dx);
-    const uint32_t dE = (uint32_t)(by * Dx + (bx + 1) % Dx);
-    const row_t hN = (row_t)ld_cg(&P.edges[(gbase + dN) * 4 + EDGE_S]);
-    const row_t hS = (row_t)ld_cg(&P.edges[(gbase + dS) * 4 + EDGE_N]);
-    const uint64_t hW = ld_cg(&P.edges[(gbase + dW) * 4 + EDGE_E]);
-    const uint64_t hE = ld_cg(&P.edges[(gbase + dE) * 4 + EDGE_W]);
-
-    const uint64_t seed = __ldg(&P.rep_seed[r]);
+    const uint64_t seed = *reinterpret_cast<const uint64_t *>(rt + RT_SEED);
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     uint64_t Ac = 0, invc = 0;
     double a_c = 0.0, gb_c = 0.0, gh_c = 0.0;
     if (lane < 10) {
-        Ac = __ldg(&P.rep_A[(size_t)r * 16 + lane]);
-        invc = __ldg(&P.rep_inv[(size_t)r * 16 + lane]);
+        Ac = reinterpret_cast<const uint64_t *>(rt)[lane];
+        invc = reinterpret_cast<const uint64_t *>(rt + 128)[lane];
         if (GRAD) {
-            a_c = __ldg(&P.rep_grad[(size_t)r * 32 + lane]);
-            gb_c = __ldg(&P.rep_grad[(size_t)r * 32 + 10 + lane]);
-            gh_c = __ldg(&P.rep_grad[(size_t)r * 32 + 20 + lane]);
+            const double *gr = reinterpret_cast<const double *>(rt + 256);
+            a_c = gr[lane];
+            gb_c = gr[10 + lane];
+            gh_c = gr[20 + lane];
         }
     }
-
-    Planes<LD> pl;
-    pl.valid = (lane < G::NACT) ? G::FULL : (row_t)0;
-    const mem_t *trow = reinterpret_cast<const mem_t *>(slot);
-#pragma unroll
-    for (int t = 0; t < G::RPL; ++t) pl.S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
     pl.build(lane, hN, hS, hW, hE);
-
-    uint64_t *ctr = reinterpret_cast<uint64_t *>(slot + G::TILE_BYTES);
-    uint64_t H = ctr[DCTR_HASH];
-    uint64_t nflip = 0;
-    uint64_t clkM = ctr[DCTR_CLKM];
-    int64_t clkE = (int64_t)ctr[DCTR_CLKE];
-    double sc_b = 0.0, sc_h = 0.0;
-
     uint32_t n_c = class_counts<LD>(pl, lane);
     uint64_t Wc = (uint64_t)n_c * Ac;
     uint64_t Cinc = prefix16(Wc, lane);
     uint64_t R = __shfl_sync(FULL_WARP, Cinc, 9);
 
-    // score helpers: real-valued R and dR/dtheta of the current state
     double nd_minus_R = 0.0, Db = 0.0, Dh = 0.0;
     auto grad_state = [&]() {
         if (GRAD) {
@@ -337,7 +379,6 @@ __device__ __forceinline__ void visit_domain(const RunParams &P, uint8_t *slot, 
     };
     grad_state();
 
-    const int k = P.k;
     const int total = nfused * k;
     for (int base = 0; base < total; base += 32) {
         const int s = base + lane;
@@ -358,10 +399,10 @@ __device__ __forceinline__ void visit_domain(const RunParams &P, uint8_t *slot, 
             const unsigned real = __ballot_sync(FULL_WARP, lane >= pos && tgt < R);
             const int jx = real ? __ffs(real) - 1 : chunk_end;
             if (GRAD && jx > pos) {
-                // (jx - pos) null steps in the current state
+                // (jx - pos) null steps in the current state: d log(1 - R/n_d)
                 const double q = (double)(jx - pos);
-                sc_b -= q * Db / nd_minus_R;
-                sc_h -= q * Dh / nd_minus_R;
+                cn.sb -= q * Db / nd_minus_R;
+                cn.sh -= q * Dh / nd_minus_R;
             }
             if (!real) break;
             const uint64_t t = __shfl_sync(FULL_WARP, tgt, jx);
@@ -377,8 +418,8 @@ __device__ __forceinline__ void visit_domain(const RunParams &P, uint8_t *slot, 
             }
             const uint32_t jj = (uint32_t)__shfl_sync(FULL_WARP, q, c);
             if (GRAD) {
-                sc_b += __shfl_sync(FULL_WARP, gb_c, c);
-                sc_h += __shfl_sync(FULL_WARP, gh_c, c);
+                cn.sb += __shfl_sync(FULL_WARP, gb_c, c);
+                cn.sh += __shfl_sync(FULL_WARP, gh_c, c);
             }
             // rank selection: jj-th member of class c in row-major order
             row_t m[G::RPL];
@@ -388,16 +429,10 @@ __device__ __forceinline__ void visit_domain(const RunParams &P, uint8_t *slot, 
                 m[tt] = pl.mask(c, tt);
                 cl += popc_row(m[tt]);
             }
-            uint32_t incl = cl;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t v = __shfl_up_sync(FULL_WARP, incl, off);
-                if (lane >= off) incl += v;
-            }
-            const uint32_t excl = incl - cl;
-            const unsigned win = __ballot_sync(FULL_WARP, jj >= excl && jj < incl);
+            const uint32_t excl = excl_prefix_small<(LD > 32) ? 8 : 7>(cl, lane);
+            const unsigned win = __ballot_sync(FULL_WARP, jj >= excl && jj < excl + cl);
             if (!win) {
-                if (lane == 0) atomicCAS(P.err, 0, ERR_INTERNAL);
+                if (lane == 0) atomicCAS(err, 0, ERR_INTERNAL);
                 break;
             }
             const int wl = __ffs(win) - 1;
@@ -409,7 +444,7 @@ __device__ __forceinline__ void visit_domain(const RunParams &P, uint8_t *slot, 
                     const uint32_t p0 = (uint32_t)popc_row(m[0]);
                     if (rr >= p0) { rr -= p0; tsel = 1; }
                 }
-                const int col = select_bit((uint64_t)m[tsel], rr);
+                const int col = select_bit((uint64_t)(tsel ? m[G::RPL - 1] : m[0]), rr);
                 yc = ((uint32_t)(lane * G::RPL + tsel) << 8) | (uint32_t)col;
             }
             yc = __shfl_sync(FULL_WARP, yc, wl);
@@ -423,8 +458,8 @@ __device__ __forceinline__ void visit_domain(const RunParams &P, uint8_t *slot, 
                 const int j = sx - f * k;
                 const uint64_t np = np0 + (uint64_t)f;
                 const uint64_t e = (np << 32) | ((uint64_t)j << 16) | (uint64_t)(y * LD + col);
-                H = (H ^ e) * HASH_PRIME;
-                ++nflip;
+                cn.H = (cn.H ^ e) * HASH_PRIME;
+                ++cn.flips;
             }
             pl.build(lane, hN, hS, hW, hE);
             n_c = class_counts<LD>(pl, lane);
@@ -444,39 +479,26 @@ __device__ __forceinline__ void visit_domain(const RunParams &P, uint8_t *slot, 
                 const int64_t e2 = __shfl_xor_sync(FULL_WARP, e, off);
                 mant_mul(m, e, m2, e2);
             }
-            mant_mul(clkM, clkE, m, e);
+            mant_mul(cn.clkM, cn.clkE, m, e);
         }
     }
+}
 
-    // write back rows, publish edges, update counters
-    mem_t *wrow = reinterpret_cast<mem_t *>(slot);
-    if (lane < G::NACT) {
-#pragma unroll
-        for (int t = 0; t < G::RPL; ++t) wrow[lane * G::RPL + t] = (mem_t)pl.S[t];
-    }
+// Four edge words of the warp's domain (N row, S row, W column, E column);
+// lane i (< 4) returns edge i.
+template <int LD>
+__device__ __forceinline__ uint64_t edge_words(const typename Geo<LD>::row_t (&S)[Geo<LD>::RPL], int lane)
+{
+    using G = Geo<LD>;
     uint64_t colW = 0, colE = 0;
 #pragma unroll
     for (int t = 0; t < G::RPL; ++t) {
-        colW |= (uint64_t)__ballot_sync(FULL_WARP, (pl.S[t] & 1u) != 0) << (32 * t);
-        colE |= (uint64_t)__ballot_sync(FULL_WARP, ((pl.S[t] >> (LD - 1)) & 1u) != 0) << (32 * t);
+        colW |= (uint64_t)__ballot_sync(FULL_WARP, (S[t] & 1u) != 0) << (32 * t);
+        colE |= (uint64_t)__ballot_sync(FULL_WARP, ((S[t] >> (LD - 1)) & 1u) != 0) << (32 * t);
     }
-    const uint64_t rowN = (uint64_t)__shfl_sync(FULL_WARP, pl.S[0], 0);
-    const uint64_t rowS = (uint64_t)__shfl_sync(FULL_WARP, pl.S[G::RPL - 1], G::NACT - 1);
-    if (lane < 4) {
-        const uint64_t v = (lane == EDGE_N) ? rowN : (lane == EDGE_S) ? rowS : (lane == EDGE_W) ? colW : colE;
-        st_cg(&P.edges[g * 4 + lane], v);
-    }
-    if (lane == 0) {
-        ctr[DCTR_HASH] = H;
-        ctr[DCTR_FLIPS] += nflip;
-        ctr[DCTR_CLKM] = clkM;
-        ctr[DCTR_CLKE] = (uint64_t)clkE;
-        if (GRAD) {
-            reinterpret_cast<double *>(ctr)[DCTR_SB] += sc_b;
-            reinterpret_cast<double *>(ctr)[DCTR_SH] += sc_h;
-        }
-    }
-    __syncwarp();
+    const uint64_t rowN = (uint64_t)__shfl_sync(FULL_WARP, S[0], 0);
+    const uint64_t rowS = (uint64_t)__shfl_sync(FULL_WARP, S[G::RPL - 1], G::NACT - 1);
+    return (lane == EDGE_N) ? rowN : (lane == EDGE_S) ? rowS : (lane == EDGE_W) ? colW : colE;
 }
 
 // ---------------------------------------------------------------------------
@@ -518,43 +540,11 @@ __device__ __forceinline__ void domain_bonds_mag(const typename Geo<LD>::row_t (
     mag = (int)__reduce_add_sync(FULL_WARP, (unsigned)m);
 }
 
-template <int LD, bool EXPO>
-__device__ void observe_domain(const RunParams &P, const uint8_t *slot, uint64_t g, uint32_t r,
-                               uint32_t d, int64_t visits, unsigned long long *acc, int lane)
-{
-    using G = Geo<LD>;
-    using row_t = typename G::row_t;
-    using mem_t = typename G::mem_t;
-    const int Dx = __ldg(&P.rep_Dx[r]);
-    const uint64_t gbase = g - d;
-    const int bx = (int)(d % (uint32_t)Dx), by = (int)(d / (uint32_t)Dx);
-    const uint32_t dS = (uint32_t)(((by + 1) % Dx) * Dx + bx);
-    const uint32_t dE = (uint32_t)(by * Dx + (bx + 1) % Dx);
-    const uint64_t hS = ld_cg(&P.edges[(gbase + dS) * 4 + EDGE_N]);
-    const uint64_t hE = ld_cg(&P.edges[(gbase + dE) * 4 + EDGE_W]);
-    row_t S[G::RPL];
-    const mem_t *trow = reinterpret_cast<const mem_t *>(slot);
-#pragma unroll
-    for (int t = 0; t < G::RPL; ++t) S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
-    int bonds, mag;
-    domain_bonds_mag<LD>(S, hE, hS, lane, bonds, mag);
-    if (lane == 0) {
-        const uint64_t *ctr = reinterpret_cast<const uint64_t *>(slot + G::TILE_BYTES);
-        const double t = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE],
-                                     visits * (int64_t)P.k, P.lambda);
-        atomicAdd(&acc[0], (unsigned long long)(long long)bonds);
-        atomicAdd(&acc[1], (unsigned long long)(long long)mag);
-        atomicAdd(reinterpret_cast<double *>(&acc[2]), t);
-        atomicAdd(reinterpret_cast<double *>(&acc[3]), reinterpret_cast<const double *>(ctr)[DCTR_SB]);
-        atomicAdd(reinterpret_cast<double *>(&acc[4]), reinterpret_cast<const double *>(ctr)[DCTR_SH]);
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Bounded grid barrier.  Thread 0 of every CTA arrives on a monotone counter
-// and spins (acquire loads) until all CTAs of barrier number `no` arrived, or
-// until the limit expires / another CTA reported an error.  Returns false on
-// error; the caller must then leave the kernel.
+// Bounded grid barrier (GRID mode).  Thread 0 of every CTA arrives on a
+// monotone counter and spins (acquire loads) until all CTAs of barrier `no`
+// arrived, or until the limit expires / another CTA reported an error.
+// Returns false on error; the caller then leaves the kernel.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool grid_barrier(const RunParams &P, unsigned &no, int *s_ok)
 {
@@ -595,13 +585,12 @@ __device__ __forceinline__ int perm_colour(uint64_t seed, uint64_t n, int p)
     int idx = (int)__umul64hi(x, 24ull);
     int pool = 0x3210; // nibbles: remaining colours in order
     int colour = 0;
-    const int fact[4] = {6, 2, 1, 1};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int sel = idx / fact[q];
-        idx -= sel * fact[q];
+        const int f = (q == 0) ? 6 : (q == 1) ? 2 : 1; // (3 - q)!
+        const int sel = idx / f;
+        idx -= sel * f;
         const int c = (pool >> (4 * sel)) & 0xF;
-        // remove nibble sel
         const int low = pool & ((1 << (4 * sel)) - 1);
         const int high = pool >> (4 * (sel + 1));
         pool = low | (high << (4 * sel));
@@ -617,49 +606,155 @@ __device__ __forceinline__ int fixed_colour(int schedule, int p)
 }
 
 // ---------------------------------------------------------------------------
-// Persistent cooperative run kernel.
+// Persistent run kernel (both modes).
 // ---------------------------------------------------------------------------
-template <int LD, bool EXPO, bool GRAD>
-__global__ void __launch_bounds__(512) run_kernel(const RunParams P)
+template <int LD, bool EXPO, bool GRAD, bool CLUSTER>
+__global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
 {
+    using G = Geo<LD>;
+    using row_t = typename G::row_t;
+    using mem_t = typename G::mem_t;
+    constexpr int TB = G::TILE_BYTES;
+    constexpr int SB = slot_bytes<LD>();
+    constexpr int OFF_EDGE = TB, OFF_CTR = TB + 32, OFF_META = TB + 80;
+
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int W = P.total_warps;
-    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-    uint8_t *mine = smem + (size_t)wib * P.slots_per_warp * P.slot_bytes;
-    constexpr int TB = Geo<LD>::TILE_BYTES;
-    const int ctr_bytes = DCTR_WORDS * 8;
+    const int nwarps = blockDim.x >> 5;
+    const int b = blockIdx.x;
+    uint8_t *tables = smem;
+    uint8_t *slots = smem + (size_t)P.max_rt * RT_BYTES;
+    const uint32_t slot0 = P.cta_slot_off[b];
+    const int nslot = (int)(P.cta_slot_off[b + 1] - slot0);
+    const uint32_t *col_off = P.cta_col_off + (size_t)b * 5;
 
-    // slot offsets of the warp's entries: colour c entries first(c)
-    int first[4];
-    {
-        int acc = 0;
+    // ---- stage replica tables and owned slots ----
+    const uint32_t rt0 = P.cta_rt_off[b];
+    const int nrt = (int)(P.cta_rt_off[b + 1] - rt0);
+    for (int i = wib; i < nrt; i += nwarps) {
+        const uint32_t r = P.rt_rep[rt0 + i];
+        uint8_t *t = tables + (size_t)i * RT_BYTES;
+        if (lane < 16) {
+            reinterpret_cast<uint64_t *>(t)[lane] = P.rep_A[(size_t)r * 16 + lane];
+            reinterpret_cast<uint64_t *>(t + 128)[lane] = P.rep_inv[(size_t)r * 16 + lane];
+        }
+        reinterpret_cast<double *>(t + 256)[lane] = P.rep_grad[(size_t)r * 32 + lane];
+        if (lane == 0) {
+            *reinterpret_cast<uint64_t *>(t + RT_SEED) = P.rep_seed[r];
+            *reinterpret_cast<uint32_t *>(t + RT_DOMOFF) = P.rep_dom_off[r];
+            *reinterpret_cast<int32_t *>(t + RT_DX) = P.rep_Dx[r];
+        }
+    }
+    for (int i = wib; i < nslot; i += nwarps) {
+        const uint32_t s = slot0 + (uint32_t)i;
+        const uint32_t g = P.slot_g[s];
+        const uint32_t rt = P.slot_rt[s];
+        const uint32_t r = P.rt_rep[rt0 + rt];
+        uint8_t *sl = slots + (size_t)i * SB;
+        for (int q = lane * 4; q < TB; q += 128)
+            *reinterpret_cast<uint32_t *>(sl + q) = *reinterpret_cast<const uint32_t *>(P.tiles + (size_t)g * TB + q);
+        if (lane < DCTR_WORDS)
+            reinterpret_cast<uint64_t *>(sl + OFF_CTR)[lane] = P.dctr[(size_t)g * DCTR_WORDS + lane];
+        uint32_t *meta = reinterpret_cast<uint32_t *>(sl + OFF_META);
+        if (lane == 0) {
+            meta[META_G] = g;
+            meta[META_R] = r;
+            meta[META_D] = g - P.rep_dom_off[r];
+            meta[META_RT] = rt;
+        }
+        if (lane < 4) {
+            const uint32_t nb = P.slot_nb[(size_t)s * 4 + lane];
+            if (CLUSTER) {
+                // address of the edge word this slot reads from its neighbour:
+                // the N neighbour's S row, the S neighbour's N row, the W
+                // neighbour's E column, the E neighbour's W column
+                const int want = (lane == EDGE_N) ? EDGE_S : (lane == EDGE_S) ? EDGE_N : (lane == EDGE_W) ? EDGE_E : EDGE_W;
+                const uint32_t nrank = nb >> 24, nslot_ = nb & 0xFFFFFFu;
+                const uint32_t local = smem_addr(slots + (size_t)nslot_ * SB + OFF_EDGE + 8 * want);
+                meta[META_NB + lane] = map_rank(local, nrank);
+            } else {
+                meta[META_NB + lane] = nb;
+            }
+        }
+        if (CLUSTER) {
+            // edges of the staged tile, published in shared memory
+            row_t S[G::RPL];
+            const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            first[c] = acc;
-            const int n = P.n_list[c];
-            acc += (w < n) ? (n - w - 1) / W + 1 : 0;
+            for (int t = 0; t < G::RPL; ++t) S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
+            const uint64_t ew = edge_words<LD>(S, lane);
+            if (lane < 4) reinterpret_cast<uint64_t *>(sl + OFF_EDGE)[lane] = ew;
         }
     }
-    // load owned tiles and counters into shared memory
-#pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-        int sl = first[c];
-        for (int j = w; j < P.n_list[c]; j += W, ++sl) {
-            const uint64_t ent = __ldg(&P.list[c][j]);
-            const uint64_t g = ent >> 32;
-            uint8_t *dst = mine + (size_t)sl * P.slot_bytes;
-            const uint8_t *src = P.tiles + g * TB;
-            for (int b = lane * 4; b < TB; b += 128)
-                *reinterpret_cast<uint32_t *>(dst + b) = *reinterpret_cast<const uint32_t *>(src + b);
-            if (lane < DCTR_WORDS)
-                reinterpret_cast<uint64_t *>(dst + TB)[lane] = P.dctr[g * DCTR_WORDS + lane];
+    if (CLUSTER) cluster_sync();
+    else __syncthreads();
+
+    // halo of a slot: four edge words of its neighbours
+    auto read_halo = [&](const uint32_t *meta, uint64_t &hN, uint64_t &hS, uint64_t &hW, uint64_t &hE) {
+        if (CLUSTER) {
+            hN = ld_dsmem(meta[META_NB + EDGE_N]);
+            hS = ld_dsmem(meta[META_NB + EDGE_S]);
+            hW = ld_dsmem(meta[META_NB + EDGE_W]);
+            hE = ld_dsmem(meta[META_NB + EDGE_E]);
+        } else {
+            hN = ld_cg(&P.edges[(size_t)meta[META_NB + EDGE_N] * 4 + EDGE_S]);
+            hS = ld_cg(&P.edges[(size_t)meta[META_NB + EDGE_S] * 4 + EDGE_N]);
+            hW = ld_cg(&P.edges[(size_t)meta[META_NB + EDGE_W] * 4 + EDGE_E]);
+            hE = ld_cg(&P.edges[(size_t)meta[META_NB + EDGE_E] * 4 + EDGE_W]);
         }
-    }
-    __syncwarp();
-    (void)ctr_bytes;
+    };
+
+    auto visit = [&](uint8_t *sl, uint64_t np0, int nf) {
+        const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
+        uint64_t hN, hS, hW, hE;
+        read_halo(meta, hN, hS, hW, hE);
+        const uint8_t *rt = tables + (size_t)meta[META_RT] * RT_BYTES;
+        Planes<LD> pl;
+        pl.valid = (lane < G::NACT) ? G::FULL : (row_t)0;
+        const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
+#pragma unroll
+        for (int t = 0; t < G::RPL; ++t) pl.S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
+        uint64_t *ctr = reinterpret_cast<uint64_t *>(sl + OFF_CTR);
+        Counters cn;
+        cn.H = ctr[DCTR_HASH];
+        cn.flips = 0;
+        cn.clkM = ctr[DCTR_CLKM];
+        cn.clkE = (int64_t)ctr[DCTR_CLKE];
+        cn.sb = 0.0;
+        cn.sh = 0.0;
+        visit_core<LD, EXPO, GRAD>(pl, cn, rt, (row_t)hN, (row_t)hS, hW, hE, meta[META_D], np0, nf, P.k, lane, P.err);
+        mem_t *wrow = reinterpret_cast<mem_t *>(sl);
+        if (lane < G::NACT) {
+#pragma unroll
+            for (int t = 0; t < G::RPL; ++t) wrow[lane * G::RPL + t] = (mem_t)pl.S[t];
+        }
+        const uint64_t ew = edge_words<LD>(pl.S, lane);
+        if (lane < 4) {
+            if (CLUSTER) reinterpret_cast<uint64_t *>(sl + OFF_EDGE)[lane] = ew;
+            else st_cg(&P.edges[(size_t)meta[META_G] * 4 + lane], ew);
+        }
+        if (lane == 0) {
+            ctr[DCTR_HASH] = cn.H;
+            ctr[DCTR_FLIPS] += cn.flips;
+            ctr[DCTR_CLKM] = cn.clkM;
+            ctr[DCTR_CLKE] = (uint64_t)cn.clkE;
+            if (GRAD) {
+                reinterpret_cast<double *>(ctr)[DCTR_SB] += cn.sb;
+                reinterpret_cast<double *>(ctr)[DCTR_SH] += cn.sh;
+            }
+        }
+        __syncwarp();
+    };
+
+    auto phase_sync = [&](unsigned &bar_no) -> bool {
+        if (CLUSTER) {
+            cluster_sync();
+            return true;
+        }
+        return grid_barrier(P, bar_no, &s_ok);
+    };
 
     const int nph = (P.schedule == SCHED_PALINDROME) ? 8 : 4;
     const uint64_t gp_begin = (uint64_t)P.sched_begin * nph;
@@ -691,30 +786,22 @@ __global__ void __launch_bounds__(512) run_kernel(const RunParams P)
                 ++nf;
             }
         }
-        if (started) ok = grid_barrier(P, bar_no, &s_ok);
+        if (started) ok = phase_sync(bar_no);
         started = true;
         if (!ok) break;
         if (P.schedule != SCHED_RANDOM_PERM) {
-            int sl = first[colour];
-            for (int j = w; j < P.n_list[colour]; j += W, ++sl) {
-                const uint64_t ent = __ldg(&P.list[colour][j]);
-                const uint64_t g = ent >> 32;
-                const uint32_t r = (uint32_t)ent;
-                const uint32_t d = (uint32_t)(g - __ldg(&P.rep_dom_off[r]));
-                visit_domain<LD, EXPO, GRAD>(P, mine + (size_t)sl * P.slot_bytes, g, r, d, np0, nf, lane);
-            }
+            const int i0 = (int)col_off[colour], i1 = (int)col_off[colour + 1];
+            for (int i = i0 + wib; i < i1; i += nwarps) visit(slots + (size_t)i * SB, np0, nf);
         } else {
-#pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                int sl = first[c];
-                for (int j = w; j < P.n_list[c]; j += W, ++sl) {
-                    const uint64_t ent = __ldg(&P.list[c][j]);
-                    const uint32_t r = (uint32_t)ent;
-                    if (perm_colour(__ldg(&P.rep_seed[r]), n, p) != c) continue;
-                    const uint64_t g = ent >> 32;
-                    const uint32_t d = (uint32_t)(g - __ldg(&P.rep_dom_off[r]));
-                    visit_domain<LD, EXPO, GRAD>(P, mine + (size_t)sl * P.slot_bytes, g, r, d, np0, 1, lane);
-                }
+            for (int i = wib; i < nslot; i += nwarps) {
+                uint8_t *sl = slots + (size_t)i * SB;
+                const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
+                const uint32_t d = meta[META_D];
+                const uint8_t *rt = tables + (size_t)meta[META_RT] * RT_BYTES;
+                const int Dx = *reinterpret_cast<const int32_t *>(rt + RT_DX);
+                const int c = (int)((d % (uint32_t)Dx) & 1u) | (int)(((d / (uint32_t)Dx) & 1u) << 1);
+                if (perm_colour(*reinterpret_cast<const uint64_t *>(rt + RT_SEED), n, p) != c) continue;
+                visit(sl, np0, 1);
             }
         }
         gp += (uint64_t)nf;
@@ -722,40 +809,52 @@ __global__ void __launch_bounds__(512) run_kernel(const RunParams P)
         if (gp % nph == 0) {
             const int64_t nl_done = (int64_t)(gp / nph - (uint64_t)P.sched_begin);
             if (P.obs_every > 0 && P.obs_acc != nullptr && nl_done > 0 && (nl_done % P.obs_every) == 0) {
-                ok = grid_barrier(P, bar_no, &s_ok);
+                ok = phase_sync(bar_no);
                 if (!ok) break;
                 const int64_t o = nl_done / P.obs_every - 1;
                 const int64_t visits = P.visits_before + nl_done * (nph == 8 ? 2 : 1);
-#pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    int sl = first[c];
-                    for (int j = w; j < P.n_list[c]; j += W, ++sl) {
-                        const uint64_t ent = __ldg(&P.list[c][j]);
-                        const uint64_t g = ent >> 32;
-                        const uint32_t r = (uint32_t)ent;
-                        const uint32_t d = (uint32_t)(g - __ldg(&P.rep_dom_off[r]));
-                        observe_domain<LD, EXPO>(P, mine + (size_t)sl * P.slot_bytes, g, r, d, visits,
-                                                 P.obs_acc + ((size_t)o * P.n_rep + r) * OBS_WORDS, lane);
+                for (int i = wib; i < nslot; i += nwarps) {
+                    const uint8_t *sl = slots + (size_t)i * SB;
+                    const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
+                    uint64_t hN, hS, hW, hE;
+                    read_halo(meta, hN, hS, hW, hE);
+                    row_t S[G::RPL];
+                    const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
+#pragma unroll
+                    for (int t = 0; t < G::RPL; ++t) S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
+                    int bonds, mag;
+                    domain_bonds_mag<LD>(S, hE, hS, lane, bonds, mag);
+                    if (lane == 0) {
+                        const uint64_t *ctr = reinterpret_cast<const uint64_t *>(sl + OFF_CTR);
+                        const double tdom = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE],
+                                                        visits * (int64_t)P.k, P.lambda);
+                        unsigned long long *acc = P.obs_acc + ((size_t)o * P.n_rep + meta[META_R]) * OBS_WORDS;
+                        atomicAdd(&acc[0], (unsigned long long)(long long)bonds);
+                        atomicAdd(&acc[1], (unsigned long long)(long long)mag);
+                        atomicAdd(reinterpret_cast<double *>(&acc[2]), tdom);
+                        atomicAdd(reinterpret_cast<double *>(&acc[3]), reinterpret_cast<const double *>(ctr)[DCTR_SB]);
+                        atomicAdd(reinterpret_cast<double *>(&acc[4]), reinterpret_cast<const double *>(ctr)[DCTR_SH]);
                     }
                 }
             }
         }
     }
-    if (!ok) return;
-    // write owned tiles and counters back
-#pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-        int sl = first[c];
-        for (int j = w; j < P.n_list[c]; j += W, ++sl) {
-            const uint64_t ent = __ldg(&P.list[c][j]);
-            const uint64_t g = ent >> 32;
-            const uint8_t *src = mine + (size_t)sl * P.slot_bytes;
-            uint8_t *dst = P.tiles + g * TB;
-            for (int b = lane * 4; b < TB; b += 128)
-                *reinterpret_cast<uint32_t *>(dst + b) = *reinterpret_cast<const uint32_t *>(src + b);
-            if (lane < DCTR_WORDS)
-                P.dctr[g * DCTR_WORDS + lane] = reinterpret_cast<const uint64_t *>(src + TB)[lane];
-        }
+    if (CLUSTER) {
+        // no CTA may leave while another still reads its shared memory
+        cluster_sync();
+    } else if (!ok) {
+        return;
+    }
+    // write owned tiles and counters back (and edges, for the observables kernel)
+    for (int i = wib; i < nslot; i += nwarps) {
+        const uint8_t *sl = slots + (size_t)i * SB;
+        const uint32_t g = reinterpret_cast<const uint32_t *>(sl + OFF_META)[META_G];
+        for (int q = lane * 4; q < TB; q += 128)
+            *reinterpret_cast<uint32_t *>(P.tiles + (size_t)g * TB + q) = *reinterpret_cast<const uint32_t *>(sl + q);
+        if (lane < DCTR_WORDS)
+            P.dctr[(size_t)g * DCTR_WORDS + lane] = reinterpret_cast<const uint64_t *>(sl + OFF_CTR)[lane];
+        if (CLUSTER && lane < 4)
+            P.edges[(size_t)g * 4 + lane] = reinterpret_cast<const uint64_t *>(sl + OFF_EDGE)[lane];
     }
 }
 
@@ -852,18 +951,8 @@ __global__ void pack_kernel(const LayoutParams P)
 #pragma unroll
             for (int t = 0; t < G::RPL; ++t) trow[lane * G::RPL + t] = (mem_t)S[t];
         }
-        uint64_t colW = 0, colE = 0;
-#pragma unroll
-        for (int t = 0; t < G::RPL; ++t) {
-            colW |= (uint64_t)__ballot_sync(FULL_WARP, (S[t] & 1u) != 0) << (32 * t);
-            colE |= (uint64_t)__ballot_sync(FULL_WARP, ((S[t] >> (LD - 1)) & 1u) != 0) << (32 * t);
-        }
-        const uint64_t rowN = (uint64_t)__shfl_sync(FULL_WARP, S[0], 0);
-        const uint64_t rowS = (uint64_t)__shfl_sync(FULL_WARP, S[G::RPL - 1], G::NACT - 1);
-        if (lane < 4) {
-            const uint64_t v = (lane == EDGE_N) ? rowN : (lane == EDGE_S) ? rowS : (lane == EDGE_W) ? colW : colE;
-            P.edges[(uint64_t)g * 4 + lane] = v;
-        }
+        const uint64_t ew = edge_words<LD>(S, lane);
+        if (lane < 4) P.edges[(uint64_t)g * 4 + lane] = ew;
     }
 }
 
@@ -901,27 +990,42 @@ __global__ void unpack_kernel(const LayoutParams P)
     }
 }
 
-// Observables of the current state from the global tiles (kmc_observables).
+// Observables of the current state from the global tiles and edges (kmc_observables).
 template <int LD, bool EXPO>
 __global__ void observe_kernel(const RunParams P, const uint32_t *dom_rep, int n_dom, int64_t visits,
                                unsigned long long *acc /* [n_rep][OBS_WORDS] */)
 {
     using G = Geo<LD>;
+    using row_t = typename G::row_t;
+    using mem_t = typename G::mem_t;
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    __shared__ __align__(16) uint8_t buf[32][G::TILE_BYTES + DCTR_WORDS * 8];
-    uint8_t *slot = buf[threadIdx.x >> 5];
     for (int g = wg; g < n_dom; g += nw) {
         const uint32_t r = dom_rep[g];
+        const int Dx = P.rep_Dx[r];
         const uint32_t d = (uint32_t)g - P.rep_dom_off[r];
-        for (int b = lane * 4; b < G::TILE_BYTES; b += 128)
-            *reinterpret_cast<uint32_t *>(slot + b) = *reinterpret_cast<const uint32_t *>(P.tiles + (uint64_t)g * G::TILE_BYTES + b);
-        if (lane < DCTR_WORDS)
-            reinterpret_cast<uint64_t *>(slot + G::TILE_BYTES)[lane] = P.dctr[(uint64_t)g * DCTR_WORDS + lane];
-        __syncwarp();
-        observe_domain<LD, EXPO>(P, slot, (uint64_t)g, r, d, visits, acc + (size_t)r * OBS_WORDS, lane);
-        __syncwarp();
+        const int bx = (int)(d % (uint32_t)Dx), by = (int)(d / (uint32_t)Dx);
+        const uint64_t gbase = (uint64_t)g - d;
+        const uint64_t hS = P.edges[(gbase + (uint32_t)(((by + 1) % Dx) * Dx + bx)) * 4 + EDGE_N];
+        const uint64_t hE = P.edges[(gbase + (uint32_t)(by * Dx + (bx + 1) % Dx)) * 4 + EDGE_W];
+        row_t S[G::RPL];
+        const mem_t *trow = reinterpret_cast<const mem_t *>(P.tiles + (uint64_t)g * G::TILE_BYTES);
+#pragma unroll
+        for (int t = 0; t < G::RPL; ++t) S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
+        int bonds, mag;
+        domain_bonds_mag<LD>(S, hE, hS, lane, bonds, mag);
+        if (lane == 0) {
+            const uint64_t *ctr = P.dctr + (uint64_t)g * DCTR_WORDS;
+            const double t = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE], visits * (int64_t)P.k,
+                                         P.lambda);
+            unsigned long long *a = acc + (size_t)r * OBS_WORDS;
+            atomicAdd(&a[0], (unsigned long long)(long long)bonds);
+            atomicAdd(&a[1], (unsigned long long)(long long)mag);
+            atomicAdd(reinterpret_cast<double *>(&a[2]), t);
+            atomicAdd(reinterpret_cast<double *>(&a[3]), __longlong_as_double((long long)ctr[DCTR_SB]));
+            atomicAdd(reinterpret_cast<double *>(&a[4]), __longlong_as_double((long long)ctr[DCTR_SH]));
+        }
     }
 }
 

@@ -11,6 +11,7 @@ def run_both(L, Ld, k, seeds, beta, h, n_sched, *, law=0, init=0, schedule=0, ti
     lat = kmc.Lattice(L, Ld, k, seeds, init=init)
     if launch is not None:
         lat.set_launch(*launch)
+        assert lat.launch()[0] == launch[0]
     lat.set_rates(beta, h, J=J, nu=nu, law=law)
     chunks = chunks or [n_sched]
     obs_gpu = []

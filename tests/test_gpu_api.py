@@ -1,0 +1,147 @@
+"""C-ABI behaviour on the GPU: argument errors, device-side errors, the bounded
+grid barrier, the detailed-balance check of user rate tables, launch plans."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import assert_parity, run_both
+from oracle import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _kmc():
+    import paper_1403_4674_gb300 as kmc
+    return kmc
+
+
+@pytest.mark.parametrize("L,Ld,k", [([48], 16, 1), ([64], 12, 1), ([64], 16, 0), ([64], 16, 70000),
+                                    ([8], 8, 1), ([64, 80], 16, 1)])
+def test_invalid_geometry_rejected(L, Ld, k):
+    kmc = _kmc()
+    with pytest.raises(kmc.KmcError) as ei:
+        kmc.Lattice(L, Ld, k, [1] * len(L))
+    assert ei.value.status == -1
+
+
+def test_invalid_run_arguments_rejected():
+    kmc = _kmc()
+    lat = kmc.Lattice([64], 16, 1, [1])
+    for args in [(-1, 0, 0, 0), (1, 7, 0, 0), (1, 0, 5, 0), (1, 0, 0, -3)]:
+        with pytest.raises(kmc.KmcError) as ei:
+            kmc.kmc_run_schedule(lat.ctx, *args, None)
+        assert ei.value.status == -1
+    with pytest.raises(kmc.KmcError):
+        lat.set_rates([-0.5])
+    with pytest.raises(kmc.KmcError):
+        lat.set_rates([0.4], nu=0.0)
+    with pytest.raises(kmc.KmcError):
+        lat.set_launch(kmc.KMC_LAUNCH_CLUSTER, 3, 16)
+    lat.close()
+
+
+def test_spins_that_are_not_pm1_raise_device_error():
+    import torch
+    kmc = _kmc()
+    spins = torch.ones(64 * 64, dtype=torch.int8, device="cuda")
+    spins[100] = 0
+    lat = kmc.Lattice([64], 16, 1, [1], init=kmc.KMC_INIT_KEEP, spins=spins)
+    lat.run(1)
+    with pytest.raises(kmc.KmcError) as ei:
+        lat.sync()
+    assert ei.value.status == -6
+    lat.spins.fill_(1)
+    lat.run(1)
+    lat.sync()  # error word was cleared; the context stays usable
+    lat.close()
+
+
+def test_grid_barrier_gives_up_and_context_survives():
+    """A barrier that waits for an arrival that never comes returns KMC_ETIMEOUT."""
+    kmc = _kmc()
+    lat = kmc.Lattice([128], 16, 2, [5])
+    lat.set_launch(kmc.KMC_LAUNCH_GRID, 4, 4)
+    kmc.kmc_debug_barrier(lat.ctx, 1, 20_000_000)  # 20 ms
+    lat.run(3)
+    with pytest.raises(kmc.KmcError) as ei:
+        lat.sync()
+    assert ei.value.status == -5
+    kmc.kmc_debug_barrier(lat.ctx, 0, 0)
+    lat.reset(kmc.KMC_INIT_RANDOM)
+    lat.set_rates([0.4], [0.0])
+    lat.run(3)
+    lat.sync()
+    ref = orc.Replica(L=128, Ld=16, k=2, seed=5, beta=0.4)
+    ref.run(3)
+    assert np.array_equal(lat.replica_spins(0).cpu().numpy(), ref.spins)
+    lat.close()
+
+
+def test_rate_table_detailed_balance_check():
+    kmc = _kmc()
+    lat = kmc.Lattice([64], 16, 4, [9])
+    beta, h = 0.45, 0.1
+    a, _ = orc.rate_table(1.0, beta, h, orc.RATE_BARKER, 8)
+    bad = a.copy()
+    bad[3] *= 1.01
+    with pytest.raises(kmc.KmcError) as ei:
+        kmc.kmc_set_rate_table(lat.ctx, 1.0, [beta], [h], 1.0, bad)
+    assert ei.value.status == -4
+    # a balanced user table drives exactly the same chain as the built-in law
+    kmc.kmc_set_rate_table(lat.ctx, 1.0, [beta], [h], 1.0, a)
+    lat.run(5)
+    lat.sync()
+    ref = orc.Replica(L=64, Ld=16, k=4, seed=9, beta=beta, h=h, law=orc.RATE_BARKER)
+    ref.run(5)
+    assert np.array_equal(lat.replica_spins(0).cpu().numpy(), ref.spins)
+    lat.close()
+
+
+def test_rate_table_matches_oracle_fixed_point():
+    kmc = _kmc()
+    for Ld, log2nd in ((8, 6), (16, 8), (32, 10), (64, 12)):
+        lat = kmc.Lattice([2 * Ld], Ld, 1, [1])
+        for law in (0, 1):
+            lat.set_rates([1 / 2.269], [0.01], law=law)
+            a, A = lat.rate_table(0)
+            ra, rA = orc.rate_table(1.0, 1 / 2.269, 0.01, law, log2nd)
+            assert np.array_equal(A, rA)
+            assert np.array_equal(a, ra)
+        lat.close()
+
+
+def test_observables_and_counters():
+    kmc = _kmc()
+    L, Ld, k, n = 128, 32, 4, 6
+    lat = kmc.Lattice([L], Ld, k, [77])
+    lat.set_rates([0.5], [0.05])
+    lat.run(n)
+    ob = lat.observables()
+    ref = orc.Replica(L=L, Ld=Ld, k=k, seed=77, beta=0.5, h=0.05)
+    ref.run(n)
+    e, m, _, T = ref.observables()
+    assert ob["e"][0] == e and ob["m"][0] == m
+    assert math.isclose(ob["t"][0], T, rel_tol=1e-12)
+    assert ob["steps"][0] == 2 * (L // Ld) ** 2 * k * n
+    assert ob["flips"][0] == int(ref.flips.sum())
+    assert lat.kernel_launches() > 0
+    lat.close()
+
+
+def test_profile_counts_run_kernel_launches():
+    kmc = _kmc()
+    lat = kmc.Lattice([64], 16, 2, [3])
+    lat.profile(True)
+    lat.run(4)
+    lat.run(4)
+    ms, n = lat.profile_read()
+    assert n == 2 and ms > 0
+    lat.close()

@@ -86,10 +86,24 @@ def test_minimum_lattice_two_domains_per_side():
     assert_parity(gpu, ref, 1)
 
 
-@pytest.mark.parametrize("launch", [(1, 1), (3, 2), (7, 16)])
-def test_launch_shape_does_not_change_results(launch):
+CLUSTER, GRID = 1, 2
+
+
+@pytest.mark.parametrize("launch", [(CLUSTER, 1, 16), (CLUSTER, 2, 4), (CLUSTER, 4, 16), (CLUSTER, 16, 1),
+                                    (GRID, 1, 1), (GRID, 3, 2), (GRID, 7, 16), (GRID, 152, 16)])
+def test_launch_plan_does_not_change_results(launch):
+    """CLUSTER (DSMEM halos, cluster barriers) and GRID (L2 halos, grid barrier) plans."""
     gpu, ref = run_both([256], 16, 4, [2024], [0.42], [0.01], 4, obs_every=2, launch=launch)
     assert_parity(gpu, ref, 1)
+
+
+@pytest.mark.parametrize("launch", [(CLUSTER, 8, 16), (GRID, 152, 16)])
+def test_batch_under_both_plans(launch):
+    L = [32, 64, 96, 128, 160, 192, 224, 256]
+    seeds = list(range(101, 109))
+    gpu, ref = run_both(L, 16, 6, seeds, [0.45] * 8, [0.02] * 8, 3, obs_every=1, launch=launch,
+                        schedule=orc.SCHED_RANDOM_PERM)
+    assert_parity(gpu, ref, len(L))
 
 
 @pytest.mark.parametrize("k", [1, 4, 16])
@@ -101,6 +115,7 @@ def test_config_1024_k(k):
 
 
 def test_config_8192_one_schedule():
-    """8192^2 (67M sites), T=2.269, h=0.01, L_d=64, k=8: one full schedule vs the oracle."""
+    """8192^2 (67M sites), T=2.269, h=0.01, L_d=64, k=8: one full schedule vs the oracle
+    (a GRID plan: the bit state is larger than one cluster's shared memory)."""
     gpu, ref = run_both([8192], 64, 8, [8192], [1 / 2.269], [0.01], 1, obs_every=1)
     assert_parity(gpu, ref, 1)
