@@ -205,6 +205,41 @@ kmc_status kmc_debug_barrier(kmc_ctx *ctx, int32_t extra, int64_t limit_ns);
 kmc_status kmc_profile(kmc_ctx *ctx, int32_t enable);
 kmc_status kmc_profile_read(kmc_ctx *ctx, double *run_kernel_ms, int64_t *run_kernel_launches);
 
+/*
+ * kmc_run_schedule_noalloc -- run schedules on one replica without allocating
+ * any device memory.  This operation has no counterpart in the paper; it
+ * exists for callers that cannot call cudaMalloc, for example code running
+ * inside a memory pool owned by another runtime, or a process whose device
+ * memory is fully reserved before this library is used.
+ *
+ * The library's working memory for this call (bit tiles, edges, counters,
+ * launch plan, rate table, error word) lives in one file-scope device array
+ * of KMC_NOALLOC_MAX_BYTES bytes that every GPU loading the library holds
+ * until the process exits.  The call makes no cudaMalloc, cudaFree or other
+ * allocating call.  The first call on each device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture.
+ *
+ * Arguments are those of kmc_create_lattice + kmc_set_rates +
+ * kmc_run_schedule for a single replica: spins_dev (L*L int8, +-1, in/out,
+ * 8-byte aligned), sched_begin is the global schedule index of the first
+ * schedule (the Philox stream position), obs_dev as in kmc_run_schedule with
+ * n_replicas = 1 (may be NULL).  Domain clocks and counters start at zero at
+ * every call, so T in obs_dev is the time since this call began.
+ * The lattice must fit one cluster of 16 CTAs and its working memory must
+ * fit the array; otherwise KMC_EINVAL.  If err is non-NULL, a message of at
+ * most err_len bytes (terminated) describes a failure, or is empty.
+ * Synchronising: returns after the stream has run the work.  Every call
+ * shares the one array, so calls that overlap on the GPU (other host
+ * threads, other streams) race and must not be made.
+ */
+#define KMC_NOALLOC_MAX_BYTES (4 * 1024 * 1024)
+kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uint64_t seed, double J,
+                                    double beta, double h, double nu, int32_t rate_law,
+                                    int64_t sched_begin, int64_t n_schedules, int32_t schedule,
+                                    int32_t time_mode, int32_t obs_every, int8_t *spins_dev,
+                                    double *obs_dev, void *stream, char *err, int32_t err_len);
+
 /* Number of kernels this context launched so far (all kinds). */
 int64_t kmc_kernel_launches(const kmc_ctx *ctx);
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "kmc_create_lattice", "kmc_set_rates", "kmc_set_rate_table", "kmc_run_schedule",
     "kmc_observables", "kmc_grad", "kmc_enable_grad", "kmc_reset", "kmc_sync",
     "kmc_domain_state", "kmc_get_rate_table", "kmc_set_launch", "kmc_get_launch",
-    "kmc_debug_barrier", "kmc_profile", "kmc_profile_read", "kmc_kernel_launches", "kmc_last_error", "kmc_destroy", "kmc_version",
+    "kmc_debug_barrier", "kmc_run_schedule_noalloc", "kmc_profile", "kmc_profile_read", "kmc_kernel_launches", "kmc_last_error", "kmc_destroy", "kmc_version",
 ]
 
 
@@ -71,6 +71,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmc_set_launch.argtypes = [vp, i32, i32, i32]
     L.kmc_get_launch.argtypes = [vp, P(i32), P(i32), P(i32), P(i32), P(i32)]
     L.kmc_debug_barrier.argtypes = [vp, i32, i64]
+    L.kmc_run_schedule_noalloc.argtypes = [i32, i32, i32, u64, dbl, dbl, dbl, dbl, i32, i64, i64, i32,
+                                           i32, i32, vp, vp, vp, ctypes.c_char_p, i32]
     L.kmc_profile.argtypes = [vp, i32]
     L.kmc_profile_read.argtypes = [vp, P(dbl), P(i64)]
     L.kmc_kernel_launches.argtypes = [vp]

@@ -150,6 +150,23 @@ def kmc_profile_read(ctx):
     return ms.value, n.value
 
 
+def kmc_run_schedule_noalloc(L: int, L_d: int, k_steps: int, seed: int, J: float, beta: float, h: float,
+                             nu: float, rate_law: int, sched_begin: int, n_schedules: int, schedule: int,
+                             time_mode: int, obs_every: int, spins_dev: torch.Tensor,
+                             obs_dev: Optional[torch.Tensor] = None, stream=None):
+    """One replica, no device allocation (see include/kmc.h); raises KmcError on failure."""
+    if spins_dev.dtype != torch.int8 or not spins_dev.is_cuda:
+        raise KmcError(-1, "spins_dev must be an int8 CUDA tensor")
+    err = ctypes.create_string_buffer(256)
+    obs_ptr = ctypes.c_void_p(obs_dev.data_ptr()) if obs_dev is not None else ctypes.c_void_p()
+    st = load().kmc_run_schedule_noalloc(L, L_d, k_steps, seed, J, beta, h, nu, rate_law, sched_begin,
+                                         n_schedules, schedule, time_mode, obs_every,
+                                         ctypes.c_void_p(spins_dev.data_ptr()), obs_ptr,
+                                         ctypes.c_void_p(_stream_handle(stream)), err, len(err))
+    if st != 0:
+        raise KmcError(st, err.value.decode())
+
+
 def kmc_kernel_launches(ctx) -> int:
     return load().kmc_kernel_launches(ctx)
 

@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -88,6 +89,12 @@ struct kmc_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
     std::string err;
 };
+
+// Working memory of kmc_run_schedule_noalloc: every GPU that loads this
+// library holds these bytes until the process exits.  Host code must not use
+// the symbol as an address; it resolves the device address per device with
+// cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KMC_NOALLOC_MAX_BYTES];
 
 namespace {
 
@@ -632,6 +639,35 @@ void free_all(kmc_ctx *c)
 
 } // namespace
 
+namespace {
+
+const int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+void noalloc_message(char *err, int32_t err_len, const std::string &msg)
+{
+    if (err && err_len > 0) {
+        std::strncpy(err, msg.c_str(), (size_t)err_len - 1);
+        err[err_len - 1] = '\0';
+    }
+}
+
+// Carves aligned sub-arrays out of the static scratch array.
+struct Carver {
+    unsigned char *base;
+    size_t off = 0;
+    template <typename T> T *take(size_t n)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+} // namespace
+
 extern "C" {
 
 int32_t kmc_version(void) { return 10100; }
@@ -1063,6 +1099,202 @@ kmc_status kmc_grad(kmc_ctx *c, double *score_dev, int32_t reset)
     ++c->launches;
     CUDA_TRY(c, cudaGetLastError());
     return sync_ctx(c);
+}
+
+kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uint64_t seed, double J, double beta,
+                                    double h, double nu, int32_t rate_law, int64_t sched_begin, int64_t n_schedules,
+                                    int32_t schedule, int32_t time_mode, int32_t obs_every, int8_t *spins_dev,
+                                    double *obs_dev, void *stream, char *err, int32_t err_len)
+{
+    // A host-side context holds the geometry and the launch plan; it owns no
+    // device memory: every device pointer below points into g_noalloc_scratch.
+    kmc_ctx c;
+    auto bad = [&](kmc_status st, const std::string &msg) {
+        noalloc_message(err, err_len, msg);
+        return st;
+    };
+    if (ld_index(L_d) < 0) return bad(KMC_EINVAL, "L_d must be 8, 16, 32 or 64");
+    if (L < 2 * L_d || L % (2 * L_d) != 0 || L > 65536) return bad(KMC_EINVAL, "L must be a positive multiple of 2*L_d");
+    if (k_steps < 1 || k_steps > 65535) return bad(KMC_EINVAL, "k_steps must be in 1..65535");
+    if (!spins_dev || ((uintptr_t)spins_dev) % 8 != 0) return bad(KMC_EINVAL, "spins_dev must be non-null and 8-byte aligned");
+    if (n_schedules < 0 || sched_begin < 0 || sched_begin + n_schedules >= (1ll << 52))
+        return bad(KMC_EINVAL, "bad schedule range");
+    if (schedule < KMC_SCHEDULE_PALINDROME || schedule > KMC_SCHEDULE_RANDOM_PERM) return bad(KMC_EINVAL, "bad schedule kind");
+    if (time_mode != KMC_TIME_EXPONENTIAL && time_mode != KMC_TIME_EXPECTED) return bad(KMC_EINVAL, "bad time mode");
+    if (obs_every < 0) return bad(KMC_EINVAL, "obs_every must be >= 0");
+    if (rate_law != KMC_RATE_METROPOLIS && rate_law != KMC_RATE_BARKER) return bad(KMC_EINVAL, "bad rate law");
+    if (!(beta >= 0.0) || !std::isfinite(beta) || !std::isfinite(h) || !std::isfinite(J) || !(nu > 0.0))
+        return bad(KMC_EINVAL, "beta >= 0, finite J and h, nu > 0 required");
+
+    c.n_rep = 1;
+    c.LD = L_d;
+    c.log2nd = 2 * (L_d == 8 ? 3 : L_d == 16 ? 4 : L_d == 32 ? 5 : 6);
+    c.k = k_steps;
+    c.spins = spins_dev;
+    c.stream = (cudaStream_t)stream;
+    c.L.assign(1, L);
+    c.Dx.assign(1, L / L_d);
+    c.seed.assign(1, seed);
+    c.dom_off = {0u, (uint32_t)(c.Dx[0] * c.Dx[0])};
+    c.site_off = {0ull};
+    c.blk_off = {0ull, (uint64_t)L * L / 128};
+    c.n_dom = c.Dx[0] * c.Dx[0];
+    c.dom_rep.assign(c.n_dom, 0u);
+    c.J = J;
+    c.nu = nu;
+    c.h.assign(1, h);
+    c.a.resize(10);
+    c.A.resize(10);
+    c.inv.resize(10);
+    c.gb.resize(10);
+    c.gh.resize(10);
+    build_table(J, beta, h, rate_law, c.log2nd, c.a.data(), c.A.data(), c.inv.data(), c.gb.data(), c.gh.data());
+
+    cudaError_t ce = cudaGetDevice(&c.dev);
+    if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+    if (c.dev < 0 || c.dev >= NOALLOC_MAX_DEVICES) return bad(KMC_EINVAL, "device index out of range");
+    ce = cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, c.dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&c.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.dev);
+    if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("device attributes: ") + cudaGetErrorString(ce));
+    c.smem_optin -= 1024;
+
+    // the replica must fit one cluster of at most 16 CTAs
+    const int per_colour = c.n_dom / 4;
+    const int need = (per_colour + MAX_WPB - 1) / MAX_WPB;
+    int C = 1;
+    while (C < need) C *= 2;
+    if (C > 16) return bad(KMC_EINVAL, "lattice too large for the no-alloc path: more than one cluster of 16 CTAs");
+    Plan pl;
+    kmc_status st = plan_cluster(&c, C, MAX_WPB, 1, pl);
+    if (st != KMC_OK) return bad(st, c.err);
+    st = check_plan(&c, pl);
+    if (st != KMC_OK) return bad(st, c.err);
+
+    // scratch layout (every sub-array 256-byte aligned)
+    const int64_t n_obs = (obs_every > 0 && obs_dev) ? n_schedules / obs_every : 0;
+    std::vector<uint32_t> flat;
+    for (auto *v : {&pl.cta_slot_off, &pl.cta_col_off, &pl.cta_rt_off, &pl.rt_rep, &pl.slot_g, &pl.slot_rt, &pl.slot_nb})
+        flat.insert(flat.end(), v->begin(), v->end());
+    const size_t tile = (size_t)L_d * L_d / 8;
+    // one carving sequence, run twice: to measure (null base) and to place
+    auto carve = [&](Carver &cv) {
+        c.d_tiles = cv.take<uint8_t>((size_t)c.n_dom * tile);
+        c.d_edges = cv.take<uint64_t>((size_t)c.n_dom * 4);
+        c.d_dctr = cv.take<uint64_t>((size_t)c.n_dom * DCTR_WORDS);
+        c.d_dom_rep = cv.take<uint32_t>((size_t)c.n_dom);
+        c.d_plan = cv.take<uint32_t>(flat.size());
+        c.d_obs_acc = cv.take<unsigned long long>((size_t)std::max<int64_t>(n_obs, 1) * OBS_WORDS);
+        c.d_L = cv.take<int32_t>(1);
+        c.d_Dx = cv.take<int32_t>(1);
+        c.d_dom_off = cv.take<uint32_t>(2);
+        c.d_site_off = cv.take<uint64_t>(1);
+        c.d_blk_off = cv.take<uint64_t>(2);
+        c.d_seed = cv.take<uint64_t>(1);
+        c.d_A = cv.take<uint64_t>(16);
+        c.d_inv = cv.take<uint64_t>(16);
+        c.d_grad = cv.take<double>(32);
+        c.d_h = cv.take<double>(1);
+        c.d_err = cv.take<int>(1);
+        c.d_bar = cv.take<unsigned>(1);
+    };
+    Carver measure{nullptr};
+    carve(measure);
+    const size_t need_bytes = measure.off;
+    if (need_bytes > (size_t)KMC_NOALLOC_MAX_BYTES) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "needs %zu bytes of working memory; the no-alloc path holds %d", need_bytes,
+                 KMC_NOALLOC_MAX_BYTES);
+        return bad(KMC_EINVAL, msg);
+    }
+
+    // device address of the scratch array on this device (resolved once per device)
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[c.dev]) {
+            void *p = nullptr;
+            ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
+            g_noalloc_ptr[c.dev] = static_cast<unsigned char *>(p);
+        }
+        base = g_noalloc_ptr[c.dev];
+    }
+    Carver cv{base};
+    carve(cv);
+    c.plan_words = flat.size();
+
+    // inputs of this call; the array keeps the previous call's contents, so
+    // everything the kernels read is written (or cleared) here first
+    cudaStream_t s = c.stream;
+    std::vector<uint64_t> A16(16, 0), inv16(16, 0);
+    std::vector<double> g32(32, 0.0);
+    for (int q = 0; q < 10; ++q) {
+        A16[q] = c.A[q];
+        inv16[q] = c.inv[q];
+        g32[q] = c.a[q];
+        g32[10 + q] = c.gb[q];
+        g32[20 + q] = c.gh[q];
+    }
+    struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
+        {c.d_L, c.L.data(), 4}, {c.d_Dx, c.Dx.data(), 4}, {c.d_dom_off, c.dom_off.data(), 8},
+        {c.d_site_off, c.site_off.data(), 8}, {c.d_blk_off, c.blk_off.data(), 16}, {c.d_seed, c.seed.data(), 8},
+        {c.d_A, A16.data(), 128}, {c.d_inv, inv16.data(), 128}, {c.d_grad, g32.data(), 256}, {c.d_h, c.h.data(), 8},
+        {c.d_dom_rep, c.dom_rep.data(), (size_t)c.n_dom * 4}, {c.d_plan, flat.data(), flat.size() * 4},
+    };
+    for (const Up &u : ups) {
+        // pageable host source: the copy has completed when the call returns
+        ce = cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, s);
+        if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(ce));
+    }
+    ce = cudaMemsetAsync(c.d_err, 0, sizeof(int), s);
+    if (ce == cudaSuccess && n_obs > 0) ce = cudaMemsetAsync(c.d_obs_acc, 0, (size_t)n_obs * c.n_rep * OBS_WORDS * 8, s);
+    if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(ce));
+    c.plan = std::move(pl);
+
+    if ((st = launch_reset_counters(&c, s)) != KMC_OK) return bad(st, c.err);
+    if (n_schedules > 0) {
+        if ((st = launch_pack(&c, s)) != KMC_OK) return bad(st, c.err);
+        RunParams P = run_params(&c);
+        P.schedule = schedule;
+        P.obs_every = n_obs > 0 ? obs_every : 0;
+        P.obs_acc = n_obs > 0 ? c.d_obs_acc : nullptr;
+        P.sched_begin = sched_begin;
+        P.n_sched = n_schedules;
+        P.visits_before = 0;
+        RunKernel kern = run_kernel_for(c.LD, time_mode == KMC_TIME_EXPONENTIAL, false, true);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c.plan.n_cta);
+        cfg.blockDim = dim3(c.plan.wpb * 32);
+        cfg.dynamicSmemBytes = c.plan.smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c.plan.cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ce = cudaLaunchKernelEx(&cfg, kern, P);
+        if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("cudaLaunchKernelEx: ") + cudaGetErrorString(ce));
+        if (n_obs > 0) {
+            const int n_rec = (int)n_obs;
+            finalize_obs_kernel<<<grid_for(n_rec, 256), 256, 0, s>>>(c.d_obs_acc, n_rec, 1, c.d_L, c.d_Dx, J, c.d_h,
+                                                                      obs_dev, 4);
+            ce = cudaGetLastError();
+            if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("finalize: ") + cudaGetErrorString(ce));
+        }
+        if ((st = launch_unpack(&c, s)) != KMC_OK) return bad(st, c.err);
+    }
+    // synchronising: the device error word lives in the shared array
+    st = sync_ctx(&c);
+    // the kmc_ctx destructor must not free the static array
+    c.d_L = nullptr; c.d_Dx = nullptr; c.d_dom_off = nullptr; c.d_dom_rep = nullptr; c.d_site_off = nullptr;
+    c.d_blk_off = nullptr; c.d_seed = nullptr; c.d_A = nullptr; c.d_inv = nullptr; c.d_grad = nullptr; c.d_h = nullptr;
+    c.d_tiles = nullptr; c.d_edges = nullptr; c.d_dctr = nullptr; c.d_bar = nullptr; c.d_err = nullptr;
+    c.d_obs_acc = nullptr; c.d_plan = nullptr;
+    if (st != KMC_OK) return bad(st, c.err);
+    noalloc_message(err, err_len, "");
+    return KMC_OK;
 }
 
 kmc_status kmc_profile(kmc_ctx *c, int32_t enable)
