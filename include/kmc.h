@@ -97,6 +97,7 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
  *   rate_law    KMC_RATE_METROPOLIS: a_c = min(1, exp(-beta dE_c));
  *               KMC_RATE_BARKER:     a_c = 1 / (1 + exp(beta dE_c)),
  *               dE_c = 2 s (J (2q - 4) + h) for class c = 5 (s>0) + q.
+ * The upload is ordered on the stream of the context's last call.
  * The table is built on the host in FP64 and held in fixed point,
  * A_c = round(a_c 2^P), P = 63 - log2(n_d), so that every trajectory
  * decision on the device is an exact integer comparison.
@@ -177,11 +178,13 @@ kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, ui
  *   KMC_LAUNCH_AUTO: the library's choice (CLUSTER when every replica fits
  *     one cluster of at most 16 CTAs, else GRID); size and warps ignored.
  *   KMC_LAUNCH_CLUSTER: every replica resident in one thread-block cluster of
- *     `size` CTAs (1, 2, 4, 8 or 16); halos exchanged through distributed
- *     shared memory, colour phases separated by the hardware cluster barrier;
- *     no device-wide synchronisation.
- *   KMC_LAUNCH_GRID: one cooperative grid of `size` CTAs; halos through L2,
- *     colour phases separated by a bounded grid barrier (kmc_debug_barrier).
+ *     `size` CTAs (1, 2, 4, 8 or 16); halos and visit counters read through
+ *     distributed shared memory; no device-wide synchronisation.
+ *   KMC_LAUNCH_GRID: one cooperative grid of `size` CTAs; halos and visit
+ *     counters through L2.
+ * In both plans a visit starts as soon as its four neighbours have finished
+ * their visits of earlier colour phases (per-domain dataflow instead of a
+ * barrier per phase); observation points synchronise the whole replica.
  * warps_per_cta: 1..16.  Returns KMC_EINVAL if the plan cannot be scheduled
  * or the state does not fit in shared memory; the previous plan then stays.
  * Results do not depend on the plan. */
@@ -192,10 +195,13 @@ kmc_status kmc_set_launch(kmc_ctx *ctx, int32_t mode, int32_t size, int32_t warp
 kmc_status kmc_get_launch(const kmc_ctx *ctx, int32_t *mode, int32_t *size, int32_t *ctas,
                           int32_t *warps_per_cta, int32_t *smem_bytes);
 
-/* Test hook for the bounded grid barrier (GRID plans): the next run's first
- * barrier waits for `extra` arrivals that never come and gives up after
- * limit_ns nanoseconds (KMC_ETIMEOUT at the next kmc_sync).  extra = 0
- * restores the normal barrier; limit_ns = 0 restores the default (2 s). */
+/* Test hook for the bounded waits of the run kernel.  A domain visit waits
+ * (bounded spin) until its four neighbours have completed their earlier
+ * visits; GRID plans also use a bounded grid barrier at observation points.
+ * With extra > 0 every visit waits for `extra` more neighbour visits than
+ * will ever come, so the waits give up after limit_ns nanoseconds and the
+ * next kmc_sync returns KMC_ETIMEOUT; the context stays usable.  extra = 0
+ * restores normal waits; limit_ns = 0 restores the default limit (2 s). */
 kmc_status kmc_debug_barrier(kmc_ctx *ctx, int32_t extra, int64_t limit_ns);
 
 /* Event timing of the persistent run kernel: with enable != 0 every

@@ -546,12 +546,12 @@ kmc_status upload_rates(kmc_ctx *c)
             g32[(size_t)r * 32 + 20 + q] = c->gh[(size_t)r * 10 + q];
         }
     }
-    // synchronous copies: the host vectors are temporaries and the tables may
-    // be read by work already queued on another stream
-    CUDA_TRY(c, cudaMemcpy(c->d_A, A16.data(), A16.size() * 8, cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(c->d_inv, inv16.data(), inv16.size() * 8, cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(c->d_grad, g32.data(), g32.size() * 8, cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(c->d_h, c->h.data(), c->h.size() * 8, cudaMemcpyHostToDevice));
+    // ordered on the context's stream, after any run already queued there; the
+    // sources are pageable, so each copy has consumed them when the call returns
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_A, A16.data(), A16.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_inv, inv16.data(), inv16.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_grad, g32.data(), g32.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_h, c->h.data(), c->h.size() * 8, cudaMemcpyHostToDevice, c->stream));
     return KMC_OK;
 }
 
@@ -751,7 +751,7 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     ALLOC(c->d_grad, (size_t)n_replicas * 32);
     ALLOC(c->d_h, n_replicas);
     ALLOC(c->d_tiles, ndom * tile);
-    ALLOC(c->d_edges, ndom * 4);
+    ALLOC(c->d_edges, ndom * EDGE_WORDS);
     ALLOC(c->d_dctr, ndom * DCTR_WORDS);
     ALLOC(c->d_bar, 1);
     ALLOC(c->d_err, 1);
@@ -936,8 +936,6 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     if (time_mode != KMC_TIME_EXPONENTIAL && time_mode != KMC_TIME_EXPECTED) return fail(c, KMC_EINVAL, "bad time mode");
     if (obs_every < 0) return fail(c, KMC_EINVAL, "obs_every must be >= 0");
     if (c->sched_done + n_schedules >= (1ll << 52)) return fail(c, KMC_EINVAL, "schedule index overflow");
-    if (c->debug_extra > 0 && c->plan.mode != KMC_LAUNCH_GRID)
-        return fail(c, KMC_EINVAL, "the barrier test hook needs the GRID launch mode");
     c->stream = (cudaStream_t)stream;
     if (n_schedules == 0) return KMC_OK;
     cudaStream_t s = c->stream;
@@ -1179,7 +1177,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     // one carving sequence, run twice: to measure (null base) and to place
     auto carve = [&](Carver &cv) {
         c.d_tiles = cv.take<uint8_t>((size_t)c.n_dom * tile);
-        c.d_edges = cv.take<uint64_t>((size_t)c.n_dom * 4);
+        c.d_edges = cv.take<uint64_t>((size_t)c.n_dom * EDGE_WORDS);
         c.d_dctr = cv.take<uint64_t>((size_t)c.n_dom * DCTR_WORDS);
         c.d_dom_rep = cv.take<uint32_t>((size_t)c.n_dom);
         c.d_plan = cv.take<uint32_t>(flat.size());

@@ -6,9 +6,13 @@
 //   * bit tiles: replica r, domain d = by*Dx + bx owns LD*LD bits, row y of
 //     the domain at bits [y*LD, (y+1)*LD) of the tile, bit x = column x,
 //     1 = spin up.  Tile bytes = LD*LD/8.  Global domain id g = dom_off[r] + d.
-//   * edges[g*4 + {N,S,W,E}]: the domain's first row, last row, first column
-//     and last column as bit masks.  Column bit of row y is
-//     (y % RPL)*32 + y / RPL (RPL = rows per lane, 2 for LD = 64, else 1).
+//   * edges[g*8 + ...]: the domain's first row, last row, first column and
+//     last column (N, S, W, E) as bit masks, each split into 32-bit halves
+//     and stamped with the number of visits the domain has completed in the
+//     current launch: word 2e+h = count << 32 | half h of edge e.  Column bit
+//     of row y is (y % RPL)*32 + y / RPL (RPL = rows per lane, 2 for LD = 64,
+//     else 1).  A neighbour reads its halo and checks that it is current with
+//     the same 64-bit loads.
 //   * per-domain counters dctr[g*6 + ...]: event hash, real flips, clock
 //     mantissa, clock exponent, score d/dbeta, score d/dh.
 //
@@ -47,8 +51,15 @@ constexpr int OBS_WORDS = 5; // bonds, mag, clock sum, score beta sum, score h s
 //   [512] seed, [520] dom_off, [524] Dx.
 constexpr int RT_BYTES = 528;
 constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524;
-// Slot: [tile][edges 32][counters 48][meta 32]; meta u32: g, replica, d, rt, nb[4].
-constexpr int SLOT_EXTRA = 32 + 48 + 32;
+// Slot: [tile][stamped edges 64][counters 48][meta 32];
+// meta u32: g, replica, d, rt, nb[4].
+constexpr int SLOT_EXTRA = 64 + 48 + 32;
+constexpr int EDGE_WORDS = 8; // stamped 64-bit words per domain
+
+__host__ __device__ constexpr uint64_t stamp(uint32_t count, uint32_t half)
+{
+    return ((uint64_t)count << 32) | half;
+}
 constexpr int META_G = 0, META_R = 1, META_D = 2, META_RT = 3, META_NB = 4;
 
 template <int LD> __host__ __device__ constexpr int slot_bytes() { return ((LD * LD / 8 + SLOT_EXTRA) + 15) / 16 * 16; }
@@ -142,7 +153,13 @@ __device__ __forceinline__ uint32_t map_rank(uint32_t local_addr, uint32_t rank)
 __device__ __forceinline__ uint64_t ld_dsmem(uint32_t addr)
 {
     uint64_t v;
-    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    asm volatile("ld.volatile.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_volatile_global(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ void cluster_sync()
@@ -184,18 +201,6 @@ __device__ __forceinline__ int select_bit(uint64_t m, uint32_t rr)
     return pos;
 }
 
-// Exclusive prefix over lanes of a small count v < 2^NBITS, from NBITS ballots
-// of its bit planes (no shuffle chain).
-template <int NBITS>
-__device__ __forceinline__ uint32_t excl_prefix_small(uint32_t v, int lane)
-{
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t s = 0;
-#pragma unroll
-    for (int b = 0; b < NBITS; ++b) s += (uint32_t)__popc(__ballot_sync(FULL_WARP, (v >> b) & 1u) & lt) << b;
-    return s;
-}
-
 // Normalised unsigned mantissa product for the exponential clock:
 // value = (m / 2^63) * 2^e with m in [2^63, 2^64).
 __device__ __forceinline__ void mant_mul(uint64_t &m, int64_t &e, uint64_t m2, int64_t e2)
@@ -209,6 +214,15 @@ __device__ __forceinline__ void mant_mul(uint64_t &m, int64_t &e, uint64_t m2, i
         m = (hi << 1) | (lo >> 63);
         e = e + e2;
     }
+}
+
+__device__ __forceinline__ void mant_mul32(uint64_t &m, int &e, uint64_t m2, int e2)
+{
+    const uint64_t hi = __umul64hi(m, m2);
+    const uint64_t lo = m * m2;
+    const bool top = (hi >> 63) != 0;
+    m = top ? hi : ((hi << 1) | (lo >> 63));
+    e = e + e2 + (top ? 1 : 0);
 }
 
 // Domain clock from its state: EXPONENTIAL: -ln(prod v)/Lambda; EXPECTED: steps/Lambda.
@@ -268,36 +282,43 @@ template <int LD> struct Planes {
         }
     }
 
-    // sites of class c = 5*up + q in row t
-    __device__ __forceinline__ row_t mask(int c, int t) const
+    // Sites of one class in row t.  The class c = 5*up + q is given as masks:
+    // UP all ones for up spins, Q2/Q1/Q0 all ones where the bit of q is set.
+    __device__ __forceinline__ row_t mask_q(int t, row_t UP, row_t Q2, row_t Q1, row_t Q0) const
     {
-        const bool up = c >= 5;
-        const int q = up ? c - 5 : c;
-        const row_t sp = up ? S[t] : (row_t)~S[t];
-        row_t e;
-        if (q == 4) {
-            e = b2[t];
-        } else {
-            e = (row_t)~b2[t] & ((q & 2) ? b1[t] : (row_t)~b1[t]) & ((q & 1) ? b0[t] : (row_t)~b0[t]);
-        }
-        return sp & e & valid;
+        const row_t diff = (b2[t] ^ Q2) | (b1[t] ^ Q1) | (b0[t] ^ Q0); // up-neighbour count != q
+        return (S[t] ^ (row_t)~UP) & (row_t)~diff & valid;
     }
 };
 
-// Class counts of the warp's domain: lane c (< 10) receives n_c.
+// Class counts of the warp's domain: lane c (< 10) receives n_c.  Per lane,
+// class q (down spin) is counted in the low and class q+5 (up spin) in the
+// high half-word, so five warp reductions cover the ten classes.
 template <int LD>
 __device__ __forceinline__ uint32_t class_counts(const Planes<LD> &P, int lane)
 {
-    uint32_t mine = 0;
+    using row_t = typename Geo<LD>::row_t;
+    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0;
 #pragma unroll
-    for (int c = 0; c < 10; ++c) {
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int t = 0; t < Geo<LD>::RPL; ++t) cnt += popc_row(P.mask(c, t));
-        const uint32_t tot = __reduce_add_sync(FULL_WARP, cnt);
-        if (lane == c) mine = tot;
+    for (int t = 0; t < Geo<LD>::RPL; ++t) {
+        const row_t b2 = P.b2[t], b1 = P.b1[t], b0 = P.b0[t];
+        const row_t up = P.S[t], dn = (row_t)~P.S[t] & P.valid;
+        const row_t n2 = (row_t)~b2;
+        const row_t e0 = n2 & (row_t)~b1 & (row_t)~b0, e1 = n2 & (row_t)~b1 & b0;
+        const row_t e2 = n2 & b1 & (row_t)~b0, e3 = n2 & b1 & b0, e4 = b2;
+        w0 += (uint32_t)popc_row(dn & e0) | ((uint32_t)popc_row(up & e0) << 16);
+        w1 += (uint32_t)popc_row(dn & e1) | ((uint32_t)popc_row(up & e1) << 16);
+        w2 += (uint32_t)popc_row(dn & e2) | ((uint32_t)popc_row(up & e2) << 16);
+        w3 += (uint32_t)popc_row(dn & e3) | ((uint32_t)popc_row(up & e3) << 16);
+        w4 += (uint32_t)popc_row(dn & e4) | ((uint32_t)popc_row(up & e4) << 16);
     }
-    return mine;
+    const uint32_t t0 = __reduce_add_sync(FULL_WARP, w0), t1 = __reduce_add_sync(FULL_WARP, w1);
+    const uint32_t t2 = __reduce_add_sync(FULL_WARP, w2), t3 = __reduce_add_sync(FULL_WARP, w3);
+    const uint32_t t4 = __reduce_add_sync(FULL_WARP, w4);
+    const int q = (lane < 5) ? lane : lane - 5;
+    const uint32_t tw = (q == 0) ? t0 : (q == 1) ? t1 : (q == 2) ? t2 : (q == 3) ? t3 : t4;
+    const uint32_t n = (lane < 5) ? (tw & 0xFFFFu) : (tw >> 16);
+    return (lane < 10) ? n : 0u;
 }
 
 // Inclusive prefix over lanes 0..15 of w (64-bit).
@@ -384,6 +405,7 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const u
         const int s = base + lane;
         uint64_t tgt = ~0ull;
         uint64_t V = 1ull << 53;
+        uint64_t ebase = 0;
         if (s < total) {
             const int f = s / k;
             const int j = s - f * k;
@@ -392,8 +414,24 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const u
                 make_uint4((uint32_t)j, d, (uint32_t)np, (uint32_t)(np >> 32) & 0xFFFFFFu), key);
             tgt = (((uint64_t)w.y << 32) | w.x) >> 1;
             V = ((((uint64_t)w.w << 32) | w.z) >> 11) + 1ull;
+            ebase = (np << 32) | ((uint64_t)j << 16); // event word of this step, site bits added on a flip
         }
         const int chunk_end = min(32, total - base);
+        if (EXPO) {
+            // product of this chunk's variates: butterfly over the smallest power of
+            // two covering the chunk (lanes past its end hold v = 1)
+            const int z = __clzll((long long)V);
+            uint64_t m = V << z;
+            int e = 10 - z;
+            for (int off = 1; off < chunk_end; off <<= 1) {
+                const uint64_t m2 = __shfl_xor_sync(FULL_WARP, m, off);
+                const int e2 = __shfl_xor_sync(FULL_WARP, e, off);
+                mant_mul32(m, e, m2, e2);
+            }
+            m = __shfl_sync(FULL_WARP, m, 0);
+            e = __shfl_sync(FULL_WARP, e, 0);
+            mant_mul(cn.clkM, cn.clkE, m, (int64_t)e);
+        }
         int pos = 0;
         while (true) {
             const unsigned real = __ballot_sync(FULL_WARP, lane >= pos && tgt < R);
@@ -406,31 +444,47 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const u
             }
             if (!real) break;
             const uint64_t t = __shfl_sync(FULL_WARP, tgt, jx);
+            const uint64_t ev = __shfl_sync(FULL_WARP, ebase, jx);
             const unsigned sel = __ballot_sync(FULL_WARP, lane < 10 && t < Cinc);
             const int c = __ffs(sel) - 1;
-            uint64_t q = 0;
+            uint32_t q = 0;
             if (lane == c) {
+                // exact floor((t - C_{c-1}) / A_c): reciprocal estimate, then at
+                // most three corrections
                 const uint64_t x = t - (Cinc - Wc);
-                q = __umul64hi(x, invc);
-                if ((q + 1) * Ac <= x) ++q;
-                if ((q + 1) * Ac <= x) ++q;
-                if ((q + 1) * Ac <= x) ++q;
+                uint64_t qq = __umul64hi(x, invc);
+                uint64_t r = x - qq * Ac;
+                if (r >= Ac) { ++qq; r -= Ac; }
+                if (r >= Ac) { ++qq; r -= Ac; }
+                if (r >= Ac) { ++qq; }
+                q = (uint32_t)qq;
             }
-            const uint32_t jj = (uint32_t)__shfl_sync(FULL_WARP, q, c);
+            const uint32_t jj = __shfl_sync(FULL_WARP, q, c);
             if (GRAD) {
                 cn.sb += __shfl_sync(FULL_WARP, gb_c, c);
                 cn.sh += __shfl_sync(FULL_WARP, gh_c, c);
             }
             // rank selection: jj-th member of class c in row-major order
+            const int qc = (c >= 5) ? c - 5 : c;
+            const row_t UP = (c >= 5) ? (row_t)~(row_t)0 : (row_t)0;
+            const row_t Q2 = (qc & 4) ? (row_t)~(row_t)0 : (row_t)0;
+            const row_t Q1 = (qc & 2) ? (row_t)~(row_t)0 : (row_t)0;
+            const row_t Q0 = (qc & 1) ? (row_t)~(row_t)0 : (row_t)0;
             row_t m[G::RPL];
             uint32_t cl = 0;
 #pragma unroll
             for (int tt = 0; tt < G::RPL; ++tt) {
-                m[tt] = pl.mask(c, tt);
+                m[tt] = pl.mask_q(tt, UP, Q2, Q1, Q0);
                 cl += popc_row(m[tt]);
             }
-            const uint32_t excl = excl_prefix_small<(LD > 32) ? 8 : 7>(cl, lane);
-            const unsigned win = __ballot_sync(FULL_WARP, jj >= excl && jj < excl + cl);
+            uint32_t incl = cl;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t v = __shfl_up_sync(FULL_WARP, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const uint32_t excl = incl - cl;
+            const unsigned win = __ballot_sync(FULL_WARP, jj >= excl && jj < incl);
             if (!win) {
                 if (lane == 0) atomicCAS(err, 0, ERR_INTERNAL);
                 break;
@@ -452,15 +506,8 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const u
 #pragma unroll
             for (int tt = 0; tt < G::RPL; ++tt)
                 if (lane * G::RPL + tt == y) pl.S[tt] ^= (row_t)1 << col;
-            {
-                const int sx = base + jx;
-                const int f = sx / k;
-                const int j = sx - f * k;
-                const uint64_t np = np0 + (uint64_t)f;
-                const uint64_t e = (np << 32) | ((uint64_t)j << 16) | (uint64_t)(y * LD + col);
-                cn.H = (cn.H ^ e) * HASH_PRIME;
-                ++cn.flips;
-            }
+            cn.H = (cn.H ^ (ev | (uint64_t)(y * LD + col))) * HASH_PRIME;
+            ++cn.flips;
             pl.build(lane, hN, hS, hW, hE);
             n_c = class_counts<LD>(pl, lane);
             Wc = (uint64_t)n_c * Ac;
@@ -469,23 +516,33 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const u
             grad_state();
             pos = jx + 1;
         }
-        if (EXPO) {
-            const int z = __clzll((long long)V);
-            uint64_t m = V << z;
-            int64_t e = 10 - z;
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) {
-                const uint64_t m2 = __shfl_xor_sync(FULL_WARP, m, off);
-                const int64_t e2 = __shfl_xor_sync(FULL_WARP, e, off);
-                mant_mul(m, e, m2, e2);
-            }
-            mant_mul(cn.clkM, cn.clkE, m, e);
-        }
     }
 }
 
-// Four edge words of the warp's domain (N row, S row, W column, E column);
-// lane i (< 4) returns edge i.
+// Four edge words of the warp's domain (N row, S row, W column, E column),
+// the same in every lane.
+struct Edges {
+    uint64_t w[4];
+};
+template <int LD>
+__device__ __forceinline__ Edges all_edges(const typename Geo<LD>::row_t (&S)[Geo<LD>::RPL])
+{
+    using G = Geo<LD>;
+    Edges e;
+    uint64_t colW = 0, colE = 0;
+#pragma unroll
+    for (int t = 0; t < G::RPL; ++t) {
+        colW |= (uint64_t)__ballot_sync(FULL_WARP, (S[t] & 1u) != 0) << (32 * t);
+        colE |= (uint64_t)__ballot_sync(FULL_WARP, ((S[t] >> (LD - 1)) & 1u) != 0) << (32 * t);
+    }
+    e.w[EDGE_N] = (uint64_t)__shfl_sync(FULL_WARP, S[0], 0);
+    e.w[EDGE_S] = (uint64_t)__shfl_sync(FULL_WARP, S[G::RPL - 1], G::NACT - 1);
+    e.w[EDGE_W] = colW;
+    e.w[EDGE_E] = colE;
+    return e;
+}
+
+// Lane i (< 4) returns edge i of the warp's domain.
 template <int LD>
 __device__ __forceinline__ uint64_t edge_words(const typename Geo<LD>::row_t (&S)[Geo<LD>::RPL], int lane)
 {
@@ -499,6 +556,14 @@ __device__ __forceinline__ uint64_t edge_words(const typename Geo<LD>::row_t (&S
     const uint64_t rowN = (uint64_t)__shfl_sync(FULL_WARP, S[0], 0);
     const uint64_t rowS = (uint64_t)__shfl_sync(FULL_WARP, S[G::RPL - 1], G::NACT - 1);
     return (lane == EDGE_N) ? rowN : (lane == EDGE_S) ? rowS : (lane == EDGE_W) ? colW : colE;
+}
+
+// Stamped word w (0..7) of the warp's edges: half (w & 1) of edge (w >> 1).
+__device__ __forceinline__ uint64_t stamped_word(const Edges &e, int w, uint32_t count)
+{
+    const int q = (w >> 1) & 3;
+    const uint64_t x = (q == 0) ? e.w[0] : (q == 1) ? e.w[1] : (q == 2) ? e.w[2] : e.w[3];
+    return stamp(count, (w & 1) ? (uint32_t)(x >> 32) : (uint32_t)x);
 }
 
 // ---------------------------------------------------------------------------
@@ -616,7 +681,9 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
     using mem_t = typename G::mem_t;
     constexpr int TB = G::TILE_BYTES;
     constexpr int SB = slot_bytes<LD>();
-    constexpr int OFF_EDGE = TB, OFF_CTR = TB + 32, OFF_META = TB + 80;
+    constexpr int OFF_EDGE = TB, OFF_CTR = TB + 64, OFF_META = TB + 112;
+    // stamped words a halo read needs per neighbour: one half for LD <= 32, two for 64
+    constexpr int HALVES = (LD > 32) ? 2 : 1;
 
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_ok;
@@ -667,49 +734,85 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         if (lane < 4) {
             const uint32_t nb = P.slot_nb[(size_t)s * 4 + lane];
             if (CLUSTER) {
-                // address of the edge word this slot reads from its neighbour:
-                // the N neighbour's S row, the S neighbour's N row, the W
-                // neighbour's E column, the E neighbour's W column
-                const int want = (lane == EDGE_N) ? EDGE_S : (lane == EDGE_S) ? EDGE_N : (lane == EDGE_W) ? EDGE_E : EDGE_W;
+                // address of the neighbour's slot in the cluster's shared memory
                 const uint32_t nrank = nb >> 24, nslot_ = nb & 0xFFFFFFu;
-                const uint32_t local = smem_addr(slots + (size_t)nslot_ * SB + OFF_EDGE + 8 * want);
-                meta[META_NB + lane] = map_rank(local, nrank);
+                meta[META_NB + lane] = map_rank(smem_addr(slots + (size_t)nslot_ * SB), nrank);
             } else {
                 meta[META_NB + lane] = nb;
             }
         }
         if (CLUSTER) {
-            // edges of the staged tile, published in shared memory
+            // edges of the staged tile, stamped with visit count 0
             row_t S[G::RPL];
             const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
 #pragma unroll
             for (int t = 0; t < G::RPL; ++t) S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
-            const uint64_t ew = edge_words<LD>(S, lane);
-            if (lane < 4) reinterpret_cast<uint64_t *>(sl + OFF_EDGE)[lane] = ew;
+            const Edges ew = all_edges<LD>(S);
+            if (lane < EDGE_WORDS) reinterpret_cast<uint64_t *>(sl + OFF_EDGE)[lane] = stamped_word(ew, lane, 0u);
         }
     }
     if (CLUSTER) cluster_sync();
     else __syncthreads();
 
-    // halo of a slot: four edge words of its neighbours
-    auto read_halo = [&](const uint32_t *meta, uint64_t &hN, uint64_t &hS, uint64_t &hW, uint64_t &hE) {
-        if (CLUSTER) {
-            hN = ld_dsmem(meta[META_NB + EDGE_N]);
-            hS = ld_dsmem(meta[META_NB + EDGE_S]);
-            hW = ld_dsmem(meta[META_NB + EDGE_W]);
-            hE = ld_dsmem(meta[META_NB + EDGE_E]);
-        } else {
-            hN = ld_cg(&P.edges[(size_t)meta[META_NB + EDGE_N] * 4 + EDGE_S]);
-            hS = ld_cg(&P.edges[(size_t)meta[META_NB + EDGE_S] * 4 + EDGE_N]);
-            hW = ld_cg(&P.edges[(size_t)meta[META_NB + EDGE_W] * 4 + EDGE_E]);
-            hE = ld_cg(&P.edges[(size_t)meta[META_NB + EDGE_E] * 4 + EDGE_W]);
+    // Halo of a slot once its neighbours are ready.  Lane i (< 4*HALVES)
+    // reads half (i / 4) of the edge word that borders on neighbour i % 4
+    // (the N neighbour's S row, the S neighbour's N row, the W neighbour's E
+    // column, the E neighbour's W column) until its stamp shows that the
+    // neighbour has completed `need` visits, i.e. all its visits of earlier
+    // phases (bounded spin).  A neighbour cannot complete another visit before
+    // this one, so the stamp then equals `need`.
+    auto wait_halo = [&](const uint32_t *meta, uint32_t needNS, uint32_t needWE, uint64_t &hN, uint64_t &hS,
+                         uint64_t &hW, uint64_t &hE) -> bool {
+        uint32_t half = 0;
+        int good = 1;
+        if (lane < 4 * HALVES) {
+            const int dir = lane & 3, hf = lane >> 2;
+            const uint32_t need = ((dir < 2) ? needNS : needWE) + (uint32_t)P.debug_extra;
+            const int want = (dir == EDGE_N) ? EDGE_S : (dir == EDGE_S) ? EDGE_N : (dir == EDGE_W) ? EDGE_E : EDGE_W;
+            const uint32_t nb = meta[META_NB + dir];
+            const int word = 2 * want + hf;
+            auto load = [&]() -> uint64_t {
+                return CLUSTER ? ld_dsmem(nb + OFF_EDGE + 8 * word)
+                               : ld_volatile_global(&P.edges[(size_t)nb * EDGE_WORDS + word]);
+            };
+            uint64_t v = load();
+            if ((uint32_t)(v >> 32) < need) {
+                const uint64_t t0 = global_ns();
+                unsigned spins = 0;
+                while (true) {
+                    v = load();
+                    if ((uint32_t)(v >> 32) >= need) break;
+                    if ((++spins & 63u) == 0) {
+                        if (*(volatile int *)P.err != 0) { good = 0; break; }
+                        if (global_ns() - t0 > P.bar_limit_ns) {
+                            atomicCAS(P.err, 0, ERR_TIMEOUT);
+                            good = 0;
+                            break;
+                        }
+                    }
+                }
+            }
+            half = (uint32_t)v;
         }
+        const bool all = __all_sync(FULL_WARP, good != 0);
+        uint64_t h[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint64_t lo = __shfl_sync(FULL_WARP, half, q);
+            const uint64_t hi = (HALVES == 2) ? (uint64_t)__shfl_sync(FULL_WARP, half, 4 + q) : 0ull;
+            h[q] = lo | (hi << 32);
+        }
+        hN = h[EDGE_N];
+        hS = h[EDGE_S];
+        hW = h[EDGE_W];
+        hE = h[EDGE_E];
+        return all;
     };
 
-    auto visit = [&](uint8_t *sl, uint64_t np0, int nf) {
+    // One visit; publishes the slot's edges, then (release) its visit count.
+    auto visit = [&](uint8_t *sl, uint64_t np0, int nf, uint64_t hN, uint64_t hS, uint64_t hW, uint64_t hE,
+                     uint32_t count_after) {
         const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
-        uint64_t hN, hS, hW, hE;
-        read_halo(meta, hN, hS, hW, hE);
         const uint8_t *rt = tables + (size_t)meta[META_RT] * RT_BYTES;
         Planes<LD> pl;
         pl.valid = (lane < G::NACT) ? G::FULL : (row_t)0;
@@ -730,11 +833,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
 #pragma unroll
             for (int t = 0; t < G::RPL; ++t) wrow[lane * G::RPL + t] = (mem_t)pl.S[t];
         }
-        const uint64_t ew = edge_words<LD>(pl.S, lane);
-        if (lane < 4) {
-            if (CLUSTER) reinterpret_cast<uint64_t *>(sl + OFF_EDGE)[lane] = ew;
-            else st_cg(&P.edges[(size_t)meta[META_G] * 4 + lane], ew);
-        }
+        const Edges ew = all_edges<LD>(pl.S);
         if (lane == 0) {
             ctr[DCTR_HASH] = cn.H;
             ctr[DCTR_FLIPS] += cn.flips;
@@ -745,25 +844,30 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                 reinterpret_cast<double *>(ctr)[DCTR_SH] += cn.sh;
             }
         }
+        if (lane < EDGE_WORDS) {
+            const uint64_t wv = stamped_word(ew, lane, count_after);
+            if (CLUSTER) reinterpret_cast<volatile uint64_t *>(sl + OFF_EDGE)[lane] = wv;
+            else st_cg(&P.edges[(size_t)meta[META_G] * EDGE_WORDS + lane], wv);
+        }
         __syncwarp();
     };
 
-    auto phase_sync = [&](unsigned &bar_no) -> bool {
-        if (CLUSTER) {
-            cluster_sync();
-            return true;
-        }
-        return grid_barrier(P, bar_no, &s_ok);
+    auto phase_sync = [&](unsigned &bar_no) {
+        if (CLUSTER) cluster_sync();
+        else grid_barrier(P, bar_no, &s_ok);
     };
+
+    // completed visit groups per colour in this launch (PALINDROME, FIXED)
+    uint32_t gc0 = 0, gc1 = 0, gc2 = 0, gc3 = 0;
+    auto gcount = [&](int c) { return c == 0 ? gc0 : c == 1 ? gc1 : c == 2 ? gc2 : gc3; };
 
     const int nph = (P.schedule == SCHED_PALINDROME) ? 8 : 4;
     const uint64_t gp_begin = (uint64_t)P.sched_begin * nph;
     const uint64_t gp_end = (uint64_t)(P.sched_begin + P.n_sched) * nph;
     unsigned bar_no = 0;
-    bool started = false;
-    bool ok = true;
+    bool ok = true; // uniform within the warp; a warp that failed skips work but keeps every barrier
     uint64_t gp = gp_begin;
-    while (gp < gp_end && ok) {
+    while (gp < gp_end) {
         const uint64_t n = gp / nph;
         const int p = (int)(gp % nph);
         // global phase index of the Philox counter: 8 slots per schedule for every
@@ -771,9 +875,8 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         // have consecutive indices
         const uint64_t np0 = n * 8 + (uint64_t)p;
         int nf = 1;
-        int colour = 0;
         if (P.schedule != SCHED_RANDOM_PERM) {
-            colour = fixed_colour(P.schedule, p);
+            const int colour = fixed_colour(P.schedule, p);
             // fuse following phases of the same colour unless an observation intervenes
             while (gp + nf < gp_end) {
                 const uint64_t g2 = gp + nf;
@@ -785,66 +888,109 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                 }
                 ++nf;
             }
-        }
-        if (started) ok = phase_sync(bar_no);
-        started = true;
-        if (!ok) break;
-        if (P.schedule != SCHED_RANDOM_PERM) {
-            const int i0 = (int)col_off[colour], i1 = (int)col_off[colour + 1];
-            for (int i = i0 + wib; i < i1; i += nwarps) visit(slots + (size_t)i * SB, np0, nf);
-        } else {
+            // a neighbour across a row has colour ^ 2, across a column colour ^ 1
+            const uint32_t needNS = gcount(colour ^ 2), needWE = gcount(colour ^ 1);
+            const uint32_t after = gcount(colour) + 1;
+            if (ok) {
+                const int i0 = (int)col_off[colour], i1 = (int)col_off[colour + 1];
+                for (int i = i0 + wib; i < i1; i += nwarps) {
+                    uint8_t *sl = slots + (size_t)i * SB;
+                    uint64_t hN, hS, hW, hE;
+                    if (!wait_halo(reinterpret_cast<const uint32_t *>(sl + OFF_META), needNS, needWE, hN, hS, hW, hE)) {
+                        ok = false;
+                        break;
+                    }
+                    visit(sl, np0, nf, hN, hS, hW, hE, after);
+                }
+            }
+            if (colour == 0) ++gc0;
+            else if (colour == 1) ++gc1;
+            else if (colour == 2) ++gc2;
+            else ++gc3;
+        } else if (ok) {
+            // RANDOM_PERM: every replica draws its own colour order per schedule
+            const uint32_t done_before = (uint32_t)(n - (uint64_t)P.sched_begin);
             for (int i = wib; i < nslot; i += nwarps) {
                 uint8_t *sl = slots + (size_t)i * SB;
                 const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
                 const uint32_t d = meta[META_D];
                 const uint8_t *rt = tables + (size_t)meta[META_RT] * RT_BYTES;
+                const uint64_t seed = *reinterpret_cast<const uint64_t *>(rt + RT_SEED);
                 const int Dx = *reinterpret_cast<const int32_t *>(rt + RT_DX);
                 const int c = (int)((d % (uint32_t)Dx) & 1u) | (int)(((d / (uint32_t)Dx) & 1u) << 1);
-                if (perm_colour(*reinterpret_cast<const uint64_t *>(rt + RT_SEED), n, p) != c) continue;
-                visit(sl, np0, 1);
+                if (perm_colour(seed, n, p) != c) continue;
+                // neighbours' colours c^2 (rows) and c^1 (columns): done in this
+                // schedule iff they came earlier in its order
+                int posNS = 0, posWE = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int cq = perm_colour(seed, n, q);
+                    if (cq == (c ^ 2)) posNS = q;
+                    if (cq == (c ^ 1)) posWE = q;
+                }
+                uint64_t hN, hS, hW, hE;
+                if (!wait_halo(meta, done_before + (posNS < p ? 1u : 0u), done_before + (posWE < p ? 1u : 0u), hN, hS,
+                               hW, hE)) {
+                    ok = false;
+                    break;
+                }
+                visit(sl, np0, 1, hN, hS, hW, hE, done_before + 1u);
             }
         }
         gp += (uint64_t)nf;
-        // endpoint observation after a completed schedule (Sec. 2.3)
+        // endpoint observation after a completed schedule (Sec. 2.3): all visits
+        // done before, no visit of the next schedule until every domain is observed
         if (gp % nph == 0) {
             const int64_t nl_done = (int64_t)(gp / nph - (uint64_t)P.sched_begin);
             if (P.obs_every > 0 && P.obs_acc != nullptr && nl_done > 0 && (nl_done % P.obs_every) == 0) {
-                ok = phase_sync(bar_no);
-                if (!ok) break;
-                const int64_t o = nl_done / P.obs_every - 1;
-                const int64_t visits = P.visits_before + nl_done * (nph == 8 ? 2 : 1);
-                for (int i = wib; i < nslot; i += nwarps) {
-                    const uint8_t *sl = slots + (size_t)i * SB;
-                    const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
-                    uint64_t hN, hS, hW, hE;
-                    read_halo(meta, hN, hS, hW, hE);
-                    row_t S[G::RPL];
-                    const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
+                phase_sync(bar_no);
+                if (ok && *(volatile int *)P.err == 0) {
+                    const int64_t o = nl_done / P.obs_every - 1;
+                    const int64_t visits = P.visits_before + nl_done * (nph == 8 ? 2 : 1);
+                    for (int i = wib; i < nslot; i += nwarps) {
+                        const uint8_t *sl = slots + (size_t)i * SB;
+                        const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
+                        // E neighbour's W column and S neighbour's N row (stamps dropped)
+                        uint32_t half = 0;
+                        if (lane < 4) {
+                            const int dir = (lane & 1) ? EDGE_E : EDGE_S, hf = lane >> 1;
+                            const uint32_t nb = meta[META_NB + dir];
+                            const int word = 2 * ((dir == EDGE_S) ? EDGE_N : EDGE_W) + hf;
+                            half = (uint32_t)(CLUSTER ? ld_dsmem(nb + OFF_EDGE + 8 * word)
+                                                      : ld_volatile_global(&P.edges[(size_t)nb * EDGE_WORDS + word]));
+                        }
+                        const uint64_t hS = (uint64_t)__shfl_sync(FULL_WARP, half, 0) |
+                                            ((uint64_t)__shfl_sync(FULL_WARP, half, 2) << 32);
+                        const uint64_t hE = (uint64_t)__shfl_sync(FULL_WARP, half, 1) |
+                                            ((uint64_t)__shfl_sync(FULL_WARP, half, 3) << 32);
+                        row_t S[G::RPL];
+                        const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
 #pragma unroll
-                    for (int t = 0; t < G::RPL; ++t) S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
-                    int bonds, mag;
-                    domain_bonds_mag<LD>(S, hE, hS, lane, bonds, mag);
-                    if (lane == 0) {
-                        const uint64_t *ctr = reinterpret_cast<const uint64_t *>(sl + OFF_CTR);
-                        const double tdom = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE],
-                                                        visits * (int64_t)P.k, P.lambda);
-                        unsigned long long *acc = P.obs_acc + ((size_t)o * P.n_rep + meta[META_R]) * OBS_WORDS;
-                        atomicAdd(&acc[0], (unsigned long long)(long long)bonds);
-                        atomicAdd(&acc[1], (unsigned long long)(long long)mag);
-                        atomicAdd(reinterpret_cast<double *>(&acc[2]), tdom);
-                        atomicAdd(reinterpret_cast<double *>(&acc[3]), reinterpret_cast<const double *>(ctr)[DCTR_SB]);
-                        atomicAdd(reinterpret_cast<double *>(&acc[4]), reinterpret_cast<const double *>(ctr)[DCTR_SH]);
+                        for (int t = 0; t < G::RPL; ++t) S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
+                        int bonds, mag;
+                        domain_bonds_mag<LD>(S, hE, hS, lane, bonds, mag);
+                        if (lane == 0) {
+                            const uint64_t *ctr = reinterpret_cast<const uint64_t *>(sl + OFF_CTR);
+                            const double tdom = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE],
+                                                            visits * (int64_t)P.k, P.lambda);
+                            unsigned long long *acc = P.obs_acc + ((size_t)o * P.n_rep + meta[META_R]) * OBS_WORDS;
+                            atomicAdd(&acc[0], (unsigned long long)(long long)bonds);
+                            atomicAdd(&acc[1], (unsigned long long)(long long)mag);
+                            atomicAdd(reinterpret_cast<double *>(&acc[2]), tdom);
+                            atomicAdd(reinterpret_cast<double *>(&acc[3]), reinterpret_cast<const double *>(ctr)[DCTR_SB]);
+                            atomicAdd(reinterpret_cast<double *>(&acc[4]), reinterpret_cast<const double *>(ctr)[DCTR_SH]);
+                        }
                     }
                 }
+                phase_sync(bar_no);
             }
         }
     }
     if (CLUSTER) {
         // no CTA may leave while another still reads its shared memory
         cluster_sync();
-    } else if (!ok) {
-        return;
     }
+    if (*(volatile int *)P.err != 0) return;
     // write owned tiles and counters back (and edges, for the observables kernel)
     for (int i = wib; i < nslot; i += nwarps) {
         const uint8_t *sl = slots + (size_t)i * SB;
@@ -853,8 +999,8 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
             *reinterpret_cast<uint32_t *>(P.tiles + (size_t)g * TB + q) = *reinterpret_cast<const uint32_t *>(sl + q);
         if (lane < DCTR_WORDS)
             P.dctr[(size_t)g * DCTR_WORDS + lane] = reinterpret_cast<const uint64_t *>(sl + OFF_CTR)[lane];
-        if (CLUSTER && lane < 4)
-            P.edges[(size_t)g * 4 + lane] = reinterpret_cast<const uint64_t *>(sl + OFF_EDGE)[lane];
+        if (CLUSTER && lane < EDGE_WORDS)
+            P.edges[(size_t)g * EDGE_WORDS + lane] = reinterpret_cast<const uint64_t *>(sl + OFF_EDGE)[lane];
     }
 }
 
@@ -951,8 +1097,8 @@ __global__ void pack_kernel(const LayoutParams P)
 #pragma unroll
             for (int t = 0; t < G::RPL; ++t) trow[lane * G::RPL + t] = (mem_t)S[t];
         }
-        const uint64_t ew = edge_words<LD>(S, lane);
-        if (lane < 4) P.edges[(uint64_t)g * 4 + lane] = ew;
+        const Edges ew = all_edges<LD>(S);
+        if (lane < EDGE_WORDS) P.edges[(uint64_t)g * EDGE_WORDS + lane] = stamped_word(ew, lane, 0u);
     }
 }
 
@@ -1007,8 +1153,10 @@ __global__ void observe_kernel(const RunParams P, const uint32_t *dom_rep, int n
         const uint32_t d = (uint32_t)g - P.rep_dom_off[r];
         const int bx = (int)(d % (uint32_t)Dx), by = (int)(d / (uint32_t)Dx);
         const uint64_t gbase = (uint64_t)g - d;
-        const uint64_t hS = P.edges[(gbase + (uint32_t)(((by + 1) % Dx) * Dx + bx)) * 4 + EDGE_N];
-        const uint64_t hE = P.edges[(gbase + (uint32_t)(by * Dx + (bx + 1) % Dx)) * 4 + EDGE_W];
+        const uint64_t *eS = P.edges + (gbase + (uint32_t)(((by + 1) % Dx) * Dx + bx)) * EDGE_WORDS;
+        const uint64_t *eE = P.edges + (gbase + (uint32_t)(by * Dx + (bx + 1) % Dx)) * EDGE_WORDS;
+        const uint64_t hS = (eS[2 * EDGE_N] & 0xFFFFFFFFull) | (eS[2 * EDGE_N + 1] << 32);
+        const uint64_t hE = (eE[2 * EDGE_W] & 0xFFFFFFFFull) | (eE[2 * EDGE_W + 1] << 32);
         row_t S[G::RPL];
         const mem_t *trow = reinterpret_cast<const mem_t *>(P.tiles + (uint64_t)g * G::TILE_BYTES);
 #pragma unroll

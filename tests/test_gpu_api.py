@@ -64,11 +64,12 @@ def test_spins_that_are_not_pm1_raise_device_error():
     lat.close()
 
 
-def test_grid_barrier_gives_up_and_context_survives():
-    """A barrier that waits for an arrival that never comes returns KMC_ETIMEOUT."""
+@pytest.mark.parametrize("plan", [(2, 4, 4), (1, 2, 4), (1, 1, 16)])
+def test_bounded_waits_give_up_and_context_survives(plan):
+    """Neighbour waits that wait for visits that never come return KMC_ETIMEOUT."""
     kmc = _kmc()
     lat = kmc.Lattice([128], 16, 2, [5])
-    lat.set_launch(kmc.KMC_LAUNCH_GRID, 4, 4)
+    lat.set_launch(*plan)
     kmc.kmc_debug_barrier(lat.ctx, 1, 20_000_000)  # 20 ms
     lat.run(3)
     with pytest.raises(kmc.KmcError) as ei:
