@@ -155,6 +155,17 @@ kmc_status kmc_observables(kmc_ctx *ctx, double *E_per_site, double *m, double *
  */
 kmc_status kmc_grad(kmc_ctx *ctx, double *score_dev, int32_t reset);
 
+/*
+ * kmc_lr_estimate -- likelihood-ratio gradient of E[A] over the replicas:
+ * grad_dev[j] = (1/R) sum_r (A_r - mean A) S_r,j for j = {beta, h}, where
+ * A_dev[r] (device, n_replicas doubles) is an observable of replica r at the
+ * current endpoint and S_r the path score accumulated since the last reset
+ * (kmc_grad with reset, or kmc_reset).  Subtracting the replica mean is a
+ * baseline: E[S] = 0, so the estimate stays unbiased.  Asynchronous, on the
+ * context's stream; needs n_replicas >= 2.
+ */
+kmc_status kmc_lr_estimate(kmc_ctx *ctx, const double *A_dev, double *grad_dev);
+
 /* Turn score accumulation on (enable != 0) or off for following runs. */
 kmc_status kmc_enable_grad(kmc_ctx *ctx, int32_t enable);
 

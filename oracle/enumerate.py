@@ -130,6 +130,35 @@ class Enumerator:
         rates = [r / tot for r in raw]
         return self._apply_rates(p, sites, rates)
 
+    # -- exact derivatives (forward mode) ----------------------------------------
+    def set_score_table(self, grad30: np.ndarray):
+        """Real-valued a_c and dlog a_c/d(beta, h) used for derivatives."""
+        self.ga = np.asarray(grad30[0:10], dtype=np.float64)
+        self.gb = np.asarray(grad30[10:20], dtype=np.float64)
+        self.gh = np.asarray(grad30[20:30], dtype=np.float64)
+
+    def step_deriv(self, d: int, p: np.ndarray, dps):
+        """One domain step and its derivative: d(T p) = (dT) p + T (dp), for
+        dp in dps = (dp/dbeta, dp/dh).  Rates a_c/n_d, d rate = a_c g_c / n_d."""
+        sites = self.domain_sites(d)
+        rates = [self.ga[self.cls[:, i]] / self.nd for i in sites]
+        out = self._apply_rates(p, sites, rates)
+        douts = []
+        for dp, g in zip(dps, (self.gb, self.gh)):
+            drates = [self.ga[self.cls[:, i]] * g[self.cls[:, i]] / self.nd for i in sites]
+            dT_p = -p * sum(drates)
+            for i, dr in zip(sites, drates):
+                dT_p = dT_p + (dr * p)[self.idx ^ (1 << i)]
+            douts.append(dT_p + self._apply_rates(dp, sites, rates))
+        return out, douts
+
+    def schedule_deriv(self, colours, p: np.ndarray, dps):
+        for c in colours:
+            for d in self.domains_of_colour(c):
+                for _ in range(self.k):
+                    p, dps = self.step_deriv(d, p, dps)
+        return p, dps
+
     # -- checks -----------------------------------------------------------------
     def stationarity_error(self, op) -> float:
         return float(np.max(np.abs(op(self.pi) - self.pi)) / np.max(self.pi))

@@ -38,7 +38,9 @@
  * Pins (tests/test_oracle_*.py): Philox against PyTorch's engine; the
  * rate table against closed forms; the sampler against exact enumeration of
  * the same chain, the beta = 0 closed form and the Erlang clock law; the
- * long-run energy against Kaufman's exact finite lattice.
+ * long-run energy against Kaufman's exact finite lattice; the score table
+ * against finite differences of the rate table, and the likelihood-ratio
+ * estimator against the exact derivative of the enumerated distribution.
  * Parity unpinned: the per-domain event hash (a fingerprint this build
  * defines for CPU/GPU event-sequence parity, not a quantity of the paper)
  * and the Philox counter layout (likewise a definition of this build).
@@ -146,6 +148,37 @@ int orc_rate_table(double J, double beta, double h, int law, int log2_nd,
     return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * Derivatives of log a_c for the likelihood-ratio score (the acceptance
+ * table above as a function of beta and h):
+ *   Metropolis, dE_c > 0: dlog a/dbeta = -dE_c, dlog a/dh = -2 beta sigma;
+ *               dE_c <= 0: both 0 (a = 1);
+ *   Barker: dlog a/dbeta = -dE_c (1 - a_c), dlog a/dh = -2 beta sigma (1 - a_c).
+ * grad[0..9] = a_c, grad[10..19] = dlog a_c/dbeta, grad[20..29] = dlog a_c/dh.
+ * ---------------------------------------------------------------------- */
+int orc_score_table(double J, double beta, double h, int law, double grad[30])
+{
+    if (law != ORC_RATE_METROPOLIS && law != ORC_RATE_BARKER) return -1;
+    for (int c = 0; c < 10; ++c) {
+        int sp = c / 5, q = c % 5;
+        double sigma = sp ? 1.0 : -1.0;
+        double dE = 2.0 * sigma * (J * (double)(2 * q - 4) + h);
+        double a, db, dh;
+        if (law == ORC_RATE_METROPOLIS) {
+            if (dE <= 0.0) { a = 1.0; db = 0.0; dh = 0.0; }
+            else { a = exp(-beta * dE); db = -dE; dh = -beta * 2.0 * sigma; }
+        } else {
+            a = 1.0 / (1.0 + exp(beta * dE));
+            db = -dE * (1.0 - a);
+            dh = -beta * 2.0 * sigma * (1.0 - a);
+        }
+        grad[c] = a;
+        grad[10 + c] = db;
+        grad[20 + c] = dh;
+    }
+    return 0;
+}
+
 /* dE of class c, for tests and for the score. */
 double orc_class_dE(int c, double J, double h)
 {
@@ -249,7 +282,7 @@ static void orc_visit(int8_t *s, int L, int Ld, int bx, int by, int k,
                       const uint64_t A[10], uint32_t key0, uint32_t key1,
                       uint64_t np, uint32_t d, int time_mode,
                       double *esum, uint64_t *hash, int64_t *flips,
-                      int64_t *steps)
+                      int64_t *steps, const double *grad, double *score)
 {
     const int x0 = bx * Ld, y0 = by * Ld, nd = Ld * Ld;
     /* frozen halo, collected before the domain process runs */
@@ -285,6 +318,18 @@ static void orc_visit(int8_t *s, int L, int Ld, int bx, int by, int k,
         }
         uint64_t R = 0;
         for (int c = 0; c < 10; ++c) R += n[c] * A[c];
+        /* likelihood-ratio score of this step: the step's probability is
+         * a_c/n_d for a real flip of a class-c site and 1 - R/n_d for a null
+         * step, R = sum_c n_c a_c (real-valued acceptances) */
+        double Rr = 0.0, Db = 0.0, Dh = 0.0;
+        if (grad) {
+            for (int c = 0; c < 10; ++c) {
+                double w = (double)n[c] * grad[c];
+                Rr += w;
+                Db += w * grad[10 + c];
+                Dh += w * grad[20 + c];
+            }
+        }
 
         uint32_t ctr[4] = {(uint32_t)j, d, (uint32_t)np,
                            (uint32_t)((np >> 32) & 0xFFFFFFu) | (ORC_TAG_STEP << 24)};
@@ -296,7 +341,13 @@ static void orc_visit(int8_t *s, int L, int Ld, int bx, int by, int k,
         if (time_mode == ORC_TIME_EXPONENTIAL)
             *esum += -log(ldexp((double)V, -53));
         *steps += 1;
-        if (target >= R) continue; /* null step */
+        if (target >= R) { /* null step */
+            if (grad) {
+                score[0] -= Db / ((double)nd - Rr);
+                score[1] -= Dh / ((double)nd - Rr);
+            }
+            continue;
+        }
 
         uint64_t C = 0;
         int c = 0;
@@ -304,6 +355,10 @@ static void orc_visit(int8_t *s, int L, int Ld, int bx, int by, int k,
             uint64_t w_c = n[c] * A[c];
             if (target < C + w_c) break;
             C += w_c;
+        }
+        if (grad) {
+            score[0] += grad[10 + c];
+            score[1] += grad[20 + c];
         }
         uint64_t jj = (target - C) / A[c];
         int site = -1;
@@ -386,11 +441,12 @@ static void orc_observe(const int8_t *s, int L, double J, double h,
  * order because they do not interact (Sec. 2.2).
  * Returns 0, or -1 for an invalid configuration.
  * ---------------------------------------------------------------------- */
-int orc_run_replica(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
-                    uint64_t seed, int schedule, int time_mode, double nu,
-                    double J, double h, int64_t sched_begin, int64_t n_sched,
-                    int obs_every, double *esum, int64_t *steps,
-                    uint64_t *hash, int64_t *flips, double *obs)
+int orc_run_replica_grad(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
+                         uint64_t seed, int schedule, int time_mode, double nu,
+                         double J, double h, int64_t sched_begin, int64_t n_sched,
+                         int obs_every, double *esum, int64_t *steps,
+                         uint64_t *hash, int64_t *flips, double *obs,
+                         const double *grad, double *score)
 {
     if (L <= 0 || Ld <= 0 || L % Ld != 0) return -1;
     int Dx = L / Ld;
@@ -414,16 +470,35 @@ int orc_run_replica(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
                 if (colour != col[p]) continue;
                 orc_visit(s, L, Ld, bx, by, k, A, key0, key1, np,
                           (uint32_t)d, time_mode, &esum[d], &hash[d],
-                          &flips[d], &steps[d]);
+                          &flips[d], &steps[d], grad,
+                          score ? &score[2 * d] : NULL);
             }
         }
         if (obs_every > 0 && obs != NULL && (nl + 1) % obs_every == 0) {
             int64_t o = (nl + 1) / obs_every - 1;
+            int width = score ? 6 : 4;
             orc_observe(s, L, J, h, time_mode, esum, steps, ND, nd, nu,
-                        &obs[4 * o]);
+                        &obs[width * o]);
+            if (score) {
+                double sb = 0.0, sh = 0.0;
+                for (int d = 0; d < ND; ++d) { sb += score[2 * d]; sh += score[2 * d + 1]; }
+                obs[width * o + 4] = sb;
+                obs[width * o + 5] = sh;
+            }
         }
     }
     return 0;
+}
+
+int orc_run_replica(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
+                    uint64_t seed, int schedule, int time_mode, double nu,
+                    double J, double h, int64_t sched_begin, int64_t n_sched,
+                    int obs_every, double *esum, int64_t *steps,
+                    uint64_t *hash, int64_t *flips, double *obs)
+{
+    return orc_run_replica_grad(s, L, Ld, k, A, seed, schedule, time_mode, nu,
+                                J, h, sched_begin, n_sched, obs_every, esum,
+                                steps, hash, flips, obs, NULL, NULL);
 }
 
 uint64_t orc_hash_basis(void) { return ORC_HASH_BASIS; }
@@ -433,10 +508,11 @@ uint64_t orc_hash_basis(void) { return ORC_HASH_BASIS; }
  * seed0 + r, starts from s0 (copied), runs n_sched schedules and writes its
  * final state to out[r*L*L ...].  Plain loop over orc_run_replica.
  * ---------------------------------------------------------------------- */
-int orc_sample_final_states(const int8_t *s0, int L, int Ld, int k,
-                            const uint64_t A[10], uint64_t seed0,
-                            int64_t n_runs, int schedule, int64_t n_sched,
-                            int8_t *out)
+int orc_sample_final_states_grad(const int8_t *s0, int L, int Ld, int k,
+                                 const uint64_t A[10], uint64_t seed0,
+                                 int64_t n_runs, int schedule, int64_t n_sched,
+                                 int8_t *out, const double *grad,
+                                 double *score_out)
 {
     int Dx = (Ld > 0) ? L / Ld : 0;
     int ND = Dx * Dx;
@@ -445,14 +521,32 @@ int orc_sample_final_states(const int8_t *s0, int L, int Ld, int k,
     int64_t *steps = (int64_t *)calloc((size_t)ND, sizeof(int64_t));
     uint64_t *hash = (uint64_t *)calloc((size_t)ND, sizeof(uint64_t));
     int64_t *flips = (int64_t *)calloc((size_t)ND, sizeof(int64_t));
+    double *score = (double *)calloc((size_t)ND * 2, sizeof(double));
     int rc = 0;
     for (int64_t r = 0; r < n_runs && rc == 0; ++r) {
         int8_t *s = out + r * (int64_t)L * L;
         memcpy(s, s0, (size_t)L * L);
-        rc = orc_run_replica(s, L, Ld, k, A, seed0 + (uint64_t)r, schedule,
-                             ORC_TIME_EXPECTED, 1.0, 1.0, 0.0, 0, n_sched, 0,
-                             esum, steps, hash, flips, NULL);
+        memset(score, 0, sizeof(double) * (size_t)ND * 2);
+        rc = orc_run_replica_grad(s, L, Ld, k, A, seed0 + (uint64_t)r,
+                                  schedule, ORC_TIME_EXPECTED, 1.0, 1.0, 0.0,
+                                  0, n_sched, 0, esum, steps, hash, flips,
+                                  NULL, grad, grad ? score : NULL);
+        if (grad && score_out) {
+            double sb = 0.0, sh = 0.0;
+            for (int d = 0; d < ND; ++d) { sb += score[2 * d]; sh += score[2 * d + 1]; }
+            score_out[2 * r] = sb;
+            score_out[2 * r + 1] = sh;
+        }
     }
-    free(esum); free(steps); free(hash); free(flips);
+    free(esum); free(steps); free(hash); free(flips); free(score);
     return rc;
+}
+
+int orc_sample_final_states(const int8_t *s0, int L, int Ld, int k,
+                            const uint64_t A[10], uint64_t seed0,
+                            int64_t n_runs, int schedule, int64_t n_sched,
+                            int8_t *out)
+{
+    return orc_sample_final_states_grad(s0, L, Ld, k, A, seed0, n_runs,
+                                        schedule, n_sched, out, NULL, NULL);
 }

@@ -83,6 +83,13 @@ def lib():
                                               u64p, ctypes.c_uint64, ctypes.c_int64,
                                               ctypes.c_int, ctypes.c_int64, i8p]
         L.orc_sample_final_states.restype = ctypes.c_int
+        L.orc_score_table.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, dp]
+        L.orc_score_table.restype = ctypes.c_int
+        L.orc_run_replica_grad.argtypes = L.orc_run_replica.argtypes + [dp, dp]
+        L.orc_run_replica_grad.restype = ctypes.c_int
+        L.orc_sample_final_states_grad.argtypes = L.orc_sample_final_states.argtypes + [dp, dp]
+        L.orc_sample_final_states_grad.restype = ctypes.c_int
         L.orc_hash_basis.argtypes = []
         L.orc_hash_basis.restype = ctypes.c_uint64
         _lib = L
@@ -140,6 +147,33 @@ def energy_mag(s: np.ndarray):
     return b.value, m.value
 
 
+def score_table(J: float, beta: float, h: float, law: int) -> np.ndarray:
+    """[a_c (10), dlog a_c/dbeta (10), dlog a_c/dh (10)]."""
+    g = np.zeros(30, dtype=np.float64)
+    if lib().orc_score_table(J, beta, h, law, _ptr(g, ctypes.c_double)) != 0:
+        raise ValueError("bad rate law")
+    return g
+
+
+def sample_final_states_with_score(s0: np.ndarray, Ld: int, k: int, A: np.ndarray, grad: np.ndarray,
+                                   seed0: int, n_runs: int, n_sched: int,
+                                   schedule: int = SCHED_PALINDROME):
+    """Final states and path scores d log P / d(beta, h) of n_runs independent runs."""
+    s0 = np.ascontiguousarray(s0, dtype=np.int8)
+    L = s0.shape[0]
+    A = np.ascontiguousarray(A, dtype=np.uint64)
+    grad = np.ascontiguousarray(grad, dtype=np.float64)
+    out = np.zeros((n_runs, L, L), dtype=np.int8)
+    score = np.zeros((n_runs, 2), dtype=np.float64)
+    rc = lib().orc_sample_final_states_grad(_ptr(s0, ctypes.c_int8), L, Ld, k,
+                                            _ptr(A, ctypes.c_uint64), seed0, n_runs, schedule,
+                                            n_sched, _ptr(out, ctypes.c_int8),
+                                            _ptr(grad, ctypes.c_double), _ptr(score, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle rejected the configuration")
+    return out, score
+
+
 def sample_final_states(s0: np.ndarray, Ld: int, k: int, A: np.ndarray, seed0: int,
                         n_runs: int, n_sched: int, schedule: int = SCHED_PALINDROME):
     """Final states of n_runs independent runs (seeds seed0..seed0+n_runs-1) from s0."""
@@ -174,6 +208,8 @@ class Replica:
     hash: np.ndarray = field(default=None)
     flips: np.ndarray = field(default=None)
     sched_done: int = 0
+    grad: np.ndarray = field(default=None)
+    score: np.ndarray = field(default=None)
 
     def __post_init__(self):
         if self.spins is None:
@@ -190,19 +226,28 @@ class Replica:
     def n_domains(self) -> int:
         return (self.L // self.Ld) ** 2
 
+    def enable_score(self):
+        """Accumulate the likelihood-ratio score per domain from now on."""
+        self.grad = score_table(self.J, self.beta, self.h, self.law)
+        self.score = np.zeros((self.n_domains, 2), dtype=np.float64)
+
     def run(self, n_sched: int, schedule: int = SCHED_PALINDROME,
             time_mode: int = TIME_EXPONENTIAL, obs_every: int = 0) -> np.ndarray:
         n_obs = n_sched // obs_every if obs_every > 0 else 0
-        obs = np.zeros((max(n_obs, 1), 4), dtype=np.float64)
+        with_score = getattr(self, "score", None) is not None
+        width = 6 if with_score else 4
+        obs = np.zeros((max(n_obs, 1), width), dtype=np.float64)
         s = np.ascontiguousarray(self.spins.reshape(-1))
         A = np.ascontiguousarray(self.A)
-        rc = lib().orc_run_replica(
+        gptr = _ptr(self.grad, ctypes.c_double) if with_score else None
+        sptr = _ptr(self.score, ctypes.c_double) if with_score else None
+        rc = lib().orc_run_replica_grad(
             _ptr(s, ctypes.c_int8), self.L, self.Ld, self.k, _ptr(A, ctypes.c_uint64),
             self.seed, schedule, time_mode, self.nu, self.J, self.h,
             self.sched_done, n_sched, obs_every,
             _ptr(self.esum, ctypes.c_double), _ptr(self.steps, ctypes.c_int64),
             _ptr(self.hash, ctypes.c_uint64), _ptr(self.flips, ctypes.c_int64),
-            _ptr(obs, ctypes.c_double))
+            _ptr(obs, ctypes.c_double), gptr, sptr)
         if rc != 0:
             raise ValueError("oracle rejected the configuration")
         self.spins = s.reshape(self.L, self.L)

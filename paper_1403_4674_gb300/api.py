@@ -113,6 +113,13 @@ def kmc_grad(ctx, score_dev: torch.Tensor, reset: int = 0):
     _check(ctx, load().kmc_grad(ctx, ctypes.c_void_p(score_dev.data_ptr()), reset))
 
 
+def kmc_lr_estimate(ctx, A_dev: torch.Tensor, grad_dev: torch.Tensor, stream=None):
+    if A_dev.dtype != torch.float64 or grad_dev.dtype != torch.float64 or not A_dev.is_cuda:
+        raise KmcError(-1, "A_dev and grad_dev must be float64 CUDA tensors")
+    _check(ctx, load().kmc_lr_estimate(ctx, ctypes.c_void_p(A_dev.data_ptr()),
+                                       ctypes.c_void_p(grad_dev.data_ptr())))
+
+
 def kmc_enable_grad(ctx, enable: bool):
     _check(ctx, load().kmc_enable_grad(ctx, int(bool(enable))))
 
@@ -244,6 +251,12 @@ class Lattice:
     def score(self, reset: bool = False) -> torch.Tensor:
         out = torch.empty((self.n_replicas, 2), dtype=torch.float64, device=self.spins.device)
         kmc_grad(self.ctx, out, int(reset))
+        return out
+
+    def lr_estimate(self, A: torch.Tensor) -> torch.Tensor:
+        """d E[A] / d(beta, h) from per-replica A and the accumulated scores."""
+        out = torch.empty(2, dtype=torch.float64, device=self.spins.device)
+        kmc_lr_estimate(self.ctx, A.contiguous(), out)
         return out
 
     def reset(self, init: int = KMC_INIT_RANDOM, stream=None):

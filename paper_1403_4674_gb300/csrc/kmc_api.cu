@@ -1295,6 +1295,17 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     return KMC_OK;
 }
 
+kmc_status kmc_lr_estimate(kmc_ctx *c, const double *A_dev, double *grad_dev)
+{
+    if (!c) return KMC_EINVAL;
+    if (!A_dev || !grad_dev) return fail(c, KMC_EINVAL, "A_dev and grad_dev required");
+    if (c->n_rep < 2) return fail(c, KMC_EINVAL, "the estimate needs at least two replicas");
+    lr_estimate_kernel<<<1, 256, 0, c->stream>>>(A_dev, c->d_dctr, c->d_dom_off, c->n_rep, grad_dev);
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    return KMC_OK;
+}
+
 kmc_status kmc_profile(kmc_ctx *c, int32_t enable)
 {
     if (!c) return KMC_EINVAL;

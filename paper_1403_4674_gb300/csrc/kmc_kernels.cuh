@@ -1249,4 +1249,48 @@ __global__ void score_reduce_kernel(const uint64_t *dctr, const uint32_t *rep_do
     score[2 * r + 1] = sh;
 }
 
+// Likelihood-ratio estimate of d E[A]/d theta over the replicas: out[j] =
+// (1/R) sum_r (A_r - mean A) S_r,j, j = beta, h; one block, fixed order.
+__global__ void lr_estimate_kernel(const double *A, const uint64_t *dctr, const uint32_t *rep_dom_off, int n_rep,
+                                   double *out)
+{
+    __shared__ double red[3][256];
+    const int t = threadIdx.x;
+    double a = 0.0;
+    for (int r = t; r < n_rep; r += blockDim.x) a += A[r];
+    red[0][t] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w) red[0][t] += red[0][t + w];
+        __syncthreads();
+    }
+    const double mean = red[0][0] / (double)n_rep;
+    __syncthreads();
+    double sb = 0.0, sh = 0.0;
+    for (int r = t; r < n_rep; r += blockDim.x) {
+        double xb = 0.0, xh = 0.0;
+        for (uint32_t g = rep_dom_off[r]; g < rep_dom_off[r + 1]; ++g) {
+            xb += __longlong_as_double((long long)dctr[(uint64_t)g * DCTR_WORDS + DCTR_SB]);
+            xh += __longlong_as_double((long long)dctr[(uint64_t)g * DCTR_WORDS + DCTR_SH]);
+        }
+        const double c = A[r] - mean;
+        sb += c * xb;
+        sh += c * xh;
+    }
+    red[1][t] = sb;
+    red[2][t] = sh;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            red[1][t] += red[1][t + w];
+            red[2][t] += red[2][t + w];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        out[0] = red[1][0] / (double)n_rep;
+        out[1] = red[2][0] / (double)n_rep;
+    }
+}
+
 } // namespace kmcdev

@@ -1,0 +1,121 @@
+"""Likelihood-ratio gradients on the GPU.
+
+The run kernel's GRAD variant accumulates the path score d log P / d(beta, h)
+(App. A: step probabilities a_c/n_d and 1 - R/n_d) per domain.  Checked
+against the oracle's score (tests/test_oracle_score.py pins the oracle to the
+exact derivative of the enumerated chain), against common-random-number finite
+differences, and through the torch.autograd wrapper.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
+@pytest.mark.parametrize("Ld,k", [(16, 4), (32, 16), (8, 40)])
+def test_score_parity_with_oracle(law, Ld, k):
+    import paper_1403_4674_gb300 as kmc
+    L = [4 * Ld, 6 * Ld]
+    seeds, beta, h = [21, 22], [0.45, 0.4], [0.1, -0.05]
+    lat = kmc.Lattice(L, Ld, k, seeds)
+    lat.enable_grad(True)
+    lat.set_rates(beta, h, law=law)
+    obs = lat.run(6, obs_every=2).cpu().numpy()
+    score = lat.score().cpu().numpy()
+    for r in range(2):
+        ref = orc.Replica(L=L[r], Ld=Ld, k=k, seed=seeds[r], beta=beta[r], h=h[r], law=law)
+        ref.enable_score()
+        robs = ref.run(6, obs_every=2)
+        # the score does not change the trajectory
+        assert np.array_equal(lat.replica_spins(r).cpu().numpy(), ref.spins)
+        assert np.array_equal(obs[:, r, :3], robs[:, :3])
+        scale = 1.0 + np.abs(robs[:, 4:6])
+        assert np.all(np.abs(obs[:, r, 4:6] - robs[:, 4:6]) <= 1e-9 * scale), (obs[:, r, 4:6], robs[:, 4:6])
+        np.testing.assert_allclose(score[r], ref.score.sum(axis=0), rtol=1e-9, atol=1e-9)
+    lat.close()
+
+
+def test_score_reset_starts_a_new_segment():
+    import paper_1403_4674_gb300 as kmc
+    lat = kmc.Lattice([64], 16, 4, [5])
+    lat.enable_grad(True)
+    lat.set_rates([0.44], [0.02])
+    lat.run(3)
+    first = lat.score(reset=True).cpu().numpy()
+    assert np.all(first != 0)
+    assert np.all(lat.score().cpu().numpy() == 0)
+    lat.run(2)
+    ref = orc.Replica(L=64, Ld=16, k=4, seed=5, beta=0.44, h=0.02)
+    ref.run(3)
+    ref.enable_score()
+    ref.run(2)
+    np.testing.assert_allclose(lat.score().cpu().numpy()[0], ref.score.sum(axis=0), rtol=1e-9, atol=1e-9)
+    lat.close()
+
+
+def _final_obs(L, Ld, k, seeds, beta, h, n, grad, col):
+    import paper_1403_4674_gb300 as kmc
+    lat = kmc.Lattice(L, Ld, k, seeds, init=kmc.KMC_INIT_ALL_UP)
+    lat.enable_grad(grad)
+    nrep = len(L)
+    lat.set_rates([beta] * nrep, [h] * nrep)
+    obs = lat.run(n, obs_every=n)
+    A = obs[-1, :, col].contiguous()
+    out = (A.cpu().numpy(), lat.lr_estimate(A).cpu().numpy() if grad else None,
+           lat.score().cpu().numpy() if grad else None)
+    lat.close()
+    return out
+
+
+@pytest.mark.parametrize("param,col", [("beta", 0), ("beta", 1), ("h", 1)])
+def test_lr_gradient_matches_crn_finite_difference(param, col):
+    """d E[A]/d theta: likelihood ratio vs common-random-number central difference, step 1e-4.
+
+    A = e (col 0) or m (col 1); e depends on h explicitly, so the h case uses m,
+    whose whole h-dependence goes through the path distribution."""
+    R, L, Ld, k, n = 4096, 16, 8, 4, 3
+    beta, h, d = 1 / 2.4, 0.02, 1e-4
+    seeds = list(range(1000, 1000 + R))
+    A, lr, S = _final_obs([L] * R, Ld, k, seeds, beta, h, n, True, col)
+    j = 0 if param == "beta" else 1
+    x = (A - A.mean()) * S[:, j]
+    se_lr = x.std(ddof=1) / math.sqrt(R)
+    assert lr[j] == pytest.approx(x.mean(), rel=1e-9, abs=1e-12)
+    bp, hp = (beta + d, h) if j == 0 else (beta, h + d)
+    bm, hm = (beta - d, h) if j == 0 else (beta, h - d)
+    Ap, _, _ = _final_obs([L] * R, Ld, k, seeds, bp, hp, n, False, col)
+    Am, _, _ = _final_obs([L] * R, Ld, k, seeds, bm, hm, n, False, col)
+    diff = (Ap - Am) / (2 * d)
+    fd, se_fd = diff.mean(), diff.std(ddof=1) / math.sqrt(R)
+    assert abs(lr[j] - fd) < 5 * math.hypot(se_lr, se_fd), (lr[j], se_lr, fd, se_fd)
+
+
+def test_autograd_function_backward():
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300.autograd import expectation
+    lat = kmc.Lattice([32] * 1024, 8, 4, list(range(7, 7 + 1024)))
+    beta = torch.tensor(0.42, dtype=torch.float64, requires_grad=True)
+    h = torch.tensor(0.05, dtype=torch.float64, requires_grad=True)
+    e = expectation(lat, beta, h, n_schedules=4, observable="e")
+    e.backward()
+    assert torch.isfinite(beta.grad) and torch.isfinite(h.grad)
+    # raising beta lowers the energy reached from a random start; raising h
+    # lowers it through the path and through the explicit -h*m term
+    assert beta.grad.item() < 0
+    assert h.grad.item() < 0
+    m = expectation(lat, beta.detach().requires_grad_(), h.detach().requires_grad_(), 4, "m")
+    assert torch.isfinite(m)
+    lat.close()

@@ -1,0 +1,115 @@
+"""Pins of the oracle's likelihood-ratio score (path gradient).
+
+The score of a path is d log P(path) / d theta for theta = (beta, h); the
+paper's transition matrices (Sec. 2.2, App. A) make P(path) explicit: each
+uniformised step has probability a_c/n_d (real flip of a class-c site) or
+1 - R/n_d (null step).  Pinned by: finite differences of the rate table,
+E[score] = 0, and E[A * score] against the exact forward-mode derivative
+d E[A] / d theta of the enumerated distribution.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from oracle.enumerate import Enumerator
+from oracle.exact_ising import lattice_energy_all_states
+
+PAL = [0, 1, 2, 3, 3, 2, 1, 0]
+
+
+@pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
+@pytest.mark.parametrize("beta,h", [(0.4, 0.1), (1 / 2.4, 0.02), (0.8, -0.3)])
+def test_score_table_is_derivative_of_log_rate(law, beta, h):
+    g = orc.score_table(1.0, beta, h, law)
+    a, _ = orc.rate_table(1.0, beta, h, law, 8)
+    assert np.array_equal(g[:10], a)
+    d = 1e-6
+    for c in range(10):
+        if law == orc.RATE_METROPOLIS and orc.class_dE(c, 1.0, h) <= 0:
+            assert g[10 + c] == 0 and g[20 + c] == 0
+            continue
+        fb = (math.log(orc.rate_table(1.0, beta + d, h, law, 8)[0][c])
+              - math.log(orc.rate_table(1.0, beta - d, h, law, 8)[0][c])) / (2 * d)
+        fh = (math.log(orc.rate_table(1.0, beta, h + d, law, 8)[0][c])
+              - math.log(orc.rate_table(1.0, beta, h - d, law, 8)[0][c])) / (2 * d)
+        assert g[10 + c] == pytest.approx(fb, rel=1e-7, abs=1e-9)
+        assert g[20 + c] == pytest.approx(fh, rel=1e-7, abs=1e-9)
+
+
+def _indices(states):
+    flat = (states.reshape(len(states), -1) > 0).astype(np.int64)
+    return (flat << np.arange(flat.shape[1])).sum(axis=1)
+
+
+@pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
+def test_lr_estimator_matches_exact_derivative(law):
+    """E[A S] = d E[A] / d theta on a 2x2 lattice after one palindromic schedule."""
+    L, Ld, k, beta, h = 2, 1, 2, 0.5, 0.3
+    E = Enumerator(L, Ld, k, beta=beta, h=h, law=law, quantised=False)
+    g = orc.score_table(1.0, beta, h, law)
+    E.set_score_table(g)
+    _, A = orc.rate_table(1.0, beta, h, law, 0)
+    s0 = np.ones((L, L), dtype=np.int8)
+    s0[0, 1] = -1
+    p0 = np.zeros(E.S)
+    p0[_indices(s0[None])[0]] = 1.0
+    p, (dpb, dph) = E.schedule_deriv(PAL, p0, (np.zeros(E.S), np.zeros(E.S)))
+    H, mag = lattice_energy_all_states(L, 1.0, h)
+    n = 200000
+    fs, score = orc.sample_final_states_with_score(s0, Ld, k, A, g, 31337, n, 1)
+    idx = _indices(fs)
+    for obs in (H.astype(float), mag.astype(float)):
+        exact_b = float(obs @ dpb)
+        exact_h = float(obs @ dph)
+        a = obs[idx]
+        c = a - a.mean()
+        for j, exact in ((0, exact_b), (1, exact_h)):
+            x = c * score[:, j]
+            est, se = x.mean(), x.std(ddof=1) / math.sqrt(n)
+            assert abs(est - exact) < 5 * se + 1e-3 * abs(exact), (j, est, se, exact)
+    # the score of every parameter has mean zero
+    for j in range(2):
+        assert abs(score[:, j].mean()) < 5 * score[:, j].std(ddof=1) / math.sqrt(n)
+
+
+def test_lr_estimator_4x4_two_domains_per_side():
+    L, Ld, k, beta, h = 4, 2, 3, 0.45, 0.15
+    law = orc.RATE_METROPOLIS
+    E = Enumerator(L, Ld, k, beta=beta, h=h, law=law, quantised=False)
+    g = orc.score_table(1.0, beta, h, law)
+    E.set_score_table(g)
+    _, A = orc.rate_table(1.0, beta, h, law, 2)
+    s0 = orc.init_spins(L, orc.INIT_RANDOM, 5)
+    p0 = np.zeros(E.S)
+    p0[_indices(s0[None])[0]] = 1.0
+    p, (dpb, dph) = E.schedule_deriv(PAL, p0, (np.zeros(E.S), np.zeros(E.S)))
+    H, mag = lattice_energy_all_states(L, 1.0, h)
+    n = 100000
+    fs, score = orc.sample_final_states_with_score(s0, Ld, k, A, g, 777, n, 1)
+    a = H.astype(float)[_indices(fs)]
+    c = a - a.mean()
+    for j, dp in ((0, dpb), (1, dph)):
+        exact = float(H.astype(float) @ dp)
+        x = c * score[:, j]
+        est, se = x.mean(), x.std(ddof=1) / math.sqrt(n)
+        assert abs(est - exact) < 5 * se + 1e-3 * abs(exact), (j, est, se, exact)
+
+
+def test_derivative_enumeration_matches_finite_difference():
+    """The forward-mode derivative itself against a central difference in beta and h."""
+    L, Ld, k, beta, h = 2, 1, 2, 0.5, 0.3
+    s0 = np.ones((L, L), dtype=np.int8)
+    p0 = np.zeros(16)
+    p0[_indices(s0[None])[0]] = 1.0
+    E = Enumerator(L, Ld, k, beta=beta, h=h, quantised=False)
+    E.set_score_table(orc.score_table(1.0, beta, h, 0))
+    _, (dpb, dph) = E.schedule_deriv(PAL, p0, (np.zeros(16), np.zeros(16)))
+    d = 1e-6
+    fd_b = (Enumerator(L, Ld, k, beta=beta + d, h=h, quantised=False).schedule(PAL, p0)
+            - Enumerator(L, Ld, k, beta=beta - d, h=h, quantised=False).schedule(PAL, p0)) / (2 * d)
+    fd_h = (Enumerator(L, Ld, k, beta=beta, h=h + d, quantised=False).schedule(PAL, p0)
+            - Enumerator(L, Ld, k, beta=beta, h=h - d, quantised=False).schedule(PAL, p0)) / (2 * d)
+    assert np.max(np.abs(dpb - fd_b)) < 1e-7
+    assert np.max(np.abs(dph - fd_h)) < 1e-7
