@@ -4,9 +4,10 @@
 Default workload (one bench step = the whole configuration):
   1024x1024 periodic 2D Ising, J=1, h=0, L_d=32 (32x32 domains, 4 colours),
   T in {1.5, 2.269, 3.0}, random and all-up starts, k in {1, 4, 16} steps per
-  domain visit, 1e4 palindromic schedules per run, energy/magnetisation every
-  10 schedules.  The three temperatures of one (k, start) run as one batch of
-  three replicas, so a step is six runs = 18 lattice trajectories.
+  domain visit, 1e4 palindromic schedules, energy/magnetisation every 10
+  schedules.  All 18 trajectories (T x start x k) are replicas of one context
+  with per-replica k and start, so a step is one run-kernel launch; its launch
+  plan is measured and chosen before the timed region.
 
 An event is one uniformised domain step (the unit k counts); real flips are
 reported beside it.  `value` times the device work with inputs resident in
@@ -15,8 +16,12 @@ times the same work through the public API with host buffers: pinned host ->
 device copy of the initial spins, the run, device -> host copy of the final
 spins and observables.
 
+`variants` adds, at N = 1, the batched configuration (512 uneven replicas,
+domain side, k and plan autotuned per group, one CUDA graph per step) and
+the gradient configuration (256 x 256^2 with likelihood-ratio scores).
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload ising1024|ising8192|batched]
+                    [--workload ising1024|ising8192] [--no-variants]
 """
 from __future__ import annotations
 
@@ -42,48 +47,33 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ising1024", choices=["ising1024", "ising8192", "batched"])
+    ap.add_argument("--workload", default="ising1024", choices=["ising1024", "ising8192"])
     ap.add_argument("--schedules", type=int, default=0, help="override schedules per run (0 = workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the batched and gradient variants")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------------------
-# workloads: list of runs (L list, L_d, k, betas, hs, seeds, init, schedules, obs_every)
+# workloads
 # ---------------------------------------------------------------------------
-def workload_runs(name: str, rank: int, sched_override: int):
+def main_workload(name: str, rank: int, sched_override: int):
+    """The timed workload of the JSON line (one context, one run-kernel launch per step)."""
     from paper_1403_4674_gb300 import workloads as wl
-    runs = []
     if name == "ising1024":
-        Ts = [1.5, 2.269, 3.0]
-        for k in (1, 4, 16):
-            seeds = wl.replica_seeds(1024 * 1000 + 17 * k + 7919 * rank, 3)
-            for init in (0, 1):
-                runs.append(dict(L=[1024] * 3, Ld=32, k=k, beta=[1 / T for T in Ts], h=[0.0] * 3,
-                                 seeds=seeds, init=init, schedules=10000, obs_every=10))
+        w = wl.ising1024_all(seed_master=1024 + 7919 * rank)
         desc = ("1024x1024 periodic Ising, J=1, h=0, L_d=32, T in {1.5,2.269,3.0} x {random, all-up} "
-                "x k in {1,4,16}, 1e4 palindromic schedules per run, obs every 10")
+                "x k in {1,4,16} (18 replicas in one launch), 1e4 palindromic schedules, obs every 10")
     elif name == "ising8192":
         w = wl.lattice_8192(seed=8192 + rank)
-        runs.append(dict(L=w.L, Ld=w.L_d, k=w.k, beta=w.beta, h=w.h, seeds=w.seeds, init=0,
-                         schedules=w.schedules, obs_every=0))
         desc = "8192x8192 periodic Ising, T=2.269, h=0.01, L_d=64, k=8, 2000 palindromic schedules"
     else:
-        w = wl.batched_replicas(512, master=512 + rank)
-        runs.append(dict(L=w.L, Ld=w.L_d, k=w.k, beta=w.beta, h=w.h, seeds=w.seeds, init=0,
-                         schedules=200, obs_every=10))
-        desc = ("512 replicas, L=16*round(exp(U[ln32,ln512])/16), T~U[1.5,3.5], h~U[-0.1,0.1], "
-                "L_d=8, k=8, 200 palindromic schedules, obs every 10")
+        raise ValueError(name)
     if sched_override > 0:
-        for r in runs:
-            r["schedules"] = sched_override
+        w.schedules = sched_override
         desc += " (schedules overridden to %d)" % sched_override
-    return runs, desc
-
-
-def run_events(run) -> int:
-    return int(sum(2 * (L // run["Ld"]) ** 2 * run["k"] for L in run["L"]) * run["schedules"])
+    return w, desc
 
 
 def visit_bytes(Ld: int, k: int) -> int:
@@ -93,9 +83,9 @@ def visit_bytes(Ld: int, k: int) -> int:
     return (Ld + 2) ** 2 - 4 + 32 * k + 4 * Ld
 
 
-def run_algorithmic_bytes(run) -> int:
-    visits = sum(2 * (L // run["Ld"]) ** 2 for L in run["L"]) * run["schedules"]
-    return visits * visit_bytes(run["Ld"], run["k"])
+def schedule_bytes(L, Ld: int, ks) -> int:
+    """Algorithmic bytes of one palindromic schedule (two visits per domain)."""
+    return int(sum(2 * (x // Ld) ** 2 * visit_bytes(Ld, k) for x, k in zip(L, ks)))
 
 
 # ---------------------------------------------------------------------------
@@ -152,22 +142,22 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # oracle CPU baseline (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
-def oracle_sample(runs, budget_s: float):
+def oracle_sample(w, budget_s: float):
     """Time the CPU oracle, single-threaded, on a bounded sample: for each
-    distinct k, replica 0 of the random-start run for as many schedules as fit
-    in budget_s / (#k values).  Returns (events/s, description, events, seconds)."""
+    distinct k, the first random-start replica of that k for as many schedules
+    as fit in budget_s / (#k values).  Returns (events/s, description, events, seconds)."""
     from oracle import oracle as orc
     by_k = {}
-    for r in runs:
-        if r["init"] == 0 and r["k"] not in by_k:
-            by_k[r["k"]] = r
+    for r in range(len(w.L)):
+        if w.init_of(r) == 0 and w.k_of(r) not in by_k:
+            by_k[w.k_of(r)] = r
     per = budget_s / max(1, len(by_k))
     ev = 0
     secs = 0.0
     parts = []
     for k, r in sorted(by_k.items()):
-        L, Ld = r["L"][0], r["Ld"]
-        rep = orc.Replica(L=L, Ld=Ld, k=k, seed=r["seeds"][0], beta=r["beta"][0], h=r["h"][0])
+        L, Ld = w.L[r], w.L_d
+        rep = orc.Replica(L=L, Ld=Ld, k=k, seed=w.seeds[r], beta=w.beta[r], h=w.h[r])
         steps_per_sched = 2 * (L // Ld) ** 2 * k
         t0 = time.perf_counter()
         rep.run(1)
@@ -178,7 +168,7 @@ def oracle_sample(runs, budget_s: float):
         dt = time.perf_counter() - t0
         ev += n * steps_per_sched
         secs += dt
-        parts.append("L=%d k=%d T=%.4g: %d schedules" % (L, k, 1 / r["beta"][0], n))
+        parts.append("L=%d k=%d T=%.4g: %d schedules" % (L, k, 1 / w.beta[r], n))
     return ev / secs, "; ".join(parts), ev, secs
 
 
@@ -186,16 +176,16 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    runs, desc = workload_runs(args.workload, 0, args.schedules)
+    w, desc = main_workload(args.workload, 0, args.schedules)
     budget = 8.0
     for _ in range(args.warmup):
-        oracle_sample(runs, 1.0)
-    vals, evs, secs = [], 0, 0.0
+        oracle_sample(w, 1.0)
+    evs, secs = 0, 0.0
+    sample = ""
     for _ in range(args.steps):
-        v, sample, e, s = oracle_sample(runs, budget)
-        vals.append(v)
+        _, sample, e, s_ = oracle_sample(w, budget)
         evs += e
-        secs += s
+        secs += s_
     value = evs / secs
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
@@ -208,9 +198,124 @@ def reference_arm(args):
     return 0
 
 
+# DRAM traffic of one run-kernel launch of the default workload, from
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (summary in
+# profiles/run_kernel_ising1024x18_traffic.md), and the SHA-256 of the kernel
+# source it was taken on; reported as null once the source has changed.
+TRAFFIC_BYTES_PER_LAUNCH = None
+TRAFFIC_KERNEL_SHA256 = None
+
+
+def kernel_source_sha256() -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1403_4674_gb300", "csrc", "kmc_kernels.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def device_time(step, steps: int, warmup: int, flush, stream):
+    """Per-step device milliseconds (CUDA events on `stream`, L2 flushed before
+    each timed step outside the event pair)."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def roofline(bytes_per_launch: float, launch_s: float, peaks: dict, traffic=None):
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_per_launch / launch_s / 1e9 if launch_s > 0 else 0.0
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+
 # ---------------------------------------------------------------------------
 # GB300 arm
 # ---------------------------------------------------------------------------
+def variant_batched(args, peaks, flush, stream):
+    """512 uneven replicas: domain side, k and launch plan per group chosen by
+    the autotuner; one CUDA graph per step (all groups concurrent)."""
+    import torch
+    from paper_1403_4674_gb300 import autotune, workloads as wl
+    w = wl.batched_replicas(512, master=512)
+    n_sched, obs_every = 200, 10
+    t0 = time.perf_counter()
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    plans = [(0, 0, 16), (1, 4, 16), (1, 16, 16), (2, sm, 16), (2, 2 * sm, 8)]
+    choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
+                                  Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=20)
+    tune_s = time.perf_counter() - t0
+    batch = autotune.Batch(w.L, w.beta, w.h, w.seeds, choices)
+    graph = batch.capture(n_sched, obs_every, reset=0)
+    ms = device_time(graph.replay, args.steps, args.warmup, flush, stream)
+    ev = batch.events_per_schedule() * n_sched
+    by = sum(schedule_bytes(lat.L, lat.L_d, lat.ks) for lat in batch.lattices) * n_sched
+    dev_s = sum(ms) / 1000.0
+    out = {"value": ev * args.steps / dev_s, "unit": UNIT, "ms_per_step": statistics.mean(ms),
+           "workload": "512 replicas, L=16*round(exp(U[ln32,ln512])/16), T~U[1.5,3.5], h~U[-0.1,0.1], "
+                       "%d palindromic schedules, obs every %d; L_d, k and plan autotuned per group; "
+                       "one CUDA graph per step" % (n_sched, obs_every),
+           "groups": [{"replicas": len(ch.replicas), "L_d": ch.L_d, "k": ch.k, "plan": list(ch.plan),
+                       "tuned_events_per_s": ch.events_per_s} for ch in choices],
+           "tune_s": tune_s, "events_per_step": ev,
+           "roofline": roofline(by, dev_s / args.steps, peaks)}
+    out["roofline"]["note"] = "step-level: the groups' run kernels overlap on concurrent streams"
+    batch.close()
+    return out
+
+
+def variant_grad(args, peaks, flush, stream):
+    """256 x 256^2 at T=2.4, h=0.02, k=8, 5000 schedules with FP64 score
+    accumulation, then LR estimates of d<e>/d(beta,h) and d<m>/d(beta,h)."""
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import autotune, workloads as wl
+    w = wl.grad_replicas(256, seed_master=256, k=8)
+    lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds, init=0)
+    lat.set_rates(w.beta, w.h)
+    lat.enable_grad(True)
+    plan, _ = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=100)
+    lat.profile(True)
+    n = w.schedules
+    out_obs = torch.empty((1, lat.n_replicas, 6), dtype=torch.float64, device="cuda")
+    grads = {}
+
+    def step():
+        lat.reset(kmc.KMC_INIT_RANDOM)
+        lat.run(n, obs_every=n, out=out_obs)
+        grads["e"] = lat.lr_estimate(out_obs[0, :, 0])
+        grads["m"] = lat.lr_estimate(out_obs[0, :, 1])
+
+    ms = device_time(step, args.steps, args.warmup, flush, stream)
+    lat.sync()
+    lat.profile_read()
+    step()
+    run_ms, run_n = lat.profile_read()
+    ev = lat.events_per_schedule() * n
+    by = schedule_bytes(lat.L, lat.L_d, lat.ks) * n
+    dev_s = sum(ms) / 1000.0
+    ge, gm = grads["e"].cpu().numpy(), grads["m"].cpu().numpy()
+    out = {"value": ev * args.steps / dev_s, "unit": UNIT, "ms_per_step": statistics.mean(ms),
+           "workload": "256 x 256^2 Ising, T=2.4, h=0.02, L_d=32, k=8, %d palindromic schedules, FP64 scores, "
+                       "LR gradients of <e> and <m> w.r.t. (beta, h) per step" % n,
+           "plan": list(plan), "launch": list(lat.launch()),
+           "lr_grad_e_beta_h": [float(ge[0]), float(ge[1])], "lr_grad_m_beta_h": [float(gm[0]), float(gm[1])],
+           "events_per_step": ev,
+           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks)}
+    lat.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -221,15 +326,16 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     # the CPU baseline runs before any CUDA work (rank 0, N = 1 only)
-    runs, desc = workload_runs(args.workload, rank, args.schedules)
+    w, desc = main_workload(args.workload, rank, args.schedules)
     cpu = None
     if world == 1 and not args.no_cpu:
-        v, sample, e, s = oracle_sample(runs, 12.0)
+        v, sample, e, s = oracle_sample(w, 12.0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%s; %d events in %.1f s, single thread" % (sample, e, s)}
 
     import torch
     import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import autotune
 
     torch.cuda.set_device(local)
     dist = None
@@ -237,129 +343,85 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
 
-    # one context and one stream per run, created outside the timed region.  The
-    # runs of a step are independent trajectories, so they are launched
-    # concurrently (longest first) and the step ends when all have finished.
-    runs.sort(key=lambda r: -r["k"])
-    for r in runs:
-        r["stream"] = torch.cuda.Stream()
-        with torch.cuda.stream(r["stream"]):
-            r["lat"] = kmc.Lattice(r["L"], r["Ld"], r["k"], r["seeds"], init=r["init"])
-            r["lat"].profile(True)
-    ctxs = {id(r): r["lat"] for r in runs}
+    # one context for the whole workload, created and tuned outside the timed region
+    ks = [w.k_of(r) for r in range(len(w.L))]
+    inits = [w.init_of(r) for r in range(len(w.L))]
+    lat = kmc.Lattice(w.L, w.L_d, ks[0], w.seeds, init=inits[0])
+    per_replica = len(set(ks)) > 1 or len(set(inits)) > 1
+    if per_replica:
+        lat.set_replica_params(k=ks, init=inits)
+    reset_mode = kmc.KMC_INIT_PER_REPLICA if per_replica else inits[0]
+    lat.reset(reset_mode)
+    lat.set_rates(w.beta, w.h)
+    t0 = time.perf_counter()
+    plan, trials = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=200 if w.L[0] <= 1024 else 2)
+    tune_s = time.perf_counter() - t0
+    lat.profile(True)
+    n_obs = w.schedules // w.obs_every if w.obs_every > 0 else 0
+    obs_buf = (torch.empty((n_obs, lat.n_replicas, 4), dtype=torch.float64, device="cuda") if n_obs > 0 else None)
 
     def step():
-        start = torch.cuda.Event()
-        start.record(stream)
-        done = []
-        for r in runs:
-            r["stream"].wait_event(start)
-            with torch.cuda.stream(r["stream"]):
-                lat = r["lat"]
-                lat.reset(r["init"])
-                lat.set_rates(r["beta"], r["h"])
-                r["obs"] = lat.run(r["schedules"], obs_every=r["obs_every"])
-                ev = torch.cuda.Event()
-                ev.record(r["stream"])
-                done.append(ev)
-        for ev in done:
-            stream.wait_event(ev)
+        lat.reset(reset_mode)
+        lat.run(w.schedules, obs_every=w.obs_every, out=obs_buf)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    for lat in ctxs.values():
-        lat.profile_read()  # discard warm-up timings
-    launches0 = sum(lat.kernel_launches() for lat in ctxs.values())
+    lat.profile_read()  # discard warm-up timings
+    launches0 = lat.kernel_launches()
 
     clocks = ClockSampler(local)
     clocks.start()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms = []
     t_wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # L2 flush between timed steps (outside the event pair)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+    step_ms = device_time(step, args.steps, 0, flush, stream)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    launches = sum(lat.kernel_launches() for lat in ctxs.values()) - launches0
+    launches = lat.kernel_launches() - launches0
+    run_ms, run_n = lat.profile_read()
 
-    for r in runs:
-        with torch.cuda.stream(r["stream"]):
-            r["lat"].sync()
-    run_ms, run_n = 0.0, 0
-    for lat in ctxs.values():
-        ms, n = lat.profile_read()
-        run_ms += ms
-        run_n += n
-
-    events_step = sum(run_events(r) for r in runs)
-    bytes_step = sum(run_algorithmic_bytes(r) for r in runs)
+    events_step = lat.events_per_schedule() * w.schedules
+    bytes_step = schedule_bytes(lat.L, lat.L_d, lat.ks) * w.schedules
     dev_s = sum(step_ms) / 1000.0
     if dist is not None:
         t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dev_s = float(t.item())
     value = events_step * args.steps * world / dev_s
-
-    # real flips of the last step (reported beside events)
-    flips = 0
-    for r in runs:
-        with torch.cuda.stream(r["stream"]):
-            flips += int(r["lat"].observables()["flips"].sum())
+    flips = int(lat.observables()["flips"].sum())
 
     # end-to-end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        host_in = {}
-        for r in runs:
-            with torch.cuda.stream(r["stream"]):
-                lat = r["lat"]
-                lat.reset(r["init"])
-                lat.sync()
-                host_in[id(r)] = lat.spins.cpu().pin_memory()
-        host_out = {id(r): torch.empty_like(host_in[id(r)]).pin_memory() for r in runs}
-        h2d = sum(host_in[id(r)].numel() for r in runs)
-        d2h = 0
+        lat.reset(reset_mode)
+        lat.sync()
+        host_in = lat.spins.cpu().pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        host_obs = torch.empty(obs_buf.shape, dtype=torch.float64).pin_memory() if obs_buf is not None else None
+        d2h = host_out.numel() + (host_obs.numel() * 8 if host_obs is not None else 0)
 
         def e2e_step():
-            """Host buffers in, public API, host buffers out; runs concurrent as above."""
-            nonlocal d2h
-            d2h = 0
-            outs = []
-            for r in runs:
-                with torch.cuda.stream(r["stream"]):
-                    lat = r["lat"]
-                    lat.spins.copy_(host_in[id(r)], non_blocking=True)
-                    lat.reset(kmc.KMC_INIT_KEEP)
-                    lat.set_rates(r["beta"], r["h"])
-                    obs = lat.run(r["schedules"], obs_every=r["obs_every"])
-                    host_out[id(r)].copy_(lat.spins, non_blocking=True)
-                    d2h += lat.spins.numel()
-                    if obs is not None:
-                        o = torch.empty(obs.shape, dtype=obs.dtype, pin_memory=True)
-                        o.copy_(obs, non_blocking=True)
-                        d2h += obs.numel() * 8
-                        outs.append(o)
+            lat.spins.copy_(host_in, non_blocking=True)
+            lat.reset(kmc.KMC_INIT_KEEP)
+            lat.run(w.schedules, obs_every=w.obs_every, out=obs_buf)
+            host_out.copy_(lat.spins, non_blocking=True)
+            if host_obs is not None:
+                host_obs.copy_(obs_buf, non_blocking=True)
             torch.cuda.synchronize()
-            return outs
 
         e2e_step()
-        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step()
@@ -369,28 +431,20 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         e2e = {"value": events_step * args.steps * world / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(d2h)}
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    traffic = TRAFFIC_BYTES_PER_LAUNCH if (TRAFFIC_KERNEL_SHA256 == kernel_source_sha256()
+                                           and args.workload == "ising1024" and args.schedules == 0) else None
     avg_run_s = (run_ms / 1000.0) / max(run_n, 1)
-    # The run kernels of a step overlap in time (one stream per run), so the
-    # device-level rate divides the algorithmic bytes of all of them by the
-    # step time; the per-launch rate divides one launch's bytes by its own
-    # event time.
-    achieved = (bytes_step * args.steps) / dev_s / 1e9 if dev_s > 0 else 0.0
-    per_launch = (bytes_step * args.steps) / (run_ms / 1000.0) / 1e9 if run_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "kernel": "kmcdev::run_kernel", "peak_source": peak_src,
-                "per_launch_achieved": per_launch,
-                "run_kernel_ms_avg": 1000 * avg_run_s, "run_kernel_launches": run_n,
-                "run_kernel_busy_over_step": (run_ms / 1000.0) / dev_s if dev_s > 0 else None}
+    roof = roofline(bytes_step, avg_run_s, peaks, traffic)
+    roof.update({"kernel": "kmcdev::run_kernel", "run_kernel_ms_avg": 1000 * avg_run_s,
+                 "run_kernel_launches": run_n, "algorithmic_bytes_per_launch": bytes_step,
+                 "step_level_achieved": bytes_step * args.steps / dev_s / 1e9})
+
+    variants = None
+    if world == 1 and not args.no_variants and args.workload == "ising1024":
+        variants = {"batched": variant_batched(args, peaks, flush, stream),
+                    "grad": variant_grad(args, peaks, flush, stream)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -401,15 +455,14 @@ def main():
                            "real_flips_per_step": flips,
                            "real_flips_per_s": flips * world / (dev_s / args.steps),
                            "l2": "flushed between timed steps (512 MB write outside the event pair)",
-                           "parallelism": ("replicas only" if world > 1 else "1 GPU") +
-                                          ", %d independent runs per step on concurrent streams" % len(runs),
-                           "launch": [list(lat.launch()) for lat in ctxs.values()],
+                           "parallelism": ("replicas only, %d ranks" % world if world > 1 else "1 GPU") +
+                                          ", one run-kernel launch per step",
+                           "plan": list(plan), "launch": list(lat.launch()), "tune_s": tune_s,
                            "wall_s": wall},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk}
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "variants": variants}
         print(json.dumps(line), flush=True)
-    for lat in ctxs.values():
-        lat.close()
+    lat.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

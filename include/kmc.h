@@ -50,7 +50,7 @@ typedef enum {
     KMC_EDEVICE = -6       /* device error word set (e.g. a spin not +-1) */
 } kmc_status;
 
-enum { KMC_INIT_RANDOM = 0, KMC_INIT_ALL_UP = 1, KMC_INIT_KEEP = 2 };
+enum { KMC_INIT_RANDOM = 0, KMC_INIT_ALL_UP = 1, KMC_INIT_KEEP = 2, KMC_INIT_PER_REPLICA = 3 };
 enum { KMC_RATE_METROPOLIS = 0, KMC_RATE_BARKER = 1 };
 enum {
     KMC_SCHEDULE_PALINDROME = 0,  /* 0 1 2 3 3 2 1 0: its own reverse (Eq. 10) */
@@ -58,6 +58,7 @@ enum {
     KMC_SCHEDULE_RANDOM_PERM = 2  /* uniform colour order per schedule (Eq. 10) */
 };
 enum { KMC_TIME_EXPONENTIAL = 0, KMC_TIME_EXPECTED = 1 };
+enum { KMC_OBS_SCHEDULE = 0, KMC_OBS_PASS = 1 };
 
 /*
  * kmc_create_lattice -- bind a batch of replicas and initialise them.
@@ -125,10 +126,14 @@ kmc_status kmc_set_rate_table(kmc_ctx *ctx, double J, const double *beta, const 
  *               KMC_TIME_EXPECTED: by its mean 1/Lambda_d (the paper's
  *               choice, Sec. 2.1).
  *   obs_every   if > 0 and obs_dev != NULL, after every obs_every-th
- *               schedule of this call the endpoint observables (Sec. 2.3)
+ *               schedule of this call (or colour pass, see
+ *               kmc_set_observation) the endpoint observables (Sec. 2.3)
  *               of replica r go to obs_dev[(o*n_replicas + r)*4 + {0..3}] =
  *               {e = E/N, m = M/N, e*m, T}, T = mean domain clock;
- *               o = 0 .. n_schedules/obs_every - 1.  obs_dev is a caller
+ *               o = 0 .. units/obs_every - 1, units = n_schedules, or
+ *               n_schedules times the passes per schedule (8 for the
+ *               palindrome, else 4).  With scores enabled the record has 6
+ *               doubles (summed scores d/dbeta, d/dh).  obs_dev is a caller
  *               device buffer of at least that many doubles.
  * Asynchronous; spins_dev holds the final state when the stream reaches
  * the end of the call.
@@ -136,6 +141,21 @@ kmc_status kmc_set_rate_table(kmc_ctx *ctx, double J, const double *beta, const 
 kmc_status kmc_run_schedule(kmc_ctx *ctx, int64_t n_schedules, int32_t schedule,
                             int32_t time_mode, int32_t obs_every, double *obs_dev,
                             void *stream);
+
+/*
+ * kmc_set_observation -- where kmc_run_schedule takes its records.
+ *   KMC_OBS_SCHEDULE  after every obs_every-th schedule (schedule endpoints).
+ *   KMC_OBS_PASS      after every obs_every-th colour pass: every pass ends
+ *                     the domain processes of one colour, and the schedule
+ *                     sequence read with shifted registers ends there
+ *                     (Sec. 2.3), so these are valid observation points too.
+ *                     The records are built from per-visit changes of the
+ *                     bond sum, magnetisation, clocks and scores, with no
+ *                     synchronisation between domains; same-colour passes of
+ *                     a schedule are not fused.
+ * A host-side setting; takes effect at the next kmc_run_schedule.
+ */
+kmc_status kmc_set_observation(kmc_ctx *ctx, int32_t unit);
 
 /*
  * kmc_observables -- synchronise and return the current endpoint observables
@@ -169,9 +189,28 @@ kmc_status kmc_lr_estimate(kmc_ctx *ctx, const double *A_dev, double *grad_dev);
 /* Turn score accumulation on (enable != 0) or off for following runs. */
 kmc_status kmc_enable_grad(kmc_ctx *ctx, int32_t enable);
 
-/* Re-initialise spins from the seeds (init as in kmc_create_lattice), zero
- * clocks, counters, scores and the schedule index.  Asynchronous. */
+/* Re-initialise spins from the seeds (init as in kmc_create_lattice, or
+ * KMC_INIT_PER_REPLICA for the per-replica modes of kmc_set_replica_params),
+ * zero clocks, counters, scores and the schedule index.  Asynchronous; it
+ * enqueues only device work, so it may be captured in a CUDA graph. */
 kmc_status kmc_reset(kmc_ctx *ctx, int32_t init, void *stream);
+
+/*
+ * kmc_set_replica_params -- per-replica steps per visit and start modes.
+ * The paper runs all N_TRAJ trajectories of an experiment with one N_I
+ * (Sec. 3); per-replica values let one persistent launch carry several
+ * experiments side by side (each replica's trajectory is exactly the one a
+ * context of its own would produce).
+ *   k_steps[r]  host array or NULL: steps per visit of replica r (1..65535).
+ *               Only allowed before the first run after create or reset
+ *               (the EXPECTED clock counts visits * k).
+ *   init[r]     host array or NULL: KMC_INIT_RANDOM, KMC_INIT_ALL_UP or
+ *               KMC_INIT_KEEP, used by kmc_reset(ctx, KMC_INIT_PER_REPLICA).
+ * The launch plan is rebuilt so that replicas of equal k share clusters.
+ * Synchronous on the host arrays (copied before the call returns); must not
+ * be called while the context's stream is capturing.
+ */
+kmc_status kmc_set_replica_params(kmc_ctx *ctx, const int32_t *k_steps, const int32_t *init);
 
 /* Wait for all work of the context and raise any device-side error. */
 kmc_status kmc_sync(kmc_ctx *ctx);

@@ -441,20 +441,42 @@ static void orc_observe(const int8_t *s, int L, double J, double h,
  * order because they do not interact (Sec. 2.2).
  * Returns 0, or -1 for an invalid configuration.
  * ---------------------------------------------------------------------- */
-int orc_run_replica_grad(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
-                         uint64_t seed, int schedule, int time_mode, double nu,
-                         double J, double h, int64_t sched_begin, int64_t n_sched,
-                         int obs_every, double *esum, int64_t *steps,
-                         uint64_t *hash, int64_t *flips, double *obs,
-                         const double *grad, double *score)
+static void orc_record(const int8_t *s, int L, double J, double h, int time_mode,
+                       const double *esum, const int64_t *steps, int ND, int nd,
+                       double nu, const double *score, double *rec)
+{
+    orc_observe(s, L, J, h, time_mode, esum, steps, ND, nd, nu, rec);
+    if (score) {
+        double sb = 0.0, sh = 0.0;
+        for (int d = 0; d < ND; ++d) { sb += score[2 * d]; sh += score[2 * d + 1]; }
+        rec[4] = sb;
+        rec[5] = sh;
+    }
+}
+
+/* obs_unit 0: a record after every obs_every-th schedule of the call (the
+ * schedule endpoints of Sec. 2.3); obs_unit 1: after every obs_every-th
+ * colour pass of the call.  Every colour pass ends the domain processes of
+ * one colour, so its end is a domain-process endpoint; the schedules read
+ * with shifted registers end there (Sec. 2.3), which makes these valid
+ * observation points as well. */
+int orc_run_replica_obs(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
+                        uint64_t seed, int schedule, int time_mode, double nu,
+                        double J, double h, int64_t sched_begin, int64_t n_sched,
+                        int obs_every, int obs_unit, double *esum, int64_t *steps,
+                        uint64_t *hash, int64_t *flips, double *obs,
+                        const double *grad, double *score)
 {
     if (L <= 0 || Ld <= 0 || L % Ld != 0) return -1;
     int Dx = L / Ld;
     if (Dx < 2 || (Dx & 1)) return -1;
     if (orc_log2(Ld * Ld) < 0) return -1;
     if (k < 0 || k > 65535) return -1;
+    if (obs_unit != 0 && obs_unit != 1) return -1;
     const int ND = Dx * Dx, nd = Ld * Ld;
+    const int width = score ? 6 : 4;
     uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+    int64_t passes = 0; /* colour passes completed in this call */
     for (int64_t nl = 0; nl < n_sched; ++nl) {
         uint64_t n = (uint64_t)(sched_begin + nl);
         int col[8];
@@ -473,21 +495,28 @@ int orc_run_replica_grad(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
                           &flips[d], &steps[d], grad,
                           score ? &score[2 * d] : NULL);
             }
+            ++passes;
+            if (obs_unit == 1 && obs_every > 0 && obs != NULL && passes % obs_every == 0)
+                orc_record(s, L, J, h, time_mode, esum, steps, ND, nd, nu, score,
+                           &obs[width * (passes / obs_every - 1)]);
         }
-        if (obs_every > 0 && obs != NULL && (nl + 1) % obs_every == 0) {
-            int64_t o = (nl + 1) / obs_every - 1;
-            int width = score ? 6 : 4;
-            orc_observe(s, L, J, h, time_mode, esum, steps, ND, nd, nu,
-                        &obs[width * o]);
-            if (score) {
-                double sb = 0.0, sh = 0.0;
-                for (int d = 0; d < ND; ++d) { sb += score[2 * d]; sh += score[2 * d + 1]; }
-                obs[width * o + 4] = sb;
-                obs[width * o + 5] = sh;
-            }
-        }
+        if (obs_unit == 0 && obs_every > 0 && obs != NULL && (nl + 1) % obs_every == 0)
+            orc_record(s, L, J, h, time_mode, esum, steps, ND, nd, nu, score,
+                       &obs[width * ((nl + 1) / obs_every - 1)]);
     }
     return 0;
+}
+
+int orc_run_replica_grad(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
+                         uint64_t seed, int schedule, int time_mode, double nu,
+                         double J, double h, int64_t sched_begin, int64_t n_sched,
+                         int obs_every, double *esum, int64_t *steps,
+                         uint64_t *hash, int64_t *flips, double *obs,
+                         const double *grad, double *score)
+{
+    return orc_run_replica_obs(s, L, Ld, k, A, seed, schedule, time_mode, nu, J, h,
+                               sched_begin, n_sched, obs_every, 0, esum, steps, hash,
+                               flips, obs, grad, score);
 }
 
 int orc_run_replica(int8_t *s, int L, int Ld, int k, const uint64_t A[10],

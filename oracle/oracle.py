@@ -88,6 +88,9 @@ def lib():
         L.orc_score_table.restype = ctypes.c_int
         L.orc_run_replica_grad.argtypes = L.orc_run_replica.argtypes + [dp, dp]
         L.orc_run_replica_grad.restype = ctypes.c_int
+        ra = L.orc_run_replica.argtypes
+        L.orc_run_replica_obs.argtypes = ra[:14] + [ctypes.c_int] + ra[14:] + [dp, dp]
+        L.orc_run_replica_obs.restype = ctypes.c_int
         L.orc_sample_final_states_grad.argtypes = L.orc_sample_final_states.argtypes + [dp, dp]
         L.orc_sample_final_states_grad.restype = ctypes.c_int
         L.orc_hash_basis.argtypes = []
@@ -232,8 +235,12 @@ class Replica:
         self.score = np.zeros((self.n_domains, 2), dtype=np.float64)
 
     def run(self, n_sched: int, schedule: int = SCHED_PALINDROME,
-            time_mode: int = TIME_EXPONENTIAL, obs_every: int = 0) -> np.ndarray:
-        n_obs = n_sched // obs_every if obs_every > 0 else 0
+            time_mode: int = TIME_EXPONENTIAL, obs_every: int = 0, obs_per_pass: bool = False) -> np.ndarray:
+        """Run schedules; with obs_per_pass the records are taken after every
+        obs_every-th colour pass instead of every obs_every-th schedule."""
+        passes = 8 if schedule == SCHED_PALINDROME else 4
+        units = n_sched * passes if obs_per_pass else n_sched
+        n_obs = units // obs_every if obs_every > 0 else 0
         with_score = getattr(self, "score", None) is not None
         width = 6 if with_score else 4
         obs = np.zeros((max(n_obs, 1), width), dtype=np.float64)
@@ -241,10 +248,10 @@ class Replica:
         A = np.ascontiguousarray(self.A)
         gptr = _ptr(self.grad, ctypes.c_double) if with_score else None
         sptr = _ptr(self.score, ctypes.c_double) if with_score else None
-        rc = lib().orc_run_replica_grad(
+        rc = lib().orc_run_replica_obs(
             _ptr(s, ctypes.c_int8), self.L, self.Ld, self.k, _ptr(A, ctypes.c_uint64),
             self.seed, schedule, time_mode, self.nu, self.J, self.h,
-            self.sched_done, n_sched, obs_every,
+            self.sched_done, n_sched, obs_every, 1 if obs_per_pass else 0,
             _ptr(self.esum, ctypes.c_double), _ptr(self.steps, ctypes.c_int64),
             _ptr(self.hash, ctypes.c_uint64), _ptr(self.flips, ctypes.c_int64),
             _ptr(obs, ctypes.c_double), gptr, sptr)

@@ -13,11 +13,12 @@ import torch
 
 from ._lib import KmcError, load
 
-KMC_INIT_RANDOM, KMC_INIT_ALL_UP, KMC_INIT_KEEP = 0, 1, 2
+KMC_INIT_RANDOM, KMC_INIT_ALL_UP, KMC_INIT_KEEP, KMC_INIT_PER_REPLICA = 0, 1, 2, 3
 KMC_RATE_METROPOLIS, KMC_RATE_BARKER = 0, 1
 KMC_SCHEDULE_PALINDROME, KMC_SCHEDULE_FIXED, KMC_SCHEDULE_RANDOM_PERM = 0, 1, 2
 KMC_TIME_EXPONENTIAL, KMC_TIME_EXPECTED = 0, 1
 KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID = 0, 1, 2
+KMC_OBS_SCHEDULE, KMC_OBS_PASS = 0, 1
 
 _i32, _i64, _u64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
 
@@ -128,6 +129,16 @@ def kmc_reset(ctx, init: int, stream=None):
     _check(ctx, load().kmc_reset(ctx, init, ctypes.c_void_p(_stream_handle(stream))))
 
 
+def kmc_set_replica_params(ctx, k_steps: Optional[Sequence[int]] = None, init: Optional[Sequence[int]] = None):
+    kp = ctypes.cast(_arr(k_steps, _i32), ctypes.c_void_p) if k_steps is not None else None
+    ip = ctypes.cast(_arr(init, _i32), ctypes.c_void_p) if init is not None else None
+    _check(ctx, load().kmc_set_replica_params(ctx, kp, ip))
+
+
+def kmc_set_observation(ctx, unit: int):
+    _check(ctx, load().kmc_set_observation(ctx, unit))
+
+
 def kmc_sync(ctx):
     _check(ctx, load().kmc_sync(ctx))
 
@@ -196,6 +207,7 @@ class Lattice:
         self.L = [int(x) for x in L]
         self.L_d = int(L_d)
         self.k = int(k)
+        self.ks = [self.k] * len(self.L)  # per-replica steps per visit
         self.seeds = [int(s) for s in seeds]
         total = sum(x * x for x in self.L)
         if spins is None:
@@ -206,6 +218,7 @@ class Lattice:
         self.dom_offsets = np.concatenate([[0], np.cumsum([(x // self.L_d) ** 2 for x in self.L])]).astype(np.int64)
         self.ctx = kmc_create_lattice(self.L, self.L_d, self.k, init, self.seeds, self.spins, stream)
         self.grad_enabled = False
+        self.obs_unit = KMC_OBS_SCHEDULE
 
     @property
     def n_replicas(self) -> int:
@@ -226,12 +239,23 @@ class Lattice:
         kmc_set_rates(self.ctx, J, beta.tolist(), h.tolist(), nu, law)
 
     def run(self, n_schedules: int, schedule: int = KMC_SCHEDULE_PALINDROME,
-            time_mode: int = KMC_TIME_EXPONENTIAL, obs_every: int = 0, stream=None) -> Optional[torch.Tensor]:
+            time_mode: int = KMC_TIME_EXPONENTIAL, obs_every: int = 0, stream=None,
+            out: Optional[torch.Tensor] = None) -> Optional[torch.Tensor]:
+        """Run schedules; returns the observation records [n_obs, n_replicas, 4 or 6]
+        (written into `out` when given, e.g. a buffer allocated before a graph capture)."""
         obs = None
-        if obs_every > 0 and n_schedules // obs_every > 0:
+        units = n_schedules
+        if self.obs_unit == KMC_OBS_PASS:
+            units *= 8 if schedule == KMC_SCHEDULE_PALINDROME else 4
+        if obs_every > 0 and units // obs_every > 0:
             width = 6 if self.grad_enabled else 4
-            obs = torch.empty((n_schedules // obs_every, self.n_replicas, width), dtype=torch.float64,
-                              device=self.spins.device)
+            shape = (units // obs_every, self.n_replicas, width)
+            if out is not None:
+                if tuple(out.shape) != shape or out.dtype != torch.float64 or not out.is_contiguous():
+                    raise KmcError(-1, "out must be a contiguous float64 tensor of shape %s" % (shape,))
+                obs = out
+            else:
+                obs = torch.empty(shape, dtype=torch.float64, device=self.spins.device)
         kmc_run_schedule(self.ctx, n_schedules, schedule, time_mode, obs_every, obs, stream)
         return obs
 
@@ -264,6 +288,30 @@ class Lattice:
 
     def sync(self):
         kmc_sync(self.ctx)
+
+    def set_observation(self, unit: int):
+        """KMC_OBS_SCHEDULE: records at schedule endpoints; KMC_OBS_PASS: at
+        every colour pass (register-shifted endpoints, Sec. 2.3)."""
+        kmc_set_observation(self.ctx, unit)
+        self.obs_unit = unit
+
+    def set_replica_params(self, k: Optional[Sequence[int]] = None, init: Optional[Sequence[int]] = None):
+        """Per-replica steps per visit and start modes (kmc_reset with
+        KMC_INIT_PER_REPLICA uses the modes)."""
+        if k is not None:
+            k = [int(x) for x in k]
+            assert len(k) == self.n_replicas
+        if init is not None:
+            init = [int(x) for x in init]
+            assert len(init) == self.n_replicas
+        kmc_set_replica_params(self.ctx, k, init)
+        if k is not None:
+            self.ks = k
+
+    def events_per_schedule(self, schedule: int = KMC_SCHEDULE_PALINDROME) -> int:
+        """Uniformised steps of one schedule over all replicas (Eq. 11)."""
+        visits = 2 if schedule == KMC_SCHEDULE_PALINDROME else 1
+        return int(sum(visits * (x // self.L_d) ** 2 * k for x, k in zip(self.L, self.ks)))
 
     def set_launch(self, mode: int = KMC_LAUNCH_AUTO, size: int = 0, warps_per_cta: int = 16):
         kmc_set_launch(self.ctx, mode, size, warps_per_cta)

@@ -43,8 +43,9 @@ struct kmc_ctx {
     int n_rep = 0;
     int LD = 0;
     int log2nd = 0;
-    int k = 1;
+    int k = 1;                       // default steps per visit
     std::vector<int32_t> L, Dx;
+    std::vector<int32_t> kr, init_r; // per-replica steps per visit and start mode
     std::vector<uint64_t> seed;
     std::vector<uint32_t> dom_off;   // n_rep + 1
     std::vector<uint64_t> site_off;  // n_rep
@@ -54,7 +55,7 @@ struct kmc_ctx {
     int8_t *spins = nullptr;
     cudaStream_t stream = nullptr;
 
-    int32_t *d_L = nullptr, *d_Dx = nullptr;
+    int32_t *d_L = nullptr, *d_Dx = nullptr, *d_k = nullptr, *d_init = nullptr;
     uint32_t *d_dom_off = nullptr, *d_dom_rep = nullptr;
     uint64_t *d_site_off = nullptr, *d_blk_off = nullptr, *d_seed = nullptr;
     uint64_t *d_A = nullptr, *d_inv = nullptr;
@@ -78,10 +79,12 @@ struct kmc_ctx {
     int64_t sched_done = 0;
     int64_t visits_done = 0;
     int last_time_mode = KMC_TIME_EXPONENTIAL;
+    int obs_unit = KMC_OBS_SCHEDULE;
     bool grad = false;
 
     int sm_count = 0, smem_optin = 0;
     Plan plan;
+    int req_mode = KMC_LAUNCH_AUTO, req_size = 0, req_wpb = 16; // last requested plan
     int64_t launches = 0;
     int debug_extra = 0;
     uint64_t bar_limit_ns = 2000000000ull;
@@ -120,6 +123,24 @@ kmc_status fail(kmc_ctx *c, kmc_status s, const char *fmt, ...)
         if (e_ != cudaSuccess)                                                               \
             return fail((ctx), KMC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
     } while (0)
+
+// Calls that copy from pageable host memory or synchronise cannot be part of
+// a CUDA graph: refuse them while the context's stream is capturing.
+bool capturing(const kmc_ctx *c)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st != cudaStreamCaptureStatusNone;
+}
+
+kmc_status refuse_capture(kmc_ctx *c, const char *what)
+{
+    if (capturing(c)) return fail(c, KMC_EINVAL, "%s cannot run while the stream is capturing a graph", what);
+    return KMC_OK;
+}
 
 int ld_index(int LD) { return LD == 8 ? 0 : LD == 16 ? 1 : LD == 32 ? 2 : LD == 64 ? 3 : -1; }
 
@@ -201,6 +222,7 @@ LayoutParams layout_params(kmc_ctx *c)
     P.rep_site_off = c->d_site_off;
     P.rep_blk_off = c->d_blk_off;
     P.rep_seed = c->d_seed;
+    P.rep_init = c->d_init;
     P.dom_rep = c->d_dom_rep;
     P.spins = c->spins;
     P.tiles = c->d_tiles;
@@ -215,8 +237,8 @@ RunParams run_params(kmc_ctx *c)
     RunParams P;
     std::memset(&P, 0, sizeof P);
     P.n_rep = c->n_rep;
-    P.k = c->k;
     P.rep_Dx = c->d_Dx;
+    P.rep_k = c->d_k;
     P.rep_dom_off = c->d_dom_off;
     P.rep_seed = c->d_seed;
     P.rep_A = c->d_A;
@@ -336,7 +358,9 @@ void finish_plan(const kmc_ctx *c, Plan &pl, const std::vector<std::vector<uint3
 
 // CLUSTER plan: every replica inside one cluster of `C` CTAs; a replica with
 // n domains spreads over m = ceil(n/4 / (wpb*load)) CTAs (one visit per warp
-// and phase when load = 1); replicas that need one CTA share CTAs.
+// and phase when load = 1); replicas that need one CTA share CTAs.  Replicas
+// are packed in order of decreasing k, so that a cluster's observation
+// barriers join replicas of equal cost per visit.
 kmc_status plan_cluster(kmc_ctx *c, int C, int wpb, int load, Plan &pl)
 {
     pl = Plan();
@@ -357,7 +381,10 @@ kmc_status plan_cluster(kmc_ctx *c, int C, int wpb, int load, Plan &pl)
             cta_nrep.push_back(0);
         }
     };
-    for (int r = 0; r < c->n_rep; ++r) {
+    std::vector<int> order(c->n_rep);
+    for (int r = 0; r < c->n_rep; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return c->kr[x] > c->kr[y]; });
+    for (int r : order) {
         const int n = c->Dx[r] * c->Dx[r];
         const int per_colour = n / 4;
         const int m = (per_colour + cap_per_colour - 1) / cap_per_colour;
@@ -417,7 +444,9 @@ kmc_status plan_cluster(kmc_ctx *c, int C, int wpb, int load, Plan &pl)
     return KMC_OK;
 }
 
-// GRID plan: each colour list (all replicas, ascending g) cut into n_cta contiguous chunks.
+// GRID plan: each colour list (all replicas, ascending g) cut into n_cta
+// contiguous chunks of equal estimated cost; a visit costs about k + 8
+// step-equivalents (the fixed part is halo, class build and publication).
 kmc_status plan_grid(kmc_ctx *c, int n_cta, int wpb, Plan &pl)
 {
     pl = Plan();
@@ -428,10 +457,18 @@ kmc_status plan_grid(kmc_ctx *c, int n_cta, int wpb, Plan &pl)
     for (uint32_t g = 0; g < (uint32_t)c->n_dom; ++g) lists[domain_colour(c, g)].push_back(g);
     std::vector<std::vector<uint32_t>> cta_doms(n_cta);
     for (int q = 0; q < 4; ++q) {
-        const size_t n = lists[q].size();
-        for (int b = 0; b < n_cta; ++b) {
-            const size_t i0 = n * b / n_cta, i1 = n * (b + 1) / n_cta;
-            for (size_t i = i0; i < i1; ++i) cta_doms[b].push_back(lists[q][i]);
+        const std::vector<uint32_t> &lq = lists[q];
+        uint64_t total = 0;
+        for (uint32_t g : lq) total += (uint64_t)c->kr[c->dom_rep[g]] + 8;
+        uint64_t acc = 0;
+        int b = 0;
+        for (uint32_t g : lq) {
+            const uint64_t w = (uint64_t)c->kr[c->dom_rep[g]] + 8;
+            // the chunk whose cost interval holds this domain's midpoint
+            const uint64_t mid2 = 2 * acc + w; // twice the midpoint
+            while (b + 1 < n_cta && mid2 * (uint64_t)n_cta >= 2 * total * (uint64_t)(b + 1)) ++b;
+            cta_doms[b].push_back(g);
+            acc += w;
         }
     }
     finish_plan(c, pl, cta_doms);
@@ -447,7 +484,12 @@ kmc_status check_plan(kmc_ctx *c, const Plan &pl)
     for (int e = 0; e < 2; ++e) {
         for (int gv = 0; gv < 2; ++gv) {
             RunKernel kern = run_kernel_for(c->LD, e == 0, gv == 1, pl.mode == KMC_LAUNCH_CLUSTER);
-            CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+            // the attribute belongs to the kernel, not to the context: only
+            // ever raise it, so that plans of other contexts stay launchable
+            cudaFuncAttributes fa;
+            CUDA_TRY(c, cudaFuncGetAttributes(&fa, (const void *)kern));
+            if ((size_t)fa.maxDynamicSharedSizeBytes < pl.smem)
+                CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
             if (pl.mode == KMC_LAUNCH_CLUSTER) {
                 if (pl.cluster > 8)
                     CUDA_TRY(c, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -531,6 +573,28 @@ kmc_status default_plan(kmc_ctx *c)
         why = c->err;
     }
     return fail(c, KMC_EINVAL, "no launch plan fits this batch: %s", why.c_str());
+}
+
+// Endpoint observables of the packed state into acc[n_rep][OBS_WORDS]
+// (bond sum, magnetisation, summed domain clocks, summed scores).
+kmc_status launch_observe(kmc_ctx *c, cudaStream_t s, bool expo, unsigned long long *acc)
+{
+    CUDA_TRY(c, cudaMemsetAsync(acc, 0, (size_t)c->n_rep * OBS_WORDS * 8, s));
+    RunParams P = run_params(c);
+    const int blocks = grid_for(c->n_dom, 8);
+#define KMC_OBS(LDV)                                                                                         \
+    if (expo) observe_kernel<LDV, true><<<blocks, 256, 0, s>>>(P, c->d_dom_rep, c->n_dom, c->visits_done, acc); \
+    else observe_kernel<LDV, false><<<blocks, 256, 0, s>>>(P, c->d_dom_rep, c->n_dom, c->visits_done, acc);
+    switch (c->LD) {
+    case 8: KMC_OBS(8) break;
+    case 16: KMC_OBS(16) break;
+    case 32: KMC_OBS(32) break;
+    default: KMC_OBS(64) break;
+    }
+#undef KMC_OBS
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    return KMC_OK;
 }
 
 kmc_status upload_rates(kmc_ctx *c)
@@ -624,7 +688,7 @@ kmc_status sync_ctx(kmc_ctx *c)
 
 void free_all(kmc_ctx *c)
 {
-    void **ptrs[] = {(void **)&c->d_L, (void **)&c->d_Dx, (void **)&c->d_dom_off, (void **)&c->d_dom_rep,
+    void **ptrs[] = {(void **)&c->d_L, (void **)&c->d_Dx, (void **)&c->d_k, (void **)&c->d_init, (void **)&c->d_dom_off, (void **)&c->d_dom_rep,
                      (void **)&c->d_site_off, (void **)&c->d_blk_off, (void **)&c->d_seed, (void **)&c->d_A,
                      (void **)&c->d_inv, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_tiles,
                      (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_bar, (void **)&c->d_err,
@@ -703,6 +767,8 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     c->spins = spins_dev;
     c->stream = (cudaStream_t)stream;
     c->L.assign(L, L + n_replicas);
+    c->kr.assign(n_replicas, k_steps);
+    c->init_r.assign(n_replicas, init);
     c->seed.assign(seeds, seeds + n_replicas);
     c->Dx.resize(n_replicas);
     c->dom_off.assign(n_replicas + 1, 0);
@@ -741,6 +807,8 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
 #define ALLOC(p, n) if ((s = dev_alloc(c, &(p), (n))) != KMC_OK) return bail(s)
     ALLOC(c->d_L, n_replicas);
     ALLOC(c->d_Dx, n_replicas);
+    ALLOC(c->d_k, n_replicas);
+    ALLOC(c->d_init, n_replicas);
     ALLOC(c->d_dom_off, n_replicas + 1);
     ALLOC(c->d_dom_rep, ndom);
     ALLOC(c->d_site_off, n_replicas);
@@ -764,6 +832,8 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
         {c->d_L, c->L.data(), (size_t)n_replicas * 4},
         {c->d_Dx, c->Dx.data(), (size_t)n_replicas * 4},
+        {c->d_k, c->kr.data(), (size_t)n_replicas * 4},
+        {c->d_init, c->init_r.data(), (size_t)n_replicas * 4},
         {c->d_dom_off, c->dom_off.data(), (size_t)(n_replicas + 1) * 4},
         {c->d_dom_rep, c->dom_rep.data(), (size_t)ndom * 4},
         {c->d_site_off, c->site_off.data(), (size_t)n_replicas * 8},
@@ -789,10 +859,15 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
 kmc_status kmc_reset(kmc_ctx *c, int32_t init, void *stream)
 {
     if (!c) return KMC_EINVAL;
-    if (init < KMC_INIT_RANDOM || init > KMC_INIT_KEEP) return fail(c, KMC_EINVAL, "bad init mode");
+    if (init < KMC_INIT_RANDOM || init > KMC_INIT_PER_REPLICA) return fail(c, KMC_EINVAL, "bad init mode");
     c->stream = (cudaStream_t)stream;
     kmc_status s;
-    if (init != KMC_INIT_KEEP && (s = launch_init(c, init, c->stream)) != KMC_OK) return s;
+    bool any = init != KMC_INIT_KEEP;
+    if (init == KMC_INIT_PER_REPLICA) {
+        any = false;
+        for (int32_t m : c->init_r) any = any || m != KMC_INIT_KEEP;
+    }
+    if (any && (s = launch_init(c, init, c->stream)) != KMC_OK) return s;
     if ((s = launch_reset_counters(c, c->stream)) != KMC_OK) return s;
     c->sched_done = 0;
     c->visits_done = 0;
@@ -802,6 +877,7 @@ kmc_status kmc_reset(kmc_ctx *c, int32_t init, void *stream)
 kmc_status kmc_set_rates(kmc_ctx *c, double J, const double *beta, const double *h, double nu, int32_t rate_law)
 {
     if (!c) return KMC_EINVAL;
+    if (refuse_capture(c, "kmc_set_rates") != KMC_OK) return KMC_EINVAL;
     if (!beta || !h) return fail(c, KMC_EINVAL, "beta and h arrays required");
     if (rate_law != KMC_RATE_METROPOLIS && rate_law != KMC_RATE_BARKER) return fail(c, KMC_EINVAL, "bad rate law");
     if (!std::isfinite(J) || !(nu > 0.0) || !std::isfinite(nu)) return fail(c, KMC_EINVAL, "J finite and nu > 0 required");
@@ -829,6 +905,7 @@ kmc_status kmc_set_rates(kmc_ctx *c, double J, const double *beta, const double 
 kmc_status kmc_set_rate_table(kmc_ctx *c, double J, const double *beta, const double *h, double nu, const double *a)
 {
     if (!c) return KMC_EINVAL;
+    if (refuse_capture(c, "kmc_set_rate_table") != KMC_OK) return KMC_EINVAL;
     if (!beta || !h || !a) return fail(c, KMC_EINVAL, "beta, h and a arrays required");
     if (!std::isfinite(J) || !(nu > 0.0)) return fail(c, KMC_EINVAL, "J finite and nu > 0 required");
     const int P = 63 - c->log2nd;
@@ -879,7 +956,12 @@ kmc_status kmc_get_rate_table(const kmc_ctx *c, int32_t replica, double *a, uint
 kmc_status kmc_set_launch(kmc_ctx *c, int32_t mode, int32_t size, int32_t warps_per_cta)
 {
     if (!c) return KMC_EINVAL;
-    if (mode == KMC_LAUNCH_AUTO) return default_plan(c);
+    if (refuse_capture(c, "kmc_set_launch") != KMC_OK) return KMC_EINVAL;
+    if (mode == KMC_LAUNCH_AUTO) {
+        const kmc_status s = default_plan(c);
+        if (s == KMC_OK) c->req_mode = KMC_LAUNCH_AUTO;
+        return s;
+    }
     if (warps_per_cta < 1 || warps_per_cta > MAX_WPB) return fail(c, KMC_EINVAL, "warps_per_cta must be 1..%d", MAX_WPB);
     Plan pl;
     kmc_status s;
@@ -896,7 +978,52 @@ kmc_status kmc_set_launch(kmc_ctx *c, int32_t mode, int32_t size, int32_t warps_
     } else {
         return fail(c, KMC_EINVAL, "bad launch mode %d", mode);
     }
-    return install_plan(c, pl);
+    if ((s = install_plan(c, pl)) != KMC_OK) return s;
+    c->req_mode = mode;
+    c->req_size = size;
+    c->req_wpb = warps_per_cta;
+    return KMC_OK;
+}
+
+kmc_status kmc_set_observation(kmc_ctx *c, int32_t unit)
+{
+    if (!c) return KMC_EINVAL;
+    if (unit != KMC_OBS_SCHEDULE && unit != KMC_OBS_PASS) return fail(c, KMC_EINVAL, "bad observation unit %d", unit);
+    c->obs_unit = unit;
+    return KMC_OK;
+}
+
+kmc_status kmc_set_replica_params(kmc_ctx *c, const int32_t *k_steps, const int32_t *init)
+{
+    if (!c) return KMC_EINVAL;
+    kmc_status s;
+    if ((s = refuse_capture(c, "kmc_set_replica_params")) != KMC_OK) return s;
+    if (k_steps) {
+        if (c->sched_done != 0) return fail(c, KMC_EINVAL, "per-replica k can only change before the first run after a reset");
+        for (int r = 0; r < c->n_rep; ++r)
+            if (k_steps[r] < 1 || k_steps[r] > 65535) return fail(c, KMC_EINVAL, "replica %d: k_steps must be in 1..65535", r);
+    }
+    if (init)
+        for (int r = 0; r < c->n_rep; ++r)
+            if (init[r] < KMC_INIT_RANDOM || init[r] > KMC_INIT_KEEP) return fail(c, KMC_EINVAL, "replica %d: bad init mode", r);
+    if (init) {
+        c->init_r.assign(init, init + c->n_rep);
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_init, c->init_r.data(), (size_t)c->n_rep * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    if (k_steps) {
+        const std::vector<int32_t> old = c->kr;
+        c->kr.assign(k_steps, k_steps + c->n_rep);
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_k, c->kr.data(), (size_t)c->n_rep * 4, cudaMemcpyHostToDevice, c->stream));
+        // cost-aware plans depend on k: rebuild the requested plan
+        if ((s = kmc_set_launch(c, c->req_mode, c->req_size, c->req_wpb)) != KMC_OK) {
+            c->kr = old;
+            const std::string why = c->err;
+            CUDA_TRY(c, cudaMemcpyAsync(c->d_k, c->kr.data(), (size_t)c->n_rep * 4, cudaMemcpyHostToDevice, c->stream));
+            return fail(c, s, "%s", why.c_str());
+        }
+    }
+    // pageable sources: consumed when the copies return
+    return KMC_OK;
 }
 
 kmc_status kmc_get_launch(const kmc_ctx *c, int32_t *mode, int32_t *size, int32_t *ctas, int32_t *warps_per_cta,
@@ -941,9 +1068,14 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     cudaStream_t s = c->stream;
     kmc_status st;
     const bool want_obs = obs_every > 0 && obs_dev != nullptr;
-    const int64_t n_obs = want_obs ? n_schedules / obs_every : 0;
+    const bool pass_obs = c->obs_unit == KMC_OBS_PASS;
+    const int64_t units = pass_obs ? n_schedules * (schedule == KMC_SCHEDULE_PALINDROME ? 8 : 4) : n_schedules;
+    const int64_t n_obs = want_obs ? units / obs_every : 0;
+    const bool cap = capturing(c);
     if (want_obs && n_obs > 0) {
         const size_t words = (size_t)n_obs * c->n_rep * OBS_WORDS;
+        if (words > c->obs_acc_words && cap)
+            return fail(c, KMC_EINVAL, "observation buffer must be sized by an uncaptured run of at least as many records");
         if (words > c->obs_acc_words) {
             if (c->d_obs_acc) cudaFree(c->d_obs_acc);
             c->d_obs_acc = nullptr;
@@ -954,10 +1086,15 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
         CUDA_TRY(c, cudaMemsetAsync(c->d_obs_acc, 0, words * 8, s));
     }
     if ((st = launch_pack(c, s)) != KMC_OK) return st;
+    unsigned long long *base = reinterpret_cast<unsigned long long *>(c->d_tmp);
+    if (pass_obs && n_obs > 0 && (st = launch_observe(c, s, time_mode == KMC_TIME_EXPONENTIAL, base)) != KMC_OK)
+        return st;
     RunParams P = run_params(c);
     P.schedule = schedule;
     P.obs_every = want_obs ? obs_every : 0;
     P.obs_acc = (want_obs && n_obs > 0) ? c->d_obs_acc : nullptr;
+    P.obs_pass = (pass_obs && n_obs > 0) ? 1 : 0;
+    P.n_obs = n_obs;
     P.sched_begin = c->sched_done;
     P.n_sched = n_schedules;
     P.visits_before = c->visits_done;
@@ -965,7 +1102,8 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     const bool cluster = pl.mode == KMC_LAUNCH_CLUSTER;
     RunKernel kern = run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad, cluster);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (c->prof) {
+    const bool prof = c->prof && !cap;
+    if (prof) {
         CUDA_TRY(c, cudaEventCreate(&ev0));
         CUDA_TRY(c, cudaEventCreate(&ev1));
         CUDA_TRY(c, cudaEventRecord(ev0, s));
@@ -990,14 +1128,20 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
         CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)kern, dim3(pl.n_cta), dim3(pl.wpb * 32), args, pl.smem, s));
     }
     ++c->launches;
-    if (c->prof) {
+    if (prof) {
         CUDA_TRY(c, cudaEventRecord(ev1, s));
         c->prof_events.emplace_back(ev0, ev1);
     }
     if (want_obs && n_obs > 0) {
-        const int n_rec = (int)(n_obs * c->n_rep);
-        finalize_obs_kernel<<<grid_for(n_rec, 256), 256, 0, s>>>(c->d_obs_acc, n_rec, c->n_rep, c->d_L, c->d_Dx, c->J,
-                                                                  c->d_h, obs_dev, c->grad ? 6 : 4);
+        if (pass_obs) {
+            finalize_pass_obs_kernel<<<grid_for(c->n_rep, 128), 128, 0, s>>>(base, c->d_obs_acc, n_obs, c->n_rep, c->d_L,
+                                                                             c->d_Dx, c->J, c->d_h, obs_dev,
+                                                                             c->grad ? 6 : 4);
+        } else {
+            const int n_rec = (int)(n_obs * c->n_rep);
+            finalize_obs_kernel<<<grid_for(n_rec, 256), 256, 0, s>>>(c->d_obs_acc, n_rec, c->n_rep, c->d_L, c->d_Dx,
+                                                                      c->J, c->d_h, obs_dev, c->grad ? 6 : 4);
+        }
         ++c->launches;
         CUDA_TRY(c, cudaGetLastError());
     }
@@ -1017,27 +1161,13 @@ kmc_status kmc_sync(kmc_ctx *c)
 kmc_status kmc_observables(kmc_ctx *c, double *E_per_site, double *m, double *t, int64_t *steps, int64_t *flips)
 {
     if (!c) return KMC_EINVAL;
+    if (refuse_capture(c, "kmc_observables") != KMC_OK) return KMC_EINVAL;
     kmc_status st;
     cudaStream_t s = c->stream;
     if ((st = launch_pack(c, s)) != KMC_OK) return st;
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(c->d_tmp);
     const size_t words = (size_t)c->n_rep * OBS_WORDS;
-    CUDA_TRY(c, cudaMemsetAsync(acc, 0, words * 8, s));
-    RunParams P = run_params(c);
-    const bool expo = c->last_time_mode == KMC_TIME_EXPONENTIAL;
-    const int blocks = grid_for(c->n_dom, 8);
-#define KMC_OBS(LDV)                                                                                         \
-    if (expo) observe_kernel<LDV, true><<<blocks, 256, 0, s>>>(P, c->d_dom_rep, c->n_dom, c->visits_done, acc); \
-    else observe_kernel<LDV, false><<<blocks, 256, 0, s>>>(P, c->d_dom_rep, c->n_dom, c->visits_done, acc);
-    switch (c->LD) {
-    case 8: KMC_OBS(8) break;
-    case 16: KMC_OBS(16) break;
-    case 32: KMC_OBS(32) break;
-    default: KMC_OBS(64) break;
-    }
-#undef KMC_OBS
-    ++c->launches;
-    CUDA_TRY(c, cudaGetLastError());
+    if ((st = launch_observe(c, s, c->last_time_mode == KMC_TIME_EXPONENTIAL, acc)) != KMC_OK) return st;
     std::vector<unsigned long long> h_acc(words);
     CUDA_TRY(c, cudaMemcpyAsync(h_acc.data(), acc, words * 8, cudaMemcpyDeviceToHost, s));
     if ((st = sync_ctx(c)) != KMC_OK) return st;
@@ -1052,7 +1182,7 @@ kmc_status kmc_observables(kmc_ctx *c, double *E_per_site, double *m, double *t,
         if (E_per_site) E_per_site[r] = e;
         if (m) m[r] = mg / N;
         if (t) t[r] = tsum / ((double)c->Dx[r] * c->Dx[r]);
-        if (steps) steps[r] = c->visits_done * (int64_t)c->k * (int64_t)c->Dx[r] * c->Dx[r];
+        if (steps) steps[r] = c->visits_done * (int64_t)c->kr[r] * (int64_t)c->Dx[r] * c->Dx[r];
     }
     if (flips) {
         std::vector<int64_t> fl(c->n_dom);
@@ -1069,16 +1199,18 @@ kmc_status kmc_observables(kmc_ctx *c, double *E_per_site, double *m, double *t,
 kmc_status kmc_domain_state(kmc_ctx *c, uint64_t *hash, int64_t *flips, double *t)
 {
     if (!c) return KMC_EINVAL;
+    if (refuse_capture(c, "kmc_domain_state") != KMC_OK) return KMC_EINVAL;
     cudaStream_t s = c->stream;
     uint64_t *dh = reinterpret_cast<uint64_t *>(c->d_tmp);
     int64_t *df = reinterpret_cast<int64_t *>(dh + c->n_dom);
     double *dt = reinterpret_cast<double *>(df + c->n_dom);
-    const int64_t steps = c->visits_done * (int64_t)c->k;
     const double lambda = (double)(c->LD * c->LD) * c->nu;
     if (c->last_time_mode == KMC_TIME_EXPONENTIAL)
-        domain_state_kernel<true><<<grid_for(c->n_dom, 256), 256, 0, s>>>(c->d_dctr, c->n_dom, steps, lambda, dh, df, dt);
+        domain_state_kernel<true><<<grid_for(c->n_dom, 256), 256, 0, s>>>(c->d_dctr, c->n_dom, c->visits_done,
+                                                                            c->d_dom_rep, c->d_k, lambda, dh, df, dt);
     else
-        domain_state_kernel<false><<<grid_for(c->n_dom, 256), 256, 0, s>>>(c->d_dctr, c->n_dom, steps, lambda, dh, df, dt);
+        domain_state_kernel<false><<<grid_for(c->n_dom, 256), 256, 0, s>>>(c->d_dctr, c->n_dom, c->visits_done,
+                                                                             c->d_dom_rep, c->d_k, lambda, dh, df, dt);
     ++c->launches;
     CUDA_TRY(c, cudaGetLastError());
     const size_t n = (size_t)c->n_dom;
@@ -1091,6 +1223,7 @@ kmc_status kmc_domain_state(kmc_ctx *c, uint64_t *hash, int64_t *flips, double *
 kmc_status kmc_grad(kmc_ctx *c, double *score_dev, int32_t reset)
 {
     if (!c) return KMC_EINVAL;
+    if (refuse_capture(c, "kmc_grad") != KMC_OK) return KMC_EINVAL;
     if (!score_dev) return fail(c, KMC_EINVAL, "score_dev required");
     score_reduce_kernel<<<grid_for(c->n_rep, 128), 128, 0, c->stream>>>(c->d_dctr, c->d_dom_off, c->n_rep, score_dev,
                                                                           reset, c->d_dctr);
@@ -1128,6 +1261,8 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     c.LD = L_d;
     c.log2nd = 2 * (L_d == 8 ? 3 : L_d == 16 ? 4 : L_d == 32 ? 5 : 6);
     c.k = k_steps;
+    c.kr.assign(1, k_steps);
+    c.init_r.assign(1, KMC_INIT_KEEP);
     c.spins = spins_dev;
     c.stream = (cudaStream_t)stream;
     c.L.assign(1, L);
@@ -1184,6 +1319,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
         c.d_obs_acc = cv.take<unsigned long long>((size_t)std::max<int64_t>(n_obs, 1) * OBS_WORDS);
         c.d_L = cv.take<int32_t>(1);
         c.d_Dx = cv.take<int32_t>(1);
+        c.d_k = cv.take<int32_t>(1);
         c.d_dom_off = cv.take<uint32_t>(2);
         c.d_site_off = cv.take<uint64_t>(1);
         c.d_blk_off = cv.take<uint64_t>(2);
@@ -1234,7 +1370,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
         g32[20 + q] = c.gh[q];
     }
     struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
-        {c.d_L, c.L.data(), 4}, {c.d_Dx, c.Dx.data(), 4}, {c.d_dom_off, c.dom_off.data(), 8},
+        {c.d_L, c.L.data(), 4}, {c.d_Dx, c.Dx.data(), 4}, {c.d_k, c.kr.data(), 4}, {c.d_dom_off, c.dom_off.data(), 8},
         {c.d_site_off, c.site_off.data(), 8}, {c.d_blk_off, c.blk_off.data(), 16}, {c.d_seed, c.seed.data(), 8},
         {c.d_A, A16.data(), 128}, {c.d_inv, inv16.data(), 128}, {c.d_grad, g32.data(), 256}, {c.d_h, c.h.data(), 8},
         {c.d_dom_rep, c.dom_rep.data(), (size_t)c.n_dom * 4}, {c.d_plan, flat.data(), flat.size() * 4},
@@ -1286,7 +1422,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     // synchronising: the device error word lives in the shared array
     st = sync_ctx(&c);
     // the kmc_ctx destructor must not free the static array
-    c.d_L = nullptr; c.d_Dx = nullptr; c.d_dom_off = nullptr; c.d_dom_rep = nullptr; c.d_site_off = nullptr;
+    c.d_L = nullptr; c.d_Dx = nullptr; c.d_k = nullptr; c.d_dom_off = nullptr; c.d_dom_rep = nullptr; c.d_site_off = nullptr;
     c.d_blk_off = nullptr; c.d_seed = nullptr; c.d_A = nullptr; c.d_inv = nullptr; c.d_grad = nullptr; c.d_h = nullptr;
     c.d_tiles = nullptr; c.d_edges = nullptr; c.d_dctr = nullptr; c.d_bar = nullptr; c.d_err = nullptr;
     c.d_obs_acc = nullptr; c.d_plan = nullptr;

@@ -43,14 +43,15 @@ constexpr uint64_t HASH_PRIME = 0x00000100000001b3ull; // FNV-1a 64 prime
 constexpr uint32_t TAG_INIT = 1u, TAG_PERM = 2u;       // step draws use tag 0
 constexpr int ERR_TIMEOUT = 1, ERR_SPIN = 2, ERR_INTERNAL = 3;
 constexpr int SCHED_PALINDROME = 0, SCHED_FIXED = 1, SCHED_RANDOM_PERM = 2;
+constexpr int INIT_KEEP = 2, INIT_PER_REPLICA = 3;
 constexpr int OBS_WORDS = 5; // bonds, mag, clock sum, score beta sum, score h sum
 
 // Replica table staged in shared memory (bytes):
 //   [0,128) A[16] fixed-point acceptance, [128,256) inv[16] = floor((2^64-1)/A),
 //   [256,512) grad[32] = a[10], dlog a/dbeta[10], dlog a/dh[10],
-//   [512] seed, [520] dom_off, [524] Dx.
-constexpr int RT_BYTES = 528;
-constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524;
+//   [512] seed, [520] dom_off, [524] Dx, [528] k (steps per visit).
+constexpr int RT_BYTES = 544;
+constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524, RT_K = 528;
 // Slot: [tile][stamped edges 64][counters 48][meta 32];
 // meta u32: g, replica, d, rt, nb[4].
 constexpr int SLOT_EXTRA = 64 + 48 + 32;
@@ -66,7 +67,6 @@ template <int LD> __host__ __device__ constexpr int slot_bytes() { return ((LD *
 
 struct RunParams {
     int n_rep;
-    int k;
     int schedule;
     int obs_every;
     int64_t sched_begin;
@@ -74,6 +74,7 @@ struct RunParams {
     int64_t visits_before; // per-domain visits before this launch (clock mode EXPECTED)
     // per replica (global)
     const int32_t *rep_Dx;
+    const int32_t *rep_k;    // steps per domain visit
     const uint32_t *rep_dom_off;
     const uint64_t *rep_seed;
     const uint64_t *rep_A;   // [n_rep][16]
@@ -93,8 +94,11 @@ struct RunParams {
     uint8_t *tiles;
     uint64_t *dctr;
     uint64_t *edges;
-    // observables scratch [n_obs][n_rep][OBS_WORDS]
+    // observables scratch [n_obs][n_rep][OBS_WORDS]: schedule mode holds the
+    // records, pass mode the per-record changes (bonds, mag, clock, scores)
     unsigned long long *obs_acc;
+    int obs_pass;   // 1: a record after every obs_every-th colour pass
+    int64_t n_obs;  // records of this launch
     // grid barrier
     unsigned *bar_count;
     int *err;
@@ -344,6 +348,11 @@ struct Counters {
     uint64_t H, flips, clkM;
     int64_t clkE;
     double sb, sh;
+    // this visit only: change of the bond sum and of the magnetisation, and
+    // the product of its clock variates (mantissa vM, exponent vE)
+    int dbonds, dmag;
+    uint64_t vM;
+    int64_t vE;
 };
 
 // ---------------------------------------------------------------------------
@@ -431,6 +440,7 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const u
             m = __shfl_sync(FULL_WARP, m, 0);
             e = __shfl_sync(FULL_WARP, e, 0);
             mant_mul(cn.clkM, cn.clkE, m, (int64_t)e);
+            mant_mul(cn.vM, cn.vE, m, (int64_t)e);
         }
         int pos = 0;
         while (true) {
@@ -466,6 +476,11 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const u
             }
             // rank selection: jj-th member of class c in row-major order
             const int qc = (c >= 5) ? c - 5 : c;
+            // flipping spin s with neighbour sum 2qc - 4 changes the bond sum
+            // by -2 s (2qc - 4) and the magnetisation by -2 s
+            const int sgn = (c >= 5) ? 1 : -1;
+            cn.dbonds -= 2 * sgn * (2 * qc - 4);
+            cn.dmag -= 2 * sgn;
             const row_t UP = (c >= 5) ? (row_t)~(row_t)0 : (row_t)0;
             const row_t Q2 = (qc & 4) ? (row_t)~(row_t)0 : (row_t)0;
             const row_t Q1 = (qc & 2) ? (row_t)~(row_t)0 : (row_t)0;
@@ -712,6 +727,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
             *reinterpret_cast<uint64_t *>(t + RT_SEED) = P.rep_seed[r];
             *reinterpret_cast<uint32_t *>(t + RT_DOMOFF) = P.rep_dom_off[r];
             *reinterpret_cast<int32_t *>(t + RT_DX) = P.rep_Dx[r];
+            *reinterpret_cast<int32_t *>(t + RT_K) = P.rep_k[r];
         }
     }
     for (int i = wib; i < nslot; i += nwarps) {
@@ -811,7 +827,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
 
     // One visit; publishes the slot's edges, then (release) its visit count.
     auto visit = [&](uint8_t *sl, uint64_t np0, int nf, uint64_t hN, uint64_t hS, uint64_t hW, uint64_t hE,
-                     uint32_t count_after) {
+                     uint32_t count_after, int64_t pass) {
         const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
         const uint8_t *rt = tables + (size_t)meta[META_RT] * RT_BYTES;
         Planes<LD> pl;
@@ -827,7 +843,12 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         cn.clkE = (int64_t)ctr[DCTR_CLKE];
         cn.sb = 0.0;
         cn.sh = 0.0;
-        visit_core<LD, EXPO, GRAD>(pl, cn, rt, (row_t)hN, (row_t)hS, hW, hE, meta[META_D], np0, nf, P.k, lane, P.err);
+        cn.dbonds = 0;
+        cn.dmag = 0;
+        cn.vM = 1ull << 63;
+        cn.vE = 0;
+        const int k = *reinterpret_cast<const int32_t *>(rt + RT_K);
+        visit_core<LD, EXPO, GRAD>(pl, cn, rt, (row_t)hN, (row_t)hS, hW, hE, meta[META_D], np0, nf, k, lane, P.err);
         mem_t *wrow = reinterpret_cast<mem_t *>(sl);
         if (lane < G::NACT) {
 #pragma unroll
@@ -842,6 +863,21 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
             if (GRAD) {
                 reinterpret_cast<double *>(ctr)[DCTR_SB] += cn.sb;
                 reinterpret_cast<double *>(ctr)[DCTR_SH] += cn.sh;
+            }
+            // pass observation: this visit's changes go to the first record at
+            // or after its pass; the finalize kernel accumulates the records
+            const int64_t o = P.obs_pass ? pass / P.obs_every : P.n_obs;
+            if (o < P.n_obs) {
+                unsigned long long *acc = P.obs_acc + ((size_t)o * P.n_rep + meta[META_R]) * OBS_WORDS;
+                const double dt = EXPO ? domain_time(true, cn.vM, cn.vE, 0, P.lambda)
+                                       : __ddiv_rn((double)(nf * k), P.lambda);
+                if (cn.dbonds != 0) atomicAdd(&acc[0], (unsigned long long)(long long)cn.dbonds);
+                if (cn.dmag != 0) atomicAdd(&acc[1], (unsigned long long)(long long)cn.dmag);
+                atomicAdd(reinterpret_cast<double *>(&acc[2]), dt);
+                if (GRAD) {
+                    atomicAdd(reinterpret_cast<double *>(&acc[3]), cn.sb);
+                    atomicAdd(reinterpret_cast<double *>(&acc[4]), cn.sh);
+                }
             }
         }
         if (lane < EDGE_WORDS) {
@@ -877,8 +913,9 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         int nf = 1;
         if (P.schedule != SCHED_RANDOM_PERM) {
             const int colour = fixed_colour(P.schedule, p);
-            // fuse following phases of the same colour unless an observation intervenes
-            while (gp + nf < gp_end) {
+            // fuse following phases of the same colour unless an observation
+            // intervenes (pass observation: every pass ends on its own)
+            while (!P.obs_pass && gp + nf < gp_end) {
                 const uint64_t g2 = gp + nf;
                 const int p2 = (int)(g2 % nph);
                 if (fixed_colour(P.schedule, p2) != colour) break;
@@ -900,7 +937,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                         ok = false;
                         break;
                     }
-                    visit(sl, np0, nf, hN, hS, hW, hE, after);
+                    visit(sl, np0, nf, hN, hS, hW, hE, after, (int64_t)(gp - gp_begin));
                 }
             }
             if (colour == 0) ++gc0;
@@ -934,7 +971,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                     ok = false;
                     break;
                 }
-                visit(sl, np0, 1, hN, hS, hW, hE, done_before + 1u);
+                visit(sl, np0, 1, hN, hS, hW, hE, done_before + 1u, (int64_t)(gp - gp_begin));
             }
         }
         gp += (uint64_t)nf;
@@ -942,7 +979,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         // done before, no visit of the next schedule until every domain is observed
         if (gp % nph == 0) {
             const int64_t nl_done = (int64_t)(gp / nph - (uint64_t)P.sched_begin);
-            if (P.obs_every > 0 && P.obs_acc != nullptr && nl_done > 0 && (nl_done % P.obs_every) == 0) {
+            if (!P.obs_pass && P.obs_every > 0 && P.obs_acc != nullptr && nl_done > 0 && (nl_done % P.obs_every) == 0) {
                 phase_sync(bar_no);
                 if (ok && *(volatile int *)P.err == 0) {
                     const int64_t o = nl_done / P.obs_every - 1;
@@ -971,8 +1008,10 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                         domain_bonds_mag<LD>(S, hE, hS, lane, bonds, mag);
                         if (lane == 0) {
                             const uint64_t *ctr = reinterpret_cast<const uint64_t *>(sl + OFF_CTR);
+                            const uint8_t *rt = tables + (size_t)meta[META_RT] * RT_BYTES;
+                            const int64_t k = *reinterpret_cast<const int32_t *>(rt + RT_K);
                             const double tdom = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE],
-                                                            visits * (int64_t)P.k, P.lambda);
+                                                            visits * k, P.lambda);
                             unsigned long long *acc = P.obs_acc + ((size_t)o * P.n_rep + meta[META_R]) * OBS_WORDS;
                             atomicAdd(&acc[0], (unsigned long long)(long long)bonds);
                             atomicAdd(&acc[1], (unsigned long long)(long long)mag);
@@ -986,10 +1025,11 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
             }
         }
     }
-    if (CLUSTER) {
-        // no CTA may leave while another still reads its shared memory
-        cluster_sync();
-    }
+    // every warp of the CTA must have finished its visits before any warp
+    // writes a slot back; in CLUSTER mode, also no CTA may leave while another
+    // still reads its shared memory
+    if (CLUSTER) cluster_sync();
+    else __syncthreads();
     if (*(volatile int *)P.err != 0) return;
     // write owned tiles and counters back (and edges, for the observables kernel)
     for (int i = wib; i < nslot; i += nwarps) {
@@ -1016,6 +1056,7 @@ struct LayoutParams {
     const uint64_t *rep_site_off;
     const uint64_t *rep_blk_off; // prefix of L^2/128 init blocks, n_rep+1 entries
     const uint64_t *rep_seed;
+    const int32_t *rep_init; // per-replica start (init mode INIT_PER_REPLICA)
     const uint32_t *dom_rep;
     int8_t *spins;
     uint8_t *tiles;
@@ -1024,7 +1065,8 @@ struct LayoutParams {
     int *err;
 };
 
-// iid +-1 from Philox (block b of 128 sites: counter {b_lo, b_hi, 0, TAG_INIT<<24}) or all up.
+// iid +-1 from Philox (block b of 128 sites: counter {b_lo, b_hi, 0, TAG_INIT<<24}) or all up;
+// init = INIT_PER_REPLICA takes each replica's mode from rep_init (INIT_KEEP leaves it alone).
 __global__ void init_spins_kernel(const LayoutParams P, int init)
 {
     const uint64_t total = P.rep_blk_off[P.n_rep];
@@ -1036,9 +1078,11 @@ __global__ void init_spins_kernel(const LayoutParams P, int init)
             if (P.rep_blk_off[mid] <= t) lo = mid; else hi = mid - 1;
         }
         const int r = lo;
+        const int mode = (init == INIT_PER_REPLICA) ? P.rep_init[r] : init;
+        if (mode == INIT_KEEP) continue;
         const uint64_t b = t - P.rep_blk_off[r];
         uint4 w = make_uint4(~0u, ~0u, ~0u, ~0u);
-        if (init == 0) {
+        if (mode == 0) {
             const uint64_t seed = P.rep_seed[r];
             w = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(b >> 32), 0u, TAG_INIT << 24),
                               make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
@@ -1165,8 +1209,8 @@ __global__ void observe_kernel(const RunParams P, const uint32_t *dom_rep, int n
         domain_bonds_mag<LD>(S, hE, hS, lane, bonds, mag);
         if (lane == 0) {
             const uint64_t *ctr = P.dctr + (uint64_t)g * DCTR_WORDS;
-            const double t = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE], visits * (int64_t)P.k,
-                                         P.lambda);
+            const double t = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE],
+                                         visits * (int64_t)P.rep_k[r], P.lambda);
             unsigned long long *a = acc + (size_t)r * OBS_WORDS;
             atomicAdd(&a[0], (unsigned long long)(long long)bonds);
             atomicAdd(&a[1], (unsigned long long)(long long)mag);
@@ -1203,17 +1247,55 @@ __global__ void finalize_obs_kernel(const unsigned long long *acc, int n_rec, in
     }
 }
 
+// Pass observation: record o = base + the changes of every record up to o.
+// One thread per replica walks its records in order (the integer sums are
+// exact; the clock and score sums add the per-record totals in record order).
+__global__ void finalize_pass_obs_kernel(const unsigned long long *base /* [n_rep][OBS_WORDS] */,
+                                         const unsigned long long *acc, int64_t n_obs, int n_rep,
+                                         const int32_t *rep_L, const int32_t *rep_Dx, double J,
+                                         const double *rep_h, double *out, int stride)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rep) return;
+    const unsigned long long *b0 = base + (size_t)r * OBS_WORDS;
+    long long bonds = (long long)b0[0], mag = (long long)b0[1];
+    double tsum = __longlong_as_double((long long)b0[2]);
+    double sb = __longlong_as_double((long long)b0[3]), sh = __longlong_as_double((long long)b0[4]);
+    const double N = (double)rep_L[r] * (double)rep_L[r];
+    const double nD = (double)rep_Dx[r] * (double)rep_Dx[r];
+    for (int64_t o = 0; o < n_obs; ++o) {
+        const unsigned long long *a = acc + ((size_t)o * n_rep + r) * OBS_WORDS;
+        bonds += (long long)a[0];
+        mag += (long long)a[1];
+        tsum = __dadd_rn(tsum, __longlong_as_double((long long)a[2]));
+        sb = __dadd_rn(sb, __longlong_as_double((long long)a[3]));
+        sh = __dadd_rn(sh, __longlong_as_double((long long)a[4]));
+        const double b = (double)bonds, m = (double)mag;
+        const double e = __ddiv_rn(__dsub_rn(__dmul_rn(-J, b), __dmul_rn(rep_h[r], m)), N);
+        const double mm = __ddiv_rn(m, N);
+        double *w = out + ((size_t)o * n_rep + r) * stride;
+        w[0] = e;
+        w[1] = mm;
+        w[2] = __dmul_rn(e, mm);
+        w[3] = __ddiv_rn(tsum, nD);
+        if (stride >= 6) {
+            w[4] = sb;
+            w[5] = sh;
+        }
+    }
+}
+
 // per-domain counters -> host-facing arrays (hash, flips, clock)
 template <bool EXPO>
-__global__ void domain_state_kernel(const uint64_t *dctr, int n_dom, int64_t steps, double lambda,
-                                    uint64_t *hash, int64_t *flips, double *t)
+__global__ void domain_state_kernel(const uint64_t *dctr, int n_dom, int64_t visits, const uint32_t *dom_rep,
+                                    const int32_t *rep_k, double lambda, uint64_t *hash, int64_t *flips, double *t)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_dom) return;
     const uint64_t *c = dctr + (uint64_t)g * DCTR_WORDS;
     hash[g] = c[DCTR_HASH];
     flips[g] = (int64_t)c[DCTR_FLIPS];
-    t[g] = domain_time(EXPO, c[DCTR_CLKM], (int64_t)c[DCTR_CLKE], steps, lambda);
+    t[g] = domain_time(EXPO, c[DCTR_CLKM], (int64_t)c[DCTR_CLKE], visits * (int64_t)rep_k[dom_rep[g]], lambda);
 }
 
 // zero counters: hash basis, flips 0, clock 1.0 (m = 2^63, e = 0), scores 0

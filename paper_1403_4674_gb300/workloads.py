@@ -9,7 +9,7 @@ implementation.  The paper's workloads are Ising lattices it builds itself
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List
+from typing import List, Optional
 
 import numpy as np
 
@@ -30,6 +30,14 @@ class Workload:
     nu: float = 1.0
     law: int = 0             # Metropolis
     note: str = ""
+    ks: Optional[List[int]] = None     # per-replica k (default: k for all)
+    inits: Optional[List[int]] = None  # per-replica start (default: init for all)
+
+    def k_of(self, r: int) -> int:
+        return self.ks[r] if self.ks is not None else self.k
+
+    def init_of(self, r: int) -> int:
+        return self.inits[r] if self.inits is not None else self.init
 
     @property
     def sites(self) -> int:
@@ -37,7 +45,7 @@ class Workload:
 
     def steps_per_schedule(self) -> int:
         """Uniformised steps of one palindromic schedule (two visits per domain)."""
-        return int(sum(2 * (x // self.L_d) ** 2 * self.k for x in self.L))
+        return int(sum(2 * (x // self.L_d) ** 2 * self.k_of(r) for r, x in enumerate(self.L)))
 
 
 def replica_seeds(master: int, n: int) -> List[int]:
@@ -67,6 +75,25 @@ def batch_1024(k: int, seed_master: int = 1024) -> Workload:
     seeds = replica_seeds(seed_master + k, 3)
     return Workload("ising1024x3_k%d" % k, [1024] * 3, 32, k, [1 / T for T in Ts], [0.0] * 3, seeds,
                     schedules=10000, obs_every=10)
+
+
+def ising1024_all(seed_master: int = 1024) -> Workload:
+    """Every 1024^2 trajectory of the T x start x k grid as one batch of 18
+    replicas: T in {1.5, 2.269, 3.0}, random and all-up starts, k in {1, 4, 16},
+    1e4 palindromic schedules, observables every 10 schedules."""
+    Ts = [1.5, 2.269, 3.0]
+    L, ks, inits, beta, seeds = [], [], [], [], []
+    for k in (1, 4, 16):
+        sk = replica_seeds(seed_master + k, 3)
+        for init in (0, 1):
+            for T, sd in zip(Ts, sk):
+                L.append(1024)
+                ks.append(k)
+                inits.append(init)
+                beta.append(1 / T)
+                seeds.append(sd)
+    return Workload("ising1024x18", L, 32, 1, beta, [0.0] * len(L), seeds, schedules=10000, obs_every=10,
+                    ks=ks, inits=inits)
 
 
 def lattice_8192(seed: int = 8192) -> Workload:

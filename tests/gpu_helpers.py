@@ -6,13 +6,23 @@ from oracle import oracle as orc
 
 
 def run_both(L, Ld, k, seeds, beta, h, n_sched, *, law=0, init=0, schedule=0, time_mode=0,
-             obs_every=0, nu=1.0, J=1.0, launch=None, chunks=None):
+             obs_every=0, nu=1.0, J=1.0, launch=None, chunks=None, obs_per_pass=False):
     import paper_1403_4674_gb300 as kmc
-    lat = kmc.Lattice(L, Ld, k, seeds, init=init)
+    n = len(L)
+    ks = list(k) if isinstance(k, (list, tuple)) else [k] * n
+    inits = list(init) if isinstance(init, (list, tuple)) else [init] * n
+    per_replica = isinstance(k, (list, tuple)) or isinstance(init, (list, tuple))
+    lat = kmc.Lattice(L, Ld, ks[0], seeds, init=inits[0])
+    if per_replica:
+        # per-replica steps and starts in one context
+        lat.set_replica_params(k=ks, init=inits)
+        lat.reset(kmc.KMC_INIT_PER_REPLICA)
     if launch is not None:
         lat.set_launch(*launch)
         assert lat.launch()[0] == launch[0]
     lat.set_rates(beta, h, J=J, nu=nu, law=law)
+    if obs_per_pass:
+        lat.set_observation(kmc.KMC_OBS_PASS)
     chunks = chunks or [n_sched]
     obs_gpu = []
     for c in chunks:
@@ -29,11 +39,12 @@ def run_both(L, Ld, k, seeds, beta, h, n_sched, *, law=0, init=0, schedule=0, ti
 
     ref = {"spins": [], "hash": [], "flips": [], "t": [], "obs": []}
     for r in range(len(L)):
-        rep = orc.Replica(L=L[r], Ld=Ld, k=k, seed=seeds[r], beta=beta[r], h=h[r], J=J, nu=nu,
-                          law=law, init=init)
+        rep = orc.Replica(L=L[r], Ld=Ld, k=ks[r], seed=seeds[r], beta=beta[r], h=h[r], J=J, nu=nu,
+                          law=law, init=inits[r])
         obs_r = []
         for c in chunks:
-            o = rep.run(c, schedule=schedule, time_mode=time_mode, obs_every=obs_every)
+            o = rep.run(c, schedule=schedule, time_mode=time_mode, obs_every=obs_every,
+                        obs_per_pass=obs_per_pass)
             obs_r.append(o)
         ref["spins"].append(rep.spins.copy())
         ref["hash"].append(rep.hash.copy())

@@ -3,6 +3,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from paper_1403_4674_gb300 import _lib, build
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -41,3 +43,16 @@ def test_product_path_does_not_import_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 for bad in ("import oracle", "from oracle", "liborc", "kmc_oracle"):
                     assert bad not in src, (f, bad)
+
+
+def test_autotune_host_logic():
+    from paper_1403_4674_gb300 import autotune
+    assert autotune.max_domain_side(32) == 16
+    assert autotune.max_domain_side(48) == 8
+    assert autotune.max_domain_side(64) == 32
+    assert autotune.max_domain_side(128) == 64
+    assert autotune.max_domain_side(96, (8, 16)) == 16
+    with pytest.raises(ValueError):
+        autotune.max_domain_side(24)
+    plans = autotune.plan_candidates(152)
+    assert plans[0][0] == 0 and (2, 152, 16) in plans and (1, 16, 16) in plans

@@ -146,3 +146,45 @@ def test_profile_counts_run_kernel_launches():
     ms, n = lat.profile_read()
     assert n == 2 and ms > 0
     lat.close()
+
+
+@pytest.mark.parametrize("launch", [(1, 4, 16), (2, 152, 16)])
+def test_cuda_graph_replay_matches_eager(launch):
+    """reset + run captured in one CUDA graph (cluster launch or cooperative
+    launch inside) replays the eager trajectory bit for bit; calls that copy
+    from pageable memory or synchronise refuse to run while capturing."""
+    import torch
+    kmc = _kmc()
+    L, seeds = [128, 64], [7, 8]
+    lat = kmc.Lattice(L, 16, 4, seeds)
+    lat.set_launch(*launch)
+    lat.set_rates([0.44, 0.5], [0.0, 0.02])
+    obs_eager = lat.run(6, obs_every=2).clone()
+    lat.sync()
+    spins_eager = lat.spins.clone()
+    hash_eager = lat.domain_state()[0]
+
+    out = torch.empty_like(obs_eager)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            lat.reset(kmc.KMC_INIT_RANDOM)
+            lat.run(6, obs_every=2, out=out)
+            with pytest.raises(kmc.KmcError):
+                lat.set_rates([0.1, 0.1], [0.0, 0.0])
+    for _ in range(2):
+        lat.spins.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(lat.spins, spins_eager)
+        # e, m, e*m are integer sums; the clock column sums FP64 domain clocks
+        # with atomics, whose order may differ between runs
+        assert torch.equal(out[..., :3], obs_eager[..., :3])
+        torch.testing.assert_close(out[..., 3], obs_eager[..., 3], rtol=1e-12, atol=0)
+    # the context's host counters saw one captured run: resync them eagerly
+    lat.reset(kmc.KMC_INIT_RANDOM)
+    lat.run(6)
+    assert np.array_equal(lat.domain_state()[0], hash_eager)
+    lat.close()

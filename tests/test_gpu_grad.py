@@ -25,19 +25,22 @@ def _cuda():
 
 @pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
 @pytest.mark.parametrize("Ld,k", [(16, 4), (32, 16), (8, 40)])
-def test_score_parity_with_oracle(law, Ld, k):
+@pytest.mark.parametrize("per_pass", [False, True])
+def test_score_parity_with_oracle(law, Ld, k, per_pass):
     import paper_1403_4674_gb300 as kmc
     L = [4 * Ld, 6 * Ld]
     seeds, beta, h = [21, 22], [0.45, 0.4], [0.1, -0.05]
     lat = kmc.Lattice(L, Ld, k, seeds)
     lat.enable_grad(True)
     lat.set_rates(beta, h, law=law)
+    if per_pass:
+        lat.set_observation(kmc.KMC_OBS_PASS)
     obs = lat.run(6, obs_every=2).cpu().numpy()
     score = lat.score().cpu().numpy()
     for r in range(2):
         ref = orc.Replica(L=L[r], Ld=Ld, k=k, seed=seeds[r], beta=beta[r], h=h[r], law=law)
         ref.enable_score()
-        robs = ref.run(6, obs_every=2)
+        robs = ref.run(6, obs_every=2, obs_per_pass=per_pass)
         # the score does not change the trajectory
         assert np.array_equal(lat.replica_spins(r).cpu().numpy(), ref.spins)
         assert np.array_equal(obs[:, r, :3], robs[:, :3])

@@ -119,3 +119,72 @@ def test_config_8192_one_schedule():
     (a GRID plan: the bit state is larger than one cluster's shared memory)."""
     gpu, ref = run_both([8192], 64, 8, [8192], [1 / 2.269], [0.01], 1, obs_every=1)
     assert_parity(gpu, ref, 1)
+
+
+@pytest.mark.parametrize("launch", [None, (CLUSTER, 4, 16), (GRID, 152, 16), (GRID, 5, 4)])
+@pytest.mark.parametrize("time_mode", [orc.TIME_EXPONENTIAL, orc.TIME_EXPECTED])
+def test_per_replica_steps_and_starts(launch, time_mode):
+    """One context, replicas with their own k and start (random, all-up, kept):
+    each replica's trajectory is the one the oracle runs for it alone."""
+    L = [64, 128, 64, 96, 128, 64]
+    ks = [16, 1, 4, 1, 16, 7]
+    inits = [orc.INIT_RANDOM, orc.INIT_ALL_UP, orc.INIT_RANDOM, orc.INIT_ALL_UP, orc.INIT_RANDOM, orc.INIT_ALL_UP]
+    seeds = [31, 32, 33, 34, 35, 36]
+    beta = [1 / 1.5, 1 / 2.269, 1 / 3.0, 1 / 1.5, 1 / 2.269, 1 / 3.0]
+    gpu, ref = run_both(L, 16, ks, seeds, beta, [0.0, 0.01, -0.02, 0.0, 0.03, 0.0], 6, init=inits,
+                        obs_every=2, launch=launch, time_mode=time_mode)
+    assert_parity(gpu, ref, len(L))
+    # Eq. 11: steps = visits * k * N_D per replica
+    steps = gpu["observables"]["steps"]
+    for r in range(len(L)):
+        assert steps[r] == 6 * 2 * ks[r] * (L[r] // 16) ** 2
+
+
+def test_per_replica_keep_leaves_spins():
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    lat = kmc.Lattice([64, 64], 16, 2, [5, 6], init=kmc.KMC_INIT_RANDOM)
+    lat.run(3)
+    lat.sync()
+    before = lat.replica_spins(0).clone()
+    lat.set_replica_params(init=[kmc.KMC_INIT_KEEP, kmc.KMC_INIT_ALL_UP])
+    lat.reset(kmc.KMC_INIT_PER_REPLICA)
+    lat.sync()
+    assert torch.equal(lat.replica_spins(0), before)
+    assert bool((lat.replica_spins(1) == 1).all())
+    # k may change only before the first run after a reset
+    lat.set_replica_params(k=[3, 1])
+    lat.run(1)
+    with pytest.raises(kmc.KmcError):
+        lat.set_replica_params(k=[1, 1])
+    lat.close()
+
+
+@pytest.mark.parametrize("launch", [(GRID, 152, 16), (GRID, 5, 4), (GRID, 40, 2), (CLUSTER, 2, 16)])
+def test_plans_without_observation_points(launch):
+    """No observation point means no replica-wide barrier in the launch: the
+    write-back at the end must still wait for every warp's last visit."""
+    L = [128, 64, 96]
+    gpu, ref = run_both(L, 16, [4, 1, 9], [21, 22, 23], [0.5, 0.4, 0.3], [0.0, 0.02, -0.01], 6, launch=launch)
+    assert_parity(gpu, ref, len(L), obs=False)
+    gpu, ref = run_both(L, 16, 3, [24, 25, 26], [0.5, 0.4, 0.3], [0.0, 0.02, -0.01], 7,
+                        schedule=orc.SCHED_RANDOM_PERM, launch=launch)
+    assert_parity(gpu, ref, len(L), obs=False)
+
+
+@pytest.mark.parametrize("launch", [None, (GRID, 152, 16), (CLUSTER, 4, 8)])
+@pytest.mark.parametrize("schedule,time_mode", [(orc.SCHED_PALINDROME, orc.TIME_EXPONENTIAL),
+                                                (orc.SCHED_PALINDROME, orc.TIME_EXPECTED),
+                                                (orc.SCHED_RANDOM_PERM, orc.TIME_EXPONENTIAL)])
+@pytest.mark.parametrize("obs_every", [1, 3])
+def test_register_shifted_endpoints(launch, schedule, time_mode, obs_every):
+    """Records after colour passes (Sec. 2.3 register-shifted endpoints),
+    built on the device from per-visit changes, equal the oracle's full
+    recomputation after the same passes."""
+    L = [64, 96, 128]
+    gpu, ref = run_both(L, 16, [3, 1, 5], [41, 42, 43], [0.5, 0.35, 0.44], [0.03, 0.0, -0.02], 5,
+                        obs_every=obs_every, launch=launch, schedule=schedule, time_mode=time_mode,
+                        obs_per_pass=True, chunks=[2, 3])
+    assert_parity(gpu, ref, len(L))
+    passes = 8 if schedule == orc.SCHED_PALINDROME else 4
+    assert gpu["obs"].shape[0] == (2 * passes) // obs_every + (3 * passes) // obs_every

@@ -169,3 +169,35 @@ def test_invalid_domain_counts_rejected():
         orc.Replica(L=24, Ld=8, k=1, seed=1, beta=0.5).run(1)  # 3 domains per side
     with pytest.raises(ValueError):
         orc.Replica(L=12, Ld=6, k=1, seed=1, beta=0.5).run(1)  # n_d = 36 not 2^m
+
+
+def test_pass_records_contain_schedule_records():
+    """Every 8th colour-pass record of a palindromic run is the schedule record."""
+    a = orc.Replica(L=16, Ld=4, k=2, seed=3, beta=0.4, h=0.05)
+    b = orc.Replica(L=16, Ld=4, k=2, seed=3, beta=0.4, h=0.05)
+    per_pass = a.run(5, obs_every=1, obs_per_pass=True)
+    per_sched = b.run(5, obs_every=1)
+    assert per_pass.shape == (40, 4)
+    np.testing.assert_array_equal(per_pass[7::8], per_sched)
+
+
+def test_register_shifted_endpoints_sample_equilibrium():
+    """Sec. 2.3: the end of every colour pass is a valid observation point.
+    At equilibrium the mean energy observed after each of the 8 passes of the
+    palindrome (also mid-schedule) matches the exact <H>/N of the 4x4 lattice."""
+    from oracle.enumerate import Enumerator
+    L, Ld, k, beta, h = 4, 2, 3, 0.4, 0.1
+    E = Enumerator(L, Ld, k, beta=beta, h=h, quantised=False)
+    exact = float(E.pi @ E.H) / (L * L)
+    recs = []
+    for r in range(32):
+        rep = orc.Replica(L=L, Ld=Ld, k=k, seed=5000 + r, beta=beta, h=h)
+        rep.run(20)
+        recs.append(rep.run(600, obs_every=1, obs_per_pass=True)[:, 0].reshape(600, 8))
+    e = np.stack(recs)  # [replica, schedule, pass]
+    for p in range(8):
+        x = e[:, :, p]
+        # batch means over replicas give the error bar
+        means = x.mean(axis=1)
+        err = means.std(ddof=1) / np.sqrt(len(means))
+        assert abs(x.mean() - exact) < 4.5 * err + 1e-3, (p, x.mean(), exact, err)
