@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the batched and gradient variants")
+    ap.add_argument("--plan", default="", help="launch plan mode,size,warps (skips the plan tuning)")
     return ap.parse_args()
 
 
@@ -360,7 +361,11 @@ def main():
     lat.reset(reset_mode)
     lat.set_rates(w.beta, w.h)
     t0 = time.perf_counter()
-    plan, trials = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=200 if w.L[0] <= 1024 else 2)
+    if args.plan:
+        plan = tuple(int(x) for x in args.plan.split(","))
+        lat.set_launch(*plan)
+    else:
+        plan, _ = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=200 if w.L[0] <= 1024 else 2)
     tune_s = time.perf_counter() - t0
     lat.profile(True)
     n_obs = w.schedules // w.obs_every if w.obs_every > 0 else 0

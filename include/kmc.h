@@ -46,7 +46,7 @@ typedef enum {
     KMC_ENOMEM = -2,       /* device or host allocation failed */
     KMC_ECUDA = -3,        /* a CUDA runtime call failed */
     KMC_ENOTBALANCED = -4, /* rate table violates detailed balance */
-    KMC_ETIMEOUT = -5,     /* a bounded device wait (phase barrier) gave up */
+    KMC_ETIMEOUT = -5,     /* a bounded device wait (neighbour's visit) gave up */
     KMC_EDEVICE = -6       /* device error word set (e.g. a spin not +-1) */
 } kmc_status;
 
@@ -234,7 +234,8 @@ kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, ui
  *     counters through L2.
  * In both plans a visit starts as soon as its four neighbours have finished
  * their visits of earlier colour phases (per-domain dataflow instead of a
- * barrier per phase); observation points synchronise the whole replica.
+ * barrier per phase); observation records are built from per-visit changes,
+ * so no point of a launch synchronises a whole replica.
  * warps_per_cta: 1..16.  Returns KMC_EINVAL if the plan cannot be scheduled
  * or the state does not fit in shared memory; the previous plan then stays.
  * Results do not depend on the plan. */
@@ -247,8 +248,7 @@ kmc_status kmc_get_launch(const kmc_ctx *ctx, int32_t *mode, int32_t *size, int3
 
 /* Test hook for the bounded waits of the run kernel.  A domain visit waits
  * (bounded spin) until its four neighbours have completed their earlier
- * visits; GRID plans also use a bounded grid barrier at observation points.
- * With extra > 0 every visit waits for `extra` more neighbour visits than
+ * visits.  With extra > 0 every visit waits for `extra` more neighbour visits than
  * will ever come, so the waits give up after limit_ns nanoseconds and the
  * next kmc_sync returns KMC_ETIMEOUT; the context stays usable.  extra = 0
  * restores normal waits; limit_ns = 0 restores the default limit (2 s). */

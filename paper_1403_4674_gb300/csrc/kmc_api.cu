@@ -1,7 +1,7 @@
 // kmc_api.cu -- host side of the C ABI declared in include/kmc.h.
 //
 // Owns the library's device scratch (bit tiles, edges, per-domain counters,
-// launch plan, rate tables, barrier counter, error word), validates
+// launch plan, rate tables, error word), validates
 // arguments, builds the fixed-point rate table on the host, plans which CTA
 // (and which thread-block cluster) owns which domain, and enqueues the
 // kernels of kmc_kernels.cuh on the caller's stream.
@@ -62,7 +62,6 @@ struct kmc_ctx {
     double *d_grad = nullptr, *d_h = nullptr;
     uint8_t *d_tiles = nullptr;
     uint64_t *d_edges = nullptr, *d_dctr = nullptr;
-    unsigned *d_bar = nullptr;
     int *d_err = nullptr;
     unsigned long long *d_obs_acc = nullptr;
     size_t obs_acc_words = 0;
@@ -260,7 +259,6 @@ RunParams run_params(kmc_ctx *c)
     P.tiles = c->d_tiles;
     P.dctr = c->d_dctr;
     P.edges = c->d_edges;
-    P.bar_count = c->d_bar;
     P.err = c->d_err;
     P.bar_limit_ns = c->bar_limit_ns;
     P.debug_extra = c->debug_extra;
@@ -675,7 +673,7 @@ kmc_status check_device_error(kmc_ctx *c)
     if (e == 0) return KMC_OK;
     int zero = 0;
     CUDA_TRY(c, cudaMemcpy(c->d_err, &zero, sizeof zero, cudaMemcpyHostToDevice));
-    if (e == ERR_TIMEOUT) return fail(c, KMC_ETIMEOUT, "a phase barrier gave up waiting (bounded wait)");
+    if (e == ERR_TIMEOUT) return fail(c, KMC_ETIMEOUT, "a bounded wait for a neighbour's visit gave up");
     if (e == ERR_SPIN) return fail(c, KMC_EDEVICE, "spin buffer holds a byte that is not +1 or -1");
     return fail(c, KMC_EDEVICE, "device error word %d", e);
 }
@@ -691,7 +689,7 @@ void free_all(kmc_ctx *c)
     void **ptrs[] = {(void **)&c->d_L, (void **)&c->d_Dx, (void **)&c->d_k, (void **)&c->d_init, (void **)&c->d_dom_off, (void **)&c->d_dom_rep,
                      (void **)&c->d_site_off, (void **)&c->d_blk_off, (void **)&c->d_seed, (void **)&c->d_A,
                      (void **)&c->d_inv, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_tiles,
-                     (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_bar, (void **)&c->d_err,
+                     (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_err,
                      (void **)&c->d_obs_acc, (void **)&c->d_tmp, (void **)&c->d_plan};
     for (void **p : ptrs) {
         if (*p) cudaFree(*p);
@@ -821,7 +819,6 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     ALLOC(c->d_tiles, ndom * tile);
     ALLOC(c->d_edges, ndom * EDGE_WORDS);
     ALLOC(c->d_dctr, ndom * DCTR_WORDS);
-    ALLOC(c->d_bar, 1);
     ALLOC(c->d_err, 1);
     {
         uint8_t *tmp = nullptr;
@@ -1086,9 +1083,9 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
         CUDA_TRY(c, cudaMemsetAsync(c->d_obs_acc, 0, words * 8, s));
     }
     if ((st = launch_pack(c, s)) != KMC_OK) return st;
+    // records are built from the state before the launch plus per-visit changes
     unsigned long long *base = reinterpret_cast<unsigned long long *>(c->d_tmp);
-    if (pass_obs && n_obs > 0 && (st = launch_observe(c, s, time_mode == KMC_TIME_EXPONENTIAL, base)) != KMC_OK)
-        return st;
+    if (n_obs > 0 && (st = launch_observe(c, s, time_mode == KMC_TIME_EXPONENTIAL, base)) != KMC_OK) return st;
     RunParams P = run_params(c);
     P.schedule = schedule;
     P.obs_every = want_obs ? obs_every : 0;
@@ -1123,7 +1120,6 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
         cfg.numAttrs = 1;
         CUDA_TRY(c, cudaLaunchKernelEx(&cfg, kern, P));
     } else {
-        CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), s));
         void *args[] = {(void *)&P};
         CUDA_TRY(c, cudaLaunchCooperativeKernel((const void *)kern, dim3(pl.n_cta), dim3(pl.wpb * 32), args, pl.smem, s));
     }
@@ -1133,15 +1129,8 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
         c->prof_events.emplace_back(ev0, ev1);
     }
     if (want_obs && n_obs > 0) {
-        if (pass_obs) {
-            finalize_pass_obs_kernel<<<grid_for(c->n_rep, 128), 128, 0, s>>>(base, c->d_obs_acc, n_obs, c->n_rep, c->d_L,
-                                                                             c->d_Dx, c->J, c->d_h, obs_dev,
-                                                                             c->grad ? 6 : 4);
-        } else {
-            const int n_rec = (int)(n_obs * c->n_rep);
-            finalize_obs_kernel<<<grid_for(n_rec, 256), 256, 0, s>>>(c->d_obs_acc, n_rec, c->n_rep, c->d_L, c->d_Dx,
-                                                                      c->J, c->d_h, obs_dev, c->grad ? 6 : 4);
-        }
+        finalize_obs_kernel<<<grid_for(c->n_rep, 128), 128, 0, s>>>(base, c->d_obs_acc, n_obs, c->n_rep, c->d_L, c->d_Dx,
+                                                                    c->J, c->d_h, obs_dev, c->grad ? 6 : 4);
         ++c->launches;
         CUDA_TRY(c, cudaGetLastError());
     }
@@ -1329,7 +1318,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
         c.d_grad = cv.take<double>(32);
         c.d_h = cv.take<double>(1);
         c.d_err = cv.take<int>(1);
-        c.d_bar = cv.take<unsigned>(1);
+        c.d_tmp = cv.take<unsigned long long>(OBS_WORDS); // observation base of the replica
     };
     Carver measure{nullptr};
     carve(measure);
@@ -1388,10 +1377,15 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     if ((st = launch_reset_counters(&c, s)) != KMC_OK) return bad(st, c.err);
     if (n_schedules > 0) {
         if ((st = launch_pack(&c, s)) != KMC_OK) return bad(st, c.err);
+        if (n_obs > 0 &&
+            (st = launch_observe(&c, s, time_mode == KMC_TIME_EXPONENTIAL,
+                                 reinterpret_cast<unsigned long long *>(c.d_tmp))) != KMC_OK)
+            return bad(st, c.err);
         RunParams P = run_params(&c);
         P.schedule = schedule;
         P.obs_every = n_obs > 0 ? obs_every : 0;
         P.obs_acc = n_obs > 0 ? c.d_obs_acc : nullptr;
+        P.n_obs = n_obs;
         P.sched_begin = sched_begin;
         P.n_sched = n_schedules;
         P.visits_before = 0;
@@ -1411,9 +1405,8 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
         ce = cudaLaunchKernelEx(&cfg, kern, P);
         if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("cudaLaunchKernelEx: ") + cudaGetErrorString(ce));
         if (n_obs > 0) {
-            const int n_rec = (int)n_obs;
-            finalize_obs_kernel<<<grid_for(n_rec, 256), 256, 0, s>>>(c.d_obs_acc, n_rec, 1, c.d_L, c.d_Dx, J, c.d_h,
-                                                                      obs_dev, 4);
+            finalize_obs_kernel<<<1, 32, 0, s>>>(reinterpret_cast<unsigned long long *>(c.d_tmp), c.d_obs_acc, n_obs, 1,
+                                                 c.d_L, c.d_Dx, J, c.d_h, obs_dev, 4);
             ce = cudaGetLastError();
             if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("finalize: ") + cudaGetErrorString(ce));
         }
@@ -1424,7 +1417,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     // the kmc_ctx destructor must not free the static array
     c.d_L = nullptr; c.d_Dx = nullptr; c.d_k = nullptr; c.d_dom_off = nullptr; c.d_dom_rep = nullptr; c.d_site_off = nullptr;
     c.d_blk_off = nullptr; c.d_seed = nullptr; c.d_A = nullptr; c.d_inv = nullptr; c.d_grad = nullptr; c.d_h = nullptr;
-    c.d_tiles = nullptr; c.d_edges = nullptr; c.d_dctr = nullptr; c.d_bar = nullptr; c.d_err = nullptr;
+    c.d_tiles = nullptr; c.d_edges = nullptr; c.d_dctr = nullptr; c.d_tmp = nullptr; c.d_err = nullptr;
     c.d_obs_acc = nullptr; c.d_plan = nullptr;
     if (st != KMC_OK) return bad(st, c.err);
     noalloc_message(err, err_len, "");

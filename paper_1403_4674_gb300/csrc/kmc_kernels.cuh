@@ -18,15 +18,18 @@
 //
 // The run kernel is persistent: every CTA owns a fixed set of domains (its
 // "slots") for the whole launch; their tiles, edges, counters and the rate
-// tables of their replicas live in shared memory.  Between colour phases the
-// only communication is the frozen halo (Sec. 2.2) -- the four edge words of
-// each neighbour:
+// tables of their replicas live in shared memory.  The only communication
+// between domains is the frozen halo (Sec. 2.2) -- the four edge words of
+// each neighbour, stamped with the neighbour's visit count, so a visit starts
+// as soon as its neighbours have finished their visits of earlier colour
+// phases (no barrier per phase, no barrier at observation points):
 //   * CLUSTER mode: every replica is resident in one thread-block cluster
 //     (1..16 CTAs); halos are read from the owner CTA through distributed
-//     shared memory and phases are separated by the hardware cluster barrier;
+//     shared memory;
 //   * GRID mode (a replica larger than a cluster can hold): one cooperative
-//     grid; halos go through L2 and phases are separated by a bounded grid
-//     barrier.
+//     grid; halos go through L2.
+// Observation records are sums of per-visit changes (bond sum, magnetisation,
+// clock, scores) added to the state before the launch.
 #pragma once
 
 #include <cstdint>
@@ -52,9 +55,14 @@ constexpr int OBS_WORDS = 5; // bonds, mag, clock sum, score beta sum, score h s
 //   [512] seed, [520] dom_off, [524] Dx, [528] k (steps per visit).
 constexpr int RT_BYTES = 544;
 constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524, RT_K = 528;
-// Slot: [tile][stamped edges 64][counters 48][meta 32];
-// meta u32: g, replica, d, rt, nb[4].
-constexpr int SLOT_EXTRA = 64 + 48 + 32;
+// Slot: [tile][stamped edges 64][counters 48][meta 32][observation 48];
+// meta u32: g, replica, d, rt, nb[4];
+// observation, since the record began: u32 record, i32 bond change, i32
+// magnetisation change, u32 steps (EXPECTED clock), u64 mantissa and i64
+// exponent of the product of clock variates (EXPONENTIAL clock), f64 score
+// changes d/dbeta, d/dh.
+constexpr int SLOT_EXTRA = 64 + 48 + 32 + 48;
+constexpr uint32_t NO_RECORD = 0xFFFFFFFFu;
 constexpr int EDGE_WORDS = 8; // stamped 64-bit words per domain
 
 __host__ __device__ constexpr uint64_t stamp(uint32_t count, uint32_t half)
@@ -99,8 +107,6 @@ struct RunParams {
     unsigned long long *obs_acc;
     int obs_pass;   // 1: a record after every obs_every-th colour pass
     int64_t n_obs;  // records of this launch
-    // grid barrier
-    unsigned *bar_count;
     int *err;
     uint64_t bar_limit_ns;
     int debug_extra;
@@ -136,12 +142,6 @@ __device__ __forceinline__ uint64_t global_ns()
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
 }
 // distributed shared memory (thread-block clusters)
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -286,6 +286,63 @@ template <int LD> struct Planes {
         }
     }
 
+    // Bit-sliced +1 / -1 of the up-neighbour count of the sites in mask m of
+    // row t (the count stays within 0..4).
+    __device__ __forceinline__ void inc(int t, row_t m)
+    {
+        const row_t c0 = b0[t] & m;
+        b0[t] ^= m;
+        const row_t c1 = b1[t] & c0;
+        b1[t] ^= c0;
+        b2[t] ^= c1;
+    }
+    __device__ __forceinline__ void dec(int t, row_t m)
+    {
+        const row_t d0 = (row_t)~b0[t] & m;
+        b0[t] ^= m;
+        const row_t d1 = (row_t)~b1[t] & d0;
+        b1[t] ^= d0;
+        b2[t] ^= d1;
+    }
+
+    // Counts from the domain's own spins only (halo taken as down); the halo
+    // is added by add_halo once it has arrived, so a warp builds this part
+    // while it waits for its neighbours.
+    __device__ __forceinline__ void build_interior(int lane) { build(lane, (row_t)0, (row_t)0, 0ull, 0ull); }
+
+    // Add the frozen halo's up spins: the N row to row 0, the S row to row
+    // LD-1, the W and E columns to columns 0 and LD-1 (a corner site takes two
+    // halo neighbours, hence two additions).
+    __device__ __forceinline__ void add_halo(int lane, row_t hN, row_t hS, uint64_t hW, uint64_t hE)
+    {
+#pragma unroll
+        for (int t = 0; t < G::RPL; ++t) {
+            const int y = lane * G::RPL + t;
+            const int cb = (y % G::RPL) * 32 + y / G::RPL;
+            const row_t mrow = (y == 0) ? hN : ((y == LD - 1) ? hS : (row_t)0);
+            const row_t mcol = (row_t)((hW >> cb) & 1ull) | (row_t)(((hE >> cb) & 1ull) << (LD - 1));
+            inc(t, mrow);
+            inc(t, mcol);
+        }
+    }
+
+    // After the spin at (y, col) flipped: its in-domain neighbours (row y at
+    // col-1 and col+1, rows y-1 and y+1 at col) gain an up neighbour if the
+    // spin is now up, else lose one.  Bit-sliced +-1 on the count planes;
+    // halo neighbours are outside the domain and unchanged.
+    __device__ __forceinline__ void flip_update(int lane, int y, int col, bool now_up)
+    {
+        const row_t bitc = (row_t)1 << col;
+        const row_t mh = (row_t)(((col > 0) ? (bitc >> 1) : (row_t)0) | ((col < LD - 1) ? (bitc << 1) : (row_t)0));
+#pragma unroll
+        for (int t = 0; t < G::RPL; ++t) {
+            const int yy = lane * G::RPL + t;
+            const row_t m = (yy == y) ? mh : ((yy == y - 1 || (yy == y + 1 && yy < LD)) ? bitc : (row_t)0);
+            if (now_up) inc(t, m);
+            else dec(t, m);
+        }
+    }
+
     // Sites of one class in row t.  The class c = 5*up + q is given as masks:
     // UP all ones for up spins, Q2/Q1/Q0 all ones where the bit of q is set.
     __device__ __forceinline__ row_t mask_q(int t, row_t UP, row_t Q2, row_t Q1, row_t Q0) const
@@ -356,6 +413,82 @@ struct Counters {
 };
 
 // ---------------------------------------------------------------------------
+// The random numbers of 32 consecutive steps of a visit (lane i: step base+i)
+// and the product of their clock variates.  They depend only on the replica
+// seed, the domain and the counters, so a warp draws the first chunk of a
+// visit before it waits for the halo.
+// ---------------------------------------------------------------------------
+struct Chunk {
+    uint64_t tgt;   // step target, ~0 past the visit's last step
+    uint64_t ebase; // np << 32 | j << 16: the step's event word without the site
+    uint64_t m;     // clock: product of the chunk's variates, mantissa in [2^63, 2^64)
+    int e;          // and its binary exponent (warp-uniform)
+};
+
+template <bool EXPO>
+__device__ __forceinline__ Chunk draw_chunk(uint2 key, uint32_t d, uint64_t np0, int base, int total, int k,
+                                            int lane)
+{
+    Chunk ch;
+    const int s = base + lane;
+    ch.tgt = ~0ull;
+    ch.ebase = 0;
+    uint64_t V = 1ull << 53;
+    if (s < total) {
+        const int f = s / k;
+        const int j = s - f * k;
+        const uint64_t np = np0 + (uint64_t)f;
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)j, d, (uint32_t)np, (uint32_t)(np >> 32) & 0xFFFFFFu), key);
+        ch.tgt = (((uint64_t)w.y << 32) | w.x) >> 1;
+        V = ((((uint64_t)w.w << 32) | w.z) >> 11) + 1ull;
+        ch.ebase = (np << 32) | ((uint64_t)j << 16); // site bits added on a flip
+    }
+    ch.m = 1ull << 63;
+    ch.e = 0;
+    if (EXPO) {
+        // product of this chunk's variates: butterfly over the smallest power of
+        // two covering the chunk (lanes past its end hold v = 1)
+        const int chunk_end = min(32, total - base);
+        const int z = __clzll((long long)V);
+        uint64_t m = V << z;
+        int e = 10 - z;
+        for (int off = 1; off < chunk_end; off <<= 1) {
+            const uint64_t m2 = __shfl_xor_sync(FULL_WARP, m, off);
+            const int e2 = __shfl_xor_sync(FULL_WARP, e, off);
+            mant_mul32(m, e, m2, e2);
+        }
+        ch.m = __shfl_sync(FULL_WARP, m, 0);
+        ch.e = __shfl_sync(FULL_WARP, e, 0);
+    }
+    return ch;
+}
+
+// Lane c (< 10) holds class c's fixed-point rate, its reciprocal and (scores)
+// a_c, dlog a_c/dbeta, dlog a_c/dh; loaded before the halo wait.
+struct RateRegs {
+    uint64_t A, inv;
+    double a, gb, gh;
+};
+
+template <bool GRAD>
+__device__ __forceinline__ RateRegs load_rates(const uint8_t *rt, int lane)
+{
+    RateRegs r = {0ull, 0ull, 0.0, 0.0, 0.0};
+    if (lane < 10) {
+        r.A = reinterpret_cast<const uint64_t *>(rt)[lane];
+        r.inv = reinterpret_cast<const uint64_t *>(rt + 128)[lane];
+        if (GRAD) {
+            const double *gr = reinterpret_cast<const double *>(rt + 256);
+            r.a = gr[lane];
+            r.gb = gr[10 + lane];
+            r.gh = gr[20 + lane];
+        }
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // One domain visit (Sec. 2.2): nfused consecutive global phases of the same
 // colour, k uniformised steps each, with the halo hN/hS/hW/hE frozen.
 //
@@ -370,28 +503,16 @@ struct Counters {
 // events.  rt: the replica table in shared memory.
 // ---------------------------------------------------------------------------
 template <int LD, bool EXPO, bool GRAD>
-__device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const uint8_t *rt,
+__device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const RateRegs &rr, uint2 key,
                                            typename Geo<LD>::row_t hN, typename Geo<LD>::row_t hS,
                                            uint64_t hW, uint64_t hE, uint32_t d, uint64_t np0,
-                                           int nfused, int k, int lane, int *err)
+                                           int nfused, int k, int lane, int *err, const Chunk &first)
 {
     using G = Geo<LD>;
     using row_t = typename G::row_t;
-    const uint64_t seed = *reinterpret_cast<const uint64_t *>(rt + RT_SEED);
-    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    uint64_t Ac = 0, invc = 0;
-    double a_c = 0.0, gb_c = 0.0, gh_c = 0.0;
-    if (lane < 10) {
-        Ac = reinterpret_cast<const uint64_t *>(rt)[lane];
-        invc = reinterpret_cast<const uint64_t *>(rt + 128)[lane];
-        if (GRAD) {
-            const double *gr = reinterpret_cast<const double *>(rt + 256);
-            a_c = gr[lane];
-            gb_c = gr[10 + lane];
-            gh_c = gr[20 + lane];
-        }
-    }
-    pl.build(lane, hN, hS, hW, hE);
+    const uint64_t Ac = rr.A, invc = rr.inv;
+    const double a_c = rr.a, gb_c = rr.gb, gh_c = rr.gh;
+    pl.add_halo(lane, hN, hS, hW, hE); // pl holds the interior counts
     uint32_t n_c = class_counts<LD>(pl, lane);
     uint64_t Wc = (uint64_t)n_c * Ac;
     uint64_t Cinc = prefix16(Wc, lane);
@@ -411,36 +532,13 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const u
 
     const int total = nfused * k;
     for (int base = 0; base < total; base += 32) {
-        const int s = base + lane;
-        uint64_t tgt = ~0ull;
-        uint64_t V = 1ull << 53;
-        uint64_t ebase = 0;
-        if (s < total) {
-            const int f = s / k;
-            const int j = s - f * k;
-            const uint64_t np = np0 + (uint64_t)f;
-            const uint4 w = philox4x32_10(
-                make_uint4((uint32_t)j, d, (uint32_t)np, (uint32_t)(np >> 32) & 0xFFFFFFu), key);
-            tgt = (((uint64_t)w.y << 32) | w.x) >> 1;
-            V = ((((uint64_t)w.w << 32) | w.z) >> 11) + 1ull;
-            ebase = (np << 32) | ((uint64_t)j << 16); // event word of this step, site bits added on a flip
-        }
+        const Chunk ch = (base == 0) ? first : draw_chunk<EXPO>(key, d, np0, base, total, k, lane);
+        const uint64_t tgt = ch.tgt, ebase = ch.ebase;
         const int chunk_end = min(32, total - base);
+        const bool last_chunk = base + 32 >= total;
         if (EXPO) {
-            // product of this chunk's variates: butterfly over the smallest power of
-            // two covering the chunk (lanes past its end hold v = 1)
-            const int z = __clzll((long long)V);
-            uint64_t m = V << z;
-            int e = 10 - z;
-            for (int off = 1; off < chunk_end; off <<= 1) {
-                const uint64_t m2 = __shfl_xor_sync(FULL_WARP, m, off);
-                const int e2 = __shfl_xor_sync(FULL_WARP, e, off);
-                mant_mul32(m, e, m2, e2);
-            }
-            m = __shfl_sync(FULL_WARP, m, 0);
-            e = __shfl_sync(FULL_WARP, e, 0);
-            mant_mul(cn.clkM, cn.clkE, m, (int64_t)e);
-            mant_mul(cn.vM, cn.vE, m, (int64_t)e);
+            mant_mul(cn.clkM, cn.clkE, ch.m, (int64_t)ch.e);
+            mant_mul(cn.vM, cn.vE, ch.m, (int64_t)ch.e);
         }
         int pos = 0;
         while (true) {
@@ -523,13 +621,15 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const u
                 if (lane * G::RPL + tt == y) pl.S[tt] ^= (row_t)1 << col;
             cn.H = (cn.H ^ (ev | (uint64_t)(y * LD + col))) * HASH_PRIME;
             ++cn.flips;
-            pl.build(lane, hN, hS, hW, hE);
+            pos = jx + 1;
+            // the classes are needed again only if a step of this visit remains
+            if (last_chunk && pos >= chunk_end) break;
+            pl.flip_update(lane, y, col, c < 5);
             n_c = class_counts<LD>(pl, lane);
             Wc = (uint64_t)n_c * Ac;
             Cinc = prefix16(Wc, lane);
             R = __shfl_sync(FULL_WARP, Cinc, 9);
             grad_state();
-            pos = jx + 1;
         }
     }
 }
@@ -620,40 +720,6 @@ __device__ __forceinline__ void domain_bonds_mag(const typename Geo<LD>::row_t (
     mag = (int)__reduce_add_sync(FULL_WARP, (unsigned)m);
 }
 
-// ---------------------------------------------------------------------------
-// Bounded grid barrier (GRID mode).  Thread 0 of every CTA arrives on a
-// monotone counter and spins (acquire loads) until all CTAs of barrier `no`
-// arrived, or until the limit expires / another CTA reported an error.
-// Returns false on error; the caller then leaves the kernel.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_barrier(const RunParams &P, unsigned &no, int *s_ok)
-{
-    __syncthreads();
-    ++no;
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned target = no * gridDim.x + (unsigned)P.debug_extra;
-        __threadfence();
-        atomicAdd(P.bar_count, 1u);
-        const uint64_t t0 = global_ns();
-        unsigned spins = 0;
-        while (ld_acquire(P.bar_count) < target) {
-            if ((++spins & 255u) == 0) {
-                if (*(volatile int *)P.err != 0) { ok = 0; break; }
-                if (global_ns() - t0 > P.bar_limit_ns) {
-                    atomicCAS(P.err, 0, ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
-}
-
 // Colour order of schedule n for replica seed (RANDOM_PERM), Lehmer decode of
 // floor(x * 24 / 2^64), x = w0 | w1 << 32 of Philox {0, 0, n_lo, n_hi | TAG_PERM << 24}.
 __device__ __forceinline__ int perm_colour(uint64_t seed, uint64_t n, int p)
@@ -696,12 +762,11 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
     using mem_t = typename G::mem_t;
     constexpr int TB = G::TILE_BYTES;
     constexpr int SB = slot_bytes<LD>();
-    constexpr int OFF_EDGE = TB, OFF_CTR = TB + 64, OFF_META = TB + 112;
+    constexpr int OFF_EDGE = TB, OFF_CTR = TB + 64, OFF_META = TB + 112, OFF_OBS = TB + 144;
     // stamped words a halo read needs per neighbour: one half for LD <= 32, two for 64
     constexpr int HALVES = (LD > 32) ? 2 : 1;
 
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_ok;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -741,6 +806,11 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         if (lane < DCTR_WORDS)
             reinterpret_cast<uint64_t *>(sl + OFF_CTR)[lane] = P.dctr[(size_t)g * DCTR_WORDS + lane];
         uint32_t *meta = reinterpret_cast<uint32_t *>(sl + OFF_META);
+        if (lane < 6) {
+            // observation accumulators: no record yet, changes zero, clock product 1
+            uint64_t *ob = reinterpret_cast<uint64_t *>(sl + OFF_OBS);
+            ob[lane] = (lane == 0) ? (uint64_t)NO_RECORD : (lane == 2) ? (1ull << 63) : 0ull;
+        }
         if (lane == 0) {
             meta[META_G] = g;
             meta[META_R] = r;
@@ -757,8 +827,9 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                 meta[META_NB + lane] = nb;
             }
         }
-        if (CLUSTER) {
-            // edges of the staged tile, stamped with visit count 0
+        {
+            // edges of the staged tile, stamped with visit count 0 (the slot's
+            // copy; in GRID mode the global copy is the one neighbours read)
             row_t S[G::RPL];
             const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
 #pragma unroll
@@ -826,36 +897,105 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
     };
 
     // One visit; publishes the slot's edges, then (release) its visit count.
-    auto visit = [&](uint8_t *sl, uint64_t np0, int nf, uint64_t hN, uint64_t hS, uint64_t hW, uint64_t hE,
-                     uint32_t count_after, int64_t pass) {
+    const int nph = (P.schedule == SCHED_PALINDROME) ? 8 : 4; // colour passes per schedule
+
+    // A slot's summed changes of one record go to the replica's record (lane
+    // 0 of the warp; records past the launch's last one are dropped).
+    auto flush_record = [&](const uint8_t *sl, uint32_t rep) {
+        const uint32_t *ob = reinterpret_cast<const uint32_t *>(sl + OFF_OBS);
+        const double *obd = reinterpret_cast<const double *>(sl + OFF_OBS + 32);
+        const uint64_t *obm = reinterpret_cast<const uint64_t *>(sl + OFF_OBS + 16);
+        const uint32_t o = ob[0];
+        if (o == NO_RECORD || (int64_t)o >= P.n_obs) return;
+        unsigned long long *acc = P.obs_acc + ((size_t)o * P.n_rep + rep) * OBS_WORDS;
+        if (ob[1] != 0) atomicAdd(&acc[0], (unsigned long long)(long long)(int)ob[1]);
+        if (ob[2] != 0) atomicAdd(&acc[1], (unsigned long long)(long long)(int)ob[2]);
+        // the record's clock advance of this domain: one logarithm per record
+        const double dt = EXPO ? domain_time(true, obm[0], (int64_t)obm[1], 0, P.lambda)
+                               : __ddiv_rn((double)ob[3], P.lambda);
+        atomicAdd(reinterpret_cast<double *>(&acc[2]), dt);
+        if (GRAD) {
+            atomicAdd(reinterpret_cast<double *>(&acc[3]), obd[0]);
+            atomicAdd(reinterpret_cast<double *>(&acc[4]), obd[1]);
+        }
+    };
+
+    // Everything of a visit that does not depend on the halo, done before the
+    // warp waits for its neighbours: the domain's rows and their interior
+    // neighbour counts, its counters, the rate table and the first 32 steps'
+    // random numbers.
+    struct Prep {
+        Planes<LD> pl;
+        Counters cn;
+        RateRegs rr;
+        uint2 key;
+        Chunk first;
+        int k;
+    };
+    auto prepare = [&](const uint8_t *sl, uint64_t np0, int nf) -> Prep {
+        Prep pp;
         const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
         const uint8_t *rt = tables + (size_t)meta[META_RT] * RT_BYTES;
-        Planes<LD> pl;
-        pl.valid = (lane < G::NACT) ? G::FULL : (row_t)0;
+        const uint64_t seed = *reinterpret_cast<const uint64_t *>(rt + RT_SEED);
+        pp.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+        pp.k = *reinterpret_cast<const int32_t *>(rt + RT_K);
+        pp.rr = load_rates<GRAD>(rt, lane);
+        pp.pl.valid = (lane < G::NACT) ? G::FULL : (row_t)0;
         const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
 #pragma unroll
-        for (int t = 0; t < G::RPL; ++t) pl.S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
-        uint64_t *ctr = reinterpret_cast<uint64_t *>(sl + OFF_CTR);
-        Counters cn;
-        cn.H = ctr[DCTR_HASH];
-        cn.flips = 0;
-        cn.clkM = ctr[DCTR_CLKM];
-        cn.clkE = (int64_t)ctr[DCTR_CLKE];
-        cn.sb = 0.0;
-        cn.sh = 0.0;
-        cn.dbonds = 0;
-        cn.dmag = 0;
-        cn.vM = 1ull << 63;
-        cn.vE = 0;
-        const int k = *reinterpret_cast<const int32_t *>(rt + RT_K);
-        visit_core<LD, EXPO, GRAD>(pl, cn, rt, (row_t)hN, (row_t)hS, hW, hE, meta[META_D], np0, nf, k, lane, P.err);
-        mem_t *wrow = reinterpret_cast<mem_t *>(sl);
-        if (lane < G::NACT) {
-#pragma unroll
-            for (int t = 0; t < G::RPL; ++t) wrow[lane * G::RPL + t] = (mem_t)pl.S[t];
+        for (int t = 0; t < G::RPL; ++t) pp.pl.S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
+        pp.pl.build_interior(lane);
+        const uint64_t *ctr = reinterpret_cast<const uint64_t *>(sl + OFF_CTR);
+        pp.cn.H = ctr[DCTR_HASH];
+        pp.cn.flips = 0;
+        pp.cn.clkM = ctr[DCTR_CLKM];
+        pp.cn.clkE = (int64_t)ctr[DCTR_CLKE];
+        pp.cn.sb = 0.0;
+        pp.cn.sh = 0.0;
+        pp.cn.dbonds = 0;
+        pp.cn.dmag = 0;
+        pp.cn.vM = 1ull << 63;
+        pp.cn.vE = 0;
+        pp.first = draw_chunk<EXPO>(pp.key, meta[META_D], np0, 0, nf * pp.k, pp.k, lane);
+        return pp;
+    };
+
+    // The visit once the halo is here.  The edges (with the new visit count)
+    // are published first, since neighbours wait for them; then the tile, the
+    // counters and the observation sums are stored in the slot.
+    auto visit = [&](uint8_t *sl, Prep &pp, uint64_t np0, int nf, uint64_t hN, uint64_t hS, uint64_t hW,
+                     uint64_t hE, uint32_t count_after, int64_t pass) {
+        const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
+        Counters &cn = pp.cn;
+        const int k = pp.k;
+        visit_core<LD, EXPO, GRAD>(pp.pl, cn, pp.rr, pp.key, (row_t)hN, (row_t)hS, hW, hE, meta[META_D], np0, nf, k,
+                                   lane, P.err, pp.first);
+        uint64_t *es = reinterpret_cast<uint64_t *>(sl + OFF_EDGE);
+        const bool changed = cn.flips != 0; // warp-uniform
+        uint64_t wv = 0;
+        if (changed) {
+            const Edges ew = all_edges<LD>(pp.pl.S);
+            wv = stamped_word(ew, lane & 7, count_after);
+        } else if (lane < EDGE_WORDS) {
+            wv = (es[lane] & 0xFFFFFFFFull) | ((uint64_t)count_after << 32); // same edges, new count
         }
-        const Edges ew = all_edges<LD>(pl.S);
+        if (lane < EDGE_WORDS) {
+            if (CLUSTER) {
+                reinterpret_cast<volatile uint64_t *>(es)[lane] = wv;
+            } else {
+                es[lane] = wv;
+                st_cg(&P.edges[(size_t)meta[META_G] * EDGE_WORDS + lane], wv);
+            }
+        }
+        if (changed) {
+            mem_t *wrow = reinterpret_cast<mem_t *>(sl);
+            if (lane < G::NACT) {
+#pragma unroll
+                for (int t = 0; t < G::RPL; ++t) wrow[lane * G::RPL + t] = (mem_t)pp.pl.S[t];
+            }
+        }
         if (lane == 0) {
+            uint64_t *ctr = reinterpret_cast<uint64_t *>(sl + OFF_CTR);
             ctr[DCTR_HASH] = cn.H;
             ctr[DCTR_FLIPS] += cn.flips;
             ctr[DCTR_CLKM] = cn.clkM;
@@ -864,43 +1004,51 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                 reinterpret_cast<double *>(ctr)[DCTR_SB] += cn.sb;
                 reinterpret_cast<double *>(ctr)[DCTR_SH] += cn.sh;
             }
-            // pass observation: this visit's changes go to the first record at
-            // or after its pass; the finalize kernel accumulates the records
-            const int64_t o = P.obs_pass ? pass / P.obs_every : P.n_obs;
-            if (o < P.n_obs) {
-                unsigned long long *acc = P.obs_acc + ((size_t)o * P.n_rep + meta[META_R]) * OBS_WORDS;
-                const double dt = EXPO ? domain_time(true, cn.vM, cn.vE, 0, P.lambda)
-                                       : __ddiv_rn((double)(nf * k), P.lambda);
-                if (cn.dbonds != 0) atomicAdd(&acc[0], (unsigned long long)(long long)cn.dbonds);
-                if (cn.dmag != 0) atomicAdd(&acc[1], (unsigned long long)(long long)cn.dmag);
-                atomicAdd(reinterpret_cast<double *>(&acc[2]), dt);
+            // observation: the visit's changes belong to the first record at or
+            // after its pass (the finalize kernel adds the records up); they are
+            // summed per slot and leave the CTA once per record
+            if (P.n_obs > 0) {
+                const int64_t o = (P.obs_pass ? pass : pass / nph) / P.obs_every;
+                uint32_t *ob = reinterpret_cast<uint32_t *>(sl + OFF_OBS);
+                uint64_t *obm = reinterpret_cast<uint64_t *>(sl + OFF_OBS + 16);
+                double *obd = reinterpret_cast<double *>(sl + OFF_OBS + 32);
+                if ((int64_t)ob[0] != o) {
+                    flush_record(sl, meta[META_R]);
+                    ob[0] = (uint32_t)o;
+                    ob[1] = 0;
+                    ob[2] = 0;
+                    ob[3] = 0;
+                    obm[0] = 1ull << 63;
+                    obm[1] = 0;
+                    obd[0] = 0.0;
+                    obd[1] = 0.0;
+                }
+                ob[1] = (uint32_t)((int)ob[1] + cn.dbonds);
+                ob[2] = (uint32_t)((int)ob[2] + cn.dmag);
+                if (EXPO) {
+                    uint64_t m = obm[0];
+                    int64_t e = (int64_t)obm[1];
+                    mant_mul(m, e, cn.vM, cn.vE);
+                    obm[0] = m;
+                    obm[1] = (uint64_t)e;
+                } else {
+                    ob[3] += (uint32_t)(nf * k);
+                }
                 if (GRAD) {
-                    atomicAdd(reinterpret_cast<double *>(&acc[3]), cn.sb);
-                    atomicAdd(reinterpret_cast<double *>(&acc[4]), cn.sh);
+                    obd[0] += cn.sb;
+                    obd[1] += cn.sh;
                 }
             }
         }
-        if (lane < EDGE_WORDS) {
-            const uint64_t wv = stamped_word(ew, lane, count_after);
-            if (CLUSTER) reinterpret_cast<volatile uint64_t *>(sl + OFF_EDGE)[lane] = wv;
-            else st_cg(&P.edges[(size_t)meta[META_G] * EDGE_WORDS + lane], wv);
-        }
         __syncwarp();
-    };
-
-    auto phase_sync = [&](unsigned &bar_no) {
-        if (CLUSTER) cluster_sync();
-        else grid_barrier(P, bar_no, &s_ok);
     };
 
     // completed visit groups per colour in this launch (PALINDROME, FIXED)
     uint32_t gc0 = 0, gc1 = 0, gc2 = 0, gc3 = 0;
     auto gcount = [&](int c) { return c == 0 ? gc0 : c == 1 ? gc1 : c == 2 ? gc2 : gc3; };
 
-    const int nph = (P.schedule == SCHED_PALINDROME) ? 8 : 4;
     const uint64_t gp_begin = (uint64_t)P.sched_begin * nph;
     const uint64_t gp_end = (uint64_t)(P.sched_begin + P.n_sched) * nph;
-    unsigned bar_no = 0;
     bool ok = true; // uniform within the warp; a warp that failed skips work but keeps every barrier
     uint64_t gp = gp_begin;
     while (gp < gp_end) {
@@ -932,12 +1080,13 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                 const int i0 = (int)col_off[colour], i1 = (int)col_off[colour + 1];
                 for (int i = i0 + wib; i < i1; i += nwarps) {
                     uint8_t *sl = slots + (size_t)i * SB;
+                    Prep pp = prepare(sl, np0, nf);
                     uint64_t hN, hS, hW, hE;
                     if (!wait_halo(reinterpret_cast<const uint32_t *>(sl + OFF_META), needNS, needWE, hN, hS, hW, hE)) {
                         ok = false;
                         break;
                     }
-                    visit(sl, np0, nf, hN, hS, hW, hE, after, (int64_t)(gp - gp_begin));
+                    visit(sl, pp, np0, nf, hN, hS, hW, hE, after, (int64_t)(gp - gp_begin));
                 }
             }
             if (colour == 0) ++gc0;
@@ -965,65 +1114,17 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                     if (cq == (c ^ 2)) posNS = q;
                     if (cq == (c ^ 1)) posWE = q;
                 }
+                Prep pp = prepare(sl, np0, 1);
                 uint64_t hN, hS, hW, hE;
                 if (!wait_halo(meta, done_before + (posNS < p ? 1u : 0u), done_before + (posWE < p ? 1u : 0u), hN, hS,
                                hW, hE)) {
                     ok = false;
                     break;
                 }
-                visit(sl, np0, 1, hN, hS, hW, hE, done_before + 1u, (int64_t)(gp - gp_begin));
+                visit(sl, pp, np0, 1, hN, hS, hW, hE, done_before + 1u, (int64_t)(gp - gp_begin));
             }
         }
         gp += (uint64_t)nf;
-        // endpoint observation after a completed schedule (Sec. 2.3): all visits
-        // done before, no visit of the next schedule until every domain is observed
-        if (gp % nph == 0) {
-            const int64_t nl_done = (int64_t)(gp / nph - (uint64_t)P.sched_begin);
-            if (!P.obs_pass && P.obs_every > 0 && P.obs_acc != nullptr && nl_done > 0 && (nl_done % P.obs_every) == 0) {
-                phase_sync(bar_no);
-                if (ok && *(volatile int *)P.err == 0) {
-                    const int64_t o = nl_done / P.obs_every - 1;
-                    const int64_t visits = P.visits_before + nl_done * (nph == 8 ? 2 : 1);
-                    for (int i = wib; i < nslot; i += nwarps) {
-                        const uint8_t *sl = slots + (size_t)i * SB;
-                        const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
-                        // E neighbour's W column and S neighbour's N row (stamps dropped)
-                        uint32_t half = 0;
-                        if (lane < 4) {
-                            const int dir = (lane & 1) ? EDGE_E : EDGE_S, hf = lane >> 1;
-                            const uint32_t nb = meta[META_NB + dir];
-                            const int word = 2 * ((dir == EDGE_S) ? EDGE_N : EDGE_W) + hf;
-                            half = (uint32_t)(CLUSTER ? ld_dsmem(nb + OFF_EDGE + 8 * word)
-                                                      : ld_volatile_global(&P.edges[(size_t)nb * EDGE_WORDS + word]));
-                        }
-                        const uint64_t hS = (uint64_t)__shfl_sync(FULL_WARP, half, 0) |
-                                            ((uint64_t)__shfl_sync(FULL_WARP, half, 2) << 32);
-                        const uint64_t hE = (uint64_t)__shfl_sync(FULL_WARP, half, 1) |
-                                            ((uint64_t)__shfl_sync(FULL_WARP, half, 3) << 32);
-                        row_t S[G::RPL];
-                        const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
-#pragma unroll
-                        for (int t = 0; t < G::RPL; ++t) S[t] = (lane < G::NACT) ? (row_t)trow[lane * G::RPL + t] : (row_t)0;
-                        int bonds, mag;
-                        domain_bonds_mag<LD>(S, hE, hS, lane, bonds, mag);
-                        if (lane == 0) {
-                            const uint64_t *ctr = reinterpret_cast<const uint64_t *>(sl + OFF_CTR);
-                            const uint8_t *rt = tables + (size_t)meta[META_RT] * RT_BYTES;
-                            const int64_t k = *reinterpret_cast<const int32_t *>(rt + RT_K);
-                            const double tdom = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE],
-                                                            visits * k, P.lambda);
-                            unsigned long long *acc = P.obs_acc + ((size_t)o * P.n_rep + meta[META_R]) * OBS_WORDS;
-                            atomicAdd(&acc[0], (unsigned long long)(long long)bonds);
-                            atomicAdd(&acc[1], (unsigned long long)(long long)mag);
-                            atomicAdd(reinterpret_cast<double *>(&acc[2]), tdom);
-                            atomicAdd(reinterpret_cast<double *>(&acc[3]), reinterpret_cast<const double *>(ctr)[DCTR_SB]);
-                            atomicAdd(reinterpret_cast<double *>(&acc[4]), reinterpret_cast<const double *>(ctr)[DCTR_SH]);
-                        }
-                    }
-                }
-                phase_sync(bar_no);
-            }
-        }
     }
     // every warp of the CTA must have finished its visits before any warp
     // writes a slot back; in CLUSTER mode, also no CTA may leave while another
@@ -1031,10 +1132,12 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
     if (CLUSTER) cluster_sync();
     else __syncthreads();
     if (*(volatile int *)P.err != 0) return;
-    // write owned tiles and counters back (and edges, for the observables kernel)
+    // write owned tiles and counters back (and edges, for the observables
+    // kernel), and each slot's open record
     for (int i = wib; i < nslot; i += nwarps) {
         const uint8_t *sl = slots + (size_t)i * SB;
         const uint32_t g = reinterpret_cast<const uint32_t *>(sl + OFF_META)[META_G];
+        if (lane == 0 && P.n_obs > 0) flush_record(sl, reinterpret_cast<const uint32_t *>(sl + OFF_META)[META_R]);
         for (int q = lane * 4; q < TB; q += 128)
             *reinterpret_cast<uint32_t *>(P.tiles + (size_t)g * TB + q) = *reinterpret_cast<const uint32_t *>(sl + q);
         if (lane < DCTR_WORDS)
@@ -1221,36 +1324,11 @@ __global__ void observe_kernel(const RunParams P, const uint32_t *dom_rep, int n
     }
 }
 
-// obs_acc -> {e, m, e*m, T (, score beta, score h)} per record; same FP order as the oracle.
-__global__ void finalize_obs_kernel(const unsigned long long *acc, int n_rec, int n_rep,
-                                    const int32_t *rep_L, const int32_t *rep_Dx, double J,
-                                    const double *rep_h, double *out, int stride)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_rec) return;
-    const int r = i % n_rep;
-    const unsigned long long *a = acc + (size_t)i * OBS_WORDS;
-    const double N = (double)rep_L[r] * (double)rep_L[r];
-    const double b = (double)(long long)a[0];
-    const double m = (double)(long long)a[1];
-    const double e = __ddiv_rn(__dsub_rn(__dmul_rn(-J, b), __dmul_rn(rep_h[r], m)), N);
-    const double mm = __ddiv_rn(m, N);
-    const double nD = (double)rep_Dx[r] * (double)rep_Dx[r];
-    double *o = out + (size_t)i * stride;
-    o[0] = e;
-    o[1] = mm;
-    o[2] = __dmul_rn(e, mm);
-    o[3] = __ddiv_rn(__longlong_as_double((long long)a[2]), nD);
-    if (stride >= 6) {
-        o[4] = __longlong_as_double((long long)a[3]);
-        o[5] = __longlong_as_double((long long)a[4]);
-    }
-}
-
-// Pass observation: record o = base + the changes of every record up to o.
-// One thread per replica walks its records in order (the integer sums are
-// exact; the clock and score sums add the per-record totals in record order).
-__global__ void finalize_pass_obs_kernel(const unsigned long long *base /* [n_rep][OBS_WORDS] */,
+// Records {e, m, e*m, T (, score beta, score h)}: record o = base (the state
+// before the launch) + the changes of every record up to o.  One thread per
+// replica walks its records in order; the integer sums are exact and e, m
+// follow the oracle's FP64 formula.
+__global__ void finalize_obs_kernel(const unsigned long long *base /* [n_rep][OBS_WORDS] */,
                                          const unsigned long long *acc, int64_t n_obs, int n_rep,
                                          const int32_t *rep_L, const int32_t *rep_Dx, double J,
                                          const double *rep_h, double *out, int stride)
