@@ -464,20 +464,19 @@ __device__ __forceinline__ Chunk draw_chunk(uint2 key, uint32_t d, uint64_t np0,
     return ch;
 }
 
-// Lane c (< 10) holds class c's fixed-point rate, its reciprocal and (scores)
-// a_c, dlog a_c/dbeta, dlog a_c/dh; loaded before the halo wait.
+// Lane c (< 10) holds class c's fixed-point rate and (scores) a_c,
+// dlog a_c/dbeta, dlog a_c/dh; loaded before the halo wait.
 struct RateRegs {
-    uint64_t A, inv;
+    uint64_t A;
     double a, gb, gh;
 };
 
 template <bool GRAD>
 __device__ __forceinline__ RateRegs load_rates(const uint8_t *rt, int lane)
 {
-    RateRegs r = {0ull, 0ull, 0.0, 0.0, 0.0};
+    RateRegs r = {0ull, 0.0, 0.0, 0.0};
     if (lane < 10) {
         r.A = reinterpret_cast<const uint64_t *>(rt)[lane];
-        r.inv = reinterpret_cast<const uint64_t *>(rt + 128)[lane];
         if (GRAD) {
             const double *gr = reinterpret_cast<const double *>(rt + 256);
             r.a = gr[lane];
@@ -510,7 +509,10 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
 {
     using G = Geo<LD>;
     using row_t = typename G::row_t;
-    const uint64_t Ac = rr.A, invc = rr.inv;
+    const uint64_t Ac = rr.A;
+    // 1/A_c from below (A_c rounded up, its reciprocal rounded down), so that
+    // the FP32 quotient estimate below never exceeds the exact quotient
+    const float invAf = (lane < 10) ? __frcp_rd(__ull2float_ru(Ac)) : 0.0f;
     const double a_c = rr.a, gb_c = rr.gb, gh_c = rr.gh;
     pl.add_halo(lane, hN, hS, hW, hE); // pl holds the interior counts
     uint32_t n_c = class_counts<LD>(pl, lane);
@@ -555,18 +557,15 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             const uint64_t ev = __shfl_sync(FULL_WARP, ebase, jx);
             const unsigned sel = __ballot_sync(FULL_WARP, lane < 10 && t < Cinc);
             const int c = __ffs(sel) - 1;
-            uint32_t q = 0;
-            if (lane == c) {
-                // exact floor((t - C_{c-1}) / A_c): reciprocal estimate, then at
-                // most three corrections
-                const uint64_t x = t - (Cinc - Wc);
-                uint64_t qq = __umul64hi(x, invc);
-                uint64_t r = x - qq * Ac;
-                if (r >= Ac) { ++qq; r -= Ac; }
-                if (r >= Ac) { ++qq; r -= Ac; }
-                if (r >= Ac) { ++qq; }
-                q = (uint32_t)qq;
-            }
+            // exact jj = floor((t - C_{c-1}) / A_c) < n_c <= 4096, computed by
+            // every lane for its own class (lane c's is kept).  Each of the
+            // four FP32 steps (x and A_c converted, reciprocal, product) rounds
+            // downwards, so the estimate e obeys x/A_c (1 - 2^-21) < e <= x/A_c;
+            // as x/A_c < 4096, e truncates to jj or jj - 1, and one exact
+            // integer comparison decides which.
+            const uint64_t x = t - (Cinc - Wc);
+            uint32_t q = (uint32_t)__fmul_rz(__ull2float_rz(x), invAf);
+            q = (x - (uint64_t)q * Ac >= Ac) ? q + 1u : q;
             const uint32_t jj = __shfl_sync(FULL_WARP, q, c);
             if (GRAD) {
                 cn.sb += __shfl_sync(FULL_WARP, gb_c, c);
@@ -603,19 +602,30 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
                 break;
             }
             const int wl = __ffs(win) - 1;
-            uint32_t yc = 0;
-            if (lane == wl) {
-                uint32_t rr = jj - excl;
-                int tsel = 0;
-                if (G::RPL == 2) {
+            int y, col;
+            if (G::RPL == 1) {
+                // the (jj - excl)-th set bit of the winning lane's row: lane i
+                // tests whether bits 0..i hold more members than that
+                const uint32_t mw = (uint32_t)__shfl_sync(FULL_WARP, (uint32_t)m[0], wl);
+                const uint32_t rr = __shfl_sync(FULL_WARP, jj - excl, wl);
+                const uint32_t upto = (lane == 31) ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+                const unsigned past = __ballot_sync(FULL_WARP, (uint32_t)__popc(mw & upto) > rr);
+                y = wl;
+                col = __ffs(past) - 1;
+            } else {
+                uint32_t yc = 0;
+                if (lane == wl) {
+                    uint32_t rr = jj - excl;
+                    int tsel = 0;
                     const uint32_t p0 = (uint32_t)popc_row(m[0]);
                     if (rr >= p0) { rr -= p0; tsel = 1; }
+                    const int cc = select_bit((uint64_t)(tsel ? m[G::RPL - 1] : m[0]), rr);
+                    yc = ((uint32_t)(lane * G::RPL + tsel) << 8) | (uint32_t)cc;
                 }
-                const int col = select_bit((uint64_t)(tsel ? m[G::RPL - 1] : m[0]), rr);
-                yc = ((uint32_t)(lane * G::RPL + tsel) << 8) | (uint32_t)col;
+                yc = __shfl_sync(FULL_WARP, yc, wl);
+                y = (int)(yc >> 8);
+                col = (int)(yc & 255u);
             }
-            yc = __shfl_sync(FULL_WARP, yc, wl);
-            const int y = (int)(yc >> 8), col = (int)(yc & 255u);
 #pragma unroll
             for (int tt = 0; tt < G::RPL; ++tt)
                 if (lane * G::RPL + tt == y) pl.S[tt] ^= (row_t)1 << col;
