@@ -205,6 +205,17 @@ __device__ __forceinline__ int select_bit(uint64_t m, uint32_t rr)
     return pos;
 }
 
+// 64-bit unsigned integer to FP32, rounded toward zero / upwards, from two
+// 32-bit conversions (exact scaling by 2^32, one directed addition).
+__device__ __forceinline__ float u64_to_float_rz(uint64_t x)
+{
+    return __fadd_rz(__fmul_rz(__uint2float_rz((uint32_t)(x >> 32)), 4294967296.0f), __uint2float_rz((uint32_t)x));
+}
+__device__ __forceinline__ float u64_to_float_ru(uint64_t x)
+{
+    return __fadd_ru(__fmul_ru(__uint2float_ru((uint32_t)(x >> 32)), 4294967296.0f), __uint2float_ru((uint32_t)x));
+}
+
 // Normalised unsigned mantissa product for the exponential clock:
 // value = (m / 2^63) * 2^e with m in [2^63, 2^64).
 __device__ __forceinline__ void mant_mul(uint64_t &m, int64_t &e, uint64_t m2, int64_t e2)
@@ -511,8 +522,10 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
     using row_t = typename G::row_t;
     const uint64_t Ac = rr.A;
     // 1/A_c from below (A_c rounded up, its reciprocal rounded down), so that
-    // the FP32 quotient estimate below never exceeds the exact quotient
-    const float invAf = (lane < 10) ? __frcp_rd(__ull2float_ru(Ac)) : 0.0f;
+    // the FP32 quotient estimate below never exceeds the exact quotient.  The
+    // 64-bit integers are converted in two 32-bit halves (the 64-bit integer
+    // conversion runs on the FP64 unit).
+    const float invAf = (lane < 10) ? __frcp_rd(u64_to_float_ru(Ac)) : 0.0f;
     const double a_c = rr.a, gb_c = rr.gb, gh_c = rr.gh;
     pl.add_halo(lane, hN, hS, hW, hE); // pl holds the interior counts
     uint32_t n_c = class_counts<LD>(pl, lane);
@@ -558,13 +571,13 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             const unsigned sel = __ballot_sync(FULL_WARP, lane < 10 && t < Cinc);
             const int c = __ffs(sel) - 1;
             // exact jj = floor((t - C_{c-1}) / A_c) < n_c <= 4096, computed by
-            // every lane for its own class (lane c's is kept).  Each of the
-            // four FP32 steps (x and A_c converted, reciprocal, product) rounds
-            // downwards, so the estimate e obeys x/A_c (1 - 2^-21) < e <= x/A_c;
+            // every lane for its own class (lane c's is kept).  Every FP32
+            // step (x and A_c converted, reciprocal, product) rounds toward
+            // the lower side, so the estimate e obeys x/A_c (1 - 2^-20) < e <= x/A_c;
             // as x/A_c < 4096, e truncates to jj or jj - 1, and one exact
             // integer comparison decides which.
             const uint64_t x = t - (Cinc - Wc);
-            uint32_t q = (uint32_t)__fmul_rz(__ull2float_rz(x), invAf);
+            uint32_t q = (uint32_t)__fmul_rz(u64_to_float_rz(x), invAf);
             q = (x - (uint64_t)q * Ac >= Ac) ? q + 1u : q;
             const uint32_t jj = __shfl_sync(FULL_WARP, q, c);
             if (GRAD) {
