@@ -58,7 +58,8 @@ struct kmc_ctx {
     int32_t *d_L = nullptr, *d_Dx = nullptr, *d_k = nullptr, *d_init = nullptr;
     uint32_t *d_dom_off = nullptr, *d_dom_rep = nullptr;
     uint64_t *d_site_off = nullptr, *d_blk_off = nullptr, *d_seed = nullptr;
-    uint64_t *d_A = nullptr, *d_inv = nullptr;
+    uint64_t *d_A = nullptr;
+    int64_t *d_gfix = nullptr; // [n_rep][GFIX_WORDS] fixed-point score products
     double *d_grad = nullptr, *d_h = nullptr;
     uint8_t *d_tiles = nullptr;
     uint64_t *d_edges = nullptr, *d_dctr = nullptr;
@@ -72,7 +73,7 @@ struct kmc_ctx {
 
     double J = 1.0, nu = 1.0;
     std::vector<double> beta, h, a, gb, gh;
-    std::vector<uint64_t> A, inv;
+    std::vector<uint64_t> A;
     int law = KMC_RATE_METROPOLIS;
 
     int64_t sched_done = 0;
@@ -152,7 +153,7 @@ int slot_bytes_for(int LD)
 // round(a_c 2^P), P = 63 - log2(n_d), reciprocal floor((2^64-1)/A_c) and the
 // score derivatives d log a_c / d beta, d log a_c / d h.
 void build_table(double J, double beta, double h, int law, int log2nd, double *a, uint64_t *A,
-                 uint64_t *inv, double *gb, double *gh)
+                 double *gb, double *gh)
 {
     const int P = 63 - log2nd;
     for (int c = 0; c < 10; ++c) {
@@ -177,7 +178,6 @@ void build_table(double J, double beta, double h, int law, int log2nd, double *a
         }
         a[c] = ac;
         A[c] = (uint64_t)std::nearbyint(std::ldexp(ac, P));
-        inv[c] = A[c] ? (~0ull) / A[c] : 0ull;
         gb[c] = dlb;
         gh[c] = dlh;
     }
@@ -241,7 +241,7 @@ RunParams run_params(kmc_ctx *c)
     P.rep_dom_off = c->d_dom_off;
     P.rep_seed = c->d_seed;
     P.rep_A = c->d_A;
-    P.rep_inv = c->d_inv;
+    P.rep_gfix = c->d_gfix;
     P.rep_grad = c->d_grad;
     const Plan &pl = c->plan;
     uint32_t *base = c->d_plan;
@@ -595,14 +595,36 @@ kmc_status launch_observe(kmc_ctx *c, cudaStream_t s, bool expo, unsigned long l
     return KMC_OK;
 }
 
+// Fixed-point products a_c dlog a_c / d(beta, h) for the score of null steps:
+// round(x 2^Q) with Q <= 40 chosen so that n_d sum_c |x_c| 2^Q < 2^62 (the
+// device sums n_c x_c 2^Q over the classes in int64), and 2^-Q.
+void build_gfix(const double *a, const double *gb, const double *gh, int log2nd, int64_t *out)
+{
+    double mx = 0.0;
+    for (int c = 0; c < 10; ++c) mx = std::max(mx, std::max(std::fabs(a[c] * gb[c]), std::fabs(a[c] * gh[c])));
+    int Q = 40;
+    if (mx > 0.0) {
+        int e = 0;
+        std::frexp(mx, &e); // mx < 2^e
+        Q = std::max(0, std::min(40, 58 - log2nd - e));
+    }
+    for (int c = 0; c < 10; ++c) {
+        out[c] = (int64_t)std::llround(std::ldexp(a[c] * gb[c], Q));
+        out[10 + c] = (int64_t)std::llround(std::ldexp(a[c] * gh[c], Q));
+    }
+    const double scale = std::ldexp(1.0, -Q);
+    std::memcpy(&out[20], &scale, 8);
+    out[21] = out[22] = out[23] = 0;
+}
+
 kmc_status upload_rates(kmc_ctx *c)
 {
-    std::vector<uint64_t> A16((size_t)c->n_rep * 16, 0), inv16((size_t)c->n_rep * 16, 0);
+    std::vector<uint64_t> A16((size_t)c->n_rep * 16, 0);
+    std::vector<int64_t> gfix((size_t)c->n_rep * GFIX_WORDS, 0);
     std::vector<double> g32((size_t)c->n_rep * 32, 0.0);
     for (int r = 0; r < c->n_rep; ++r) {
         for (int q = 0; q < 10; ++q) {
             A16[(size_t)r * 16 + q] = c->A[(size_t)r * 10 + q];
-            inv16[(size_t)r * 16 + q] = c->inv[(size_t)r * 10 + q];
             g32[(size_t)r * 32 + q] = c->a[(size_t)r * 10 + q];
             g32[(size_t)r * 32 + 10 + q] = c->gb[(size_t)r * 10 + q];
             g32[(size_t)r * 32 + 20 + q] = c->gh[(size_t)r * 10 + q];
@@ -611,7 +633,10 @@ kmc_status upload_rates(kmc_ctx *c)
     // ordered on the context's stream, after any run already queued there; the
     // sources are pageable, so each copy has consumed them when the call returns
     CUDA_TRY(c, cudaMemcpyAsync(c->d_A, A16.data(), A16.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_inv, inv16.data(), inv16.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    for (int r = 0; r < c->n_rep; ++r)
+        build_gfix(&c->a[(size_t)r * 10], &c->gb[(size_t)r * 10], &c->gh[(size_t)r * 10], c->log2nd,
+                   &gfix[(size_t)r * GFIX_WORDS]);
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_gfix, gfix.data(), gfix.size() * 8, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_grad, g32.data(), g32.size() * 8, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_h, c->h.data(), c->h.size() * 8, cudaMemcpyHostToDevice, c->stream));
     return KMC_OK;
@@ -688,7 +713,7 @@ void free_all(kmc_ctx *c)
 {
     void **ptrs[] = {(void **)&c->d_L, (void **)&c->d_Dx, (void **)&c->d_k, (void **)&c->d_init, (void **)&c->d_dom_off, (void **)&c->d_dom_rep,
                      (void **)&c->d_site_off, (void **)&c->d_blk_off, (void **)&c->d_seed, (void **)&c->d_A,
-                     (void **)&c->d_inv, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_tiles,
+                     (void **)&c->d_gfix, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_tiles,
                      (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_err,
                      (void **)&c->d_obs_acc, (void **)&c->d_tmp, (void **)&c->d_plan};
     for (void **p : ptrs) {
@@ -813,7 +838,7 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     ALLOC(c->d_blk_off, n_replicas + 1);
     ALLOC(c->d_seed, n_replicas);
     ALLOC(c->d_A, (size_t)n_replicas * 16);
-    ALLOC(c->d_inv, (size_t)n_replicas * 16);
+    ALLOC(c->d_gfix, (size_t)n_replicas * GFIX_WORDS);
     ALLOC(c->d_grad, (size_t)n_replicas * 32);
     ALLOC(c->d_h, n_replicas);
     ALLOC(c->d_tiles, ndom * tile);
@@ -883,9 +908,9 @@ kmc_status kmc_set_rates(kmc_ctx *c, double J, const double *beta, const double 
             return fail(c, KMC_EINVAL, "replica %d: beta >= 0 and finite h required", r);
     const size_t n = (size_t)c->n_rep * 10;
     std::vector<double> a(n), gb(n), gh(n);
-    std::vector<uint64_t> A(n), inv(n);
+    std::vector<uint64_t> A(n);
     for (int r = 0; r < c->n_rep; ++r)
-        build_table(J, beta[r], h[r], rate_law, c->log2nd, &a[r * 10], &A[r * 10], &inv[r * 10], &gb[r * 10], &gh[r * 10]);
+        build_table(J, beta[r], h[r], rate_law, c->log2nd, &a[r * 10], &A[r * 10], &gb[r * 10], &gh[r * 10]);
     c->J = J;
     c->nu = nu;
     c->law = rate_law;
@@ -893,7 +918,6 @@ kmc_status kmc_set_rates(kmc_ctx *c, double J, const double *beta, const double 
     c->h.assign(h, h + c->n_rep);
     c->a = a;
     c->A = A;
-    c->inv = inv;
     c->gb = gb;
     c->gh = gh;
     return upload_rates(c);
@@ -908,7 +932,7 @@ kmc_status kmc_set_rate_table(kmc_ctx *c, double J, const double *beta, const do
     const int P = 63 - c->log2nd;
     const size_t n = (size_t)c->n_rep * 10;
     std::vector<double> av(a, a + n), gb(n, 0.0), gh(n, 0.0);
-    std::vector<uint64_t> A(n), inv(n);
+    std::vector<uint64_t> A(n);
     for (int r = 0; r < c->n_rep; ++r) {
         if (!(beta[r] >= 0.0) || !std::isfinite(h[r])) return fail(c, KMC_EINVAL, "replica %d: bad beta/h", r);
         for (int q = 0; q < 10; ++q) {
@@ -925,7 +949,6 @@ kmc_status kmc_set_rate_table(kmc_ctx *c, double J, const double *beta, const do
                             "replica %d class %d: a_c/a_cbar = %.17g but exp(-beta dE) = %.17g (detailed balance, Eq. 4)",
                             r, q, ratio, want);
             A[r * 10 + q] = (uint64_t)std::nearbyint(std::ldexp(ac, P));
-            inv[r * 10 + q] = A[r * 10 + q] ? (~0ull) / A[r * 10 + q] : 0ull;
         }
     }
     c->J = J;
@@ -934,7 +957,6 @@ kmc_status kmc_set_rate_table(kmc_ctx *c, double J, const double *beta, const do
     c->h.assign(h, h + c->n_rep);
     c->a = av;
     c->A = A;
-    c->inv = inv;
     c->gb = gb; // no closed-form derivatives for a user table
     c->gh = gh;
     return upload_rates(c);
@@ -1267,10 +1289,9 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     c.h.assign(1, h);
     c.a.resize(10);
     c.A.resize(10);
-    c.inv.resize(10);
     c.gb.resize(10);
     c.gh.resize(10);
-    build_table(J, beta, h, rate_law, c.log2nd, c.a.data(), c.A.data(), c.inv.data(), c.gb.data(), c.gh.data());
+    build_table(J, beta, h, rate_law, c.log2nd, c.a.data(), c.A.data(), c.gb.data(), c.gh.data());
 
     cudaError_t ce = cudaGetDevice(&c.dev);
     if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
@@ -1314,7 +1335,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
         c.d_blk_off = cv.take<uint64_t>(2);
         c.d_seed = cv.take<uint64_t>(1);
         c.d_A = cv.take<uint64_t>(16);
-        c.d_inv = cv.take<uint64_t>(16);
+        c.d_gfix = cv.take<int64_t>(GFIX_WORDS);
         c.d_grad = cv.take<double>(32);
         c.d_h = cv.take<double>(1);
         c.d_err = cv.take<int>(1);
@@ -1349,11 +1370,12 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     // inputs of this call; the array keeps the previous call's contents, so
     // everything the kernels read is written (or cleared) here first
     cudaStream_t s = c.stream;
-    std::vector<uint64_t> A16(16, 0), inv16(16, 0);
+    std::vector<uint64_t> A16(16, 0);
+    std::vector<int64_t> gfix(GFIX_WORDS, 0);
+    build_gfix(c.a.data(), c.gb.data(), c.gh.data(), c.log2nd, gfix.data());
     std::vector<double> g32(32, 0.0);
     for (int q = 0; q < 10; ++q) {
         A16[q] = c.A[q];
-        inv16[q] = c.inv[q];
         g32[q] = c.a[q];
         g32[10 + q] = c.gb[q];
         g32[20 + q] = c.gh[q];
@@ -1361,7 +1383,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
         {c.d_L, c.L.data(), 4}, {c.d_Dx, c.Dx.data(), 4}, {c.d_k, c.kr.data(), 4}, {c.d_dom_off, c.dom_off.data(), 8},
         {c.d_site_off, c.site_off.data(), 8}, {c.d_blk_off, c.blk_off.data(), 16}, {c.d_seed, c.seed.data(), 8},
-        {c.d_A, A16.data(), 128}, {c.d_inv, inv16.data(), 128}, {c.d_grad, g32.data(), 256}, {c.d_h, c.h.data(), 8},
+        {c.d_A, A16.data(), 128}, {c.d_gfix, gfix.data(), GFIX_WORDS * 8}, {c.d_grad, g32.data(), 256}, {c.d_h, c.h.data(), 8},
         {c.d_dom_rep, c.dom_rep.data(), (size_t)c.n_dom * 4}, {c.d_plan, flat.data(), flat.size() * 4},
     };
     for (const Up &u : ups) {
@@ -1416,7 +1438,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     st = sync_ctx(&c);
     // the kmc_ctx destructor must not free the static array
     c.d_L = nullptr; c.d_Dx = nullptr; c.d_k = nullptr; c.d_dom_off = nullptr; c.d_dom_rep = nullptr; c.d_site_off = nullptr;
-    c.d_blk_off = nullptr; c.d_seed = nullptr; c.d_A = nullptr; c.d_inv = nullptr; c.d_grad = nullptr; c.d_h = nullptr;
+    c.d_blk_off = nullptr; c.d_seed = nullptr; c.d_A = nullptr; c.d_gfix = nullptr; c.d_grad = nullptr; c.d_h = nullptr;
     c.d_tiles = nullptr; c.d_edges = nullptr; c.d_dctr = nullptr; c.d_tmp = nullptr; c.d_err = nullptr;
     c.d_obs_acc = nullptr; c.d_plan = nullptr;
     if (st != KMC_OK) return bad(st, c.err);

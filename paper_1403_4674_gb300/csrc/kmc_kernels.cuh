@@ -50,11 +50,14 @@ constexpr int INIT_KEEP = 2, INIT_PER_REPLICA = 3;
 constexpr int OBS_WORDS = 5; // bonds, mag, clock sum, score beta sum, score h sum
 
 // Replica table staged in shared memory (bytes):
-//   [0,128) A[16] fixed-point acceptance, [128,256) inv[16] = floor((2^64-1)/A),
+//   [0,128) A[16] fixed-point acceptance,
+//   [128,256) Gb[16] = round(a dlog a/dbeta 2^Q) (int64, scores),
 //   [256,512) grad[32] = a[10], dlog a/dbeta[10], dlog a/dh[10],
-//   [512] seed, [520] dom_off, [524] Dx, [528] k (steps per visit).
-constexpr int RT_BYTES = 544;
-constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524, RT_K = 528;
+//   [512] seed, [520] dom_off, [524] Dx, [528] k (steps per visit),
+//   [544,624) Gh[10] = round(a dlog a/dh 2^Q), [624] 2^-Q (double).
+constexpr int RT_BYTES = 640;
+constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524, RT_K = 528, RT_GB = 128, RT_GH = 544, RT_GSCALE = 624;
+constexpr int GFIX_WORDS = 24; // per replica: Gb[10], Gh[10], 2^-Q bits, pad
 // Slot: [tile][stamped edges 64][counters 48][meta 32][observation 48];
 // meta u32: g, replica, d, rt, nb[4];
 // observation, since the record began: u32 record, i32 bond change, i32
@@ -86,7 +89,7 @@ struct RunParams {
     const uint32_t *rep_dom_off;
     const uint64_t *rep_seed;
     const uint64_t *rep_A;   // [n_rep][16]
-    const uint64_t *rep_inv; // [n_rep][16]
+    const int64_t *rep_gfix; // [n_rep][GFIX_WORDS]
     const double *rep_grad;  // [n_rep][32]
     // plan: per CTA slot ranges (colour-sorted), replica tables, neighbours
     const uint32_t *cta_slot_off; // [n_cta + 1]
@@ -404,7 +407,8 @@ __device__ __forceinline__ uint64_t prefix16(uint64_t w, int lane)
     return w;
 }
 
-__device__ __forceinline__ double warp_sum10(double v)
+// Sum over lanes 0..15 (every lane receives it).
+__device__ __forceinline__ int64_t warp_isum16(int64_t v)
 {
 #pragma unroll
     for (int off = 8; off >= 1; off >>= 1) v += __shfl_xor_sync(FULL_WARP, v, off);
@@ -475,26 +479,31 @@ __device__ __forceinline__ Chunk draw_chunk(uint2 key, uint32_t d, uint64_t np0,
     return ch;
 }
 
-// Lane c (< 10) holds class c's fixed-point rate and (scores) a_c,
-// dlog a_c/dbeta, dlog a_c/dh; loaded before the halo wait.
+// Lane c (< 10) holds class c's fixed-point rate and (scores) dlog a_c /
+// d(beta, h) and the fixed-point products a_c dlog a_c / d(beta, h); loaded
+// before the halo wait.
 struct RateRegs {
     uint64_t A;
-    double a, gb, gh;
+    double gb, gh;
+    int64_t Gb, Gh;
+    double gscale;
 };
 
 template <bool GRAD>
 __device__ __forceinline__ RateRegs load_rates(const uint8_t *rt, int lane)
 {
-    RateRegs r = {0ull, 0.0, 0.0, 0.0};
+    RateRegs r = {0ull, 0.0, 0.0, 0, 0, 0.0};
     if (lane < 10) {
         r.A = reinterpret_cast<const uint64_t *>(rt)[lane];
         if (GRAD) {
             const double *gr = reinterpret_cast<const double *>(rt + 256);
-            r.a = gr[lane];
             r.gb = gr[10 + lane];
             r.gh = gr[20 + lane];
+            r.Gb = reinterpret_cast<const int64_t *>(rt + RT_GB)[lane];
+            r.Gh = reinterpret_cast<const int64_t *>(rt + RT_GH)[lane];
         }
     }
+    if (GRAD) r.gscale = *reinterpret_cast<const double *>(rt + RT_GSCALE);
     return r;
 }
 
@@ -526,21 +535,28 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
     // 64-bit integers are converted in two 32-bit halves (the 64-bit integer
     // conversion runs on the FP64 unit).
     const float invAf = (lane < 10) ? __frcp_rd(u64_to_float_ru(Ac)) : 0.0f;
-    const double a_c = rr.a, gb_c = rr.gb, gh_c = rr.gh;
+    const double gb_c = rr.gb, gh_c = rr.gh;
     pl.add_halo(lane, hN, hS, hW, hE); // pl holds the interior counts
     uint32_t n_c = class_counts<LD>(pl, lane);
     uint64_t Wc = (uint64_t)n_c * Ac;
     uint64_t Cinc = prefix16(Wc, lane);
     uint64_t R = __shfl_sync(FULL_WARP, Cinc, 9);
 
-    double nd_minus_R = 0.0, Db = 0.0, Dh = 0.0;
+    // Score of a null step in the current state: d log(1 - R/n_d) =
+    // -sum_c n_c a_c dlog a_c / (n_d - R).  The numerator is an exact int64
+    // sum of the fixed-point products a_c dlog a_c 2^Q, and n_d - R comes
+    // from the exact fixed-point rate sum, (n_d 2^P - R') 2^-P with
+    // n_d 2^P = 2^63; one FP64 reciprocal per state.
+    double nb_over = 0.0, nh_over = 0.0;
     auto grad_state = [&]() {
         if (GRAD) {
-            const double w = (double)n_c * a_c;
-            const double Rr = warp_sum10(w);
-            Db = warp_sum10(w * gb_c);
-            Dh = warp_sum10(w * gh_c);
-            nd_minus_R = (double)(LD * LD) - Rr;
+            const int64_t sb = warp_isum16((int64_t)n_c * rr.Gb), sh = warp_isum16((int64_t)n_c * rr.Gh);
+            const uint64_t gap = (1ull << 63) - R;
+            const double inv = gap ? __drcp_rn(__ull2double_rn(gap)) : 0.0; // 2^-P / (n_d - R)
+            constexpr int PBITS = 63 - 2 * (LD == 8 ? 3 : LD == 16 ? 4 : LD == 32 ? 5 : 6);
+            const double w = rr.gscale * inv * (double)(1ull << PBITS);
+            nb_over = (double)sb * w;
+            nh_over = (double)sh * w;
         }
     };
     grad_state();
@@ -560,10 +576,10 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             const unsigned real = __ballot_sync(FULL_WARP, lane >= pos && tgt < R);
             const int jx = real ? __ffs(real) - 1 : chunk_end;
             if (GRAD && jx > pos) {
-                // (jx - pos) null steps in the current state: d log(1 - R/n_d)
+                // (jx - pos) null steps in the current state
                 const double q = (double)(jx - pos);
-                cn.sb -= q * Db / nd_minus_R;
-                cn.sh -= q * Dh / nd_minus_R;
+                cn.sb -= q * nb_over;
+                cn.sh -= q * nh_over;
             }
             if (!real) break;
             const uint64_t t = __shfl_sync(FULL_WARP, tgt, jx);
@@ -808,8 +824,10 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         uint8_t *t = tables + (size_t)i * RT_BYTES;
         if (lane < 16) {
             reinterpret_cast<uint64_t *>(t)[lane] = P.rep_A[(size_t)r * 16 + lane];
-            reinterpret_cast<uint64_t *>(t + 128)[lane] = P.rep_inv[(size_t)r * 16 + lane];
+            reinterpret_cast<int64_t *>(t + RT_GB)[lane] = (lane < 10) ? P.rep_gfix[(size_t)r * GFIX_WORDS + lane] : 0;
         }
+        if (lane < 10) reinterpret_cast<int64_t *>(t + RT_GH)[lane] = P.rep_gfix[(size_t)r * GFIX_WORDS + 10 + lane];
+        if (lane == 10) *reinterpret_cast<int64_t *>(t + RT_GSCALE) = P.rep_gfix[(size_t)r * GFIX_WORDS + 20];
         reinterpret_cast<double *>(t + 256)[lane] = P.rep_grad[(size_t)r * 32 + lane];
         if (lane == 0) {
             *reinterpret_cast<uint64_t *>(t + RT_SEED) = P.rep_seed[r];
