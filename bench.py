@@ -77,6 +77,22 @@ def main_workload(name: str, rank: int, sched_override: int):
     return w, desc
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, world: int, max_seconds: float) -> float:
+    """Units of every rank over the slowest rank's time (weak scaling: each
+    rank runs its own replicas of the same workload)."""
+    return units_per_rank_step * steps * world / max_seconds
+
+
 def visit_bytes(Ld: int, k: int) -> int:
     """Algorithmic HBM bytes of one domain visit: the domain plus its halo read
     once ((L_d+2)^2 - 4 bytes of int8 state), write-back of at most k dirty 32-byte
@@ -399,12 +415,8 @@ def main():
 
     events_step = lat.events_per_schedule() * w.schedules
     bytes_step = schedule_bytes(lat.L, lat.L_d, lat.ks) * w.schedules
-    dev_s = sum(step_ms) / 1000.0
-    if dist is not None:
-        t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
-    value = events_step * args.steps * world / dev_s
+    dev_s = max_over_ranks(sum(step_ms) / 1000.0, dist, "cuda")
+    value = whole_job_rate(events_step, args.steps, world, dev_s)
     flips = int(lat.observables()["flips"].sum())
 
     # end-to-end through the public API with host buffers
@@ -430,12 +442,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step()
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": events_step * args.steps * world / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": whole_job_rate(events_step, args.steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(d2h)}
 
     traffic = TRAFFIC_BYTES_PER_LAUNCH if (TRAFFIC_KERNEL_SHA256 == kernel_source_sha256()
