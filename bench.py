@@ -217,10 +217,10 @@ def reference_arm(args):
 
 # DRAM traffic of one run-kernel launch of the default workload, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (summary in
-# profiles/run_kernel_ising1024x18_traffic.md), and the SHA-256 of the kernel
+# profiles/run_kernel_ising1024x18_launches.md), and the SHA-256 of the kernel
 # source it was taken on; reported as null once the source has changed.
-TRAFFIC_BYTES_PER_LAUNCH = None
-TRAFFIC_KERNEL_SHA256 = None
+TRAFFIC_BYTES_PER_LAUNCH = 4709888
+TRAFFIC_KERNEL_SHA256 = "46ac65c128a0270692e58b7463b54dd423e0e7ebb9aee7a0b1cecfad35a2b4bf"
 
 
 def kernel_source_sha256() -> str:

@@ -151,7 +151,9 @@ def tune_batch(L: Sequence[int], beta: Sequence[float], h: Sequence[float], seed
                                   [h[i] for i in idx], plans, trial_schedules, law)
         ok = [t for t in trials if t.error is None]
         if not ok:
-            raise KmcError(-1, "no configuration runs for replicas %s" % idx)
+            errs = sorted({str(t.error) for t in trials})[:3]
+            raise KmcError(-1, "no configuration runs for a group of %d replicas (largest L = %d): %s"
+                           % (len(idx), max(Lg), "; ".join(errs)))
         best = max(ok, key=lambda t: t.events_per_s)
         out.append(GroupChoice(idx, best.L_d, best.k, best.plan, best.events_per_s, trials))
     return out

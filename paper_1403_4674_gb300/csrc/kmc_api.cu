@@ -540,8 +540,10 @@ kmc_status install_plan(kmc_ctx *c, Plan &pl)
 }
 
 // Default plan: clusters when every replica fits one (smallest power of two
-// that covers the largest replica at one visit per warp and phase, up to 16),
-// otherwise the cooperative grid.
+// that covers the largest replica at one visit per warp and phase, up to 16);
+// otherwise the cooperative grid; if the batch's state does not fit the
+// grid's shared memory, clusters of 16 CTAs with several visits per warp and
+// phase (clusters run in waves, so the batch need not be resident at once).
 kmc_status default_plan(kmc_ctx *c)
 {
     int need = 1;
@@ -568,6 +570,12 @@ kmc_status default_plan(kmc_ctx *c)
     for (int wpb = MAX_WPB; wpb >= 4; wpb /= 2) {
         Plan pl;
         if (plan_grid(c, c->sm_count, wpb, pl) == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
+        why = c->err;
+    }
+    {
+        const int load = (need + 15) / 16;
+        Plan pl;
+        if (plan_cluster(c, 16, MAX_WPB, load, pl) == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
         why = c->err;
     }
     return fail(c, KMC_EINVAL, "no launch plan fits this batch: %s", why.c_str());
