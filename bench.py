@@ -221,6 +221,11 @@ def reference_arm(args):
 # source it was taken on; reported as null once the source has changed.
 TRAFFIC_BYTES_PER_LAUNCH = 4709888
 TRAFFIC_KERNEL_SHA256 = "46ac65c128a0270692e58b7463b54dd423e0e7ebb9aee7a0b1cecfad35a2b4bf"
+# Warp instructions per uniformised step of the same workload and kernel
+# (ncu smsp__inst_executed.sum over one 200-schedule launch / its steps;
+# profiles/run_kernel_ising1024x18_small_full.md).  Includes the halo polls.
+INST_PER_STEP = 8403080341 / 51609600
+ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 
 
 def kernel_source_sha256() -> str:
@@ -453,6 +458,15 @@ def main():
     roof.update({"kernel": "kmcdev::run_kernel", "run_kernel_ms_avg": 1000 * avg_run_s,
                  "run_kernel_launches": run_n, "algorithmic_bytes_per_launch": bytes_step,
                  "step_level_achieved": bytes_step * args.steps / dev_s / 1e9})
+    # the bound this kernel actually meets: instruction issue
+    if traffic is not None and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        issue_peak = ISSUE_PER_SM_CYCLE * sms * clk["sm_mhz"] * 1e6
+        issue_ach = INST_PER_STEP * events_step / avg_run_s if avg_run_s > 0 else 0.0
+        roof["issue"] = {"bound": "issue", "achieved": issue_ach, "peak": issue_peak, "unit": "warp-inst/s",
+                         "frac": issue_ach / issue_peak,
+                         "source": "ncu warp instructions per step of this kernel (%.1f) x steps / launch time; "
+                                   "peak = 4 per SM cycle x %d SMs x median SM clock" % (INST_PER_STEP, sms)}
 
     variants = None
     if world == 1 and not args.no_variants and args.workload == "ising1024":
