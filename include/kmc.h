@@ -57,7 +57,7 @@ enum {
     KMC_SCHEDULE_FIXED = 1,       /* 0 1 2 3: stationary, NOT reversible (tests) */
     KMC_SCHEDULE_RANDOM_PERM = 2  /* uniform colour order per schedule (Eq. 10) */
 };
-enum { KMC_TIME_EXPONENTIAL = 0, KMC_TIME_EXPECTED = 1 };
+enum { KMC_TIME_EXPONENTIAL = 0, KMC_TIME_EXPECTED = 1, KMC_TIME_HORIZON = 2 };
 enum { KMC_OBS_SCHEDULE = 0, KMC_OBS_PASS = 1 };
 
 /*
@@ -124,7 +124,12 @@ kmc_status kmc_set_rate_table(kmc_ctx *ctx, double J, const double *beta, const 
  *   time_mode   KMC_TIME_EXPONENTIAL: each step advances the domain clock by
  *               Exp(Lambda_d) (Sec. 2.1, Erlang variate as a sum of -log u);
  *               KMC_TIME_EXPECTED: by its mean 1/Lambda_d (the paper's
- *               choice, Sec. 2.1).
+ *               choice, Sec. 2.1);
+ *               KMC_TIME_HORIZON: every visit runs its domain for the fixed
+ *               time dtau of kmc_set_horizon instead of k steps: a
+ *               Poisson(n_d nu dtau) number of uniformised steps, so the
+ *               visit is exp(dtau Q_d) and stays reversible; the clock
+ *               advances by exactly dtau per visit.
  *   obs_every   if > 0 and obs_dev != NULL, after every obs_every-th
  *               schedule of this call (or colour pass, see
  *               kmc_set_observation) the endpoint observables (Sec. 2.3)
@@ -141,6 +146,18 @@ kmc_status kmc_set_rate_table(kmc_ctx *ctx, double J, const double *beta, const 
 kmc_status kmc_run_schedule(kmc_ctx *ctx, int64_t n_schedules, int32_t schedule,
                             int32_t time_mode, int32_t obs_every, double *obs_dev,
                             void *stream);
+
+/*
+ * kmc_set_horizon -- domain time per visit for KMC_TIME_HORIZON runs (the
+ * continuous-time domain process over a fixed horizon, Sec. 2.1 with the
+ * domain's total rate Lambda_d = n_d nu).  The step count of a visit is drawn
+ * by inverting a table of the Poisson CDF (64-bit fixed point) with one
+ * Philox uniform per visit.  dtau = 0 turns the mode off.  KMC_EINVAL if
+ * n_d nu dtau is so large that the table exceeds 1024 entries (mean above
+ * about 650 steps per visit).  The table follows nu; it is rebuilt by
+ * kmc_set_rates.  Not while the stream is capturing.
+ */
+kmc_status kmc_set_horizon(kmc_ctx *ctx, double dtau);
 
 /*
  * kmc_set_observation -- where kmc_run_schedule takes its records.

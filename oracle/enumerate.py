@@ -130,6 +130,22 @@ class Enumerator:
         rates = [r / tot for r in raw]
         return self._apply_rates(p, sites, rates)
 
+    # -- fixed-time visits (Sec. 2.1 over a horizon) -----------------------------
+    def horizon_domain(self, d: int, p: np.ndarray, probs) -> np.ndarray:
+        """sum_K probs[K] step(d)^K p: a Poisson number of uniformised steps."""
+        acc = probs[0] * p
+        q = p
+        for K in range(1, len(probs)):
+            q = self.step(d, q)
+            acc = acc + probs[K] * q
+        return acc
+
+    def horizon_schedule(self, colours, p: np.ndarray, probs) -> np.ndarray:
+        for c in colours:
+            for d in self.domains_of_colour(c):
+                p = self.horizon_domain(d, p, probs)
+        return p
+
     # -- exact derivatives (forward mode) ----------------------------------------
     def set_score_table(self, grad30: np.ndarray):
         """Real-valued a_c and dlog a_c/d(beta, h) used for derivatives."""

@@ -28,7 +28,11 @@
  *     Eqs. 9-10): the palindrome 0 1 2 3 3 2 1 0 by default;
  *   - the clock: Erlang / Poisson variate of Sec. 2.1 (Eq. 2) as a sum of
  *     -log(u), or its expectation N*tau_S;
- *   - observables at schedule endpoints only (Sec. 2.3).
+ *   - observables at schedule endpoints only (Sec. 2.3);
+ *   - optionally, a domain process that runs for a fixed time dtau instead
+ *     of a fixed number of steps: the continuous-time chain of the domain
+ *     over dtau, exp(dtau Q_d) = sum_K Poisson(K; n_d nu dtau) P_d^K, i.e. a
+ *     Poisson number of uniformised steps, reversible because P_d is.
  *
  * Everything that steers the trajectory is integer: the rate table is held
  * in fixed point, A_c = round(a_c * 2^P) with P = 63 - log2(n_d), so that a
@@ -87,6 +91,7 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
 #define ORC_TAG_STEP 0u
 #define ORC_TAG_INIT 1u
 #define ORC_TAG_PERM 2u
+#define ORC_TAG_HORIZON 3u
 
 /* Rate laws, schedules, time modes, initial states. */
 #define ORC_RATE_METROPOLIS 0
@@ -96,6 +101,7 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
 #define ORC_SCHED_RANDOM_PERM 2
 #define ORC_TIME_EXPONENTIAL 0
 #define ORC_TIME_EXPECTED 1
+#define ORC_TIME_HORIZON 2
 #define ORC_INIT_RANDOM 0
 #define ORC_INIT_ALL_UP 1
 
@@ -408,7 +414,7 @@ double orc_domain_time(int time_mode, double esum, int64_t steps, int nd,
                        double nu)
 {
     double lambda = (double)nd * nu;
-    if (time_mode == ORC_TIME_EXPONENTIAL) return esum / lambda;
+    if (time_mode == ORC_TIME_EXPONENTIAL || time_mode == ORC_TIME_HORIZON) return esum / lambda;
     return (double)steps / lambda;
 }
 
@@ -441,6 +447,45 @@ static void orc_observe(const int8_t *s, int L, double J, double h,
  * order because they do not interact (Sec. 2.2).
  * Returns 0, or -1 for an invalid configuration.
  * ---------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------
+ * Fixed-time domain process: the number of uniformised steps in a visit of
+ * domain time dtau is Poisson with mean mu = n_d nu dtau (uniformisation,
+ * Sec. 2.1: events of a domain arrive at total rate n_d nu).  K is drawn by
+ * inversion: thresholds T_k = floor(F(k) 2^64) of the Poisson CDF F, with
+ * p_k = exp(-mu + k ln mu - lnGamma(k+1)) summed in k order, for
+ * k < kmax = ceil(mu + 12 sqrt(mu) + 30); K = the first k with U < T_k for
+ * the uniform U = w0 | w1 << 32 of Philox {0, d, np_lo, np_hi | TAG_HORIZON<<24},
+ * or kmax if there is none.
+ * ---------------------------------------------------------------------- */
+int orc_horizon_kmax(double mu)
+{
+    return (int)ceil(mu + 12.0 * sqrt(mu) + 30.0);
+}
+
+void orc_horizon_table(double mu, int kmax, uint64_t *out)
+{
+    double logmu = log(mu);
+    double F = 0.0;
+    for (int k = 0; k < kmax; ++k) {
+        double lp = -mu + (double)k * logmu - lgamma((double)k + 1.0);
+        F += exp(lp);
+        out[k] = (F >= 1.0) ? UINT64_MAX : (uint64_t)ldexp(F, 64);
+    }
+}
+
+static int orc_horizon_steps(const uint64_t *tab, int kmax, uint32_t key0, uint32_t key1,
+                             uint64_t np, uint32_t d)
+{
+    uint32_t ctr[4] = {0u, d, (uint32_t)np, (uint32_t)((np >> 32) & 0xFFFFFFu) | (ORC_TAG_HORIZON << 24)};
+    uint32_t key[2] = {key0, key1};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    uint64_t U = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+    for (int k = 0; k < kmax; ++k)
+        if (U < tab[k]) return k;
+    return kmax;
+}
+
 static void orc_record(const int8_t *s, int L, double J, double h, int time_mode,
                        const double *esum, const int64_t *steps, int ND, int nd,
                        double nu, const double *score, double *rec)
@@ -460,12 +505,12 @@ static void orc_record(const int8_t *s, int L, double J, double h, int time_mode
  * one colour, so its end is a domain-process endpoint; the schedules read
  * with shifted registers end there (Sec. 2.3), which makes these valid
  * observation points as well. */
-int orc_run_replica_obs(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
-                        uint64_t seed, int schedule, int time_mode, double nu,
-                        double J, double h, int64_t sched_begin, int64_t n_sched,
-                        int obs_every, int obs_unit, double *esum, int64_t *steps,
-                        uint64_t *hash, int64_t *flips, double *obs,
-                        const double *grad, double *score)
+int orc_run_replica_ex(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
+                       uint64_t seed, int schedule, int time_mode, double nu,
+                       double J, double h, int64_t sched_begin, int64_t n_sched,
+                       int obs_every, int obs_unit, double dtau, double *esum, int64_t *steps,
+                       uint64_t *hash, int64_t *flips, double *obs,
+                       const double *grad, double *score)
 {
     if (L <= 0 || Ld <= 0 || L % Ld != 0) return -1;
     int Dx = L / Ld;
@@ -474,6 +519,16 @@ int orc_run_replica_obs(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
     if (k < 0 || k > 65535) return -1;
     if (obs_unit != 0 && obs_unit != 1) return -1;
     const int ND = Dx * Dx, nd = Ld * Ld;
+    uint64_t *htab = NULL;
+    int hkmax = 0;
+    if (time_mode == ORC_TIME_HORIZON) {
+        if (!(dtau > 0.0)) return -1;
+        double mu = (double)nd * nu * dtau;
+        hkmax = orc_horizon_kmax(mu);
+        if (hkmax > 1024) return -1;
+        htab = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)hkmax);
+        orc_horizon_table(mu, hkmax, htab);
+    }
     const int width = score ? 6 : 4;
     uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
     int64_t passes = 0; /* colour passes completed in this call */
@@ -481,7 +536,7 @@ int orc_run_replica_obs(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
         uint64_t n = (uint64_t)(sched_begin + nl);
         int col[8];
         int nph = orc_schedule_colours(schedule, n, seed, col);
-        if (nph < 0) return -1;
+        if (nph < 0) { free(htab); return -1; }
         for (int p = 0; p < nph; ++p) {
             /* eight phase slots per schedule index for every schedule kind,
              * so that no two kinds ever share a Philox counter */
@@ -490,10 +545,15 @@ int orc_run_replica_obs(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
                 int bx = d % Dx, by = d / Dx;
                 int colour = (bx & 1) | ((by & 1) << 1);
                 if (colour != col[p]) continue;
-                orc_visit(s, L, Ld, bx, by, k, A, key0, key1, np,
+                int kv = k;
+                if (time_mode == ORC_TIME_HORIZON)
+                    kv = orc_horizon_steps(htab, hkmax, key0, key1, np, (uint32_t)d);
+                orc_visit(s, L, Ld, bx, by, kv, A, key0, key1, np,
                           (uint32_t)d, time_mode, &esum[d], &hash[d],
                           &flips[d], &steps[d], grad,
                           score ? &score[2 * d] : NULL);
+                /* fixed-time visit: the domain clock advances by dtau */
+                if (time_mode == ORC_TIME_HORIZON) esum[d] += dtau * (double)nd * nu;
             }
             ++passes;
             if (obs_unit == 1 && obs_every > 0 && obs != NULL && passes % obs_every == 0)
@@ -504,7 +564,20 @@ int orc_run_replica_obs(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
             orc_record(s, L, J, h, time_mode, esum, steps, ND, nd, nu, score,
                        &obs[width * ((nl + 1) / obs_every - 1)]);
     }
+    free(htab);
     return 0;
+}
+
+int orc_run_replica_obs(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
+                        uint64_t seed, int schedule, int time_mode, double nu,
+                        double J, double h, int64_t sched_begin, int64_t n_sched,
+                        int obs_every, int obs_unit, double *esum, int64_t *steps,
+                        uint64_t *hash, int64_t *flips, double *obs,
+                        const double *grad, double *score)
+{
+    return orc_run_replica_ex(s, L, Ld, k, A, seed, schedule, time_mode, nu, J, h, sched_begin,
+                              n_sched, obs_every, obs_unit, 0.0, esum, steps, hash, flips, obs,
+                              grad, score);
 }
 
 int orc_run_replica_grad(int8_t *s, int L, int Ld, int k, const uint64_t A[10],

@@ -29,6 +29,7 @@ SCHED_FIXED = 1
 SCHED_RANDOM_PERM = 2
 TIME_EXPONENTIAL = 0
 TIME_EXPECTED = 1
+TIME_HORIZON = 2  # each visit runs for domain time dtau: Poisson(n_d nu dtau) steps
 INIT_RANDOM = 0
 INIT_ALL_UP = 1
 
@@ -91,6 +92,12 @@ def lib():
         ra = L.orc_run_replica.argtypes
         L.orc_run_replica_obs.argtypes = ra[:14] + [ctypes.c_int] + ra[14:] + [dp, dp]
         L.orc_run_replica_obs.restype = ctypes.c_int
+        L.orc_run_replica_ex.argtypes = ra[:14] + [ctypes.c_int, ctypes.c_double] + ra[14:] + [dp, dp]
+        L.orc_run_replica_ex.restype = ctypes.c_int
+        L.orc_horizon_kmax.argtypes = [ctypes.c_double]
+        L.orc_horizon_kmax.restype = ctypes.c_int
+        L.orc_horizon_table.argtypes = [ctypes.c_double, ctypes.c_int, u64p]
+        L.orc_horizon_table.restype = None
         L.orc_sample_final_states_grad.argtypes = L.orc_sample_final_states.argtypes + [dp, dp]
         L.orc_sample_final_states_grad.restype = ctypes.c_int
         L.orc_hash_basis.argtypes = []
@@ -192,6 +199,18 @@ def sample_final_states(s0: np.ndarray, Ld: int, k: int, A: np.ndarray, seed0: i
     return out
 
 
+def horizon_kmax(mu: float) -> int:
+    return int(lib().orc_horizon_kmax(float(mu)))
+
+
+def horizon_table(mu: float) -> np.ndarray:
+    """Poisson CDF thresholds floor(F(k) 2^64), k < kmax(mu)."""
+    kmax = horizon_kmax(mu)
+    out = np.zeros(kmax, dtype=np.uint64)
+    lib().orc_horizon_table(float(mu), kmax, _ptr(out, ctypes.c_uint64))
+    return out
+
+
 @dataclass
 class Replica:
     """One lattice replica and its per-domain counters (oracle side)."""
@@ -213,6 +232,7 @@ class Replica:
     sched_done: int = 0
     grad: np.ndarray = field(default=None)
     score: np.ndarray = field(default=None)
+    dtau: float = 0.0  # domain time per visit (time mode TIME_HORIZON)
 
     def __post_init__(self):
         if self.spins is None:
@@ -248,10 +268,10 @@ class Replica:
         A = np.ascontiguousarray(self.A)
         gptr = _ptr(self.grad, ctypes.c_double) if with_score else None
         sptr = _ptr(self.score, ctypes.c_double) if with_score else None
-        rc = lib().orc_run_replica_obs(
+        rc = lib().orc_run_replica_ex(
             _ptr(s, ctypes.c_int8), self.L, self.Ld, self.k, _ptr(A, ctypes.c_uint64),
             self.seed, schedule, time_mode, self.nu, self.J, self.h,
-            self.sched_done, n_sched, obs_every, 1 if obs_per_pass else 0,
+            self.sched_done, n_sched, obs_every, 1 if obs_per_pass else 0, float(self.dtau),
             _ptr(self.esum, ctypes.c_double), _ptr(self.steps, ctypes.c_int64),
             _ptr(self.hash, ctypes.c_uint64), _ptr(self.flips, ctypes.c_int64),
             _ptr(obs, ctypes.c_double), gptr, sptr)

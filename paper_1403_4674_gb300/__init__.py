@@ -9,9 +9,9 @@ Python binding.
 """
 from .api import (KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID, KMC_OBS_PASS, KMC_OBS_SCHEDULE, KMC_INIT_ALL_UP, KMC_INIT_KEEP, KMC_INIT_PER_REPLICA, KMC_INIT_RANDOM, KMC_RATE_BARKER,  # noqa: F401
                   KMC_RATE_METROPOLIS, KMC_SCHEDULE_FIXED, KMC_SCHEDULE_PALINDROME,
-                  KMC_SCHEDULE_RANDOM_PERM, KMC_TIME_EXPECTED, KMC_TIME_EXPONENTIAL, Lattice,
+                  KMC_SCHEDULE_RANDOM_PERM, KMC_TIME_EXPECTED, KMC_TIME_EXPONENTIAL, KMC_TIME_HORIZON, Lattice,
                   kmc_create_lattice, kmc_debug_barrier, kmc_destroy, kmc_domain_state,
                   kmc_enable_grad, kmc_get_launch, kmc_get_rate_table, kmc_grad,
                   kmc_kernel_launches, kmc_lr_estimate, kmc_observables, kmc_profile, kmc_profile_read, kmc_reset, kmc_run_schedule, kmc_run_schedule_noalloc,
-                  kmc_set_launch, kmc_set_observation, kmc_set_rate_table, kmc_set_replica_params, kmc_set_rates, kmc_sync, kmc_version)
+                  kmc_set_horizon, kmc_set_launch, kmc_set_observation, kmc_set_rate_table, kmc_set_replica_params, kmc_set_rates, kmc_sync, kmc_version)
 from ._lib import KmcError  # noqa: F401

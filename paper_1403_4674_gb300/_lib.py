@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "KMC_OK", -1: "KMC_EINVAL", -2: "KMC_ENOMEM", -3: "KMC_ECUDA"
 EXPORTS = [
     "kmc_create_lattice", "kmc_set_rates", "kmc_set_rate_table", "kmc_run_schedule",
     "kmc_observables", "kmc_grad", "kmc_lr_estimate", "kmc_enable_grad", "kmc_reset", "kmc_sync",
-    "kmc_domain_state", "kmc_get_rate_table", "kmc_set_launch", "kmc_get_launch", "kmc_set_replica_params", "kmc_set_observation",
+    "kmc_domain_state", "kmc_get_rate_table", "kmc_set_launch", "kmc_get_launch", "kmc_set_replica_params", "kmc_set_observation", "kmc_set_horizon",
     "kmc_debug_barrier", "kmc_run_schedule_noalloc", "kmc_profile", "kmc_profile_read", "kmc_kernel_launches", "kmc_last_error", "kmc_destroy", "kmc_version",
 ]
 
@@ -68,6 +68,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmc_reset.argtypes = [vp, i32, vp]
     L.kmc_set_replica_params.argtypes = [vp, vp, vp]
     L.kmc_set_observation.argtypes = [vp, i32]
+    L.kmc_set_horizon.argtypes = [vp, dbl]
     L.kmc_sync.argtypes = [vp]
     L.kmc_domain_state.argtypes = [vp, P(u64), P(i64), P(dbl)]
     L.kmc_get_rate_table.argtypes = [vp, i32, P(dbl), P(u64)]

@@ -16,7 +16,7 @@ from ._lib import KmcError, load
 KMC_INIT_RANDOM, KMC_INIT_ALL_UP, KMC_INIT_KEEP, KMC_INIT_PER_REPLICA = 0, 1, 2, 3
 KMC_RATE_METROPOLIS, KMC_RATE_BARKER = 0, 1
 KMC_SCHEDULE_PALINDROME, KMC_SCHEDULE_FIXED, KMC_SCHEDULE_RANDOM_PERM = 0, 1, 2
-KMC_TIME_EXPONENTIAL, KMC_TIME_EXPECTED = 0, 1
+KMC_TIME_EXPONENTIAL, KMC_TIME_EXPECTED, KMC_TIME_HORIZON = 0, 1, 2
 KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID = 0, 1, 2
 KMC_OBS_SCHEDULE, KMC_OBS_PASS = 0, 1
 
@@ -133,6 +133,10 @@ def kmc_set_replica_params(ctx, k_steps: Optional[Sequence[int]] = None, init: O
     kp = ctypes.cast(_arr(k_steps, _i32), ctypes.c_void_p) if k_steps is not None else None
     ip = ctypes.cast(_arr(init, _i32), ctypes.c_void_p) if init is not None else None
     _check(ctx, load().kmc_set_replica_params(ctx, kp, ip))
+
+
+def kmc_set_horizon(ctx, dtau: float):
+    _check(ctx, load().kmc_set_horizon(ctx, float(dtau)))
 
 
 def kmc_set_observation(ctx, unit: int):
@@ -288,6 +292,10 @@ class Lattice:
 
     def sync(self):
         kmc_sync(self.ctx)
+
+    def set_horizon(self, dtau: float):
+        """Domain time per visit for KMC_TIME_HORIZON runs (0 turns it off)."""
+        kmc_set_horizon(self.ctx, dtau)
 
     def set_observation(self, unit: int):
         """KMC_OBS_SCHEDULE: records at schedule endpoints; KMC_OBS_PASS: at

@@ -66,7 +66,7 @@ struct kmc_ctx {
     int *d_err = nullptr;
     unsigned long long *d_obs_acc = nullptr;
     size_t obs_acc_words = 0;
-    void *d_tmp = nullptr; // n_dom * 24 + n_rep * 64 bytes, host-facing staging
+    void *d_tmp = nullptr; // n_dom * 32 + n_rep * 64 bytes, host-facing staging
     // device copy of the launch plan
     uint32_t *d_plan = nullptr;
     size_t plan_words = 0;
@@ -79,6 +79,9 @@ struct kmc_ctx {
     int64_t sched_done = 0;
     int64_t visits_done = 0;
     int last_time_mode = KMC_TIME_EXPONENTIAL;
+    double dtau = 0.0;          // fixed-time visits (KMC_TIME_HORIZON): domain time per visit
+    int hkmax = 0;
+    uint64_t *d_htab = nullptr; // Poisson CDF thresholds, HORIZON_MAX_STEPS words
     int obs_unit = KMC_OBS_SCHEDULE;
     bool grad = false;
 
@@ -583,10 +586,13 @@ kmc_status default_plan(kmc_ctx *c)
 
 // Endpoint observables of the packed state into acc[n_rep][OBS_WORDS]
 // (bond sum, magnetisation, summed domain clocks, summed scores).
-kmc_status launch_observe(kmc_ctx *c, cudaStream_t s, bool expo, unsigned long long *acc)
+kmc_status launch_observe(kmc_ctx *c, cudaStream_t s, int time_mode, unsigned long long *acc)
 {
     CUDA_TRY(c, cudaMemsetAsync(acc, 0, (size_t)c->n_rep * OBS_WORDS * 8, s));
     RunParams P = run_params(c);
+    const bool expo = time_mode == KMC_TIME_EXPONENTIAL;
+    P.horizon = time_mode == KMC_TIME_HORIZON;
+    P.dtau = c->dtau;
     const int blocks = grid_for(c->n_dom, 8);
 #define KMC_OBS(LDV)                                                                                         \
     if (expo) observe_kernel<LDV, true><<<blocks, 256, 0, s>>>(P, c->d_dom_rep, c->n_dom, c->visits_done, acc); \
@@ -625,6 +631,62 @@ void build_gfix(const double *a, const double *gb, const double *gh, int log2nd,
     out[21] = out[22] = out[23] = 0;
 }
 
+kmc_status sync_ctx(kmc_ctx *c);
+
+// Per-domain counters to host arrays of n_dom entries (any may be NULL).
+kmc_status domain_state(kmc_ctx *c, uint64_t *hash, int64_t *flips, double *t, int64_t *steps)
+{
+    cudaStream_t s = c->stream;
+    uint64_t *dh = reinterpret_cast<uint64_t *>(c->d_tmp);
+    int64_t *df = reinterpret_cast<int64_t *>(dh + c->n_dom);
+    double *dt = reinterpret_cast<double *>(df + c->n_dom);
+    int64_t *ds = reinterpret_cast<int64_t *>(dt + c->n_dom);
+    const double lambda = (double)(c->LD * c->LD) * c->nu;
+    const double dtau = c->last_time_mode == KMC_TIME_HORIZON ? c->dtau : 0.0;
+    if (c->last_time_mode == KMC_TIME_EXPONENTIAL)
+        domain_state_kernel<true><<<grid_for(c->n_dom, 256), 256, 0, s>>>(
+            c->d_dctr, c->n_dom, c->visits_done, c->d_dom_rep, c->d_k, lambda, dtau, dh, df, dt, ds);
+    else
+        domain_state_kernel<false><<<grid_for(c->n_dom, 256), 256, 0, s>>>(
+            c->d_dctr, c->n_dom, c->visits_done, c->d_dom_rep, c->d_k, lambda, dtau, dh, df, dt, ds);
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    const size_t n = (size_t)c->n_dom;
+    if (hash) CUDA_TRY(c, cudaMemcpyAsync(hash, dh, n * 8, cudaMemcpyDeviceToHost, s));
+    if (flips) CUDA_TRY(c, cudaMemcpyAsync(flips, df, n * 8, cudaMemcpyDeviceToHost, s));
+    if (t) CUDA_TRY(c, cudaMemcpyAsync(t, dt, n * 8, cudaMemcpyDeviceToHost, s));
+    if (steps) CUDA_TRY(c, cudaMemcpyAsync(steps, ds, n * 8, cudaMemcpyDeviceToHost, s));
+    return sync_ctx(c);
+}
+
+// Poisson CDF thresholds of the fixed-time visit: floor(F(k) 2^64) for
+// k < kmax = ceil(mu + 12 sqrt(mu) + 30), mu = n_d nu dtau, with the pmf
+// exp(-mu + k ln mu - lnGamma(k + 1)) summed in k order.
+kmc_status upload_horizon(kmc_ctx *c)
+{
+    if (!(c->dtau > 0.0)) return KMC_OK;
+    const double mu = (double)(c->LD * c->LD) * c->nu * c->dtau;
+    const int kmax = (int)std::ceil(mu + 12.0 * std::sqrt(mu) + 30.0);
+    if (kmax > HORIZON_MAX_STEPS)
+        return fail(c, KMC_EINVAL, "visit time too long: n_d nu dtau = %g needs %d > %d table entries", mu, kmax,
+                    HORIZON_MAX_STEPS);
+    if (!c->d_htab) {
+        kmc_status st = dev_alloc(c, &c->d_htab, HORIZON_MAX_STEPS);
+        if (st != KMC_OK) return st;
+    }
+    std::vector<uint64_t> tab(kmax);
+    const double logmu = std::log(mu);
+    double F = 0.0;
+    for (int k = 0; k < kmax; ++k) {
+        const double lp = -mu + (double)k * logmu - std::lgamma((double)k + 1.0);
+        F += std::exp(lp);
+        tab[k] = (F >= 1.0) ? UINT64_MAX : (uint64_t)std::ldexp(F, 64);
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_htab, tab.data(), (size_t)kmax * 8, cudaMemcpyHostToDevice, c->stream));
+    c->hkmax = kmax;
+    return KMC_OK; // pageable source: consumed when the copy returns
+}
+
 kmc_status upload_rates(kmc_ctx *c)
 {
     std::vector<uint64_t> A16((size_t)c->n_rep * 16, 0);
@@ -647,7 +709,7 @@ kmc_status upload_rates(kmc_ctx *c)
     CUDA_TRY(c, cudaMemcpyAsync(c->d_gfix, gfix.data(), gfix.size() * 8, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_grad, g32.data(), g32.size() * 8, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_h, c->h.data(), c->h.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    return KMC_OK;
+    return upload_horizon(c); // the table depends on nu
 }
 
 kmc_status launch_pack(kmc_ctx *c, cudaStream_t s)
@@ -723,7 +785,7 @@ void free_all(kmc_ctx *c)
                      (void **)&c->d_site_off, (void **)&c->d_blk_off, (void **)&c->d_seed, (void **)&c->d_A,
                      (void **)&c->d_gfix, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_tiles,
                      (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_err,
-                     (void **)&c->d_obs_acc, (void **)&c->d_tmp, (void **)&c->d_plan};
+                     (void **)&c->d_obs_acc, (void **)&c->d_tmp, (void **)&c->d_plan, (void **)&c->d_htab};
     for (void **p : ptrs) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -855,7 +917,7 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     ALLOC(c->d_err, 1);
     {
         uint8_t *tmp = nullptr;
-        ALLOC(tmp, ndom * 24 + (size_t)n_replicas * 64);
+        ALLOC(tmp, ndom * 32 + (size_t)n_replicas * 64);
         c->d_tmp = tmp;
     }
 #undef ALLOC
@@ -1012,6 +1074,18 @@ kmc_status kmc_set_launch(kmc_ctx *c, int32_t mode, int32_t size, int32_t warps_
     return KMC_OK;
 }
 
+kmc_status kmc_set_horizon(kmc_ctx *c, double dtau)
+{
+    if (!c) return KMC_EINVAL;
+    if (refuse_capture(c, "kmc_set_horizon") != KMC_OK) return KMC_EINVAL;
+    if (!(dtau >= 0.0) || !std::isfinite(dtau)) return fail(c, KMC_EINVAL, "dtau must be finite and >= 0");
+    const double old = c->dtau;
+    c->dtau = dtau;
+    kmc_status st = upload_horizon(c);
+    if (st != KMC_OK) c->dtau = old;
+    return st;
+}
+
 kmc_status kmc_set_observation(kmc_ctx *c, int32_t unit)
 {
     if (!c) return KMC_EINVAL;
@@ -1087,7 +1161,10 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     if (n_schedules < 0) return fail(c, KMC_EINVAL, "n_schedules must be >= 0");
     if (schedule < KMC_SCHEDULE_PALINDROME || schedule > KMC_SCHEDULE_RANDOM_PERM)
         return fail(c, KMC_EINVAL, "bad schedule kind");
-    if (time_mode != KMC_TIME_EXPONENTIAL && time_mode != KMC_TIME_EXPECTED) return fail(c, KMC_EINVAL, "bad time mode");
+    if (time_mode != KMC_TIME_EXPONENTIAL && time_mode != KMC_TIME_EXPECTED && time_mode != KMC_TIME_HORIZON)
+        return fail(c, KMC_EINVAL, "bad time mode");
+    if (time_mode == KMC_TIME_HORIZON && !(c->dtau > 0.0))
+        return fail(c, KMC_EINVAL, "KMC_TIME_HORIZON needs a visit time (kmc_set_horizon)");
     if (obs_every < 0) return fail(c, KMC_EINVAL, "obs_every must be >= 0");
     if (c->sched_done + n_schedules >= (1ll << 52)) return fail(c, KMC_EINVAL, "schedule index overflow");
     c->stream = (cudaStream_t)stream;
@@ -1115,13 +1192,19 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     if ((st = launch_pack(c, s)) != KMC_OK) return st;
     // records are built from the state before the launch plus per-visit changes
     unsigned long long *base = reinterpret_cast<unsigned long long *>(c->d_tmp);
-    if (n_obs > 0 && (st = launch_observe(c, s, time_mode == KMC_TIME_EXPONENTIAL, base)) != KMC_OK) return st;
+    if (n_obs > 0 && (st = launch_observe(c, s, time_mode, base)) != KMC_OK) return st;
     RunParams P = run_params(c);
     P.schedule = schedule;
     P.obs_every = want_obs ? obs_every : 0;
     P.obs_acc = (want_obs && n_obs > 0) ? c->d_obs_acc : nullptr;
     P.obs_pass = (pass_obs && n_obs > 0) ? 1 : 0;
     P.n_obs = n_obs;
+    if (time_mode == KMC_TIME_HORIZON) {
+        P.horizon = 1;
+        P.hkmax = c->hkmax;
+        P.htab = c->d_htab;
+        P.dtau = c->dtau;
+    }
     P.sched_begin = c->sched_done;
     P.n_sched = n_schedules;
     P.visits_before = c->visits_done;
@@ -1186,7 +1269,7 @@ kmc_status kmc_observables(kmc_ctx *c, double *E_per_site, double *m, double *t,
     if ((st = launch_pack(c, s)) != KMC_OK) return st;
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(c->d_tmp);
     const size_t words = (size_t)c->n_rep * OBS_WORDS;
-    if ((st = launch_observe(c, s, c->last_time_mode == KMC_TIME_EXPONENTIAL, acc)) != KMC_OK) return st;
+    if ((st = launch_observe(c, s, c->last_time_mode, acc)) != KMC_OK) return st;
     std::vector<unsigned long long> h_acc(words);
     CUDA_TRY(c, cudaMemcpyAsync(h_acc.data(), acc, words * 8, cudaMemcpyDeviceToHost, s));
     if ((st = sync_ctx(c)) != KMC_OK) return st;
@@ -1201,15 +1284,19 @@ kmc_status kmc_observables(kmc_ctx *c, double *E_per_site, double *m, double *t,
         if (E_per_site) E_per_site[r] = e;
         if (m) m[r] = mg / N;
         if (t) t[r] = tsum / ((double)c->Dx[r] * c->Dx[r]);
-        if (steps) steps[r] = c->visits_done * (int64_t)c->kr[r] * (int64_t)c->Dx[r] * c->Dx[r];
     }
-    if (flips) {
-        std::vector<int64_t> fl(c->n_dom);
-        if ((st = kmc_domain_state(c, nullptr, fl.data(), nullptr)) != KMC_OK) return st;
+    if (flips || steps) {
+        // per-domain counts, summed per replica (Eq. 11: the step counter)
+        std::vector<int64_t> fl(c->n_dom), sp(c->n_dom);
+        if ((st = domain_state(c, nullptr, fl.data(), nullptr, sp.data())) != KMC_OK) return st;
         for (int r = 0; r < c->n_rep; ++r) {
-            int64_t f = 0;
-            for (uint32_t g = c->dom_off[r]; g < c->dom_off[r + 1]; ++g) f += fl[g];
-            flips[r] = f;
+            int64_t f = 0, q = 0;
+            for (uint32_t g = c->dom_off[r]; g < c->dom_off[r + 1]; ++g) {
+                f += fl[g];
+                q += sp[g];
+            }
+            if (flips) flips[r] = f;
+            if (steps) steps[r] = q;
         }
     }
     return KMC_OK;
@@ -1219,24 +1306,7 @@ kmc_status kmc_domain_state(kmc_ctx *c, uint64_t *hash, int64_t *flips, double *
 {
     if (!c) return KMC_EINVAL;
     if (refuse_capture(c, "kmc_domain_state") != KMC_OK) return KMC_EINVAL;
-    cudaStream_t s = c->stream;
-    uint64_t *dh = reinterpret_cast<uint64_t *>(c->d_tmp);
-    int64_t *df = reinterpret_cast<int64_t *>(dh + c->n_dom);
-    double *dt = reinterpret_cast<double *>(df + c->n_dom);
-    const double lambda = (double)(c->LD * c->LD) * c->nu;
-    if (c->last_time_mode == KMC_TIME_EXPONENTIAL)
-        domain_state_kernel<true><<<grid_for(c->n_dom, 256), 256, 0, s>>>(c->d_dctr, c->n_dom, c->visits_done,
-                                                                            c->d_dom_rep, c->d_k, lambda, dh, df, dt);
-    else
-        domain_state_kernel<false><<<grid_for(c->n_dom, 256), 256, 0, s>>>(c->d_dctr, c->n_dom, c->visits_done,
-                                                                             c->d_dom_rep, c->d_k, lambda, dh, df, dt);
-    ++c->launches;
-    CUDA_TRY(c, cudaGetLastError());
-    const size_t n = (size_t)c->n_dom;
-    if (hash) CUDA_TRY(c, cudaMemcpyAsync(hash, dh, n * 8, cudaMemcpyDeviceToHost, s));
-    if (flips) CUDA_TRY(c, cudaMemcpyAsync(flips, df, n * 8, cudaMemcpyDeviceToHost, s));
-    if (t) CUDA_TRY(c, cudaMemcpyAsync(t, dt, n * 8, cudaMemcpyDeviceToHost, s));
-    return sync_ctx(c);
+    return domain_state(c, hash, flips, t, nullptr);
 }
 
 kmc_status kmc_grad(kmc_ctx *c, double *score_dev, int32_t reset)
@@ -1408,8 +1478,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     if (n_schedules > 0) {
         if ((st = launch_pack(&c, s)) != KMC_OK) return bad(st, c.err);
         if (n_obs > 0 &&
-            (st = launch_observe(&c, s, time_mode == KMC_TIME_EXPONENTIAL,
-                                 reinterpret_cast<unsigned long long *>(c.d_tmp))) != KMC_OK)
+            (st = launch_observe(&c, s, time_mode, reinterpret_cast<unsigned long long *>(c.d_tmp))) != KMC_OK)
             return bad(st, c.err);
         RunParams P = run_params(&c);
         P.schedule = schedule;

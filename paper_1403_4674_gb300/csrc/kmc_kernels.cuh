@@ -13,8 +13,8 @@
 //     of row y is (y % RPL)*32 + y / RPL (RPL = rows per lane, 2 for LD = 64,
 //     else 1).  A neighbour reads its halo and checks that it is current with
 //     the same 64-bit loads.
-//   * per-domain counters dctr[g*6 + ...]: event hash, real flips, clock
-//     mantissa, clock exponent, score d/dbeta, score d/dh.
+//   * per-domain counters dctr[g*7 + ...]: event hash, real flips, clock
+//     mantissa, clock exponent, score d/dbeta, score d/dh, steps.
 //
 // The run kernel is persistent: every CTA owns a fixed set of domains (its
 // "slots") for the whole launch; their tiles, edges, counters and the rate
@@ -40,10 +40,11 @@ namespace kmcdev {
 constexpr uint32_t FULL_WARP = 0xffffffffu;
 constexpr int EDGE_N = 0, EDGE_S = 1, EDGE_W = 2, EDGE_E = 3;
 constexpr int DCTR_HASH = 0, DCTR_FLIPS = 1, DCTR_CLKM = 2, DCTR_CLKE = 3,
-              DCTR_SB = 4, DCTR_SH = 5, DCTR_WORDS = 6;
+              DCTR_SB = 4, DCTR_SH = 5, DCTR_STEPS = 6, DCTR_WORDS = 7;
 constexpr uint64_t HASH_BASIS = 0xcbf29ce484222325ull; // FNV-1a 64 offset basis
 constexpr uint64_t HASH_PRIME = 0x00000100000001b3ull; // FNV-1a 64 prime
-constexpr uint32_t TAG_INIT = 1u, TAG_PERM = 2u;       // step draws use tag 0
+constexpr uint32_t TAG_INIT = 1u, TAG_PERM = 2u, TAG_HORIZON = 3u; // step draws use tag 0
+constexpr int HORIZON_MAX_STEPS = 1024; // table length limit of the fixed-time visit
 constexpr int ERR_TIMEOUT = 1, ERR_SPIN = 2, ERR_INTERNAL = 3;
 constexpr int SCHED_PALINDROME = 0, SCHED_FIXED = 1, SCHED_RANDOM_PERM = 2;
 constexpr int INIT_KEEP = 2, INIT_PER_REPLICA = 3;
@@ -58,13 +59,13 @@ constexpr int OBS_WORDS = 5; // bonds, mag, clock sum, score beta sum, score h s
 constexpr int RT_BYTES = 640;
 constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524, RT_K = 528, RT_GB = 128, RT_GH = 544, RT_GSCALE = 624;
 constexpr int GFIX_WORDS = 24; // per replica: Gb[10], Gh[10], 2^-Q bits, pad
-// Slot: [tile][stamped edges 64][counters 48][meta 32][observation 48];
+// Slot: [tile][stamped edges 64][counters 56][meta 32][observation 48];
 // meta u32: g, replica, d, rt, nb[4];
 // observation, since the record began: u32 record, i32 bond change, i32
 // magnetisation change, u32 steps (EXPECTED clock), u64 mantissa and i64
 // exponent of the product of clock variates (EXPONENTIAL clock), f64 score
 // changes d/dbeta, d/dh.
-constexpr int SLOT_EXTRA = 64 + 48 + 32 + 48;
+constexpr int SLOT_EXTRA = 64 + 56 + 32 + 48;
 constexpr uint32_t NO_RECORD = 0xFFFFFFFFu;
 constexpr int EDGE_WORDS = 8; // stamped 64-bit words per domain
 
@@ -110,6 +111,11 @@ struct RunParams {
     unsigned long long *obs_acc;
     int obs_pass;   // 1: a record after every obs_every-th colour pass
     int64_t n_obs;  // records of this launch
+    // fixed-time visits: K ~ Poisson(n_d nu dtau) steps by table inversion
+    int horizon;
+    int hkmax;
+    const uint64_t *htab; // [hkmax] floor(F(k) 2^64) of the Poisson CDF
+    double dtau;
     int *err;
     uint64_t bar_limit_ns;
     int debug_extra;
@@ -479,6 +485,28 @@ __device__ __forceinline__ Chunk draw_chunk(uint2 key, uint32_t d, uint64_t np0,
     return ch;
 }
 
+// Steps of a fixed-time visit (domain time dtau): the number of uniformised
+// events in that time is Poisson(n_d nu dtau) (Sec. 2.1), drawn by inversion
+// with the uniform U = w0 | w1 << 32 of Philox {0, d, np_lo, np_hi |
+// TAG_HORIZON << 24}: K = the first k with U < tab[k] = floor(F(k) 2^64), or
+// kmax.  Two rounds of 32 parallel comparisons: the last threshold of every
+// block of 32, then the thresholds of the first block whose last one exceeds U.
+__device__ __forceinline__ int horizon_steps(uint2 key, uint32_t d, uint64_t np, const uint64_t *tab, int kmax,
+                                             int lane)
+{
+    const uint4 w = philox4x32_10(
+        make_uint4(0u, d, (uint32_t)np, ((uint32_t)(np >> 32) & 0xFFFFFFu) | (TAG_HORIZON << 24)), key);
+    const uint64_t U = ((uint64_t)w.y << 32) | w.x;
+    const int nblk = (kmax + 31) / 32; // <= 32: kmax <= HORIZON_MAX_STEPS
+    const int last = min(32 * lane + 31, kmax - 1);
+    const unsigned mb = __ballot_sync(FULL_WARP, lane < nblk && U < __ldg(&tab[lane < nblk ? last : 0]));
+    if (!mb) return kmax;
+    const int b = __ffs(mb) - 1;
+    const int i = 32 * b + lane;
+    const unsigned mk = __ballot_sync(FULL_WARP, i < kmax && U < __ldg(&tab[i < kmax ? i : 0]));
+    return 32 * b + __ffs(mk) - 1;
+}
+
 // Lane c (< 10) holds class c's fixed-point rate and (scores) dlog a_c /
 // d(beta, h) and the fixed-point products a_c dlog a_c / d(beta, h); loaded
 // before the halo wait.
@@ -525,7 +553,7 @@ template <int LD, bool EXPO, bool GRAD>
 __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const RateRegs &rr, uint2 key,
                                            typename Geo<LD>::row_t hN, typename Geo<LD>::row_t hS,
                                            uint64_t hW, uint64_t hE, uint32_t d, uint64_t np0,
-                                           int nfused, int k, int lane, int *err, const Chunk &first)
+                                           int nfused, int k, int lane, int *err, const Chunk &first, int total)
 {
     using G = Geo<LD>;
     using row_t = typename G::row_t;
@@ -561,7 +589,6 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
     };
     grad_state();
 
-    const int total = nfused * k;
     for (int base = 0; base < total; base += 32) {
         const Chunk ch = (base == 0) ? first : draw_chunk<EXPO>(key, d, np0, base, total, k, lane);
         const uint64_t tgt = ch.tgt, ebase = ch.ebase;
@@ -801,7 +828,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
     using mem_t = typename G::mem_t;
     constexpr int TB = G::TILE_BYTES;
     constexpr int SB = slot_bytes<LD>();
-    constexpr int OFF_EDGE = TB, OFF_CTR = TB + 64, OFF_META = TB + 112, OFF_OBS = TB + 144;
+    constexpr int OFF_EDGE = TB, OFF_CTR = TB + 64, OFF_META = TB + 120, OFF_OBS = TB + 152;
     // stamped words a halo read needs per neighbour: one half for LD <= 32, two for 64
     constexpr int HALVES = (LD > 32) ? 2 : 1;
 
@@ -953,7 +980,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         if (ob[2] != 0) atomicAdd(&acc[1], (unsigned long long)(long long)(int)ob[2]);
         // the record's clock advance of this domain: one logarithm per record
         const double dt = EXPO ? domain_time(true, obm[0], (int64_t)obm[1], 0, P.lambda)
-                               : __ddiv_rn((double)ob[3], P.lambda);
+                               : P.horizon ? __dmul_rn((double)ob[3], P.dtau) : __ddiv_rn((double)ob[3], P.lambda);
         atomicAdd(reinterpret_cast<double *>(&acc[2]), dt);
         if (GRAD) {
             atomicAdd(reinterpret_cast<double *>(&acc[3]), obd[0]);
@@ -979,7 +1006,8 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         const uint8_t *rt = tables + (size_t)meta[META_RT] * RT_BYTES;
         const uint64_t seed = *reinterpret_cast<const uint64_t *>(rt + RT_SEED);
         pp.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-        pp.k = *reinterpret_cast<const int32_t *>(rt + RT_K);
+        pp.k = P.horizon ? horizon_steps(pp.key, meta[META_D], np0, P.htab, P.hkmax, lane)
+                         : *reinterpret_cast<const int32_t *>(rt + RT_K);
         pp.rr = load_rates<GRAD>(rt, lane);
         pp.pl.valid = (lane < G::NACT) ? G::FULL : (row_t)0;
         const mem_t *trow = reinterpret_cast<const mem_t *>(sl);
@@ -997,7 +1025,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         pp.cn.dmag = 0;
         pp.cn.vM = 1ull << 63;
         pp.cn.vE = 0;
-        pp.first = draw_chunk<EXPO>(pp.key, meta[META_D], np0, 0, nf * pp.k, pp.k, lane);
+        pp.first = draw_chunk<EXPO>(pp.key, meta[META_D], np0, 0, nf * pp.k, max(pp.k, 1), lane);
         return pp;
     };
 
@@ -1009,8 +1037,8 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
         Counters &cn = pp.cn;
         const int k = pp.k;
-        visit_core<LD, EXPO, GRAD>(pp.pl, cn, pp.rr, pp.key, (row_t)hN, (row_t)hS, hW, hE, meta[META_D], np0, nf, k,
-                                   lane, P.err, pp.first);
+        visit_core<LD, EXPO, GRAD>(pp.pl, cn, pp.rr, pp.key, (row_t)hN, (row_t)hS, hW, hE, meta[META_D], np0, nf,
+                                   max(k, 1), lane, P.err, pp.first, nf * k);
         uint64_t *es = reinterpret_cast<uint64_t *>(sl + OFF_EDGE);
         const bool changed = cn.flips != 0; // warp-uniform
         uint64_t wv = 0;
@@ -1039,6 +1067,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
             uint64_t *ctr = reinterpret_cast<uint64_t *>(sl + OFF_CTR);
             ctr[DCTR_HASH] = cn.H;
             ctr[DCTR_FLIPS] += cn.flips;
+            ctr[DCTR_STEPS] += (uint64_t)(nf * k);
             ctr[DCTR_CLKM] = cn.clkM;
             ctr[DCTR_CLKE] = (uint64_t)cn.clkE;
             if (GRAD) {
@@ -1073,7 +1102,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
                     obm[0] = m;
                     obm[1] = (uint64_t)e;
                 } else {
-                    ob[3] += (uint32_t)(nf * k);
+                    ob[3] += P.horizon ? 1u : (uint32_t)(nf * k); // visits (fixed time) or steps
                 }
                 if (GRAD) {
                     obd[0] += cn.sb;
@@ -1104,7 +1133,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
             const int colour = fixed_colour(P.schedule, p);
             // fuse following phases of the same colour unless an observation
             // intervenes (pass observation: every pass ends on its own)
-            while (!P.obs_pass && gp + nf < gp_end) {
+            while (!P.obs_pass && !P.horizon && gp + nf < gp_end) {
                 const uint64_t g2 = gp + nf;
                 const int p2 = (int)(g2 % nph);
                 if (fixed_colour(P.schedule, p2) != colour) break;
@@ -1353,8 +1382,9 @@ __global__ void observe_kernel(const RunParams P, const uint32_t *dom_rep, int n
         domain_bonds_mag<LD>(S, hE, hS, lane, bonds, mag);
         if (lane == 0) {
             const uint64_t *ctr = P.dctr + (uint64_t)g * DCTR_WORDS;
-            const double t = domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE],
-                                         visits * (int64_t)P.rep_k[r], P.lambda);
+            const double t = P.horizon ? __dmul_rn((double)visits, P.dtau)
+                                       : domain_time(EXPO, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE],
+                                                     visits * (int64_t)P.rep_k[r], P.lambda);
             unsigned long long *a = acc + (size_t)r * OBS_WORDS;
             atomicAdd(&a[0], (unsigned long long)(long long)bonds);
             atomicAdd(&a[1], (unsigned long long)(long long)mag);
@@ -1405,16 +1435,21 @@ __global__ void finalize_obs_kernel(const unsigned long long *base /* [n_rep][OB
 }
 
 // per-domain counters -> host-facing arrays (hash, flips, clock)
+// dtau > 0: fixed-time visits, the clock is visits * dtau.
 template <bool EXPO>
 __global__ void domain_state_kernel(const uint64_t *dctr, int n_dom, int64_t visits, const uint32_t *dom_rep,
-                                    const int32_t *rep_k, double lambda, uint64_t *hash, int64_t *flips, double *t)
+                                    const int32_t *rep_k, double lambda, double dtau, uint64_t *hash,
+                                    int64_t *flips, double *t, int64_t *steps)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_dom) return;
     const uint64_t *c = dctr + (uint64_t)g * DCTR_WORDS;
     hash[g] = c[DCTR_HASH];
     flips[g] = (int64_t)c[DCTR_FLIPS];
-    t[g] = domain_time(EXPO, c[DCTR_CLKM], (int64_t)c[DCTR_CLKE], visits * (int64_t)rep_k[dom_rep[g]], lambda);
+    steps[g] = (int64_t)c[DCTR_STEPS];
+    t[g] = dtau > 0.0 ? __dmul_rn((double)visits, dtau)
+                      : domain_time(EXPO, c[DCTR_CLKM], (int64_t)c[DCTR_CLKE], visits * (int64_t)rep_k[dom_rep[g]],
+                                    lambda);
 }
 
 // zero counters: hash basis, flips 0, clock 1.0 (m = 2^63, e = 0), scores 0
@@ -1429,6 +1464,7 @@ __global__ void reset_counters_kernel(uint64_t *dctr, int n_dom)
     c[DCTR_CLKE] = 0;
     c[DCTR_SB] = 0;
     c[DCTR_SH] = 0;
+    c[DCTR_STEPS] = 0;
 }
 
 // per-replica score sums in fixed domain order (kmc_grad)

@@ -6,7 +6,7 @@ from oracle import oracle as orc
 
 
 def run_both(L, Ld, k, seeds, beta, h, n_sched, *, law=0, init=0, schedule=0, time_mode=0,
-             obs_every=0, nu=1.0, J=1.0, launch=None, chunks=None, obs_per_pass=False):
+             obs_every=0, nu=1.0, J=1.0, launch=None, chunks=None, obs_per_pass=False, dtau=0.0):
     import paper_1403_4674_gb300 as kmc
     n = len(L)
     ks = list(k) if isinstance(k, (list, tuple)) else [k] * n
@@ -23,6 +23,8 @@ def run_both(L, Ld, k, seeds, beta, h, n_sched, *, law=0, init=0, schedule=0, ti
     lat.set_rates(beta, h, J=J, nu=nu, law=law)
     if obs_per_pass:
         lat.set_observation(kmc.KMC_OBS_PASS)
+    if dtau > 0:
+        lat.set_horizon(dtau)
     chunks = chunks or [n_sched]
     obs_gpu = []
     for c in chunks:
@@ -40,7 +42,7 @@ def run_both(L, Ld, k, seeds, beta, h, n_sched, *, law=0, init=0, schedule=0, ti
     ref = {"spins": [], "hash": [], "flips": [], "t": [], "obs": []}
     for r in range(len(L)):
         rep = orc.Replica(L=L[r], Ld=Ld, k=ks[r], seed=seeds[r], beta=beta[r], h=h[r], J=J, nu=nu,
-                          law=law, init=inits[r])
+                          law=law, init=inits[r], dtau=dtau)
         obs_r = []
         for c in chunks:
             o = rep.run(c, schedule=schedule, time_mode=time_mode, obs_every=obs_every,

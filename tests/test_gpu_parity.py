@@ -188,3 +188,39 @@ def test_register_shifted_endpoints(launch, schedule, time_mode, obs_every):
     assert_parity(gpu, ref, len(L))
     passes = 8 if schedule == orc.SCHED_PALINDROME else 4
     assert gpu["obs"].shape[0] == (2 * passes) // obs_every + (3 * passes) // obs_every
+
+
+@pytest.mark.parametrize("Ld,dtau", [(8, 0.05), (16, 0.02), (32, 0.004), (64, 0.002), (16, 0.3)])
+@pytest.mark.parametrize("launch", [None, (GRID, 152, 16)])
+def test_fixed_time_visits(Ld, dtau, launch):
+    """KMC_TIME_HORIZON: each visit runs its domain for domain time dtau (a
+    Poisson number of steps by table inversion); bit-exact against the
+    oracle, clock exactly dtau per visit, step counts per replica (Eq. 11)."""
+    L = [4 * Ld, 6 * Ld]
+    gpu, ref = run_both(L, Ld, 1, [61, 62], [0.45, 0.3], [0.02, -0.03], 5, obs_every=1, launch=launch,
+                        time_mode=orc.TIME_HORIZON, dtau=dtau, nu=1.1)
+    assert_parity(gpu, ref, len(L))
+
+
+def test_fixed_time_visits_with_pass_records_and_perm_schedule():
+    gpu, ref = run_both([64, 128], 16, 1, [71, 72], [0.5, 0.4], [0.0, 0.01], 4, obs_every=3,
+                        time_mode=orc.TIME_HORIZON, dtau=0.05, obs_per_pass=True,
+                        schedule=orc.SCHED_RANDOM_PERM, chunks=[1, 3])
+    assert_parity(gpu, ref, 2)
+
+
+def test_fixed_time_steps_and_errors():
+    import paper_1403_4674_gb300 as kmc
+    lat = kmc.Lattice([64], 16, 1, [5])
+    with pytest.raises(kmc.KmcError):
+        lat.run(1, time_mode=kmc.KMC_TIME_HORIZON)  # no visit time set
+    with pytest.raises(kmc.KmcError):
+        lat.set_horizon(10.0)  # n_d nu dtau = 2560 steps per visit: table too long
+    lat.set_horizon(0.05)
+    lat.run(4, time_mode=kmc.KMC_TIME_HORIZON)
+    ob = lat.observables()
+    ref = orc.Replica(L=64, Ld=16, k=1, seed=5, beta=0.4, dtau=0.05)
+    ref.run(4, time_mode=orc.TIME_HORIZON)
+    assert ob["steps"][0] == int(ref.steps.sum())
+    assert ob["t"][0] == pytest.approx(8 * 0.05, rel=1e-13)
+    lat.close()
