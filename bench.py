@@ -17,8 +17,9 @@ device copy of the initial spins, the run, device -> host copy of the final
 spins and observables.
 
 `variants` adds, at N = 1, the batched configuration (512 uneven replicas,
-domain side, k and plan autotuned per group, one CUDA graph per step) and
-the gradient configuration (256 x 256^2 with likelihood-ratio scores).
+domain side, k and plan autotuned per group, one CUDA graph per step), the
+gradient configuration (256 x 256^2 with likelihood-ratio scores) and one
+8192^2 lattice (L_d = 64, k = 8).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                     [--workload ising1024|ising8192] [--no-variants]
@@ -219,12 +220,12 @@ def reference_arm(args):
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (summary in
 # profiles/run_kernel_ising1024x18_launches.md), and the SHA-256 of the kernel
 # source it was taken on; reported as null once the source has changed.
-TRAFFIC_BYTES_PER_LAUNCH = 4709888
-TRAFFIC_KERNEL_SHA256 = "46ac65c128a0270692e58b7463b54dd423e0e7ebb9aee7a0b1cecfad35a2b4bf"
+TRAFFIC_BYTES_PER_LAUNCH = 5386240
+TRAFFIC_KERNEL_SHA256 = "9f481df04bc0a946cea115bc874e96ed3d64567f330101d15eba157fb600e43f"
 # Warp instructions per uniformised step of the same workload and kernel
 # (ncu smsp__inst_executed.sum over one 200-schedule launch / its steps;
 # profiles/run_kernel_ising1024x18_small_full.md).  Includes the halo polls.
-INST_PER_STEP = 8403080341 / 51609600
+INST_PER_STEP = 8355554016 / 51609600
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 
 
@@ -333,6 +334,39 @@ def variant_grad(args, peaks, flush, stream):
            "plan": list(plan), "launch": list(lat.launch()),
            "lr_grad_e_beta_h": [float(ge[0]), float(ge[1])], "lr_grad_m_beta_h": [float(gm[0]), float(gm[1])],
            "events_per_step": ev,
+           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks)}
+    lat.close()
+    return out
+
+
+def variant_lattice8192(args, peaks, flush, stream):
+    """One 8192^2 lattice (67M sites), T=2.269, h=0.01, L_d=64, k=8, 2000
+    palindromic schedules, plan tuned."""
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import autotune, workloads as wl
+    w = wl.lattice_8192(seed=8192)
+    lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds, init=0)
+    lat.set_rates(w.beta, w.h)
+    plan, _ = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=20)
+    lat.profile(True)
+    n = w.schedules
+
+    def step():
+        lat.reset(kmc.KMC_INIT_RANDOM)
+        lat.run(n)
+
+    ms = device_time(step, args.steps, args.warmup, flush, stream)
+    lat.sync()
+    lat.profile_read()
+    step()
+    run_ms, run_n = lat.profile_read()
+    ev = lat.events_per_schedule() * n
+    by = schedule_bytes(lat.L, lat.L_d, lat.ks) * n
+    dev_s = sum(ms) / 1000.0
+    out = {"value": ev * args.steps / dev_s, "unit": UNIT, "ms_per_step": statistics.mean(ms),
+           "workload": "8192x8192 periodic Ising (67M sites), T=2.269, h=0.01, L_d=64, k=8, %d palindromic "
+                       "schedules" % n,
+           "plan": list(plan), "launch": list(lat.launch()), "events_per_step": ev,
            "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks)}
     lat.close()
     return out
@@ -471,7 +505,8 @@ def main():
     variants = None
     if world == 1 and not args.no_variants and args.workload == "ising1024":
         variants = {"batched": variant_batched(args, peaks, flush, stream),
-                    "grad": variant_grad(args, peaks, flush, stream)}
+                    "grad": variant_grad(args, peaks, flush, stream),
+                    "lattice8192": variant_lattice8192(args, peaks, flush, stream)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -138,10 +138,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 key)
     return c;
 }
 
-__device__ __forceinline__ uint64_t ld_cg(const uint64_t *p)
-{
-    return (uint64_t)__ldcg((const unsigned long long *)p);
-}
 __device__ __forceinline__ void st_cg(uint64_t *p, uint64_t v)
 {
     __stcg((unsigned long long *)p, (unsigned long long)v);
@@ -536,8 +532,9 @@ __device__ __forceinline__ RateRegs load_rates(const uint8_t *rt, int lane)
 }
 
 // ---------------------------------------------------------------------------
-// One domain visit (Sec. 2.2): nfused consecutive global phases of the same
-// colour, k uniformised steps each, with the halo hN/hS/hW/hE frozen.
+// One domain visit (Sec. 2.2): `total` uniformised steps with the halo
+// hN/hS/hW/hE frozen -- k steps in each of nfused consecutive global phases
+// of the same colour, or a Poisson number for a fixed-time visit.
 //
 // Step j of global phase np draws Philox {j, d, np_lo, np_hi} with the replica
 // seed: target = (w0 | w1<<32) >> 1 uniform on [0, n_d 2^P), V = (w2 | w3<<32)
@@ -547,13 +544,13 @@ __device__ __forceinline__ RateRegs load_rates(const uint8_t *rt, int lane)
 // row-major order flips (the n-fold way's cumulative selection, Sec. 2.1).
 // Steps are drawn 32 at a time (lane i draws step base+i); runs of null steps
 // are skipped with one ballot since the state does not change between real
-// events.  rt: the replica table in shared memory.
+// events.  rr: the replica's rates, held by lanes 0..9.
 // ---------------------------------------------------------------------------
 template <int LD, bool EXPO, bool GRAD>
 __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const RateRegs &rr, uint2 key,
                                            typename Geo<LD>::row_t hN, typename Geo<LD>::row_t hS,
                                            uint64_t hW, uint64_t hE, uint32_t d, uint64_t np0,
-                                           int nfused, int k, int lane, int *err, const Chunk &first, int total)
+                                           int k, int lane, int *err, const Chunk &first, int total)
 {
     using G = Geo<LD>;
     using row_t = typename G::row_t;
@@ -721,22 +718,6 @@ __device__ __forceinline__ Edges all_edges(const typename Geo<LD>::row_t (&S)[Ge
     e.w[EDGE_W] = colW;
     e.w[EDGE_E] = colE;
     return e;
-}
-
-// Lane i (< 4) returns edge i of the warp's domain.
-template <int LD>
-__device__ __forceinline__ uint64_t edge_words(const typename Geo<LD>::row_t (&S)[Geo<LD>::RPL], int lane)
-{
-    using G = Geo<LD>;
-    uint64_t colW = 0, colE = 0;
-#pragma unroll
-    for (int t = 0; t < G::RPL; ++t) {
-        colW |= (uint64_t)__ballot_sync(FULL_WARP, (S[t] & 1u) != 0) << (32 * t);
-        colE |= (uint64_t)__ballot_sync(FULL_WARP, ((S[t] >> (LD - 1)) & 1u) != 0) << (32 * t);
-    }
-    const uint64_t rowN = (uint64_t)__shfl_sync(FULL_WARP, S[0], 0);
-    const uint64_t rowS = (uint64_t)__shfl_sync(FULL_WARP, S[G::RPL - 1], G::NACT - 1);
-    return (lane == EDGE_N) ? rowN : (lane == EDGE_S) ? rowS : (lane == EDGE_W) ? colW : colE;
 }
 
 // Stamped word w (0..7) of the warp's edges: half (w & 1) of edge (w >> 1).
@@ -1037,7 +1018,7 @@ __global__ void __launch_bounds__(512, 1) run_kernel(const RunParams P)
         const uint32_t *meta = reinterpret_cast<const uint32_t *>(sl + OFF_META);
         Counters &cn = pp.cn;
         const int k = pp.k;
-        visit_core<LD, EXPO, GRAD>(pp.pl, cn, pp.rr, pp.key, (row_t)hN, (row_t)hS, hW, hE, meta[META_D], np0, nf,
+        visit_core<LD, EXPO, GRAD>(pp.pl, cn, pp.rr, pp.key, (row_t)hN, (row_t)hS, hW, hE, meta[META_D], np0,
                                    max(k, 1), lane, P.err, pp.first, nf * k);
         uint64_t *es = reinterpret_cast<uint64_t *>(sl + OFF_EDGE);
         const bool changed = cn.flips != 0; // warp-uniform
