@@ -203,7 +203,10 @@ kmc_status kmc_grad(kmc_ctx *ctx, double *score_dev, int32_t reset);
  */
 kmc_status kmc_lr_estimate(kmc_ctx *ctx, const double *A_dev, double *grad_dev);
 
-/* Turn score accumulation on (enable != 0) or off for following runs. */
+/* Turn score accumulation on (enable != 0) or off for following runs.  The
+ * score-carrying kernels use more registers; if they do not fit the current
+ * launch plan's shape, the plan is rebuilt (requested plan first, else the
+ * default).  Not while the stream is capturing. */
 kmc_status kmc_enable_grad(kmc_ctx *ctx, int32_t enable);
 
 /* Re-initialise spins from the seeds (init as in kmc_create_lattice, or

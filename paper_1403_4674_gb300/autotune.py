@@ -43,10 +43,13 @@ def max_domain_side(L: int, candidates: Sequence[int] = DOMAIN_SIDES) -> int:
 def plan_candidates(sm_count: int) -> List[Plan]:
     """Launch plans worth measuring: the library default, clusters of every
     size (the library packs as many replicas per cluster as fit), and
-    cooperative grids of one or two CTAs per SM."""
+    cooperative grids of one to three CTAs per SM (24 resident warps where the
+    kernel's registers allow; the library rejects shapes that do not fit)."""
     out: List[Plan] = [(KMC_LAUNCH_AUTO, 0, 16)]
     out += [(KMC_LAUNCH_CLUSTER, c, 16) for c in (1, 2, 4, 8, 16)]
-    out += [(KMC_LAUNCH_GRID, sm_count, 16), (KMC_LAUNCH_GRID, 2 * sm_count, 8)]
+    out += [(KMC_LAUNCH_CLUSTER, c, 8) for c in (4, 16)]
+    out += [(KMC_LAUNCH_GRID, sm_count, 16), (KMC_LAUNCH_GRID, 2 * sm_count, 8),
+            (KMC_LAUNCH_GRID, 2 * sm_count, 12), (KMC_LAUNCH_GRID, 3 * sm_count, 8)]
     return out
 
 
@@ -74,9 +77,11 @@ def _timed_events_per_s(lat: Lattice, n_sched: int, stream: torch.cuda.Stream) -
 
 
 def measure(L: Sequence[int], L_d: int, ks: Sequence[int], seeds: Sequence[int], beta: Sequence[float],
-            h: Sequence[float], plans: Sequence[Plan], trial_schedules: int = 50, law: int = 0) -> List[Trial]:
+            h: Sequence[float], plans: Sequence[Plan], trial_schedules: int = 50, law: int = 0,
+            grad: bool = False) -> List[Trial]:
     """Events/s of one group geometry under each plan, on a scratch context
-    (the caller's lattices are not touched)."""
+    (the caller's lattices are not touched); grad measures the score-carrying
+    kernels."""
     stream = torch.cuda.Stream()
     trials: List[Trial] = []
     with torch.cuda.stream(stream):
@@ -88,6 +93,8 @@ def measure(L: Sequence[int], L_d: int, ks: Sequence[int], seeds: Sequence[int],
             if any(k != ks[0] for k in ks):
                 lat.set_replica_params(k=list(ks))
             lat.set_rates(list(beta), list(h), law=law)
+            if grad:
+                lat.enable_grad(True)
             for p in plans:
                 t = Trial(L_d, max(ks), p)
                 try:
@@ -110,7 +117,8 @@ def tune_plan(lat: Lattice, beta: Sequence[float], h: Sequence[float], plans: Op
     the fastest on `lat`."""
     if plans is None:
         plans = plan_candidates(torch.cuda.get_device_properties(lat.spins.device).multi_processor_count)
-    trials = measure(lat.L, lat.L_d, lat.ks, lat.seeds, beta, h, plans, trial_schedules, law)
+    trials = measure(lat.L, lat.L_d, lat.ks, lat.seeds, beta, h, plans, trial_schedules, law,
+                     grad=lat.grad_enabled)
     ok = [t for t in trials if t.error is None]
     if not ok:
         raise KmcError(-1, "no launch plan runs: " + "; ".join(str(t.error) for t in trials))
@@ -156,7 +164,48 @@ def tune_batch(L: Sequence[int], beta: Sequence[float], h: Sequence[float], seed
                            % (len(idx), max(Lg), "; ".join(errs)))
         best = max(ok, key=lambda t: t.events_per_s)
         out.append(GroupChoice(idx, best.L_d, best.k, best.plan, best.events_per_s, trials))
+    # Groups that chose the same (L_d, k) can share one context; groups tuned
+    # alone may compete for SMs when run side by side (cooperative grids wait
+    # for a whole GPU).  Keep whichever partition runs the whole batch faster.
+    keys = {}
+    for ch in out:
+        keys.setdefault((ch.L_d, ch.k), []).append(ch)
+    if any(len(v) > 1 for v in keys.values()):
+        merged: List[GroupChoice] = []
+        for (Ld, k), chs in keys.items():
+            if len(chs) == 1:
+                merged.append(chs[0])
+                continue
+            idx = sorted(i for ch in chs for i in ch.replicas)
+            trials = measure([L[i] for i in idx], Ld, [k] * len(idx), [seeds[i] for i in idx],
+                             [beta[i] for i in idx], [h[i] for i in idx], plans, trial_schedules, law)
+            okm = [t for t in trials if t.error is None]
+            if not okm:
+                merged = []
+                break
+            best = max(okm, key=lambda t: t.events_per_s)
+            merged.append(GroupChoice(idx, Ld, k, best.plan, best.events_per_s, trials))
+        if merged and batch_events_per_s(L, beta, h, seeds, merged, trial_schedules, law) > \
+                batch_events_per_s(L, beta, h, seeds, out, trial_schedules, law):
+            out = merged
     return out
+
+
+def batch_events_per_s(L, beta, h, seeds, choices: List[GroupChoice], n_sched: int, law: int = 0) -> float:
+    """Measured events/s of a whole batch step (all groups concurrently)."""
+    batch = Batch(L, beta, h, seeds, choices, law=law)
+    try:
+        batch.run(2)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.run(n_sched)
+        e1.record()
+        e1.synchronize()
+        return batch.events_per_schedule() * n_sched / (e0.elapsed_time(e1) / 1000.0)
+    finally:
+        batch.close()
 
 
 class Batch:

@@ -480,10 +480,14 @@ kmc_status plan_grid(kmc_ctx *c, int n_cta, int wpb, Plan &pl)
 }
 
 // Can this plan run?  Shared memory, cluster support and (GRID) co-residency.
+// Only the kernels this context can launch are checked: both clock modes,
+// and the score-carrying variant only while scores are on (it holds more
+// registers, so fewer of its CTAs fit an SM; kmc_enable_grad re-checks).
 kmc_status check_plan(kmc_ctx *c, const Plan &pl)
 {
     for (int e = 0; e < 2; ++e) {
         for (int gv = 0; gv < 2; ++gv) {
+            if (gv == 1 && !c->grad) continue;
             RunKernel kern = run_kernel_for(c->LD, e == 0, gv == 1, pl.mode == KMC_LAUNCH_CLUSTER);
             // the attribute belongs to the kernel, not to the context: only
             // ever raise it, so that plans of other contexts stay launchable
@@ -570,9 +574,12 @@ kmc_status default_plan(kmc_ctx *c)
             why = c->err;
         }
     }
-    for (int wpb = MAX_WPB; wpb >= 4; wpb /= 2) {
+    // cooperative grids, most resident warps per SM first (the 80-register
+    // kernels fit three CTAs of 8 warps or two of 12 on an SM)
+    const int grid_shapes[][2] = {{8, 3}, {12, 2}, {16, 1}, {8, 2}, {8, 1}, {4, 1}};
+    for (const auto &gs : grid_shapes) {
         Plan pl;
-        if (plan_grid(c, c->sm_count, wpb, pl) == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
+        if (plan_grid(c, c->sm_count * gs[1], gs[0], pl) == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
         why = c->err;
     }
     {
@@ -1150,7 +1157,22 @@ kmc_status kmc_debug_barrier(kmc_ctx *c, int32_t extra, int64_t limit_ns)
 kmc_status kmc_enable_grad(kmc_ctx *c, int32_t enable)
 {
     if (!c) return KMC_EINVAL;
+    const bool was = c->grad;
     c->grad = enable != 0;
+    if (c->grad && !was) {
+        if (refuse_capture(c, "kmc_enable_grad") != KMC_OK) {
+            c->grad = was;
+            return KMC_EINVAL;
+        }
+        // the score kernels may not fit the current plan's shape: re-plan
+        Plan pl = c->plan;
+        if (check_plan(c, pl) != KMC_OK &&
+            kmc_set_launch(c, c->req_mode, c->req_size, c->req_wpb) != KMC_OK && default_plan(c) != KMC_OK) {
+            const std::string why = c->err;
+            c->grad = was;
+            return fail(c, KMC_EINVAL, "no launch plan fits the score kernels: %s", why.c_str());
+        }
+    }
     return KMC_OK;
 }
 

@@ -188,3 +188,25 @@ def test_cuda_graph_replay_matches_eager(launch):
     lat.run(6)
     assert np.array_equal(lat.domain_state()[0], hash_eager)
     lat.close()
+
+
+def test_enable_grad_replans_when_score_kernels_do_not_fit():
+    """Three 8-warp CTAs per SM fit the plain kernels (80 registers) but not
+    the score-carrying ones; turning scores on re-plans, results stay exact."""
+    import torch
+    kmc = _kmc()
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    lat = kmc.Lattice([256, 128], 16, 4, [1, 2])
+    lat.set_launch(2, 3 * sm, 8)
+    assert lat.launch()[2] == 3 * sm
+    lat.enable_grad(True)
+    mode, size, ctas, wpb, _ = lat.launch()
+    assert ctas * wpb <= 2 * sm * 16
+    lat.set_rates([0.4, 0.5], [0.0, 0.01])
+    lat.run(3)
+    lat.sync()
+    for r, (L, seed, beta, h) in enumerate([(256, 1, 0.4, 0.0), (128, 2, 0.5, 0.01)]):
+        ref = orc.Replica(L=L, Ld=16, k=4, seed=seed, beta=beta, h=h)
+        ref.run(3)
+        assert np.array_equal(lat.replica_spins(r).cpu().numpy(), ref.spins)
+    lat.close()
