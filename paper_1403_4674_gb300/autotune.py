@@ -49,7 +49,8 @@ def plan_candidates(sm_count: int) -> List[Plan]:
     out += [(KMC_LAUNCH_CLUSTER, c, 16) for c in (1, 2, 4, 8, 16)]
     out += [(KMC_LAUNCH_CLUSTER, c, 8) for c in (4, 16)]
     out += [(KMC_LAUNCH_GRID, sm_count, 16), (KMC_LAUNCH_GRID, 2 * sm_count, 8),
-            (KMC_LAUNCH_GRID, 2 * sm_count, 12), (KMC_LAUNCH_GRID, 3 * sm_count, 8)]
+            (KMC_LAUNCH_GRID, 2 * sm_count, 10), (KMC_LAUNCH_GRID, 2 * sm_count, 12),
+            (KMC_LAUNCH_GRID, 3 * sm_count, 8)]
     return out
 
 

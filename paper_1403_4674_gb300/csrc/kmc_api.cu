@@ -575,8 +575,9 @@ kmc_status default_plan(kmc_ctx *c)
         }
     }
     // cooperative grids, most resident warps per SM first (the 80-register
-    // kernels fit three CTAs of 8 warps or two of 12 on an SM)
-    const int grid_shapes[][2] = {{8, 3}, {12, 2}, {16, 1}, {8, 2}, {8, 1}, {4, 1}};
+    // kernels fit three CTAs of 8 warps or two of 12 on an SM, the 96-register
+    // ones two of 10)
+    const int grid_shapes[][2] = {{8, 3}, {12, 2}, {10, 2}, {16, 1}, {8, 2}, {8, 1}, {4, 1}};
     for (const auto &gs : grid_shapes) {
         Plan pl;
         if (plan_grid(c, c->sm_count * gs[1], gs[0], pl) == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;

@@ -801,11 +801,14 @@ __device__ __forceinline__ int fixed_colour(int schedule, int p)
 // ---------------------------------------------------------------------------
 // Persistent run kernel (both modes).
 // ---------------------------------------------------------------------------
-// Registers per thread: 80 lets 24 warps share an SM (three CTAs of 8 warps
-// or two of 12), which hides the latency of the visit's warp-collective
-// chains better than 16 warps at 128 registers; the score-carrying kernels
-// and the 64-column domains keep 128 (at 80 they would spill).
-template <int LD, bool GRAD> constexpr int run_kernel_regs() { return (GRAD || LD == 64) ? 128 : 80; }
+// Registers per thread, the fewest each variant compiles to without spills:
+// 80 lets 24 warps share an SM (three CTAs of 8 warps or two of 12), 96 lets
+// 20 (two of 10), which hides the latency of the visit's warp-collective
+// chains better than 16 warps at 128 registers.
+template <int LD, bool GRAD> constexpr int run_kernel_regs()
+{
+    return (GRAD && LD == 64) ? 128 : (GRAD || LD == 64) ? 96 : 80;
+}
 
 template <int LD, bool EXPO, bool GRAD, bool CLUSTER>
 __global__ void __maxnreg__((run_kernel_regs<LD, GRAD>())) run_kernel(const RunParams P)
