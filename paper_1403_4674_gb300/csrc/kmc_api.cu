@@ -349,6 +349,9 @@ void finish_plan(const kmc_ctx *c, Plan &pl, const std::vector<std::vector<uint3
                 const uint32_t cta = where_cta[gn];
                 const uint32_t rank = cta % (uint32_t)pl.cluster;
                 pl.slot_nb[s * 4 + side] = (rank << 24) | where_slot[gn];
+            } else if (where_cta[gn] == where_cta[g]) {
+                // same CTA: the halo is polled in shared memory (bit 31 flags it)
+                pl.slot_nb[s * 4 + side] = 0x80000000u | where_slot[gn];
             } else {
                 pl.slot_nb[s * 4 + side] = gn;
             }

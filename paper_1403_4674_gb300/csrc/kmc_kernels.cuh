@@ -99,7 +99,8 @@ struct RunParams {
     const uint32_t *rt_rep;       // replica id of each staged table
     const uint32_t *slot_g;       // global domain id of each slot
     const uint32_t *slot_rt;      // local table index of each slot
-    const uint32_t *slot_nb;      // [n_slots][4]: GRID: neighbour g; CLUSTER: rank << 24 | local slot
+    const uint32_t *slot_nb;      // [n_slots][4]: CLUSTER: rank << 24 | local slot; GRID: neighbour g, or
+                                  // 1 << 31 | local slot when the neighbour is in the same CTA
     int max_rt;                   // table capacity per CTA (uniform layout)
     int cluster;                  // 0 = GRID mode, else cluster size
     // state
@@ -163,6 +164,12 @@ __device__ __forceinline__ uint64_t ld_dsmem(uint32_t addr)
 {
     uint64_t v;
     asm volatile("ld.volatile.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_volatile_shared(uint32_t addr)
+{
+    uint64_t v;
+    asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
     return v;
 }
 __device__ __forceinline__ uint64_t ld_volatile_global(const uint64_t *p)
@@ -881,6 +888,9 @@ __global__ void __maxnreg__((run_kernel_regs<LD, GRAD>())) run_kernel(const RunP
                 // address of the neighbour's slot in the cluster's shared memory
                 const uint32_t nrank = nb >> 24, nslot_ = nb & 0xFFFFFFu;
                 meta[META_NB + lane] = map_rank(smem_addr(slots + (size_t)nslot_ * SB), nrank);
+            } else if (nb & 0x80000000u) {
+                // neighbour in this CTA: shared-memory address of its slot, flagged
+                meta[META_NB + lane] = 0x80000000u | smem_addr(slots + (size_t)(nb & 0x7FFFFFFFu) * SB);
             } else {
                 meta[META_NB + lane] = nb;
             }
@@ -917,8 +927,9 @@ __global__ void __maxnreg__((run_kernel_regs<LD, GRAD>())) run_kernel(const RunP
             const uint32_t nb = meta[META_NB + dir];
             const int word = 2 * want + hf;
             auto load = [&]() -> uint64_t {
-                return CLUSTER ? ld_dsmem(nb + OFF_EDGE + 8 * word)
-                               : ld_volatile_global(&P.edges[(size_t)nb * EDGE_WORDS + word]);
+                if (CLUSTER) return ld_dsmem(nb + OFF_EDGE + 8 * word);
+                if (nb & 0x80000000u) return ld_volatile_shared((nb & 0x7FFFFFFFu) + OFF_EDGE + 8 * word);
+                return ld_volatile_global(&P.edges[(size_t)nb * EDGE_WORDS + word]);
             };
             uint64_t v = load();
             if ((uint32_t)(v >> 32) < need) {
@@ -1039,12 +1050,10 @@ __global__ void __maxnreg__((run_kernel_regs<LD, GRAD>())) run_kernel(const RunP
             wv = (es[lane] & 0xFFFFFFFFull) | ((uint64_t)count_after << 32); // same edges, new count
         }
         if (lane < EDGE_WORDS) {
-            if (CLUSTER) {
-                reinterpret_cast<volatile uint64_t *>(es)[lane] = wv;
-            } else {
-                es[lane] = wv;
-                st_cg(&P.edges[(size_t)meta[META_G] * EDGE_WORDS + lane], wv);
-            }
+            // the slot's copy (read by this CTA's and, in CLUSTER mode, the
+            // cluster's other warps) and, in GRID mode, the global copy
+            reinterpret_cast<volatile uint64_t *>(es)[lane] = wv;
+            if (!CLUSTER) st_cg(&P.edges[(size_t)meta[META_G] * EDGE_WORDS + lane], wv);
         }
         if (changed) {
             mem_t *wrow = reinterpret_cast<mem_t *>(sl);
