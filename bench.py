@@ -220,12 +220,12 @@ def reference_arm(args):
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (summary in
 # profiles/run_kernel_ising1024x18_launches.md), and the SHA-256 of the kernel
 # source it was taken on; reported as null once the source has changed.
-TRAFFIC_BYTES_PER_LAUNCH = 5386240
-TRAFFIC_KERNEL_SHA256 = "9f481df04bc0a946cea115bc874e96ed3d64567f330101d15eba157fb600e43f"
+TRAFFIC_BYTES_PER_LAUNCH = 5900544
+TRAFFIC_KERNEL_SHA256 = "b39ba3d388a38893f15cdb6fd56ac906dd582dd56ceedfb94a7ab6b4e6d710c6"
 # Warp instructions per uniformised step of the same workload and kernel
 # (ncu smsp__inst_executed.sum over one 200-schedule launch / its steps;
 # profiles/run_kernel_ising1024x18_small_full.md).  Includes the halo polls.
-INST_PER_STEP = 8355554016 / 51609600
+INST_PER_STEP = 8933046445 / 51609600
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 
 
