@@ -237,21 +237,30 @@ kmc_status kmc_sync(kmc_ctx *ctx);
 
 /* Per-domain state for parity checks, host arrays of total-domain length,
  * domains of replica r at offset sum_{q<r} (L[q]/L_d)^2, domain d = by*Dx + bx:
- * event hash (FNV-1a over real events, see DESIGN), real-flip count and
- * domain clock.  Any pointer may be NULL.  Synchronising. */
+ * event hash, real-flip count and domain clock.  The hash starts at the
+ * FNV-1a 64 offset basis and folds every real event of the domain as
+ * H <- (H xor e) * 0x100000001b3 with e = np << 32 | j << 16 | site (np = 8n + p
+ * the global colour phase, j the step within the visit, site = y L_d + x).
+ * Any pointer may be NULL.  Synchronising. */
 kmc_status kmc_domain_state(kmc_ctx *ctx, uint64_t *hash, int64_t *flips, double *t);
 
 /* Fixed-point and FP64 acceptance table of replica r (host arrays of 10). */
 kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, uint64_t *A);
 
 /* Launch plan of the persistent run kernel.
- *   KMC_LAUNCH_AUTO: the library's choice (CLUSTER when every replica fits
- *     one cluster of at most 16 CTAs, else GRID); size and warps ignored.
+ *   KMC_LAUNCH_AUTO: the library's choice: CLUSTER when every replica fits
+ *     one cluster of at most 16 CTAs at one visit per warp and phase, else a
+ *     cooperative GRID (the shape with the most resident warps per SM that
+ *     fits: three CTAs of 8 warps, two of 12 or 10, one of 16, ...), else
+ *     16-CTA clusters with several visits per warp; size and warps ignored.
  *   KMC_LAUNCH_CLUSTER: every replica resident in one thread-block cluster of
  *     `size` CTAs (1, 2, 4, 8 or 16); halos and visit counters read through
  *     distributed shared memory; no device-wide synchronisation.
- *   KMC_LAUNCH_GRID: one cooperative grid of `size` CTAs; halos and visit
- *     counters through L2.
+ *   KMC_LAUNCH_GRID: one cooperative grid of `size` CTAs, all resident at
+ *     once; halos and visit counters through L2, or shared memory when the
+ *     neighbour domain is in the same CTA.  The run kernels hold 80 to 128
+ *     registers per thread (by domain side and scores), so two or three CTAs
+ *     of 8-12 warps can share an SM.
  * In both plans a visit starts as soon as its four neighbours have finished
  * their visits of earlier colour phases (per-domain dataflow instead of a
  * barrier per phase); observation records are built from per-visit changes,

@@ -363,8 +363,9 @@ void finish_plan(const kmc_ctx *c, Plan &pl, const std::vector<std::vector<uint3
 // CLUSTER plan: every replica inside one cluster of `C` CTAs; a replica with
 // n domains spreads over m = ceil(n/4 / (wpb*load)) CTAs (one visit per warp
 // and phase when load = 1); replicas that need one CTA share CTAs.  Replicas
-// are packed in order of decreasing k, so that a cluster's observation
-// barriers join replicas of equal cost per visit.
+// are packed in order of decreasing k, so that the CTAs of a cluster (which
+// all wait for its slowest at the end of the launch) carry replicas of about
+// equal cost per visit.
 kmc_status plan_cluster(kmc_ctx *c, int C, int wpb, int load, Plan &pl)
 {
     pl = Plan();
