@@ -1,0 +1,124 @@
+"""Parity in the launch configurations the benchmark times: the workloads'
+own contexts, plans and parameters, a few schedules, against the oracle (all
+replicas where the oracle is quick, a seeded sample otherwise)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _sm():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def _check(spins_of, obs, idx, n, L, Ld, ks, seeds, beta, h, inits, scores=None):
+    """spins_of(r) -> device spins of replica r; obs[rec, r, :]; idx: replicas to check."""
+    for r in idx:
+        ref = orc.Replica(L=L[r], Ld=Ld, k=ks[r], seed=seeds[r], beta=beta[r], h=h[r], init=inits[r])
+        if scores is not None:
+            ref.enable_score()
+        robs = ref.run(n, obs_every=1)
+        assert np.array_equal(spins_of(r), ref.spins), "replica %d: spins differ" % r
+        assert np.array_equal(obs[:, r, :3], robs[:, :3]), "replica %d: e, m, e*m differ" % r
+        np.testing.assert_allclose(obs[:, r, 3], robs[:, 3], rtol=1e-12, atol=0)
+        if scores is not None:
+            np.testing.assert_allclose(scores[r], ref.score.sum(axis=0), rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("plan", ["grid_2x10", "grid_3x8", "grid_1x16", "cluster_16"])
+def test_ising1024_all_replicas(plan):
+    """The 18 replicas of 1024^2 (T x start x k) in one context and launch,
+    per-replica k and start, profiling on, as the benchmark runs them."""
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
+    w = wl.ising1024_all()
+    n = len(w.L)
+    ks = [w.k_of(r) for r in range(n)]
+    inits = [w.init_of(r) for r in range(n)]
+    lat = kmc.Lattice(w.L, w.L_d, ks[0], w.seeds, init=inits[0])
+    lat.set_replica_params(k=ks, init=inits)
+    lat.reset(kmc.KMC_INIT_PER_REPLICA)
+    lat.set_rates(w.beta, w.h)
+    sm = _sm()
+    lat.set_launch(*{"grid_2x10": (2, 2 * sm, 10), "grid_3x8": (2, 3 * sm, 8), "grid_1x16": (2, sm, 16),
+                     "cluster_16": (1, 16, 16)}[plan])
+    lat.profile(True)
+    obs = lat.run(3, obs_every=1).cpu().numpy()
+    lat.sync()
+    _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, range(n), 3, w.L, w.L_d, ks, w.seeds, w.beta,
+           w.h, inits)
+    lat.close()
+
+
+def test_batched_512_autotuned_graph_sample():
+    """The 512 uneven replicas grouped and planned by the autotuner with the
+    benchmark's candidates, one CUDA graph per step (reset, then schedules on
+    every group concurrently); six replicas of every group checked, the
+    largest and smallest among them."""
+    import torch
+    from paper_1403_4674_gb300 import autotune, workloads as wl
+    w = wl.batched_replicas(512, master=512)
+    sm = _sm()
+    plans = [(0, 0, 16), (1, 4, 16), (1, 16, 16), (1, 16, 8), (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
+    choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
+                                  Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=4)
+    assert sorted(i for ch in choices for i in ch.replicas) == list(range(len(w.L)))
+    batch = autotune.Batch(w.L, w.beta, w.h, w.seeds, choices)
+    graph = batch.capture(2, 1, reset=0)
+    graph.replay()
+    graph.replay()  # a replay repeats the trajectories from the reset
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    for ch, lat, o in zip(choices, batch.lattices, batch.outs):
+        Lg = [w.L[i] for i in ch.replicas]
+        sub = {int(np.argmax(Lg)), int(np.argmin(Lg))}
+        sub |= set(rng.choice(len(Lg), min(4, len(Lg)), replace=False).tolist())
+        _check(lambda j: lat.replica_spins(j).cpu().numpy(), o.cpu().numpy(), sorted(sub), 2, Lg, ch.L_d,
+               [ch.k] * len(Lg), [w.seeds[i] for i in ch.replicas], [w.beta[i] for i in ch.replicas],
+               [w.h[i] for i in ch.replicas], [0] * len(Lg))
+    batch.close()
+
+
+def test_grad_256_replicas_sample():
+    """256 x 256^2 with scores, one 16-warp CTA per SM on the grid plan;
+    two schedules, eight replicas' spins, records and scores checked."""
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
+    w = wl.grad_replicas(256, seed_master=256, k=8)
+    n = len(w.L)
+    lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
+    lat.set_rates(w.beta, w.h)
+    lat.enable_grad(True)
+    lat.set_launch(2, _sm(), 16)
+    obs = lat.run(2, obs_every=1).cpu().numpy()
+    scores = lat.score().cpu().numpy()
+    _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [0, 37, 101, 128, 177, 200, 254, 255], 2,
+           w.L, w.L_d, [w.k] * n, w.seeds, w.beta, w.h, [0] * n, scores=scores)
+    lat.close()
+
+
+def test_lattice8192_one_schedule():
+    """8192^2 at L_d = 64, k = 8 on the 16-warp grid: one schedule, checked
+    on every site against the oracle (one replica; the C oracle runs it in
+    seconds)."""
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
+    w = wl.lattice_8192()
+    lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
+    lat.set_rates(w.beta, w.h)
+    lat.set_launch(2, _sm(), 16)
+    obs = lat.run(1, obs_every=1).cpu().numpy()
+    lat.sync()
+    _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [0], 1, w.L, w.L_d, [w.k], w.seeds, w.beta, w.h,
+           [0])
+    lat.close()
