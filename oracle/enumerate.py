@@ -205,3 +205,105 @@ class Enumerator:
             e[j] = 1.0
             M[:, j] = op(e)
         return M
+
+
+class RingEnumerator:
+    """Exact operators of the N_S-spin ring of Sec. 3.1 (all 2^N_S states;
+    state index = configuration word, bit n set iff spin n is up).
+
+    ``step(d)``: one uniformised step of domain d (App. A, Eq. Glauber_TM
+    with selection probability 1/L_d = N_D/N_S): spin i of d flips with
+    probability a_c(i)/L_d.  The halo spins of d (outside it) do not change
+    during its process, so the classes read from the current state are the
+    classes under the frozen halo.  ``domain(d)`` = step(d)^k (Eqs. 4-5);
+    ``phase`` runs a colour (d & 1) or a single domain; ``schedule`` a list
+    of phases (Eq. 8); ``random_perm_schedule`` the average over all N_D!
+    domain orders (the paper's uniformly random schedule, Sec. 2.2).
+    """
+
+    def __init__(self, NS: int, Ld: int, k: int, beta: float, J: float = 1.0, h: float = 0.0,
+                 law: int = orc.RATE_BARKER, quantised: bool = True):
+        if NS > 14:
+            raise ValueError("state space too large to enumerate")
+        self.NS, self.Ld, self.k = NS, Ld, k
+        self.ND = NS // Ld
+        self.beta, self.J, self.h = beta, J, h
+        self.S = 1 << NS
+        self.idx = np.arange(self.S, dtype=np.int64)
+        self.bits = ((self.idx[:, None] >> np.arange(NS)) & 1).astype(np.int64)
+        sig = 2 * self.bits - 1
+        self.bonds = sum(sig[:, n] * sig[:, (n + 1) % NS] for n in range(NS))
+        self.mag = sig.sum(axis=1)
+        self.H = -J * self.bonds - h * self.mag
+        w = np.exp(-beta * (self.H - self.H.min()))
+        self.pi = w / w.sum()
+        log2nd = int(round(np.log2(Ld)))
+        a, A = orc.ring_rate_table(J, beta, h, law, log2nd)
+        self.acc = (np.array([float(x) for x in A]) / float(2 ** (63 - log2nd))) if quantised else a
+        self.cls = np.zeros((self.S, NS), dtype=np.int64)
+        for n in range(NS):
+            self.cls[:, n] = 3 * self.bits[:, n] + self.bits[:, (n - 1) % NS] + self.bits[:, (n + 1) % NS]
+
+    def domain_sites(self, d: int):
+        return list(range(d * self.Ld, (d + 1) * self.Ld))
+
+    def _apply_rates(self, p: np.ndarray, sites, rates) -> np.ndarray:
+        out = p * (1.0 - sum(rates))
+        for i, r in zip(sites, rates):
+            out = out + (r * p)[self.idx ^ (1 << i)]
+        return out
+
+    def step(self, d: int, p: np.ndarray) -> np.ndarray:
+        sites = self.domain_sites(d)
+        return self._apply_rates(p, sites, [self.acc[self.cls[:, i]] / self.Ld for i in sites])
+
+    def domain(self, d: int, p: np.ndarray) -> np.ndarray:
+        for _ in range(self.k):
+            p = self.step(d, p)
+        return p
+
+    def phase(self, unit: int, p: np.ndarray, is_domain: bool) -> np.ndarray:
+        for d in range(self.ND):
+            if (d == unit) if is_domain else ((d & 1) == unit):
+                p = self.domain(d, p)
+        return p
+
+    def schedule(self, phases, p: np.ndarray, is_domain: bool = False) -> np.ndarray:
+        for u in phases:
+            p = self.phase(u, p, is_domain)
+        return p
+
+    def random_perm_schedule(self, p: np.ndarray) -> np.ndarray:
+        import itertools
+        perms = list(itertools.permutations(range(self.ND)))
+        return sum(self.schedule(list(q), p, True) for q in perms) / len(perms)
+
+    def reference_step(self, p: np.ndarray, law: int = orc.RATE_BARKER) -> np.ndarray:
+        """Textbook random-site kernel on the whole ring from energy differences."""
+        sites = list(range(self.NS))
+        rates = []
+        for i in sites:
+            dE = self.H[self.idx ^ (1 << i)] - self.H
+            acc = np.minimum(1.0, np.exp(-self.beta * dE)) if law == orc.RATE_METROPOLIS \
+                else 1.0 / (1.0 + np.exp(self.beta * dE))
+            rates.append(acc / self.NS)
+        return self._apply_rates(p, sites, rates)
+
+    def spin_means(self, p: np.ndarray) -> np.ndarray:
+        """<sigma_n> under p, n = 0..N_S-1."""
+        return (2 * self.bits - 1).T @ p
+
+    def stationarity_error(self, op) -> float:
+        return float(np.max(np.abs(op(self.pi) - self.pi)) / np.max(self.pi))
+
+    def detailed_balance_error(self, op, n_probe: int = 4, seed: int = 0) -> float:
+        rng = np.random.default_rng(seed)
+        worst = 0.0
+        for _ in range(n_probe):
+            x = rng.standard_normal(self.S)
+            y = rng.standard_normal(self.S)
+            a = float(x @ op(self.pi * y))
+            b = float(y @ op(self.pi * x))
+            scale = float(np.abs(x) @ op(self.pi * np.abs(y)))
+            worst = max(worst, abs(a - b) / scale)
+        return worst

@@ -32,7 +32,11 @@
  *   - optionally, a domain process that runs for a fixed time dtau instead
  *     of a fixed number of steps: the continuous-time chain of the domain
  *     over dtau, exp(dtau Q_d) = sum_K Poisson(K; n_d nu dtau) P_d^K, i.e. a
- *     Poisson number of uniformised steps, reversible because P_d is.
+ *     Poisson number of uniformised steps, reversible because P_d is;
+ *   - the 1D ring of Sec. 3.1 (N_S <= 64 spins, toroidal, contiguous
+ *     domains of Eq. 1D partitions) with the same step protocol, colour
+ *     schedules (colours d & 1) and the paper's uniformly random order of
+ *     all domains per sweep (Sec. 2.2, Fig. 1).
  *
  * Everything that steers the trajectory is integer: the rate table is held
  * in fixed point, A_c = round(a_c * 2^P) with P = 63 - log2(n_d), so that a
@@ -44,7 +48,10 @@
  * the same chain, the beta = 0 closed form and the Erlang clock law; the
  * long-run energy against Kaufman's exact finite lattice; the score table
  * against finite differences of the rate table, and the likelihood-ratio
- * estimator against the exact derivative of the enumerated distribution.
+ * estimator against the exact derivative of the enumerated distribution;
+ * the ring against its transfer-matrix equilibrium, the textbook
+ * random-site kernel, its enumerated final-state distribution and
+ * time-dependent spin averages, and the beta = 0 closed form.
  * Parity unpinned: the per-domain event hash (a fingerprint this build
  * defines for CPU/GPU event-sequence parity, not a quantity of the paper)
  * and the Philox counter layout (likewise a definition of this build).
@@ -651,4 +658,263 @@ int orc_sample_final_states(const int8_t *s0, int L, int Ld, int k,
 {
     return orc_sample_final_states_grad(s0, L, Ld, k, A, seed0, n_runs,
                                         schedule, n_sched, out, NULL, NULL);
+}
+
+/* ========================================================================
+ * The 1D ring of Sec. 3.1: N_S spins with toroidal periodicity, energy
+ * beta*H = -beta*J*sum_n s_n s_{n+1} (App. A, Eq. for beta*H, 1D line; here
+ * with a field term -h*sum(s) as in 2D).  The ring is cut into N_D
+ * contiguous domains of L_d = N_S/N_D spins (Sec. 3.1, Eq. 1D partitions:
+ * domain d holds spins d*L_d .. d*L_d + L_d - 1).  A configuration is a
+ * 64-bit word, bit n set iff spin n is up (N_S <= 64).
+ *
+ * Class c = 3*sp + q: sp = 1 for an up spin, q = number of up neighbours
+ * (0..2); neighbour sum 2q - 2; dE_c = 2*sigma*(J*(2q-2) + h).  Rates and
+ * fixed point as in 2D: A_c = round(a_c 2^P), P = 63 - log2(L_d).
+ * ====================================================================== */
+int orc_ring_rate_table(double J, double beta, double h, int law, int log2_nd,
+                        double a_out[6], uint64_t A_out[6])
+{
+    if (log2_nd < 0 || log2_nd > 6) return -1;
+    if (law != ORC_RATE_METROPOLIS && law != ORC_RATE_BARKER) return -1;
+    if (!(beta >= 0.0) || !isfinite(beta) || !isfinite(J) || !isfinite(h))
+        return -1;
+    int P = 63 - log2_nd;
+    for (int sp = 0; sp < 2; ++sp) {
+        for (int q = 0; q <= 2; ++q) {
+            int c = 3 * sp + q;
+            double sigma = sp ? 1.0 : -1.0;
+            double dE = 2.0 * sigma * (J * (double)(2 * q - 2) + h);
+            double a;
+            if (law == ORC_RATE_METROPOLIS)
+                a = (dE <= 0.0) ? 1.0 : exp(-beta * dE);
+            else
+                a = 1.0 / (1.0 + exp(beta * dE));
+            a_out[c] = a;
+            A_out[c] = (uint64_t)nearbyint(ldexp(a, P));
+        }
+    }
+    return 0;
+}
+
+static int orc_ring_spin(uint64_t S, int n) { return ((S >> n) & 1u) ? 1 : -1; }
+
+/* bonds = sum_n s_n s_{n+1 mod N_S}, mag = sum_n s_n. */
+void orc_ring_energy_mag(uint64_t S, int NS, int64_t *bonds, int64_t *mag)
+{
+    int64_t b = 0, m = 0;
+    for (int n = 0; n < NS; ++n) {
+        b += orc_ring_spin(S, n) * orc_ring_spin(S, (n + 1) % NS);
+        m += orc_ring_spin(S, n);
+    }
+    *bonds = b;
+    *mag = m;
+}
+
+/* ------------------------------------------------------------------------
+ * Schedules of the ring.  Colour of domain d: d & 1 (N_D even; with N_D = 1
+ * the single domain has colour 0).  One schedule is a list of phases; a
+ * phase runs a set of domains that share no halo:
+ *   PALINDROME: colours 0 1 1 0 (N_D = 1: 0 0), its own reverse;
+ *   FIXED:      colours 0 1 (N_D = 1: 0), a negative test as in 2D;
+ *   RANDOM_PERM: the paper's own protocol (Sec. 2.2, Fig. 1: a new random
+ *               schedule after every sweep): a uniform random order of the
+ *               N_D domains, one domain per phase, from a Fisher-Yates
+ *               shuffle; draw i (i = N_D-1 down to 1) uses Philox
+ *               {i, 0, n_lo, n_hi | TAG_PERM<<24} and swaps position i with
+ *               floor(x (i+1) / 2^64), x = w0 | w1<<32.
+ * out[p] is a colour (is_domain = 0) or a domain (is_domain = 1).  Returns
+ * the number of phases, or -1.
+ * ---------------------------------------------------------------------- */
+int orc_ring_schedule(int schedule, uint64_t n, uint64_t seed, int ND, int out[64], int *is_domain)
+{
+    if (ND < 1 || ND > 64) return -1;
+    *is_domain = 0;
+    if (schedule == ORC_SCHED_PALINDROME || schedule == ORC_SCHED_FIXED) {
+        if (ND != 1 && (ND & 1)) return -1;
+        int ncol = (ND == 1) ? 1 : 2;
+        int np = 0;
+        for (int c = 0; c < ncol; ++c) out[np++] = c;
+        if (schedule == ORC_SCHED_PALINDROME)
+            for (int c = ncol - 1; c >= 0; --c) out[np++] = c;
+        return np;
+    }
+    if (schedule == ORC_SCHED_RANDOM_PERM) {
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        for (int i = 0; i < ND; ++i) out[i] = i;
+        for (int i = ND - 1; i >= 1; --i) {
+            uint32_t ctr[4] = {(uint32_t)i, 0u, (uint32_t)n,
+                               (uint32_t)((n >> 32) & 0xFFFFFFu) | (ORC_TAG_PERM << 24)};
+            uint32_t w[4];
+            orc_philox4x32_10(ctr, key, w);
+            uint64_t x = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+            int j = (int)(((unsigned __int128)x * (unsigned)(i + 1)) >> 64);
+            int t = out[i]; out[i] = out[j]; out[j] = t;
+        }
+        *is_domain = 1;
+        return ND;
+    }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------
+ * One domain process of the ring: domain d, k uniformised steps with the
+ * two halo spins (left of the first, right of the last site) frozen.  With
+ * N_D = 1 the domain is the whole ring and both neighbours of every spin
+ * are its own.  Step j of phase np uses Philox {j, d, np_lo, np_hi |
+ * TAG_STEP<<24} exactly as in 2D: target, null step if target >= R',
+ * class by cumulative rate, member jj = (target - C_{c-1}) / A_c in
+ * ascending site order.  Event word e = np<<32 | j<<16 | (site - d*L_d);
+ * the trajectory's hash folds all its events in order.
+ * ---------------------------------------------------------------------- */
+static void orc_ring_visit(uint64_t *S, int NS, int Ld, int d, int k, const uint64_t A[6],
+                           uint32_t key0, uint32_t key1, uint64_t np, int time_mode,
+                           double *esum, int64_t *steps, uint64_t *hash, int64_t *flips)
+{
+    const int ND = NS / Ld, first = d * Ld;
+    int cls[64];
+    int haloL = 0, haloR = 0;
+    if (ND > 1) {
+        haloL = orc_ring_spin(*S, (first - 1 + NS) % NS);
+        haloR = orc_ring_spin(*S, (first + Ld) % NS);
+    }
+    for (int j = 0; j < k; ++j) {
+        uint64_t n[6] = {0};
+        for (int x = 0; x < Ld; ++x) {
+            int site = first + x;
+            int lf, rt;
+            if (ND == 1) {
+                lf = orc_ring_spin(*S, (site - 1 + NS) % NS);
+                rt = orc_ring_spin(*S, (site + 1) % NS);
+            } else {
+                lf = (x > 0) ? orc_ring_spin(*S, site - 1) : haloL;
+                rt = (x < Ld - 1) ? orc_ring_spin(*S, site + 1) : haloR;
+            }
+            int c = 3 * (orc_ring_spin(*S, site) > 0) + (lf > 0) + (rt > 0);
+            cls[x] = c;
+            n[c] += 1;
+        }
+        uint64_t R = 0;
+        for (int c = 0; c < 6; ++c) R += n[c] * A[c];
+
+        uint32_t ctr[4] = {(uint32_t)j, (uint32_t)d, (uint32_t)np,
+                           (uint32_t)((np >> 32) & 0xFFFFFFu) | (ORC_TAG_STEP << 24)};
+        uint32_t key[2] = {key0, key1};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        uint64_t target = ((uint64_t)w[0] | ((uint64_t)w[1] << 32)) >> 1;
+        uint64_t V = (((uint64_t)w[2] | ((uint64_t)w[3] << 32)) >> 11) + 1u;
+        if (time_mode == ORC_TIME_EXPONENTIAL)
+            esum[d] += -log(ldexp((double)V, -53));
+        steps[d] += 1;
+        if (target >= R) continue;
+
+        uint64_t C = 0;
+        int c;
+        for (c = 0; c < 6; ++c) {
+            uint64_t wc = n[c] * A[c];
+            if (target < C + wc) break;
+            C += wc;
+        }
+        uint64_t jj = (target - C) / A[c];
+        int x = -1;
+        uint64_t seen = 0;
+        for (int i = 0; i < Ld; ++i) {
+            if (cls[i] == c) {
+                if (seen == jj) { x = i; break; }
+                ++seen;
+            }
+        }
+        *S ^= 1ull << (first + x);
+        *flips += 1;
+        uint64_t e = (np << 32) | ((uint64_t)j << 16) | (uint64_t)x;
+        *hash = (*hash ^ e) * ORC_HASH_PRIME;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Run n_sched schedules of one ring trajectory from global schedule index
+ * sched_begin.  Phase p of schedule n has the Philox phase index
+ * np = n*64 + p.  A "pass" is one phase (a colour, or one domain for
+ * RANDOM_PERM); its end is a domain-process endpoint (Sec. 2.3), and after
+ * every obs_every-th pass of the call the record {e, m, e*m, T} goes to
+ * obs[4*i] and the configuration word to obs_state[i] (either may be NULL).
+ * e = (-J bonds - h mag)/N_S, m = mag/N_S, T = mean over domains of t_d,
+ * t_d = esum_d/(L_d nu) (exponential) or steps_d/(L_d nu) (expected).
+ * esum and steps are per domain [N_D]; hash and flips per trajectory.
+ * ---------------------------------------------------------------------- */
+int orc_ring_run(uint64_t *S, int NS, int Ld, int k, const uint64_t A[6], uint64_t seed,
+                 int schedule, int time_mode, double nu, double J, double h,
+                 int64_t sched_begin, int64_t n_sched, int obs_every,
+                 double *esum, int64_t *steps, uint64_t *hash, int64_t *flips,
+                 double *obs, uint64_t *obs_state)
+{
+    if (NS < 2 || NS > 64 || Ld < 1 || NS % Ld != 0 || orc_log2(Ld) < 0) return -1;
+    if (k < 0 || k > 65535) return -1;
+    if (time_mode != ORC_TIME_EXPONENTIAL && time_mode != ORC_TIME_EXPECTED) return -1;
+    const int ND = NS / Ld;
+    uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+    int64_t passes = 0;
+    for (int64_t nl = 0; nl < n_sched; ++nl) {
+        uint64_t n = (uint64_t)(sched_begin + nl);
+        int ph[64], is_domain;
+        int nph = orc_ring_schedule(schedule, n, seed, ND, ph, &is_domain);
+        if (nph < 0) return -1;
+        for (int p = 0; p < nph; ++p) {
+            uint64_t np = n * 64u + (uint64_t)p;
+            for (int d = 0; d < ND; ++d) {
+                if (is_domain ? (d != ph[p]) : ((d & 1) != ph[p])) continue;
+                orc_ring_visit(S, NS, Ld, d, k, A, key0, key1, np, time_mode, esum, steps, hash, flips);
+            }
+            ++passes;
+            if (obs_every > 0 && passes % obs_every == 0) {
+                int64_t i = passes / obs_every - 1;
+                if (obs) {
+                    int64_t b, m;
+                    orc_ring_energy_mag(*S, NS, &b, &m);
+                    double e = (-J * (double)b - h * (double)m) / (double)NS;
+                    double tsum = 0.0;
+                    for (int d = 0; d < ND; ++d)
+                        tsum += orc_domain_time(time_mode, esum[d], steps[d], Ld, nu);
+                    obs[4 * i] = e;
+                    obs[4 * i + 1] = (double)m / (double)NS;
+                    obs[4 * i + 2] = e * ((double)m / (double)NS);
+                    obs[4 * i + 3] = tsum / (double)ND;
+                }
+                if (obs_state) obs_state[i] = *S;
+            }
+        }
+    }
+    return 0;
+}
+
+/* Many independent ring trajectories, one after another: trajectory r
+ * starts from S[r] with seed seeds[r] and runs n_sched schedules from
+ * schedule 0; S[r] receives its final configuration; obs / obs_state (or
+ * NULL) receive its records at [r * n_rec ...]; hash[r], flips[r] its
+ * event hash and real-event count.  A plain loop over orc_ring_run. */
+int orc_ring_run_many(int64_t n_traj, uint64_t *S, const uint64_t *seeds, int NS, int Ld, int k,
+                      const uint64_t A[6], int schedule, int time_mode, double nu, double J, double h,
+                      int64_t n_sched, int obs_every, int64_t n_rec, double *obs, uint64_t *obs_state,
+                      uint64_t *hash, int64_t *flips)
+{
+    if (NS < 2 || NS > 64 || Ld < 1 || NS % Ld != 0) return -1;
+    const int ND = NS / Ld;
+    double *esum = (double *)calloc((size_t)ND, sizeof(double));
+    int64_t *steps = (int64_t *)calloc((size_t)ND, sizeof(int64_t));
+    int rc = 0;
+    for (int64_t r = 0; r < n_traj && rc == 0; ++r) {
+        memset(esum, 0, sizeof(double) * (size_t)ND);
+        memset(steps, 0, sizeof(int64_t) * (size_t)ND);
+        uint64_t hh = ORC_HASH_BASIS;
+        int64_t ff = 0;
+        rc = orc_ring_run(&S[r], NS, Ld, k, A, seeds[r], schedule, time_mode, nu, J, h, 0, n_sched,
+                          obs_every, esum, steps, &hh, &ff, obs ? &obs[4 * r * n_rec] : NULL,
+                          obs_state ? &obs_state[r * n_rec] : NULL);
+        if (hash) hash[r] = hh;
+        if (flips) flips[r] = ff;
+    }
+    free(esum);
+    free(steps);
+    return rc;
 }

@@ -102,6 +102,24 @@ def lib():
         L.orc_sample_final_states_grad.restype = ctypes.c_int
         L.orc_hash_basis.argtypes = []
         L.orc_hash_basis.restype = ctypes.c_uint64
+        L.orc_ring_rate_table.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_int, dp, u64p]
+        L.orc_ring_rate_table.restype = ctypes.c_int
+        L.orc_ring_energy_mag.argtypes = [ctypes.c_uint64, ctypes.c_int, i64p, i64p]
+        L.orc_ring_energy_mag.restype = None
+        L.orc_ring_schedule.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.orc_ring_schedule.restype = ctypes.c_int
+        L.orc_ring_run.argtypes = [u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_uint64,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                   dp, i64p, u64p, i64p, dp, u64p]
+        L.orc_ring_run.restype = ctypes.c_int
+        L.orc_ring_run_many.argtypes = [ctypes.c_int64, u64p, u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        u64p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, dp, u64p,
+                                        u64p, i64p]
+        L.orc_ring_run_many.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -298,3 +316,129 @@ class Replica:
             tsum += float(t)
         T = tsum / self.n_domains
         return e, mm, e * mm, T
+
+
+# ---------------------------------------------------------------------------
+# The 1D ring of Sec. 3.1 (configuration = 64-bit word, bit n = spin n up)
+# ---------------------------------------------------------------------------
+def ring_rate_table(J: float, beta: float, h: float, law: int, log2_nd: int):
+    """(a[6], A[6]) for the ring's classes c = 3*up + (number of up neighbours)."""
+    a = np.zeros(6, dtype=np.float64)
+    A = np.zeros(6, dtype=np.uint64)
+    rc = lib().orc_ring_rate_table(J, beta, h, law, log2_nd, _ptr(a, ctypes.c_double), _ptr(A, ctypes.c_uint64))
+    if rc != 0:
+        raise ValueError("invalid ring rate-table arguments")
+    return a, A
+
+
+def ring_energy_mag(S: int, NS: int):
+    b = ctypes.c_int64()
+    m = ctypes.c_int64()
+    lib().orc_ring_energy_mag(int(S), NS, ctypes.byref(b), ctypes.byref(m))
+    return b.value, m.value
+
+
+def ring_schedule(schedule: int, n: int, seed: int, ND: int):
+    """(phases, is_domain): colours per phase, or domains for RANDOM_PERM."""
+    out = (ctypes.c_int * 64)()
+    isd = ctypes.c_int()
+    nph = lib().orc_ring_schedule(schedule, n, seed, ND, out, ctypes.byref(isd))
+    if nph < 0:
+        raise ValueError("bad ring schedule")
+    return [out[i] for i in range(nph)], bool(isd.value)
+
+
+def ring_passes(schedule: int, ND: int) -> int:
+    """Phases ("passes") of one ring schedule."""
+    if schedule == SCHED_RANDOM_PERM:
+        return ND
+    ncol = 1 if ND == 1 else 2
+    return 2 * ncol if schedule == SCHED_PALINDROME else ncol
+
+
+@dataclass
+class Ring:
+    """One trajectory of the N_S-spin ring cut into N_D = N_S/L_d domains."""
+    NS: int
+    Ld: int
+    k: int
+    seed: int
+    beta: float
+    state: int = 0
+    J: float = 1.0
+    h: float = 0.0
+    nu: float = 1.0
+    law: int = RATE_BARKER
+    esum: np.ndarray = field(default=None)
+    steps: np.ndarray = field(default=None)
+    hash: int = 0
+    flips: int = 0
+    sched_done: int = 0
+
+    def __post_init__(self):
+        self.state = int(self.state)
+        nD = self.NS // self.Ld
+        self.esum = np.zeros(nD, dtype=np.float64)
+        self.steps = np.zeros(nD, dtype=np.int64)
+        self.hash = int(lib().orc_hash_basis())
+        log2nd = int(round(np.log2(self.Ld)))
+        self.a, self.A = ring_rate_table(self.J, self.beta, self.h, self.law, log2nd)
+
+    @property
+    def n_domains(self) -> int:
+        return self.NS // self.Ld
+
+    def run(self, n_sched: int, schedule: int = SCHED_PALINDROME, time_mode: int = TIME_EXPONENTIAL,
+            obs_every: int = 0):
+        """Run schedules; returns (records [n_rec, 4], states [n_rec]) with a
+        record after every obs_every-th pass (phase) of this call."""
+        n_rec = n_sched * ring_passes(schedule, self.n_domains) // obs_every if obs_every > 0 else 0
+        obs = np.zeros((max(n_rec, 1), 4), dtype=np.float64)
+        st = np.zeros(max(n_rec, 1), dtype=np.uint64)
+        S = np.array([self.state], dtype=np.uint64)
+        H = np.array([self.hash], dtype=np.uint64)
+        F = np.array([self.flips], dtype=np.int64)
+        A = np.ascontiguousarray(self.A)
+        rc = lib().orc_ring_run(_ptr(S, ctypes.c_uint64), self.NS, self.Ld, self.k, _ptr(A, ctypes.c_uint64),
+                                self.seed, schedule, time_mode, self.nu, self.J, self.h, self.sched_done,
+                                n_sched, obs_every, _ptr(self.esum, ctypes.c_double),
+                                _ptr(self.steps, ctypes.c_int64), _ptr(H, ctypes.c_uint64),
+                                _ptr(F, ctypes.c_int64), _ptr(obs, ctypes.c_double), _ptr(st, ctypes.c_uint64))
+        if rc != 0:
+            raise ValueError("oracle rejected the ring configuration")
+        self.state, self.hash, self.flips = int(S[0]), int(H[0]), int(F[0])
+        self.sched_done += n_sched
+        return obs[:n_rec], st[:n_rec]
+
+    def spins(self) -> np.ndarray:
+        return np.array([1 if (self.state >> n) & 1 else -1 for n in range(self.NS)], dtype=np.int8)
+
+    def clock(self, time_mode: int = TIME_EXPONENTIAL) -> float:
+        tsum = 0.0
+        for d in range(self.n_domains):
+            tsum += lib().orc_domain_time(time_mode, float(self.esum[d]), int(self.steps[d]), self.Ld, self.nu)
+        return tsum / self.n_domains
+
+
+def ring_run_many(states, seeds, NS: int, Ld: int, k: int, beta: float, n_sched: int, *, J: float = 1.0,
+                  h: float = 0.0, nu: float = 1.0, law: int = RATE_BARKER, schedule: int = SCHED_PALINDROME,
+                  time_mode: int = TIME_EXPONENTIAL, obs_every: int = 0):
+    """Independent ring trajectories from schedule 0 (trajectory r: start
+    states[r], seed seeds[r]).  Returns (final states, records
+    [n_traj, n_rec, 4], record states [n_traj, n_rec], hashes, flips)."""
+    S = np.ascontiguousarray(np.asarray(states, dtype=np.uint64)).copy()
+    sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    n = len(S)
+    _, A = ring_rate_table(J, beta, h, law, int(round(np.log2(Ld))))
+    n_rec = n_sched * ring_passes(schedule, NS // Ld) // obs_every if obs_every > 0 else 0
+    obs = np.zeros((n, max(n_rec, 1), 4), dtype=np.float64)
+    st = np.zeros((n, max(n_rec, 1)), dtype=np.uint64)
+    H = np.zeros(n, dtype=np.uint64)
+    F = np.zeros(n, dtype=np.int64)
+    rc = lib().orc_ring_run_many(n, _ptr(S, ctypes.c_uint64), _ptr(sd, ctypes.c_uint64), NS, Ld, k,
+                                 _ptr(A, ctypes.c_uint64), schedule, time_mode, nu, J, h, n_sched, obs_every,
+                                 max(n_rec, 1), _ptr(obs, ctypes.c_double), _ptr(st, ctypes.c_uint64),
+                                 _ptr(H, ctypes.c_uint64), _ptr(F, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError("oracle rejected the ring configuration")
+    return S, obs[:, :n_rec], st[:, :n_rec], H, F

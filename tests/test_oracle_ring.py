@@ -1,0 +1,241 @@
+"""Pins of the oracle's 1D ring (Sec. 3.1): rate table, exact operators,
+sampler and clock against closed forms and exact enumeration.
+
+The enumerator is pinned to the transfer-matrix equilibrium of the periodic
+ring and to the textbook random-site kernel; the sampler to the enumerated
+distribution (final states and the paper's time-dependent spin averages,
+Eq. time dependent averages) and to the beta = 0 closed form.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import oracle as orc
+from oracle.enumerate import RingEnumerator
+
+# the paper's first initial condition: spins 6 and 7 up (Sec. 3.1)
+IC0 = 0b11000000
+
+
+def _chi2_pvalue(counts, probs, min_expected=5.0):
+    n = counts.sum()
+    exp = probs * n
+    keep = exp >= min_expected
+    obs_k = np.append(counts[keep], counts[~keep].sum())
+    exp_k = np.append(exp[keep], exp[~keep].sum())
+    if exp_k[-1] < min_expected:
+        obs_k[-2] += obs_k[-1]
+        exp_k[-2] += exp_k[-1]
+        obs_k, exp_k = obs_k[:-1], exp_k[:-1]
+    chi2 = ((obs_k - exp_k) ** 2 / exp_k).sum()
+    return stats.chi2.sf(chi2, len(obs_k) - 1)
+
+
+@pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
+def test_ring_rate_table_detailed_balance_and_values(law):
+    beta, J, h = 0.5, 1.0, 0.2
+    a, A = orc.ring_rate_table(J, beta, h, law, 2)
+    for c in range(6):
+        sp, q = divmod(c, 3)
+        sigma = 1 if sp else -1
+        dE = 2 * sigma * (J * (2 * q - 2) + h)
+        cbar = 3 * (1 - sp) + q  # the flipped spin's class: same neighbours
+        assert a[c] / a[cbar] == pytest.approx(math.exp(-beta * dE), rel=2e-16 * 4)
+        expect = min(1.0, math.exp(-beta * dE)) if law == orc.RATE_METROPOLIS else 1 / (1 + math.exp(beta * dE))
+        assert a[c] == pytest.approx(expect, rel=1e-15)
+        assert int(A[c]) == round(a[c] * 2.0 ** 61)
+    # Barker at beta J = 0.5, h = 0: a lone down spin between two down spins
+    a0, _ = orc.ring_rate_table(1.0, 0.5, 0.0, orc.RATE_BARKER, 3)
+    assert a0[0] == pytest.approx(1 / (1 + math.exp(2.0)), rel=1e-15)
+    assert a0[1] == 0.5 and a0[4] == 0.5
+
+
+@pytest.mark.parametrize("NS,beta", [(8, 0.5), (6, 0.3), (10, 0.8)])
+def test_ring_equilibrium_energy_transfer_matrix(NS, beta):
+    """<H>/N_S of the periodic ring at h = 0: -(t + t^(N-1)) / (1 + t^N), t = tanh(beta J)."""
+    E = RingEnumerator(NS, 2, 1, beta)
+    t = math.tanh(beta)
+    assert float(E.pi @ E.H) / NS == pytest.approx(-(t + t ** (NS - 1)) / (1 + t ** NS), rel=1e-13)
+
+
+def test_ring8_equilibrium_values():
+    """1 x 8 ring at beta J = 0.5: <H>/N = -0.465649 with sd 0.32116 (transfer
+    matrix values for the paper's 1D system)."""
+    E = RingEnumerator(8, 1, 1, 0.5)
+    e = E.H / 8
+    mean = float(E.pi @ e)
+    sd = math.sqrt(float(E.pi @ e ** 2) - mean ** 2)
+    assert mean == pytest.approx(-0.465649, abs=5e-7)
+    assert sd == pytest.approx(0.32116, abs=5e-6)
+
+
+@pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
+def test_ring_unpartitioned_single_step_is_textbook(law):
+    """N_D = 1, k = 1: the uniformised class step is the random-site kernel
+    built from energy differences (App. A with N_D/N_S = 1/N_S)."""
+    E = RingEnumerator(8, 8, 1, 0.5, h=0.1, law=law, quantised=False)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        p = rng.random(E.S)
+        p /= p.sum()
+        assert np.max(np.abs(E.step(0, p) - E.reference_step(p, law))) < 1e-15
+
+
+@pytest.mark.parametrize("Ld", [1, 2, 4])
+def test_ring_schedules_stationarity_and_balance(Ld):
+    E = RingEnumerator(8, Ld, 3, 0.5)
+    pal = lambda p: E.schedule([0, 1, 1, 0], p)
+    assert E.stationarity_error(pal) < 1e-14
+    assert E.detailed_balance_error(pal) < 1e-14
+    fixed = lambda p: E.schedule([0, 1], p)
+    assert E.stationarity_error(fixed) < 1e-14
+    assert E.detailed_balance_error(fixed) > 1e-4  # not closed under reversal
+    if E.ND <= 4:
+        perm = E.random_perm_schedule
+        assert E.stationarity_error(perm) < 1e-14
+        assert E.detailed_balance_error(perm) < 1e-14
+
+
+def test_ring_schedule_sequences():
+    assert orc.ring_schedule(orc.SCHED_PALINDROME, 3, 1, 4) == ([0, 1, 1, 0], False)
+    assert orc.ring_schedule(orc.SCHED_PALINDROME, 3, 1, 1) == ([0, 0], False)
+    assert orc.ring_schedule(orc.SCHED_FIXED, 3, 1, 8) == ([0, 1], False)
+    with pytest.raises(ValueError):
+        orc.ring_schedule(orc.SCHED_PALINDROME, 0, 1, 3)  # odd N_D cannot be 2-coloured
+    # Fisher-Yates over Philox: all 24 orders of 4 domains, uniformly
+    perms = list(itertools.permutations(range(4)))
+    counts = np.zeros(24)
+    for n in range(24000):
+        p, isd = orc.ring_schedule(orc.SCHED_RANDOM_PERM, n, 99, 4)
+        assert isd
+        counts[perms.index(tuple(p))] += 1
+    assert stats.chisquare(counts).pvalue > 1e-5
+    # an odd N_D is fine for domain orders
+    p, _ = orc.ring_schedule(orc.SCHED_RANDOM_PERM, 5, 99, 3)
+    assert sorted(p) == [0, 1, 2]
+
+
+def _state_counts(S, NS):
+    return np.bincount(np.asarray(S, dtype=np.int64), minlength=1 << NS)
+
+
+@pytest.mark.parametrize("Ld,schedule", [(8, orc.SCHED_PALINDROME), (4, orc.SCHED_PALINDROME),
+                                         (2, orc.SCHED_PALINDROME), (1, orc.SCHED_PALINDROME),
+                                         (2, orc.SCHED_FIXED), (2, orc.SCHED_RANDOM_PERM)])
+def test_ring_final_state_distribution(Ld, schedule):
+    k, beta, n = 2, 0.5, 60000
+    E = RingEnumerator(8, Ld, k, beta)
+    p0 = np.zeros(E.S)
+    p0[IC0] = 1.0
+    if schedule == orc.SCHED_RANDOM_PERM:
+        pe = E.random_perm_schedule(p0)
+    else:
+        phases, isd = orc.ring_schedule(schedule, 0, 0, E.ND)
+        pe = E.schedule(phases, p0, isd)
+    S, _, _, _, _ = orc.ring_run_many([IC0] * n, np.arange(1000, 1000 + n), 8, Ld, k, beta, 1, schedule=schedule)
+    assert _chi2_pvalue(_state_counts(S, 8), pe) > 1e-5
+
+
+@pytest.mark.parametrize("schedule", [orc.SCHED_PALINDROME, orc.SCHED_RANDOM_PERM])
+def test_ring_time_dependent_spin_averages(schedule):
+    """<sigma_n(s)> over trajectories at every pass endpoint (Sec. 3.1,
+    Eq. time dependent averages) against the exact evolution of p(s): N_D = 4,
+    N_I = 5, from the paper's IC (..., up, up)."""
+    NS, Ld, k, beta, n_traj, n_sched = 8, 2, 5, 0.5, 40000, 6
+    E = RingEnumerator(NS, Ld, k, beta)
+    _, _, st, _, _ = orc.ring_run_many([IC0] * n_traj, np.arange(7, 7 + n_traj), NS, Ld, k, beta, n_sched,
+                                       schedule=schedule, obs_every=1)
+    sig = 2 * ((st[:, :, None] >> np.arange(NS, dtype=np.uint64)) & np.uint64(1)).astype(np.int64) - 1
+    mean = sig.mean(axis=0)  # [record, site]
+    # exact: the expected spins after each phase
+    p = np.zeros(E.S)
+    p[IC0] = 1.0
+    exact = []
+    if schedule == orc.SCHED_PALINDROME:
+        for _ in range(n_sched):
+            for c in [0, 1, 1, 0]:
+                p = E.phase(c, p, False)
+                exact.append(E.spin_means(p))
+    else:
+        # the average over domain orders of the spin means after each
+        # position of the schedule, one schedule from the IC
+        import itertools
+        perms = list(itertools.permutations(range(E.ND)))
+        acc = np.zeros((E.ND, NS))
+        for q in perms:
+            pp = p.copy()
+            for i, d in enumerate(q):
+                pp = E.phase(d, pp, True)
+                acc[i] += E.spin_means(pp)
+        exact = list(acc / len(perms))
+        mean = mean[:E.ND]
+    exact = np.array(exact)
+    se = np.sqrt(np.maximum(1 - exact ** 2, 1e-12) / n_traj)
+    z = np.abs(mean - exact) / se
+    # Bonferroni over every (record, site) pair
+    assert z.max() < stats.norm.isf(1e-6 / (2 * z.size)), z.max()
+
+
+def test_ring_beta_zero_closed_form():
+    """beta = 0, Metropolis: every step flips a uniform spin of the domain;
+    from all up, <m> after n palindromic schedules is (1 - 2/L_d)^(2 k n).
+    Barker at beta = 0 accepts half the steps: (1 - 1/L_d)^(2 k n)."""
+    NS, Ld, k, n, n_traj = 16, 4, 2, 3, 40000
+    for law, expect in [(orc.RATE_METROPOLIS, (1 - 2 / Ld) ** (2 * k * n)),
+                        (orc.RATE_BARKER, (1 - 1 / Ld) ** (2 * k * n))]:
+        S, obs, _, H, F = orc.ring_run_many([(1 << NS) - 1] * n_traj, np.arange(1, n_traj + 1), NS, Ld, k, 0.0,
+                                            n, obs_every=4, law=law)
+        m = obs[:, -1, 1]
+        assert abs(m.mean() - expect) < 5 * m.std(ddof=1) / math.sqrt(n_traj) + 1e-12
+        if law == orc.RATE_METROPOLIS:
+            assert np.all(F == (NS // Ld) * 2 * k * n)  # no null steps
+
+
+def test_ring_clock_modes():
+    r = orc.Ring(NS=8, Ld=2, k=5, seed=4, beta=0.5, state=IC0)
+    obs, _ = r.run(7, time_mode=orc.TIME_EXPECTED, obs_every=1)
+    # T = s / (N_S nu): a colour pass of N_D/2 domains advances s by N_I N_D / 2
+    s = np.arange(1, 29) * 5 * 2
+    np.testing.assert_array_equal(obs[:, 3], s / 8.0)
+    r = orc.Ring(NS=8, Ld=2, k=5, seed=4, beta=0.5, state=IC0)
+    obs, _ = r.run(40, time_mode=orc.TIME_EXPONENTIAL, obs_every=160)
+    # exponential: each domain's clock is Gamma(steps, 1) / L_d
+    steps = r.steps
+    assert np.all(steps == 2 * 5 * 40)
+    z = (r.esum - steps).sum() / math.sqrt(steps.sum())
+    assert abs(z) < 5
+
+
+def test_ring_resume_is_bit_exact():
+    a = orc.Ring(NS=8, Ld=2, k=5, seed=77, beta=0.5, state=IC0)
+    b = orc.Ring(NS=8, Ld=2, k=5, seed=77, beta=0.5, state=IC0)
+    oa, sa = a.run(10, obs_every=2)
+    ob1, sb1 = b.run(4, obs_every=2)
+    ob2, sb2 = b.run(6, obs_every=2)
+    assert a.state == b.state and a.hash == b.hash and a.flips == b.flips
+    np.testing.assert_array_equal(sa, np.concatenate([sb1, sb2]))
+    np.testing.assert_array_equal(oa[:, :3], np.concatenate([ob1, ob2])[:, :3])
+
+
+def test_ring_long_run_energy():
+    """Long-run mean energy of the partitioned ring against the transfer
+    matrix (N_D = 4, N_I = 5, beta J = 0.5): batch means over trajectories."""
+    n_traj = 64
+    S, obs, _, _, _ = orc.ring_run_many([IC0] * n_traj, np.arange(50, 50 + n_traj), 8, 2, 5, 0.5, 2000,
+                                        obs_every=4)
+    e = obs[:, 50:, 0]
+    per = e.mean(axis=1)
+    t = math.tanh(0.5)
+    exact = -(t + t ** 7) / (1 + t ** 8)
+    assert abs(per.mean() - exact) < 5 * per.std(ddof=1) / math.sqrt(n_traj)
+
+
+def test_ring_invalid_configurations():
+    with pytest.raises(ValueError):
+        orc.Ring(NS=8, Ld=3, k=1, seed=1, beta=0.5).run(1)  # L_d not a power of two
+    with pytest.raises(ValueError):
+        orc.Ring(NS=12, Ld=4, k=1, seed=1, beta=0.5).run(1)  # N_D = 3 cannot be 2-coloured
+    orc.Ring(NS=12, Ld=4, k=1, seed=1, beta=0.5).run(1, schedule=orc.SCHED_RANDOM_PERM)
