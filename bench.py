@@ -18,8 +18,9 @@ spins and observables.
 
 `variants` adds, at N = 1, the batched configuration (512 uneven replicas,
 domain side, k and plan autotuned per group, one CUDA graph per step), the
-gradient configuration (256 x 256^2 with likelihood-ratio scores) and one
-8192^2 lattice (L_d = 64, k = 8).
+gradient configuration (256 x 256^2 with likelihood-ratio scores), one
+8192^2 lattice (L_d = 64, k = 8) and the paper's 1D experiment (the 8-spin
+ring of Sec. 3.1 over its whole N_D x N_I grid, 768000 trajectories).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                     [--workload ising1024|ising8192] [--no-variants]
@@ -372,6 +373,58 @@ def variant_lattice8192(args, peaks, flush, stream):
     return out
 
 
+def variant_ring(args, peaks, flush, stream):
+    """The paper's 1D experiment (Sec. 3.1) as one step: the 8-spin ring at
+    beta J = 0.5, Barker, its 8 pair-of-up-spins ICs x 6000 trajectories for
+    every N_D in {1, 2, 4, 8} and N_I in {1, 2, 5, 10}: S = 800 steps per
+    trajectory in random domain orders per sweep, ensemble sums after every
+    domain process.  16 contexts (one per setting, 48000 trajectories each)
+    on 16 streams; each timed step continues every trajectory by S steps."""
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
+    NS, S, per_ic = 8, 800, 6000
+    ics = [(1 << i) | (1 << ((i + 1) % 8)) for i in (6, 5, 4, 3, 2, 1, 0, 7)]
+    runs = []
+    for a, ND in enumerate((1, 2, 4, 8)):
+        for b, NI in enumerate((1, 2, 5, 10)):
+            n = 8 * per_ic
+            ring = kmc.Ring(NS, NS // ND, NI, wl.replica_seeds(800 + 4 * a + b, n), [ics[i % 8] for i in range(n)])
+            ring.set_rates([0.5] * n, [0.0] * n, law=kmc.KMC_RATE_BARKER)
+            n_sched = S // (NI * ND)
+            n_rec = ring.n_records(n_sched, kmc.KMC_SCHEDULE_RANDOM_PERM, 1)
+            ens = torch.empty((n_rec, 4 + NS), dtype=torch.int64, device="cuda")
+            runs.append((ring, n_sched, ens, torch.cuda.Stream()))
+
+    def step():
+        main = torch.cuda.current_stream()
+        start = torch.cuda.Event()
+        start.record(main)
+        for ring, n_sched, ens, st in runs:
+            st.wait_event(start)
+            with torch.cuda.stream(st):
+                ring.run(n_sched, schedule=kmc.KMC_SCHEDULE_RANDOM_PERM, obs_every=1, records=False,
+                         ensemble=True, out=(None, None, ens))
+                ev = torch.cuda.Event()
+                ev.record(st)
+            main.wait_event(ev)
+
+    ms = device_time(step, args.steps, args.warmup, flush, stream)
+    ev = sum(r.n_traj for r, _, _, _ in runs) * S
+    dev_s = sum(ms) / 1000.0
+    # <H>/N_S at the last record of the N_D = 4, N_I = 5 setting (equilibrium: -0.465649)
+    ens = runs[10][2][-1].cpu().numpy()
+    out = {"value": ev * args.steps / dev_s, "unit": UNIT, "ms_per_step": statistics.mean(ms),
+           "workload": "8-spin ring (Sec. 3.1), beta J = 0.5, Barker, 8 ICs x 6000 trajectories for each of "
+                       "N_D in {1,2,4,8} x N_I in {1,2,5,10}, S = 800 steps per trajectory, random domain order "
+                       "per sweep, ensemble sums after every domain process",
+           "events_per_step": ev, "launches_per_step": len(runs),
+           "energy_per_site_ND4_NI5": float(-ens[0] / (runs[10][0].n_traj * NS))}
+    for r, _, _, _ in runs:
+        r.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -506,7 +559,8 @@ def main():
     if world == 1 and not args.no_variants and args.workload == "ising1024":
         variants = {"batched": variant_batched(args, peaks, flush, stream),
                     "grad": variant_grad(args, peaks, flush, stream),
-                    "lattice8192": variant_lattice8192(args, peaks, flush, stream)}
+                    "lattice8192": variant_lattice8192(args, peaks, flush, stream),
+                    "ring8": variant_ring(args, peaks, flush, stream)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

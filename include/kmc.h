@@ -332,6 +332,103 @@ const char *kmc_last_error(const kmc_ctx *ctx);
 void kmc_destroy(kmc_ctx *ctx);
 int32_t kmc_version(void);
 
+/* ------------------------------------------------------------------------
+ * The 1D ring (Sec. 3.1).  N_S spins on a torus, beta H = -beta J sum_n
+ * s_n s_{n+1} - beta h sum_n s_n (App. A, 1D line, with a field), cut into
+ * N_D = N_S / L_d contiguous domains: domain d holds spins d*L_d ..
+ * d*L_d + L_d - 1 (Eq. 1D partitions).  Each domain process runs k
+ * uniformised steps with its two halo spins frozen (with N_D = 1 the domain
+ * is the whole ring and every neighbour is its own).  The step protocol is
+ * the lattice's: class c = 3 (s > 0) + q, q = number of up neighbours
+ * (0..2), dE_c = 2 s (J (2q - 2) + h); A_c = round(a_c 2^P), P = 63 -
+ * log2(L_d); step j of phase np draws Philox4x32-10 {j, d, np_lo, np_hi},
+ * key = the trajectory seed; target = (w0 | w1<<32) >> 1; null step iff
+ * target >= R' = sum_c n_c A_c; else the first class with target < C_c and
+ * member jj = (target - C_{c-1}) / A_c in ascending site order flips.  The
+ * event hash of a trajectory folds every real event in order as
+ * H <- (H xor e) * 0x100000001b3 (FNV-1a prime) from 0xcbf29ce484222325,
+ * e = np << 32 | j << 16 | (site - d*L_d).
+ *
+ * A configuration is a 64-bit word: bit n set iff spin n is up.  Every
+ * trajectory of a context has the same N_S, L_d and k; seeds, starting
+ * words, beta and h are per trajectory (the paper runs N_TRAJ independent
+ * trajectories per setting, from several initial conditions).  The work is
+ * data parallel over trajectories: one GPU thread runs one trajectory.
+ * ---------------------------------------------------------------------- */
+typedef struct kmc_ring kmc_ring; /* opaque, library-owned */
+
+/*
+ * kmc_ring_create -- n_traj trajectories of an n_sites-spin ring.
+ *   n_traj      >= 1.
+ *   n_sites     N_S, 2..64.
+ *   L_d         domain length: a power of two dividing N_S (1..64).
+ *   k_steps     uniformised steps per domain process (N_I), 0..65535.
+ *   seeds       host [n_traj]: 64-bit Philox keys.
+ *   init        host [n_traj]: starting configuration words (bits >= N_S
+ *               must be 0).
+ *   stream      stream of the upload (cudaStream_t, NULL = legacy default).
+ * The rate table defaults to Barker (Glauber, App. A) at beta = 0.5, J = 1,
+ * h = 0, nu = 1 -- the paper's 1D setting -- until kmc_ring_set_rates.
+ * Counters (steps, real flips, clock, hash) start at zero / the FNV basis.
+ */
+kmc_status kmc_ring_create(kmc_ring **out, int32_t n_traj, int32_t n_sites, int32_t L_d, int32_t k_steps,
+                           const uint64_t *seeds, const uint64_t *init, void *stream);
+
+/*
+ * kmc_ring_set_rates -- acceptance table of App. A for every trajectory:
+ * beta[i], h[i] host arrays [n_traj] (beta >= 0, h finite), J finite,
+ * nu > 0, rate_law KMC_RATE_METROPOLIS or KMC_RATE_BARKER.  The FP64 table
+ * is checked against detailed balance (a_c / a_cbar = exp(-beta dE_c) to
+ * 1e-12 relative; KMC_ENOTBALANCED otherwise).
+ */
+kmc_status kmc_ring_set_rates(kmc_ring *ring, double J, const double *beta, const double *h, double nu,
+                              int32_t rate_law);
+
+/*
+ * kmc_ring_run -- n_schedules schedules of every trajectory, continuing the
+ * global schedule count (the Philox stream position) of earlier calls.
+ * Phases of schedule n, with Philox phase index np = 64 n + p:
+ *   KMC_SCHEDULE_PALINDROME: colours 0 1 1 0 (colour of domain d = d & 1;
+ *                 N_D = 1: 0 0); needs N_D = 1 or even;
+ *   KMC_SCHEDULE_FIXED: colours 0 1 (N_D = 1: 0): a negative test;
+ *   KMC_SCHEDULE_RANDOM_PERM: the paper's random schedule per sweep: a
+ *                 uniform order of the N_D domains (Fisher-Yates; draw i =
+ *                 N_D-1 .. 1 from Philox {i, 0, n_lo, n_hi | 2 << 24}, swap
+ *                 with floor(x (i+1) / 2^64), x = w0 | w1<<32), one domain
+ *                 per phase; any N_D.
+ * A "pass" is one phase; its end is a domain-process endpoint (Sec. 2.3).
+ *   time_mode   KMC_TIME_EXPONENTIAL (Sec. 2.1: clock = sum of -ln v,
+ *               v = (((w2 | w3<<32) >> 11) + 1) 2^-53) or KMC_TIME_EXPECTED.
+ *               The trajectory clock is the mean over domains of t_d =
+ *               (its clock sum or steps) / (L_d nu).
+ *   obs_every   passes between records (0: none).  n_rec = n_schedules *
+ *               passes per schedule / obs_every.
+ *   obs_dev     device double [n_rec][n_traj][4] or NULL: {e, m, e*m, T},
+ *               e = (-J bonds - h mag) / N_S, m = mag / N_S, bonds = sum_n
+ *               s_n s_{n+1}, mag = sum_n s_n; 32-byte aligned.
+ *   state_dev   device uint64 [n_rec][n_traj] or NULL: the configuration
+ *               words at the records (for per-spin time series).
+ *   ens_dev     device int64 [n_rec][4 + N_S] or NULL, overwritten: sums
+ *               over all trajectories at each record (Eq. time dependent
+ *               averages, exact integers): bonds, mag, bonds*mag, mag^2,
+ *               then for each spin n the number of trajectories with it up.
+ * Asynchronous on `stream`; one kernel launch (plus a memset of ens_dev).
+ */
+kmc_status kmc_ring_run(kmc_ring *ring, int64_t n_schedules, int32_t schedule, int32_t time_mode,
+                        int32_t obs_every, double *obs_dev, uint64_t *state_dev, int64_t *ens_dev,
+                        void *stream);
+
+/*
+ * kmc_ring_state -- synchronise the last stream used and copy the counters
+ * to host arrays [n_traj] (any may be NULL): configuration words, event
+ * hashes, real flips, steps and the clock T of the last run's time mode.
+ */
+kmc_status kmc_ring_state(kmc_ring *ring, uint64_t *state, uint64_t *hash, int64_t *flips, int64_t *steps,
+                          double *t);
+
+const char *kmc_ring_last_error(const kmc_ring *ring);
+void kmc_ring_destroy(kmc_ring *ring);
+
 #ifdef __cplusplus
 }
 #endif

@@ -347,3 +347,128 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# The 1D ring (Sec. 3.1): C-ABI wrappers and a convenience class
+# ---------------------------------------------------------------------------
+def _ring_check(ring, status: int):
+    if status != 0:
+        msg = load().kmc_ring_last_error(ring)
+        raise KmcError(status, msg.decode() if msg else "")
+
+
+def kmc_ring_create(n_sites: int, L_d: int, k_steps: int, seeds: Sequence[int], init: Sequence[int],
+                    stream=None) -> ctypes.c_void_p:
+    lib = load()
+    if not torch.cuda.is_available():
+        raise KmcError(-3, "no CUDA device: the library has no CPU path")
+    seeds = [int(x) for x in seeds]
+    init = [int(x) for x in init]
+    if len(seeds) != len(init):
+        raise KmcError(-1, "one seed and one starting word per trajectory")
+    ring = ctypes.c_void_p()
+    st = lib.kmc_ring_create(ctypes.byref(ring), len(seeds), n_sites, L_d, k_steps, _arr(seeds, _u64),
+                             _arr(init, _u64), ctypes.c_void_p(_stream_handle(stream)))
+    if st != 0:
+        raise KmcError(st, "kmc_ring_create rejected n_traj=%d N_S=%d L_d=%d k=%d" % (len(seeds), n_sites, L_d,
+                                                                                        k_steps))
+    return ring
+
+
+def kmc_ring_set_rates(ring, J: float, beta: Sequence[float], h: Sequence[float], nu: float, rate_law: int):
+    _ring_check(ring, load().kmc_ring_set_rates(ring, J, _arr(beta, _dbl), _arr(h, _dbl), nu, rate_law))
+
+
+def kmc_ring_run(ring, n_schedules: int, schedule: int, time_mode: int, obs_every: int,
+                 obs_dev: Optional[torch.Tensor], state_dev: Optional[torch.Tensor], ens_dev: Optional[torch.Tensor],
+                 stream=None):
+    def ptr(t, dtype):
+        if t is None:
+            return None
+        if t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+            raise KmcError(-1, "buffers must be contiguous CUDA tensors of dtype %s" % dtype)
+        return ctypes.c_void_p(t.data_ptr())
+    _ring_check(ring, load().kmc_ring_run(ring, n_schedules, schedule, time_mode, obs_every,
+                                          ptr(obs_dev, torch.float64), ptr(state_dev, torch.int64),
+                                          ptr(ens_dev, torch.int64), ctypes.c_void_p(_stream_handle(stream))))
+
+
+def kmc_ring_state(ring, n_traj: int):
+    S = (_u64 * n_traj)()
+    H = (_u64 * n_traj)()
+    F = (_i64 * n_traj)()
+    St = (_i64 * n_traj)()
+    T = (_dbl * n_traj)()
+    _ring_check(ring, load().kmc_ring_state(ring, S, H, F, St, T))
+    return (np.frombuffer(S, dtype=np.uint64).copy(), np.frombuffer(H, dtype=np.uint64).copy(),
+            np.frombuffer(F, dtype=np.int64).copy(), np.frombuffer(St, dtype=np.int64).copy(),
+            np.frombuffer(T, dtype=np.float64).copy())
+
+
+def kmc_ring_destroy(ring):
+    load().kmc_ring_destroy(ring)
+
+
+def ring_passes(schedule: int, n_domains: int) -> int:
+    """Phases of one ring schedule: N_D for random domain orders, else 4 / 2
+    colour passes (2 / 1 when N_D = 1)."""
+    if schedule == KMC_SCHEDULE_RANDOM_PERM:
+        return n_domains
+    ncol = 1 if n_domains == 1 else 2
+    return 2 * ncol if schedule == KMC_SCHEDULE_PALINDROME else ncol
+
+
+class Ring:
+    """n_traj trajectories of an N_S-spin ring cut into N_S/L_d domains
+    (Sec. 3.1), one GPU thread each."""
+
+    def __init__(self, n_sites: int, L_d: int, k: int, seeds: Sequence[int], init: Sequence[int], stream=None):
+        self.n_sites, self.L_d, self.k = int(n_sites), int(L_d), int(k)
+        self.n_traj = len(seeds)
+        self.ctx = kmc_ring_create(n_sites, L_d, k, seeds, init, stream)
+
+    @property
+    def n_domains(self) -> int:
+        return self.n_sites // self.L_d
+
+    def set_rates(self, beta, h=None, J: float = 1.0, nu: float = 1.0, law: int = KMC_RATE_BARKER):
+        beta = list(beta) if hasattr(beta, "__len__") else [float(beta)] * self.n_traj
+        h = [0.0] * self.n_traj if h is None else (list(h) if hasattr(h, "__len__") else [float(h)] * self.n_traj)
+        kmc_ring_set_rates(self.ctx, J, beta, h, nu, law)
+
+    def n_records(self, n_sched: int, schedule: int, obs_every: int) -> int:
+        return n_sched * ring_passes(schedule, self.n_domains) // obs_every if obs_every > 0 else 0
+
+    def run(self, n_sched: int, schedule: int = KMC_SCHEDULE_PALINDROME, time_mode: int = KMC_TIME_EXPONENTIAL,
+            obs_every: int = 0, records: bool = True, states: bool = False, ensemble: bool = False, stream=None,
+            out=None):
+        """Returns (obs [n_rec, n_traj, 4] | None, states [n_rec, n_traj] int64 | None,
+        ens [n_rec, 4 + N_S] int64 | None); out = that tuple of buffers to reuse."""
+        n_rec = self.n_records(n_sched, schedule, obs_every)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is not None:
+            obs, st, ens = out
+        else:
+            obs = torch.empty((n_rec, self.n_traj, 4), dtype=torch.float64, device=dev) \
+                if (records and n_rec > 0) else None
+            st = torch.empty((n_rec, self.n_traj), dtype=torch.int64, device=dev) if (states and n_rec > 0) else None
+            ens = torch.empty((n_rec, 4 + self.n_sites), dtype=torch.int64, device=dev) \
+                if (ensemble and n_rec > 0) else None
+        kmc_ring_run(self.ctx, n_sched, schedule, time_mode, obs_every, obs, st, ens, stream)
+        return obs, st, ens
+
+    def state(self):
+        """(words, hashes, flips, steps, T) on the host."""
+        return kmc_ring_state(self.ctx, self.n_traj)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            kmc_ring_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

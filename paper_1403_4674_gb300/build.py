@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkmc_gb300.so")
 SOURCES = [os.path.join(CSRC, "kmc_api.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "kmc_kernels.cuh"), os.path.join(ROOT, "include", "kmc.h")]
+DEPS = SOURCES + [os.path.join(CSRC, "kmc_kernels.cuh"), os.path.join(CSRC, "kmc_ring.cuh"),
+        os.path.join(ROOT, "include", "kmc.h")]
 
 
 def nvcc() -> str:

@@ -7,6 +7,7 @@
 // kernels of kmc_kernels.cuh on the caller's stream.
 #include "kmc.h"
 #include "kmc_kernels.cuh"
+#include "kmc_ring.cuh"
 
 #include <cuda_runtime.h>
 
@@ -1599,6 +1600,255 @@ void kmc_destroy(kmc_ctx *c)
     c->prof_events.clear();
     free_all(c);
     delete c;
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------
+// The 1D ring (Sec. 3.1): one thread per trajectory, see kmc_ring.cuh.
+// ---------------------------------------------------------------------------
+struct kmc_ring {
+    int n_traj = 0, NS = 0, Ld = 0, k = 0, log2nd = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t *d_seed = nullptr, *d_A = nullptr, *d_state = nullptr, *d_hash = nullptr, *d_clkM = nullptr;
+    int64_t *d_clkE = nullptr, *d_flips = nullptr, *d_steps = nullptr;
+    double *d_h = nullptr, *d_t = nullptr;
+    double J = 1.0, nu = 1.0;
+    int64_t sched_done = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+kmc_status ring_fail(kmc_ring *g, kmc_status s, const char *fmt, ...)
+{
+    if (g) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        g->err = buf;
+    }
+    return s;
+}
+
+#define RING_CUDA_TRY(g, call)                                                                   \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return ring_fail((g), KMC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+// Ring acceptance table (App. A, Eq. Glauber_TM) for classes c = 3 up + q:
+// dE_c = 2 s (J (2q - 2) + h); A_c = round(a_c 2^P), P = 63 - log2(L_d).
+void ring_table(double J, double beta, double h, int law, int log2nd, double *a, uint64_t *A)
+{
+    const int P = 63 - log2nd;
+    for (int c = 0; c < kmcring::RING_CLASSES; ++c) {
+        const int up = c / 3, q = c % 3;
+        const double sigma = up ? 1.0 : -1.0;
+        const double dE = 2.0 * sigma * (J * (double)(2 * q - 2) + h);
+        double ac;
+        if (law == KMC_RATE_METROPOLIS) ac = (dE <= 0.0) ? 1.0 : std::exp(-beta * dE);
+        else ac = 1.0 / (1.0 + std::exp(beta * dE));
+        a[c] = ac;
+        A[c] = (uint64_t)std::nearbyint(std::ldexp(ac, P));
+    }
+}
+
+void ring_free(kmc_ring *g)
+{
+    void *ptrs[] = {g->d_seed, g->d_A, g->d_state, g->d_hash, g->d_clkM, g->d_clkE, g->d_flips, g->d_steps,
+                    g->d_h, g->d_t};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+template <typename T>
+kmc_status ring_alloc(kmc_ring *g, T **p, size_t n)
+{
+    cudaError_t e = cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
+    if (e != cudaSuccess) return ring_fail(g, KMC_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    return KMC_OK;
+}
+
+int ring_passes(int schedule, int ND)
+{
+    if (schedule == KMC_SCHEDULE_RANDOM_PERM) return ND;
+    const int ncol = (ND == 1) ? 1 : 2;
+    return schedule == KMC_SCHEDULE_PALINDROME ? 2 * ncol : ncol;
+}
+
+} // namespace
+
+extern "C" {
+
+kmc_status kmc_ring_set_rates(kmc_ring *g, double J, const double *beta, const double *h, double nu, int32_t rate_law)
+{
+    if (!g) return KMC_EINVAL;
+    if (!beta || !h) return ring_fail(g, KMC_EINVAL, "beta and h arrays required");
+    if (rate_law != KMC_RATE_METROPOLIS && rate_law != KMC_RATE_BARKER) return ring_fail(g, KMC_EINVAL, "bad rate law");
+    if (!std::isfinite(J) || !(nu > 0.0) || !std::isfinite(nu)) return ring_fail(g, KMC_EINVAL, "J finite and nu > 0 required");
+    const int nc = kmcring::RING_CLASSES;
+    std::vector<double> a((size_t)g->n_traj * nc);
+    std::vector<uint64_t> A((size_t)g->n_traj * nc);
+    for (int i = 0; i < g->n_traj; ++i) {
+        if (!(beta[i] >= 0.0) || !std::isfinite(beta[i]) || !std::isfinite(h[i]))
+            return ring_fail(g, KMC_EINVAL, "trajectory %d: beta >= 0 and finite h required", i);
+        ring_table(J, beta[i], h[i], rate_law, g->log2nd, &a[(size_t)i * nc], &A[(size_t)i * nc]);
+        for (int c = 0; c < nc; ++c) {
+            const int up = c / 3, q = c % 3;
+            const double dE = 2.0 * (up ? 1.0 : -1.0) * (J * (double)(2 * q - 2) + h[i]);
+            const double ratio = a[(size_t)i * nc + c] / a[(size_t)i * nc + 3 * (1 - up) + q];
+            const double want = std::exp(-beta[i] * dE);
+            if (std::fabs(ratio - want) > 1e-12 * want)
+                return ring_fail(g, KMC_ENOTBALANCED, "trajectory %d class %d: a_c/a_cbar = %.17g, exp(-beta dE) = %.17g",
+                                 i, c, ratio, want);
+        }
+    }
+    RING_CUDA_TRY(g, cudaMemcpyAsync(g->d_A, A.data(), A.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, g->stream));
+    RING_CUDA_TRY(g, cudaMemcpyAsync(g->d_h, h, (size_t)g->n_traj * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    RING_CUDA_TRY(g, cudaStreamSynchronize(g->stream)); // the host vectors go out of scope
+    g->J = J;
+    g->nu = nu;
+    return KMC_OK;
+}
+
+kmc_status kmc_ring_create(kmc_ring **out, int32_t n_traj, int32_t n_sites, int32_t L_d, int32_t k_steps,
+                           const uint64_t *seeds, const uint64_t *init, void *stream)
+{
+    if (!out) return KMC_EINVAL;
+    *out = nullptr;
+    if (n_traj < 1 || n_sites < 2 || n_sites > 64 || L_d < 1 || L_d > 64 || (L_d & (L_d - 1)) ||
+        n_sites % L_d != 0 || k_steps < 0 || k_steps > 65535 || !seeds || !init)
+        return KMC_EINVAL;
+    const uint64_t NM = (n_sites == 64) ? ~0ull : ((1ull << n_sites) - 1ull);
+    for (int i = 0; i < n_traj; ++i)
+        if (init[i] & ~NM) return KMC_EINVAL;
+    kmc_ring *g = new kmc_ring();
+    g->n_traj = n_traj;
+    g->NS = n_sites;
+    g->Ld = L_d;
+    g->k = k_steps;
+    while ((1 << g->log2nd) < L_d) ++g->log2nd;
+    g->stream = (cudaStream_t)stream;
+    const size_t n = (size_t)n_traj;
+    kmc_status st = KMC_OK;
+    if ((st = ring_alloc(g, &g->d_seed, n)) || (st = ring_alloc(g, &g->d_A, n * kmcring::RING_CLASSES)) ||
+        (st = ring_alloc(g, &g->d_state, n)) || (st = ring_alloc(g, &g->d_hash, n)) ||
+        (st = ring_alloc(g, &g->d_clkM, n)) || (st = ring_alloc(g, &g->d_clkE, n)) ||
+        (st = ring_alloc(g, &g->d_flips, n)) || (st = ring_alloc(g, &g->d_steps, n)) ||
+        (st = ring_alloc(g, &g->d_h, n)) || (st = ring_alloc(g, &g->d_t, n))) {
+        ring_free(g);
+        delete g;
+        return st;
+    }
+    std::vector<uint64_t> basis(n, HASH_BASIS), one(n, 1ull << 63);
+    if (cudaMemcpyAsync(g->d_seed, seeds, n * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g->d_state, init, n * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g->d_hash, basis.data(), n * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g->d_clkM, one.data(), n * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_clkE, 0, n * 8, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_flips, 0, n * 8, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_steps, 0, n * 8, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_t, 0, n * 8, g->stream) != cudaSuccess || cudaStreamSynchronize(g->stream) != cudaSuccess) {
+        cudaGetLastError();
+        ring_free(g);
+        delete g;
+        return KMC_ECUDA;
+    }
+    std::vector<double> beta(n, 0.5), h(n, 0.0);
+    if ((st = kmc_ring_set_rates(g, 1.0, beta.data(), h.data(), 1.0, KMC_RATE_BARKER)) != KMC_OK) {
+        ring_free(g);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return KMC_OK;
+}
+
+kmc_status kmc_ring_run(kmc_ring *g, int64_t n_schedules, int32_t schedule, int32_t time_mode, int32_t obs_every,
+                        double *obs_dev, uint64_t *state_dev, int64_t *ens_dev, void *stream)
+{
+    if (!g) return KMC_EINVAL;
+    const int ND = g->NS / g->Ld;
+    if (n_schedules < 0) return ring_fail(g, KMC_EINVAL, "n_schedules must be >= 0");
+    if (schedule != KMC_SCHEDULE_PALINDROME && schedule != KMC_SCHEDULE_FIXED && schedule != KMC_SCHEDULE_RANDOM_PERM)
+        return ring_fail(g, KMC_EINVAL, "bad schedule %d", schedule);
+    if (schedule != KMC_SCHEDULE_RANDOM_PERM && ND != 1 && (ND & 1))
+        return ring_fail(g, KMC_EINVAL, "colour schedules need N_D = 1 or even (N_D = %d)", ND);
+    if (time_mode != KMC_TIME_EXPONENTIAL && time_mode != KMC_TIME_EXPECTED)
+        return ring_fail(g, KMC_EINVAL, "the ring supports KMC_TIME_EXPONENTIAL and KMC_TIME_EXPECTED");
+    if (obs_every < 0) return ring_fail(g, KMC_EINVAL, "obs_every must be >= 0");
+    if ((reinterpret_cast<uintptr_t>(obs_dev) & 31u) != 0)
+        return ring_fail(g, KMC_EINVAL, "obs_dev must be 32-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(state_dev) & 7u) != 0 || (reinterpret_cast<uintptr_t>(ens_dev) & 7u) != 0)
+        return ring_fail(g, KMC_EINVAL, "state_dev and ens_dev must be 8-byte aligned");
+    if (g->sched_done > (int64_t)(((1ull << 56) / kmcring::RING_PHASE_SLOTS) - (uint64_t)n_schedules))
+        return ring_fail(g, KMC_EINVAL, "schedule count past the Philox phase range");
+    const int64_t n_rec = obs_every > 0 ? n_schedules * ring_passes(schedule, ND) / obs_every : 0;
+    g->stream = (cudaStream_t)stream;
+    if (ens_dev && n_rec > 0)
+        RING_CUDA_TRY(g, cudaMemsetAsync(ens_dev, 0, (size_t)n_rec * (kmcring::RING_ENS_FIXED + g->NS) * 8, g->stream));
+    if (n_schedules == 0) return KMC_OK;
+    kmcring::RingParams P;
+    P.n_traj = g->n_traj;
+    P.NS = g->NS;
+    P.Ld = g->Ld;
+    P.k = g->k;
+    P.schedule = schedule;
+    P.obs_every = n_rec > 0 ? obs_every : 0;
+    P.sched_begin = g->sched_done;
+    P.n_sched = n_schedules;
+    P.J = g->J;
+    P.nu = g->nu;
+    P.seed = g->d_seed;
+    P.A = g->d_A;
+    P.h = g->d_h;
+    P.state = g->d_state;
+    P.hash = g->d_hash;
+    P.clkM = g->d_clkM;
+    P.clkE = g->d_clkE;
+    P.flips = g->d_flips;
+    P.steps = g->d_steps;
+    P.t = g->d_t;
+    P.obs = n_rec > 0 ? obs_dev : nullptr;
+    P.obs_state = n_rec > 0 ? state_dev : nullptr;
+    P.ens = n_rec > 0 ? reinterpret_cast<unsigned long long *>(ens_dev) : nullptr;
+    const int blocks = (g->n_traj + kmcring::RING_BLOCK - 1) / kmcring::RING_BLOCK;
+    if (time_mode == KMC_TIME_EXPONENTIAL)
+        kmcring::ring_kernel<true><<<blocks, kmcring::RING_BLOCK, 0, g->stream>>>(P);
+    else
+        kmcring::ring_kernel<false><<<blocks, kmcring::RING_BLOCK, 0, g->stream>>>(P);
+    RING_CUDA_TRY(g, cudaGetLastError());
+    ++g->launches;
+    g->sched_done += n_schedules;
+    return KMC_OK;
+}
+
+kmc_status kmc_ring_state(kmc_ring *g, uint64_t *state, uint64_t *hash, int64_t *flips, int64_t *steps, double *t)
+{
+    if (!g) return KMC_EINVAL;
+    RING_CUDA_TRY(g, cudaStreamSynchronize(g->stream));
+    const size_t n = (size_t)g->n_traj * 8;
+    if (state) RING_CUDA_TRY(g, cudaMemcpy(state, g->d_state, n, cudaMemcpyDeviceToHost));
+    if (hash) RING_CUDA_TRY(g, cudaMemcpy(hash, g->d_hash, n, cudaMemcpyDeviceToHost));
+    if (flips) RING_CUDA_TRY(g, cudaMemcpy(flips, g->d_flips, n, cudaMemcpyDeviceToHost));
+    if (steps) RING_CUDA_TRY(g, cudaMemcpy(steps, g->d_steps, n, cudaMemcpyDeviceToHost));
+    if (t) RING_CUDA_TRY(g, cudaMemcpy(t, g->d_t, n, cudaMemcpyDeviceToHost));
+    return KMC_OK;
+}
+
+const char *kmc_ring_last_error(const kmc_ring *g) { return g ? g->err.c_str() : "null ring"; }
+
+void kmc_ring_destroy(kmc_ring *g)
+{
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    ring_free(g);
+    delete g;
 }
 
 } // extern "C"
