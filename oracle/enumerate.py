@@ -307,3 +307,47 @@ class RingEnumerator:
             scale = float(np.abs(x) @ op(self.pi * np.abs(y)))
             worst = max(worst, abs(a - b) / scale)
         return worst
+
+
+class PartEnumerator(Enumerator):
+    """Exact operators of an L x L lattice under a block or vertical-stripe
+    partition with any domain size n_d (Sec. 3.2).  The sampler's per-step
+    flip probability of a class-c site is A_c / M with A_c = round(a_c 2^P),
+    M = n_d 2^P, P = 63 - ceil(log2 n_d) (to 2^-64), i.e. (A_c / 2^P) / n_d.
+    ``random_perm_schedule`` averages the schedule over all N_D! domain orders."""
+
+    def __init__(self, L: int, kind: int, ND: int, k: int, beta: float, J: float = 1.0, h: float = 0.0,
+                 law: int = orc.RATE_BARKER, quantised: bool = True):
+        super().__init__(L, L, k, beta, J=J, h=h, law=law, quantised=False)
+        self.kind, self.ND = kind, ND
+        self.geom = [orc.part_geometry(L, kind, ND, d) for d in range(ND)]
+        x0, y0, w, hh, _ = self.geom[0]
+        self.nd = w * hh
+        self.Dx = None
+        P, _ = orc.part_scale(L, kind, ND)
+        a, A = orc.rate_table(J, beta, h, law, 63 - P)
+        self.acc = (np.array([float(x) for x in A]) / float(2 ** P)) if quantised else a
+
+    def domain_sites(self, d: int):
+        x0, y0, w, hh, _ = self.geom[d]
+        return [(y0 + yy) * self.L + x0 + xx for yy in range(hh) for xx in range(w)]
+
+    def domain_colour(self, d: int) -> int:
+        return self.geom[d][4]
+
+    def domains_of_colour(self, c: int):
+        return [d for d in range(self.ND) if self.geom[d][4] == c]
+
+    def phase(self, unit: int, p: np.ndarray, is_domain: bool) -> np.ndarray:
+        return self.domain(unit, p) if is_domain else self.colour(unit, p)
+
+    def random_perm_schedule(self, p: np.ndarray) -> np.ndarray:
+        import itertools
+        perms = list(itertools.permutations(range(self.ND)))
+        out = np.zeros_like(p)
+        for q in perms:
+            pp = p
+            for d in q:
+                pp = self.domain(d, pp)
+            out = out + pp
+        return out / len(perms)

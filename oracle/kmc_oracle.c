@@ -138,7 +138,7 @@ static int orc_log2(int v)
 int orc_rate_table(double J, double beta, double h, int law, int log2_nd,
                    double a_out[10], uint64_t A_out[10])
 {
-    if (log2_nd < 0 || log2_nd > 12) return -1;
+    if (log2_nd < 0 || log2_nd > 16) return -1;
     if (law != ORC_RATE_METROPOLIS && law != ORC_RATE_BARKER) return -1;
     if (!(beta >= 0.0) || !isfinite(beta) || !isfinite(J) || !isfinite(h))
         return -1;
@@ -911,6 +911,245 @@ int orc_ring_run_many(int64_t n_traj, uint64_t *S, const uint64_t *seeds, int NS
         rc = orc_ring_run(&S[r], NS, Ld, k, A, seeds[r], schedule, time_mode, nu, J, h, 0, n_sched,
                           obs_every, esum, steps, &hh, &ff, obs ? &obs[4 * r * n_rec] : NULL,
                           obs_state ? &obs_state[r * n_rec] : NULL);
+        if (hash) hash[r] = hh;
+        if (flips) flips[r] = ff;
+    }
+    free(esum);
+    free(steps);
+    return rc;
+}
+
+/* ========================================================================
+ * Small 2D lattices under the partitions of Sec. 3.2: an L x L periodic
+ * lattice cut either into a Dx x Dx grid of square blocks (the checkerboard
+ * of Sec. 2.2, Fig. 1) or into N_D vertical stripes of width L/N_D and full
+ * height (Fig. 1 caption: the striped partition; Sec. 3.2 uses both).  The
+ * domain size n_d need not be a power of two (the paper's 12^2 and 100^2
+ * lattices), so the step target is taken as a multiply-high:
+ *   P = 63 - ceil(log2 n_d),  M = n_d 2^P <= 2^63,
+ *   target = floor(X M / 2^64),  X = w0 | w1<<32,
+ * uniform on [0, M) up to one X value per interval boundary (probabilities
+ * exact to 2^-64).  With n_d a power of two M = 2^63 and the target is
+ * X >> 1, the lattice protocol above.  A_c = round(a_c 2^P); a step is null
+ * iff target >= R' = sum_c n_c A_c, so site i flips with probability
+ * A_c(i)/M = (A_c/2^P)/n_d (App. A, selection probability 1/n_d).
+ *
+ * Colours: blocks (bx&1) | ((by&1)<<1) (Dx even), stripes d & 1 (N_D even),
+ * a single domain colour 0.  Schedules: PALINDROME = colours ascending then
+ * descending, FIXED = ascending, RANDOM_PERM = the paper's uniform random
+ * order of all N_D domains per sweep (Fisher-Yates as for the ring, one
+ * domain per phase).  Phase p of schedule n has Philox phase index
+ * np = 64 n + p.  One trajectory's event hash folds its events in order.
+ * ====================================================================== */
+#define ORC_PART_BLOCKS 0
+#define ORC_PART_STRIPES 1
+
+static int orc_ceil_log2(int v)
+{
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+/* Domain d's rectangle: x0, y0, width, height; its colour; -1 if invalid. */
+int orc_part_geometry(int L, int kind, int ND, int d, int *x0, int *y0, int *w, int *hgt, int *colour)
+{
+    if (L < 2 || ND < 1 || d < 0 || d >= ND) return -1;
+    if (kind == ORC_PART_BLOCKS) {
+        int Dx = 0;
+        while ((Dx + 1) * (Dx + 1) <= ND) ++Dx;
+        if (Dx * Dx != ND || L % Dx != 0) return -1;
+        int side = L / Dx, bx = d % Dx, by = d / Dx;
+        *x0 = bx * side; *y0 = by * side; *w = side; *hgt = side;
+        *colour = (Dx == 1) ? 0 : ((Dx & 1) ? -1 : ((bx & 1) | ((by & 1) << 1)));
+        return 0;
+    }
+    if (kind == ORC_PART_STRIPES) {
+        if (L % ND != 0) return -1;
+        *x0 = d * (L / ND); *y0 = 0; *w = L / ND; *hgt = L;
+        *colour = (ND == 1) ? 0 : ((ND & 1) ? -1 : (d & 1));
+        return 0;
+    }
+    return -1;
+}
+
+static int orc_part_ncolours(int kind, int ND)
+{
+    if (ND == 1) return 1;
+    return kind == ORC_PART_BLOCKS ? 4 : 2;
+}
+
+/* Phases of schedule n: colours (is_domain 0) or domains (is_domain 1). */
+int orc_part_schedule(int kind, int schedule, uint64_t n, uint64_t seed, int ND, int out[64], int *is_domain)
+{
+    if (ND < 1 || ND > 64) return -1;
+    *is_domain = 0;
+    if (schedule == ORC_SCHED_PALINDROME || schedule == ORC_SCHED_FIXED) {
+        if (kind == ORC_PART_BLOCKS) {
+            int Dx = 0;
+            while ((Dx + 1) * (Dx + 1) <= ND) ++Dx;
+            if (Dx * Dx != ND || (Dx > 1 && (Dx & 1))) return -1;
+        } else if (kind != ORC_PART_STRIPES || (ND > 1 && (ND & 1))) {
+            return -1;
+        }
+        int nc = orc_part_ncolours(kind, ND), np = 0;
+        for (int c = 0; c < nc; ++c) out[np++] = c;
+        if (schedule == ORC_SCHED_PALINDROME)
+            for (int c = nc - 1; c >= 0; --c) out[np++] = c;
+        return np;
+    }
+    if (schedule == ORC_SCHED_RANDOM_PERM) {
+        int isd;
+        int r = orc_ring_schedule(ORC_SCHED_RANDOM_PERM, n, seed, ND, out, &isd);
+        *is_domain = 1;
+        return r;
+    }
+    return -1;
+}
+
+static void orc_part_visit(int8_t *s, int L, int x0, int y0, int W, int H, int d, int k, const uint64_t A[10],
+                           uint64_t M, uint32_t key0, uint32_t key1, uint64_t np, int time_mode,
+                           double *esum, int64_t *steps, uint64_t *hash, int64_t *flips)
+{
+    const int nd = W * H;
+    int8_t *frozen = (int8_t *)malloc((size_t)L * L);
+    int *cls = (int *)malloc(sizeof(int) * (size_t)nd);
+    /* the halo is frozen: neighbours outside the domain are read from this
+     * copy taken before the process runs */
+    memcpy(frozen, s, (size_t)L * L);
+#define PSITE(xx, yy) s[(int64_t)(yy) * L + (xx)]
+#define INDOM(xx, yy) ((xx) >= x0 && (xx) < x0 + W && (yy) >= y0 && (yy) < y0 + H)
+#define NB(xx, yy) (INDOM(xx, yy) ? PSITE(xx, yy) : frozen[(int64_t)(yy) * L + (xx)])
+    for (int j = 0; j < k; ++j) {
+        uint64_t n[10] = {0};
+        for (int yy = 0; yy < H; ++yy) {
+            for (int xx = 0; xx < W; ++xx) {
+                int x = x0 + xx, y = y0 + yy;
+                int up = NB(x, (y - 1 + L) % L), dn = NB(x, (y + 1) % L);
+                int lf = NB((x - 1 + L) % L, y), rt = NB((x + 1) % L, y);
+                int q = (up > 0) + (dn > 0) + (lf > 0) + (rt > 0);
+                int c = 5 * (PSITE(x, y) > 0) + q;
+                cls[yy * W + xx] = c;
+                n[c] += 1;
+            }
+        }
+        uint64_t R = 0;
+        for (int c = 0; c < 10; ++c) R += n[c] * A[c];
+        uint32_t ctr[4] = {(uint32_t)j, (uint32_t)d, (uint32_t)np,
+                           (uint32_t)((np >> 32) & 0xFFFFFFu) | (ORC_TAG_STEP << 24)};
+        uint32_t key[2] = {key0, key1};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        uint64_t X = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+        uint64_t target = (uint64_t)(((unsigned __int128)X * M) >> 64);
+        uint64_t V = (((uint64_t)w[2] | ((uint64_t)w[3] << 32)) >> 11) + 1u;
+        if (time_mode == ORC_TIME_EXPONENTIAL) esum[d] += -log(ldexp((double)V, -53));
+        steps[d] += 1;
+        if (target >= R) continue;
+        uint64_t C = 0;
+        int c;
+        for (c = 0; c < 10; ++c) {
+            uint64_t wc = n[c] * A[c];
+            if (target < C + wc) break;
+            C += wc;
+        }
+        uint64_t jj = (target - C) / A[c];
+        int site = -1;
+        uint64_t seen = 0;
+        for (int i = 0; i < nd; ++i) {
+            if (cls[i] == c) {
+                if (seen == jj) { site = i; break; }
+                ++seen;
+            }
+        }
+        int xs = x0 + site % W, ys = y0 + site / W;
+        PSITE(xs, ys) = (int8_t)(-PSITE(xs, ys));
+        *flips += 1;
+        uint64_t e = (np << 32) | ((uint64_t)j << 16) | (uint64_t)site;
+        *hash = (*hash ^ e) * ORC_HASH_PRIME;
+    }
+#undef NB
+#undef INDOM
+#undef PSITE
+    free(frozen);
+    free(cls);
+}
+
+/* n_d and the fixed-point scale of a partition: returns P and sets *M. */
+int orc_part_scale(int L, int kind, int ND, uint64_t *M)
+{
+    int x0, y0, w, hh, col;
+    if (orc_part_geometry(L, kind, ND, 0, &x0, &y0, &w, &hh, &col) != 0) return -1;
+    int nd = w * hh;
+    if (nd > 16384) return -1;
+    int P = 63 - orc_ceil_log2(nd);
+    *M = (uint64_t)nd << P;
+    return P;
+}
+
+/* Run n_sched schedules of one trajectory from schedule sched_begin.
+ * esum/steps per domain [N_D]; hash/flips of the trajectory; a record
+ * {e, m, e*m, T} after every obs_every-th pass of the call to obs[4 i]. */
+int orc_part_run(int8_t *s, int L, int kind, int ND, int k, const uint64_t A[10], uint64_t seed,
+                 int schedule, int time_mode, double nu, double J, double h, int64_t sched_begin,
+                 int64_t n_sched, int obs_every, double *esum, int64_t *steps, uint64_t *hash,
+                 int64_t *flips, double *obs)
+{
+    if (L < 2 || L > 4096 || ND < 1 || ND > 64 || k < 0 || k > 65535) return -1;
+    if (time_mode != ORC_TIME_EXPONENTIAL && time_mode != ORC_TIME_EXPECTED) return -1;
+    uint64_t M;
+    if (orc_part_scale(L, kind, ND, &M) < 0) return -1;
+    int x0, y0, W, H, col0;
+    orc_part_geometry(L, kind, ND, 0, &x0, &y0, &W, &H, &col0);
+    const int nd = W * H;
+    uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+    int64_t passes = 0;
+    for (int64_t nl = 0; nl < n_sched; ++nl) {
+        uint64_t n = (uint64_t)(sched_begin + nl);
+        int ph[64], is_domain;
+        int nph = orc_part_schedule(kind, schedule, n, seed, ND, ph, &is_domain);
+        if (nph < 0) return -1;
+        for (int p = 0; p < nph; ++p) {
+            uint64_t np = n * 64u + (uint64_t)p;
+            for (int d = 0; d < ND; ++d) {
+                int dx0, dy0, dw, dh, col;
+                orc_part_geometry(L, kind, ND, d, &dx0, &dy0, &dw, &dh, &col);
+                if (is_domain ? (d != ph[p]) : (col != ph[p])) continue;
+                orc_part_visit(s, L, dx0, dy0, dw, dh, d, k, A, M, key0, key1, np, time_mode, esum, steps,
+                               hash, flips);
+            }
+            ++passes;
+            if (obs_every > 0 && obs && passes % obs_every == 0) {
+                int64_t i = passes / obs_every - 1;
+                orc_observe(s, L, J, h, time_mode, esum, steps, ND, nd, nu, &obs[4 * i]);
+            }
+        }
+    }
+    return 0;
+}
+
+/* Independent partitioned trajectories: trajectory r starts from s0 with
+ * seed seeds[r], runs n_sched schedules from schedule 0; its final spins go
+ * to out[r*L*L ...], its records (or nothing if obs is NULL) to
+ * obs[4 r n_rec ...], its hash and real flips to hash[r], flips[r]. */
+int orc_part_run_many(int64_t n_traj, const int8_t *s0, const uint64_t *seeds, int L, int kind, int ND, int k,
+                      const uint64_t A[10], int schedule, int time_mode, double nu, double J, double h,
+                      int64_t n_sched, int obs_every, int64_t n_rec, int8_t *out, double *obs, uint64_t *hash,
+                      int64_t *flips)
+{
+    if (ND < 1 || ND > 64) return -1;
+    double *esum = (double *)calloc((size_t)ND, sizeof(double));
+    int64_t *steps = (int64_t *)calloc((size_t)ND, sizeof(int64_t));
+    int rc = 0;
+    for (int64_t r = 0; r < n_traj && rc == 0; ++r) {
+        int8_t *s = out + r * (int64_t)L * L;
+        memcpy(s, s0, (size_t)L * L);
+        memset(esum, 0, sizeof(double) * (size_t)ND);
+        memset(steps, 0, sizeof(int64_t) * (size_t)ND);
+        uint64_t hh = ORC_HASH_BASIS;
+        int64_t ff = 0;
+        rc = orc_part_run(s, L, kind, ND, k, A, seeds[r], schedule, time_mode, nu, J, h, 0, n_sched, obs_every,
+                          esum, steps, &hh, &ff, obs ? &obs[4 * r * n_rec] : NULL);
         if (hash) hash[r] = hh;
         if (flips) flips[r] = ff;
     }

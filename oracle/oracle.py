@@ -115,6 +115,22 @@ def lib():
                                    ctypes.c_double, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                    dp, i64p, u64p, i64p, dp, u64p]
         L.orc_ring_run.restype = ctypes.c_int
+        L.orc_part_geometry.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int)] * 5
+        L.orc_part_geometry.restype = ctypes.c_int
+        L.orc_part_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.orc_part_schedule.restype = ctypes.c_int
+        L.orc_part_scale.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p]
+        L.orc_part_scale.restype = ctypes.c_int
+        L.orc_part_run.argtypes = [i8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_uint64,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int, dp, i64p, u64p, i64p, dp]
+        L.orc_part_run.restype = ctypes.c_int
+        L.orc_part_run_many.argtypes = [ctypes.c_int64, i8p, u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, u64p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                        i8p, dp, u64p, i64p]
+        L.orc_part_run_many.restype = ctypes.c_int
         L.orc_ring_run_many.argtypes = [ctypes.c_int64, u64p, u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         u64p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, dp, u64p,
@@ -442,3 +458,124 @@ def ring_run_many(states, seeds, NS: int, Ld: int, k: int, beta: float, n_sched:
     if rc != 0:
         raise ValueError("oracle rejected the ring configuration")
     return S, obs[:, :n_rec], st[:, :n_rec], H, F
+
+
+# ---------------------------------------------------------------------------
+# Small 2D lattices under block or vertical-stripe partitions (Sec. 3.2)
+# ---------------------------------------------------------------------------
+PART_BLOCKS = 0
+PART_STRIPES = 1
+
+
+def part_geometry(L: int, kind: int, ND: int, d: int):
+    """(x0, y0, width, height, colour) of domain d; colour -1 when the
+    partition cannot be coloured (odd number of stripes or blocks per side)."""
+    v = [ctypes.c_int() for _ in range(5)]
+    if lib().orc_part_geometry(L, kind, ND, d, *[ctypes.byref(x) for x in v]) != 0:
+        raise ValueError("bad partition")
+    return tuple(x.value for x in v)
+
+
+def part_schedule(kind: int, schedule: int, n: int, seed: int, ND: int):
+    out = (ctypes.c_int * 64)()
+    isd = ctypes.c_int()
+    nph = lib().orc_part_schedule(kind, schedule, n, seed, ND, out, ctypes.byref(isd))
+    if nph < 0:
+        raise ValueError("bad partition schedule")
+    return [out[i] for i in range(nph)], bool(isd.value)
+
+
+def part_scale(L: int, kind: int, ND: int):
+    """(P, M): fixed-point bits of the acceptance and M = n_d 2^P."""
+    M = np.zeros(1, dtype=np.uint64)
+    P = lib().orc_part_scale(L, kind, ND, _ptr(M, ctypes.c_uint64))
+    if P < 0:
+        raise ValueError("bad partition")
+    return int(P), int(M[0])
+
+
+def part_passes(kind: int, schedule: int, ND: int) -> int:
+    if schedule == SCHED_RANDOM_PERM:
+        return ND
+    nc = 1 if ND == 1 else (4 if kind == PART_BLOCKS else 2)
+    return 2 * nc if schedule == SCHED_PALINDROME else nc
+
+
+@dataclass
+class Partitioned:
+    """One trajectory of an L x L lattice cut into N_D blocks or stripes."""
+    L: int
+    kind: int
+    ND: int
+    k: int
+    seed: int
+    beta: float
+    spins: np.ndarray = field(default=None)
+    J: float = 1.0
+    h: float = 0.0
+    nu: float = 1.0
+    law: int = RATE_BARKER
+    esum: np.ndarray = field(default=None)
+    steps: np.ndarray = field(default=None)
+    hash: int = 0
+    flips: int = 0
+    sched_done: int = 0
+
+    def __post_init__(self):
+        if self.spins is None:
+            self.spins = np.ones((self.L, self.L), dtype=np.int8)
+        self.spins = np.ascontiguousarray(self.spins, dtype=np.int8).copy()
+        self.esum = np.zeros(self.ND, dtype=np.float64)
+        self.steps = np.zeros(self.ND, dtype=np.int64)
+        self.hash = int(lib().orc_hash_basis())
+        self.P, self.M = part_scale(self.L, self.kind, self.ND)
+        self.a, self.A = rate_table(self.J, self.beta, self.h, self.law, 63 - self.P)
+
+    def run(self, n_sched: int, schedule: int = SCHED_PALINDROME, time_mode: int = TIME_EXPONENTIAL,
+            obs_every: int = 0) -> np.ndarray:
+        n_rec = n_sched * part_passes(self.kind, schedule, self.ND) // obs_every if obs_every > 0 else 0
+        obs = np.zeros((max(n_rec, 1), 4), dtype=np.float64)
+        s = self.spins.reshape(-1)
+        H = np.array([self.hash], dtype=np.uint64)
+        F = np.array([self.flips], dtype=np.int64)
+        A = np.ascontiguousarray(self.A)
+        rc = lib().orc_part_run(_ptr(s, ctypes.c_int8), self.L, self.kind, self.ND, self.k, _ptr(A, ctypes.c_uint64),
+                                self.seed, schedule, time_mode, self.nu, self.J, self.h, self.sched_done, n_sched,
+                                obs_every, _ptr(self.esum, ctypes.c_double), _ptr(self.steps, ctypes.c_int64),
+                                _ptr(H, ctypes.c_uint64), _ptr(F, ctypes.c_int64), _ptr(obs, ctypes.c_double))
+        if rc != 0:
+            raise ValueError("oracle rejected the partitioned configuration")
+        self.hash, self.flips = int(H[0]), int(F[0])
+        self.sched_done += n_sched
+        return obs[:n_rec]
+
+    def clock(self, time_mode: int = TIME_EXPONENTIAL) -> float:
+        x0, y0, w, hh, _ = part_geometry(self.L, self.kind, self.ND, 0)
+        tsum = 0.0
+        for d in range(self.ND):
+            tsum += lib().orc_domain_time(time_mode, float(self.esum[d]), int(self.steps[d]), w * hh, self.nu)
+        return tsum / self.ND
+
+
+def part_run_many(s0, seeds, L: int, kind: int, ND: int, k: int, beta: float, n_sched: int, *, J: float = 1.0,
+                  h: float = 0.0, nu: float = 1.0, law: int = RATE_BARKER, schedule: int = SCHED_PALINDROME,
+                  time_mode: int = TIME_EXPONENTIAL, obs_every: int = 0):
+    """Independent partitioned trajectories from the same start s0 [L, L].
+    Returns (final spins [n, L, L], records [n, n_rec, 4], hashes, flips)."""
+    s0 = np.ascontiguousarray(s0, dtype=np.int8).reshape(-1)
+    sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    n = len(sd)
+    P, _ = part_scale(L, kind, ND)
+    _, A = rate_table(J, beta, h, law, 63 - P)
+    n_rec = n_sched * part_passes(kind, schedule, ND) // obs_every if obs_every > 0 else 0
+    out = np.zeros((n, L, L), dtype=np.int8)
+    obs = np.zeros((n, max(n_rec, 1), 4), dtype=np.float64)
+    H = np.zeros(n, dtype=np.uint64)
+    F = np.zeros(n, dtype=np.int64)
+    rc = lib().orc_part_run_many(n, _ptr(s0, ctypes.c_int8), _ptr(sd, ctypes.c_uint64), L, kind, ND, k,
+                                 _ptr(A, ctypes.c_uint64), schedule, time_mode, nu, J, h, n_sched, obs_every,
+                                 max(n_rec, 1), _ptr(out, ctypes.c_int8), _ptr(obs, ctypes.c_double),
+                                 _ptr(H, ctypes.c_uint64), _ptr(F, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError("oracle rejected the partitioned configuration")
+    return out, obs[:, :n_rec], H, F
