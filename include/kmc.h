@@ -429,6 +429,72 @@ kmc_status kmc_ring_state(kmc_ring *ring, uint64_t *state, uint64_t *hash, int64
 const char *kmc_ring_last_error(const kmc_ring *ring);
 void kmc_ring_destroy(kmc_ring *ring);
 
+/* ------------------------------------------------------------------------
+ * Small lattices under the partitions of Sec. 3.2.  An L x L periodic
+ * lattice (L <= 128; App. A energy with a field) cut into
+ *   KMC_PART_BLOCKS:  a Dx x Dx grid of square blocks (N_D = Dx^2, L % Dx
+ *                     == 0), colour (bx & 1) | ((by & 1) << 1), domain
+ *                     d = by Dx + bx (the checkerboard of Sec. 2.2), or
+ *   KMC_PART_STRIPES: N_D vertical stripes of width L / N_D and full height
+ *                     (the striped partition of Fig. 1 and Sec. 3.2),
+ *                     colour d & 1.
+ * n_d = W H may be any size up to 16384: the step target is
+ * floor(X M / 2^64), X = w0 | w1<<32, M = n_d 2^P, P = 63 - ceil(log2 n_d),
+ * A_c = round(a_c 2^P) -- the lattice protocol when n_d is a power of two.
+ * Steps, classes (c = 5 up + q), member order (row-major within the
+ * domain) and the event hash are those of the lattice; the hash folds all
+ * events of a trajectory in order, e = np << 32 | j << 16 | local site.
+ * The work is data parallel over trajectories: one warp runs one trajectory
+ * (the paper runs N_TRAJ independent trajectories per setting).
+ * ---------------------------------------------------------------------- */
+enum { KMC_PART_BLOCKS = 0, KMC_PART_STRIPES = 1 };
+typedef struct kmc_part kmc_part; /* opaque, library-owned */
+
+/*
+ * kmc_part_create -- n_traj trajectories of an L x L lattice.
+ *   partition   KMC_PART_BLOCKS or KMC_PART_STRIPES; n_domains N_D, 1..64.
+ *   k_steps     uniformised steps per domain process (N_I), 0..65535.
+ *   seeds       host [n_traj]: Philox keys.
+ *   spins_dev   device int8 [n_traj][L][L], +1 / -1, row-major; caller-owned,
+ *               holds the state between runs (read at the start of every
+ *               run, written at its end).
+ * Rates default to Barker at beta = 1/2.4, J = 1, h = 0, nu = 1 (the
+ * paper's 2D setting).
+ */
+kmc_status kmc_part_create(kmc_part **out, int32_t n_traj, int32_t L, int32_t partition, int32_t n_domains,
+                           int32_t k_steps, const uint64_t *seeds, int8_t *spins_dev, void *stream);
+
+/* kmc_part_set_rates -- as kmc_ring_set_rates, classes c = 5 up + q. */
+kmc_status kmc_part_set_rates(kmc_part *part, double J, const double *beta, const double *h, double nu,
+                              int32_t rate_law);
+
+/*
+ * kmc_part_run -- n_schedules schedules of every trajectory (continuing the
+ * global schedule count); phases of schedule n have Philox phase index
+ * np = 64 n + p:
+ *   KMC_SCHEDULE_PALINDROME: colours ascending then descending (blocks
+ *                 0 1 2 3 3 2 1 0, stripes 0 1 1 0, one domain 0 0);
+ *                 needs Dx (blocks) or N_D (stripes) to be 1 or even;
+ *   KMC_SCHEDULE_FIXED: colours ascending once (negative test);
+ *   KMC_SCHEDULE_RANDOM_PERM: the paper's random order of all N_D domains
+ *                 per sweep (Fisher-Yates as for the ring), one per phase.
+ *   obs_every   passes between records; obs_dev device double
+ *               [n_rec][n_traj][4] or NULL (32-byte aligned): {e, m, e*m, T},
+ *               e = (-J bonds - h mag) / L^2, T = the mean over domains of
+ *               t_d = (clock sum or steps of d) / (n_d nu).
+ * Asynchronous on `stream`, one kernel launch.  A spin byte that is not
+ * +-1 sets the context's device error word (KMC_EDEVICE at kmc_part_state).
+ */
+kmc_status kmc_part_run(kmc_part *part, int64_t n_schedules, int32_t schedule, int32_t time_mode,
+                        int32_t obs_every, double *obs_dev, void *stream);
+
+/* kmc_part_state -- synchronise and copy host arrays [n_traj] (any may be
+ * NULL): event hashes, real flips, steps, clock T of the last run's mode. */
+kmc_status kmc_part_state(kmc_part *part, uint64_t *hash, int64_t *flips, int64_t *steps, double *t);
+
+const char *kmc_part_last_error(const kmc_part *part);
+void kmc_part_destroy(kmc_part *part);
+
 #ifdef __cplusplus
 }
 #endif

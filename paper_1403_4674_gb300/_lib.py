@@ -31,6 +31,7 @@ EXPORTS = [
     "kmc_domain_state", "kmc_get_rate_table", "kmc_set_launch", "kmc_get_launch", "kmc_set_replica_params", "kmc_set_observation", "kmc_set_horizon",
     "kmc_debug_barrier", "kmc_run_schedule_noalloc", "kmc_profile", "kmc_profile_read", "kmc_kernel_launches", "kmc_last_error", "kmc_destroy", "kmc_version",
     "kmc_ring_create", "kmc_ring_set_rates", "kmc_ring_run", "kmc_ring_state", "kmc_ring_last_error", "kmc_ring_destroy",
+    "kmc_part_create", "kmc_part_set_rates", "kmc_part_run", "kmc_part_state", "kmc_part_last_error", "kmc_part_destroy",
 ]
 
 
@@ -96,6 +97,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmc_ring_last_error.restype = ctypes.c_char_p
     L.kmc_ring_destroy.argtypes = [vp]
     L.kmc_ring_destroy.restype = None
+    L.kmc_part_create.argtypes = [P(vp), i32, i32, i32, i32, i32, P(u64), vp, vp]
+    L.kmc_part_set_rates.argtypes = [vp, dbl, P(dbl), P(dbl), dbl, i32]
+    L.kmc_part_run.argtypes = [vp, i64, i32, i32, i32, vp, vp]
+    L.kmc_part_state.argtypes = [vp, P(u64), P(i64), P(i64), P(dbl)]
+    L.kmc_part_last_error.argtypes = [vp]
+    L.kmc_part_last_error.restype = ctypes.c_char_p
+    L.kmc_part_destroy.argtypes = [vp]
+    L.kmc_part_destroy.restype = None
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is ctypes.c_int:  # default restype: kmc_status

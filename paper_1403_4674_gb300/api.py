@@ -472,3 +472,114 @@ class Ring:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Small lattices under block or vertical-stripe partitions (Sec. 3.2)
+# ---------------------------------------------------------------------------
+KMC_PART_BLOCKS, KMC_PART_STRIPES = 0, 1
+
+
+def _part_check(part, status: int):
+    if status != 0:
+        msg = load().kmc_part_last_error(part)
+        raise KmcError(status, msg.decode() if msg else "")
+
+
+def kmc_part_create(L: int, partition: int, n_domains: int, k_steps: int, seeds: Sequence[int],
+                    spins_dev: torch.Tensor, stream=None) -> ctypes.c_void_p:
+    lib = load()
+    if not torch.cuda.is_available():
+        raise KmcError(-3, "no CUDA device: the library has no CPU path")
+    seeds = [int(x) for x in seeds]
+    if spins_dev.dtype != torch.int8 or not spins_dev.is_cuda or not spins_dev.is_contiguous() \
+            or spins_dev.numel() != len(seeds) * L * L:
+        raise KmcError(-1, "spins_dev must be a contiguous int8 CUDA tensor [n_traj, L, L]")
+    part = ctypes.c_void_p()
+    st = lib.kmc_part_create(ctypes.byref(part), len(seeds), L, partition, n_domains, k_steps, _arr(seeds, _u64),
+                             ctypes.c_void_p(spins_dev.data_ptr()), ctypes.c_void_p(_stream_handle(stream)))
+    if st != 0:
+        raise KmcError(st, "kmc_part_create rejected L=%d partition=%d N_D=%d k=%d" % (L, partition, n_domains,
+                                                                                       k_steps))
+    return part
+
+
+def kmc_part_set_rates(part, J: float, beta: Sequence[float], h: Sequence[float], nu: float, rate_law: int):
+    _part_check(part, load().kmc_part_set_rates(part, J, _arr(beta, _dbl), _arr(h, _dbl), nu, rate_law))
+
+
+def kmc_part_run(part, n_schedules: int, schedule: int, time_mode: int, obs_every: int,
+                 obs_dev: Optional[torch.Tensor], stream=None):
+    if obs_dev is not None and (obs_dev.dtype != torch.float64 or not obs_dev.is_cuda or not obs_dev.is_contiguous()):
+        raise KmcError(-1, "obs_dev must be a contiguous float64 CUDA tensor")
+    _part_check(part, load().kmc_part_run(part, n_schedules, schedule, time_mode, obs_every,
+                                          None if obs_dev is None else ctypes.c_void_p(obs_dev.data_ptr()),
+                                          ctypes.c_void_p(_stream_handle(stream))))
+
+
+def kmc_part_state(part, n_traj: int):
+    H = (_u64 * n_traj)()
+    F = (_i64 * n_traj)()
+    St = (_i64 * n_traj)()
+    T = (_dbl * n_traj)()
+    _part_check(part, load().kmc_part_state(part, H, F, St, T))
+    return (np.frombuffer(H, dtype=np.uint64).copy(), np.frombuffer(F, dtype=np.int64).copy(),
+            np.frombuffer(St, dtype=np.int64).copy(), np.frombuffer(T, dtype=np.float64).copy())
+
+
+def kmc_part_destroy(part):
+    load().kmc_part_destroy(part)
+
+
+def part_passes(partition: int, schedule: int, n_domains: int) -> int:
+    if schedule == KMC_SCHEDULE_RANDOM_PERM:
+        return n_domains
+    nc = 1 if n_domains == 1 else (4 if partition == KMC_PART_BLOCKS else 2)
+    return 2 * nc if schedule == KMC_SCHEDULE_PALINDROME else nc
+
+
+class Partitioned:
+    """n_traj trajectories of an L x L lattice (L <= 128) cut into N_D square
+    blocks or vertical stripes (Sec. 3.2), one GPU warp each.  `spins` is the
+    caller-visible int8 state [n_traj, L, L]."""
+
+    def __init__(self, L: int, partition: int, n_domains: int, k: int, seeds: Sequence[int],
+                 spins: Optional[torch.Tensor] = None, stream=None):
+        self.L, self.partition, self.n_domains, self.k = int(L), int(partition), int(n_domains), int(k)
+        self.n_traj = len(seeds)
+        if spins is None:
+            spins = torch.ones((self.n_traj, L, L), dtype=torch.int8, device="cuda")
+        self.spins = spins
+        self.ctx = kmc_part_create(L, partition, n_domains, k, seeds, spins, stream)
+
+    def set_rates(self, beta, h=None, J: float = 1.0, nu: float = 1.0, law: int = KMC_RATE_BARKER):
+        beta = list(beta) if hasattr(beta, "__len__") else [float(beta)] * self.n_traj
+        h = [0.0] * self.n_traj if h is None else (list(h) if hasattr(h, "__len__") else [float(h)] * self.n_traj)
+        kmc_part_set_rates(self.ctx, J, beta, h, nu, law)
+
+    def n_records(self, n_sched: int, schedule: int, obs_every: int) -> int:
+        return n_sched * part_passes(self.partition, schedule, self.n_domains) // obs_every if obs_every > 0 else 0
+
+    def run(self, n_sched: int, schedule: int = KMC_SCHEDULE_PALINDROME, time_mode: int = KMC_TIME_EXPONENTIAL,
+            obs_every: int = 0, stream=None, out: Optional[torch.Tensor] = None) -> Optional[torch.Tensor]:
+        n_rec = self.n_records(n_sched, schedule, obs_every)
+        obs = out
+        if obs is None and n_rec > 0:
+            obs = torch.empty((n_rec, self.n_traj, 4), dtype=torch.float64, device=self.spins.device)
+        kmc_part_run(self.ctx, n_sched, schedule, time_mode, obs_every, obs, stream)
+        return obs
+
+    def state(self):
+        """(hashes, flips, steps, T) on the host."""
+        return kmc_part_state(self.ctx, self.n_traj)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            kmc_part_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

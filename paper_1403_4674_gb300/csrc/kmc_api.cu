@@ -8,6 +8,7 @@
 #include "kmc.h"
 #include "kmc_kernels.cuh"
 #include "kmc_ring.cuh"
+#include "kmc_part.cuh"
 
 #include <cuda_runtime.h>
 
@@ -1848,6 +1849,261 @@ void kmc_ring_destroy(kmc_ring *g)
     if (!g) return;
     cudaStreamSynchronize(g->stream);
     ring_free(g);
+    delete g;
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------
+// Small lattices under block or stripe partitions (Sec. 3.2): one warp per
+// trajectory, see kmc_part.cuh.
+// ---------------------------------------------------------------------------
+struct kmc_part {
+    int n_traj = 0, L = 0, kind = 0, ND = 0, k = 0, Dx = 0, W = 0, H = 0, ncol = 1, P = 0;
+    uint64_t M = 0;
+    int8_t *spins = nullptr;
+    cudaStream_t stream = nullptr;
+    uint64_t *d_seed = nullptr, *d_A = nullptr, *d_hash = nullptr, *d_clkM = nullptr;
+    int64_t *d_clkE = nullptr, *d_flips = nullptr, *d_steps = nullptr;
+    double *d_h = nullptr, *d_t = nullptr;
+    int *d_err = nullptr;
+    double J = 1.0, nu = 1.0;
+    int64_t sched_done = 0;
+    std::string err;
+};
+
+namespace {
+
+kmc_status part_fail(kmc_part *g, kmc_status s, const char *fmt, ...)
+{
+    if (g) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        g->err = buf;
+    }
+    return s;
+}
+
+#define PART_CUDA_TRY(g, call)                                                                   \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return part_fail((g), KMC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+void part_free(kmc_part *g)
+{
+    void *ptrs[] = {g->d_seed, g->d_A, g->d_hash, g->d_clkM, g->d_clkE, g->d_flips, g->d_steps, g->d_h, g->d_t,
+                    g->d_err};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+template <typename T>
+bool part_alloc(T **p, size_t n)
+{
+    return cudaMalloc((void **)p, (n ? n : 1) * sizeof(T)) == cudaSuccess;
+}
+
+} // namespace
+
+extern "C" {
+
+kmc_status kmc_part_set_rates(kmc_part *g, double J, const double *beta, const double *h, double nu, int32_t rate_law)
+{
+    if (!g) return KMC_EINVAL;
+    if (!beta || !h) return part_fail(g, KMC_EINVAL, "beta and h arrays required");
+    if (rate_law != KMC_RATE_METROPOLIS && rate_law != KMC_RATE_BARKER) return part_fail(g, KMC_EINVAL, "bad rate law");
+    if (!std::isfinite(J) || !(nu > 0.0) || !std::isfinite(nu)) return part_fail(g, KMC_EINVAL, "J finite and nu > 0 required");
+    std::vector<double> a((size_t)g->n_traj * 10), gb(10), gh(10);
+    std::vector<uint64_t> A((size_t)g->n_traj * 10);
+    for (int i = 0; i < g->n_traj; ++i) {
+        if (!(beta[i] >= 0.0) || !std::isfinite(beta[i]) || !std::isfinite(h[i]))
+            return part_fail(g, KMC_EINVAL, "trajectory %d: beta >= 0 and finite h required", i);
+        // A_c = round(a_c 2^P), P = 63 - ceil(log2 n_d): the lattice table with log2 n_d rounded up
+        build_table(J, beta[i], h[i], rate_law, 63 - g->P, &a[(size_t)i * 10], &A[(size_t)i * 10], gb.data(), gh.data());
+        for (int c = 0; c < 10; ++c) {
+            const int up = c / 5, q = c % 5;
+            const double dE = 2.0 * (up ? 1.0 : -1.0) * (J * (double)(2 * q - 4) + h[i]);
+            const double ratio = a[(size_t)i * 10 + c] / a[(size_t)i * 10 + 5 * (1 - up) + q];
+            const double want = std::exp(-beta[i] * dE);
+            if (std::fabs(ratio - want) > 1e-12 * want)
+                return part_fail(g, KMC_ENOTBALANCED, "trajectory %d class %d: a_c/a_cbar = %.17g, exp(-beta dE) = %.17g",
+                                 i, c, ratio, want);
+        }
+    }
+    PART_CUDA_TRY(g, cudaMemcpyAsync(g->d_A, A.data(), A.size() * 8, cudaMemcpyHostToDevice, g->stream));
+    PART_CUDA_TRY(g, cudaMemcpyAsync(g->d_h, h, (size_t)g->n_traj * 8, cudaMemcpyHostToDevice, g->stream));
+    PART_CUDA_TRY(g, cudaStreamSynchronize(g->stream));
+    g->J = J;
+    g->nu = nu;
+    return KMC_OK;
+}
+
+kmc_status kmc_part_create(kmc_part **out, int32_t n_traj, int32_t L, int32_t partition, int32_t n_domains,
+                           int32_t k_steps, const uint64_t *seeds, int8_t *spins_dev, void *stream)
+{
+    if (!out) return KMC_EINVAL;
+    *out = nullptr;
+    if (n_traj < 1 || L < 2 || L > kmcpart::PART_MAX_L || n_domains < 1 || n_domains > 64 || k_steps < 0 ||
+        k_steps > 65535 || !seeds || !spins_dev)
+        return KMC_EINVAL;
+    int Dx = 0, W = 0, H = 0, ncol = 1;
+    if (partition == KMC_PART_BLOCKS) {
+        while ((Dx + 1) * (Dx + 1) <= n_domains) ++Dx;
+        if (Dx * Dx != n_domains || L % Dx != 0) return KMC_EINVAL;
+        W = H = L / Dx;
+        ncol = (Dx == 1) ? 1 : 4;
+    } else if (partition == KMC_PART_STRIPES) {
+        if (L % n_domains != 0) return KMC_EINVAL;
+        W = L / n_domains;
+        H = L;
+        ncol = (n_domains == 1) ? 1 : 2;
+    } else {
+        return KMC_EINVAL;
+    }
+    const int nd = W * H;
+    if (nd > 16384) return KMC_EINVAL;
+    int lg = 0;
+    while ((1 << lg) < nd) ++lg;
+    kmc_part *g = new kmc_part();
+    g->n_traj = n_traj;
+    g->L = L;
+    g->kind = partition;
+    g->ND = n_domains;
+    g->k = k_steps;
+    g->Dx = Dx;
+    g->W = W;
+    g->H = H;
+    g->ncol = ncol;
+    g->P = 63 - lg;
+    g->M = (uint64_t)nd << g->P;
+    g->spins = spins_dev;
+    g->stream = (cudaStream_t)stream;
+    const size_t n = (size_t)n_traj;
+    if (!part_alloc(&g->d_seed, n) || !part_alloc(&g->d_A, n * 10) || !part_alloc(&g->d_hash, n) ||
+        !part_alloc(&g->d_clkM, n) || !part_alloc(&g->d_clkE, n) || !part_alloc(&g->d_flips, n) ||
+        !part_alloc(&g->d_steps, n) || !part_alloc(&g->d_h, n) || !part_alloc(&g->d_t, n) || !part_alloc(&g->d_err, 1)) {
+        cudaGetLastError();
+        part_free(g);
+        delete g;
+        return KMC_ENOMEM;
+    }
+    std::vector<uint64_t> basis(n, HASH_BASIS), one(n, 1ull << 63);
+    if (cudaMemcpyAsync(g->d_seed, seeds, n * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g->d_hash, basis.data(), n * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g->d_clkM, one.data(), n * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_clkE, 0, n * 8, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_flips, 0, n * 8, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_steps, 0, n * 8, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_t, 0, n * 8, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream) != cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess) {
+        cudaGetLastError();
+        part_free(g);
+        delete g;
+        return KMC_ECUDA;
+    }
+    std::vector<double> beta(n, 1.0 / 2.4), h(n, 0.0);
+    kmc_status st = kmc_part_set_rates(g, 1.0, beta.data(), h.data(), 1.0, KMC_RATE_BARKER);
+    if (st != KMC_OK) {
+        part_free(g);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return KMC_OK;
+}
+
+kmc_status kmc_part_run(kmc_part *g, int64_t n_schedules, int32_t schedule, int32_t time_mode, int32_t obs_every,
+                        double *obs_dev, void *stream)
+{
+    if (!g) return KMC_EINVAL;
+    if (n_schedules < 0 || obs_every < 0) return part_fail(g, KMC_EINVAL, "n_schedules and obs_every must be >= 0");
+    if (schedule != KMC_SCHEDULE_PALINDROME && schedule != KMC_SCHEDULE_FIXED && schedule != KMC_SCHEDULE_RANDOM_PERM)
+        return part_fail(g, KMC_EINVAL, "bad schedule %d", schedule);
+    if (schedule != KMC_SCHEDULE_RANDOM_PERM) {
+        const int per_side = (g->kind == KMC_PART_BLOCKS) ? g->Dx : g->ND;
+        if (per_side != 1 && (per_side & 1))
+            return part_fail(g, KMC_EINVAL, "colour schedules need an even number of %s (or one domain)",
+                             g->kind == KMC_PART_BLOCKS ? "blocks per side" : "stripes");
+    }
+    if (time_mode != KMC_TIME_EXPONENTIAL && time_mode != KMC_TIME_EXPECTED)
+        return part_fail(g, KMC_EINVAL, "KMC_TIME_EXPONENTIAL or KMC_TIME_EXPECTED required");
+    if ((reinterpret_cast<uintptr_t>(obs_dev) & 31u) != 0) return part_fail(g, KMC_EINVAL, "obs_dev must be 32-byte aligned");
+    if (g->sched_done > (int64_t)(((1ull << 56) / kmcpart::PART_PHASE_SLOTS) - (uint64_t)n_schedules))
+        return part_fail(g, KMC_EINVAL, "schedule count past the Philox phase range");
+    if (n_schedules == 0) return KMC_OK;
+    const int passes = (schedule == KMC_SCHEDULE_RANDOM_PERM) ? g->ND
+                       : (schedule == KMC_SCHEDULE_PALINDROME ? 2 * g->ncol : g->ncol);
+    const int64_t n_rec = obs_every > 0 ? n_schedules * passes / obs_every : 0;
+    g->stream = (cudaStream_t)stream;
+    kmcpart::PartParams P;
+    P.n_traj = g->n_traj;
+    P.L = g->L;
+    P.kind = g->kind;
+    P.ND = g->ND;
+    P.k = g->k;
+    P.Dx = g->Dx;
+    P.W = g->W;
+    P.H = g->H;
+    P.ncol = g->ncol;
+    P.schedule = schedule;
+    P.obs_every = n_rec > 0 ? obs_every : 0;
+    P.sched_begin = g->sched_done;
+    P.n_sched = n_schedules;
+    P.M = g->M;
+    P.J = g->J;
+    P.nu = g->nu;
+    P.seed = g->d_seed;
+    P.A = g->d_A;
+    P.h = g->d_h;
+    P.spins = g->spins;
+    P.hash = g->d_hash;
+    P.clkM = g->d_clkM;
+    P.clkE = g->d_clkE;
+    P.flips = g->d_flips;
+    P.steps = g->d_steps;
+    P.t = g->d_t;
+    P.obs = n_rec > 0 ? obs_dev : nullptr;
+    P.err = g->d_err;
+    const int blocks = (g->n_traj + kmcpart::PART_WARPS - 1) / kmcpart::PART_WARPS;
+    const size_t smem = (size_t)kmcpart::PART_WARPS * (2 * kmcpart::PART_MAX_L + 8) * sizeof(uint64_t);
+    if (time_mode == KMC_TIME_EXPONENTIAL)
+        kmcpart::part_kernel<true><<<blocks, kmcpart::PART_WARPS * 32, smem, g->stream>>>(P);
+    else
+        kmcpart::part_kernel<false><<<blocks, kmcpart::PART_WARPS * 32, smem, g->stream>>>(P);
+    PART_CUDA_TRY(g, cudaGetLastError());
+    g->sched_done += n_schedules;
+    return KMC_OK;
+}
+
+kmc_status kmc_part_state(kmc_part *g, uint64_t *hash, int64_t *flips, int64_t *steps, double *t)
+{
+    if (!g) return KMC_EINVAL;
+    PART_CUDA_TRY(g, cudaStreamSynchronize(g->stream));
+    int err = 0;
+    PART_CUDA_TRY(g, cudaMemcpy(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    const size_t n = (size_t)g->n_traj * 8;
+    if (hash) PART_CUDA_TRY(g, cudaMemcpy(hash, g->d_hash, n, cudaMemcpyDeviceToHost));
+    if (flips) PART_CUDA_TRY(g, cudaMemcpy(flips, g->d_flips, n, cudaMemcpyDeviceToHost));
+    if (steps) PART_CUDA_TRY(g, cudaMemcpy(steps, g->d_steps, n, cudaMemcpyDeviceToHost));
+    if (t) PART_CUDA_TRY(g, cudaMemcpy(t, g->d_t, n, cudaMemcpyDeviceToHost));
+    if (err & 1) return part_fail(g, KMC_EDEVICE, "a spin byte was not +1 or -1");
+    if (err) return part_fail(g, KMC_EDEVICE, "device error word %d", err);
+    return KMC_OK;
+}
+
+const char *kmc_part_last_error(const kmc_part *g) { return g ? g->err.c_str() : "null partitioned lattice"; }
+
+void kmc_part_destroy(kmc_part *g)
+{
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    part_free(g);
     delete g;
 }
 
