@@ -19,8 +19,9 @@ spins and observables.
 `variants` adds, at N = 1, the batched configuration (512 uneven replicas,
 domain side, k and plan autotuned per group, one CUDA graph per step), the
 gradient configuration (256 x 256^2 with likelihood-ratio scores), one
-8192^2 lattice (L_d = 64, k = 8) and the paper's 1D experiment (the 8-spin
-ring of Sec. 3.1 over its whole N_D x N_I grid, 768000 trajectories).
+8192^2 lattice (L_d = 64, k = 8), the paper's 1D experiment (the 8-spin
+ring of Sec. 3.1 over its whole N_D x N_I grid, 768000 trajectories) and its
+2D experiments (12^2 and 100^2 in stripes and blocks, Sec. 3.2).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                     [--workload ising1024|ising8192] [--no-variants]
@@ -425,6 +426,61 @@ def variant_ring(args, peaks, flush, stream):
     return out
 
 
+def variant_part(args, peaks, flush, stream):
+    """The paper's 2D experiments (Sec. 3.2) as one step: 12^2 x 500 and
+    100^2 x 50 trajectories at T = 2.4, Barker, from the all-up state, in
+    vertical stripes (N_D = 2, 4) and square blocks (N_D = 4; 16 for 100^2),
+    N_I in {1, 2, 5, 10}, the random domain order per sweep; per timed step
+    every trajectory advances 1.6e4 (12^2) or 1.6e5 (100^2) steps with 64
+    energy records.  28 contexts on 28 streams."""
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
+    S_, B_ = kmc.KMC_PART_STRIPES, kmc.KMC_PART_BLOCKS
+    settings = []
+    for L, n_traj, S, parts in [(12, 500, 16000, [(S_, 2), (S_, 4), (B_, 4)]),
+                                (100, 50, 160000, [(S_, 2), (S_, 4), (B_, 4), (B_, 16)])]:
+        for kind, ND in parts:
+            for NI in (1, 2, 5, 10):
+                settings.append((L, n_traj, S, kind, ND, NI))
+    runs = []
+    for i, (L, n_traj, S, kind, ND, NI) in enumerate(settings):
+        g = kmc.Partitioned(L, kind, ND, NI, wl.replica_seeds(1200 + i, n_traj))
+        g.set_rates([1 / 2.4] * n_traj, law=kmc.KMC_RATE_BARKER)
+        n_sched = S // (ND * NI)
+        obs_every = max(1, n_sched * ND // 64)
+        obs = torch.empty((g.n_records(n_sched, kmc.KMC_SCHEDULE_RANDOM_PERM, obs_every), n_traj, 4),
+                          dtype=torch.float64, device="cuda")
+        runs.append((g, n_sched, obs_every, obs, torch.cuda.Stream(), n_traj * S))
+
+    def step():
+        main = torch.cuda.current_stream()
+        start = torch.cuda.Event()
+        start.record(main)
+        for g, n_sched, obs_every, obs, st, _ in runs:
+            st.wait_event(start)
+            with torch.cuda.stream(st):
+                g.run(n_sched, schedule=kmc.KMC_SCHEDULE_RANDOM_PERM, obs_every=obs_every, out=obs)
+                ev = torch.cuda.Event()
+                ev.record(st)
+            main.wait_event(ev)
+
+    ms = device_time(step, args.steps, args.warmup, flush, stream)
+    ev = sum(r[5] for r in runs)
+    dev_s = sum(ms) / 1000.0
+    # mean energy per site over the last records of the 12^2, 4-stripe, N_I = 5 setting
+    e12 = float(runs[6][3][-16:, :, 0].mean().item())
+    out = {"value": ev * args.steps / dev_s, "unit": UNIT, "ms_per_step": statistics.mean(ms),
+           "workload": "Sec. 3.2 grid: 12^2 x 500 and 100^2 x 50 trajectories, T = 2.4, Barker, stripes N_D in "
+                       "{2,4}, blocks N_D = 4 (and 16 for 100^2), N_I in {1,2,5,10}, random domain order per "
+                       "sweep; per step 1.6e4 (12^2) / 1.6e5 (100^2) steps per trajectory",
+           "events_per_step": ev, "launches_per_step": len(runs),
+           "energy_per_site_12x12_stripes4_NI5": e12}
+    for r in runs:
+        r[0].close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -560,7 +616,8 @@ def main():
         variants = {"batched": variant_batched(args, peaks, flush, stream),
                     "grad": variant_grad(args, peaks, flush, stream),
                     "lattice8192": variant_lattice8192(args, peaks, flush, stream),
-                    "ring8": variant_ring(args, peaks, flush, stream)}
+                    "ring8": variant_ring(args, peaks, flush, stream),
+                    "partitions2d": variant_part(args, peaks, flush, stream)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

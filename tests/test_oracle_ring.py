@@ -239,3 +239,18 @@ def test_ring_invalid_configurations():
     with pytest.raises(ValueError):
         orc.Ring(NS=12, Ld=4, k=1, seed=1, beta=0.5).run(1)  # N_D = 3 cannot be 2-coloured
     orc.Ring(NS=12, Ld=4, k=1, seed=1, beta=0.5).run(1, schedule=orc.SCHED_RANDOM_PERM)
+
+
+def test_table1_ring_row_is_not_the_exact_ring():
+    """Table 1's 1x8 row (<H>/N_S = -0.238(0.138) at 1/(beta J) = 2) is not the
+    exact periodic 8-ring at beta J = 0.5 (-0.465649, sd 0.32116): read as a
+    Table 1 anomaly; the pins above use the transfer matrix."""
+    import json
+    import os
+    rows = {r["lattice"]: r for r in json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                                                 "table1_energies.json")))["rows"]}
+    r8 = rows["1x8"]
+    E = RingEnumerator(8, 1, 1, 1.0 / r8["T"])
+    exact = float(E.pi @ E.H) / 8
+    assert exact == pytest.approx(-0.465649, abs=5e-7)
+    assert abs(exact - r8["analytic"]) > 0.2 and abs(exact - r8["sim"]) > 0.2
