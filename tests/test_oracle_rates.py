@@ -65,4 +65,4 @@ def test_invalid_arguments_rejected():
     with pytest.raises(ValueError):
         orc.rate_table(1.0, 0.4, 0.0, 7, 8)
     with pytest.raises(ValueError):
-        orc.rate_table(1.0, 0.4, 0.0, 0, 13)
+        orc.rate_table(1.0, 0.4, 0.0, 0, 17)  # n_d <= 2^16 (100^2 stripes need 2^13)
