@@ -2071,7 +2071,7 @@ kmc_status kmc_part_run(kmc_part *g, int64_t n_schedules, int32_t schedule, int3
     P.obs = n_rec > 0 ? obs_dev : nullptr;
     P.err = g->d_err;
     const int blocks = (g->n_traj + kmcpart::PART_WARPS - 1) / kmcpart::PART_WARPS;
-    const size_t smem = (size_t)kmcpart::PART_WARPS * (2 * kmcpart::PART_MAX_L + 8) * sizeof(uint64_t);
+    const size_t smem = (size_t)kmcpart::PART_WARPS * kmcpart::PART_WARP_WORDS * sizeof(uint64_t);
     if (time_mode == KMC_TIME_EXPONENTIAL)
         kmcpart::part_kernel<true><<<blocks, kmcpart::PART_WARPS * 32, smem, g->stream>>>(P);
     else

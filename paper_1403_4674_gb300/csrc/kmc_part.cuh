@@ -31,6 +31,9 @@ constexpr int PART_MAX_L = 128;
 constexpr int PART_PHASE_SLOTS = 64; // Philox phase index np = n*64 + p
 constexpr int PART_BLOCKS = 0, PART_STRIPES = 1;
 constexpr uint32_t PART_TAG_PERM = 2u;
+// shared memory per warp (64-bit words): bit rows, the domain order, and the
+// class counts of every domain (int [64][10])
+constexpr int PART_WARP_WORDS = 2 * PART_MAX_L + 8 + 64 * 10 / 2;
 
 struct PartParams {
     int n_traj, L, kind, ND, k;
@@ -129,6 +132,15 @@ __device__ __forceinline__ int select128(u128 m, uint32_t rr)
     return 64 + kmcdev::select_bit((uint64_t)(m >> 64), rr - pl);
 }
 
+// Class 5 up + (number of up neighbours) of site (x, y), from the live rows.
+__device__ __forceinline__ int site_class(const uint64_t *rows, int x, int y, int L)
+{
+    const int xm = (x == 0) ? L - 1 : x - 1, xp = (x == L - 1) ? 0 : x + 1;
+    const int ym = (y == 0) ? L - 1 : y - 1, yp = (y == L - 1) ? 0 : y + 1;
+    auto bit = [&](int xx, int yy) { return (int)((rows[2 * yy + (xx >> 6)] >> (xx & 63)) & 1ull); };
+    return 5 * bit(x, y) + bit(xm, y) + bit(xp, y) + bit(x, ym) + bit(x, yp);
+}
+
 template <bool EXPO>
 __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams P)
 {
@@ -137,8 +149,9 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
     const int tr = blockIdx.x * PART_WARPS + warp;
     if (tr >= P.n_traj) return; // whole warps only; no CTA-wide barrier below
     const int L = P.L;
-    uint64_t *rows = part_smem + (size_t)warp * (2 * PART_MAX_L + 8);
+    uint64_t *rows = part_smem + (size_t)warp * PART_WARP_WORDS;
     uint8_t *order = reinterpret_cast<uint8_t *>(rows + 2 * PART_MAX_L);
+    int *dcount = reinterpret_cast<int *>(rows + 2 * PART_MAX_L + 8); // [N_D][10] class counts
     const u128 Lm = (L == 128) ? ~(u128)0 : (((u128)1 << L) - 1);
     const int8_t *sp = P.spins + (size_t)tr * L * L;
 
@@ -172,8 +185,7 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
     const u128 DM0 = (W == 128) ? ~(u128)0 : (((u128)1 << W) - 1);
     const uint64_t M = P.M;
 
-    auto visit = [&](int d, uint64_t np) {
-        int x0, y0;
+    auto domain_origin = [&](int d, int &x0, int &y0) {
         if (P.kind == PART_STRIPES) {
             x0 = d * W;
             y0 = 0;
@@ -181,8 +193,21 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
             x0 = (d % P.Dx) * W;
             y0 = (d / P.Dx) * W;
         }
+    };
+    // class counts of every domain, kept up to date flip by flip
+    for (int d = 0; d < P.ND; ++d) {
+        int x0, y0;
+        domain_origin(d, x0, y0);
+        const uint32_t n = part_counts(rows, lane, y0, Hd, RPL, L, Lm, DM0 << x0);
+        if (lane < 10) dcount[d * 10 + lane] = (int)n;
+    }
+    __syncwarp();
+
+    auto visit = [&](int d, uint64_t np) {
+        int x0, y0;
+        domain_origin(d, x0, y0);
         const u128 DM = DM0 << x0;
-        uint32_t n_c = part_counts(rows, lane, y0, Hd, RPL, L, Lm, DM);
+        uint32_t n_c = (lane < 10) ? (uint32_t)dcount[d * 10 + lane] : 0u;
         uint64_t Wc = (uint64_t)n_c * A;
         uint64_t Cinc = kmcdev::prefix16(Wc, lane);
         uint64_t R = __shfl_sync(FULL_WARP, Cinc, 9);
@@ -257,14 +282,34 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
                 }
                 yx = __shfl_sync(FULL_WARP, yx, wl);
                 const int yy = (int)(yx >> 8), x = (int)(yx & 255u);
+                // the flip changes the classes of the site and its four
+                // neighbours (lanes 0..4); their domains' counts follow
+                const int y = y0 + yy;
+                int sx = x, sy = y;
+                if (lane == 1) sx = (x == 0) ? L - 1 : x - 1;
+                if (lane == 2) sx = (x == L - 1) ? 0 : x + 1;
+                if (lane == 3) sy = (y == 0) ? L - 1 : y - 1;
+                if (lane == 4) sy = (y == L - 1) ? 0 : y + 1;
+                const bool mine = lane < 5 && !(L == 2 && (lane == 2 || lane == 4)); // L = 2: x-1 = x+1
+                const int sd = (P.kind == PART_STRIPES) ? sx / W : (sy / W) * P.Dx + sx / W;
                 __syncwarp();
-                if (lane == 0) rows[2 * (y0 + yy) + (x >> 6)] ^= 1ull << (x & 63);
+                const int old_c = mine ? site_class(rows, sx, sy, L) : 0;
+                __syncwarp();
+                if (lane == 0) rows[2 * y + (x >> 6)] ^= 1ull << (x & 63);
+                __syncwarp();
+                if (mine) {
+                    const int new_c = site_class(rows, sx, sy, L);
+                    if (new_c != old_c) {
+                        atomicAdd(&dcount[sd * 10 + old_c], -1);
+                        atomicAdd(&dcount[sd * 10 + new_c], 1);
+                    }
+                }
                 __syncwarp();
                 const uint64_t ev = (np << 32) | ((uint64_t)(base + jx) << 16) | (uint64_t)(yy * W + (x - x0));
                 H = (H ^ ev) * HASH_PRIME;
                 ++flips;
                 pos = jx + 1;
-                n_c = part_counts(rows, lane, y0, Hd, RPL, L, Lm, DM);
+                n_c = (lane < 10) ? (uint32_t)dcount[d * 10 + lane] : 0u;
                 Wc = (uint64_t)n_c * A;
                 Cinc = kmcdev::prefix16(Wc, lane);
                 R = __shfl_sync(FULL_WARP, Cinc, 9);

@@ -57,30 +57,28 @@ __device__ __forceinline__ uint64_t ring_right(uint64_t S, int NS, uint64_t NM)
     return (S >> 1) | ((S & 1ull) << (NS - 1));
 }
 
-// Class masks of one domain (DM: its sites) and the inclusive cumulative
-// rates C_c = sum_{c' <= c} n_c' A_c' in class order 0..5.
-struct RingClasses {
-    uint64_t M[RING_CLASSES];
-    uint64_t C[RING_CLASSES];
-};
+// Sites of class c = 3 up + q of one domain (DM: its sites).
+__device__ __forceinline__ uint64_t ring_class_mask(uint64_t S, uint64_t DM, int NS, uint64_t NM, int c)
+{
+    const uint64_t lw = ring_left(S, NS, NM), rw = ring_right(S, NS, NM);
+    const int q = (c >= 3) ? c - 3 : c;
+    const uint64_t qm = (q == 0) ? ~(lw | rw) : ((q == 1) ? (lw ^ rw) : (lw & rw));
+    return ((c >= 3) ? S : ~S) & qm & DM;
+}
 
-__device__ __forceinline__ void ring_classes(RingClasses &rc, uint64_t S, uint64_t DM, int NS, uint64_t NM,
-                                             const uint64_t (&A)[RING_CLASSES])
+// Inclusive cumulative rates C_c = sum_{c' <= c} n_c' A_c' in class order 0..5.
+__device__ __forceinline__ void ring_cumulative(uint64_t (&C)[RING_CLASSES], uint64_t S, uint64_t DM, int NS,
+                                                uint64_t NM, const uint64_t (&A)[RING_CLASSES])
 {
     const uint64_t lw = ring_left(S, NS, NM), rw = ring_right(S, NS, NM);
     const uint64_t q0 = ~(lw | rw), q1 = lw ^ rw, q2 = lw & rw;
     const uint64_t up = S & DM, dn = ~S & DM;
-    rc.M[0] = dn & q0;
-    rc.M[1] = dn & q1;
-    rc.M[2] = dn & q2;
-    rc.M[3] = up & q0;
-    rc.M[4] = up & q1;
-    rc.M[5] = up & q2;
+    const uint64_t M[RING_CLASSES] = {dn & q0, dn & q1, dn & q2, up & q0, up & q1, up & q2};
     uint64_t acc = 0;
 #pragma unroll
     for (int c = 0; c < RING_CLASSES; ++c) {
-        acc += (uint64_t)__popcll(rc.M[c]) * A[c];
-        rc.C[c] = acc;
+        acc += (uint64_t)__popcll(M[c]) * A[c];
+        C[c] = acc;
     }
 }
 
@@ -89,16 +87,20 @@ __device__ __forceinline__ void ring_classes(RingClasses &rc, uint64_t S, uint64
 // w1<<32) >> 1 on [0, L_d 2^P); target >= R' is a null step; otherwise the
 // class is the first c with target < C_c and the member jj = (target -
 // C_{c-1}) / A_c, counted in ascending site order, flips (App. A, the
-// n-fold way's cumulative selection of Sec. 2.1).
+// n-fold way's cumulative selection of Sec. 2.1).  jj < n_c <= 64: an FP32
+// estimate with every rounding toward the lower side (x down, A_c up, the
+// reciprocal down, the product toward zero) is jj or jj - 1, and one exact
+// integer comparison decides.
 template <bool EXPO>
 __device__ __forceinline__ void ring_visit(uint64_t &S, uint64_t &H, int64_t &flips, uint64_t &clkM, int64_t &clkE,
                                            int d, int Ld, int k, int NS, uint64_t NM, uint64_t DM0, uint64_t np,
-                                           uint2 key, const uint64_t (&A)[RING_CLASSES])
+                                           uint2 key, const uint64_t (&A)[RING_CLASSES],
+                                           const float (&invA)[RING_CLASSES])
 {
     const int first = d * Ld;
     const uint64_t DM = DM0 << first;
-    RingClasses rc;
-    ring_classes(rc, S, DM, NS, NM, A);
+    uint64_t C[RING_CLASSES];
+    ring_cumulative(C, S, DM, NS, NM, A);
     for (int j = 0; j < k; ++j) {
         const uint4 w = kmcdev::philox4x32_10(
             make_uint4((uint32_t)j, (uint32_t)d, (uint32_t)np, (uint32_t)(np >> 32) & 0xFFFFFFu), key);
@@ -108,22 +110,27 @@ __device__ __forceinline__ void ring_visit(uint64_t &S, uint64_t &H, int64_t &fl
             const int z = __clzll((long long)V);
             kmcdev::mant_mul(clkM, clkE, V << z, (int64_t)(10 - z));
         }
-        if (tgt >= rc.C[RING_CLASSES - 1]) continue; // null step
-        uint64_t lo = 0, Ac = A[0], Mc = rc.M[0];
+        if (tgt >= C[RING_CLASSES - 1]) continue; // null step
+        uint64_t lo = 0, Ac = A[0];
+        float inv = invA[0];
+        int c = 0;
 #pragma unroll
-        for (int c = 1; c < RING_CLASSES; ++c) {
-            if (tgt >= rc.C[c - 1]) {
-                lo = rc.C[c - 1];
-                Ac = A[c];
-                Mc = rc.M[c];
+        for (int cc = 1; cc < RING_CLASSES; ++cc) {
+            if (tgt >= C[cc - 1]) {
+                lo = C[cc - 1];
+                Ac = A[cc];
+                inv = invA[cc];
+                c = cc;
             }
         }
-        const uint32_t jj = (uint32_t)((tgt - lo) / Ac); // < n_c <= 64
-        const int site = kmcdev::select_bit(Mc, jj);
+        const uint64_t x = tgt - lo;
+        uint32_t jj = (uint32_t)__fmul_rz(kmcdev::u64_to_float_rz(x), inv);
+        jj = (x - (uint64_t)jj * Ac >= Ac) ? jj + 1u : jj;
+        const int site = kmcdev::select_bit(ring_class_mask(S, DM, NS, NM, c), jj);
         S ^= 1ull << site;
         ++flips;
         H = (H ^ ((np << 32) | ((uint64_t)j << 16) | (uint64_t)(site - first))) * HASH_PRIME;
-        ring_classes(rc, S, DM, NS, NM, A);
+        ring_cumulative(C, S, DM, NS, NM, A);
     }
 }
 
@@ -154,7 +161,7 @@ __device__ __forceinline__ double ring_clock(bool expo, uint64_t M, int64_t E, i
 }
 
 template <bool EXPO>
-__global__ void __launch_bounds__(RING_BLOCK) ring_kernel(const RingParams P)
+__global__ void __launch_bounds__(RING_BLOCK, 6) ring_kernel(const RingParams P)
 {
     __shared__ int ens_blk[RING_ENS_FIXED + 64];
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -167,8 +174,12 @@ __global__ void __launch_bounds__(RING_BLOCK) ring_kernel(const RingParams P)
     const uint64_t DM0 = (Ld == 64) ? ~0ull : ((1ull << Ld) - 1ull);
 
     uint64_t A[RING_CLASSES];
+    float invA[RING_CLASSES]; // 1/A_c from below: A_c rounded up, reciprocal rounded down
 #pragma unroll
-    for (int c = 0; c < RING_CLASSES; ++c) A[c] = P.A[(size_t)r * RING_CLASSES + c];
+    for (int c = 0; c < RING_CLASSES; ++c) {
+        A[c] = P.A[(size_t)r * RING_CLASSES + c];
+        invA[c] = A[c] ? __frcp_rd(kmcdev::u64_to_float_ru(A[c])) : 0.0f;
+    }
     const uint64_t seed = P.seed[r];
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const double hr = P.h[r];
@@ -191,13 +202,13 @@ __global__ void __launch_bounds__(RING_BLOCK) ring_kernel(const RingParams P)
             const uint64_t np = n * RING_PHASE_SLOTS + (uint64_t)p;
             if (active) {
                 if (perm) {
-                    ring_visit<EXPO>(S, H, flips, clkM, clkE, order[p], Ld, k, NS, NM, DM0, np, key, A);
+                    ring_visit<EXPO>(S, H, flips, clkM, clkE, order[p], Ld, k, NS, NM, DM0, np, key, A, invA);
                     steps += k;
                 } else {
                     // colour of phase p: 0 1 [1 0] (one colour when N_D = 1)
                     const int col = (p < ncol) ? p : (2 * ncol - 1 - p);
                     for (int d = col; d < ND; d += ncol) {
-                        ring_visit<EXPO>(S, H, flips, clkM, clkE, d, Ld, k, NS, NM, DM0, np, key, A);
+                        ring_visit<EXPO>(S, H, flips, clkM, clkE, d, Ld, k, NS, NM, DM0, np, key, A, invA);
                         steps += k;
                     }
                 }
