@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "kMC events/s on 1 GB300 (plain vs batched+grad), % of roofline, bit-exact"
 UNIT = "events/s"
+L2_FLUSH_FLOATS = 512 * 1024 * 1024 // 4  # a 512 MB buffer written between timed steps (L2 is 129 MB)
 
 
 def parse():
@@ -56,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the batched and gradient variants")
     ap.add_argument("--plan", default="", help="launch plan mode,size,warps (skips the plan tuning)")
+    ap.add_argument("--only", default="", choices=["", "batched", "grad", "lattice8192", "ring8", "partitions2d"],
+                    help="time one variant alone and print its JSON object (profiling runs; not the contract line)")
     return ap.parse_args()
 
 
@@ -481,10 +484,29 @@ def variant_part(args, peaks, flush, stream):
     return out
 
 
+VARIANTS = {"batched": "variant_batched", "grad": "variant_grad", "lattice8192": "variant_lattice8192",
+            "ring8": "variant_ring", "partitions2d": "variant_part"}
+
+
+def only_variant(args):
+    import torch
+    torch.cuda.set_device(0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    flush = torch.empty(L2_FLUSH_FLOATS, dtype=torch.float32, device="cuda")
+    out = globals()[VARIANTS[args.only]](args, peaks, flush, torch.cuda.current_stream())
+    print(json.dumps({"variant": args.only, **out}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.only:
+        return only_variant(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -539,7 +561,7 @@ def main():
         lat.reset(reset_mode)
         lat.run(w.schedules, obs_every=w.obs_every, out=obs_buf)
 
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_FLOATS, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
