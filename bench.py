@@ -232,6 +232,26 @@ TRAFFIC_KERNEL_SHA256 = "b39ba3d388a38893f15cdb6fd56ac906dd582dd56ceedfb94a7ab6b
 # profiles/run_kernel_ising1024x18_small_full.md).  Includes the halo polls.
 INST_PER_STEP = 8933046445 / 51609600
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
+# The same for the variants, from `ncu --metrics smsp__inst_executed.sum` over
+# a full-size timed launch of `bench.py --only grad` / `--only batched`
+# (profiles/run_kernel_variants_instructions.md).  Batched: measured on the
+# single-context configuration of the same 512 replicas (L_d = 8, k = 16)
+# that the tuner chose under the profiler.
+INST_PER_STEP_GRAD = 297033429567 / 1310720000
+INST_PER_STEP_BATCHED = 318837499070 / 2636876800
+
+
+def issue_roofline(inst_per_step: float, steps_per_s: float, peaks: dict, source: str):
+    """Issue-rate view: warp instructions per second against 4 per SM cycle x
+    the SMs x the maximum SM clock (runs stay at it: see the clocks record)."""
+    import torch
+    if TRAFFIC_KERNEL_SHA256 != kernel_source_sha256():
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = ISSUE_PER_SM_CYCLE * sms * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    ach = inst_per_step * steps_per_s
+    return {"bound": "issue", "achieved": ach, "peak": peak, "unit": "warp-inst/s", "frac": ach / peak,
+            "source": source % inst_per_step}
 
 
 def kernel_source_sha256() -> str:
@@ -298,6 +318,11 @@ def variant_batched(args, peaks, flush, stream):
            "tune_s": tune_s, "events_per_step": ev,
            "roofline": roofline(by, dev_s / args.steps, peaks)}
     out["roofline"]["note"] = "step-level: the groups' run kernels overlap on concurrent streams"
+    iss = issue_roofline(INST_PER_STEP_BATCHED, ev * args.steps / dev_s, peaks,
+                         "ncu warp instructions per step (%.1f, single-context configuration of the same batch) x "
+                         "steps/s of the whole step; peak = 4 per SM cycle x SMs x maximum SM clock")
+    if iss is not None:
+        out["roofline"]["issue"] = iss
     batch.close()
     return out
 
@@ -340,6 +365,11 @@ def variant_grad(args, peaks, flush, stream):
            "lr_grad_e_beta_h": [float(ge[0]), float(ge[1])], "lr_grad_m_beta_h": [float(gm[0]), float(gm[1])],
            "events_per_step": ev,
            "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks)}
+    iss = issue_roofline(INST_PER_STEP_GRAD, ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0, peaks,
+                         "ncu warp instructions per step of this kernel (%.1f) x steps / launch time; "
+                         "peak = 4 per SM cycle x SMs x maximum SM clock")
+    if iss is not None:
+        out["roofline"]["issue"] = iss
     lat.close()
     return out
 

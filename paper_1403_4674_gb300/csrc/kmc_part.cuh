@@ -370,13 +370,13 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
                     const int64_t mag = 2ll * up - (int64_t)L * L;
                     const double e = __ddiv_rn(__dsub_rn(__dmul_rn(-P.J, (double)bonds), __dmul_rn(hr, (double)mag)), N);
                     const double m = __ddiv_rn((double)mag, N);
-                    double4 v;
+                    double4_32a v;
                     v.x = e;
                     v.y = m;
                     v.z = __dmul_rn(e, m);
                     v.w = kmcdev::domain_time(EXPO, clkM, clkE, steps, __dmul_rn(N, P.nu));
                     const int64_t rec = passes / P.obs_every - 1;
-                    reinterpret_cast<double4 *>(P.obs)[(size_t)rec * P.n_traj + tr] = v;
+                    reinterpret_cast<double4_32a *>(P.obs)[(size_t)rec * P.n_traj + tr] = v;
                 }
             }
         }

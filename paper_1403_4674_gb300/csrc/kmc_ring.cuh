@@ -226,12 +226,12 @@ __global__ void __launch_bounds__(RING_BLOCK, 6) ring_kernel(const RingParams P)
                         const double e = __ddiv_rn(__dsub_rn(__dmul_rn(-P.J, (double)bonds), __dmul_rn(hr, (double)mag)),
                                                    (double)NS);
                         const double m = __ddiv_rn((double)mag, (double)NS);
-                        double4 v;
+                        double4_32a v;
                         v.x = e;
                         v.y = m;
                         v.z = __dmul_rn(e, m);
                         v.w = ring_clock(EXPO, clkM, clkE, steps, NS, P.nu);
-                        reinterpret_cast<double4 *>(P.obs)[o] = v;
+                        reinterpret_cast<double4_32a *>(P.obs)[o] = v;
                     }
                     if (P.obs_state) P.obs_state[o] = S;
                 }
