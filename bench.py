@@ -239,6 +239,7 @@ ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four sch
 # that the tuner chose under the profiler.
 INST_PER_STEP_GRAD = 297033429567 / 1310720000
 INST_PER_STEP_BATCHED = 318837499070 / 2636876800
+INST_PER_STEP_8192 = 160917810000 / 524288000  # one 2000-schedule launch of `bench.py --only lattice8192`
 
 
 def issue_roofline(inst_per_step: float, steps_per_s: float, peaks: dict, source: str):
@@ -403,6 +404,11 @@ def variant_lattice8192(args, peaks, flush, stream):
                        "schedules" % n,
            "plan": list(plan), "launch": list(lat.launch()), "events_per_step": ev,
            "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks)}
+    iss = issue_roofline(INST_PER_STEP_8192, ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0, peaks,
+                         "ncu warp instructions per step of this kernel (%.1f) x steps / launch time; "
+                         "peak = 4 per SM cycle x SMs x maximum SM clock")
+    if iss is not None:
+        out["roofline"]["issue"] = iss
     lat.close()
     return out
 
