@@ -117,5 +117,24 @@ def time_dependent_average(A: np.ndarray) -> np.ndarray:
     return np.asarray(A, dtype=np.float64).mean(axis=0)
 
 
-__all__ = ["autocorrelation", "efficiency", "fit_tau", "rescale_time", "steps_per_schedule", "tau_par",
-           "time_dependent_average"]
+def ring_ensemble_averages(ens: np.ndarray, n_traj: int, n_sites: int, J: float = 1.0, h: float = 0.0) -> dict:
+    """Time-dependent averages over trajectories (Sec. 3.1, Eq. time dependent
+    averages) from the ring's device ensemble sums.
+
+    ens: [n_rec, 4 + N_S] int64 rows {sum bonds, sum mag, sum bonds*mag,
+    sum mag^2, number of trajectories with spin n up (n = 0..N_S-1)}, as
+    kmc_ring_run writes them.  Returns per record: <sigma_n> [n_rec, N_S],
+    <H>/N_S, <m>, and <A> = <H m> / N_S^2 (the paper's 1D observable, per
+    site), with H = -J bonds - h mag."""
+    ens = np.asarray(ens, dtype=np.int64)
+    n = float(n_traj)
+    N = float(n_sites)
+    bonds, mag, bm, m2 = (ens[:, i].astype(np.float64) for i in range(4))
+    spins = 2.0 * ens[:, 4:4 + n_sites].astype(np.float64) / n - 1.0
+    H = (-J * bonds - h * mag) / n
+    A = (-J * bm - h * m2) / n
+    return {"spin": spins, "energy": H / N, "magnetisation": mag / (n * N), "A": A / (N * N)}
+
+
+__all__ = ["autocorrelation", "efficiency", "fit_tau", "rescale_time", "ring_ensemble_averages", "steps_per_schedule",
+           "tau_par", "time_dependent_average"]

@@ -76,3 +76,24 @@ def test_tau_par_of_oracle_trajectories_matches_exact_chain():
         rows.append(obs[:, 0] * obs[:, 1] * (L * L) ** 2)  # H m from e and m per site
     est = stats.tau_par(np.array(rows), steps_per_record=sps, max_lag=40)
     assert abs(est / tau_exact - 1.0) < 0.08, (est, tau_exact)
+
+
+def test_ring_ensemble_averages_match_per_trajectory_records():
+    """The averages from the ring's ensemble sums equal the means over the
+    oracle's per-trajectory records (e, m, e*m) and record states."""
+    from oracle import oracle as orc
+    from paper_1403_4674_gb300 import stats as st
+    n, NS, J, h = 500, 8, 0.8, 0.15
+    _, obs, states, _, _ = orc.ring_run_many([0b11000000] * n, np.arange(3, 3 + n), NS, 2, 5, 0.5, 6, J=J, h=h,
+                                             obs_every=1)
+    bits = ((states[:, :, None] >> np.arange(NS, dtype=np.uint64)) & np.uint64(1)).astype(np.int64)  # [traj, rec, n]
+    sig = 2 * bits - 1
+    mag = sig.sum(axis=2)
+    bonds = (sig * np.roll(sig, -1, axis=2)).sum(axis=2)
+    ens = np.concatenate([np.stack([bonds.sum(0), mag.sum(0), (bonds * mag).sum(0), (mag * mag).sum(0)], 1),
+                          bits.sum(axis=0)], axis=1)
+    av = st.ring_ensemble_averages(ens, n, NS, J=J, h=h)
+    np.testing.assert_allclose(av["energy"], obs[:, :, 0].mean(axis=0), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(av["magnetisation"], obs[:, :, 1].mean(axis=0), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(av["A"], obs[:, :, 2].mean(axis=0), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(av["spin"], sig.mean(axis=0), rtol=0, atol=1e-15)
