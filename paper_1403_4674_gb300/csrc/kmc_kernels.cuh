@@ -578,20 +578,25 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
     // -sum_c n_c a_c dlog a_c / (n_d - R).  The numerator is an exact int64
     // sum of the fixed-point products a_c dlog a_c 2^Q, and n_d - R comes
     // from the exact fixed-point rate sum, (n_d 2^P - R') 2^-P with
-    // n_d 2^P = 2^63; one FP64 reciprocal per state.
+    // n_d 2^P = 2^63; one FP64 reciprocal per state.  It is formed only for
+    // states that have null steps (a real event that directly follows another
+    // needs none): FP64 is this GPU's slowest pipe.
     double nb_over = 0.0, nh_over = 0.0;
+    bool state_scored = false; // nb_over / nh_over belong to the current state (warp-uniform)
+    constexpr int PBITS = 63 - 2 * (LD == 8 ? 3 : LD == 16 ? 4 : LD == 32 ? 5 : 6);
+    // 2^-Q 2^P: a power of two, so the scaling below is exact
+    const double scaleP = GRAD ? rr.gscale * (double)(1ull << PBITS) : 0.0;
     auto grad_state = [&]() {
         if (GRAD) {
             const int64_t sb = warp_isum16((int64_t)n_c * rr.Gb), sh = warp_isum16((int64_t)n_c * rr.Gh);
             const uint64_t gap = (1ull << 63) - R;
             const double inv = gap ? __drcp_rn(__ull2double_rn(gap)) : 0.0; // 2^-P / (n_d - R)
-            constexpr int PBITS = 63 - 2 * (LD == 8 ? 3 : LD == 16 ? 4 : LD == 32 ? 5 : 6);
-            const double w = rr.gscale * inv * (double)(1ull << PBITS);
+            const double w = inv * scaleP;
             nb_over = (double)sb * w;
             nh_over = (double)sh * w;
+            state_scored = true;
         }
     };
-    grad_state();
 
     for (int base = 0; base < total; base += 32) {
         const Chunk ch = (base == 0) ? first : draw_chunk<EXPO>(key, d, np0, base, total, k, lane);
@@ -608,6 +613,7 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             const int jx = real ? __ffs(real) - 1 : chunk_end;
             if (GRAD && jx > pos) {
                 // (jx - pos) null steps in the current state
+                if (!state_scored) grad_state();
                 const double q = (double)(jx - pos);
                 cn.sb -= q * nb_over;
                 cn.sh -= q * nh_over;
@@ -699,7 +705,7 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             Wc = (uint64_t)n_c * Ac;
             Cinc = prefix16(Wc, lane);
             R = __shfl_sync(FULL_WARP, Cinc, 9);
-            grad_state();
+            state_scored = false;
         }
     }
 }
