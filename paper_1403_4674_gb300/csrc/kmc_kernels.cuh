@@ -553,6 +553,11 @@ __device__ __forceinline__ RateRegs load_rates(const uint8_t *rt, int lane)
 // are skipped with one ballot since the state does not change between real
 // events.  rr: the replica's rates, held by lanes 0..9.
 // ---------------------------------------------------------------------------
+// 0, 1, ..., 32 as FP64: the length of a run of null steps without an
+// integer-to-FP64 conversion (FP64 is this GPU's slowest pipe)
+__constant__ double kRunLength[33] = {0,  1,  2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, 16,
+                                      17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32};
+
 template <int LD, bool EXPO, bool GRAD>
 __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const RateRegs &rr, uint2 key,
                                            typename Geo<LD>::row_t hN, typename Geo<LD>::row_t hS,
@@ -619,7 +624,7 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             if (GRAD && jx > pos) {
                 // (jx - pos) null steps in the current state
                 if (!state_scored) grad_state();
-                const double q = (double)(jx - pos);
+                const double q = kRunLength[jx - pos];
                 cn.sb -= q * nb_over;
                 cn.sh -= q * nh_over;
             }
