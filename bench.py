@@ -225,21 +225,21 @@ def reference_arm(args):
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (summary in
 # profiles/run_kernel_ising1024x18_launches.md), and the SHA-256 of the kernel
 # source it was taken on; reported as null once the source has changed.
-TRAFFIC_BYTES_PER_LAUNCH = 5900544
-TRAFFIC_KERNEL_SHA256 = "b39ba3d388a38893f15cdb6fd56ac906dd582dd56ceedfb94a7ab6b4e6d710c6"
-# Warp instructions per uniformised step of the same workload and kernel
-# (ncu smsp__inst_executed.sum over one 200-schedule launch / its steps;
-# profiles/run_kernel_ising1024x18_small_full.md).  Includes the halo polls.
-INST_PER_STEP = 8933046445 / 51609600
+TRAFFIC_BYTES_PER_LAUNCH = 5918976 + 10240
+TRAFFIC_KERNEL_SHA256 = "823b1408fb2c0056ec0d0b082d15c810f72d65cfb1afb637569c1bc640426879"
+# Warp instructions per uniformised step of the same launch (ncu
+# smsp__inst_executed.sum of the full 1e4-schedule launch / its 2.58e9 steps;
+# same capture).  Includes the halo polls.
+INST_PER_STEP = 419567533889 / 2580480000
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 # The same for the variants, from `ncu --metrics smsp__inst_executed.sum` over
 # a full-size timed launch of `bench.py --only grad` / `--only batched`
 # (profiles/run_kernel_variants_instructions.md).  Batched: measured on the
 # single-context configuration of the same 512 replicas (L_d = 8, k = 16)
 # that the tuner chose under the profiler.
-INST_PER_STEP_GRAD = 297033429567 / 1310720000
-INST_PER_STEP_BATCHED = 318837499070 / 2636876800
-INST_PER_STEP_8192 = 160917810000 / 524288000  # one 2000-schedule launch of `bench.py --only lattice8192`
+INST_PER_STEP_GRAD = 275895852430 / 1310720000
+INST_PER_STEP_BATCHED = 319013065405 / 2636876800
+INST_PER_STEP_8192 = 144441571379 / 524288000  # one 2000-schedule launch of `bench.py --only lattice8192`
 
 
 def issue_roofline(inst_per_step: float, steps_per_s: float, peaks: dict, source: str):
