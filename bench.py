@@ -297,7 +297,7 @@ def variant_batched(args, peaks, flush, stream):
     import torch
     from paper_1403_4674_gb300 import autotune, workloads as wl
     w = wl.batched_replicas(512, master=512)
-    n_sched, obs_every = 200, 10
+    n_sched, obs_every = (args.schedules if args.schedules > 0 else 200), 10  # shorter only for profiling captures
     t0 = time.perf_counter()
     sm = torch.cuda.get_device_properties(0).multi_processor_count
     plans = [(0, 0, 16), (1, 4, 16), (1, 16, 16), (1, 16, 8), (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
