@@ -619,6 +619,9 @@ def main():
     launches = lat.kernel_launches() - launches0
     run_ms, run_n = lat.profile_read()
 
+    # the timed step's final state and records, for the bit-exactness check below
+    dev_spins = lat.spins.clone()
+    dev_obs = obs_buf.clone() if obs_buf is not None else None
     events_step = lat.events_per_schedule() * w.schedules
     bytes_step = schedule_bytes(lat.L, lat.L_d, lat.ks) * w.schedules
     dev_s = max_over_ranks(sum(step_ms) / 1000.0, dist, "cuda")
@@ -627,6 +630,7 @@ def main():
 
     # end-to-end through the public API with host buffers
     e2e = None
+    bit_exact = None
     if not args.no_e2e:
         lat.reset(reset_mode)
         lat.sync()
@@ -651,6 +655,18 @@ def main():
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         e2e = {"value": whole_job_rate(events_step, args.steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(d2h)}
+        # every step restarts from the same state and Philox position, so the
+        # end-to-end run must reproduce the device-timed run bit for bit
+        # (parity with the oracle in these launch configurations is checked by
+        # tests/test_gpu_bench_configs.py)
+        # (the clock column sums the domains' FP64 clock advances with atomics,
+        # in no fixed order: equal to 1e-12 relative, the oracle tolerance)
+        bit_exact = {"e2e_spins_equal_device_run": bool(torch.equal(host_out, dev_spins.cpu()))}
+        if host_obs is not None:
+            do = dev_obs.cpu()
+            bit_exact["e2e_records_e_m_em_equal_device_run"] = bool(torch.equal(host_obs[..., :3], do[..., :3]))
+            bit_exact["e2e_records_clock_rel_diff_max"] = float(
+                ((host_obs[..., 3] - do[..., 3]).abs() / do[..., 3].abs().clamp_min(1e-300)).max().item())
 
     traffic = TRAFFIC_BYTES_PER_LAUNCH if (TRAFFIC_KERNEL_SHA256 == kernel_source_sha256()
                                            and args.workload == "ising1024" and args.schedules == 0) else None
@@ -690,7 +706,7 @@ def main():
                                           ", one run-kernel launch per step",
                            "plan": list(plan), "launch": list(lat.launch()), "tune_s": tune_s,
                            "wall_s": wall},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "bit_exact": bit_exact,
                 "clocks": clk, "variants": variants}
         print(json.dumps(line), flush=True)
     lat.close()
