@@ -203,181 +203,254 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
     }
     __syncwarp();
 
-    auto visit = [&](int d, uint64_t np) {
-        int x0, y0;
-        domain_origin(d, x0, y0);
-        const u128 DM = DM0 << x0;
+    // The real events among the steps held by lanes [lo, hi): lane i holds
+    // step j = i - lo + jbase of the visit (target tgt, ~0 for no step).
+    // Null runs are skipped by one ballot; each real event selects its class
+    // and member, flips, and updates the class counts of the domains the five
+    // touched sites belong to.
+    auto events = [&](int d, uint64_t np, int x0, int y0, u128 DM, uint64_t tgt, int lo, int hi, int jbase) {
         uint32_t n_c = (lane < 10) ? (uint32_t)dcount[d * 10 + lane] : 0u;
         uint64_t Wc = (uint64_t)n_c * A;
         uint64_t Cinc = kmcdev::prefix16(Wc, lane);
         uint64_t R = __shfl_sync(FULL_WARP, Cinc, 9);
-        for (int base = 0; base < k; base += 32) {
-            const int s = base + lane;
-            uint64_t tgt = ~0ull, V = 1ull << 53;
-            if (s < k) {
-                const uint4 w = kmcdev::philox4x32_10(
-                    make_uint4((uint32_t)s, (uint32_t)d, (uint32_t)np, (uint32_t)(np >> 32) & 0xFFFFFFu), key);
-                tgt = __umul64hi(((uint64_t)w.y << 32) | w.x, M);
-                V = ((((uint64_t)w.w << 32) | w.z) >> 11) + 1ull;
+        int pos = lo;
+        while (true) {
+            const unsigned real = __ballot_sync(FULL_WARP, lane >= pos && lane < hi && tgt < R);
+            if (!real) break;
+            const int jx = __ffs(real) - 1;
+            const uint64_t t = __shfl_sync(FULL_WARP, tgt, jx);
+            const unsigned sel = __ballot_sync(FULL_WARP, lane < 10 && t < Cinc);
+            const int c = __ffs(sel) - 1;
+            uint32_t q = 0;
+            if (lane == c) q = (uint32_t)((t - (Cinc - Wc)) / A); // < n_c
+            const uint32_t jj = __shfl_sync(FULL_WARP, q, c);
+            // jj-th member of class c in row-major order
+            uint32_t cl = 0;
+            for (int tt = 0; tt < RPL; ++tt) {
+                const int yy = lane * RPL + tt;
+                if (yy >= Hd) break;
+                cl += (uint32_t)popc128(class_mask(row_planes(rows, y0 + yy, L, Lm, DM), c));
             }
-            const int chunk_end = min(32, k - base);
-            if (EXPO) {
-                // product of the chunk's variates (lanes past its end hold 1)
-                const int z = __clzll((long long)V);
-                uint64_t m = V << z;
-                int e = 10 - z;
-                for (int off = 1; off < chunk_end; off <<= 1) {
-                    const uint64_t m2 = __shfl_xor_sync(FULL_WARP, m, off);
-                    const int e2 = __shfl_xor_sync(FULL_WARP, e, off);
-                    kmcdev::mant_mul32(m, e, m2, e2);
-                }
-                kmcdev::mant_mul(clkM, clkE, __shfl_sync(FULL_WARP, m, 0),
-                                 (int64_t)__shfl_sync(FULL_WARP, e, 0));
+            uint32_t incl = cl;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t v = __shfl_up_sync(FULL_WARP, incl, off);
+                if (lane >= off) incl += v;
             }
-            steps += chunk_end;
-            int pos = 0;
-            while (true) {
-                const unsigned real = __ballot_sync(FULL_WARP, lane >= pos && tgt < R);
-                if (!real) break;
-                const int jx = __ffs(real) - 1;
-                const uint64_t t = __shfl_sync(FULL_WARP, tgt, jx);
-                const unsigned sel = __ballot_sync(FULL_WARP, lane < 10 && t < Cinc);
-                const int c = __ffs(sel) - 1;
-                uint32_t q = 0;
-                if (lane == c) q = (uint32_t)((t - (Cinc - Wc)) / A); // < n_c
-                const uint32_t jj = __shfl_sync(FULL_WARP, q, c);
-                // jj-th member of class c in row-major order
-                uint32_t cl = 0;
+            const uint32_t excl = incl - cl;
+            const unsigned win = __ballot_sync(FULL_WARP, jj >= excl && jj < incl);
+            if (!win) {
+                if (lane == 0) atomicOr(P.err, 2);
+                break;
+            }
+            const int wl = __ffs(win) - 1;
+            uint32_t yx = 0;
+            if (lane == wl) {
+                uint32_t rr = jj - excl;
                 for (int tt = 0; tt < RPL; ++tt) {
                     const int yy = lane * RPL + tt;
-                    if (yy >= Hd) break;
-                    cl += (uint32_t)popc128(class_mask(row_planes(rows, y0 + yy, L, Lm, DM), c));
-                }
-                uint32_t incl = cl;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t v = __shfl_up_sync(FULL_WARP, incl, off);
-                    if (lane >= off) incl += v;
-                }
-                const uint32_t excl = incl - cl;
-                const unsigned win = __ballot_sync(FULL_WARP, jj >= excl && jj < incl);
-                if (!win) {
-                    if (lane == 0) atomicOr(P.err, 2);
-                    break;
-                }
-                const int wl = __ffs(win) - 1;
-                uint32_t yx = 0;
-                if (lane == wl) {
-                    uint32_t rr = jj - excl;
-                    for (int tt = 0; tt < RPL; ++tt) {
-                        const int yy = lane * RPL + tt;
-                        const u128 mk = class_mask(row_planes(rows, y0 + yy, L, Lm, DM), c);
-                        const uint32_t pc = (uint32_t)popc128(mk);
-                        if (rr < pc) {
-                            yx = ((uint32_t)yy << 8) | (uint32_t)select128(mk, rr);
-                            break;
-                        }
-                        rr -= pc;
+                    const u128 mk = class_mask(row_planes(rows, y0 + yy, L, Lm, DM), c);
+                    const uint32_t pc = (uint32_t)popc128(mk);
+                    if (rr < pc) {
+                        yx = ((uint32_t)yy << 8) | (uint32_t)select128(mk, rr);
+                        break;
                     }
+                    rr -= pc;
                 }
-                yx = __shfl_sync(FULL_WARP, yx, wl);
-                const int yy = (int)(yx >> 8), x = (int)(yx & 255u);
-                // the flip changes the classes of the site and its four
-                // neighbours (lanes 0..4); their domains' counts follow
-                const int y = y0 + yy;
-                int sx = x, sy = y;
-                if (lane == 1) sx = (x == 0) ? L - 1 : x - 1;
-                if (lane == 2) sx = (x == L - 1) ? 0 : x + 1;
-                if (lane == 3) sy = (y == 0) ? L - 1 : y - 1;
-                if (lane == 4) sy = (y == L - 1) ? 0 : y + 1;
-                const bool mine = lane < 5 && !(L == 2 && (lane == 2 || lane == 4)); // L = 2: x-1 = x+1
-                const int sd = (P.kind == PART_STRIPES) ? sx / W : (sy / W) * P.Dx + sx / W;
-                __syncwarp();
-                const int old_c = mine ? site_class(rows, sx, sy, L) : 0;
-                __syncwarp();
-                if (lane == 0) rows[2 * y + (x >> 6)] ^= 1ull << (x & 63);
-                __syncwarp();
-                if (mine) {
-                    const int new_c = site_class(rows, sx, sy, L);
-                    if (new_c != old_c) {
-                        atomicAdd(&dcount[sd * 10 + old_c], -1);
-                        atomicAdd(&dcount[sd * 10 + new_c], 1);
-                    }
-                }
-                __syncwarp();
-                const uint64_t ev = (np << 32) | ((uint64_t)(base + jx) << 16) | (uint64_t)(yy * W + (x - x0));
-                H = (H ^ ev) * HASH_PRIME;
-                ++flips;
-                pos = jx + 1;
-                n_c = (lane < 10) ? (uint32_t)dcount[d * 10 + lane] : 0u;
-                Wc = (uint64_t)n_c * A;
-                Cinc = kmcdev::prefix16(Wc, lane);
-                R = __shfl_sync(FULL_WARP, Cinc, 9);
             }
+            yx = __shfl_sync(FULL_WARP, yx, wl);
+            const int yy = (int)(yx >> 8), x = (int)(yx & 255u);
+            // the flip changes the classes of the site and its four
+            // neighbours (lanes 0..4); their domains' counts follow
+            const int y = y0 + yy;
+            int sx = x, sy = y;
+            if (lane == 1) sx = (x == 0) ? L - 1 : x - 1;
+            if (lane == 2) sx = (x == L - 1) ? 0 : x + 1;
+            if (lane == 3) sy = (y == 0) ? L - 1 : y - 1;
+            if (lane == 4) sy = (y == L - 1) ? 0 : y + 1;
+            const bool mine = lane < 5 && !(L == 2 && (lane == 2 || lane == 4)); // L = 2: x-1 = x+1
+            const int sd = (P.kind == PART_STRIPES) ? sx / W : (sy / W) * P.Dx + sx / W;
+            __syncwarp();
+            const int old_c = mine ? site_class(rows, sx, sy, L) : 0;
+            __syncwarp();
+            if (lane == 0) rows[2 * y + (x >> 6)] ^= 1ull << (x & 63);
+            __syncwarp();
+            if (mine) {
+                const int new_c = site_class(rows, sx, sy, L);
+                if (new_c != old_c) {
+                    atomicAdd(&dcount[sd * 10 + old_c], -1);
+                    atomicAdd(&dcount[sd * 10 + new_c], 1);
+                }
+            }
+            __syncwarp();
+            const uint64_t ev = (np << 32) | ((uint64_t)(jx - lo + jbase) << 16) | (uint64_t)(yy * W + (x - x0));
+            H = (H ^ ev) * HASH_PRIME;
+            ++flips;
+            pos = jx + 1;
+            n_c = (lane < 10) ? (uint32_t)dcount[d * 10 + lane] : 0u;
+            Wc = (uint64_t)n_c * A;
+            Cinc = kmcdev::prefix16(Wc, lane);
+            R = __shfl_sync(FULL_WARP, Cinc, 9);
+        }
+    };
+
+    // Step draw of lane `lane` for step j of domain d in phase np:
+    // target = floor(X M / 2^64) (tgt) and the clock variate (V).
+    auto draw = [&](uint32_t j, uint32_t d, uint64_t np, uint64_t &tgt, uint64_t &V) {
+        const uint4 w = kmcdev::philox4x32_10(make_uint4(j, d, (uint32_t)np, (uint32_t)(np >> 32) & 0xFFFFFFu), key);
+        tgt = __umul64hi(((uint64_t)w.y << 32) | w.x, M);
+        V = ((((uint64_t)w.w << 32) | w.z) >> 11) + 1ull;
+    };
+    // Product of the variates of aligned groups of `span` lanes (a power of
+    // two; lanes without a step hold 1): lane 0 of each group receives it.
+    auto variate_product = [&](uint64_t V, int span, uint64_t &m, int &e) {
+        const int z = __clzll((long long)V);
+        m = V << z;
+        e = 10 - z;
+        for (int off = 1; off < span; off <<= 1) {
+            const uint64_t m2 = __shfl_xor_sync(FULL_WARP, m, off);
+            const int e2 = __shfl_xor_sync(FULL_WARP, e, off);
+            kmcdev::mant_mul32(m, e, m2, e2);
+        }
+    };
+
+    // One visit with its own draws, 32 steps at a time.
+    auto visit = [&](int d, uint64_t np) {
+        int x0, y0;
+        domain_origin(d, x0, y0);
+        const u128 DM = DM0 << x0;
+        for (int base = 0; base < k; base += 32) {
+            uint64_t tgt = ~0ull, V = 1ull << 53;
+            if (base + lane < k) draw((uint32_t)(base + lane), (uint32_t)d, np, tgt, V);
+            const int chunk_end = min(32, k - base);
+            if (EXPO) {
+                uint64_t m;
+                int e;
+                variate_product(V, 32, m, e);
+                kmcdev::mant_mul(clkM, clkE, __shfl_sync(FULL_WARP, m, 0), (int64_t)__shfl_sync(FULL_WARP, e, 0));
+            }
+            steps += chunk_end;
+            events(d, np, x0, y0, DM, tgt, 0, chunk_end, base);
         }
     };
 
     const bool perm = P.schedule == kmcdev::SCHED_RANDOM_PERM;
     const int nph = perm ? P.ND : (P.schedule == kmcdev::SCHED_PALINDROME ? 2 * P.ncol : P.ncol);
+    const int dpp = (perm || P.ND == 1) ? 1 : P.ND / P.ncol; // visits per phase
+    const int Vs = nph * dpp;                                // visits per schedule
     const double N = (double)L * (double)L;
     int64_t passes = 0;
-    for (int64_t nl = 0; nl < P.n_sched; ++nl) {
-        const uint64_t n = (uint64_t)(P.sched_begin + nl);
-        if (perm) {
-            // the paper's random order of all domains (Fisher-Yates over Philox)
-            __syncwarp();
-            if (lane == 0) {
-                for (int i = 0; i < P.ND; ++i) order[i] = (uint8_t)i;
-                for (int i = P.ND - 1; i >= 1; --i) {
-                    const uint4 w = kmcdev::philox4x32_10(
-                        make_uint4((uint32_t)i, 0u, (uint32_t)n,
-                                   ((uint32_t)(n >> 32) & 0xFFFFFFu) | (PART_TAG_PERM << 24)), key);
-                    const int jx = (int)__umul64hi(((uint64_t)w.y << 32) | w.x, (uint64_t)(i + 1));
-                    const uint8_t tmp = order[i];
-                    order[i] = order[jx];
-                    order[jx] = tmp;
-                }
-            }
-            __syncwarp();
+
+    // colour of phase p: 0 1 .. [.. 1 0]; the i-th domain of colour col in
+    // ascending order (blocks: by = col>>1 + 2 (i / (Dx/2)), bx = col&1 + 2 (i % (Dx/2)))
+    auto phase_colour = [&](int p) { return (p < P.ncol) ? p : (2 * P.ncol - 1 - p); };
+    auto domain_of_colour = [&](int col, int i) {
+        if (P.ND == 1) return 0;
+        if (P.kind == PART_STRIPES) return col + 2 * i;
+        const int half = P.Dx / 2;
+        return ((col >> 1) + 2 * (i / half)) * P.Dx + (col & 1) + 2 * (i % half);
+    };
+    // the paper's random order of all domains of schedule n (Fisher-Yates over Philox)
+    auto shuffle = [&](uint8_t *ord, uint64_t n) {
+        for (int i = 0; i < P.ND; ++i) ord[i] = (uint8_t)i;
+        for (int i = P.ND - 1; i >= 1; --i) {
+            const uint4 w = kmcdev::philox4x32_10(
+                make_uint4((uint32_t)i, 0u, (uint32_t)n, ((uint32_t)(n >> 32) & 0xFFFFFFu) | (PART_TAG_PERM << 24)),
+                key);
+            const int jx = (int)__umul64hi(((uint64_t)w.y << 32) | w.x, (uint64_t)(i + 1));
+            const uint8_t tmp = ord[i];
+            ord[i] = ord[jx];
+            ord[jx] = tmp;
         }
-        for (int p = 0; p < nph; ++p) {
-            const uint64_t np = n * PART_PHASE_SLOTS + (uint64_t)p;
+    };
+    auto pass_done = [&]() {
+        ++passes;
+        if (P.obs != nullptr && P.obs_every > 0 && passes % P.obs_every == 0) {
+            // bonds = 2 L^2 - 2 (unlike neighbour pairs), mag = 2 (up spins) - L^2
+            int unlike = 0, up = 0;
+            for (int y = lane; y < L; y += 32) {
+                const u128 c = row_ld(rows, y);
+                const u128 s = row_ld(rows, (y == L - 1) ? 0 : y + 1);
+                unlike += popc128((c ^ rot_e(c, L)) & Lm) + popc128(c ^ s);
+                up += popc128(c);
+            }
+            unlike = __reduce_add_sync(FULL_WARP, unlike);
+            up = __reduce_add_sync(FULL_WARP, up);
+            if (lane == 0) {
+                const int64_t bonds = 2ll * L * L - 2ll * unlike;
+                const int64_t mag = 2ll * up - (int64_t)L * L;
+                const double e = __ddiv_rn(__dsub_rn(__dmul_rn(-P.J, (double)bonds), __dmul_rn(hr, (double)mag)), N);
+                const double m = __ddiv_rn((double)mag, N);
+                double4_32a v;
+                v.x = e;
+                v.y = m;
+                v.z = __dmul_rn(e, m);
+                v.w = kmcdev::domain_time(EXPO, clkM, clkE, steps, __dmul_rn(N, P.nu));
+                const int64_t rec = passes / P.obs_every - 1;
+                reinterpret_cast<double4_32a *>(P.obs)[(size_t)rec * P.n_traj + tr] = v;
+            }
+        }
+    };
+
+    // Short visits: the steps of the visits of Sw consecutive schedules are
+    // drawn together, lane i holding step i % kp of visit i / kp (kp = k
+    // rounded up to a power of two), when Sw Vs kp <= 32; the schedules'
+    // domain orders are shuffled one per lane first.
+    int kp = 1;
+    while (kp < k) kp <<= 1;
+    const int Sw = (k >= 1 && kp * Vs <= 32) ? 32 / (kp * Vs) : 0;
+    if (Sw > 0) {
+        for (int64_t nl = 0; nl < P.n_sched; nl += Sw) {
+            const int sw = (int)((P.n_sched - nl < Sw) ? (P.n_sched - nl) : Sw);
+            const uint64_t n0 = (uint64_t)(P.sched_begin + nl);
             if (perm) {
-                visit(order[p], np);
-            } else {
-                const int col = (p < P.ncol) ? p : (2 * P.ncol - 1 - p);
-                for (int d = 0; d < P.ND; ++d) {
-                    const int dc = (P.ND == 1) ? 0
-                                   : (P.kind == PART_STRIPES) ? (d & 1)
-                                                              : (((d % P.Dx) & 1) | (((d / P.Dx) & 1) << 1));
-                    if (dc == col) visit(d, np);
+                __syncwarp();
+                if (lane < sw) shuffle(order + lane * P.ND, n0 + lane);
+                __syncwarp();
+            }
+            uint64_t tgt = ~0ull, V = 1ull << 53;
+            {
+                const int t = lane / kp, j = lane % kp;
+                if (t < sw * Vs && j < k) {
+                    const int sv = t / Vs, r = t % Vs;
+                    const int p = perm ? r : r / dpp;
+                    const int d = perm ? order[sv * P.ND + r] : domain_of_colour(phase_colour(p), r % dpp);
+                    draw((uint32_t)j, (uint32_t)d, (n0 + sv) * PART_PHASE_SLOTS + (uint64_t)p, tgt, V);
                 }
             }
-            ++passes;
-            if (P.obs != nullptr && P.obs_every > 0 && passes % P.obs_every == 0) {
-                // bonds = 2 L^2 - 2 (unlike neighbour pairs), mag = 2 (up spins) - L^2
-                int unlike = 0, up = 0;
-                for (int y = lane; y < L; y += 32) {
-                    const u128 c = row_ld(rows, y);
-                    const u128 s = row_ld(rows, (y == L - 1) ? 0 : y + 1);
-                    unlike += popc128((c ^ rot_e(c, L)) & Lm) + popc128(c ^ s);
-                    up += popc128(c);
+            uint64_t pm = 0;
+            int pe = 0;
+            if (EXPO) variate_product(V, kp, pm, pe);
+            int t = 0;
+            for (int sv = 0; sv < sw; ++sv) {
+                for (int p = 0; p < nph; ++p) {
+                    const uint64_t np = (n0 + sv) * PART_PHASE_SLOTS + (uint64_t)p;
+                    for (int i = 0; i < dpp; ++i, ++t) {
+                        const int d = perm ? order[sv * P.ND + p] : domain_of_colour(phase_colour(p), i);
+                        int x0, y0;
+                        domain_origin(d, x0, y0);
+                        if (EXPO)
+                            kmcdev::mant_mul(clkM, clkE, __shfl_sync(FULL_WARP, pm, t * kp),
+                                             (int64_t)__shfl_sync(FULL_WARP, pe, t * kp));
+                        steps += k;
+                        events(d, np, x0, y0, DM0 << x0, tgt, t * kp, t * kp + k, 0);
+                    }
+                    pass_done();
                 }
-                unlike = __reduce_add_sync(FULL_WARP, unlike);
-                up = __reduce_add_sync(FULL_WARP, up);
-                if (lane == 0) {
-                    const int64_t bonds = 2ll * L * L - 2ll * unlike;
-                    const int64_t mag = 2ll * up - (int64_t)L * L;
-                    const double e = __ddiv_rn(__dsub_rn(__dmul_rn(-P.J, (double)bonds), __dmul_rn(hr, (double)mag)), N);
-                    const double m = __ddiv_rn((double)mag, N);
-                    double4_32a v;
-                    v.x = e;
-                    v.y = m;
-                    v.z = __dmul_rn(e, m);
-                    v.w = kmcdev::domain_time(EXPO, clkM, clkE, steps, __dmul_rn(N, P.nu));
-                    const int64_t rec = passes / P.obs_every - 1;
-                    reinterpret_cast<double4_32a *>(P.obs)[(size_t)rec * P.n_traj + tr] = v;
-                }
+            }
+        }
+    } else {
+        for (int64_t nl = 0; nl < P.n_sched; ++nl) {
+            const uint64_t n = (uint64_t)(P.sched_begin + nl);
+            if (perm) {
+                __syncwarp();
+                if (lane == 0) shuffle(order, n);
+                __syncwarp();
+            }
+            for (int p = 0; p < nph; ++p) {
+                const uint64_t np = n * PART_PHASE_SLOTS + (uint64_t)p;
+                for (int i = 0; i < dpp; ++i) visit(perm ? order[p] : domain_of_colour(phase_colour(p), i), np);
+                pass_done();
             }
         }
     }
