@@ -67,7 +67,13 @@ enum { KMC_OBS_SCHEDULE = 0, KMC_OBS_PASS = 1 };
  *   L[r]        host array: side of replica r; L[r] must be a multiple of
  *               2*L_d (an even number of domains per side keeps the 2x2
  *               colouring valid under periodic wrap).
- *   L_d         domain side: 8, 16, 32 or 64 (n_d = L_d^2 sites).
+ *   L_d         domain side: 8, 16, 32 or 64 (n_d = L_d^2 sites), or 0:
+ *               the library picks the largest side that divides every
+ *               lattice into an even number of domains per side and still
+ *               gives each colour phase 20 visits per SM, else the smallest
+ *               valid side (kmc_domain_side reports it; a measured choice
+ *               over sides, steps per visit and launch plans is the Python
+ *               autotuner's).
  *   k_steps     uniformised steps per domain visit (the paper's N_I),
  *               1..65535.
  *   init        KMC_INIT_RANDOM (iid +-1 from Philox4x32-10 keyed by the
@@ -327,6 +333,9 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
 
 /* Number of kernels this context launched so far (all kinds). */
 int64_t kmc_kernel_launches(const kmc_ctx *ctx);
+
+/* The context's domain side L_d (the chosen one when created with 0). */
+int32_t kmc_domain_side(const kmc_ctx *ctx);
 
 const char *kmc_last_error(const kmc_ctx *ctx);
 void kmc_destroy(kmc_ctx *ctx);

@@ -193,6 +193,10 @@ def kmc_kernel_launches(ctx) -> int:
     return load().kmc_kernel_launches(ctx)
 
 
+def kmc_domain_side(ctx) -> int:
+    return load().kmc_domain_side(ctx)
+
+
 def kmc_destroy(ctx):
     if ctx is not None and ctx.value:
         load().kmc_destroy(ctx)
@@ -219,8 +223,9 @@ class Lattice:
             spins = torch.empty(total, dtype=torch.int8, device=dev)
         self.spins = spins
         self.offsets = np.concatenate([[0], np.cumsum([x * x for x in self.L])]).astype(np.int64)
-        self.dom_offsets = np.concatenate([[0], np.cumsum([(x // self.L_d) ** 2 for x in self.L])]).astype(np.int64)
         self.ctx = kmc_create_lattice(self.L, self.L_d, self.k, init, self.seeds, self.spins, stream)
+        self.L_d = int(load().kmc_domain_side(self.ctx))  # the library's choice when L_d = 0
+        self.dom_offsets = np.concatenate([[0], np.cumsum([(x // self.L_d) ** 2 for x in self.L])]).astype(np.int64)
         self.grad_enabled = False
         self.obs_unit = KMC_OBS_SCHEDULE
 

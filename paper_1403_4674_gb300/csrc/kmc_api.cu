@@ -847,6 +847,8 @@ const char *kmc_last_error(const kmc_ctx *ctx) { return ctx ? ctx->err.c_str() :
 
 int64_t kmc_kernel_launches(const kmc_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+int32_t kmc_domain_side(const kmc_ctx *ctx) { return ctx ? ctx->LD : 0; }
+
 kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *L, int32_t L_d,
                               int32_t k_steps, int32_t init, const uint64_t *seeds, int8_t *spins_dev,
                               void *stream)
@@ -863,7 +865,33 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
     };
     if (n_replicas < 1 || !L || !seeds || !spins_dev)
         return bail(fail(c, KMC_EINVAL, "n_replicas >= 1 and non-null L, seeds, spins_dev required"));
-    if (ld_index(L_d) < 0) return bail(fail(c, KMC_EINVAL, "L_d must be 8, 16, 32 or 64 (got %d)", L_d));
+    if (L_d == 0) {
+        // automatic domain side: the largest of 64, 32, 16, 8 that divides every
+        // lattice into an even number of domains per side and still gives each
+        // colour phase 20 visits per SM (one per warp of two 10-warp CTAs);
+        // the smallest valid side if none does.  The measured choice over
+        // sides, steps per visit and plans is the autotuner's (autotune.py).
+        int sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(c, KMC_ECUDA, "device attributes for the automatic domain side"));
+        }
+        int smallest = 0;
+        for (int cand = 64; cand >= 8; cand /= 2) {
+            bool ok = true;
+            uint64_t doms = 0;
+            for (int r = 0; r < n_replicas && ok; ++r) {
+                ok = L[r] >= 2 * cand && L[r] % (2 * cand) == 0;
+                doms += ok ? (uint64_t)(L[r] / cand) * (uint64_t)(L[r] / cand) : 0;
+            }
+            if (!ok) continue;
+            smallest = cand;
+            if (L_d == 0 && doms / 4 >= (uint64_t)sms * 20) L_d = cand;
+        }
+        if (L_d == 0) L_d = smallest;
+        if (L_d == 0) return bail(fail(c, KMC_EINVAL, "no domain side of 8, 16, 32 or 64 fits every lattice"));
+    }
+    if (ld_index(L_d) < 0) return bail(fail(c, KMC_EINVAL, "L_d must be 8, 16, 32 or 64, or 0 (got %d)", L_d));
     if (k_steps < 1 || k_steps > 65535) return bail(fail(c, KMC_EINVAL, "k_steps must be in 1..65535"));
     if (init < KMC_INIT_RANDOM || init > KMC_INIT_KEEP) return bail(fail(c, KMC_EINVAL, "bad init mode"));
     if (((uintptr_t)spins_dev) % 8 != 0) return bail(fail(c, KMC_EINVAL, "spins_dev must be 8-byte aligned"));

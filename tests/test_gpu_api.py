@@ -210,3 +210,43 @@ def test_enable_grad_replans_when_score_kernels_do_not_fit():
         ref.run(3)
         assert np.array_equal(lat.replica_spins(r).cpu().numpy(), ref.spins)
     lat.close()
+
+
+def test_automatic_domain_side():
+    """L_d = 0: the largest side that divides every lattice into an even
+    number of domains per side and gives each colour phase 20 visits per SM,
+    else the smallest valid side; the run matches the oracle at that side."""
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def chosen(L):
+        lat = kmc.Lattice(L, 0, 1, list(range(1, len(L) + 1)))
+        side = lat.L_d
+        assert side == kmc.kmc_domain_side(lat.ctx)
+        lat.close()
+        return side
+
+    def expect(L):
+        valid = [c for c in (64, 32, 16, 8) if all(x >= 2 * c and x % (2 * c) == 0 for x in L)]
+        for c in valid:
+            if sum((x // c) ** 2 for x in L) // 4 >= 20 * sm:
+                return c
+        return valid[-1]
+
+    for L in ([1024] * 18, [8192], wl.batched_replicas(512, master=512).L, [64], [96, 160]):
+        assert chosen(L) == expect(L), L
+    # a run at the chosen side is the oracle's run at that side
+    L, seeds, beta, h = [96, 160], [5, 6], [0.45, 0.5], [0.0, 0.1]
+    lat = kmc.Lattice(L, 0, 3, seeds)
+    lat.set_rates(beta, h)
+    obs = lat.run(4, obs_every=2).cpu().numpy()
+    side = lat.L_d
+    assert side == expect(L)
+    for r in range(2):
+        ref = orc.Replica(L=L[r], Ld=side, k=3, seed=seeds[r], beta=beta[r], h=h[r])
+        robs = ref.run(4, obs_every=2)
+        assert np.array_equal(lat.replica_spins(r).cpu().numpy(), ref.spins)
+        assert np.array_equal(obs[:, r, :3], robs[:, :3])
+    lat.close()
