@@ -199,6 +199,18 @@ kmc_status kmc_observables(kmc_ctx *ctx, double *E_per_site, double *m, double *
 kmc_status kmc_grad(kmc_ctx *ctx, double *score_dev, int32_t reset);
 
 /*
+ * kmc_grad_nu -- score of the path's clock with respect to the rate
+ * prefactor nu, per replica: score_dev[r] (device, caller-owned) =
+ * sum over its domains of (steps_d - Lambda_d t_d) / nu.  The uniformised
+ * jump chain does not depend on nu (it only scales time, Sec. 2.1); the
+ * exponential waiting time of each step has log density
+ * ln Lambda_d - Lambda_d tau with Lambda_d = n_d nu, whose nu-derivative this
+ * sums.  Covers the steps since the last kmc_reset (or creation); every run
+ * in between must use KMC_TIME_EXPONENTIAL, else KMC_EINVAL.  Synchronising.
+ */
+kmc_status kmc_grad_nu(kmc_ctx *ctx, double *score_dev);
+
+/*
  * kmc_lr_estimate -- likelihood-ratio gradient of E[A] over the replicas:
  * grad_dev[j] = (1/R) sum_r (A_r - mean A) S_r,j for j = {beta, h}, where
  * A_dev[r] (device, n_replicas doubles) is an observable of replica r at the

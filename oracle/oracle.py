@@ -321,6 +321,18 @@ class Replica:
                                                int(self.steps[d]), nd, self.nu)
                          for d in range(self.n_domains)])
 
+    def score_nu(self) -> float:
+        """d log p / d nu of the exponential clock variates drawn so far (Sec.
+        2.1): each uniformised step of domain d waits Exp(n_d nu), log density
+        ln(n_d nu) - n_d nu tau, derivative 1/nu - n_d tau; summed over the
+        steps of every domain this is sum_d (steps_d - esum_d) / nu, esum_d
+        being the domain's sum of -ln v = n_d nu tau.  Valid for runs in
+        TIME_EXPONENTIAL only."""
+        total = 0.0
+        for d in range(self.n_domains):
+            total += (float(self.steps[d]) - float(self.esum[d])) / self.nu
+        return total
+
     def observables(self, time_mode: int = TIME_EXPONENTIAL):
         """(e, m, e*m, T) at the current state (Sec. 2.3 endpoint)."""
         b, m = energy_mag(self.spins)

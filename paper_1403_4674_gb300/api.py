@@ -114,6 +114,12 @@ def kmc_grad(ctx, score_dev: torch.Tensor, reset: int = 0):
     _check(ctx, load().kmc_grad(ctx, ctypes.c_void_p(score_dev.data_ptr()), reset))
 
 
+def kmc_grad_nu(ctx, score_dev: torch.Tensor):
+    if score_dev.dtype != torch.float64 or not score_dev.is_cuda:
+        raise KmcError(-1, "score_dev must be a float64 CUDA tensor")
+    _check(ctx, load().kmc_grad_nu(ctx, ctypes.c_void_p(score_dev.data_ptr())))
+
+
 def kmc_lr_estimate(ctx, A_dev: torch.Tensor, grad_dev: torch.Tensor, stream=None):
     if A_dev.dtype != torch.float64 or grad_dev.dtype != torch.float64 or not A_dev.is_cuda:
         raise KmcError(-1, "A_dev and grad_dev must be float64 CUDA tensors")
@@ -284,6 +290,12 @@ class Lattice:
     def score(self, reset: bool = False) -> torch.Tensor:
         out = torch.empty((self.n_replicas, 2), dtype=torch.float64, device=self.spins.device)
         kmc_grad(self.ctx, out, int(reset))
+        return out
+
+    def score_nu(self) -> torch.Tensor:
+        """d log P / d nu of the exponential clocks since the last reset, per replica."""
+        out = torch.empty(self.n_replicas, dtype=torch.float64, device=self.spins.device)
+        kmc_grad_nu(self.ctx, out)
         return out
 
     def lr_estimate(self, A: torch.Tensor) -> torch.Tensor:

@@ -81,6 +81,7 @@ struct kmc_ctx {
     int64_t sched_done = 0;
     int64_t visits_done = 0;
     int last_time_mode = KMC_TIME_EXPONENTIAL;
+    bool clocks_exponential = true; // every run since the last reset drew exponential clock variates
     double dtau = 0.0;          // fixed-time visits (KMC_TIME_HORIZON): domain time per visit
     int hkmax = 0;
     uint64_t *d_htab = nullptr; // Poisson CDF thresholds, HORIZON_MAX_STEPS words
@@ -839,6 +840,27 @@ struct Carver {
 
 } // namespace
 
+// Score of the exponential clock variates with respect to the rate
+// prefactor nu (Sec. 2.1: a domain's waiting time per uniformised step is
+// Exp(Lambda_d), Lambda_d = n_d nu, with log density ln Lambda_d - Lambda_d tau,
+// so d/dnu = 1/nu - n_d tau): per domain (steps_d - Lambda_d t_d) / nu with
+// Lambda_d t_d = -ln(product of its variates); one thread per replica sums
+// its domains in order.
+__global__ void score_nu_kernel(const uint64_t *dctr, const uint32_t *rep_dom_off, int n_rep, double nu,
+                                double *score)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rep) return;
+    double s = 0.0;
+    for (uint32_t g = rep_dom_off[r]; g < rep_dom_off[r + 1]; ++g) {
+        const uint64_t *ctr = dctr + (uint64_t)g * DCTR_WORDS;
+        // Lambda_d t_d = -ln(M 2^-63) - E ln 2
+        const double lam_t = domain_time(true, ctr[DCTR_CLKM], (int64_t)ctr[DCTR_CLKE], 0, 1.0);
+        s += (double)(int64_t)ctr[DCTR_STEPS] - lam_t;
+    }
+    score[r] = s / nu;
+}
+
 extern "C" {
 
 int32_t kmc_version(void) { return 10100; }
@@ -1005,6 +1027,7 @@ kmc_status kmc_reset(kmc_ctx *c, int32_t init, void *stream)
     if ((s = launch_reset_counters(c, c->stream)) != KMC_OK) return s;
     c->sched_done = 0;
     c->visits_done = 0;
+    c->clocks_exponential = true;
     return KMC_OK;
 }
 
@@ -1308,6 +1331,7 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     c->sched_done += n_schedules;
     c->visits_done += n_schedules * (schedule == KMC_SCHEDULE_PALINDROME ? 2 : 1);
     c->last_time_mode = time_mode;
+    if (time_mode != KMC_TIME_EXPONENTIAL) c->clocks_exponential = false;
     return KMC_OK;
 }
 
@@ -1364,6 +1388,20 @@ kmc_status kmc_domain_state(kmc_ctx *c, uint64_t *hash, int64_t *flips, double *
     if (!c) return KMC_EINVAL;
     if (refuse_capture(c, "kmc_domain_state") != KMC_OK) return KMC_EINVAL;
     return domain_state(c, hash, flips, t, nullptr);
+}
+
+kmc_status kmc_grad_nu(kmc_ctx *c, double *score_dev)
+{
+    if (!c) return KMC_EINVAL;
+    if (refuse_capture(c, "kmc_grad_nu") != KMC_OK) return KMC_EINVAL;
+    if (!score_dev) return fail(c, KMC_EINVAL, "score_dev required");
+    if (!c->clocks_exponential)
+        return fail(c, KMC_EINVAL, "the rate-prefactor score needs exponential clocks in every run since the last reset");
+    score_nu_kernel<<<grid_for(c->n_rep, 128), 128, 0, c->stream>>>(c->d_dctr, c->d_dom_off, c->n_rep, c->nu,
+                                                                       score_dev);
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    return sync_ctx(c);
 }
 
 kmc_status kmc_grad(kmc_ctx *c, double *score_dev, int32_t reset)

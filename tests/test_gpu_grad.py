@@ -122,3 +122,26 @@ def test_autograd_function_backward():
     m = expectation(lat, beta.detach().requires_grad_(), h.detach().requires_grad_(), 4, "m")
     assert torch.isfinite(m)
     lat.close()
+
+
+def test_nu_score_parity_and_lr():
+    """The rate-prefactor clock score per replica against the oracle's, and
+    refused after a run with the expected clock."""
+    import paper_1403_4674_gb300 as kmc
+    L, seeds, beta, h, nu = [64, 96], [31, 32], [0.45, 0.3], [0.0, 0.1], 1.7
+    lat = kmc.Lattice(L, 16, 5, seeds)
+    lat.set_rates(beta, h, nu=nu)
+    lat.run(7)
+    s = lat.score_nu().cpu().numpy()
+    for r in range(2):
+        ref = orc.Replica(L=L[r], Ld=16, k=5, seed=seeds[r], beta=beta[r], h=h[r], nu=nu)
+        ref.run(7)
+        steps = float(ref.steps.sum())
+        assert abs(s[r] - ref.score_nu()) <= 1e-12 * steps / nu, (s[r], ref.score_nu())
+    lat.run(1, time_mode=kmc.KMC_TIME_EXPECTED)
+    with pytest.raises(kmc.KmcError):
+        lat.score_nu()
+    lat.reset(kmc.KMC_INIT_RANDOM)
+    lat.run(1)
+    lat.score_nu()  # a reset starts a new exponential-only segment
+    lat.close()

@@ -113,3 +113,28 @@ def test_derivative_enumeration_matches_finite_difference():
             - Enumerator(L, Ld, k, beta=beta, h=h - d, quantised=False).schedule(PAL, p0)) / (2 * d)
     assert np.max(np.abs(dpb - fd_b)) < 1e-7
     assert np.max(np.abs(dph - fd_h)) < 1e-7
+
+
+def test_nu_score_of_the_exponential_clock():
+    """Score of the clock with respect to the rate prefactor nu (Sec. 2.1):
+    zero mean, variance steps/nu^2 (each step contributes (1 - E_i)/nu with
+    E_i ~ Exp(1)), and E[T S_nu] = dE[T]/dnu = -E[T]/nu, T the replica clock
+    (T scales as 1/nu path by path)."""
+    import math
+    nu, n = 2.5, 600
+    S, T = [], []
+    steps = None
+    for r in range(n):
+        rep = orc.Replica(L=16, Ld=4, k=3, seed=9000 + r, beta=0.4, h=0.05, nu=nu)
+        obs = rep.run(4, obs_every=4)
+        S.append(rep.score_nu())
+        T.append(obs[-1, 3])
+        steps = int(rep.steps.sum())
+    S, T = np.array(S), np.array(T)
+    sd = math.sqrt(steps) / nu
+    assert abs(S.mean()) < 5 * sd / math.sqrt(n)
+    assert S.var(ddof=1) == pytest.approx(steps / nu ** 2, rel=5 * math.sqrt(2 / n))
+    lr = np.mean((T - T.mean()) * S)
+    exact = -T.mean() / nu
+    se = np.std((T - T.mean()) * S, ddof=1) / math.sqrt(n)
+    assert abs(lr - exact) < 5 * se, (lr, exact, se)
