@@ -138,3 +138,29 @@ def test_nu_score_of_the_exponential_clock():
     exact = -T.mean() / nu
     se = np.std((T - T.mean()) * S, ddof=1) / math.sqrt(n)
     assert abs(lr - exact) < 5 * se, (lr, exact, se)
+
+
+@pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
+def test_long_time_derivative_is_the_equilibrium_closed_form(law):
+    """Iterating the exact forward-mode derivative of the palindromic schedule
+    chain converges to the derivative of the Boltzmann distribution: for
+    pi ~ exp(-beta H), H = -J sum s s - h M, d<A>/dbeta = -Cov(A, H) and
+    d<A>/dh = beta Cov(A, M) (the schedule keeps pi exactly, Sec. 2.2)."""
+    L, Ld, k, beta, h = 2, 1, 3, 0.45, 0.2
+    E = Enumerator(L, Ld, k, beta=beta, h=h, law=law, quantised=False)
+    E.set_score_table(orc.score_table(1.0, beta, h, law))
+    H, mag = lattice_energy_all_states(L, 1.0, h)
+    H, mag = H.astype(float), mag.astype(float)
+    p = np.zeros(E.S)
+    p[0] = 1.0
+    dps = (np.zeros(E.S), np.zeros(E.S))
+    for _ in range(400):
+        p, dps = E.schedule_deriv(PAL, p, dps)
+    w = np.exp(-beta * (H - H.min()))
+    pi = w / w.sum()
+    assert np.max(np.abs(p - pi)) < 1e-12
+    for A in (H, mag, H * mag):
+        cov_H = pi @ (A * H) - (pi @ A) * (pi @ H)
+        cov_M = pi @ (A * mag) - (pi @ A) * (pi @ mag)
+        assert float(A @ dps[0]) == pytest.approx(-cov_H, rel=1e-9, abs=1e-12)
+        assert float(A @ dps[1]) == pytest.approx(beta * cov_M, rel=1e-9, abs=1e-12)
