@@ -21,13 +21,13 @@ def _sm():
     return torch.cuda.get_device_properties(0).multi_processor_count
 
 
-def _check(spins_of, obs, idx, n, L, Ld, ks, seeds, beta, h, inits, scores=None):
+def _check(spins_of, obs, idx, n, L, Ld, ks, seeds, beta, h, inits, scores=None, obs_every=1):
     """spins_of(r) -> device spins of replica r; obs[rec, r, :]; idx: replicas to check."""
     for r in idx:
         ref = orc.Replica(L=L[r], Ld=Ld, k=ks[r], seed=seeds[r], beta=beta[r], h=h[r], init=inits[r])
         if scores is not None:
             ref.enable_score()
-        robs = ref.run(n, obs_every=1)
+        robs = ref.run(n, obs_every=obs_every)
         assert np.array_equal(spins_of(r), ref.spins), "replica %d: spins differ" % r
         assert np.array_equal(obs[:, r, :3], robs[:, :3]), "replica %d: e, m, e*m differ" % r
         np.testing.assert_allclose(obs[:, r, 3], robs[:, 3], rtol=1e-12, atol=0)
@@ -121,4 +121,28 @@ def test_lattice8192_one_schedule():
     lat.sync()
     _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [0], 1, w.L, w.L_d, [w.k], w.seeds, w.beta, w.h,
            [0])
+    lat.close()
+
+
+def test_ising1024_full_timed_length_sampled_replica():
+    """The benchmark's timed launch itself: all 18 replicas of 1024^2 in one
+    context on the 2 x 10-warp grid for the full 1e4 schedules with records
+    every 10; replica 2 (k = 1, T = 3.0, random start: the most real events
+    per step) checked against the oracle over the whole run (about a minute
+    of CPU)."""
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
+    w = wl.ising1024_all()
+    n = len(w.L)
+    ks = [w.k_of(r) for r in range(n)]
+    inits = [w.init_of(r) for r in range(n)]
+    lat = kmc.Lattice(w.L, w.L_d, ks[0], w.seeds, init=inits[0])
+    lat.set_replica_params(k=ks, init=inits)
+    lat.reset(kmc.KMC_INIT_PER_REPLICA)
+    lat.set_rates(w.beta, w.h)
+    lat.set_launch(2, 2 * _sm(), 10)
+    obs = lat.run(w.schedules, obs_every=w.obs_every).cpu().numpy()
+    lat.sync()
+    _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [2], w.schedules, w.L, w.L_d, ks, w.seeds, w.beta,
+           w.h, inits, obs_every=w.obs_every)
     lat.close()
