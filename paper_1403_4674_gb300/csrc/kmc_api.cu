@@ -631,11 +631,15 @@ void build_gfix(const double *a, const double *gb, const double *gh, int log2nd,
 {
     double mx = 0.0;
     for (int c = 0; c < 10; ++c) mx = std::max(mx, std::max(std::fabs(a[c] * gb[c]), std::fabs(a[c] * gh[c])));
-    int Q = 40;
+    // Q as large as the int64 sums allow: sum_c n_c |a_c dlog a_c| 2^Q <
+    // n_d 2^e 2^Q = 2^58.  (The null-step score sums about one term per state
+    // over a run, so the products' rounding, 2^-Q-1 each, is what limits the
+    // score's agreement with exact arithmetic over long runs.)
+    int Q = 62;
     if (mx > 0.0) {
         int e = 0;
         std::frexp(mx, &e); // mx < 2^e
-        Q = std::max(0, std::min(40, 58 - log2nd - e));
+        Q = std::max(0, std::min(62, 58 - log2nd - e));
     }
     for (int c = 0; c < 10; ++c) {
         out[c] = (int64_t)std::llround(std::ldexp(a[c] * gb[c], Q));

@@ -146,3 +146,22 @@ def test_ising1024_full_timed_length_sampled_replica():
     _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [2], w.schedules, w.L, w.L_d, ks, w.seeds, w.beta,
            w.h, inits, obs_every=w.obs_every)
     lat.close()
+
+
+def test_grad_full_timed_length_sampled_replica():
+    """The gradient benchmark's timed launch at its full length: 256 x 256^2
+    with scores on the 16-warp grid, 5000 schedules, one record at the end;
+    replica 0's spins, record and score checked against the oracle."""
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
+    w = wl.grad_replicas(256, seed_master=256, k=8)
+    n = len(w.L)
+    lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
+    lat.set_rates(w.beta, w.h)
+    lat.enable_grad(True)
+    lat.set_launch(2, _sm(), 16)
+    obs = lat.run(w.schedules, obs_every=w.schedules).cpu().numpy()
+    scores = lat.score().cpu().numpy()
+    _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [0], w.schedules, w.L, w.L_d, [w.k] * n, w.seeds,
+           w.beta, w.h, [0] * n, scores=scores, obs_every=w.schedules)
+    lat.close()
