@@ -133,3 +133,29 @@ def test_gpu_final_distribution_matches_enumeration():
     chi2 = (((cnt[keep] - pe[keep] * n) ** 2) / (pe[keep] * n)).sum()
     assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-5
     g.close()
+
+
+@pytest.mark.parametrize("L,kind,ND,k,steps_per_traj,n_traj", [(100, S, 2, 1, 160000, 3), (12, S, 4, 5, 16000, 20),
+                                                               (100, B, 16, 10, 160000, 2)])
+def test_partition_full_bench_length(L, kind, ND, k, steps_per_traj, n_traj):
+    """Settings of the 2D benchmark at their full per-step length (S steps per
+    trajectory, the random domain order, 64 energy records), from the all-up
+    start, every trajectory against the oracle."""
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    seeds = [1000 + 7 * i for i in range(n_traj)]
+    g = kmc.Partitioned(L, kind, ND, k, seeds)
+    g.set_rates([1 / 2.4] * n_traj, law=kmc.KMC_RATE_BARKER)
+    n_sched = steps_per_traj // (ND * k)
+    obs_every = max(1, n_sched * ND // 64)
+    obs = g.run(n_sched, schedule=kmc.KMC_SCHEDULE_RANDOM_PERM, obs_every=obs_every).cpu().numpy()
+    torch.cuda.synchronize()
+    hashes, flips, steps, T = g.state()
+    spins = g.spins.cpu().numpy()
+    for i in range(n_traj):
+        r = orc.Partitioned(L=L, kind=kind, ND=ND, k=k, seed=seeds[i], beta=1 / 2.4)
+        ro = r.run(n_sched, schedule=orc.SCHED_RANDOM_PERM, obs_every=obs_every)
+        assert np.array_equal(spins[i], r.spins) and int(hashes[i]) == r.hash and int(flips[i]) == r.flips
+        assert np.array_equal(obs[:, i, :3], ro[:, :3])
+        np.testing.assert_allclose(obs[:, i, 3], ro[:, 3], rtol=1e-12, atol=0)
+    g.close()
