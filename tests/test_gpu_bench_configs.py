@@ -165,3 +165,29 @@ def test_grad_full_timed_length_sampled_replica():
     _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [0], w.schedules, w.L, w.L_d, [w.k] * n, w.seeds,
            w.beta, w.h, [0] * n, scores=scores, obs_every=w.schedules)
     lat.close()
+
+
+def test_batched_512_full_step_sample():
+    """The batched benchmark's timed step itself: the tuned groups, one CUDA
+    graph of reset + 200 schedules with records every 10, replayed; the
+    largest, the smallest and one more replica of every group against the
+    oracle over the whole step."""
+    import torch
+    from paper_1403_4674_gb300 import autotune, workloads as wl
+    w = wl.batched_replicas(512, master=512)
+    sm = _sm()
+    plans = [(0, 0, 16), (1, 4, 16), (1, 16, 16), (1, 16, 8), (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
+    choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
+                                  Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=20)
+    batch = autotune.Batch(w.L, w.beta, w.h, w.seeds, choices)
+    graph = batch.capture(200, 10, reset=0)
+    graph.replay()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    for ch, lat, o in zip(choices, batch.lattices, batch.outs):
+        Lg = [w.L[i] for i in ch.replicas]
+        sub = {int(np.argmax(Lg)), int(np.argmin(Lg)), int(rng.integers(len(Lg)))}
+        _check(lambda j: lat.replica_spins(j).cpu().numpy(), o.cpu().numpy(), sorted(sub), 200, Lg, ch.L_d,
+               [ch.k] * len(Lg), [w.seeds[i] for i in ch.replicas], [w.beta[i] for i in ch.replicas],
+               [w.h[i] for i in ch.replicas], [0] * len(Lg), obs_every=10)
+    batch.close()
