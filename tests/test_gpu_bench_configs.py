@@ -191,3 +191,36 @@ def test_batched_512_full_step_sample():
                [ch.k] * len(Lg), [w.seeds[i] for i in ch.replicas], [w.beta[i] for i in ch.replicas],
                [w.h[i] for i in ch.replicas], [0] * len(Lg), obs_every=10)
     batch.close()
+
+
+def test_lattice8192_full_length_properties():
+    """The 8192^2 benchmark launch at its full 2000 schedules (too long for
+    the oracle), checked by properties that hold at any size: the records,
+    built on the device from per-visit changes, equal e and m recomputed from
+    the final spins on the host; every domain made exactly 2 k steps per
+    schedule; two runs of 1000 schedules reproduce one of 2000 bit for bit."""
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
+    w = wl.lattice_8192()
+    L, n = w.L[0], w.schedules
+    lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
+    lat.set_rates(w.beta, w.h)
+    lat.set_launch(2, _sm(), 16)
+    obs = lat.run(n, obs_every=n // 2).cpu().numpy()
+    s = lat.spins.view(L, L).to(torch.int32)
+    bonds = int((s * (torch.roll(s, -1, 1) + torch.roll(s, -1, 0))).sum().item())
+    mag = int(s.sum().item())
+    N = float(L) * float(L)
+    e = (-w.J * float(bonds) - w.h[0] * float(mag)) / N
+    m = float(mag) / N
+    assert obs[-1, 0, 0] == e and obs[-1, 0, 1] == m and obs[-1, 0, 2] == e * m
+    ob = lat.observables()
+    assert int(ob["steps"][0]) == (L // w.L_d) ** 2 * 2 * w.k * n
+    final = lat.spins.clone()
+    lat.reset(kmc.KMC_INIT_RANDOM)
+    lat.run(n // 2)
+    lat.run(n // 2)
+    torch.cuda.synchronize()
+    assert torch.equal(final, lat.spins)
+    lat.close()
