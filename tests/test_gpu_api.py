@@ -250,3 +250,26 @@ def test_automatic_domain_side():
         assert np.array_equal(lat.replica_spins(r).cpu().numpy(), ref.spins)
         assert np.array_equal(obs[:, r, :3], robs[:, :3])
     lat.close()
+
+
+def test_lattice_beyond_on_chip_capacity_is_refused():
+    """16384^2 (268M sites) at L_d = 64: the bit state plus per-domain slots
+    exceed what one GPU's shared memory holds in one launch, and one replica
+    cannot be split over cluster waves, so planning refuses it with
+    KMC_EINVAL (no partial run); the context is still destroyed cleanly and a
+    lattice that fits runs afterwards."""
+    import torch
+    kmc = _kmc()
+    with pytest.raises(kmc.KmcError) as ei:
+        lat = kmc.Lattice([16384], 64, 8, [1])
+        try:
+            lat.set_rates([0.44], [0.0])
+            lat.run(1)
+        finally:
+            lat.close()
+    assert ei.value.status == -1
+    torch.cuda.empty_cache()
+    ok = kmc.Lattice([8192], 64, 8, [1])
+    ok.set_rates([0.44], [0.0])
+    ok.run(1)
+    ok.close()

@@ -71,6 +71,7 @@ CASES = [
     (2, S, 2, 3, PAL, 13),
     (33, S, 1, 4, PAL, 9),       # odd L
     (96, S, 32, 6, PERM, 9),     # 3-wide stripes, 32 domains
+    (128, S, 64, 2, PERM, 3),    # the most domains: 64 stripes of width 2
 ]
 
 

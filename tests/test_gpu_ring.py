@@ -229,3 +229,28 @@ def test_ring_ensemble_matches_exact_time_dependent_averages():
     b_mean = ens[:, 0] / n_traj
     assert np.all(np.abs(b_mean - np.array(H_exact)) < 6 * 8 / np.sqrt(n_traj))
     ring.close()
+
+
+def test_ring_million_trajectories_sample():
+    """A million trajectories of the paper's ring in one launch; 64 sampled
+    trajectories against the oracle and the ensemble sums' totals checked
+    against the per-trajectory record states."""
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    n = 1 << 20
+    seeds = [(0x9E3779B97F4A7C15 * (i + 1)) & ((1 << 63) - 1) for i in range(n)]
+    init = [IC8[i % 8] for i in range(n)]
+    ring = kmc.Ring(8, 2, 5, seeds, init)
+    ring.set_rates([0.5] * n, [0.0] * n)
+    o, s, e = ring.run(10, schedule=kmc.KMC_SCHEDULE_RANDOM_PERM, obs_every=4, states=True, ensemble=True)
+    torch.cuda.synchronize()
+    st = s.cpu().numpy().view(np.uint64)  # [rec, traj]
+    bits = ((st[:, :, None] >> np.arange(8, dtype=np.uint64)) & np.uint64(1)).astype(np.int64)
+    assert np.array_equal(e.cpu().numpy()[:, 4:], bits.sum(axis=1))
+    words, hashes, _, _, _ = ring.state()
+    for i in np.random.default_rng(1).choice(n, 64, replace=False):
+        r = orc.Ring(NS=8, Ld=2, k=5, seed=seeds[i], beta=0.5, state=init[i])
+        _, rs = r.run(10, schedule=orc.SCHED_RANDOM_PERM, obs_every=4)
+        assert int(words[i]) == r.state and int(hashes[i]) == r.hash
+        assert np.array_equal(st[:, i], rs)
+    ring.close()
