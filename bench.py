@@ -225,12 +225,12 @@ def reference_arm(args):
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (summary in
 # profiles/run_kernel_ising1024x18_launches.md), and the SHA-256 of the kernel
 # source it was taken on; reported as null once the source has changed.
-TRAFFIC_BYTES_PER_LAUNCH = 5918976 + 10240
+TRAFFIC_BYTES_PER_LAUNCH = 5543680 + 20736
 TRAFFIC_KERNEL_SHA256 = "823b1408fb2c0056ec0d0b082d15c810f72d65cfb1afb637569c1bc640426879"
 # Warp instructions per uniformised step of the same launch (ncu
 # smsp__inst_executed.sum of the full 1e4-schedule launch / its 2.58e9 steps;
 # same capture).  Includes the halo polls.
-INST_PER_STEP = 419567533889 / 2580480000
+INST_PER_STEP = 414890015101 / 2580480000
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 # The same for the variants, from `ncu --metrics smsp__inst_executed.sum` over
 # a full-size timed launch of `bench.py --only grad` / `--only batched`

@@ -43,14 +43,17 @@ def max_domain_side(L: int, candidates: Sequence[int] = DOMAIN_SIDES) -> int:
 def plan_candidates(sm_count: int) -> List[Plan]:
     """Launch plans worth measuring: the library default, clusters of every
     size (the library packs as many replicas per cluster as fit), and
-    cooperative grids of one to three CTAs per SM (24 resident warps where the
-    kernel's registers allow; the library rejects shapes that do not fit)."""
+    cooperative grids of one to six CTAs per SM with 20-24 resident warps
+    where the kernel's registers allow (small CTAs spread the cost-balanced
+    colour chunks over more, shorter lists; the library rejects shapes that
+    do not fit)."""
     out: List[Plan] = [(KMC_LAUNCH_AUTO, 0, 16)]
     out += [(KMC_LAUNCH_CLUSTER, c, 16) for c in (1, 2, 4, 8, 16)]
     out += [(KMC_LAUNCH_CLUSTER, c, 8) for c in (4, 16)]
     out += [(KMC_LAUNCH_GRID, sm_count, 16), (KMC_LAUNCH_GRID, 2 * sm_count, 8),
             (KMC_LAUNCH_GRID, 2 * sm_count, 10), (KMC_LAUNCH_GRID, 2 * sm_count, 12),
-            (KMC_LAUNCH_GRID, 3 * sm_count, 8)]
+            (KMC_LAUNCH_GRID, 3 * sm_count, 8), (KMC_LAUNCH_GRID, 4 * sm_count, 5),
+            (KMC_LAUNCH_GRID, 5 * sm_count, 4), (KMC_LAUNCH_GRID, 6 * sm_count, 4)]
     return out
 
 
