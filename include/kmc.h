@@ -90,6 +90,11 @@ enum { KMC_OBS_SCHEDULE = 0, KMC_OBS_PASS = 1 };
  * larger batches return KMC_EINVAL.
  * The rate table defaults to Metropolis at beta = 0.4, J = 1, h = 0,
  * nu = 1 until kmc_set_rates is called.
+ * Errors: KMC_EINVAL for arguments, KMC_ENOMEM when device memory runs out,
+ * KMC_ECUDA for any other CUDA failure (no usable device included: there is
+ * no CPU fallback).  Except for a null `out` or a failed host allocation
+ * of the context itself, *out then holds a context that kmc_last_error
+ * describes and that the caller destroys.
  */
 kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *L,
                               int32_t L_d, int32_t k_steps, int32_t init,
@@ -391,6 +396,9 @@ typedef struct kmc_ring kmc_ring; /* opaque, library-owned */
  * The rate table defaults to Barker (Glauber, App. A) at beta = 0.5, J = 1,
  * h = 0, nu = 1 -- the paper's 1D setting -- until kmc_ring_set_rates.
  * Counters (steps, real flips, clock, hash) start at zero / the FNV basis.
+ * Errors: KMC_EINVAL for arguments, KMC_ENOMEM when device memory runs out,
+ * KMC_ECUDA for any other CUDA failure (no usable device included); *out
+ * stays NULL on every error.
  */
 kmc_status kmc_ring_create(kmc_ring **out, int32_t n_traj, int32_t n_sites, int32_t L_d, int32_t k_steps,
                            const uint64_t *seeds, const uint64_t *init, void *stream);
@@ -481,6 +489,7 @@ typedef struct kmc_part kmc_part; /* opaque, library-owned */
  *               run, written at its end).
  * Rates default to Barker at beta = 1/2.4, J = 1, h = 0, nu = 1 (the
  * paper's 2D setting).
+ * Errors: as kmc_ring_create (*out stays NULL on every error).
  */
 kmc_status kmc_part_create(kmc_part **out, int32_t n_traj, int32_t L, int32_t partition, int32_t n_domains,
                            int32_t k_steps, const uint64_t *seeds, int8_t *spins_dev, void *stream);

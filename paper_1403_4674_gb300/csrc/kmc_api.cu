@@ -189,12 +189,22 @@ void build_table(double J, double beta, double h, int law, int log2nd, double *a
     }
 }
 
+// Status of a failed cudaMalloc: out of device memory, or any other CUDA
+// failure (no device, driver too old, a sticky error of the context).
+kmc_status alloc_status(cudaError_t e)
+{
+    return (e == cudaErrorMemoryAllocation) ? KMC_ENOMEM : KMC_ECUDA;
+}
+
 template <typename T>
 kmc_status dev_alloc(kmc_ctx *c, T **p, size_t n)
 {
     if (n == 0) n = 1;
     cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
-    if (e != cudaSuccess) return fail(c, KMC_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, alloc_status(e), "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    }
     return KMC_OK;
 }
 
@@ -1741,7 +1751,10 @@ template <typename T>
 kmc_status ring_alloc(kmc_ring *g, T **p, size_t n)
 {
     cudaError_t e = cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
-    if (e != cudaSuccess) return ring_fail(g, KMC_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return ring_fail(g, alloc_status(e), "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    }
     return KMC_OK;
 }
 
@@ -1972,10 +1985,13 @@ void part_free(kmc_part *g)
         if (p) cudaFree(p);
 }
 
+// Allocates unless an earlier allocation failed; keeps the first error.
 template <typename T>
-bool part_alloc(T **p, size_t n)
+bool part_alloc(T **p, size_t n, cudaError_t &first)
 {
-    return cudaMalloc((void **)p, (n ? n : 1) * sizeof(T)) == cudaSuccess;
+    if (first != cudaSuccess) return false;
+    first = cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
+    return first == cudaSuccess;
 }
 
 } // namespace
@@ -2054,13 +2070,15 @@ kmc_status kmc_part_create(kmc_part **out, int32_t n_traj, int32_t L, int32_t pa
     g->spins = spins_dev;
     g->stream = (cudaStream_t)stream;
     const size_t n = (size_t)n_traj;
-    if (!part_alloc(&g->d_seed, n) || !part_alloc(&g->d_A, n * 10) || !part_alloc(&g->d_hash, n) ||
-        !part_alloc(&g->d_clkM, n) || !part_alloc(&g->d_clkE, n) || !part_alloc(&g->d_flips, n) ||
-        !part_alloc(&g->d_steps, n) || !part_alloc(&g->d_h, n) || !part_alloc(&g->d_t, n) || !part_alloc(&g->d_err, 1)) {
+    cudaError_t ae = cudaSuccess;
+    if (!part_alloc(&g->d_seed, n, ae) || !part_alloc(&g->d_A, n * 10, ae) || !part_alloc(&g->d_hash, n, ae) ||
+        !part_alloc(&g->d_clkM, n, ae) || !part_alloc(&g->d_clkE, n, ae) || !part_alloc(&g->d_flips, n, ae) ||
+        !part_alloc(&g->d_steps, n, ae) || !part_alloc(&g->d_h, n, ae) || !part_alloc(&g->d_t, n, ae) ||
+        !part_alloc(&g->d_err, 1, ae)) {
         cudaGetLastError();
         part_free(g);
         delete g;
-        return KMC_ENOMEM;
+        return alloc_status(ae);
     }
     std::vector<uint64_t> basis(n, HASH_BASIS), one(n, 1ull << 63);
     if (cudaMemcpyAsync(g->d_seed, seeds, n * 8, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||

@@ -56,3 +56,43 @@ def test_autotune_host_logic():
         autotune.max_domain_side(24)
     plans = autotune.plan_candidates(152)
     assert plans[0][0] == 0 and (2, 152, 16) in plans and (1, 16, 16) in plans
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the built library the binding raises instead of falling back."""
+    monkeypatch.setattr(_lib, "_LIB", None)
+    monkeypatch.setattr(_lib, "lib_path", lambda: os.path.join(ROOT, "no_such_dir", "libkmc_gb300.so"))
+    with pytest.raises(ImportError):
+        _lib.load(build_if_missing=False)
+
+
+def _has_cuda_device() -> bool:
+    import torch
+    return torch.cuda.device_count() > 0
+
+
+@pytest.mark.skipif(_has_cuda_device(), reason="checks the error path of a machine without a CUDA device")
+def test_no_cpu_fallback_without_a_device():
+    """On a machine without a CUDA device every constructor of the C ABI
+    returns KMC_ECUDA (not KMC_ENOMEM, and never a CPU context)."""
+    lib = _lib.load()
+    seeds = (ctypes.c_uint64 * 4)(1, 2, 3, 4)
+    L = (ctypes.c_int32 * 1)(64)
+    # a non-null, aligned placeholder: with no device nothing can use it
+    placeholder = ctypes.c_void_p(4096)
+    for L_d in (0, 16):
+        ctx = ctypes.c_void_p()
+        assert lib.kmc_create_lattice(ctypes.byref(ctx), 1, L, L_d, 1, 0, seeds, placeholder, None) == _lib.KMC_ECUDA
+        assert ctx.value is not None and lib.kmc_last_error(ctx)
+        lib.kmc_destroy(ctx)
+    ring = ctypes.c_void_p()
+    zeros = (ctypes.c_uint64 * 4)(0, 0, 0, 0)
+    assert lib.kmc_ring_create(ctypes.byref(ring), 4, 8, 2, 5, seeds, zeros, None) == _lib.KMC_ECUDA
+    assert ring.value is None
+    part = ctypes.c_void_p()
+    assert lib.kmc_part_create(ctypes.byref(part), 4, 12, 1, 2, 5, seeds, placeholder, None) == _lib.KMC_ECUDA
+    assert part.value is None
+    import paper_1403_4674_gb300 as kmc
+    with pytest.raises(kmc.KmcError) as e:
+        kmc.Ring(8, 2, 5, [1, 2], [0, 0])
+    assert e.value.status == _lib.KMC_ECUDA
