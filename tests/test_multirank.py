@@ -56,3 +56,24 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     class A:
         workload, schedules, warmup, steps, gpus = "ising1024", 0, 0, 1, 2
     assert bench.reference_arm(A()) == 0  # returns at once, no oracle work
+
+
+def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
+    """Rank 0 of the reference arm times the oracle and prints one JSON line
+    with the contract's keys (the driver computes the arms' ratio from it)."""
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+
+    class A:
+        workload, schedules, warmup, steps, gpus = "ising1024", 0, 0, 1, 1
+    assert bench.reference_arm(A()) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["config"]["workload"].startswith("1024x1024")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
