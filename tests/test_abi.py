@@ -96,3 +96,49 @@ def test_no_cpu_fallback_without_a_device():
     with pytest.raises(kmc.KmcError) as e:
         kmc.Ring(8, 2, 5, [1, 2], [0, 0])
     assert e.value.status == _lib.KMC_ECUDA
+
+
+# Invalid arguments are refused on the host, before any CUDA call.  A
+# placeholder device pointer is passed, so these run only on a machine
+# without a CUDA device (the GPU suite checks the same refusals with real
+# buffers).
+_PLACE = 4096  # non-null, 8-byte aligned; never dereferenced here
+
+
+@pytest.mark.skipif(_has_cuda_device(), reason="placeholder device pointers: machines without a CUDA device only")
+@pytest.mark.parametrize("n_rep,Ls,L_d,k,init,spins,needle", [
+    (1, [64], 12, 1, 0, _PLACE, "L_d must be"),
+    (1, [64], 16, 0, 0, _PLACE, "k_steps"),
+    (1, [64], 16, 65536, 0, _PLACE, "k_steps"),
+    (1, [64], 16, 1, 7, _PLACE, "init"),
+    (1, [64], 16, 1, 0, _PLACE + 4, "aligned"),
+    (1, [64], 16, 1, 0, 0, "non-null"),
+    (1, [48], 16, 1, 0, _PLACE, "multiple of 2*L_d"),
+    (2, [64, 72], 8, 1, 0, _PLACE, "replica 1"),
+    (1, [131072], 64, 1, 0, _PLACE, "multiple of 2*L_d"),
+    (1, [65536], 8, 1, 0, _PLACE, "too many domains"),
+])
+def test_lattice_arguments_refused_on_the_host(n_rep, Ls, L_d, k, init, spins, needle):
+    lib = _lib.load()
+    ctx = ctypes.c_void_p()
+    L = (ctypes.c_int32 * n_rep)(*Ls)
+    seeds = (ctypes.c_uint64 * n_rep)(*range(1, n_rep + 1))
+    st = lib.kmc_create_lattice(ctypes.byref(ctx), n_rep, L, L_d, k, init, seeds, ctypes.c_void_p(spins), None)
+    assert st == _lib.KMC_EINVAL
+    assert needle in lib.kmc_last_error(ctx).decode()
+    lib.kmc_destroy(ctx)
+
+
+@pytest.mark.skipif(_has_cuda_device(), reason="placeholder device pointers: machines without a CUDA device only")
+def test_ring_and_partition_arguments_refused_on_the_host():
+    lib = _lib.load()
+    seeds = (ctypes.c_uint64 * 2)(1, 2)
+    g = ctypes.c_void_p()
+    for NS, Ld, k, init in ((65, 1, 5, 0), (8, 3, 5, 0), (8, 16, 5, 0), (8, 2, 65536, 0), (8, 2, 5, 1 << 8)):
+        words = (ctypes.c_uint64 * 2)(init, 0)
+        assert lib.kmc_ring_create(ctypes.byref(g), 2, NS, Ld, k, seeds, words, None) == _lib.KMC_EINVAL
+        assert g.value is None
+    for L, kind, ND, k in ((12, 2, 2, 5), (12, 0, 2, 5), (12, 1, 5, 5), (12, 1, 2, 65536), (12, 1, 65, 5)):
+        assert lib.kmc_part_create(ctypes.byref(g), 2, L, kind, ND, k, seeds, ctypes.c_void_p(_PLACE), None) \
+            == _lib.KMC_EINVAL
+        assert g.value is None
