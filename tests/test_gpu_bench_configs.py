@@ -35,7 +35,7 @@ def _check(spins_of, obs, idx, n, L, Ld, ks, seeds, beta, h, inits, scores=None,
             np.testing.assert_allclose(scores[r], ref.score.sum(axis=0), rtol=1e-9, atol=1e-9)
 
 
-@pytest.mark.parametrize("plan", ["grid_2x10", "grid_3x8", "grid_1x16", "cluster_16"])
+@pytest.mark.parametrize("plan", ["grid_5x4", "grid_2x10", "grid_3x8", "grid_1x16", "cluster_16"])
 def test_ising1024_all_replicas(plan):
     """The 18 replicas of 1024^2 (T x start x k) in one context and launch,
     per-replica k and start, profiling on, as the benchmark runs them."""
@@ -50,8 +50,8 @@ def test_ising1024_all_replicas(plan):
     lat.reset(kmc.KMC_INIT_PER_REPLICA)
     lat.set_rates(w.beta, w.h)
     sm = _sm()
-    lat.set_launch(*{"grid_2x10": (2, 2 * sm, 10), "grid_3x8": (2, 3 * sm, 8), "grid_1x16": (2, sm, 16),
-                     "cluster_16": (1, 16, 16)}[plan])
+    lat.set_launch(*{"grid_5x4": (2, 5 * sm, 4), "grid_2x10": (2, 2 * sm, 10), "grid_3x8": (2, 3 * sm, 8),
+                     "grid_1x16": (2, sm, 16), "cluster_16": (1, 16, 16)}[plan])
     lat.profile(True)
     obs = lat.run(3, obs_every=1).cpu().numpy()
     lat.sync()
@@ -126,8 +126,8 @@ def test_lattice8192_one_schedule():
 
 def test_ising1024_full_timed_length_sampled_replica():
     """The benchmark's timed launch itself: all 18 replicas of 1024^2 in one
-    context on the 2 x 10-warp grid for the full 1e4 schedules with records
-    every 10; replica 2 (k = 1, T = 3.0, random start: the most real events
+    context on the grid the tuner picks for it (five CTAs of 4 warps per SM)
+    for the full 1e4 schedules with records every 10; replica 2 (k = 1, T = 3.0, random start: the most real events
     per step) checked against the oracle over the whole run (about a minute
     of CPU)."""
     import paper_1403_4674_gb300 as kmc
@@ -140,7 +140,7 @@ def test_ising1024_full_timed_length_sampled_replica():
     lat.set_replica_params(k=ks, init=inits)
     lat.reset(kmc.KMC_INIT_PER_REPLICA)
     lat.set_rates(w.beta, w.h)
-    lat.set_launch(2, 2 * _sm(), 10)
+    lat.set_launch(2, 5 * _sm(), 4)
     obs = lat.run(w.schedules, obs_every=w.obs_every).cpu().numpy()
     lat.sync()
     _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [2], w.schedules, w.L, w.L_d, ks, w.seeds, w.beta,
