@@ -113,6 +113,9 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
  * The table is built on the host in FP64 and held in fixed point,
  * A_c = round(a_c 2^P), P = 63 - log2(n_d), so that every trajectory
  * decision on the device is an exact integer comparison.
+ * Errors: KMC_EINVAL for null arrays, a bad law, a non-finite J, nu <= 0,
+ * beta < 0 or a non-finite h, and while the stream is capturing; the
+ * previous table then stays.
  */
 kmc_status kmc_set_rates(kmc_ctx *ctx, double J, const double *beta, const double *h,
                          double nu, int32_t rate_law);
@@ -182,6 +185,7 @@ kmc_status kmc_set_horizon(kmc_ctx *ctx, double dtau);
  *                     synchronisation between domains; same-colour passes of
  *                     a schedule are not fused.
  * A host-side setting; takes effect at the next kmc_run_schedule.
+ * KMC_EINVAL for another unit (the setting stays).
  */
 kmc_status kmc_set_observation(kmc_ctx *ctx, int32_t unit);
 
@@ -190,6 +194,10 @@ kmc_status kmc_set_observation(kmc_ctx *ctx, int32_t unit);
  * per replica into host arrays of n_replicas entries (any may be NULL):
  * E_per_site, m, t (mean domain clock, in the time mode of the last run),
  * steps (uniformised steps so far, Eq. 11), flips (real events so far).
+ * E and m follow App. A's H and magnetisation over the whole lattice
+ * (Sec. 2.3: observables at schedule endpoints).  Synchronising: raises any
+ * device-side error of earlier work (KMC_ETIMEOUT, KMC_EDEVICE); KMC_EINVAL
+ * while the stream is capturing.
  */
 kmc_status kmc_observables(kmc_ctx *ctx, double *E_per_site, double *m, double *t,
                            int64_t *steps, int64_t *flips);
@@ -197,7 +205,8 @@ kmc_status kmc_observables(kmc_ctx *ctx, double *E_per_site, double *m, double *
 /*
  * kmc_grad -- likelihood-ratio score of the path so far, per replica:
  * score_dev[r*2 + {0,1}] = d log P(path) / d{beta, h} of the uniformised
- * jump chain (device buffer, caller-owned).  reset != 0 zeroes the accumulators after
+ * jump chain (App. A: T_ji = a_c / n_d, null steps on the diagonal; the
+ * paper itself takes no derivatives) (device buffer, caller-owned).  reset != 0 zeroes the accumulators after
  * copying (a checkpointed segment boundary).  Accumulation is enabled by
  * kmc_enable_grad.  Synchronising.
  */
@@ -219,23 +228,28 @@ kmc_status kmc_grad_nu(kmc_ctx *ctx, double *score_dev);
  * kmc_lr_estimate -- likelihood-ratio gradient of E[A] over the replicas:
  * grad_dev[j] = (1/R) sum_r (A_r - mean A) S_r,j for j = {beta, h}, where
  * A_dev[r] (device, n_replicas doubles) is an observable of replica r at the
- * current endpoint and S_r the path score accumulated since the last reset
+ * current endpoint (such as Sec. 2.3's H m) and S_r the path score accumulated since the last reset
  * (kmc_grad with reset, or kmc_reset).  Subtracting the replica mean is a
  * baseline: E[S] = 0, so the estimate stays unbiased.  Asynchronous, on the
  * context's stream; needs n_replicas >= 2.
  */
 kmc_status kmc_lr_estimate(kmc_ctx *ctx, const double *A_dev, double *grad_dev);
 
-/* Turn score accumulation on (enable != 0) or off for following runs.  The
- * score-carrying kernels use more registers; if they do not fit the current
- * launch plan's shape, the plan is rebuilt (requested plan first, else the
- * default).  Not while the stream is capturing. */
+/* Turn score accumulation on (enable != 0) or off for following runs (the
+ * likelihood-ratio score of kmc_grad; the paper has no gradients, the score
+ * is that of its uniformised chain, App. A).  The score-carrying kernels use
+ * more registers; if they do not fit the current launch plan's shape, the
+ * plan is rebuilt (requested plan first, else the default).  KMC_EINVAL
+ * when turning scores on while the stream is capturing or when no plan fits
+ * the score kernels; the setting then stays. */
 kmc_status kmc_enable_grad(kmc_ctx *ctx, int32_t enable);
 
 /* Re-initialise spins from the seeds (init as in kmc_create_lattice, or
  * KMC_INIT_PER_REPLICA for the per-replica modes of kmc_set_replica_params),
- * zero clocks, counters, scores and the schedule index.  Asynchronous; it
- * enqueues only device work, so it may be captured in a CUDA graph. */
+ * zero clocks, counters, scores and the schedule index: the start of a new
+ * trajectory (Sec. 2.3, s = 0).  Asynchronous; it enqueues only device work,
+ * so it may be captured in a CUDA graph.  KMC_EINVAL for a bad init mode,
+ * KMC_ECUDA if a launch fails. */
 kmc_status kmc_reset(kmc_ctx *ctx, int32_t init, void *stream);
 
 /*
@@ -251,11 +265,16 @@ kmc_status kmc_reset(kmc_ctx *ctx, int32_t init, void *stream);
  *               KMC_INIT_KEEP, used by kmc_reset(ctx, KMC_INIT_PER_REPLICA).
  * The launch plan is rebuilt so that replicas of equal k share clusters.
  * Synchronous on the host arrays (copied before the call returns); must not
- * be called while the context's stream is capturing.
+ * be called while the context's stream is capturing.  KMC_EINVAL for a value
+ * out of range, a k change after the first run, or a capture; nothing
+ * changes then.
  */
 kmc_status kmc_set_replica_params(kmc_ctx *ctx, const int32_t *k_steps, const int32_t *init);
 
-/* Wait for all work of the context and raise any device-side error. */
+/* Wait for all work of the context and raise any device-side error:
+ * KMC_ETIMEOUT (a bounded halo wait gave up), KMC_EDEVICE (the device error
+ * word, e.g. a spin byte not +-1), KMC_ECUDA (a CUDA failure).  No
+ * counterpart in the paper. */
 kmc_status kmc_sync(kmc_ctx *ctx);
 
 /* Per-domain state for parity checks, host arrays of total-domain length,
@@ -264,10 +283,14 @@ kmc_status kmc_sync(kmc_ctx *ctx);
  * FNV-1a 64 offset basis and folds every real event of the domain as
  * H <- (H xor e) * 0x100000001b3 with e = np << 32 | j << 16 | site (np = 8n + p
  * the global colour phase, j the step within the visit, site = y L_d + x).
- * Any pointer may be NULL.  Synchronising. */
+ * Any pointer may be NULL.  Synchronising; errors as kmc_sync.  A parity
+ * aid of this library, not a quantity of the paper (the domain clock is the
+ * t_d of Sec. 2.1). */
 kmc_status kmc_domain_state(kmc_ctx *ctx, uint64_t *hash, int64_t *flips, double *t);
 
-/* Fixed-point and FP64 acceptance table of replica r (host arrays of 10). */
+/* Fixed-point and FP64 acceptance table of replica r (host arrays of 10,
+ * either may be NULL; App. A, as built by kmc_set_rates).  KMC_EINVAL for a
+ * null context or r out of range. */
 kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, uint64_t *A);
 
 /* Launch plan of the persistent run kernel.
@@ -286,7 +309,7 @@ kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, ui
  *     of 8-12 warps can share an SM.
  * In both plans a visit starts as soon as its four neighbours have finished
  * their visits of earlier colour phases (per-domain dataflow instead of a
- * barrier per phase); observation records are built from per-visit changes,
+ * barrier per phase; Sec. 2.2 lets non-interacting domains run at once); observation records are built from per-visit changes,
  * so no point of a launch synchronises a whole replica.
  * warps_per_cta: 1..16.  Returns KMC_EINVAL if the plan cannot be scheduled
  * or the state does not fit in shared memory; the previous plan then stays.
@@ -294,7 +317,8 @@ kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, ui
 enum { KMC_LAUNCH_AUTO = 0, KMC_LAUNCH_CLUSTER = 1, KMC_LAUNCH_GRID = 2 };
 kmc_status kmc_set_launch(kmc_ctx *ctx, int32_t mode, int32_t size, int32_t warps_per_cta);
 /* Current plan: mode, size (cluster size or CTA count), CTAs, warps per CTA,
- * dynamic shared memory per CTA.  Any pointer may be NULL. */
+ * dynamic shared memory per CTA.  Any pointer may be NULL.  KMC_EINVAL for a
+ * null context.  No counterpart in the paper. */
 kmc_status kmc_get_launch(const kmc_ctx *ctx, int32_t *mode, int32_t *size, int32_t *ctas,
                           int32_t *warps_per_cta, int32_t *smem_bytes);
 
@@ -303,13 +327,17 @@ kmc_status kmc_get_launch(const kmc_ctx *ctx, int32_t *mode, int32_t *size, int3
  * visits.  With extra > 0 every visit waits for `extra` more neighbour visits than
  * will ever come, so the waits give up after limit_ns nanoseconds and the
  * next kmc_sync returns KMC_ETIMEOUT; the context stays usable.  extra = 0
- * restores normal waits; limit_ns = 0 restores the default limit (2 s). */
+ * restores normal waits; limit_ns = 0 restores the default limit (2 s).
+ * KMC_EINVAL for a null context or negative arguments.  No counterpart in
+ * the paper. */
 kmc_status kmc_debug_barrier(kmc_ctx *ctx, int32_t extra, int64_t limit_ns);
 
 /* Event timing of the persistent run kernel: with enable != 0 every
  * kmc_run_schedule records a CUDA event pair around its run-kernel launch on
  * the launch stream.  kmc_profile_read synchronises, returns the summed
- * elapsed milliseconds and the number of timed launches, and clears them. */
+ * elapsed milliseconds and the number of timed launches, and clears them.
+ * KMC_EINVAL for a null context; kmc_profile_read returns KMC_ECUDA if an
+ * event cannot be read.  No counterpart in the paper. */
 kmc_status kmc_profile(kmc_ctx *ctx, int32_t enable);
 kmc_status kmc_profile_read(kmc_ctx *ctx, double *run_kernel_ms, int64_t *run_kernel_launches);
 
@@ -348,10 +376,12 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
                                     int32_t time_mode, int32_t obs_every, int8_t *spins_dev,
                                     double *obs_dev, void *stream, char *err, int32_t err_len);
 
-/* Number of kernels this context launched so far (all kinds). */
+/* Number of kernels this context launched so far (all kinds); 0 for a null
+ * context.  No counterpart in the paper (launch accounting). */
 int64_t kmc_kernel_launches(const kmc_ctx *ctx);
 
-/* The context's domain side L_d (the chosen one when created with 0). */
+/* The context's domain side L_d (the chosen one when created with 0; the
+ * equal domains of Sec. 2.2); 0 for a null context. */
 int32_t kmc_domain_side(const kmc_ctx *ctx);
 
 const char *kmc_last_error(const kmc_ctx *ctx);
@@ -450,7 +480,9 @@ kmc_status kmc_ring_run(kmc_ring *ring, int64_t n_schedules, int32_t schedule, i
 /*
  * kmc_ring_state -- synchronise the last stream used and copy the counters
  * to host arrays [n_traj] (any may be NULL): configuration words, event
- * hashes, real flips, steps and the clock T of the last run's time mode.
+ * hashes, real flips, steps (Eq. 11) and the clock T of the last run's time
+ * mode (Sec. 2.1).  KMC_EINVAL for a null ring, KMC_ECUDA if the stream or
+ * a copy fails.
  */
 kmc_status kmc_ring_state(kmc_ring *ring, uint64_t *state, uint64_t *hash, int64_t *flips, int64_t *steps,
                           double *t);
@@ -494,7 +526,9 @@ typedef struct kmc_part kmc_part; /* opaque, library-owned */
 kmc_status kmc_part_create(kmc_part **out, int32_t n_traj, int32_t L, int32_t partition, int32_t n_domains,
                            int32_t k_steps, const uint64_t *seeds, int8_t *spins_dev, void *stream);
 
-/* kmc_part_set_rates -- as kmc_ring_set_rates, classes c = 5 up + q. */
+/* kmc_part_set_rates -- as kmc_ring_set_rates (App. A, Eq. Glauber_TM),
+ * classes c = 5 up + q, dE_c = 2 s (J (2q - 4) + h); errors as
+ * kmc_ring_set_rates. */
 kmc_status kmc_part_set_rates(kmc_part *part, double J, const double *beta, const double *h, double nu,
                               int32_t rate_law);
 
@@ -503,7 +537,8 @@ kmc_status kmc_part_set_rates(kmc_part *part, double J, const double *beta, cons
  * global schedule count); phases of schedule n have Philox phase index
  * np = 64 n + p:
  *   KMC_SCHEDULE_PALINDROME: colours ascending then descending (blocks
- *                 0 1 2 3 3 2 1 0, stripes 0 1 1 0, one domain 0 0);
+ *                 0 1 2 3 3 2 1 0, stripes 0 1 1 0, one domain 0 0; the
+ *                 reversal-closed schedule of Sec. 2.2, Eqs. 9-10);
  *                 needs Dx (blocks) or N_D (stripes) to be 1 or even;
  *   KMC_SCHEDULE_FIXED: colours ascending once (negative test);
  *   KMC_SCHEDULE_RANDOM_PERM: the paper's random order of all N_D domains
@@ -514,12 +549,16 @@ kmc_status kmc_part_set_rates(kmc_part *part, double J, const double *beta, cons
  *               t_d = (clock sum or steps of d) / (n_d nu).
  * Asynchronous on `stream`, one kernel launch.  A spin byte that is not
  * +-1 sets the context's device error word (KMC_EDEVICE at kmc_part_state).
+ * KMC_EINVAL for negative counts, a bad schedule, time mode or partition
+ * for the palindrome, or a misaligned obs_dev; KMC_ECUDA if the launch fails.
  */
 kmc_status kmc_part_run(kmc_part *part, int64_t n_schedules, int32_t schedule, int32_t time_mode,
                         int32_t obs_every, double *obs_dev, void *stream);
 
 /* kmc_part_state -- synchronise and copy host arrays [n_traj] (any may be
- * NULL): event hashes, real flips, steps, clock T of the last run's mode. */
+ * NULL): event hashes, real flips, steps (Eq. 11), clock T of the last run's
+ * mode (Sec. 2.1).  KMC_EINVAL for a null handle, KMC_EDEVICE if a run found
+ * a spin byte that is not +-1, KMC_ECUDA if the stream or a copy fails. */
 kmc_status kmc_part_state(kmc_part *part, uint64_t *hash, int64_t *flips, int64_t *steps, double *t);
 
 const char *kmc_part_last_error(const kmc_part *part);
