@@ -16,8 +16,8 @@
  *   - 2D periodic Ising energy, App. A (Eq. for beta*H, 2D line; both
  *     factors read as configuration j), plus a field term -h*sum(sigma);
  *   - the lattice cut into equal square domains (Sec. 2.2), coloured 2x2 so
- *     that same-coloured domains share no halo (Sec. 2.2, "the order of
- *     updates is not important");
+ *     that same-coloured domains share no halo (Sec. 2.2: domains that do
+ *     not interact may be visited in any order, or at once);
  *   - each domain process runs k steps with its halo frozen (Sec. 2.2,
  *     Eqs. 4-5).  One step is the uniformised single-site kernel of App. A
  *     (Eq. Glauber_TM): site i of the domain flips with probability
