@@ -134,7 +134,8 @@ kmc_status kmc_set_rate_table(kmc_ctx *ctx, double J, const double *beta, const 
  * (Sec. 2.2, Eqs. 8-11).  One schedule visits every domain twice
  * (PALINDROME) or once (FIXED, RANDOM_PERM); each visit is k uniformised
  * steps with frozen halo.  The integer step counter of a replica advances by
- * k * N_D per colour pass (Eq. 11).
+ * k * N_D per sweep over all domains (Eq. 11), i.e. k * N_D / 4 per colour
+ * pass and 2 k N_D per palindromic schedule.
  *   time_mode   KMC_TIME_EXPONENTIAL: each step advances the domain clock by
  *               Exp(Lambda_d) (Sec. 2.1, Erlang variate as a sum of -log u);
  *               KMC_TIME_EXPECTED: by its mean 1/Lambda_d (the paper's
