@@ -113,8 +113,13 @@ kmc_status kmc_create_lattice(kmc_ctx **out, int32_t n_replicas, const int32_t *
  * The table is built on the host in FP64 and held in fixed point,
  * A_c = round(a_c 2^P), P = 63 - log2(n_d), so that every trajectory
  * decision on the device is an exact integer comparison.
+ * The rounding changes a_c by at most 2^-(P+1) absolute, i.e. by 2^-(P+1)/a_c
+ * relative; kmc_rate_table_error reports the largest such change.
  * Errors: KMC_EINVAL for null arrays, a bad law, a non-finite J, nu <= 0,
- * beta < 0 or a non-finite h, and while the stream is capturing; the
+ * beta < 0 or a non-finite h, and while the stream is capturing;
+ * KMC_ENOTBALANCED when some a_c < 2^-(P+1) rounds to A_c = 0 (beta dE_c of
+ * about 37-44 or more, depending on P): the quantised chain would then flip
+ * out of class cbar but never back, against detailed balance (Eq. 4).  The
  * previous table then stays.
  */
 kmc_status kmc_set_rates(kmc_ctx *ctx, double J, const double *beta, const double *h,
@@ -123,7 +128,8 @@ kmc_status kmc_set_rates(kmc_ctx *ctx, double J, const double *beta, const doubl
 /*
  * kmc_set_rate_table -- user acceptance table a[r*10 + c] in (0, 1], checked
  * against detailed balance (Eq. 4): a_c / a_cbar must equal exp(-beta dE_c)
- * to 1e-12 relative, cbar = the same site after its flip.  Otherwise
+ * to 1e-12 relative, cbar = the same site after its flip.  Otherwise, or
+ * when some a_c rounds to A_c = 0 in the fixed point of kmc_set_rates,
  * KMC_ENOTBALANCED and the previous table stays.
  */
 kmc_status kmc_set_rate_table(kmc_ctx *ctx, double J, const double *beta, const double *h,
@@ -227,14 +233,33 @@ kmc_status kmc_grad_nu(kmc_ctx *ctx, double *score_dev);
 
 /*
  * kmc_lr_estimate -- likelihood-ratio gradient of E[A] over the replicas:
- * grad_dev[j] = (1/R) sum_r (A_r - mean A) S_r,j for j = {beta, h}, where
- * A_dev[r] (device, n_replicas doubles) is an observable of replica r at the
- * current endpoint (such as Sec. 2.3's H m) and S_r the path score accumulated since the last reset
- * (kmc_grad with reset, or kmc_reset).  Subtracting the replica mean is a
- * baseline: E[S] = 0, so the estimate stays unbiased.  Asynchronous, on the
- * context's stream; needs n_replicas >= 2.
+ * grad_dev[j] = (1/(R-1)) sum_r (A_r - mean A) S_r,j for j = {beta, h},
+ * where A_dev[r] (device, n_replicas doubles) is an observable of replica r
+ * at the current endpoint (such as Sec. 2.3's H m) and S_r the path score
+ * accumulated since the last reset (kmc_grad with reset, or kmc_reset).  The
+ * replica mean is a baseline (E[S] = 0); with it the 1/(R-1) normalisation
+ * gives an unbiased estimate of Cov(A, S) = dE[A]/dtheta for an A with no
+ * explicit dependence on theta.  grad_dev: device, 2 doubles.  Asynchronous,
+ * on the context's stream; needs n_replicas >= 2 (else KMC_EINVAL).  The
+ * paper takes no derivatives: this differentiates its App. A chain.
  */
 kmc_status kmc_lr_estimate(kmc_ctx *ctx, const double *A_dev, double *grad_dev);
+
+/*
+ * kmc_lr_observable -- value and gradient of the replica mean of an endpoint
+ * observable of Sec. 2.3 (App. A energy), for a differentiable interface:
+ *   rec_dev     device record row [n_replicas][stride] as kmc_run_schedule
+ *               writes it (e, m, e*m, T, ...), stride >= 4 doubles;
+ *   observable  0: e = E/N = (-J bonds - h M)/N, 1: m = M/N, 2: e*m;
+ *   out_dev     device, 3 doubles: mean A, dE[A]/dbeta, dE[A]/dh.
+ * The gradient is kmc_lr_estimate's path term plus the replica mean of the
+ * observable's explicit dependence on h, which the path score does not
+ * hold: de/dh = -m, d(e m)/dh = -m^2, dm/dh = 0 (no explicit beta term).
+ * Asynchronous, on the context's stream.  KMC_EINVAL for null pointers, a
+ * bad observable or stride, or fewer than two replicas.
+ */
+kmc_status kmc_lr_observable(kmc_ctx *ctx, const double *rec_dev, int32_t stride, int32_t observable,
+                             double *out_dev);
 
 /* Turn score accumulation on (enable != 0) or off for following runs (the
  * likelihood-ratio score of kmc_grad; the paper has no gradients, the score
@@ -293,6 +318,15 @@ kmc_status kmc_domain_state(kmc_ctx *ctx, uint64_t *hash, int64_t *flips, double
  * either may be NULL; App. A, as built by kmc_set_rates).  KMC_EINVAL for a
  * null context or r out of range. */
 kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, uint64_t *A);
+
+/* Largest relative change of an acceptance by its fixed-point rounding,
+ * max over replicas and classes of |A_c 2^-P - a_c| / a_c (App. A rates as
+ * the device uses them; at most 2^-(P+1)/a_c).  The quantised chain is
+ * reversible with respect to the Boltzmann weights of the rounded ratios
+ * A_c/A_cbar, so this bounds how far its stationary ratios are from
+ * exp(-beta dE_c) (Eq. 4).  *max_rel_err is a host double.  KMC_EINVAL for a
+ * null argument or before the first table. */
+kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
 
 /* Launch plan of the persistent run kernel.
  *   KMC_LAUNCH_AUTO: the library's choice: CLUSTER when every replica fits

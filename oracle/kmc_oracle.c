@@ -133,7 +133,10 @@ static int orc_log2(int v)
  *   Barker:     a_c = 1 / (1 + exp(beta*dE_c))     (App. A, "Barker")
  * a_c is the acceptance of the uniformised step; the physical rate is
  * nu*a_c.  A_c = round-to-nearest-even(a_c * 2^P), P = 63 - log2(n_d).
- * Returns 0, or -1 for an invalid argument.
+ * Returns 0, -1 for an invalid argument, or -2 when some a_c rounds to
+ * A_c = 0: every a_c is positive, so the quantised chain would then leave
+ * class c's reverse but never enter it, which breaks detailed balance
+ * (Sec. 2.2, Eq. 4).
  * ---------------------------------------------------------------------- */
 int orc_rate_table(double J, double beta, double h, int law, int log2_nd,
                    double a_out[10], uint64_t A_out[10])
@@ -158,6 +161,8 @@ int orc_rate_table(double J, double beta, double h, int law, int log2_nd,
             A_out[c] = (uint64_t)nearbyint(ldexp(a, P));
         }
     }
+    for (int c = 0; c < 10; ++c)
+        if (A_out[c] == 0) return -2;
     return 0;
 }
 
@@ -271,6 +276,33 @@ int orc_schedule_colours(int schedule, uint64_t n, uint64_t seed, int out[8])
 }
 
 /* ------------------------------------------------------------------------
+ * Compensated summation (Neumaier 1974, the improved Kahan-Babuska sum):
+ * *sum + *comp carries the running total; each term's rounding error is
+ * recovered exactly and added to *comp.  The likelihood-ratio score of a
+ * domain is a sum of some 1e5 per-step terms of both signs whose total is
+ * much smaller than its partial sums; a plain running FP64 sum would carry
+ * an error of order 2^-53 times the partial sums times the square root of
+ * the number of terms, this one an error of a few ulp of the total.
+ * ---------------------------------------------------------------------- */
+static void orc_sum_add(double *sum, double *comp, double x)
+{
+    double t = *sum + x;
+    if (fabs(*sum) >= fabs(x))
+        *comp += (*sum - t) + x;
+    else
+        *comp += (x - t) + *sum;
+    *sum = t;
+}
+
+/* Compensated sum of x[0..n-1] (for tests of the summation above). */
+double orc_sum_compensated(const double *x, int64_t n)
+{
+    double sum = 0.0, comp = 0.0;
+    for (int64_t i = 0; i < n; ++i) orc_sum_add(&sum, &comp, x[i]);
+    return sum + comp;
+}
+
+/* ------------------------------------------------------------------------
  * One domain process (Sec. 2.2): domain d = by*Dx + bx of a replica, k
  * uniformised steps with the halo frozen.
  *
@@ -290,6 +322,9 @@ int orc_schedule_colours(int schedule, uint64_t n, uint64_t seed, int out[8])
  *   H <- (H xor e) * FNV_PRIME,  e = np<<32 | j<<16 | i.
  * Exponential clock: esum_d += -log(v) for every step (Sec. 2.1, the
  * Poisson variate as a sum of negative logarithms).
+ * Score (grad != NULL): score[0..1] are the domain's running sums of
+ * d log P / d(beta, h) and score[2..3] their compensations (orc_sum_add);
+ * the domain's score is score[0..1] + score[2..3].
  * ---------------------------------------------------------------------- */
 static void orc_visit(int8_t *s, int L, int Ld, int bx, int by, int k,
                       const uint64_t A[10], uint32_t key0, uint32_t key1,
@@ -356,8 +391,8 @@ static void orc_visit(int8_t *s, int L, int Ld, int bx, int by, int k,
         *steps += 1;
         if (target >= R) { /* null step */
             if (grad) {
-                score[0] -= Db / ((double)nd - Rr);
-                score[1] -= Dh / ((double)nd - Rr);
+                orc_sum_add(&score[0], &score[2], -(Db / ((double)nd - Rr)));
+                orc_sum_add(&score[1], &score[3], -(Dh / ((double)nd - Rr)));
             }
             continue;
         }
@@ -370,8 +405,8 @@ static void orc_visit(int8_t *s, int L, int Ld, int bx, int by, int k,
             C += w_c;
         }
         if (grad) {
-            score[0] += grad[10 + c];
-            score[1] += grad[20 + c];
+            orc_sum_add(&score[0], &score[2], grad[10 + c]);
+            orc_sum_add(&score[1], &score[3], grad[20 + c]);
         }
         uint64_t jj = (target - C) / A[c];
         int site = -1;
@@ -500,7 +535,10 @@ static void orc_record(const int8_t *s, int L, double J, double h, int time_mode
     orc_observe(s, L, J, h, time_mode, esum, steps, ND, nd, nu, rec);
     if (score) {
         double sb = 0.0, sh = 0.0;
-        for (int d = 0; d < ND; ++d) { sb += score[2 * d]; sh += score[2 * d + 1]; }
+        for (int d = 0; d < ND; ++d) {
+            sb += score[4 * d] + score[4 * d + 2];
+            sh += score[4 * d + 1] + score[4 * d + 3];
+        }
         rec[4] = sb;
         rec[5] = sh;
     }
@@ -558,7 +596,7 @@ int orc_run_replica_ex(int8_t *s, int L, int Ld, int k, const uint64_t A[10],
                 orc_visit(s, L, Ld, bx, by, kv, A, key0, key1, np,
                           (uint32_t)d, time_mode, &esum[d], &hash[d],
                           &flips[d], &steps[d], grad,
-                          score ? &score[2 * d] : NULL);
+                          score ? &score[4 * d] : NULL);
                 /* fixed-time visit: the domain clock advances by dtau */
                 if (time_mode == ORC_TIME_HORIZON) esum[d] += dtau * (double)nd * nu;
             }
@@ -630,19 +668,22 @@ int orc_sample_final_states_grad(const int8_t *s0, int L, int Ld, int k,
     int64_t *steps = (int64_t *)calloc((size_t)ND, sizeof(int64_t));
     uint64_t *hash = (uint64_t *)calloc((size_t)ND, sizeof(uint64_t));
     int64_t *flips = (int64_t *)calloc((size_t)ND, sizeof(int64_t));
-    double *score = (double *)calloc((size_t)ND * 2, sizeof(double));
+    double *score = (double *)calloc((size_t)ND * 4, sizeof(double));
     int rc = 0;
     for (int64_t r = 0; r < n_runs && rc == 0; ++r) {
         int8_t *s = out + r * (int64_t)L * L;
         memcpy(s, s0, (size_t)L * L);
-        memset(score, 0, sizeof(double) * (size_t)ND * 2);
+        memset(score, 0, sizeof(double) * (size_t)ND * 4);
         rc = orc_run_replica_grad(s, L, Ld, k, A, seed0 + (uint64_t)r,
                                   schedule, ORC_TIME_EXPECTED, 1.0, 1.0, 0.0,
                                   0, n_sched, 0, esum, steps, hash, flips,
                                   NULL, grad, grad ? score : NULL);
         if (grad && score_out) {
             double sb = 0.0, sh = 0.0;
-            for (int d = 0; d < ND; ++d) { sb += score[2 * d]; sh += score[2 * d + 1]; }
+            for (int d = 0; d < ND; ++d) {
+                sb += score[4 * d] + score[4 * d + 2];
+                sh += score[4 * d + 1] + score[4 * d + 3];
+            }
             score_out[2 * r] = sb;
             score_out[2 * r + 1] = sh;
         }
@@ -670,7 +711,8 @@ int orc_sample_final_states(const int8_t *s0, int L, int Ld, int k,
  *
  * Class c = 3*sp + q: sp = 1 for an up spin, q = number of up neighbours
  * (0..2); neighbour sum 2q - 2; dE_c = 2*sigma*(J*(2q-2) + h).  Rates and
- * fixed point as in 2D: A_c = round(a_c 2^P), P = 63 - log2(L_d).
+ * fixed point as in 2D: A_c = round(a_c 2^P), P = 63 - log2(L_d); -2 when
+ * some a_c rounds to 0 (as in 2D).
  * ====================================================================== */
 int orc_ring_rate_table(double J, double beta, double h, int law, int log2_nd,
                         double a_out[6], uint64_t A_out[6])
@@ -694,6 +736,8 @@ int orc_ring_rate_table(double J, double beta, double h, int law, int log2_nd,
             A_out[c] = (uint64_t)nearbyint(ldexp(a, P));
         }
     }
+    for (int c = 0; c < 6; ++c)
+        if (A_out[c] == 0) return -2;
     return 0;
 }
 

@@ -87,6 +87,8 @@ def lib():
         L.orc_score_table.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, dp]
         L.orc_score_table.restype = ctypes.c_int
+        L.orc_sum_compensated.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int64]
+        L.orc_sum_compensated.restype = ctypes.c_double
         L.orc_run_replica_grad.argtypes = L.orc_run_replica.argtypes + [dp, dp]
         L.orc_run_replica_grad.restype = ctypes.c_int
         ra = L.orc_run_replica.argtypes
@@ -159,6 +161,8 @@ def rate_table(J: float, beta: float, h: float, law: int, log2_nd: int):
     A = np.zeros(10, dtype=np.uint64)
     rc = lib().orc_rate_table(J, beta, h, law, log2_nd, _ptr(a, ctypes.c_double),
                               _ptr(A, ctypes.c_uint64))
+    if rc == -2:
+        raise ValueError("an acceptance rounds to 0 at 2^-%d (one-way rate)" % (63 - log2_nd))
     if rc != 0:
         raise ValueError("invalid rate-table arguments")
     return a, A
@@ -189,6 +193,12 @@ def energy_mag(s: np.ndarray):
     m = ctypes.c_int64()
     lib().orc_energy_mag(_ptr(s, ctypes.c_int8), L, ctypes.byref(b), ctypes.byref(m))
     return b.value, m.value
+
+
+def sum_compensated(x) -> float:
+    """The oracle's compensated sum of a float64 sequence."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib().orc_sum_compensated(_ptr(x, ctypes.c_double), x.size))
 
 
 def score_table(J: float, beta: float, h: float, law: int) -> np.ndarray:
@@ -265,7 +275,9 @@ class Replica:
     flips: np.ndarray = field(default=None)
     sched_done: int = 0
     grad: np.ndarray = field(default=None)
-    score: np.ndarray = field(default=None)
+    # per domain: running sums of the score d log P / d(beta, h) and their
+    # compensations (the oracle's compensated summation)
+    score_acc: np.ndarray = field(default=None)
     dtau: float = 0.0  # domain time per visit (time mode TIME_HORIZON)
 
     def __post_init__(self):
@@ -286,7 +298,14 @@ class Replica:
     def enable_score(self):
         """Accumulate the likelihood-ratio score per domain from now on."""
         self.grad = score_table(self.J, self.beta, self.h, self.law)
-        self.score = np.zeros((self.n_domains, 2), dtype=np.float64)
+        self.score_acc = np.zeros((self.n_domains, 4), dtype=np.float64)
+
+    @property
+    def score(self):
+        """Per-domain score [n_domains, 2] (d/dbeta, d/dh), or None before enable_score."""
+        if self.score_acc is None:
+            return None
+        return self.score_acc[:, 0:2] + self.score_acc[:, 2:4]
 
     def run(self, n_sched: int, schedule: int = SCHED_PALINDROME,
             time_mode: int = TIME_EXPONENTIAL, obs_every: int = 0, obs_per_pass: bool = False) -> np.ndarray:
@@ -295,13 +314,13 @@ class Replica:
         passes = 8 if schedule == SCHED_PALINDROME else 4
         units = n_sched * passes if obs_per_pass else n_sched
         n_obs = units // obs_every if obs_every > 0 else 0
-        with_score = getattr(self, "score", None) is not None
+        with_score = self.score_acc is not None
         width = 6 if with_score else 4
         obs = np.zeros((max(n_obs, 1), width), dtype=np.float64)
         s = np.ascontiguousarray(self.spins.reshape(-1))
         A = np.ascontiguousarray(self.A)
         gptr = _ptr(self.grad, ctypes.c_double) if with_score else None
-        sptr = _ptr(self.score, ctypes.c_double) if with_score else None
+        sptr = _ptr(self.score_acc, ctypes.c_double) if with_score else None
         rc = lib().orc_run_replica_ex(
             _ptr(s, ctypes.c_int8), self.L, self.Ld, self.k, _ptr(A, ctypes.c_uint64),
             self.seed, schedule, time_mode, self.nu, self.J, self.h,
@@ -354,6 +373,8 @@ def ring_rate_table(J: float, beta: float, h: float, law: int, log2_nd: int):
     a = np.zeros(6, dtype=np.float64)
     A = np.zeros(6, dtype=np.uint64)
     rc = lib().orc_ring_rate_table(J, beta, h, law, log2_nd, _ptr(a, ctypes.c_double), _ptr(A, ctypes.c_uint64))
+    if rc == -2:
+        raise ValueError("an acceptance rounds to 0 at 2^-%d (one-way rate)" % (63 - log2_nd))
     if rc != 0:
         raise ValueError("invalid ring rate-table arguments")
     return a, A

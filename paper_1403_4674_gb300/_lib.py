@@ -27,8 +27,8 @@ STATUS_NAMES = {0: "KMC_OK", -1: "KMC_EINVAL", -2: "KMC_ENOMEM", -3: "KMC_ECUDA"
 #: every symbol include/kmc.h declares
 EXPORTS = [
     "kmc_create_lattice", "kmc_set_rates", "kmc_set_rate_table", "kmc_run_schedule",
-    "kmc_observables", "kmc_grad", "kmc_grad_nu", "kmc_lr_estimate", "kmc_enable_grad", "kmc_reset", "kmc_sync",
-    "kmc_domain_state", "kmc_get_rate_table", "kmc_set_launch", "kmc_get_launch", "kmc_set_replica_params", "kmc_set_observation", "kmc_set_horizon",
+    "kmc_observables", "kmc_grad", "kmc_grad_nu", "kmc_lr_estimate", "kmc_lr_observable", "kmc_enable_grad", "kmc_reset", "kmc_sync",
+    "kmc_domain_state", "kmc_get_rate_table", "kmc_rate_table_error", "kmc_set_launch", "kmc_get_launch", "kmc_set_replica_params", "kmc_set_observation", "kmc_set_horizon",
     "kmc_debug_barrier", "kmc_run_schedule_noalloc", "kmc_profile", "kmc_profile_read", "kmc_kernel_launches", "kmc_domain_side", "kmc_last_error", "kmc_destroy", "kmc_version",
     "kmc_ring_create", "kmc_ring_set_rates", "kmc_ring_run", "kmc_ring_state", "kmc_ring_last_error", "kmc_ring_destroy",
     "kmc_part_create", "kmc_part_set_rates", "kmc_part_run", "kmc_part_state", "kmc_part_last_error", "kmc_part_destroy",
@@ -67,6 +67,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmc_grad.argtypes = [vp, vp, i32]
     L.kmc_grad_nu.argtypes = [vp, vp]
     L.kmc_lr_estimate.argtypes = [vp, vp, vp]
+    L.kmc_lr_observable.argtypes = [vp, vp, i32, i32, vp]
     L.kmc_enable_grad.argtypes = [vp, i32]
     L.kmc_reset.argtypes = [vp, i32, vp]
     L.kmc_set_replica_params.argtypes = [vp, vp, vp]
@@ -75,6 +76,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmc_sync.argtypes = [vp]
     L.kmc_domain_state.argtypes = [vp, P(u64), P(i64), P(dbl)]
     L.kmc_get_rate_table.argtypes = [vp, i32, P(dbl), P(u64)]
+    L.kmc_rate_table_error.argtypes = [vp, P(dbl)]
     L.kmc_set_launch.argtypes = [vp, i32, i32, i32]
     L.kmc_get_launch.argtypes = [vp, P(i32), P(i32), P(i32), P(i32), P(i32)]
     L.kmc_debug_barrier.argtypes = [vp, i32, i64]

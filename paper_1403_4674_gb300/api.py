@@ -108,6 +108,12 @@ def kmc_get_rate_table(ctx, replica: int):
     return np.array(a[:]), np.array(A[:], dtype=np.uint64)
 
 
+def kmc_rate_table_error(ctx) -> float:
+    v = _dbl()
+    _check(ctx, load().kmc_rate_table_error(ctx, ctypes.byref(v)))
+    return v.value
+
+
 def kmc_grad(ctx, score_dev: torch.Tensor, reset: int = 0):
     if score_dev.dtype != torch.float64 or not score_dev.is_cuda:
         raise KmcError(-1, "score_dev must be a float64 CUDA tensor")
@@ -125,6 +131,15 @@ def kmc_lr_estimate(ctx, A_dev: torch.Tensor, grad_dev: torch.Tensor, stream=Non
         raise KmcError(-1, "A_dev and grad_dev must be float64 CUDA tensors")
     _check(ctx, load().kmc_lr_estimate(ctx, ctypes.c_void_p(A_dev.data_ptr()),
                                        ctypes.c_void_p(grad_dev.data_ptr())))
+
+
+def kmc_lr_observable(ctx, rec_dev: torch.Tensor, observable: int, out_dev: torch.Tensor, stream=None):
+    if rec_dev.dtype != torch.float64 or not rec_dev.is_cuda or rec_dev.dim() != 2 or rec_dev.stride(1) != 1:
+        raise KmcError(-1, "rec_dev must be a float64 CUDA tensor [n_replicas, width] with unit column stride")
+    if out_dev.dtype != torch.float64 or not out_dev.is_cuda or out_dev.numel() < 3 or not out_dev.is_contiguous():
+        raise KmcError(-1, "out_dev must be a contiguous float64 CUDA tensor of 3 elements")
+    _check(ctx, load().kmc_lr_observable(ctx, ctypes.c_void_p(rec_dev.data_ptr()), int(rec_dev.stride(0)),
+                                         int(observable), ctypes.c_void_p(out_dev.data_ptr())))
 
 
 def kmc_enable_grad(ctx, enable: bool):
@@ -182,9 +197,22 @@ def kmc_run_schedule_noalloc(L: int, L_d: int, k_steps: int, seed: int, J: float
                              nu: float, rate_law: int, sched_begin: int, n_schedules: int, schedule: int,
                              time_mode: int, obs_every: int, spins_dev: torch.Tensor,
                              obs_dev: Optional[torch.Tensor] = None, stream=None):
-    """One replica, no device allocation (see include/kmc.h); raises KmcError on failure."""
-    if spins_dev.dtype != torch.int8 or not spins_dev.is_cuda:
-        raise KmcError(-1, "spins_dev must be an int8 CUDA tensor")
+    """One replica, no device allocation (see include/kmc.h); raises KmcError on failure.
+
+    The C function receives bare pointers and cannot check buffer sizes, so
+    they are checked here: spins_dev holds at least L*L int8, and with
+    obs_every > 0 obs_dev holds at least (records) * 4 float64."""
+    if spins_dev.dtype != torch.int8 or not spins_dev.is_cuda or not spins_dev.is_contiguous():
+        raise KmcError(-1, "spins_dev must be a contiguous int8 CUDA tensor")
+    if spins_dev.numel() < int(L) * int(L):
+        raise KmcError(-1, "spins_dev holds %d bytes, %d needed" % (spins_dev.numel(), int(L) * int(L)))
+    if obs_every > 0:
+        n_rec = int(n_schedules) // int(obs_every)
+        if n_rec > 0:
+            if obs_dev is None or obs_dev.dtype != torch.float64 or not obs_dev.is_cuda or not obs_dev.is_contiguous():
+                raise KmcError(-1, "obs_dev must be a contiguous float64 CUDA tensor when obs_every > 0")
+            if obs_dev.numel() < n_rec * 4:
+                raise KmcError(-1, "obs_dev holds %d doubles, %d needed" % (obs_dev.numel(), n_rec * 4))
     err = ctypes.create_string_buffer(256)
     obs_ptr = ctypes.c_void_p(obs_dev.data_ptr()) if obs_dev is not None else ctypes.c_void_p()
     st = load().kmc_run_schedule_noalloc(L, L_d, k_steps, seed, J, beta, h, nu, rate_law, sched_begin,
@@ -283,6 +311,10 @@ class Lattice:
     def rate_table(self, r: int = 0):
         return kmc_get_rate_table(self.ctx, r)
 
+    def rate_table_error(self) -> float:
+        """Largest relative change |A_c 2^-P - a_c| / a_c of an acceptance by the fixed point."""
+        return kmc_rate_table_error(self.ctx)
+
     def enable_grad(self, enable: bool = True):
         kmc_enable_grad(self.ctx, enable)
         self.grad_enabled = bool(enable)
@@ -302,6 +334,15 @@ class Lattice:
         """d E[A] / d(beta, h) from per-replica A and the accumulated scores."""
         out = torch.empty(2, dtype=torch.float64, device=self.spins.device)
         kmc_lr_estimate(self.ctx, A.contiguous(), out)
+        return out
+
+    def lr_observable(self, record: torch.Tensor, observable: int) -> torch.Tensor:
+        """[mean A, dE[A]/dbeta, dE[A]/dh] of observable 0 (e), 1 (m) or 2 (e*m)
+        from one record row [n_replicas, width] and the accumulated scores."""
+        if record.shape[0] != self.n_replicas:
+            raise KmcError(-1, "record must have one row per replica")
+        out = torch.empty(3, dtype=torch.float64, device=self.spins.device)
+        kmc_lr_observable(self.ctx, record, observable, out)
         return out
 
     def reset(self, init: int = KMC_INIT_RANDOM, stream=None):

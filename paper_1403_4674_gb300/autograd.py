@@ -4,13 +4,15 @@
 replica mean of an endpoint observable (Sec. 2.3) as a differentiable function
 of the inverse temperature and the field.  Its backward pass uses the
 likelihood-ratio (score-function) estimator
-    d E[A] / d theta = E[(A - E A) * d log P(path) / d theta],
+    d E[A] / d theta = Cov(A, d log P(path) / d theta) + E[dA/dtheta explicit],
 with the path score accumulated by the run kernel (App. A: each uniformised
-step has probability a_c/n_d or 1 - R/n_d) and the covariance taken by the
-library's estimate kernel, plus the explicit dependence of the observable on
-h (e = -J bonds/N - h m).  ``burn_in`` schedules run before the score is
-reset, so the gradient is that of E[A] after ``n_schedules`` more schedules
-from the state distribution reached by then (a checkpointed segment).
+step has probability a_c/n_d or 1 - R/n_d).  The library computes the replica
+mean, the covariance and the explicit dependence of the observable on h
+(e = -J bonds/N - h m) in one call (``kmc_lr_observable``); this module only
+passes arguments and hands the library's numbers to autograd.  ``burn_in``
+schedules run before the score is reset, so the gradient is that of E[A]
+after ``n_schedules`` more schedules from the state distribution reached by
+then (a checkpointed segment).
 """
 from __future__ import annotations
 
@@ -27,10 +29,8 @@ class _KmcExpectation(torch.autograd.Function):
                 observable: int, burn_in: int, law: int, init: int):
         lat = lattice
         nrep = lat.n_replicas
-        b = float(beta.item())
-        hv = float(h.item())
         lat.reset(init)
-        lat.set_rates([b] * nrep, [hv] * nrep, law=law)
+        lat.set_rates([float(beta.item())] * nrep, [float(h.item())] * nrep, law=law)
         if not lat.grad_enabled:
             lat.enable_grad(True)
         if burn_in > 0:
@@ -38,24 +38,15 @@ class _KmcExpectation(torch.autograd.Function):
             lat.score(reset=True)
         obs = lat.run(n_schedules, schedule=KMC_SCHEDULE_PALINDROME, time_mode=KMC_TIME_EXPONENTIAL,
                       obs_every=n_schedules)
-        A = obs[-1, :, observable].contiguous()
-        grad = lat.lr_estimate(A)
-        # e = -J bonds/N - h m and e*m depend on h explicitly as well:
-        # d e/dh = -m, d(e m)/dh = -m^2 (m has no explicit dependence)
-        m = obs[-1, :, 1]
-        if observable == 0:
-            grad[1] += -m.mean()
-        elif observable == 2:
-            grad[1] += -(m * m).mean()
-        ctx.save_for_backward(grad)
-        return A.mean().to(beta.dtype)
+        out = lat.lr_observable(obs[-1], observable)  # [mean A, dE[A]/dbeta, dE[A]/dh]
+        ctx.save_for_backward(out)
+        return out[0].to(beta.dtype)
 
     @staticmethod
     def backward(ctx, g):
-        (grad,) = ctx.saved_tensors
-        gb = (g * grad[0]).to(g.dtype)
-        gh = (g * grad[1]).to(g.dtype)
-        return gb, gh, None, None, None, None, None, None
+        (out,) = ctx.saved_tensors
+        # autograd's chain rule: the incoming gradient times the library's derivatives
+        return (g * out[1]).to(g.dtype), (g * out[2]).to(g.dtype), None, None, None, None, None, None
 
 
 def expectation(lattice: Lattice, beta: torch.Tensor, h: torch.Tensor, n_schedules: int,

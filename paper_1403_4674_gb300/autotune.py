@@ -270,7 +270,7 @@ class Batch:
         self._alloc_obs(n_sched, obs_every)
         return self.step(n_sched, obs_every, reset)
 
-    def capture(self, n_sched: int, obs_every: int = 0, reset: int = KMC_INIT_RANDOM) -> torch.cuda.CUDAGraph:
+    def capture(self, n_sched: int, obs_every: int = 0, reset: int = KMC_INIT_RANDOM) -> "BatchGraph":
         """One CUDA graph for a whole batch step (reset, then n_sched
         schedules on every group).  Buffers are sized by an eager step first;
         replaying the graph repeats the same trajectories from the reset."""
@@ -283,7 +283,23 @@ class Batch:
             with torch.cuda.graph(g, stream=cap):
                 self.step(n_sched, obs_every, reset)
         torch.cuda.current_stream().wait_stream(cap)
-        return g
+        return BatchGraph(g, "kmc batch step: %d replicas in %d groups, %d schedules"
+                          % (sum(len(l.L) for l in self.lattices), len(self.lattices), n_sched))
+
+
+class BatchGraph:
+    """A captured batch step; each replay is one NVTX range (Nsight Systems)."""
+
+    def __init__(self, graph: torch.cuda.CUDAGraph, name: str):
+        self.graph = graph
+        self.name = name
+
+    def replay(self):
+        torch.cuda.nvtx.range_push(self.name)
+        try:
+            self.graph.replay()
+        finally:
+            torch.cuda.nvtx.range_pop()
 
     def sync(self):
         for lat, st in zip(self.lattices, self.streams):

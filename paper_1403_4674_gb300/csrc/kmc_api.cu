@@ -11,6 +11,7 @@
 #include "kmc_part.cuh"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -188,6 +189,36 @@ void build_table(double J, double beta, double h, int law, int log2nd, double *a
         gh[c] = dlh;
     }
 }
+
+// First class whose fixed-point acceptance A_c rounded to 0 (n entries), or
+// -1.  Every a_c of either law is positive for finite beta, so A_c = 0 would
+// give the quantised chain a one-way rate: the flip out of class c never
+// happens while its reverse does, and detailed balance (Eq. 4) fails.
+int zero_rate_class(const uint64_t *A, int n)
+{
+    for (int c = 0; c < n; ++c)
+        if (A[c] == 0) return c;
+    return -1;
+}
+
+// NVTX range for the host span of one entry point that enqueues device work
+// (visible in Nsight Systems, and usable as an Nsight Compute filter with
+// --nvtx-include "kmc_run_schedule/"); the calls do nothing unless a tool
+// is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *fmt, ...)
+    {
+        char buf[160];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Status of a failed cudaMalloc: out of device memory, or any other CUDA
 // failure (no device, driver too old, a sticky error of the context).
@@ -634,30 +665,48 @@ kmc_status launch_observe(kmc_ctx *c, cudaStream_t s, int time_mode, unsigned lo
     return KMC_OK;
 }
 
-// Fixed-point products a_c dlog a_c / d(beta, h) for the score of null steps:
-// round(x 2^Q) with Q <= 40 chosen so that n_d sum_c |x_c| 2^Q < 2^62 (the
-// device sums n_c x_c 2^Q over the classes in int64), and 2^-Q.
-void build_gfix(const double *a, const double *gb, const double *gh, int log2nd, int64_t *out)
+// Fixed-point products x_c = a_c dlog a_c / d(beta, h) for the score of null
+// steps, in two words: X_c = round(x_c 2^Q) (int64) and the low word Y_c =
+// round((x_c 2^Q - X_c) 2^GFIX_LO_BITS) (int32, |Y_c| <= 2^17).  Q is as large
+// as keeps the device's per-state sum sum_c n_c X_c 2^GFIX_T_BITS inside
+// int64: sum_c n_c |x_c| 2^Q < n_d 2^e 2^Q = 2^58 with |x_c| < 2^e.  Also
+// stores 2^-(Q + GFIX_T_BITS), the unit of the combined per-state sum.
+// Returns false when Q would fall below 8 fraction bits (|a dlog a| of order
+// 2^(50 - log2 n_d) or more).
+bool build_gfix(const double *a, const double *gb, const double *gh, int log2nd, int64_t *out)
 {
     double mx = 0.0;
     for (int c = 0; c < 10; ++c) mx = std::max(mx, std::max(std::fabs(a[c] * gb[c]), std::fabs(a[c] * gh[c])));
-    // Q as large as the int64 sums allow: sum_c n_c |a_c dlog a_c| 2^Q <
-    // n_d 2^e 2^Q = 2^58.  (The null-step score sums about one term per state
-    // over a run, so the products' rounding, 2^-Q-1 each, is what limits the
-    // score's agreement with exact arithmetic over long runs.)
     int Q = 62;
     if (mx > 0.0) {
         int e = 0;
         std::frexp(mx, &e); // mx < 2^e
-        Q = std::max(0, std::min(62, 58 - log2nd - e));
+        Q = std::min(62, 58 - log2nd - e);
+        if (Q < 8) return false;
     }
+    int32_t *yb = reinterpret_cast<int32_t *>(&out[GFIX_YB]);
+    int32_t *yh = reinterpret_cast<int32_t *>(&out[GFIX_YH]);
+    // x_c = a_c * g_c as the exact real product of the two doubles: the
+    // rounded product p and its rounding error fma(a, g, -p) (exact), so
+    // that the words do not carry the product's rounding, which would be the
+    // same in every state.  p 2^Q is exact (power-of-two scaling) and so is
+    // its difference from the nearest integer.
+    auto split = [&](double av, double gv, int64_t &X, int32_t &Y) {
+        const double p = av * gv;
+        const double perr = std::fma(av, gv, -p);
+        const double x = std::ldexp(p, Q);
+        const double Xd = std::nearbyint(x);
+        X = (int64_t)Xd;
+        Y = (int32_t)std::nearbyint(std::ldexp((x - Xd) + std::ldexp(perr, Q), GFIX_LO_BITS));
+    };
     for (int c = 0; c < 10; ++c) {
-        out[c] = (int64_t)std::llround(std::ldexp(a[c] * gb[c], Q));
-        out[10 + c] = (int64_t)std::llround(std::ldexp(a[c] * gh[c], Q));
+        split(a[c], gb[c], out[c], yb[c]);
+        split(a[c], gh[c], out[10 + c], yh[c]);
     }
-    const double scale = std::ldexp(1.0, -Q);
+    const double scale = std::ldexp(1.0, -(Q + GFIX_T_BITS));
     std::memcpy(&out[20], &scale, 8);
-    out[21] = out[22] = out[23] = 0;
+    out[21] = 0;
+    return true;
 }
 
 kmc_status sync_ctx(kmc_ctx *c);
@@ -733,8 +782,9 @@ kmc_status upload_rates(kmc_ctx *c)
     // sources are pageable, so each copy has consumed them when the call returns
     CUDA_TRY(c, cudaMemcpyAsync(c->d_A, A16.data(), A16.size() * 8, cudaMemcpyHostToDevice, c->stream));
     for (int r = 0; r < c->n_rep; ++r)
-        build_gfix(&c->a[(size_t)r * 10], &c->gb[(size_t)r * 10], &c->gh[(size_t)r * 10], c->log2nd,
-                   &gfix[(size_t)r * GFIX_WORDS]);
+        if (!build_gfix(&c->a[(size_t)r * 10], &c->gb[(size_t)r * 10], &c->gh[(size_t)r * 10], c->log2nd,
+                        &gfix[(size_t)r * GFIX_WORDS]))
+            return fail(c, KMC_EINVAL, "replica %d: score products a_c dlog a_c too large for fixed point", r);
     CUDA_TRY(c, cudaMemcpyAsync(c->d_gfix, gfix.data(), gfix.size() * 8, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_grad, g32.data(), g32.size() * 8, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_h, c->h.data(), c->h.size() * 8, cudaMemcpyHostToDevice, c->stream));
@@ -1058,8 +1108,14 @@ kmc_status kmc_set_rates(kmc_ctx *c, double J, const double *beta, const double 
     const size_t n = (size_t)c->n_rep * 10;
     std::vector<double> a(n), gb(n), gh(n);
     std::vector<uint64_t> A(n);
-    for (int r = 0; r < c->n_rep; ++r)
+    for (int r = 0; r < c->n_rep; ++r) {
         build_table(J, beta[r], h[r], rate_law, c->log2nd, &a[r * 10], &A[r * 10], &gb[r * 10], &gh[r * 10]);
+        const int z = zero_rate_class(&A[r * 10], 10);
+        if (z >= 0)
+            return fail(c, KMC_ENOTBALANCED,
+                        "replica %d class %d: a_c = %.3g rounds to 0 at 2^-%d; the quantised chain would have a "
+                        "one-way rate (Eq. 4)", r, z, a[r * 10 + z], 63 - c->log2nd);
+    }
     c->J = J;
     c->nu = nu;
     c->law = rate_law;
@@ -1098,6 +1154,10 @@ kmc_status kmc_set_rate_table(kmc_ctx *c, double J, const double *beta, const do
                             "replica %d class %d: a_c/a_cbar = %.17g but exp(-beta dE) = %.17g (detailed balance, Eq. 4)",
                             r, q, ratio, want);
             A[r * 10 + q] = (uint64_t)std::nearbyint(std::ldexp(ac, P));
+            if (A[r * 10 + q] == 0)
+                return fail(c, KMC_ENOTBALANCED,
+                            "replica %d class %d: a_c = %.3g rounds to 0 at 2^-%d; the quantised chain would have a "
+                            "one-way rate (Eq. 4)", r, q, ac, P);
         }
     }
     c->J = J;
@@ -1109,6 +1169,20 @@ kmc_status kmc_set_rate_table(kmc_ctx *c, double J, const double *beta, const do
     c->gb = gb; // no closed-form derivatives for a user table
     c->gh = gh;
     return upload_rates(c);
+}
+
+kmc_status kmc_rate_table_error(const kmc_ctx *c, double *max_rel_err)
+{
+    if (!c || !max_rel_err) return KMC_EINVAL;
+    if (c->a.empty()) return KMC_EINVAL; // no table yet
+    const int P = 63 - c->log2nd;
+    double worst = 0.0;
+    for (size_t i = 0; i < c->a.size(); ++i) {
+        const double q = std::ldexp((double)c->A[i], -P); // exact: A_c < 2^53 or a multiple of its ulp
+        worst = std::max(worst, std::fabs(q - c->a[i]) / c->a[i]);
+    }
+    *max_rel_err = worst;
+    return KMC_OK;
 }
 
 kmc_status kmc_get_rate_table(const kmc_ctx *c, int32_t replica, double *a, uint64_t *A)
@@ -1263,6 +1337,8 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     if (c->sched_done + n_schedules >= (1ll << 52)) return fail(c, KMC_EINVAL, "schedule index overflow");
     c->stream = (cudaStream_t)stream;
     if (n_schedules == 0) return KMC_OK;
+    NvtxRange range("kmc_run_schedule %d replicas L_d=%d %lld schedules%s", c->n_rep, c->LD,
+                    (long long)n_schedules, c->grad ? " scores" : "");
     cudaStream_t s = c->stream;
     kmc_status st;
     const bool want_obs = obs_every > 0 && obs_dev != nullptr;
@@ -1479,6 +1555,8 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     c.gb.resize(10);
     c.gh.resize(10);
     build_table(J, beta, h, rate_law, c.log2nd, c.a.data(), c.A.data(), c.gb.data(), c.gh.data());
+    if (zero_rate_class(c.A.data(), 10) >= 0)
+        return bad(KMC_ENOTBALANCED, "an acceptance a_c rounds to 0 in fixed point (one-way rate, Eq. 4)");
 
     cudaError_t ce = cudaGetDevice(&c.dev);
     if (ce != cudaSuccess) return bad(KMC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
@@ -1559,7 +1637,7 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     cudaStream_t s = c.stream;
     std::vector<uint64_t> A16(16, 0);
     std::vector<int64_t> gfix(GFIX_WORDS, 0);
-    build_gfix(c.a.data(), c.gb.data(), c.gh.data(), c.log2nd, gfix.data());
+    (void)build_gfix(c.a.data(), c.gb.data(), c.gh.data(), c.log2nd, gfix.data()); // staged, unused: no scores here
     std::vector<double> g32(32, 0.0);
     for (int q = 0; q < 10; ++q) {
         A16[q] = c.A[q];
@@ -1622,11 +1700,9 @@ kmc_status kmc_run_schedule_noalloc(int32_t L, int32_t L_d, int32_t k_steps, uin
     }
     // synchronising: the device error word lives in the shared array
     st = sync_ctx(&c);
-    // the kmc_ctx destructor must not free the static array
-    c.d_L = nullptr; c.d_Dx = nullptr; c.d_k = nullptr; c.d_dom_off = nullptr; c.d_dom_rep = nullptr; c.d_site_off = nullptr;
-    c.d_blk_off = nullptr; c.d_seed = nullptr; c.d_A = nullptr; c.d_gfix = nullptr; c.d_grad = nullptr; c.d_h = nullptr;
-    c.d_tiles = nullptr; c.d_edges = nullptr; c.d_dctr = nullptr; c.d_tmp = nullptr; c.d_err = nullptr;
-    c.d_obs_acc = nullptr; c.d_plan = nullptr;
+    // c lives on this stack frame and is never handed to free_all or
+    // kmc_destroy (the only places that free device memory), so its device
+    // pointers into the static array are simply dropped here
     if (st != KMC_OK) return bad(st, c.err);
     noalloc_message(err, err_len, "");
     return KMC_OK;
@@ -1637,7 +1713,27 @@ kmc_status kmc_lr_estimate(kmc_ctx *c, const double *A_dev, double *grad_dev)
     if (!c) return KMC_EINVAL;
     if (!A_dev || !grad_dev) return fail(c, KMC_EINVAL, "A_dev and grad_dev required");
     if (c->n_rep < 2) return fail(c, KMC_EINVAL, "the estimate needs at least two replicas");
-    lr_estimate_kernel<<<1, 256, 0, c->stream>>>(A_dev, c->d_dctr, c->d_dom_off, c->n_rep, grad_dev);
+    // the kernel writes {mean, d/dbeta, d/dh}: the mean goes to scratch
+    double *out3 = reinterpret_cast<double *>(c->d_tmp);
+    lr_estimate_kernel<<<1, 256, 0, c->stream>>>(A_dev, nullptr, 1, 0, c->d_dctr, c->d_dom_off, c->n_rep, out3);
+    ++c->launches;
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(grad_dev, out3 + 1, 2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return KMC_OK;
+}
+
+kmc_status kmc_lr_observable(kmc_ctx *c, const double *rec_dev, int32_t stride, int32_t observable, double *out_dev)
+{
+    if (!c) return KMC_EINVAL;
+    if (!rec_dev || !out_dev) return fail(c, KMC_EINVAL, "rec_dev and out_dev required");
+    if (observable < 0 || observable > 2) return fail(c, KMC_EINVAL, "observable must be 0 (e), 1 (m) or 2 (e*m)");
+    if (stride < 4) return fail(c, KMC_EINVAL, "stride must be at least 4 (a record holds e, m, e*m, T)");
+    if (c->n_rep < 2) return fail(c, KMC_EINVAL, "the estimate needs at least two replicas");
+    // explicit h-dependence: e = (-J bonds - h M)/N gives de/dh = -m and
+    // d(e m)/dh = -m^2; m has none, and none of them depends on beta
+    const int xsel = (observable == 0) ? 1 : (observable == 2) ? 2 : 0;
+    lr_estimate_kernel<<<1, 256, 0, c->stream>>>(rec_dev + observable, rec_dev + 1, stride, xsel, c->d_dctr,
+                                                 c->d_dom_off, c->n_rep, out_dev);
     ++c->launches;
     CUDA_TRY(c, cudaGetLastError());
     return KMC_OK;
@@ -1782,6 +1878,10 @@ kmc_status kmc_ring_set_rates(kmc_ring *g, double J, const double *beta, const d
         if (!(beta[i] >= 0.0) || !std::isfinite(beta[i]) || !std::isfinite(h[i]))
             return ring_fail(g, KMC_EINVAL, "trajectory %d: beta >= 0 and finite h required", i);
         ring_table(J, beta[i], h[i], rate_law, g->log2nd, &a[(size_t)i * nc], &A[(size_t)i * nc]);
+        const int z = zero_rate_class(&A[(size_t)i * nc], nc);
+        if (z >= 0)
+            return ring_fail(g, KMC_ENOTBALANCED, "trajectory %d class %d: a_c = %.3g rounds to 0 in fixed point "
+                             "(one-way rate, Eq. 4)", i, z, a[(size_t)i * nc + z]);
         for (int c = 0; c < nc; ++c) {
             const int up = c / 3, q = c % 3;
             const double dE = 2.0 * (up ? 1.0 : -1.0) * (J * (double)(2 * q - 2) + h[i]);
@@ -1877,6 +1977,7 @@ kmc_status kmc_ring_run(kmc_ring *g, int64_t n_schedules, int32_t schedule, int3
     if (ens_dev && n_rec > 0)
         RING_CUDA_TRY(g, cudaMemsetAsync(ens_dev, 0, (size_t)n_rec * (kmcring::RING_ENS_FIXED + g->NS) * 8, g->stream));
     if (n_schedules == 0) return KMC_OK;
+    NvtxRange range("kmc_ring_run %d trajectories N_S=%d %lld schedules", g->n_traj, g->NS, (long long)n_schedules);
     kmcring::RingParams P;
     P.n_traj = g->n_traj;
     P.NS = g->NS;
@@ -2011,6 +2112,10 @@ kmc_status kmc_part_set_rates(kmc_part *g, double J, const double *beta, const d
             return part_fail(g, KMC_EINVAL, "trajectory %d: beta >= 0 and finite h required", i);
         // A_c = round(a_c 2^P), P = 63 - ceil(log2 n_d): the lattice table with log2 n_d rounded up
         build_table(J, beta[i], h[i], rate_law, 63 - g->P, &a[(size_t)i * 10], &A[(size_t)i * 10], gb.data(), gh.data());
+        const int z = zero_rate_class(&A[(size_t)i * 10], 10);
+        if (z >= 0)
+            return part_fail(g, KMC_ENOTBALANCED, "trajectory %d class %d: a_c = %.3g rounds to 0 in fixed point "
+                             "(one-way rate, Eq. 4)", i, z, a[(size_t)i * 10 + z]);
         for (int c = 0; c < 10; ++c) {
             const int up = c / 5, q = c % 5;
             const double dE = 2.0 * (up ? 1.0 : -1.0) * (J * (double)(2 * q - 4) + h[i]);
@@ -2129,6 +2234,8 @@ kmc_status kmc_part_run(kmc_part *g, int64_t n_schedules, int32_t schedule, int3
                        : (schedule == KMC_SCHEDULE_PALINDROME ? 2 * g->ncol : g->ncol);
     const int64_t n_rec = obs_every > 0 ? n_schedules * passes / obs_every : 0;
     g->stream = (cudaStream_t)stream;
+    NvtxRange range("kmc_part_run %d trajectories L=%d N_D=%d %lld schedules", g->n_traj, g->L, g->ND,
+                    (long long)n_schedules);
     kmcpart::PartParams P;
     P.n_traj = g->n_traj;
     P.L = g->L;

@@ -52,13 +52,21 @@ constexpr int OBS_WORDS = 5; // bonds, mag, clock sum, score beta sum, score h s
 
 // Replica table staged in shared memory (bytes):
 //   [0,128) A[16] fixed-point acceptance,
-//   [128,256) Gb[16] = round(a dlog a/dbeta 2^Q) (int64, scores),
+//   [128,256) Gb[16] = X_c = round(a dlog a/dbeta 2^Q) (int64, scores),
 //   [256,512) grad[32] = a[10], dlog a/dbeta[10], dlog a/dh[10],
 //   [512] seed, [520] dom_off, [524] Dx, [528] k (steps per visit),
-//   [544,624) Gh[10] = round(a dlog a/dh 2^Q), [624] 2^-Q (double).
-constexpr int RT_BYTES = 640;
-constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524, RT_K = 528, RT_GB = 128, RT_GH = 544, RT_GSCALE = 624;
-constexpr int GFIX_WORDS = 24; // per replica: Gb[10], Gh[10], 2^-Q bits, pad
+//   [544,624) Gh[10] = X_c of dlog a/dh, [624] 2^-(Q+4) (double),
+//   [640,680) Yb[10], [680,720) Yh[10]: the low words Y_c = round((a dlog a
+//   2^Q - X_c) 2^GFIX_LO_BITS) (int32), so that X_c 2^-Q + Y_c 2^-(Q+18)
+//   holds a dlog a to 2^-(Q+19).
+constexpr int RT_BYTES = 720;
+constexpr int RT_SEED = 512, RT_DOMOFF = 520, RT_DX = 524, RT_K = 528, RT_GB = 128, RT_GH = 544, RT_GSCALE = 624,
+              RT_YB = 640, RT_YH = 680;
+// per replica: Xb[10], Xh[10], 2^-(Q+4) bits, pad, Yb[10] and Yh[10] as
+// int32 pairs in words 22..26 and 27..31
+constexpr int GFIX_WORDS = 32, GFIX_YB = 22, GFIX_YH = 27;
+constexpr int GFIX_LO_BITS = 18; // fraction bits of the low word beyond 2^-Q
+constexpr int GFIX_T_BITS = 4;   // fraction bits of the combined per-state sum beyond 2^-Q
 // Slot: [tile][stamped edges 64][counters 56][meta 32][observation 48];
 // meta u32: g, replica, d, rt, nb[4];
 // observation, since the record began: u32 record, i32 bond change, i32
@@ -510,31 +518,19 @@ __device__ __forceinline__ int horizon_steps(uint2 key, uint32_t d, uint64_t np,
     return 32 * b + __ffs(mk) - 1;
 }
 
-// Lane c (< 10) holds class c's fixed-point rate and (scores) dlog a_c /
-// d(beta, h) and the fixed-point products a_c dlog a_c / d(beta, h); loaded
-// before the halo wait.
+// Lane c (< 10) holds class c's fixed-point rate, loaded before the halo
+// wait; the score constants stay in the replica table in shared memory
+// (rt) and are read where a state or an event needs them.
 struct RateRegs {
     uint64_t A;
-    double gb, gh;
-    int64_t Gb, Gh;
-    double gscale;
+    const uint8_t *rt;
 };
 
 template <bool GRAD>
 __device__ __forceinline__ RateRegs load_rates(const uint8_t *rt, int lane)
 {
-    RateRegs r = {0ull, 0.0, 0.0, 0, 0, 0.0};
-    if (lane < 10) {
-        r.A = reinterpret_cast<const uint64_t *>(rt)[lane];
-        if (GRAD) {
-            const double *gr = reinterpret_cast<const double *>(rt + 256);
-            r.gb = gr[10 + lane];
-            r.gh = gr[20 + lane];
-            r.Gb = reinterpret_cast<const int64_t *>(rt + RT_GB)[lane];
-            r.Gh = reinterpret_cast<const int64_t *>(rt + RT_GH)[lane];
-        }
-    }
-    if (GRAD) r.gscale = *reinterpret_cast<const double *>(rt + RT_GSCALE);
+    RateRegs r = {0ull, rt};
+    if (lane < 10) r.A = reinterpret_cast<const uint64_t *>(rt)[lane];
     return r;
 }
 
@@ -572,7 +568,6 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
     // 64-bit integers are converted in two 32-bit halves (the 64-bit integer
     // conversion runs on the FP64 unit).
     const float invAf = (lane < 10) ? __frcp_rd(u64_to_float_ru(Ac)) : 0.0f;
-    const double gb_c = rr.gb, gh_c = rr.gh;
     pl.add_halo(lane, hN, hS, hW, hE); // pl holds the interior counts
     uint32_t n_c = class_counts<LD>(pl, lane);
     uint64_t Wc = (uint64_t)n_c * Ac;
@@ -580,30 +575,50 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
     uint64_t R = __shfl_sync(FULL_WARP, Cinc, 9);
 
     // Score of a null step in the current state: d log(1 - R/n_d) =
-    // -sum_c n_c a_c dlog a_c / (n_d - R).  The numerator is an exact int64
-    // sum of the fixed-point products a_c dlog a_c 2^Q, and n_d - R comes
-    // from the exact fixed-point rate sum, (n_d 2^P - R') 2^-P with
-    // n_d 2^P = 2^63; one FP64 reciprocal per state.  It is formed only for
-    // states that have null steps (a real event that directly follows another
-    // needs none): FP64 is this GPU's slowest pipe.
+    // -sum_c n_c a_c dlog a_c / (n_d - R).  The numerator is an exact
+    // integer sum of the two fixed-point words of a_c dlog a_c (high word
+    // X_c at 2^-Q, low word Y_c at 2^-(Q+18)), rounded once per state to
+    // 2^-(Q+4); n_d - R comes from the exact fixed-point rate sum,
+    // (n_d 2^P - R') 2^-P with n_d 2^P = 2^63.  A single fixed-point word
+    // would round every class product the same way in every state, a bias
+    // that grows linearly over a run's millions of null-step states; with the
+    // low word the per-class error is 2^-(Q+19) and what remains are FP64
+    // roundings that change from state to state.  One reciprocal per state,
+    // formed only for states that have null steps (a real event that
+    // directly follows another needs none): FP64 is this GPU's slowest pipe.
     double nb_over = 0.0, nh_over = 0.0;
     bool state_scored = false; // nb_over / nh_over belong to the current state (warp-uniform)
     constexpr int PBITS = 63 - 2 * (LD == 8 ? 3 : LD == 16 ? 4 : LD == 32 ? 5 : 6);
-    // 2^-Q 2^P: a power of two, so the scaling below is exact
-    const double scaleP = GRAD ? rr.gscale * (double)(1ull << PBITS) : 0.0;
     auto grad_state = [&]() {
         if (GRAD) {
-            const int64_t sb = warp_isum16((int64_t)n_c * rr.Gb), sh = warp_isum16((int64_t)n_c * rr.Gh);
+            const uint8_t *rt = rr.rt;
+            const bool cl = lane < 10;
+            const int64_t Xb = cl ? reinterpret_cast<const int64_t *>(rt + RT_GB)[lane] : 0;
+            const int64_t Xh = cl ? reinterpret_cast<const int64_t *>(rt + RT_GH)[lane] : 0;
+            const int Yb = cl ? reinterpret_cast<const int32_t *>(rt + RT_YB)[lane] : 0;
+            const int Yh = cl ? reinterpret_cast<const int32_t *>(rt + RT_YH)[lane] : 0;
+            // 2^-(Q+4) 2^P: a power of two, so the scaling below is exact
+            const double scaleP = *reinterpret_cast<const double *>(rt + RT_GSCALE) * (double)(1ull << PBITS);
+            const int64_t xb = warp_isum16((int64_t)n_c * Xb), xh = warp_isum16((int64_t)n_c * Xh);
+            // |n_c Y_c| <= n_d 2^17 <= 2^29: exact in one 32-bit warp reduction
+            const int yb = __reduce_add_sync(FULL_WARP, (int)n_c * Yb);
+            const int yh = __reduce_add_sync(FULL_WARP, (int)n_c * Yh);
+            constexpr int SH = GFIX_LO_BITS - GFIX_T_BITS;
+            const int64_t tb = xb * (1ll << GFIX_T_BITS) + (int64_t)((yb + (1 << (SH - 1))) >> SH);
+            const int64_t th = xh * (1ll << GFIX_T_BITS) + (int64_t)((yh + (1 << (SH - 1))) >> SH);
             const uint64_t gap = (1ull << 63) - R;
-            // 2^-P / (n_d - R) = 1/gap: one Newton-Raphson step x + x (1 - gap x)
-            // from the FP32 reciprocal (relative error below 2^-44, far inside
-            // the score's tolerance; two FP64 fused multiply-adds)
+            // 2^-P / (n_d - R) = 1/gap from the FP32 reciprocal x0 = (1 - e)/g:
+            // x0 (1 + e + e^2) = (1 - e^3)/g, |e| < 2^-21, so the truncation
+            // error 2^-63 stays below FP64 rounding (the plain Newton-Raphson
+            // step x0 (1 + e) would leave a one-sided error e^2 ~ 2^-44 in
+            // every state).  Three FP64 fused multiply-adds.
             const double g = __ull2double_rn(gap);
             const double x0 = (double)__frcp_rn(u64_to_float_rz(gap));
-            const double inv = gap ? __fma_rn(x0, __fma_rn(-g, x0, 1.0), x0) : 0.0;
+            const double e = __fma_rn(-g, x0, 1.0);
+            const double inv = gap ? __fma_rn(x0, __fma_rn(e, e, e), x0) : 0.0;
             const double w = inv * scaleP;
-            nb_over = (double)sb * w;
-            nh_over = (double)sh * w;
+            nb_over = (double)tb * w;
+            nh_over = (double)th * w;
             state_scored = true;
         }
     };
@@ -644,8 +659,10 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             q = (x - (uint64_t)q * Ac >= Ac) ? q + 1u : q;
             const uint32_t jj = __shfl_sync(FULL_WARP, q, c);
             if (GRAD) {
-                cn.sb += __shfl_sync(FULL_WARP, gb_c, c);
-                cn.sh += __shfl_sync(FULL_WARP, gh_c, c);
+                // dlog a_c / d(beta, h) of the chosen class (a broadcast read)
+                const double *gr = reinterpret_cast<const double *>(rr.rt + 256);
+                cn.sb += gr[10 + c];
+                cn.sh += gr[20 + c];
             }
             // rank selection: jj-th member of class c in row-major order
             const int qc = (c >= 5) ? c - 5 : c;
@@ -866,7 +883,12 @@ __global__ void __maxnreg__((run_kernel_regs<LD, GRAD>())) run_kernel(const RunP
             reinterpret_cast<uint64_t *>(t)[lane] = P.rep_A[(size_t)r * 16 + lane];
             reinterpret_cast<int64_t *>(t + RT_GB)[lane] = (lane < 10) ? P.rep_gfix[(size_t)r * GFIX_WORDS + lane] : 0;
         }
-        if (lane < 10) reinterpret_cast<int64_t *>(t + RT_GH)[lane] = P.rep_gfix[(size_t)r * GFIX_WORDS + 10 + lane];
+        if (lane < 10) {
+            reinterpret_cast<int64_t *>(t + RT_GH)[lane] = P.rep_gfix[(size_t)r * GFIX_WORDS + 10 + lane];
+            const int32_t *lo = reinterpret_cast<const int32_t *>(P.rep_gfix + (size_t)r * GFIX_WORDS);
+            reinterpret_cast<int32_t *>(t + RT_YB)[lane] = lo[2 * GFIX_YB + lane];
+            reinterpret_cast<int32_t *>(t + RT_YH)[lane] = lo[2 * GFIX_YH + lane];
+        }
         if (lane == 10) *reinterpret_cast<int64_t *>(t + RT_GSCALE) = P.rep_gfix[(size_t)r * GFIX_WORDS + 20];
         reinterpret_cast<double *>(t + 256)[lane] = P.rep_grad[(size_t)r * 32 + lane];
         if (lane == 0) {
@@ -1501,22 +1523,38 @@ __global__ void score_reduce_kernel(const uint64_t *dctr, const uint32_t *rep_do
     score[2 * r + 1] = sh;
 }
 
-// Likelihood-ratio estimate of d E[A]/d theta over the replicas: out[j] =
-// (1/R) sum_r (A_r - mean A) S_r,j, j = beta, h; one block, fixed order.
-__global__ void lr_estimate_kernel(const double *A, const uint64_t *dctr, const uint32_t *rep_dom_off, int n_rep,
-                                   double *out)
+// Likelihood-ratio estimate of d E[A]/d theta over the replicas, with A_r
+// = A[r * stride]: out[0] = mean A, out[1 + j] = (1/(R - 1)) sum_r (A_r -
+// mean A) S_r,j + mean X_j (j = beta, h), where X_r,j = xsel-dependent
+// explicit derivative of A_r (xsel 0: none; 1: -m_r; 2: -m_r^2, m_r =
+// M[r * stride], for j = h only).  The 1/(R - 1) makes the estimate unbiased
+// with the replica mean as baseline (E[S] = 0).  One block of 256 threads,
+// sums in a fixed order.
+__global__ void lr_estimate_kernel(const double *A, const double *M, int stride, int xsel, const uint64_t *dctr,
+                                   const uint32_t *rep_dom_off, int n_rep, double *out)
 {
     __shared__ double red[3][256];
     const int t = threadIdx.x;
-    double a = 0.0;
-    for (int r = t; r < n_rep; r += blockDim.x) a += A[r];
+    double a = 0.0, x = 0.0;
+    for (int r = t; r < n_rep; r += blockDim.x) {
+        a += A[(size_t)r * stride];
+        if (xsel != 0) {
+            const double m = M[(size_t)r * stride];
+            x -= (xsel == 1) ? m : m * m;
+        }
+    }
     red[0][t] = a;
+    red[1][t] = x;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (t < w) red[0][t] += red[0][t + w];
+        if (t < w) {
+            red[0][t] += red[0][t + w];
+            red[1][t] += red[1][t + w];
+        }
         __syncthreads();
     }
     const double mean = red[0][0] / (double)n_rep;
+    const double xmean = red[1][0] / (double)n_rep;
     __syncthreads();
     double sb = 0.0, sh = 0.0;
     for (int r = t; r < n_rep; r += blockDim.x) {
@@ -1525,7 +1563,7 @@ __global__ void lr_estimate_kernel(const double *A, const uint64_t *dctr, const 
             xb += __longlong_as_double((long long)dctr[(uint64_t)g * DCTR_WORDS + DCTR_SB]);
             xh += __longlong_as_double((long long)dctr[(uint64_t)g * DCTR_WORDS + DCTR_SH]);
         }
-        const double c = A[r] - mean;
+        const double c = A[(size_t)r * stride] - mean;
         sb += c * xb;
         sh += c * xh;
     }
@@ -1540,8 +1578,9 @@ __global__ void lr_estimate_kernel(const double *A, const uint64_t *dctr, const 
         __syncthreads();
     }
     if (t == 0) {
-        out[0] = red[1][0] / (double)n_rep;
-        out[1] = red[2][0] / (double)n_rep;
+        out[0] = mean;
+        out[1] = red[1][0] / (double)(n_rep - 1);
+        out[2] = red[2][0] / (double)(n_rep - 1) + xmean;
     }
 }
 

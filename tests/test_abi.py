@@ -142,3 +142,23 @@ def test_ring_and_partition_arguments_refused_on_the_host():
         assert lib.kmc_part_create(ctypes.byref(g), 2, L, kind, ND, k, seeds, ctypes.c_void_p(_PLACE), None) \
             == _lib.KMC_EINVAL
         assert g.value is None
+
+
+@pytest.mark.skipif(_has_cuda_device(), reason="placeholder device pointers: machines without a CUDA device only")
+@pytest.mark.parametrize("L_d", [8, 16, 32, 64])
+def test_acceptance_rounding_to_zero_refused_on_the_host(L_d):
+    """Eq. 4: an acceptance that rounds to A_c = 0 in the 2^-P fixed point
+    would be a one-way rate; the library refuses the table before any CUDA
+    call (the no-allocation entry point builds it first).  Just below the
+    threshold the call gets past the table and fails later for want of a
+    device."""
+    import math
+    lib = _lib.load()
+    P = 63 - int(round(math.log2(L_d * L_d)))
+    b0 = (P + 1) * math.log(2.0) / 8.0  # exp(-8 beta) = 2^-(P+1): the largest a that rounds to 0
+    err = ctypes.create_string_buffer(256)
+    args = lambda beta: (4 * L_d, L_d, 1, 7, 1.0, beta, 0.0, 1.0, 0, 0, 1, 0, 0, 0, ctypes.c_void_p(_PLACE), None,
+                         None, err, len(err))
+    assert lib.kmc_run_schedule_noalloc(*args(1.01 * b0)) == _lib.KMC_ENOTBALANCED
+    assert b"rounds to 0" in err.value
+    assert lib.kmc_run_schedule_noalloc(*args(0.99 * b0)) == _lib.KMC_ECUDA

@@ -32,7 +32,9 @@ def _check(spins_of, obs, idx, n, L, Ld, ks, seeds, beta, h, inits, scores=None,
         assert np.array_equal(obs[:, r, :3], robs[:, :3]), "replica %d: e, m, e*m differ" % r
         np.testing.assert_allclose(obs[:, r, 3], robs[:, 3], rtol=1e-12, atol=0)
         if scores is not None:
-            np.testing.assert_allclose(scores[r], ref.score.sum(axis=0), rtol=1e-9, atol=1e-9)
+            np.testing.assert_allclose(scores[r], ref.score.sum(axis=0), rtol=1e-12, atol=1e-12)
+            if obs.shape[2] >= 6:
+                np.testing.assert_allclose(obs[:, r, 4:6], robs[:, 4:6], rtol=1e-12, atol=1e-12)
 
 
 @pytest.mark.parametrize("plan", ["grid_5x4", "grid_2x10", "grid_3x8", "grid_1x16", "cluster_16"])

@@ -45,8 +45,8 @@ def test_score_parity_with_oracle(law, Ld, k, per_pass):
         assert np.array_equal(lat.replica_spins(r).cpu().numpy(), ref.spins)
         assert np.array_equal(obs[:, r, :3], robs[:, :3])
         scale = 1.0 + np.abs(robs[:, 4:6])
-        assert np.all(np.abs(obs[:, r, 4:6] - robs[:, 4:6]) <= 1e-9 * scale), (obs[:, r, 4:6], robs[:, 4:6])
-        np.testing.assert_allclose(score[r], ref.score.sum(axis=0), rtol=1e-9, atol=1e-9)
+        assert np.all(np.abs(obs[:, r, 4:6] - robs[:, 4:6]) <= 1e-12 * scale), (obs[:, r, 4:6], robs[:, 4:6])
+        np.testing.assert_allclose(score[r], ref.score.sum(axis=0), rtol=1e-12, atol=1e-12)
     lat.close()
 
 
@@ -64,7 +64,7 @@ def test_score_reset_starts_a_new_segment():
     ref.run(3)
     ref.enable_score()
     ref.run(2)
-    np.testing.assert_allclose(lat.score().cpu().numpy()[0], ref.score.sum(axis=0), rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(lat.score().cpu().numpy()[0], ref.score.sum(axis=0), rtol=1e-12, atol=1e-12)
     lat.close()
 
 
@@ -95,7 +95,8 @@ def test_lr_gradient_matches_crn_finite_difference(param, col):
     j = 0 if param == "beta" else 1
     x = (A - A.mean()) * S[:, j]
     se_lr = x.std(ddof=1) / math.sqrt(R)
-    assert lr[j] == pytest.approx(x.mean(), rel=1e-9, abs=1e-12)
+    # unbiased sample covariance (the replica mean as baseline)
+    assert lr[j] == pytest.approx(x.sum() / (R - 1), rel=1e-12, abs=1e-12 * np.abs(x).sum() / (R - 1))
     bp, hp = (beta + d, h) if j == 0 else (beta, h + d)
     bm, hm = (beta - d, h) if j == 0 else (beta, h - d)
     Ap, _, _ = _final_obs([L] * R, Ld, k, seeds, bp, hp, n, False, col)
@@ -105,22 +106,82 @@ def test_lr_gradient_matches_crn_finite_difference(param, col):
     assert abs(lr[j] - fd) < 5 * math.hypot(se_lr, se_fd), (lr[j], se_lr, fd, se_fd)
 
 
-def test_autograd_function_backward():
+def _oracle_lr(L, Ld, k, seeds, beta, h, n, col):
+    """Oracle replicas on the same seeds: per-replica observable A, magnetisation m and score S."""
+    A, m, S = [], [], []
+    for sd in seeds:
+        ref = orc.Replica(L=L, Ld=Ld, k=k, seed=sd, beta=beta, h=h, init=orc.INIT_RANDOM)
+        ref.enable_score()
+        rec = ref.run(n, obs_every=n)[-1]
+        A.append(rec[col])
+        m.append(rec[1])
+        S.append(ref.score.sum(axis=0))
+    return np.array(A), np.array(m), np.array(S)
+
+
+@pytest.mark.parametrize("name,col", [("e", 0), ("m", 1), ("em", 2)])
+def test_autograd_value_matches_oracle_covariance(name, col):
+    """expectation(...).backward() against the same estimator built from the
+    oracle's records and scores on the same seeds: the unbiased covariance of
+    A with the path score plus the explicit h-dependence of A (de/dh = -m,
+    d(em)/dh = -m^2, computed here), to 1e-12 of the sum of the terms'
+    magnitudes; the forward value is the oracle's replica mean."""
     import torch
     import paper_1403_4674_gb300 as kmc
     from paper_1403_4674_gb300.autograd import expectation
-    lat = kmc.Lattice([32] * 1024, 8, 4, list(range(7, 7 + 1024)))
-    beta = torch.tensor(0.42, dtype=torch.float64, requires_grad=True)
-    h = torch.tensor(0.05, dtype=torch.float64, requires_grad=True)
-    e = expectation(lat, beta, h, n_schedules=4, observable="e")
-    e.backward()
-    assert torch.isfinite(beta.grad) and torch.isfinite(h.grad)
-    # raising beta lowers the energy reached from a random start; raising h
-    # lowers it through the path and through the explicit -h*m term
-    assert beta.grad.item() < 0
-    assert h.grad.item() < 0
-    m = expectation(lat, beta.detach().requires_grad_(), h.detach().requires_grad_(), 4, "m")
-    assert torch.isfinite(m)
+    R, L, Ld, k, n, b0, h0 = 256, 32, 8, 4, 4, 0.42, 0.05
+    seeds = list(range(7, 7 + R))
+    lat = kmc.Lattice([L] * R, Ld, k, seeds)
+    beta = torch.tensor(b0, dtype=torch.float64, requires_grad=True)
+    h = torch.tensor(h0, dtype=torch.float64, requires_grad=True)
+    val = expectation(lat, beta, h, n_schedules=n, observable=name)
+    val.backward()
+    lat.close()
+    A, m, S = _oracle_lr(L, Ld, k, seeds, b0, h0, n, col)
+    assert val.item() == pytest.approx(A.mean(), rel=1e-14, abs=1e-15)
+    xs = {"e": -m, "m": np.zeros(R), "em": -m * m}[name]
+    for j, got in ((0, beta.grad.item()), (1, h.grad.item())):
+        terms = (A - A.mean()) * S[:, j] / (R - 1)
+        want = terms.sum() + (xs.mean() if j == 1 else 0.0)
+        mag = np.abs(terms).sum() + (np.abs(xs).mean() if j == 1 else 0.0)
+        assert abs(got - want) <= 1e-12 * mag, (name, j, got, want, mag)
+
+
+def test_autograd_field_gradient_of_energy_matches_crn_finite_difference():
+    """d<e>/dh through torch.autograd, where the explicit term -<m> matters,
+    against a common-random-number central difference of the forward value
+    (step 1e-4) within 5 standard errors."""
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300.autograd import expectation
+    R, L, Ld, k, n = 4096, 16, 8, 4, 3
+    b0, h0, d = 1 / 2.4, 0.02, 1e-4
+    seeds = list(range(3000, 3000 + R))
+    lat = kmc.Lattice([L] * R, Ld, k, seeds)
+    beta = torch.tensor(b0, dtype=torch.float64, requires_grad=True)
+    h = torch.tensor(h0, dtype=torch.float64, requires_grad=True)
+    up = kmc.KMC_INIT_ALL_UP  # the start of _final_obs
+    expectation(lat, beta, h, n_schedules=n, observable="e", init=up).backward()
+    lr = h.grad.item()
+    # per-replica terms of the same estimate for its standard error
+    A, _, S = _final_obs([L] * R, Ld, k, seeds, b0, h0, n, True, 0)
+    m, _, _ = _final_obs([L] * R, Ld, k, seeds, b0, h0, n, False, 1)
+    x = (A - A.mean()) * S[:, 1] * R / (R - 1) - m
+    se_lr = x.std(ddof=1) / math.sqrt(R)
+    assert lr == pytest.approx(x.mean(), rel=1e-12, abs=1e-12 * np.abs(x).mean())
+    with torch.no_grad():
+        ep = expectation(lat, torch.tensor(b0, dtype=torch.float64), torch.tensor(h0 + d, dtype=torch.float64), n,
+                         init=up)
+        em = expectation(lat, torch.tensor(b0, dtype=torch.float64), torch.tensor(h0 - d, dtype=torch.float64), n,
+                         init=up)
+    Ap, _, _ = _final_obs([L] * R, Ld, k, seeds, b0, h0 + d, n, False, 0)
+    Am, _, _ = _final_obs([L] * R, Ld, k, seeds, b0, h0 - d, n, False, 0)
+    assert ep.item() == pytest.approx(Ap.mean(), rel=1e-14) and em.item() == pytest.approx(Am.mean(), rel=1e-14)
+    diff = (Ap - Am) / (2 * d)
+    fd, se_fd = diff.mean(), diff.std(ddof=1) / math.sqrt(R)
+    assert abs(lr - fd) < 5 * math.hypot(se_lr, se_fd), (lr, se_lr, fd, se_fd)
+    # without the explicit term the estimate would miss by <m>, many standard errors here
+    assert abs(lr + m.mean() - fd) > 5 * math.hypot(se_lr, se_fd)
     lat.close()
 
 

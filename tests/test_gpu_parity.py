@@ -73,10 +73,47 @@ def test_resume_across_calls_is_bit_exact():
 
 
 def test_degenerate_rates():
-    # beta = 0: every step is a real event; beta = 8: almost every step is null
-    gpu, ref = run_both([64, 64], 16, 8, [3, 4], [0.0, 8.0], [0.0, 0.0], 5, init=orc.INIT_ALL_UP)
+    # beta = 0: every step is a real event; beta = 4.5: almost every step is
+    # null (a = exp(-36) = 2.3e-16 for the aligned classes, A_c = 8 at
+    # L_d = 16, the last beta of that order whose table keeps every A_c >= 1)
+    gpu, ref = run_both([64, 64], 16, 8, [3, 4], [0.0, 4.5], [0.0, 0.0], 5, init=orc.INIT_ALL_UP)
     assert_parity(gpu, ref, 2)
     assert gpu["flips"][:16].sum() == 16 * 2 * 8 * 5
+
+
+def test_tables_rounding_an_acceptance_to_zero_are_refused():
+    """Eq. 4: an acceptance that rounds to A_c = 0 would be a one-way rate.
+    Every way of setting a table refuses it and keeps the previous one."""
+    import math
+    import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300._lib import KMC_ENOTBALANCED
+    lat = kmc.Lattice([64], 16, 4, [5])
+    lat.set_rates([0.4])
+    before = lat.rate_table(0)
+    with pytest.raises(kmc.KmcError) as e:
+        lat.set_rates([5.0])  # exp(-40) < 2^-56 at P = 55
+    assert e.value.status == KMC_ENOTBALANCED and "rounds to 0" in str(e.value)
+    with pytest.raises(kmc.KmcError) as e:
+        a = np.array([[min(1.0, math.exp(-5.0 * orc.class_dE(c, 1.0, 0.0))) for c in range(10)]])
+        kmc.kmc_set_rate_table(lat.ctx, 1.0, [5.0], [0.0], 1.0, a)
+    assert e.value.status == KMC_ENOTBALANCED
+    after = lat.rate_table(0)
+    assert np.array_equal(before[1], after[1])
+    lat.set_rates([4.5])
+    assert 1e-3 < lat.rate_table_error() < 0.1  # A_c = 8 for a = 2.3e-16 * 2^55 = 8.3
+    lat.set_rates([1 / 1.5], [0.1])
+    assert lat.rate_table_error() < 1e-12
+    lat.close()
+    ring = kmc.Ring(8, 2, 5, [1], [3])
+    with pytest.raises(kmc.KmcError) as e:
+        ring.set_rates([12.0], [0.0])  # ring: largest dE = 4, exp(-48) < 2^-63
+    assert e.value.status == KMC_ENOTBALANCED
+    ring.close()
+    part = kmc.Partitioned(12, kmc.KMC_PART_STRIPES, 4, 5, [1])
+    with pytest.raises(kmc.KmcError) as e:
+        part.set_rates([6.0])
+    assert e.value.status == KMC_ENOTBALANCED
+    part.close()
 
 
 def test_minimum_lattice_two_domains_per_side():

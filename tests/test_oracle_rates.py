@@ -66,3 +66,47 @@ def test_invalid_arguments_rejected():
         orc.rate_table(1.0, 0.4, 0.0, 7, 8)
     with pytest.raises(ValueError):
         orc.rate_table(1.0, 0.4, 0.0, 0, 17)  # n_d <= 2^16 (100^2 stripes need 2^13)
+
+
+def _beta_at_zero_threshold(P: int, dE: float) -> float:
+    """beta at which exp(-beta dE) = 2^-(P+1), the largest acceptance that rounds to A_c = 0."""
+    return (P + 1) * math.log(2.0) / dE
+
+
+@pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
+@pytest.mark.parametrize("log2nd", [6, 8, 10, 12])
+def test_acceptance_rounding_to_zero_is_refused(law, log2nd):
+    """Eq. 4: a_c > 0 for every class, so a table whose fixed point rounds
+    some a_c to 0 would make the flip out of class cbar one-way.  Just below
+    the threshold every A_c is at least 1; just above it the table is refused.
+    (The largest class energy change at J = 1, h = 0 is 8.)"""
+    P = 63 - log2nd
+    b0 = _beta_at_zero_threshold(P, 8.0)
+    a, A = orc.rate_table(1.0, 0.99 * b0, 0.0, law, log2nd)
+    assert int(A.min()) >= 1
+    with pytest.raises(ValueError, match="rounds to 0"):
+        orc.rate_table(1.0, 1.01 * b0, 0.0, law, log2nd)
+
+
+@pytest.mark.parametrize("log2ld", [0, 2, 5])
+def test_ring_acceptance_rounding_to_zero_is_refused(log2ld):
+    """The ring's classes: largest energy change 4 at J = 1, h = 0."""
+    P = 63 - log2ld
+    b0 = _beta_at_zero_threshold(P, 4.0)
+    _, A = orc.ring_rate_table(1.0, 0.99 * b0, 0.0, orc.RATE_METROPOLIS, log2ld)
+    assert int(A.min()) >= 1
+    with pytest.raises(ValueError):
+        orc.ring_rate_table(1.0, 1.01 * b0, 0.0, orc.RATE_METROPOLIS, log2ld)
+
+
+@pytest.mark.parametrize("log2nd", [6, 10, 12])
+def test_rounding_error_bound(log2nd):
+    """|A_c 2^-P - a_c| <= 2^-(P+1) for every class, so the relative change
+    is at most 2^-(P+1)/a_c; at the benchmark temperatures (T >= 1.5, |h| <=
+    0.1) it stays below 1e-12."""
+    P = 63 - log2nd
+    for T, h in [(1.5, 0.1), (1.5, -0.1), (2.269, 0.01), (3.5, 0.0)]:
+        a, A = orc.rate_table(1.0, 1 / T, h, orc.RATE_METROPOLIS, log2nd)
+        err = np.abs(A.astype(np.float64) * 2.0 ** -P - a)
+        assert np.all(err <= 2.0 ** -(P + 1))
+        assert np.max(err / a) < 1e-12

@@ -77,7 +77,9 @@ def test_noalloc_rejects_sizes_beyond_its_array(torch_cuda):
     rc, msg = _noalloc(lib, torch, 8192, 64, 8, 1, 0.4, 0.0, 0, 1, 0, spins, None)
     assert rc == -1 and "too large" in msg
     small = torch.ones(64 * 64, dtype=torch.int8, device="cuda")
-    obs = torch.empty(8, dtype=torch.float64, device="cuda")
+    # a buffer with room for every record, so that if the size check ever
+    # stopped refusing this call the run would write inside it (9.6 MB)
+    obs = torch.empty(300000 * 4, dtype=torch.float64, device="cuda")
     # 300000 observation records need more working memory than the array holds
     rc, msg = _noalloc(lib, torch, 64, 16, 1, 1, 0.4, 0.0, 0, 300000, 1, small, obs)
     assert rc == -1 and "bytes" in msg
