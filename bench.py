@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the batched and gradient variants")
     ap.add_argument("--plan", default="", help="launch plan mode,size,warps (skips the plan tuning)")
-    ap.add_argument("--only", default="", choices=["", "batched", "grad", "lattice8192", "ring8", "partitions2d"],
+    ap.add_argument("--only", default="", choices=["", "batched", "grad", "lattice8192", "ring8", "partitions2d",
+                                                    "pollcost"],
                     help="time one variant alone and print its JSON object (profiling runs; not the contract line)")
     return ap.parse_args()
 
@@ -167,18 +168,20 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def oracle_sample(w, budget_s: float):
     """Time the CPU oracle, single-threaded, on a bounded sample: for each
-    distinct k, the first random-start replica of that k for as many schedules
-    as fit in budget_s / (#k values).  Returns (events/s, description, events, seconds)."""
+    distinct k and temperature, the first random-start replica of that pair
+    for as many schedules as fit in budget_s / (#pairs).  Returns
+    (events/s, description, events, seconds)."""
     from oracle import oracle as orc
-    by_k = {}
+    by_kT = {}
     for r in range(len(w.L)):
-        if w.init_of(r) == 0 and w.k_of(r) not in by_k:
-            by_k[w.k_of(r)] = r
-    per = budget_s / max(1, len(by_k))
+        key = (w.k_of(r), round(1 / w.beta[r], 4))
+        if w.init_of(r) == 0 and key not in by_kT:
+            by_kT[key] = r
+    per = budget_s / max(1, len(by_kT))
     ev = 0
     secs = 0.0
     parts = []
-    for k, r in sorted(by_k.items()):
+    for (k, T), r in sorted(by_kT.items()):
         L, Ld = w.L[r], w.L_d
         rep = orc.Replica(L=L, Ld=Ld, k=k, seed=w.seeds[r], beta=w.beta[r], h=w.h[r])
         steps_per_sched = 2 * (L // Ld) ** 2 * k
@@ -191,8 +194,42 @@ def oracle_sample(w, budget_s: float):
         dt = time.perf_counter() - t0
         ev += n * steps_per_sched
         secs += dt
-        parts.append("L=%d k=%d T=%.4g: %d schedules" % (L, k, 1 / w.beta[r], n))
+        parts.append("L=%d k=%d T=%.4g: %d schedules" % (L, k, T, n))
     return ev / secs, "; ".join(parts), ev, secs
+
+
+def _oracle_job(job):
+    """One oracle replica for a bounded time (module level: runs in a spawned
+    worker).  job = (L, L_d, k, seed, beta, h, scores, budget_s); returns
+    (uniformised steps run, seconds)."""
+    from oracle import oracle as orc
+    L, Ld, k, seed, beta, h, scores, budget = job
+    rep = orc.Replica(L=L, Ld=Ld, k=k, seed=seed, beta=beta, h=h)
+    if scores:
+        rep.enable_score()
+    steps_per_sched = 2 * (L // Ld) ** 2 * k
+    t0 = time.perf_counter()
+    rep.run(1)
+    one = time.perf_counter() - t0
+    n = max(0, int((budget - one) / max(one, 1e-6)))
+    if n > 0:
+        rep.run(n)
+    return (n + 1) * steps_per_sched, time.perf_counter() - t0
+
+
+def oracle_parallel(jobs, label: str):
+    """Run oracle jobs on all host cores (one single-threaded oracle process
+    per job at a time, spawned); events/s = all jobs' steps / wall time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    workers = min(cores, len(jobs))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(workers) as pool:
+        res = pool.map(_oracle_job, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    ev = sum(e for e, _ in res)
+    return {"value": ev / wall, "unit": UNIT, "cores": workers, "host_cores": cores, "kind": "oracle",
+            "sample": "%s: %d oracle processes at a time, %d events in %.1f s wall" % (label, workers, ev, wall)}
 
 
 def reference_arm(args):
@@ -214,45 +251,64 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic", "config": {"workload": desc, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: " + sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "per step: " + sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-# DRAM traffic of one run-kernel launch of the default workload, from
-# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (summary in
-# profiles/run_kernel_ising1024x18_launches.md), and the SHA-256 of the kernel
-# source it was taken on; reported as null once the source has changed.
-TRAFFIC_BYTES_PER_LAUNCH = 5543680 + 20736
-TRAFFIC_KERNEL_SHA256 = "823b1408fb2c0056ec0d0b082d15c810f72d65cfb1afb637569c1bc640426879"
-# Warp instructions per uniformised step of the same launch (ncu
-# smsp__inst_executed.sum of the full 1e4-schedule launch / its 2.58e9 steps;
-# same capture).  Includes the halo polls.
-INST_PER_STEP = 414890015101 / 2580480000
+# Counters of the timed run-kernel launches from one ncu capture each
+# (profiles/run_kernel_issue_and_polls.md): warp instructions
+# (smsp__inst_executed.sum), uniformised steps and halo-poll iterations
+# (kmc_profile_polls) of one launch, DRAM bytes read + written, and the
+# instructions of one poll iteration (a launch whose every wait runs out:
+# `bench.py --only pollcost`).  They hold for the kernel source with this
+# SHA-256 and are left out of the line once the source changes.
+NCU_KERNEL_SHA256 = None
+INST_PER_POLL = None
+NCU_COUNTS = {
+    # workload: (warp instructions, steps, poll iterations, DRAM bytes) of one launch
+}
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
-# The same for the variants, from `ncu --metrics smsp__inst_executed.sum` over
-# a full-size timed launch of `bench.py --only grad` / `--only batched`
-# (profiles/run_kernel_variants_instructions.md).  Batched: measured on the
-# single-context configuration of the same 512 replicas (L_d = 8, k = 16)
-# that the tuner chose under the profiler.
-INST_PER_STEP_GRAD = 275895852430 / 1310720000
-INST_PER_STEP_BATCHED = 319013065405 / 2636876800
-INST_PER_STEP_8192 = 144441571379 / 524288000  # one 2000-schedule launch of `bench.py --only lattice8192`
 
 
-def issue_roofline(inst_per_step: float, steps_per_s: float, peaks: dict, source: str):
-    """Issue-rate view: warp instructions per second against 4 per SM cycle x
-    the SMs x the maximum SM clock (runs stay at it: see the clocks record)."""
-    import torch
-    if TRAFFIC_KERNEL_SHA256 != kernel_source_sha256():
+def ncu_counts(workload: str):
+    """The workload's ncu counters if they were taken on the current kernel source."""
+    if NCU_KERNEL_SHA256 is None or NCU_KERNEL_SHA256 != kernel_source_sha256():
         return None
+    return NCU_COUNTS.get(workload)
+
+
+def launch_traffic(workload: str):
+    """DRAM bytes (read + write) of one timed launch from the workload's ncu capture, or None."""
+    cnt = ncu_counts(workload)
+    return None if cnt is None else cnt[3]
+
+
+def issue_roofline(workload: str, steps_per_s: float, sm_mhz: float, polls_per_step=None):
+    """Issue-rate view: warp instructions per second against 4 per SM cycle x
+    the SMs x the SM clock.  Gross counts every instruction, halo polls
+    included; net leaves out the poll iterations (busy-waiting, not work).
+    With polls_per_step (this run's own count) the gross figure uses it, else
+    the capture's."""
+    import torch
+    cnt = ncu_counts(workload)
+    if cnt is None or INST_PER_POLL is None:
+        return None
+    inst, steps, polls, _ = cnt
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    peak = ISSUE_PER_SM_CYCLE * sms * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    ach = inst_per_step * steps_per_s
-    return {"bound": "issue", "achieved": ach, "peak": peak, "unit": "warp-inst/s", "frac": ach / peak,
-            "source": source % inst_per_step}
+    peak = ISSUE_PER_SM_CYCLE * sms * sm_mhz * 1e6
+    work = (inst - polls * INST_PER_POLL) / steps
+    pps = polls / steps if polls_per_step is None else polls_per_step
+    gross = work + pps * INST_PER_POLL
+    return {"bound": "issue", "unit": "warp-inst/s", "peak": peak,
+            "achieved": gross * steps_per_s, "frac": gross * steps_per_s / peak,
+            "achieved_net": work * steps_per_s, "frac_net": work * steps_per_s / peak,
+            "inst_per_step": gross, "inst_per_step_net": work, "polls_per_step": pps,
+            "inst_per_poll": INST_PER_POLL,
+            "source": "ncu smsp__inst_executed of one timed launch, less its halo-poll iterations x instructions "
+                      "per poll iteration; peak = 4 warp instructions per SM cycle x %d SMs x %.0f MHz" % (sms, sm_mhz)}
 
 
 def kernel_source_sha256() -> str:
@@ -304,6 +360,15 @@ def variant_batched(args, peaks, flush, stream):
     choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
                                   Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=20)
     tune_s = time.perf_counter() - t0
+    # oracle on a 64-replica subset, each with its group's domain side and k
+    grp = {}
+    for ch in choices:
+        for i in ch.replicas:
+            grp[i] = (ch.L_d, ch.k)
+    sub = list(range(0, len(w.L), max(1, len(w.L) // 64)))[:64]
+    cpu = None if args.no_cpu else oracle_parallel(
+        [(w.L[i], grp[i][0], grp[i][1], w.seeds[i], w.beta[i], w.h[i], False, 1.5) for i in sub],
+        "64 of the 512 replicas with their tuned L_d and k, about 1.5 s each")
     batch = autotune.Batch(w.L, w.beta, w.h, w.seeds, choices)
     graph = batch.capture(n_sched, obs_every, reset=0)
     ms = device_time(graph.replay, args.steps, args.warmup, flush, stream)
@@ -317,12 +382,11 @@ def variant_batched(args, peaks, flush, stream):
            "groups": [{"replicas": len(ch.replicas), "L_d": ch.L_d, "k": ch.k, "plan": list(ch.plan),
                        "tuned_events_per_s": ch.events_per_s} for ch in choices],
            "tune_s": tune_s, "events_per_step": ev,
-           "roofline": roofline(by, dev_s / args.steps, peaks)}
+           "roofline": roofline(by, dev_s / args.steps, peaks), "cpu_baseline": cpu}
     out["roofline"]["note"] = "step-level: the groups' run kernels overlap on concurrent streams"
-    iss = issue_roofline(INST_PER_STEP_BATCHED, ev * args.steps / dev_s, peaks,
-                         "ncu warp instructions per step (%.1f, single-context configuration of the same batch) x "
-                         "steps/s of the whole step; peak = 4 per SM cycle x SMs x maximum SM clock")
+    iss = issue_roofline("batched", ev * args.steps / dev_s, float(peaks.get("sm_max_mhz", 2070.0)))
     if iss is not None:
+        iss["note"] = "counts of the single-context configuration of the same batch; steps/s of the whole step"
         out["roofline"]["issue"] = iss
     batch.close()
     return out
@@ -335,6 +399,9 @@ def variant_grad(args, peaks, flush, stream):
     import paper_1403_4674_gb300 as kmc
     from paper_1403_4674_gb300 import autotune, workloads as wl
     w = wl.grad_replicas(256, seed_master=256, k=8)
+    cpu = None if args.no_cpu else oracle_parallel(
+        [(w.L[i], w.L_d, w.k, w.seeds[i], w.beta[i], w.h[i], True, 4.0) for i in range(16)],
+        "16 of the 256 replicas with scores, about 4 s each")
     lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds, init=0)
     lat.set_rates(w.beta, w.h)
     lat.enable_grad(True)
@@ -353,8 +420,10 @@ def variant_grad(args, peaks, flush, stream):
     ms = device_time(step, args.steps, args.warmup, flush, stream)
     lat.sync()
     lat.profile_read()
+    lat.profile_polls()
     step()
     run_ms, run_n = lat.profile_read()
+    polls = lat.profile_polls()
     ev = lat.events_per_schedule() * n
     by = schedule_bytes(lat.L, lat.L_d, lat.ks) * n
     dev_s = sum(ms) / 1000.0
@@ -364,11 +433,10 @@ def variant_grad(args, peaks, flush, stream):
                        "LR gradients of <e> and <m> w.r.t. (beta, h) per step" % n,
            "plan": list(plan), "launch": list(lat.launch()),
            "lr_grad_e_beta_h": [float(ge[0]), float(ge[1])], "lr_grad_m_beta_h": [float(gm[0]), float(gm[1])],
-           "events_per_step": ev,
-           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks)}
-    iss = issue_roofline(INST_PER_STEP_GRAD, ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0, peaks,
-                         "ncu warp instructions per step of this kernel (%.1f) x steps / launch time; "
-                         "peak = 4 per SM cycle x SMs x maximum SM clock")
+           "events_per_step": ev, "cpu_baseline": cpu,
+           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks, launch_traffic("grad"))}
+    iss = issue_roofline("grad", ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0,
+                         float(peaks.get("sm_max_mhz", 2070.0)), polls / max(ev * max(run_n, 1), 1))
     if iss is not None:
         out["roofline"]["issue"] = iss
     lat.close()
@@ -381,9 +449,17 @@ def variant_lattice8192(args, peaks, flush, stream):
     import paper_1403_4674_gb300 as kmc
     from paper_1403_4674_gb300 import autotune, workloads as wl
     w = wl.lattice_8192(seed=8192)
+    cpu = None
+    if not args.no_cpu:
+        cpu = oracle_parallel([(w.L[0], w.L_d, w.k, w.seeds[0], w.beta[0], w.h[0], False, 0.0)],
+                              "one schedule of the 8192^2 lattice (one process: a single lattice)")
     lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds, init=0)
     lat.set_rates(w.beta, w.h)
-    plan, _ = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=20)
+    if args.plan:
+        plan = tuple(int(x) for x in args.plan.split(","))
+        lat.set_launch(*plan)
+    else:
+        plan, _ = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=20)
     lat.profile(True)
     n = w.schedules
 
@@ -394,19 +470,21 @@ def variant_lattice8192(args, peaks, flush, stream):
     ms = device_time(step, args.steps, args.warmup, flush, stream)
     lat.sync()
     lat.profile_read()
+    lat.profile_polls()
     step()
     run_ms, run_n = lat.profile_read()
+    polls = lat.profile_polls()
     ev = lat.events_per_schedule() * n
     by = schedule_bytes(lat.L, lat.L_d, lat.ks) * n
     dev_s = sum(ms) / 1000.0
     out = {"value": ev * args.steps / dev_s, "unit": UNIT, "ms_per_step": statistics.mean(ms),
            "workload": "8192x8192 periodic Ising (67M sites), T=2.269, h=0.01, L_d=64, k=8, %d palindromic "
                        "schedules" % n,
-           "plan": list(plan), "launch": list(lat.launch()), "events_per_step": ev,
-           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks)}
-    iss = issue_roofline(INST_PER_STEP_8192, ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0, peaks,
-                         "ncu warp instructions per step of this kernel (%.1f) x steps / launch time; "
-                         "peak = 4 per SM cycle x SMs x maximum SM clock")
+           "plan": list(plan), "launch": list(lat.launch()), "events_per_step": ev, "cpu_baseline": cpu,
+           "polls_per_launch": polls / max(run_n, 1),
+           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks, launch_traffic("lattice8192"))}
+    iss = issue_roofline("lattice8192", ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0,
+                         float(peaks.get("sm_max_mhz", 2070.0)), polls / max(ev * max(run_n, 1), 1))
     if iss is not None:
         out["roofline"]["issue"] = iss
     lat.close()
@@ -520,8 +598,51 @@ def variant_part(args, peaks, flush, stream):
     return out
 
 
+def variant_pollcost(args, peaks, flush, stream):
+    """Instructions of one halo-poll iteration, for the net issue rate: one
+    launch of the default workload's context and plan in which every visit
+    waits for one neighbour visit more than will ever come
+    (kmc_debug_barrier), so each warp polls until the 20 ms limit and the
+    launch's instructions are almost all poll iterations.  Prints the poll
+    count; `ncu --metrics smsp__inst_executed.sum -k regex:run_kernel` of the
+    same command gives the instructions, and their ratio is the cost of one
+    iteration.  The context is checked to be usable afterwards."""
+    import torch
+    import paper_1403_4674_gb300 as kmc
+    w, desc = main_workload("ising1024", 0, 0)
+    ks = [w.k_of(r) for r in range(len(w.L))]
+    inits = [w.init_of(r) for r in range(len(w.L))]
+    lat = kmc.Lattice(w.L, w.L_d, ks[0], w.seeds, init=inits[0])
+    lat.set_replica_params(k=ks, init=inits)
+    lat.reset(kmc.KMC_INIT_PER_REPLICA)
+    lat.set_rates(w.beta, w.h)
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    plan = tuple(int(x) for x in args.plan.split(",")) if args.plan else (2, 5 * sm, 4)
+    lat.set_launch(*plan)
+    limit_ns = 20_000_000
+    kmc.kmc_debug_barrier(lat.ctx, 1, limit_ns)
+    lat.profile(True)
+    lat.run(1)
+    try:
+        lat.sync()
+        status = 0
+    except kmc.KmcError as e:
+        status = e.status
+    polls = lat.profile_polls()
+    kmc.kmc_debug_barrier(lat.ctx, 0, 0)
+    lat.reset(kmc.KMC_INIT_PER_REPLICA)
+    lat.run(1)
+    lat.sync()
+    out = {"workload": desc, "plan": list(plan), "launch": list(lat.launch()), "limit_ns": limit_ns,
+           "status_after_timeout": status, "polls": polls}
+    lat.close()
+    if status != -5:
+        raise RuntimeError("expected KMC_ETIMEOUT from the waits that run out, got %d" % status)
+    return out
+
+
 VARIANTS = {"batched": "variant_batched", "grad": "variant_grad", "lattice8192": "variant_lattice8192",
-            "ring8": "variant_ring", "partitions2d": "variant_part"}
+            "ring8": "variant_ring", "partitions2d": "variant_part", "pollcost": "variant_pollcost"}
 
 
 def only_variant(args):
@@ -553,8 +674,12 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu:
         v, sample, e, s = oracle_sample(w, 12.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": "%s; %d events in %.1f s, single thread" % (sample, e, s)}
+        # the same replicas on every host core, one oracle process per replica
+        jobs = [(w.L[r], w.L_d, w.k_of(r), w.seeds[r], w.beta[r], w.h[r], False, 5.0)
+                for r in range(len(w.L)) if w.init_of(r) == 0]
+        cpu["all_cores"] = oracle_parallel(jobs, "the %d random-start replicas (k x T), about 5 s each" % len(jobs))
 
     import torch
     import paper_1403_4674_gb300 as kmc
@@ -602,6 +727,7 @@ def main():
         step()
     torch.cuda.synchronize()
     lat.profile_read()  # discard warm-up timings
+    lat.profile_polls()
     launches0 = lat.kernel_launches()
 
     clocks = ClockSampler(local)
@@ -618,6 +744,7 @@ def main():
     clk = clocks.stop()
     launches = lat.kernel_launches() - launches0
     run_ms, run_n = lat.profile_read()
+    polls = lat.profile_polls()
 
     # the timed step's final state and records, for the bit-exactness check below
     dev_spins = lat.spins.clone()
@@ -668,22 +795,20 @@ def main():
             bit_exact["e2e_records_clock_rel_diff_max"] = float(
                 ((host_obs[..., 3] - do[..., 3]).abs() / do[..., 3].abs().clamp_min(1e-300)).max().item())
 
-    traffic = TRAFFIC_BYTES_PER_LAUNCH if (TRAFFIC_KERNEL_SHA256 == kernel_source_sha256()
-                                           and args.workload == "ising1024" and args.schedules == 0) else None
+    full = args.schedules == 0
+    traffic = launch_traffic(args.workload) if full else None
     avg_run_s = (run_ms / 1000.0) / max(run_n, 1)
     roof = roofline(bytes_step, avg_run_s, peaks, traffic)
     roof.update({"kernel": "kmcdev::run_kernel", "run_kernel_ms_avg": 1000 * avg_run_s,
                  "run_kernel_launches": run_n, "algorithmic_bytes_per_launch": bytes_step,
-                 "step_level_achieved": bytes_step * args.steps / dev_s / 1e9})
+                 "step_level_achieved": bytes_step * args.steps / dev_s / 1e9,
+                 "polls_per_launch": polls / max(run_n, 1)})
     # the bound this kernel actually meets: instruction issue
-    if traffic is not None and clk.get("sm_mhz"):
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        issue_peak = ISSUE_PER_SM_CYCLE * sms * clk["sm_mhz"] * 1e6
-        issue_ach = INST_PER_STEP * events_step / avg_run_s if avg_run_s > 0 else 0.0
-        roof["issue"] = {"bound": "issue", "achieved": issue_ach, "peak": issue_peak, "unit": "warp-inst/s",
-                         "frac": issue_ach / issue_peak,
-                         "source": "ncu warp instructions per step of this kernel (%.1f) x steps / launch time; "
-                                   "peak = 4 per SM cycle x %d SMs x median SM clock" % (INST_PER_STEP, sms)}
+    if full and clk.get("sm_mhz") and avg_run_s > 0:
+        iss = issue_roofline(args.workload, events_step / avg_run_s, clk["sm_mhz"],
+                             polls / max(events_step * max(run_n, 1), 1))
+        if iss is not None:
+            roof["issue"] = iss
 
     variants = None
     if world == 1 and not args.no_variants and args.workload == "ising1024":

@@ -376,6 +376,17 @@ kmc_status kmc_debug_barrier(kmc_ctx *ctx, int32_t extra, int64_t limit_ns);
 kmc_status kmc_profile(kmc_ctx *ctx, int32_t enable);
 kmc_status kmc_profile_read(kmc_ctx *ctx, double *run_kernel_ms, int64_t *run_kernel_launches);
 
+/* Halo-poll iterations of the profiled run-kernel launches: the sum over
+ * warps of the times a warp re-read a neighbour's edge word because the
+ * neighbour had not finished its earlier visit yet (the first read of a halo
+ * is not counted; a warp polling several neighbours at once counts its
+ * slowest lane).  With instructions per poll iteration this separates
+ * busy-waiting from the visits' own instructions.  *polls is a host int64;
+ * reading synchronises the context's stream and clears the count.  0 when
+ * profiling was never enabled.  KMC_EINVAL for null arguments.  No
+ * counterpart in the paper. */
+kmc_status kmc_profile_polls(kmc_ctx *ctx, int64_t *polls);
+
 /*
  * kmc_run_schedule_noalloc -- run schedules on one replica without allocating
  * any device memory.  This operation has no counterpart in the paper; it

@@ -12,7 +12,7 @@ from .api import (KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID, KMC_OBS_
                   KMC_SCHEDULE_RANDOM_PERM, KMC_TIME_EXPECTED, KMC_TIME_EXPONENTIAL, KMC_TIME_HORIZON, Lattice,
                   kmc_create_lattice, kmc_debug_barrier, kmc_destroy, kmc_domain_state,
                   kmc_enable_grad, kmc_get_launch, kmc_get_rate_table, kmc_grad, kmc_grad_nu,
-                  kmc_kernel_launches, kmc_domain_side, kmc_lr_estimate, kmc_lr_observable, kmc_observables, kmc_profile, kmc_profile_read, kmc_reset, kmc_run_schedule, kmc_run_schedule_noalloc,
+                  kmc_kernel_launches, kmc_domain_side, kmc_lr_estimate, kmc_lr_observable, kmc_observables, kmc_profile, kmc_profile_read, kmc_profile_polls, kmc_reset, kmc_run_schedule, kmc_run_schedule_noalloc,
                   kmc_set_horizon, kmc_set_launch, kmc_set_observation, kmc_set_rate_table, kmc_rate_table_error, kmc_set_replica_params, kmc_set_rates, kmc_sync, kmc_version,
                   Ring, kmc_ring_create, kmc_ring_destroy, kmc_ring_run, kmc_ring_set_rates, kmc_ring_state, ring_passes,
                   KMC_PART_BLOCKS, KMC_PART_STRIPES, Partitioned, kmc_part_create, kmc_part_destroy, kmc_part_run,

@@ -29,7 +29,7 @@ EXPORTS = [
     "kmc_create_lattice", "kmc_set_rates", "kmc_set_rate_table", "kmc_run_schedule",
     "kmc_observables", "kmc_grad", "kmc_grad_nu", "kmc_lr_estimate", "kmc_lr_observable", "kmc_enable_grad", "kmc_reset", "kmc_sync",
     "kmc_domain_state", "kmc_get_rate_table", "kmc_rate_table_error", "kmc_set_launch", "kmc_get_launch", "kmc_set_replica_params", "kmc_set_observation", "kmc_set_horizon",
-    "kmc_debug_barrier", "kmc_run_schedule_noalloc", "kmc_profile", "kmc_profile_read", "kmc_kernel_launches", "kmc_domain_side", "kmc_last_error", "kmc_destroy", "kmc_version",
+    "kmc_debug_barrier", "kmc_run_schedule_noalloc", "kmc_profile", "kmc_profile_read", "kmc_profile_polls", "kmc_kernel_launches", "kmc_domain_side", "kmc_last_error", "kmc_destroy", "kmc_version",
     "kmc_ring_create", "kmc_ring_set_rates", "kmc_ring_run", "kmc_ring_state", "kmc_ring_last_error", "kmc_ring_destroy",
     "kmc_part_create", "kmc_part_set_rates", "kmc_part_run", "kmc_part_state", "kmc_part_last_error", "kmc_part_destroy",
 ]
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                            i32, i32, vp, vp, vp, ctypes.c_char_p, i32]
     L.kmc_profile.argtypes = [vp, i32]
     L.kmc_profile_read.argtypes = [vp, P(dbl), P(i64)]
+    L.kmc_profile_polls.argtypes = [vp, P(i64)]
     L.kmc_kernel_launches.argtypes = [vp]
     L.kmc_kernel_launches.restype = i64
     L.kmc_domain_side.argtypes = [vp]

@@ -193,6 +193,12 @@ def kmc_profile_read(ctx):
     return ms.value, n.value
 
 
+def kmc_profile_polls(ctx) -> int:
+    n = _i64()
+    _check(ctx, load().kmc_profile_polls(ctx, ctypes.byref(n)))
+    return n.value
+
+
 def kmc_run_schedule_noalloc(L: int, L_d: int, k_steps: int, seed: int, J: float, beta: float, h: float,
                              nu: float, rate_law: int, sched_begin: int, n_schedules: int, schedule: int,
                              time_mode: int, obs_every: int, spins_dev: torch.Tensor,
@@ -391,6 +397,10 @@ class Lattice:
     def profile_read(self):
         """(summed run-kernel milliseconds, timed launches) since the last read."""
         return kmc_profile_read(self.ctx)
+
+    def profile_polls(self) -> int:
+        """Halo-poll iterations of the profiled launches since the last read."""
+        return kmc_profile_polls(self.ctx)
 
     def kernel_launches(self) -> int:
         return kmc_kernel_launches(self.ctx)

@@ -286,6 +286,16 @@ class Batch:
         return BatchGraph(g, "kmc batch step: %d replicas in %d groups, %d schedules"
                           % (sum(len(l.L) for l in self.lattices), len(self.lattices), n_sched))
 
+    def sync(self):
+        for lat, st in zip(self.lattices, self.streams):
+            with torch.cuda.stream(st):
+                lat.sync()
+
+    def close(self):
+        for lat in self.lattices:
+            lat.close()
+        self.lattices = []
+
 
 class BatchGraph:
     """A captured batch step; each replay is one NVTX range (Nsight Systems)."""
@@ -301,16 +311,6 @@ class BatchGraph:
         finally:
             torch.cuda.nvtx.range_pop()
 
-    def sync(self):
-        for lat, st in zip(self.lattices, self.streams):
-            with torch.cuda.stream(st):
-                lat.sync()
-
-    def close(self):
-        for lat in self.lattices:
-            lat.close()
-        self.lattices = []
-
 
 __all__ = ["DOMAIN_SIDES", "Batch", "GroupChoice", "Trial", "max_domain_side", "measure", "plan_candidates",
-           "tune_batch", "tune_plan", "KMC_INIT_PER_REPLICA"]
+           "tune_batch", "tune_plan", "KMC_INIT_PER_REPLICA", "BatchGraph"]

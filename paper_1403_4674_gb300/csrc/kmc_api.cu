@@ -67,6 +67,7 @@ struct kmc_ctx {
     uint8_t *d_tiles = nullptr;
     uint64_t *d_edges = nullptr, *d_dctr = nullptr;
     int *d_err = nullptr;
+    unsigned long long *d_polls = nullptr; // halo-poll iterations (profiling)
     unsigned long long *d_obs_acc = nullptr;
     size_t obs_acc_words = 0;
     void *d_tmp = nullptr; // n_dom * 32 + n_rep * 64 bytes, host-facing staging
@@ -864,7 +865,8 @@ void free_all(kmc_ctx *c)
                      (void **)&c->d_site_off, (void **)&c->d_blk_off, (void **)&c->d_seed, (void **)&c->d_A,
                      (void **)&c->d_gfix, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_tiles,
                      (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_err,
-                     (void **)&c->d_obs_acc, (void **)&c->d_tmp, (void **)&c->d_plan, (void **)&c->d_htab};
+                     (void **)&c->d_obs_acc, (void **)&c->d_tmp, (void **)&c->d_plan, (void **)&c->d_htab,
+                     (void **)&c->d_polls};
     for (void **p : ptrs) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -1383,6 +1385,7 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     RunKernel kern = run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad, cluster);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool prof = c->prof && !cap;
+    if (prof) P.polls = c->d_polls;
     if (prof) {
         CUDA_TRY(c, cudaEventCreate(&ev0));
         CUDA_TRY(c, cudaEventCreate(&ev1));
@@ -1742,7 +1745,25 @@ kmc_status kmc_lr_observable(kmc_ctx *c, const double *rec_dev, int32_t stride, 
 kmc_status kmc_profile(kmc_ctx *c, int32_t enable)
 {
     if (!c) return KMC_EINVAL;
+    if (enable && !c->d_polls) {
+        kmc_status st = dev_alloc(c, &c->d_polls, 1);
+        if (st != KMC_OK) return st;
+        CUDA_TRY(c, cudaMemset(c->d_polls, 0, sizeof(unsigned long long)));
+    }
     c->prof = enable != 0;
+    return KMC_OK;
+}
+
+kmc_status kmc_profile_polls(kmc_ctx *c, int64_t *polls)
+{
+    if (!c || !polls) return KMC_EINVAL;
+    unsigned long long v = 0;
+    if (c->d_polls) {
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        CUDA_TRY(c, cudaMemcpy(&v, c->d_polls, sizeof v, cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemset(c->d_polls, 0, sizeof v));
+    }
+    *polls = (int64_t)v;
     return KMC_OK;
 }
 

@@ -129,6 +129,9 @@ struct RunParams {
     uint64_t bar_limit_ns;
     int debug_extra;
     double lambda; // n_d * nu
+    // profiling: total over warps of the halo-poll iterations each warp ran
+    // beyond the first read (null: not counted)
+    unsigned long long *polls;
 };
 
 // ---------------------------------------------------------------------------
@@ -432,6 +435,48 @@ __device__ __forceinline__ int64_t warp_isum16(int64_t v)
     return v;
 }
 
+// Inclusive prefix over lanes 0..9 of w (64-bit; lanes >= 10 hold 0) in two
+// dependent rounds instead of four: lane c first sums w over c-3..c (three
+// shuffles issued together), then adds the sums that end at c-4 and c-8.
+// Lanes 0..11 receive their full prefix.
+__device__ __forceinline__ uint64_t prefix10(uint64_t w, int lane)
+{
+    const uint64_t a1 = __shfl_up_sync(FULL_WARP, w, 1);
+    const uint64_t a2 = __shfl_up_sync(FULL_WARP, w, 2);
+    const uint64_t a3 = __shfl_up_sync(FULL_WARP, w, 3);
+    const uint64_t s = w + (lane >= 1 ? a1 : 0ull) + (lane >= 2 ? a2 : 0ull) + (lane >= 3 ? a3 : 0ull);
+    const uint64_t b4 = __shfl_up_sync(FULL_WARP, s, 4);
+    const uint64_t b8 = __shfl_up_sync(FULL_WARP, s, 8);
+    return s + (lane >= 4 ? b4 : 0ull) + (lane >= 8 ? b8 : 0ull);
+}
+
+// Sum over the warp of 64-bit integers, modulo 2^64 (so also the exact sum of
+// int64 values whose total fits int64), from three 32-bit warp reductions of
+// 22-bit slices (each slice sum stays below 32 * 2^22 = 2^27); every lane
+// receives it.  The three reductions are independent, so one reduction's
+// latency replaces a chain of shuffles.
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t w)
+{
+    const uint32_t s0 = __reduce_add_sync(FULL_WARP, (uint32_t)(w & 0x3FFFFFull));
+    const uint32_t s1 = __reduce_add_sync(FULL_WARP, (uint32_t)((w >> 22) & 0x3FFFFFull));
+    const uint32_t s2 = __reduce_add_sync(FULL_WARP, (uint32_t)(w >> 44));
+    return (uint64_t)s0 + ((uint64_t)s1 << 22) + ((uint64_t)s2 << 44);
+}
+
+// Inclusive prefix over the warp's lanes of v (0 <= v < 2^B): one ballot per
+// bit of v (independent, so their latencies overlap) and, per lane, the
+// popcounts of the lanes at or below it, weighted by the bit.  Replaces a
+// five-round shuffle scan on the real-event path.
+template <int B>
+__device__ __forceinline__ uint32_t lane_prefix(uint32_t v, int lane)
+{
+    const uint32_t le = (lane == 31) ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+    uint32_t s = 0;
+#pragma unroll
+    for (int b = 0; b < B; ++b) s += (uint32_t)__popc(__ballot_sync(FULL_WARP, (v >> b) & 1u) & le) << b;
+    return s;
+}
+
 // Per-domain counters, identical in every lane during a visit.
 struct Counters {
     uint64_t H, flips, clkM;
@@ -571,8 +616,8 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
     pl.add_halo(lane, hN, hS, hW, hE); // pl holds the interior counts
     uint32_t n_c = class_counts<LD>(pl, lane);
     uint64_t Wc = (uint64_t)n_c * Ac;
-    uint64_t Cinc = prefix16(Wc, lane);
-    uint64_t R = __shfl_sync(FULL_WARP, Cinc, 9);
+    uint64_t Cinc = prefix10(Wc, lane);
+    uint64_t R = warp_sum64(Wc); // R' = sum_c n_c A_c <= 2^63
 
     // Score of a null step in the current state: d log(1 - R/n_d) =
     // -sum_c n_c a_c dlog a_c / (n_d - R).  The numerator is an exact
@@ -599,7 +644,8 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             const int Yh = cl ? reinterpret_cast<const int32_t *>(rt + RT_YH)[lane] : 0;
             // 2^-(Q+4) 2^P: a power of two, so the scaling below is exact
             const double scaleP = *reinterpret_cast<const double *>(rt + RT_GSCALE) * (double)(1ull << PBITS);
-            const int64_t xb = warp_isum16((int64_t)n_c * Xb), xh = warp_isum16((int64_t)n_c * Xh);
+            const int64_t xb = (int64_t)warp_sum64((uint64_t)((int64_t)n_c * Xb));
+            const int64_t xh = (int64_t)warp_sum64((uint64_t)((int64_t)n_c * Xh));
             // |n_c Y_c| <= n_d 2^17 <= 2^29: exact in one 32-bit warp reduction
             const int yb = __reduce_add_sync(FULL_WARP, (int)n_c * Yb);
             const int yh = __reduce_add_sync(FULL_WARP, (int)n_c * Yh);
@@ -682,12 +728,9 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
                 m[tt] = pl.mask_q(tt, UP, Q2, Q1, Q0);
                 cl += popc_row(m[tt]);
             }
-            uint32_t incl = cl;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t v = __shfl_up_sync(FULL_WARP, incl, off);
-                if (lane >= off) incl += v;
-            }
+            // members of class c in the lanes up to this one (cl <= RPL * LD)
+            constexpr int CB = (LD == 8) ? 4 : (LD == 16) ? 5 : (LD == 32) ? 6 : 8;
+            const uint32_t incl = lane_prefix<CB>(cl, lane);
             const uint32_t excl = incl - cl;
             const unsigned win = __ballot_sync(FULL_WARP, jj >= excl && jj < incl);
             if (!win) {
@@ -730,8 +773,8 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             pl.flip_update(lane, y, col, c < 5);
             n_c = class_counts<LD>(pl, lane);
             Wc = (uint64_t)n_c * Ac;
-            Cinc = prefix16(Wc, lane);
-            R = __shfl_sync(FULL_WARP, Cinc, 9);
+            Cinc = prefix10(Wc, lane);
+            R = warp_sum64(Wc);
             state_scored = false;
         }
     }
@@ -954,10 +997,12 @@ __global__ void __maxnreg__((run_kernel_regs<LD, GRAD>())) run_kernel(const RunP
     // neighbour has completed `need` visits, i.e. all its visits of earlier
     // phases (bounded spin).  A neighbour cannot complete another visit before
     // this one, so the stamp then equals `need`.
+    unsigned long long warp_polls = 0; // poll iterations of this warp (profiling)
     auto wait_halo = [&](const uint32_t *meta, uint32_t needNS, uint32_t needWE, uint64_t &hN, uint64_t &hS,
                          uint64_t &hW, uint64_t &hE) -> bool {
         uint32_t half = 0;
         int good = 1;
+        unsigned spins = 0;
         if (lane < 4 * HALVES) {
             const int dir = lane & 3, hf = lane >> 2;
             const uint32_t need = ((dir < 2) ? needNS : needWE) + (uint32_t)P.debug_extra;
@@ -972,7 +1017,6 @@ __global__ void __maxnreg__((run_kernel_regs<LD, GRAD>())) run_kernel(const RunP
             uint64_t v = load();
             if ((uint32_t)(v >> 32) < need) {
                 const uint64_t t0 = global_ns();
-                unsigned spins = 0;
                 while (true) {
                     v = load();
                     if ((uint32_t)(v >> 32) >= need) break;
@@ -989,6 +1033,8 @@ __global__ void __maxnreg__((run_kernel_regs<LD, GRAD>())) run_kernel(const RunP
             half = (uint32_t)v;
         }
         const bool all = __all_sync(FULL_WARP, good != 0);
+        // the warp runs the loop as long as its slowest lane
+        if (P.polls) warp_polls += __reduce_max_sync(FULL_WARP, spins);
         uint64_t h[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1233,6 +1279,7 @@ __global__ void __maxnreg__((run_kernel_regs<LD, GRAD>())) run_kernel(const RunP
         }
         gp += (uint64_t)nf;
     }
+    if (P.polls && lane == 0 && warp_polls != 0) atomicAdd(P.polls, warp_polls);
     // every warp of the CTA must have finished its visits before any warp
     // writes a slot back; in CLUSTER mode, also no CTA may leave while another
     // still reads its shared memory

@@ -56,6 +56,9 @@ def test_autotune_host_logic():
         autotune.max_domain_side(24)
     plans = autotune.plan_candidates(152)
     assert plans[0][0] == 0 and (2, 152, 16) in plans and (1, 16, 16) in plans
+    for name in ("run", "step", "capture", "sync", "close", "events_per_schedule"):
+        assert callable(getattr(autotune.Batch, name, None)), name
+    assert callable(getattr(autotune.BatchGraph, "replay", None))
 
 
 def test_missing_library_fails_loudly(monkeypatch):

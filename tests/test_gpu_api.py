@@ -273,3 +273,24 @@ def test_lattice_beyond_on_chip_capacity_is_refused():
     ok.set_rates([0.44], [0.0])
     ok.run(1)
     ok.close()
+
+
+def test_profile_counts_halo_polls():
+    """kmc_profile_polls: zero without profiling; with profiling it counts
+    the re-reads of neighbours' edge words, many when every wait runs out;
+    reading clears the count."""
+    kmc = _kmc()
+    lat = kmc.Lattice([256], 16, 4, [5])
+    lat.set_rates([0.4], [0.0])
+    assert lat.profile_polls() == 0
+    lat.profile(True)
+    lat.run(4)
+    normal = lat.profile_polls()
+    assert normal >= 0 and lat.profile_polls() == 0
+    kmc.kmc_debug_barrier(lat.ctx, 1, 5_000_000)  # 5 ms
+    lat.run(1)
+    with pytest.raises(kmc.KmcError):
+        lat.sync()
+    assert lat.profile_polls() > 1000
+    kmc.kmc_debug_barrier(lat.ctx, 0, 0)
+    lat.close()

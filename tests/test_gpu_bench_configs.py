@@ -150,23 +150,45 @@ def test_ising1024_full_timed_length_sampled_replica():
     lat.close()
 
 
-def test_grad_full_timed_length_sampled_replica():
+def _oracle_grad_replica(args):
+    """One oracle replica with scores (module level: runs in a spawned worker)."""
+    L, Ld, k, seed, beta, h, n = args
+    ref = orc.Replica(L=L, Ld=Ld, k=k, seed=seed, beta=beta, h=h)
+    ref.enable_score()
+    robs = ref.run(n, obs_every=n)
+    return ref.spins, robs, ref.score.sum(axis=0)
+
+
+def test_grad_full_timed_length_sampled_replicas():
     """The gradient benchmark's timed launch at its full length: 256 x 256^2
-    with scores on the 16-warp grid, 5000 schedules, one record at the end;
-    replica 0's spins, record and score checked against the oracle."""
+    with scores on the 16-warp grid, 5000 schedules (5.1e6 steps per
+    replica), one record at the end; four replicas' spins, records and
+    scores checked against the oracle (run in parallel worker processes),
+    the scores to 1e-12 relative."""
+    import multiprocessing as mp
     import paper_1403_4674_gb300 as kmc
     from paper_1403_4674_gb300 import workloads as wl
     w = wl.grad_replicas(256, seed_master=256, k=8)
-    n = len(w.L)
-    lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
-    lat.set_rates(w.beta, w.h)
-    lat.enable_grad(True)
-    lat.set_launch(2, _sm(), 16)
-    obs = lat.run(w.schedules, obs_every=w.schedules).cpu().numpy()
-    scores = lat.score().cpu().numpy()
-    _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [0], w.schedules, w.L, w.L_d, [w.k] * n, w.seeds,
-           w.beta, w.h, [0] * n, scores=scores, obs_every=w.schedules)
-    lat.close()
+    idx = [0, 1, 2, 131]
+    jobs = [(w.L[r], w.L_d, w.k, w.seeds[r], w.beta[r], w.h[r], w.schedules) for r in idx]
+    # the oracle workers start before this test's first GPU call, by spawn
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        pending = pool.map_async(_oracle_grad_replica, jobs)
+        lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
+        lat.set_rates(w.beta, w.h)
+        lat.enable_grad(True)
+        lat.set_launch(2, _sm(), 16)
+        obs = lat.run(w.schedules, obs_every=w.schedules).cpu().numpy()
+        scores = lat.score().cpu().numpy()
+        spins = [lat.replica_spins(r).cpu().numpy() for r in idx]
+        lat.close()
+        results = pending.get()
+    for r, sp, (rspins, robs, rscore) in zip(idx, spins, results):
+        assert np.array_equal(sp, rspins), "replica %d: spins differ" % r
+        assert np.array_equal(obs[:, r, :3], robs[:, :3]), "replica %d: e, m, e*m differ" % r
+        np.testing.assert_allclose(obs[:, r, 3], robs[:, 3], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(scores[r], rscore, rtol=1e-12, atol=1e-12, err_msg="replica %d" % r)
+        np.testing.assert_allclose(obs[:, r, 4:6], robs[:, 4:6], rtol=1e-12, atol=1e-12, err_msg="replica %d" % r)
 
 
 def test_batched_512_full_step_sample():
