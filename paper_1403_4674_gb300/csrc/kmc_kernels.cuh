@@ -435,48 +435,6 @@ __device__ __forceinline__ int64_t warp_isum16(int64_t v)
     return v;
 }
 
-// Inclusive prefix over lanes 0..9 of w (64-bit; lanes >= 10 hold 0) in two
-// dependent rounds instead of four: lane c first sums w over c-3..c (three
-// shuffles issued together), then adds the sums that end at c-4 and c-8.
-// Lanes 0..11 receive their full prefix.
-__device__ __forceinline__ uint64_t prefix10(uint64_t w, int lane)
-{
-    const uint64_t a1 = __shfl_up_sync(FULL_WARP, w, 1);
-    const uint64_t a2 = __shfl_up_sync(FULL_WARP, w, 2);
-    const uint64_t a3 = __shfl_up_sync(FULL_WARP, w, 3);
-    const uint64_t s = w + (lane >= 1 ? a1 : 0ull) + (lane >= 2 ? a2 : 0ull) + (lane >= 3 ? a3 : 0ull);
-    const uint64_t b4 = __shfl_up_sync(FULL_WARP, s, 4);
-    const uint64_t b8 = __shfl_up_sync(FULL_WARP, s, 8);
-    return s + (lane >= 4 ? b4 : 0ull) + (lane >= 8 ? b8 : 0ull);
-}
-
-// Sum over the warp of 64-bit integers, modulo 2^64 (so also the exact sum of
-// int64 values whose total fits int64), from three 32-bit warp reductions of
-// 22-bit slices (each slice sum stays below 32 * 2^22 = 2^27); every lane
-// receives it.  The three reductions are independent, so one reduction's
-// latency replaces a chain of shuffles.
-__device__ __forceinline__ uint64_t warp_sum64(uint64_t w)
-{
-    const uint32_t s0 = __reduce_add_sync(FULL_WARP, (uint32_t)(w & 0x3FFFFFull));
-    const uint32_t s1 = __reduce_add_sync(FULL_WARP, (uint32_t)((w >> 22) & 0x3FFFFFull));
-    const uint32_t s2 = __reduce_add_sync(FULL_WARP, (uint32_t)(w >> 44));
-    return (uint64_t)s0 + ((uint64_t)s1 << 22) + ((uint64_t)s2 << 44);
-}
-
-// Inclusive prefix over the warp's lanes of v (0 <= v < 2^B): one ballot per
-// bit of v (independent, so their latencies overlap) and, per lane, the
-// popcounts of the lanes at or below it, weighted by the bit.  Replaces a
-// five-round shuffle scan on the real-event path.
-template <int B>
-__device__ __forceinline__ uint32_t lane_prefix(uint32_t v, int lane)
-{
-    const uint32_t le = (lane == 31) ? 0xFFFFFFFFu : ((2u << lane) - 1u);
-    uint32_t s = 0;
-#pragma unroll
-    for (int b = 0; b < B; ++b) s += (uint32_t)__popc(__ballot_sync(FULL_WARP, (v >> b) & 1u) & le) << b;
-    return s;
-}
-
 // Per-domain counters, identical in every lane during a visit.
 struct Counters {
     uint64_t H, flips, clkM;
@@ -616,8 +574,8 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
     pl.add_halo(lane, hN, hS, hW, hE); // pl holds the interior counts
     uint32_t n_c = class_counts<LD>(pl, lane);
     uint64_t Wc = (uint64_t)n_c * Ac;
-    uint64_t Cinc = prefix10(Wc, lane);
-    uint64_t R = warp_sum64(Wc); // R' = sum_c n_c A_c <= 2^63
+    uint64_t Cinc = prefix16(Wc, lane);
+    uint64_t R = __shfl_sync(FULL_WARP, Cinc, 9);
 
     // Score of a null step in the current state: d log(1 - R/n_d) =
     // -sum_c n_c a_c dlog a_c / (n_d - R).  The numerator is an exact
@@ -644,8 +602,7 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             const int Yh = cl ? reinterpret_cast<const int32_t *>(rt + RT_YH)[lane] : 0;
             // 2^-(Q+4) 2^P: a power of two, so the scaling below is exact
             const double scaleP = *reinterpret_cast<const double *>(rt + RT_GSCALE) * (double)(1ull << PBITS);
-            const int64_t xb = (int64_t)warp_sum64((uint64_t)((int64_t)n_c * Xb));
-            const int64_t xh = (int64_t)warp_sum64((uint64_t)((int64_t)n_c * Xh));
+            const int64_t xb = warp_isum16((int64_t)n_c * Xb), xh = warp_isum16((int64_t)n_c * Xh);
             // |n_c Y_c| <= n_d 2^17 <= 2^29: exact in one 32-bit warp reduction
             const int yb = __reduce_add_sync(FULL_WARP, (int)n_c * Yb);
             const int yh = __reduce_add_sync(FULL_WARP, (int)n_c * Yh);
@@ -728,9 +685,12 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
                 m[tt] = pl.mask_q(tt, UP, Q2, Q1, Q0);
                 cl += popc_row(m[tt]);
             }
-            // members of class c in the lanes up to this one (cl <= RPL * LD)
-            constexpr int CB = (LD == 8) ? 4 : (LD == 16) ? 5 : (LD == 32) ? 6 : 8;
-            const uint32_t incl = lane_prefix<CB>(cl, lane);
+            uint32_t incl = cl;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t v = __shfl_up_sync(FULL_WARP, incl, off);
+                if (lane >= off) incl += v;
+            }
             const uint32_t excl = incl - cl;
             const unsigned win = __ballot_sync(FULL_WARP, jj >= excl && jj < incl);
             if (!win) {
@@ -773,8 +733,8 @@ __device__ __forceinline__ void visit_core(Planes<LD> &pl, Counters &cn, const R
             pl.flip_update(lane, y, col, c < 5);
             n_c = class_counts<LD>(pl, lane);
             Wc = (uint64_t)n_c * Ac;
-            Cinc = prefix10(Wc, lane);
-            R = warp_sum64(Wc);
+            Cinc = prefix16(Wc, lane);
+            R = __shfl_sync(FULL_WARP, Cinc, 9);
             state_scored = false;
         }
     }
