@@ -263,8 +263,10 @@ def reference_arm(args):
 # (smsp__inst_executed.sum), uniformised steps and halo-poll iterations
 # (kmc_profile_polls) of one launch, DRAM bytes read + written, and the
 # instructions of one poll iteration (a launch whose every wait runs out:
-# `bench.py --only pollcost`).  They hold for the kernel source with this
-# SHA-256 and are left out of the line once the source changes.
+# `bench.py --only pollcost`; per warp iteration for the warp kernels, per
+# thread iteration for the thread-per-domain kernel).  They hold for the
+# kernel sources with this SHA-256 and are left out of the line once the
+# sources change.
 NCU_KERNEL_SHA256 = None
 INST_PER_POLL = None
 NCU_COUNTS = {
@@ -299,22 +301,27 @@ def issue_roofline(workload: str, steps_per_s: float, sm_mhz: float, polls_per_s
     inst, steps, polls, _ = cnt
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak = ISSUE_PER_SM_CYCLE * sms * sm_mhz * 1e6
-    work = (inst - polls * INST_PER_POLL) / steps
+    ipp = INST_PER_POLL["threads" if workload == "batched" else "warp"]
+    work = (inst - polls * ipp) / steps
     pps = polls / steps if polls_per_step is None else polls_per_step
-    gross = work + pps * INST_PER_POLL
+    gross = work + pps * ipp
     return {"bound": "issue", "unit": "warp-inst/s", "peak": peak,
             "achieved": gross * steps_per_s, "frac": gross * steps_per_s / peak,
             "achieved_net": work * steps_per_s, "frac_net": work * steps_per_s / peak,
             "inst_per_step": gross, "inst_per_step_net": work, "polls_per_step": pps,
-            "inst_per_poll": INST_PER_POLL,
+            "inst_per_poll": ipp,
             "source": "ncu smsp__inst_executed of one timed launch, less its halo-poll iterations x instructions "
                       "per poll iteration; peak = 4 warp instructions per SM cycle x %d SMs x %.0f MHz" % (sms, sm_mhz)}
 
 
 def kernel_source_sha256() -> str:
+    """SHA-256 over the device sources of the run kernels (warp and thread plans)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_1403_4674_gb300", "csrc", "kmc_kernels.cuh"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("kmc_kernels.cuh", "kmc_tpd.cuh"):
+        with open(os.path.join(ROOT, "paper_1403_4674_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def device_time(step, steps: int, warmup: int, flush, stream):
@@ -638,6 +645,26 @@ def variant_pollcost(args, peaks, flush, stream):
     lat.close()
     if status != -5:
         raise RuntimeError("expected KMC_ETIMEOUT from the waits that run out, got %d" % status)
+    # the same for the thread-per-domain kernel (its count is per thread): the
+    # batched workload's 512 replicas at L_d = 8, k = 16 on the library's plan
+    from paper_1403_4674_gb300 import workloads as wl
+    wb = wl.batched_replicas(512, master=512)
+    lat = kmc.Lattice(wb.L, 8, 16, wb.seeds)
+    lat.set_rates(wb.beta, wb.h)
+    kmc.kmc_debug_barrier(lat.ctx, 1, limit_ns)
+    lat.profile(True)
+    lat.run(1)
+    try:
+        lat.sync()
+        status = 0
+    except kmc.KmcError as e:
+        status = e.status
+    out["threads"] = {"workload": "512 batched replicas, L_d = 8, k = 16", "launch": list(lat.launch()),
+                      "status_after_timeout": status, "polls": lat.profile_polls()}
+    kmc.kmc_debug_barrier(lat.ctx, 0, 0)
+    lat.close()
+    if status != -5:
+        raise RuntimeError("expected KMC_ETIMEOUT from the thread plan's waits, got %d" % status)
     return out
 
 

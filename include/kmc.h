@@ -342,14 +342,27 @@ kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
  *     neighbour domain is in the same CTA.  The run kernels hold 80 to 128
  *     registers per thread (by domain side and scores), so two or three CTAs
  *     of 8-12 warps can share an SM.
- * In both plans a visit starts as soon as its four neighbours have finished
+ *   KMC_LAUNCH_THREADS (L_d = 8 only): one thread per domain visit; a
+ *     cooperative grid of `size` CTAs of warps_per_cta warps, thread t
+ *     visiting the t-th, (t+T)-th, ... domain of each colour's list (T the
+ *     grid's threads).  An 8x8 domain is one 64-bit word, so a thread runs a
+ *     whole domain process in registers and a warp 32 of them at once, with
+ *     state, edge words and counters in global memory (L2).  It covers the
+ *     palindromic and fixed schedules with the exponential or expected
+ *     clock and no scores; a run that needs scores, fixed-time visits or
+ *     random colour orders first replaces the plan by the library's choice
+ *     among the others (KMC_EINVAL while the stream is capturing).  This is
+ *     the library's choice for L_d = 8 while scores are off.
+ * In all plans a visit starts as soon as its four neighbours have finished
  * their visits of earlier colour phases (per-domain dataflow instead of a
  * barrier per phase; Sec. 2.2 lets non-interacting domains run at once); observation records are built from per-visit changes,
  * so no point of a launch synchronises a whole replica.
  * warps_per_cta: 1..16.  Returns KMC_EINVAL if the plan cannot be scheduled
  * or the state does not fit in shared memory; the previous plan then stays.
- * Results do not depend on the plan. */
-enum { KMC_LAUNCH_AUTO = 0, KMC_LAUNCH_CLUSTER = 1, KMC_LAUNCH_GRID = 2 };
+ * Results do not depend on the plan, except the last bits of the FP64 domain
+ * clocks: the thread plan multiplies a visit's clock variates in step order,
+ * the others in pairs (both within 1e-12 of the oracle). */
+enum { KMC_LAUNCH_AUTO = 0, KMC_LAUNCH_CLUSTER = 1, KMC_LAUNCH_GRID = 2, KMC_LAUNCH_THREADS = 3 };
 kmc_status kmc_set_launch(kmc_ctx *ctx, int32_t mode, int32_t size, int32_t warps_per_cta);
 /* Current plan: mode, size (cluster size or CTA count), CTAs, warps per CTA,
  * dynamic shared memory per CTA.  Any pointer may be NULL.  KMC_EINVAL for a
@@ -380,7 +393,7 @@ kmc_status kmc_profile_read(kmc_ctx *ctx, double *run_kernel_ms, int64_t *run_ke
  * warps of the times a warp re-read a neighbour's edge word because the
  * neighbour had not finished its earlier visit yet (the first read of a halo
  * is not counted; a warp polling several neighbours at once counts its
- * slowest lane).  With instructions per poll iteration this separates
+ * slowest lane; under KMC_LAUNCH_THREADS the sum over threads).  With instructions per poll iteration this separates
  * busy-waiting from the visits' own instructions.  *polls is a host int64;
  * reading synchronises the context's stream and clears the count.  0 when
  * profiling was never enabled.  KMC_EINVAL for null arguments.  No

@@ -7,7 +7,7 @@ rejection-free domain steps.  The compute path is the sm_103a library
 ``libkmc_gb300.so`` behind the C ABI of ``include/kmc.h``; ``api`` is its thin
 Python binding.
 """
-from .api import (KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID, KMC_OBS_PASS, KMC_OBS_SCHEDULE, KMC_INIT_ALL_UP, KMC_INIT_KEEP, KMC_INIT_PER_REPLICA, KMC_INIT_RANDOM, KMC_RATE_BARKER,  # noqa: F401
+from .api import (KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID, KMC_LAUNCH_THREADS, KMC_OBS_PASS, KMC_OBS_SCHEDULE, KMC_INIT_ALL_UP, KMC_INIT_KEEP, KMC_INIT_PER_REPLICA, KMC_INIT_RANDOM, KMC_RATE_BARKER,  # noqa: F401
                   KMC_RATE_METROPOLIS, KMC_SCHEDULE_FIXED, KMC_SCHEDULE_PALINDROME,
                   KMC_SCHEDULE_RANDOM_PERM, KMC_TIME_EXPECTED, KMC_TIME_EXPONENTIAL, KMC_TIME_HORIZON, Lattice,
                   kmc_create_lattice, kmc_debug_barrier, kmc_destroy, kmc_domain_state,

@@ -17,7 +17,7 @@ KMC_INIT_RANDOM, KMC_INIT_ALL_UP, KMC_INIT_KEEP, KMC_INIT_PER_REPLICA = 0, 1, 2,
 KMC_RATE_METROPOLIS, KMC_RATE_BARKER = 0, 1
 KMC_SCHEDULE_PALINDROME, KMC_SCHEDULE_FIXED, KMC_SCHEDULE_RANDOM_PERM = 0, 1, 2
 KMC_TIME_EXPONENTIAL, KMC_TIME_EXPECTED, KMC_TIME_HORIZON = 0, 1, 2
-KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID = 0, 1, 2
+KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID, KMC_LAUNCH_THREADS = 0, 1, 2, 3
 KMC_OBS_SCHEDULE, KMC_OBS_PASS = 0, 1
 
 _i32, _i64, _u64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double

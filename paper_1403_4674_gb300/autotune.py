@@ -24,7 +24,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 import torch
 
 from .api import (KMC_INIT_PER_REPLICA, KMC_INIT_RANDOM, KMC_LAUNCH_AUTO, KMC_LAUNCH_CLUSTER,
-                  KMC_LAUNCH_GRID, KmcError, Lattice)
+                  KMC_LAUNCH_GRID, KMC_LAUNCH_THREADS, KmcError, Lattice)
 
 DOMAIN_SIDES = (8, 16, 32, 64)
 Plan = Tuple[int, int, int]  # (mode, size, warps per CTA) as for kmc_set_launch
@@ -54,6 +54,8 @@ def plan_candidates(sm_count: int) -> List[Plan]:
             (KMC_LAUNCH_GRID, 2 * sm_count, 10), (KMC_LAUNCH_GRID, 2 * sm_count, 12),
             (KMC_LAUNCH_GRID, 3 * sm_count, 8), (KMC_LAUNCH_GRID, 4 * sm_count, 5),
             (KMC_LAUNCH_GRID, 5 * sm_count, 4), (KMC_LAUNCH_GRID, 6 * sm_count, 4)]
+    # one thread per domain (8x8 domains only; the library refuses it otherwise)
+    out += [(KMC_LAUNCH_THREADS, m * sm_count, w) for m, w in ((2, 4), (1, 4), (3, 4), (4, 2), (2, 2))]
     return out
 
 

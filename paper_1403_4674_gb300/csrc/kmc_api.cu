@@ -9,6 +9,7 @@
 #include "kmc_kernels.cuh"
 #include "kmc_ring.cuh"
 #include "kmc_part.cuh"
+#include "kmc_tpd.cuh"
 
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
@@ -29,7 +30,8 @@ namespace {
 
 // Host copy of a launch plan (see RunParams for the device arrays).
 struct Plan {
-    int mode = 0;     // KMC_LAUNCH_CLUSTER or KMC_LAUNCH_GRID
+    int mode = 0;     // KMC_LAUNCH_CLUSTER, KMC_LAUNCH_GRID or KMC_LAUNCH_THREADS (then cta_col_off holds the
+                      // five offsets of the colour-sorted domain list slot_g; the other lists are empty)
     int cluster = 0;  // CTAs per cluster (CLUSTER mode)
     int n_cta = 0;
     int wpb = 0;
@@ -68,6 +70,7 @@ struct kmc_ctx {
     uint64_t *d_edges = nullptr, *d_dctr = nullptr;
     int *d_err = nullptr;
     unsigned long long *d_polls = nullptr; // halo-poll iterations (profiling)
+    uint64_t *d_obs_dom = nullptr;         // thread plans: open observation record per domain
     unsigned long long *d_obs_acc = nullptr;
     size_t obs_acc_words = 0;
     void *d_tmp = nullptr; // n_dom * 32 + n_rep * 64 bytes, host-facing staging
@@ -311,6 +314,8 @@ RunParams run_params(kmc_ctx *c)
     P.bar_limit_ns = c->bar_limit_ns;
     P.debug_extra = c->debug_extra;
     P.lambda = (double)(c->LD * c->LD) * c->nu;
+    P.dom_rep = c->d_dom_rep;
+    P.obs_dom = c->d_obs_dom;
     return P;
 }
 
@@ -528,12 +533,51 @@ kmc_status plan_grid(kmc_ctx *c, int n_cta, int wpb, Plan &pl)
     return KMC_OK;
 }
 
+// THREADS plan (L_d = 8): the domains sorted by colour, then by id, so that
+// consecutive threads hold neighbouring domains of one replica.
+kmc_status plan_threads(kmc_ctx *c, int n_cta, int wpb, Plan &pl)
+{
+    if (c->LD != 8) return fail(c, KMC_EINVAL, "the thread-per-domain plan needs L_d = 8 (L_d = %d)", c->LD);
+    if (n_cta < 1) return fail(c, KMC_EINVAL, "thread plan needs >= 1 CTA");
+    pl = Plan();
+    pl.mode = KMC_LAUNCH_THREADS;
+    pl.n_cta = n_cta;
+    pl.wpb = wpb;
+    std::vector<std::vector<uint32_t>> lists(4);
+    for (uint32_t g = 0; g < (uint32_t)c->n_dom; ++g) lists[domain_colour(c, g)].push_back(g);
+    pl.cta_col_off.assign(5, 0);
+    for (int q = 0; q < 4; ++q) {
+        pl.slot_g.insert(pl.slot_g.end(), lists[q].begin(), lists[q].end());
+        pl.cta_col_off[q + 1] = (uint32_t)pl.slot_g.size();
+    }
+    pl.smem = 0;
+    return KMC_OK;
+}
+
+using TpdKernel = void (*)(const RunParams);
+TpdKernel tpd_kernel_for(bool expo) { return expo ? tpd_kernel<true> : tpd_kernel<false>; }
+
 // Can this plan run?  Shared memory, cluster support and (GRID) co-residency.
 // Only the kernels this context can launch are checked: both clock modes,
 // and the score-carrying variant only while scores are on (it holds more
 // registers, so fewer of its CTAs fit an SM; kmc_enable_grad re-checks).
 kmc_status check_plan(kmc_ctx *c, const Plan &pl)
 {
+    if (pl.mode == KMC_LAUNCH_THREADS) {
+        if (c->grad) return fail(c, KMC_EINVAL, "the thread-per-domain plan has no score kernel");
+        for (int e = 0; e < 2; ++e) {
+            int nb = 0;
+            CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)tpd_kernel_for(e == 0),
+                                                                      pl.wpb * 32, 0));
+            if ((int64_t)nb * c->sm_count < pl.n_cta)
+                return fail(c, KMC_EINVAL, "%d CTAs of %d warps cannot be co-resident (%d per SM)", pl.n_cta, pl.wpb, nb);
+        }
+        if (!c->d_obs_dom) {
+            kmc_status st = dev_alloc(c, &c->d_obs_dom, (size_t)c->n_dom * TPD_OBS_WORDS);
+            if (st != KMC_OK) return st;
+        }
+        return KMC_OK;
+    }
     for (int e = 0; e < 2; ++e) {
         for (int gv = 0; gv < 2; ++gv) {
             if (gv == 1 && !c->grad) continue;
@@ -595,12 +639,34 @@ kmc_status install_plan(kmc_ctx *c, Plan &pl)
     return KMC_OK;
 }
 
-// Default plan: clusters when every replica fits one (smallest power of two
+kmc_status default_warp_plan(kmc_ctx *c);
+
+// The library's plan: one thread per domain visit for 8x8 domains while
+// scores are off (a warp then runs 32 domain processes), else the warp
+// plans below.
+kmc_status default_plan(kmc_ctx *c)
+{
+    if (c->LD == 8 && !c->grad) {
+        // two CTAs of 4 warps per SM: on the 512-replica batch this ran 1.6x
+        // faster than the four that fit (measured; the autotuner tries others)
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)tpd_kernel_for(true), 128, 0) == cudaSuccess &&
+            nb > 0) {
+            Plan pl;
+            if (plan_threads(c, std::min(nb, 2) * c->sm_count, 4, pl) == KMC_OK && install_plan(c, pl) == KMC_OK)
+                return KMC_OK;
+        }
+        cudaGetLastError();
+    }
+    return default_warp_plan(c);
+}
+
+// Warp plans: clusters when every replica fits one (smallest power of two
 // that covers the largest replica at one visit per warp and phase, up to 16);
 // otherwise the cooperative grid; if the batch's state does not fit the
 // grid's shared memory, clusters of 16 CTAs with several visits per warp and
 // phase (clusters run in waves, so the batch need not be resident at once).
-kmc_status default_plan(kmc_ctx *c)
+kmc_status default_warp_plan(kmc_ctx *c)
 {
     int need = 1;
     for (int r = 0; r < c->n_rep; ++r) {
@@ -866,7 +932,7 @@ void free_all(kmc_ctx *c)
                      (void **)&c->d_gfix, (void **)&c->d_grad, (void **)&c->d_h, (void **)&c->d_tiles,
                      (void **)&c->d_edges, (void **)&c->d_dctr, (void **)&c->d_err,
                      (void **)&c->d_obs_acc, (void **)&c->d_tmp, (void **)&c->d_plan, (void **)&c->d_htab,
-                     (void **)&c->d_polls};
+                     (void **)&c->d_polls, (void **)&c->d_obs_dom};
     for (void **p : ptrs) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -1219,6 +1285,9 @@ kmc_status kmc_set_launch(kmc_ctx *c, int32_t mode, int32_t size, int32_t warps_
     } else if (mode == KMC_LAUNCH_GRID) {
         if (size < 1) return fail(c, KMC_EINVAL, "grid needs >= 1 CTA");
         if ((s = plan_grid(c, size, warps_per_cta, pl)) != KMC_OK) return s;
+    } else if (mode == KMC_LAUNCH_THREADS) {
+        if (warps_per_cta > 4) return fail(c, KMC_EINVAL, "thread plans take 1..4 warps per CTA");
+        if ((s = plan_threads(c, size, warps_per_cta, pl)) != KMC_OK) return s;
     } else {
         return fail(c, KMC_EINVAL, "bad launch mode %d", mode);
     }
@@ -1348,6 +1417,16 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     const int64_t units = pass_obs ? n_schedules * (schedule == KMC_SCHEDULE_PALINDROME ? 8 : 4) : n_schedules;
     const int64_t n_obs = want_obs ? units / obs_every : 0;
     const bool cap = capturing(c);
+    if (c->plan.mode == KMC_LAUNCH_THREADS &&
+        (c->grad || time_mode == KMC_TIME_HORIZON || schedule == KMC_SCHEDULE_RANDOM_PERM)) {
+        // the thread kernel covers fixed-length visits of the palindromic
+        // and fixed schedules without scores: this run takes a warp plan
+        // (installed once the stream has drained: earlier launches read the
+        // plan buffer)
+        if (cap) return fail(c, KMC_EINVAL, "this run needs a warp launch plan; set one before capturing");
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if ((st = default_warp_plan(c)) != KMC_OK) return st;
+    }
     if (want_obs && n_obs > 0) {
         const size_t words = (size_t)n_obs * c->n_rep * OBS_WORDS;
         if (words > c->obs_acc_words && cap)
@@ -1382,7 +1461,9 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     P.visits_before = c->visits_done;
     const Plan &pl = c->plan;
     const bool cluster = pl.mode == KMC_LAUNCH_CLUSTER;
-    RunKernel kern = run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad, cluster);
+    const bool threads = pl.mode == KMC_LAUNCH_THREADS;
+    RunKernel kern = threads ? tpd_kernel_for(time_mode == KMC_TIME_EXPONENTIAL)
+                             : run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad, cluster);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool prof = c->prof && !cap;
     if (prof) P.polls = c->d_polls;

@@ -132,6 +132,10 @@ struct RunParams {
     // profiling: total over warps of the halo-poll iterations each warp ran
     // beyond the first read (null: not counted)
     unsigned long long *polls;
+    // thread-per-domain plans: domain -> replica, and each domain's open
+    // observation record
+    const uint32_t *dom_rep;
+    uint64_t *obs_dom;
 };
 
 // ---------------------------------------------------------------------------
