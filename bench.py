@@ -363,7 +363,8 @@ def variant_batched(args, peaks, flush, stream):
     n_sched, obs_every = (args.schedules if args.schedules > 0 else 200), 10  # shorter only for profiling captures
     t0 = time.perf_counter()
     sm = torch.cuda.get_device_properties(0).multi_processor_count
-    plans = [(0, 0, 16), (1, 4, 16), (1, 16, 16), (1, 16, 8), (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
+    plans = [(0, 0, 16), (3, 0, 4), (3, 3 * sm, 4), (3, 6 * sm, 2), (1, 4, 16), (1, 16, 16), (1, 16, 8),
+             (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
     choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
                                   Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=20)
     tune_s = time.perf_counter() - t0

@@ -343,7 +343,9 @@ kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
  *     registers per thread (by domain side and scores), so two or three CTAs
  *     of 8-12 warps can share an SM.
  *   KMC_LAUNCH_THREADS (L_d = 8 only): one thread per domain visit; a
- *     cooperative grid of `size` CTAs of warps_per_cta warps, thread t
+ *     cooperative grid of `size` CTAs (0: as many as spread each colour's
+ *     domains evenly over at most three 4-warp CTAs per SM) of warps_per_cta
+ *     (1..4) warps, thread t
  *     visiting the t-th, (t+T)-th, ... domain of each colour's list (T the
  *     grid's threads).  An 8x8 domain is one 64-bit word, so a thread runs a
  *     whole domain process in registers and a warp 32 of them at once, with

@@ -55,7 +55,8 @@ def plan_candidates(sm_count: int) -> List[Plan]:
             (KMC_LAUNCH_GRID, 3 * sm_count, 8), (KMC_LAUNCH_GRID, 4 * sm_count, 5),
             (KMC_LAUNCH_GRID, 5 * sm_count, 4), (KMC_LAUNCH_GRID, 6 * sm_count, 4)]
     # one thread per domain (8x8 domains only; the library refuses it otherwise)
-    out += [(KMC_LAUNCH_THREADS, m * sm_count, w) for m, w in ((2, 4), (1, 4), (3, 4), (4, 2), (2, 2))]
+    out += [(KMC_LAUNCH_THREADS, 0, 4)]  # the library's balanced thread grid
+    out += [(KMC_LAUNCH_THREADS, m * sm_count, w) for m, w in ((3, 4), (2, 4), (4, 4), (6, 2))]
     return out
 
 

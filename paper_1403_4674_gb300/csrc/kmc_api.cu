@@ -557,6 +557,21 @@ kmc_status plan_threads(kmc_ctx *c, int n_cta, int wpb, Plan &pl)
 using TpdKernel = void (*)(const RunParams);
 TpdKernel tpd_kernel_for(bool expo) { return expo ? tpd_kernel<true> : tpd_kernel<false>; }
 
+// CTAs of `wpb` warps for a thread plan: a phase takes as many rounds as its
+// busiest thread has domains, so the threads are the domains of a colour
+// divided by the rounds that up to three CTAs of 4 warps per SM need (the
+// fastest grid on the 512-replica batch, measured; more resident warps left
+// threads with one domain beside threads with two).
+int balanced_thread_ctas(const kmc_ctx *c, int wpb)
+{
+    const int64_t per_colour = (c->n_dom + 3) / 4;
+    const int64_t tmax = (int64_t)3 * 128 * c->sm_count;
+    const int64_t rounds = std::max<int64_t>(1, (per_colour + tmax - 1) / tmax);
+    const int64_t threads = (per_colour + rounds - 1) / rounds;
+    const int64_t per_cta = (int64_t)wpb * 32;
+    return (int)std::max<int64_t>(1, (threads + per_cta - 1) / per_cta);
+}
+
 // Can this plan run?  Shared memory, cluster support and (GRID) co-residency.
 // Only the kernels this context can launch are checked: both clock modes,
 // and the score-carrying variant only while scores are on (it holds more
@@ -647,15 +662,8 @@ kmc_status default_warp_plan(kmc_ctx *c);
 kmc_status default_plan(kmc_ctx *c)
 {
     if (c->LD == 8 && !c->grad) {
-        // two CTAs of 4 warps per SM: on the 512-replica batch this ran 1.6x
-        // faster than the four that fit (measured; the autotuner tries others)
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)tpd_kernel_for(true), 128, 0) == cudaSuccess &&
-            nb > 0) {
-            Plan pl;
-            if (plan_threads(c, std::min(nb, 2) * c->sm_count, 4, pl) == KMC_OK && install_plan(c, pl) == KMC_OK)
-                return KMC_OK;
-        }
+        Plan pl;
+        if (plan_threads(c, balanced_thread_ctas(c, 4), 4, pl) == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
         cudaGetLastError();
     }
     return default_warp_plan(c);
@@ -1287,7 +1295,9 @@ kmc_status kmc_set_launch(kmc_ctx *c, int32_t mode, int32_t size, int32_t warps_
         if ((s = plan_grid(c, size, warps_per_cta, pl)) != KMC_OK) return s;
     } else if (mode == KMC_LAUNCH_THREADS) {
         if (warps_per_cta > 4) return fail(c, KMC_EINVAL, "thread plans take 1..4 warps per CTA");
-        if ((s = plan_threads(c, size, warps_per_cta, pl)) != KMC_OK) return s;
+        // size 0: the balanced grid of the library's choice
+        if ((s = plan_threads(c, size > 0 ? size : balanced_thread_ctas(c, warps_per_cta), warps_per_cta, pl)) != KMC_OK)
+            return s;
     } else {
         return fail(c, KMC_EINVAL, "bad launch mode %d", mode);
     }

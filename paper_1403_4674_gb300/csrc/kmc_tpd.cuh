@@ -86,32 +86,6 @@ __device__ __forceinline__ void tpd_rates(uint64_t T, const TpdPlanes &pl, const
     }
 }
 
-// Spin until the 64-bit word at p carries a stamp of at least `need`
-// (bounded: gives up after limit_ns or once the error word is set).
-// Returns the word, or sets ok = false.
-__device__ __forceinline__ uint64_t tpd_wait_word(const uint64_t *p, uint32_t need, const RunParams &P, bool &ok,
-                                                  unsigned &spins)
-{
-    uint64_t v = ld_volatile_global(p);
-    if ((uint32_t)(v >> 32) >= need) return v;
-    const uint64_t t0 = global_ns();
-    unsigned n = 0;
-    while (true) {
-        v = ld_volatile_global(p);
-        ++spins;
-        if ((uint32_t)(v >> 32) >= need) return v;
-        if ((++n & 63u) == 0) {
-            if (*(volatile int *)P.err != 0) break;
-            if (global_ns() - t0 > P.bar_limit_ns) {
-                atomicCAS(P.err, 0, ERR_TIMEOUT);
-                break;
-            }
-        }
-    }
-    ok = false;
-    return v;
-}
-
 // The open record of domain g goes to its replica's record (records past
 // the launch's last one are dropped), as the warp kernel's flush.
 template <bool EXPO>
@@ -187,8 +161,16 @@ __global__ void __launch_bounds__(128) tpd_kernel(const RunParams P)
         const uint32_t needWE = gcount(colour ^ 1) + (uint32_t)P.debug_extra;
         const uint32_t after = gcount(colour) + 1;
         const int64_t pass = (int64_t)(gp - gp_begin);
-        for (uint32_t i = col_off[colour] + (uint32_t)tid; ok && i < col_off[colour + 1]; i += (uint32_t)nthreads) {
-            const uint32_t g = col_list[i];
+        // Rounds of one domain per thread: every lane of a warp runs the
+        // same trip counts (lanes without a domain in a round ride along
+        // predicated), so the halo wait and the steps stay warp-synchronous
+        // and the collectives below see the full warp.
+        const uint32_t lo = col_off[colour], hi = col_off[colour + 1];
+        const uint32_t rounds = (hi - lo + (uint32_t)nthreads - 1) / (uint32_t)nthreads;
+        for (uint32_t m = 0; m < rounds && ok; ++m) {
+            const uint32_t i = lo + (uint32_t)tid + m * (uint32_t)nthreads;
+            const bool has = i < hi;
+            const uint32_t g = has ? col_list[i] : col_list[lo];
             const uint32_t r = P.dom_rep[g];
             const uint32_t base = P.rep_dom_off[r];
             const uint32_t d = g - base;
@@ -200,7 +182,7 @@ __global__ void __launch_bounds__(128) tpd_kernel(const RunParams P)
             const uint32_t gE = base + (uint32_t)(by * Dx + (bx + 1) % Dx);
             // everything that does not depend on the halo first
             const int k = P.rep_k[r];
-            const int total = nf * k;
+            const int total = has ? nf * k : 0;
             const uint64_t seed = P.rep_seed[r];
             const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
             uint64_t A[10];
@@ -212,12 +194,51 @@ __global__ void __launch_bounds__(128) tpd_kernel(const RunParams P)
             uint64_t clkM = ctr[DCTR_CLKM];
             int64_t clkE = (int64_t)ctr[DCTR_CLKE];
             // halo: the N neighbour's S row, the S neighbour's N row, the W
-            // neighbour's E column, the E neighbour's W column (half 0 of each)
-            const uint32_t hN = (uint32_t)tpd_wait_word(P.edges + (size_t)gN * EDGE_WORDS + 2 * EDGE_S, needNS, P, ok, spins);
-            const uint32_t hS = (uint32_t)tpd_wait_word(P.edges + (size_t)gS * EDGE_WORDS + 2 * EDGE_N, needNS, P, ok, spins);
-            const uint32_t hW = (uint32_t)tpd_wait_word(P.edges + (size_t)gW * EDGE_WORDS + 2 * EDGE_E, needWE, P, ok, spins);
-            const uint32_t hE = (uint32_t)tpd_wait_word(P.edges + (size_t)gE * EDGE_WORDS + 2 * EDGE_W, needWE, P, ok, spins);
-            if (!ok) break;
+            // neighbour's E column, the E neighbour's W column (half 0 of
+            // each), stamped with the neighbour's completed visits; the warp
+            // re-reads until every lane's four are current (bounded)
+            const uint64_t *pN = P.edges + (size_t)gN * EDGE_WORDS + 2 * EDGE_S;
+            const uint64_t *pS = P.edges + (size_t)gS * EDGE_WORDS + 2 * EDGE_N;
+            const uint64_t *pW = P.edges + (size_t)gW * EDGE_WORDS + 2 * EDGE_E;
+            const uint64_t *pE = P.edges + (size_t)gE * EDGE_WORDS + 2 * EDGE_W;
+            uint64_t wN = 0, wS = 0, wW = 0, wE = 0;
+            auto current = [&]() {
+                return !has || ((uint32_t)(wN >> 32) >= needNS && (uint32_t)(wS >> 32) >= needNS &&
+                                (uint32_t)(wW >> 32) >= needWE && (uint32_t)(wE >> 32) >= needWE);
+            };
+            if (has) {
+                wN = ld_volatile_global(pN);
+                wS = ld_volatile_global(pS);
+                wW = ld_volatile_global(pW);
+                wE = ld_volatile_global(pE);
+            }
+            bool ready = current();
+            if (!__all_sync(FULL_WARP, ready)) {
+                const uint64_t t0 = global_ns();
+                unsigned n = 0;
+                while (true) {
+                    if (!ready) {
+                        wN = ld_volatile_global(pN);
+                        wS = ld_volatile_global(pS);
+                        wW = ld_volatile_global(pW);
+                        wE = ld_volatile_global(pE);
+                        ++spins;
+                        ready = current();
+                    }
+                    if (__all_sync(FULL_WARP, ready)) break;
+                    if ((++n & 63u) == 0) {
+                        const bool late = global_ns() - t0 > P.bar_limit_ns;
+                        const bool quit = late || *(volatile int *)P.err != 0;
+                        if (__any_sync(FULL_WARP, quit)) {
+                            if (late) atomicCAS(P.err, 0, ERR_TIMEOUT);
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+                if (!ok) break;
+            }
+            const uint32_t hN = (uint32_t)wN, hS = (uint32_t)wS, hW = (uint32_t)wW, hE = (uint32_t)wE;
 
             TpdPlanes pl;
             pl.build(T, hN, hS, hW, hE);
@@ -227,21 +248,23 @@ __global__ void __launch_bounds__(128) tpd_kernel(const RunParams P)
             int dbonds = 0, dmag = 0;
             uint64_t vM = 1ull << 63;
             int64_t vE = 0;
-            for (int s = 0; s < total; ++s) {
+            const int smax = (int)__reduce_max_sync(FULL_WARP, (unsigned)total);
+            for (int s = 0; s < smax; ++s) {
+                const bool act = s < total;
                 const int f = s / k;
                 const int j = s - f * k;
                 const uint64_t np = np0 + (uint64_t)f;
                 const uint4 w = philox4x32_10(make_uint4((uint32_t)j, d, (uint32_t)np, (uint32_t)(np >> 32) & 0xFFFFFFu),
                                               key);
                 const uint64_t tgt = (((uint64_t)w.y << 32) | w.x) >> 1;
-                if (EXPO) {
-                    // clock variate v = V 2^-53 as a normalised mantissa m / 2^63 times 2^(10 - z)
+                if (EXPO && act) {
+                    // clock variate v = V 2^-53 as a normalised mantissa m / 2^63
+                    // times 2^(10 - z), into the visit's product
                     const uint64_t V = ((((uint64_t)w.w << 32) | w.z) >> 11) + 1ull;
                     const int z = __clzll((long long)V);
-                    mant_mul(clkM, clkE, V << z, (int64_t)(10 - z));
                     mant_mul(vM, vE, V << z, (int64_t)(10 - z));
                 }
-                if (tgt >= C[9]) continue; // null step (App. A: the diagonal 1 - R/n_d)
+                if (!act || tgt >= C[9]) continue; // null step (App. A: the diagonal 1 - R/n_d)
                 // class: the first c with tgt < C_c; C_{c-1} and A_c along with it
                 int c = 0;
                 uint64_t Cprev = 0, Ac = A[0];
@@ -275,6 +298,8 @@ __global__ void __launch_bounds__(128) tpd_kernel(const RunParams P)
                     tpd_rates(T, pl, A, C);
                 }
             }
+            if (!has) continue;
+            if (EXPO) mant_mul(clkM, clkE, vM, vE); // the domain clock takes the visit's product
             // edges first (neighbours wait for them), then tile and counters
             uint64_t *ew = P.edges + (size_t)g * EDGE_WORDS;
             const uint64_t cnt = (uint64_t)after << 32;
