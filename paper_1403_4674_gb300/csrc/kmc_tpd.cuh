@@ -249,11 +249,15 @@ __global__ void __launch_bounds__(128) tpd_kernel(const RunParams P)
             uint64_t vM = 1ull << 63;
             int64_t vE = 0;
             const int smax = (int)__reduce_max_sync(FULL_WARP, (unsigned)total);
+            // step s = f k + j of the visit: step j of global phase np0 + f
+            int j = -1;
+            uint64_t np = np0;
             for (int s = 0; s < smax; ++s) {
                 const bool act = s < total;
-                const int f = s / k;
-                const int j = s - f * k;
-                const uint64_t np = np0 + (uint64_t)f;
+                if (++j == k) {
+                    j = 0;
+                    ++np;
+                }
                 const uint4 w = philox4x32_10(make_uint4((uint32_t)j, d, (uint32_t)np, (uint32_t)(np >> 32) & 0xFFFFFFu),
                                               key);
                 const uint64_t tgt = (((uint64_t)w.y << 32) | w.x) >> 1;
