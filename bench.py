@@ -363,10 +363,15 @@ def variant_batched(args, peaks, flush, stream):
     n_sched, obs_every = (args.schedules if args.schedules > 0 else 200), 10  # shorter only for profiling captures
     t0 = time.perf_counter()
     sm = torch.cuda.get_device_properties(0).multi_processor_count
-    plans = [(0, 0, 16), (3, 0, 4), (3, 3 * sm, 4), (3, 6 * sm, 2), (1, 4, 16), (1, 16, 16), (1, 16, 8),
-             (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
-    choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
-                                  Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=20)
+    if args.plan:
+        # profiling runs: the whole batch as one group at L_d = 8, k = 16 on the given plan
+        choices = [autotune.GroupChoice(replicas=list(range(len(w.L))), L_d=8, k=16,
+                                        plan=tuple(int(x) for x in args.plan.split(",")), events_per_s=0.0)]
+    else:
+        plans = [(0, 0, 16), (3, 0, 4), (3, 3 * sm, 4), (3, 6 * sm, 2), (1, 4, 16), (1, 16, 16), (1, 16, 8),
+                 (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
+        choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
+                                      Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=20)
     tune_s = time.perf_counter() - t0
     # oracle on a 64-replica subset, each with its group's domain side and k
     grp = {}
@@ -381,6 +386,17 @@ def variant_batched(args, peaks, flush, stream):
     graph = batch.capture(n_sched, obs_every, reset=0)
     ms = device_time(graph.replay, args.steps, args.warmup, flush, stream)
     ev = batch.events_per_schedule() * n_sched
+    # the ncu counters were taken on the whole batch as one group at L_d = 8,
+    # k = 16 on a thread-per-domain plan (its state stays in L2 on any such plan)
+    one_thread_group = len(choices) == 1 and choices[0].L_d == 8 and choices[0].k == 16 and choices[0].plan[0] == 3
+    polls = None
+    if args.plan:
+        # profiling runs: one more step outside the graph, profiled, for its halo-poll count
+        for lat in batch.lattices:
+            lat.profile(True)
+        batch.run(n_sched, obs_every, reset=0)
+        batch.sync()
+        polls = sum(lat.profile_polls() for lat in batch.lattices)
     by = sum(schedule_bytes(lat.L, lat.L_d, lat.ks) for lat in batch.lattices) * n_sched
     dev_s = sum(ms) / 1000.0
     out = {"value": ev * args.steps / dev_s, "unit": UNIT, "ms_per_step": statistics.mean(ms),
@@ -389,10 +405,12 @@ def variant_batched(args, peaks, flush, stream):
                        "one CUDA graph per step" % (n_sched, obs_every),
            "groups": [{"replicas": len(ch.replicas), "L_d": ch.L_d, "k": ch.k, "plan": list(ch.plan),
                        "tuned_events_per_s": ch.events_per_s} for ch in choices],
-           "tune_s": tune_s, "events_per_step": ev,
-           "roofline": roofline(by, dev_s / args.steps, peaks), "cpu_baseline": cpu}
+           "tune_s": tune_s, "events_per_step": ev, "polls_per_launch": polls,
+           "roofline": roofline(by, dev_s / args.steps, peaks, launch_traffic("batched") if one_thread_group else None),
+           "cpu_baseline": cpu}
     out["roofline"]["note"] = "step-level: the groups' run kernels overlap on concurrent streams"
-    iss = issue_roofline("batched", ev * args.steps / dev_s, float(peaks.get("sm_max_mhz", 2070.0)))
+    iss = issue_roofline("batched", ev * args.steps / dev_s, float(peaks.get("sm_max_mhz", 2070.0))) \
+        if one_thread_group else None
     if iss is not None:
         iss["note"] = "counts of the single-context configuration of the same batch; steps/s of the whole step"
         out["roofline"]["issue"] = iss
@@ -413,7 +431,11 @@ def variant_grad(args, peaks, flush, stream):
     lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds, init=0)
     lat.set_rates(w.beta, w.h)
     lat.enable_grad(True)
-    plan, _ = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=100)
+    if args.plan:
+        plan = tuple(int(x) for x in args.plan.split(","))
+        lat.set_launch(*plan)
+    else:
+        plan, _ = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=100)
     lat.profile(True)
     n = args.schedules if args.schedules > 0 else w.schedules  # a shorter run only for profiling captures
     out_obs = torch.empty((1, lat.n_replicas, 6), dtype=torch.float64, device="cuda")

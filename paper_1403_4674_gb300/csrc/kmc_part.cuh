@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
 
     uint64_t A = 0;
     if (lane < 10) A = P.A[(size_t)tr * 10 + lane];
+    // 1/A_c from below (A_c rounded up, its reciprocal rounded down)
+    const float invAf = (lane < 10) ? __frcp_rd(kmcdev::u64_to_float_ru(A)) : 0.0f;
     const uint64_t seed = P.seed[tr];
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const double hr = P.h[tr];
@@ -221,8 +223,12 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
             const uint64_t t = __shfl_sync(FULL_WARP, tgt, jx);
             const unsigned sel = __ballot_sync(FULL_WARP, lane < 10 && t < Cinc);
             const int c = __ffs(sel) - 1;
-            uint32_t q = 0;
-            if (lane == c) q = (uint32_t)((t - (Cinc - Wc)) / A); // < n_c
+            // exact q = floor((t - C_{c-1}) / A_c) < n_c <= 16384 from an FP32
+            // estimate with every rounding toward the lower side (so it is q or
+            // q - 1) and one integer comparison, instead of a 64-bit division
+            const uint64_t xq = t - (Cinc - Wc);
+            uint32_t q = (uint32_t)__fmul_rz(kmcdev::u64_to_float_rz(xq), invAf);
+            q = (xq - (uint64_t)q * A >= A) ? q + 1u : q;
             const uint32_t jj = __shfl_sync(FULL_WARP, q, c);
             // jj-th member of class c in row-major order
             uint32_t cl = 0;
