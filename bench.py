@@ -880,6 +880,8 @@ def main():
                            "parallelism": ("replicas only, %d ranks" % world if world > 1 else "1 GPU") +
                                           ", one run-kernel launch per step",
                            "plan": list(plan), "launch": list(lat.launch()), "tune_s": tune_s,
+                           "threads_per_domain": "one warp per 32x32 domain (not a tuner knob; 8x8 domains of "
+                                                 "other workloads run one thread per domain)",
                            "wall_s": wall},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "bit_exact": bit_exact,
                 "clocks": clk, "variants": variants}

@@ -31,9 +31,16 @@ constexpr int PART_MAX_L = 128;
 constexpr int PART_PHASE_SLOTS = 64; // Philox phase index np = n*64 + p
 constexpr int PART_BLOCKS = 0, PART_STRIPES = 1;
 constexpr uint32_t PART_TAG_PERM = 2u;
-// shared memory per warp (64-bit words): bit rows, the domain order, and the
-// class counts of every domain (int [64][10])
-constexpr int PART_WARP_WORDS = 2 * PART_MAX_L + 8 + 64 * 10 / 2;
+// shared memory per warp (64-bit words): bit rows, the domain order, the
+// class counts of every domain (int [64][10]), the rate sum R' of every
+// domain (u64 [64]), the fixed-point rates (u64 [16]) and, when the lattice
+// has at most PART_RC_ROWS domain rows (N_D x domain height), the class
+// counts of every domain row (u8 [rows][10], in 32-bit words)
+constexpr int PART_RC_ROWS = 512;
+constexpr int PART_OFF_ORDER = 2 * PART_MAX_L, PART_OFF_DCOUNT = PART_OFF_ORDER + 8,
+              PART_OFF_DR = PART_OFF_DCOUNT + 64 * 10 / 2, PART_OFF_ATAB = PART_OFF_DR + 64,
+              PART_OFF_RC = PART_OFF_ATAB + 16;
+constexpr int PART_WARP_WORDS = PART_OFF_RC + PART_RC_ROWS * 10 / 8;
 
 struct PartParams {
     int n_traj, L, kind, ND, k;
@@ -150,8 +157,11 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
     if (tr >= P.n_traj) return; // whole warps only; no CTA-wide barrier below
     const int L = P.L;
     uint64_t *rows = part_smem + (size_t)warp * PART_WARP_WORDS;
-    uint8_t *order = reinterpret_cast<uint8_t *>(rows + 2 * PART_MAX_L);
-    int *dcount = reinterpret_cast<int *>(rows + 2 * PART_MAX_L + 8); // [N_D][10] class counts
+    uint8_t *order = reinterpret_cast<uint8_t *>(rows + PART_OFF_ORDER);
+    int *dcount = reinterpret_cast<int *>(rows + PART_OFF_DCOUNT);              // [N_D][10] class counts
+    unsigned long long *dR = reinterpret_cast<unsigned long long *>(rows + PART_OFF_DR); // [N_D] R'
+    uint64_t *Atab = rows + PART_OFF_ATAB;                                       // [10] A_c
+    uint8_t *rc = reinterpret_cast<uint8_t *>(rows + PART_OFF_RC);               // [N_D * H][10]
     const u128 Lm = (L == 128) ? ~(u128)0 : (((u128)1 << L) - 1);
     const int8_t *sp = P.spins + (size_t)tr * L * L;
 
@@ -196,14 +206,31 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
             y0 = (d / P.Dx) * W;
         }
     };
-    // class counts of every domain, kept up to date flip by flip
+    // class counts of every domain (and of every domain row, when they
+    // fit) and every domain's rate sum, kept up to date flip by flip
+    const bool use_rc = P.ND * Hd <= PART_RC_ROWS;
+    if (lane < 10) Atab[lane] = A;
     for (int d = 0; d < P.ND; ++d) {
         int x0, y0;
         domain_origin(d, x0, y0);
         const uint32_t n = part_counts(rows, lane, y0, Hd, RPL, L, Lm, DM0 << x0);
         if (lane < 10) dcount[d * 10 + lane] = (int)n;
+        const uint64_t R0 = __shfl_sync(FULL_WARP, kmcdev::prefix16((uint64_t)n * A, lane), 9);
+        if (lane == 0) dR[d] = R0;
+        if (use_rc) {
+            for (int yy = lane; yy < Hd; yy += 32) {
+                const RowPlanes pr = row_planes(rows, y0 + yy, L, Lm, DM0 << x0);
+                for (int c = 0; c < 10; ++c) rc[(d * Hd + yy) * 10 + c] = (uint8_t)popc128(class_mask(pr, c));
+            }
+        }
     }
     __syncwarp();
+    // a domain row's count byte: the 32-bit word holding it and its shift
+    auto rc_word = [&](int d, int yy, int c, int &sh) {
+        const int b = (d * Hd + yy) * 10 + c;
+        sh = 8 * (b & 3);
+        return reinterpret_cast<unsigned *>(rc) + (b >> 2);
+    };
 
     // The real events among the steps held by lanes [lo, hi): lane i holds
     // step j = i - lo + jbase of the visit (target tgt, ~0 for no step).
@@ -211,10 +238,12 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
     // and member, flips, and updates the class counts of the domains the five
     // touched sites belong to.
     auto events = [&](int d, uint64_t np, int x0, int y0, u128 DM, uint64_t tgt, int lo, int hi, int jbase) {
+        // a visit without real events needs only the domain's rate sum
+        uint64_t R = dR[d];
+        if (!__any_sync(FULL_WARP, lane >= lo && lane < hi && tgt < R)) return;
         uint32_t n_c = (lane < 10) ? (uint32_t)dcount[d * 10 + lane] : 0u;
         uint64_t Wc = (uint64_t)n_c * A;
         uint64_t Cinc = kmcdev::prefix16(Wc, lane);
-        uint64_t R = __shfl_sync(FULL_WARP, Cinc, 9);
         int pos = lo;
         while (true) {
             const unsigned real = __ballot_sync(FULL_WARP, lane >= pos && lane < hi && tgt < R);
@@ -235,7 +264,8 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
             for (int tt = 0; tt < RPL; ++tt) {
                 const int yy = lane * RPL + tt;
                 if (yy >= Hd) break;
-                cl += (uint32_t)popc128(class_mask(row_planes(rows, y0 + yy, L, Lm, DM), c));
+                cl += use_rc ? (uint32_t)rc[(d * Hd + yy) * 10 + c]
+                             : (uint32_t)popc128(class_mask(row_planes(rows, y0 + yy, L, Lm, DM), c));
             }
             uint32_t incl = cl;
 #pragma unroll
@@ -255,6 +285,17 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
                 uint32_t rr = jj - excl;
                 for (int tt = 0; tt < RPL; ++tt) {
                     const int yy = lane * RPL + tt;
+                    if (use_rc) {
+                        // the row from its count, then that row's class mask alone
+                        const uint32_t pc = rc[(d * Hd + yy) * 10 + c];
+                        if (rr < pc) {
+                            const u128 mk = class_mask(row_planes(rows, y0 + yy, L, Lm, DM), c);
+                            yx = ((uint32_t)yy << 8) | (uint32_t)select128(mk, rr);
+                            break;
+                        }
+                        rr -= pc;
+                        continue;
+                    }
                     const u128 mk = class_mask(row_planes(rows, y0 + yy, L, Lm, DM), c);
                     const uint32_t pc = (uint32_t)popc128(mk);
                     if (rr < pc) {
@@ -286,6 +327,15 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
                 if (new_c != old_c) {
                     atomicAdd(&dcount[sd * 10 + old_c], -1);
                     atomicAdd(&dcount[sd * 10 + new_c], 1);
+                    atomicAdd(&dR[sd], (unsigned long long)(Atab[new_c] - Atab[old_c])); // mod 2^64
+                    if (use_rc) {
+                        const int syy = (P.kind == PART_STRIPES) ? sy : sy - (sd / P.Dx) * W;
+                        int sh0, sh1;
+                        unsigned *w0 = rc_word(sd, syy, old_c, sh0);
+                        unsigned *w1 = rc_word(sd, syy, new_c, sh1);
+                        atomicSub(w0, 1u << sh0); // the byte holds at least this site
+                        atomicAdd(w1, 1u << sh1);
+                    }
                 }
             }
             __syncwarp();
@@ -296,7 +346,7 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
             n_c = (lane < 10) ? (uint32_t)dcount[d * 10 + lane] : 0u;
             Wc = (uint64_t)n_c * A;
             Cinc = kmcdev::prefix16(Wc, lane);
-            R = __shfl_sync(FULL_WARP, Cinc, 9);
+            R = dR[d];
         }
     };
 
