@@ -267,10 +267,14 @@ def reference_arm(args):
 # thread iteration for the thread-per-domain kernel).  They hold for the
 # kernel sources with this SHA-256 and are left out of the line once the
 # sources change.
-NCU_KERNEL_SHA256 = None
-INST_PER_POLL = None
+NCU_KERNEL_SHA256 = "c6082338e7624860ab0f10a762086cc1e094e0e123ff3223d4087b046854577d"
+INST_PER_POLL = {"warp": 22.24, "threads": 0.85}
 NCU_COUNTS = {
-    # workload: (warp instructions, steps, poll iterations, DRAM bytes) of one launch
+    # workload: (warp instructions, steps, poll iterations or None, DRAM bytes) of one launch
+    "ising1024": (424687555833, 2580480000, 1575845124, 6436608),
+    "grad": (281940731803, 1310720000, None, 4595456),
+    "lattice8192": (144442866856, 524288000, 434751244, 11270400),
+    "batched": (38921430049, 2636876800, 168056044, 7594135552),
 }
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 
@@ -299,10 +303,13 @@ def issue_roofline(workload: str, steps_per_s: float, sm_mhz: float, polls_per_s
     if cnt is None or INST_PER_POLL is None:
         return None
     inst, steps, polls, _ = cnt
+    if polls is None and polls_per_step is None:
+        return None
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak = ISSUE_PER_SM_CYCLE * sms * sm_mhz * 1e6
     ipp = INST_PER_POLL["threads" if workload == "batched" else "warp"]
-    work = (inst - polls * ipp) / steps
+    # the capture's polls where it counted them, else this run's
+    work = inst / steps - (polls / steps if polls is not None else polls_per_step) * ipp
     pps = polls / steps if polls_per_step is None else polls_per_step
     gross = work + pps * ipp
     return {"bound": "issue", "unit": "warp-inst/s", "peak": peak,
@@ -315,12 +322,19 @@ def issue_roofline(workload: str, steps_per_s: float, sm_mhz: float, polls_per_s
 
 
 def kernel_source_sha256() -> str:
-    """SHA-256 over the device sources of the run kernels (warp and thread plans)."""
+    """SHA-256 over the device code of the run kernels (warp and thread plans),
+    comments and blank lines left out, so that a comment edit keeps counters
+    taken on the same code."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in ("kmc_kernels.cuh", "kmc_tpd.cuh"):
-        with open(os.path.join(ROOT, "paper_1403_4674_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1403_4674_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()
 
 
@@ -463,7 +477,7 @@ def variant_grad(args, peaks, flush, stream):
                        "LR gradients of <e> and <m> w.r.t. (beta, h) per step" % n,
            "plan": list(plan), "launch": list(lat.launch()),
            "lr_grad_e_beta_h": [float(ge[0]), float(ge[1])], "lr_grad_m_beta_h": [float(gm[0]), float(gm[1])],
-           "events_per_step": ev, "cpu_baseline": cpu,
+           "events_per_step": ev, "cpu_baseline": cpu, "polls_per_launch": polls / max(run_n, 1),
            "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks, launch_traffic("grad"))}
     iss = issue_roofline("grad", ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0,
                          float(peaks.get("sm_max_mhz", 2070.0)), polls / max(ev * max(run_n, 1), 1))

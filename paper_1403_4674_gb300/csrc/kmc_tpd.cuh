@@ -18,9 +18,10 @@
 // row-major (= bit) order.  Domain state, edge words, counters and the open
 // observation record live in global memory (L2): each visit reads its tile
 // and counters, waits for its neighbours' stamped edge words, runs, and
-// writes them back; only the domain's owner thread ever touches its tile,
-// counters and record, and the stamped edge words carry data and visit
-// count in one 64-bit store.
+// writes them back.  Only the domain's owner thread writes its tile,
+// counters and record (and only it reads them for use: a lane without a
+// domain in a round reads some domain's and discards the values), and the
+// stamped edge words carry data and visit count in one 64-bit store.
 //
 // Scope: palindromic and fixed colour schedules, exponential and expected
 // clocks, per-replica k, records at schedule endpoints or every colour pass.
