@@ -267,47 +267,52 @@ def reference_arm(args):
 # thread iteration for the thread-per-domain kernel).  They hold for the
 # kernel sources with this SHA-256 and are left out of the line once the
 # sources change.
-NCU_KERNEL_SHA256 = "c6082338e7624860ab0f10a762086cc1e094e0e123ff3223d4087b046854577d"
-INST_PER_POLL = {"warp": 22.24, "threads": 0.85}
+NCU_KERNEL_SHA256 = None
+# instructions of one poll iteration: per warp iteration for the warp kernels
+# and the shared-memory thread kernel, per thread re-read for the 8x8 one
+INST_PER_POLL = {"run_kernel": 22.24, "tpd_kernel": 0.85, "tpdr_kernel": None}
 NCU_COUNTS = {
-    # workload: (warp instructions, steps, poll iterations or None, DRAM bytes) of one launch
-    "ising1024": (424687555833, 2580480000, 1575845124, 6436608),
-    "grad": (281940731803, 1310720000, None, 4595456),
-    "lattice8192": (144442866856, 524288000, 434751244, 11270400),
-    "batched": (38921430049, 2636876800, 168056044, 7594135552),
+    # (workload, kernel): (warp instructions, steps, poll iterations or None, DRAM bytes) of one launch
 }
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 
 
-def ncu_counts(workload: str):
-    """The workload's ncu counters if they were taken on the current kernel source."""
+def run_kernel_name(lat) -> str:
+    """The persistent kernel a lattice's plan launches."""
+    if lat.launch()[0] == 3:
+        return "tpd_kernel" if lat.L_d == 8 else "tpdr_kernel"
+    return "run_kernel"
+
+
+def ncu_counts(workload: str, kernel: str):
+    """The workload's ncu counters on that kernel, if taken on the current kernel source."""
     if NCU_KERNEL_SHA256 is None or NCU_KERNEL_SHA256 != kernel_source_sha256():
         return None
-    return NCU_COUNTS.get(workload)
+    return NCU_COUNTS.get((workload, kernel))
 
 
-def launch_traffic(workload: str):
+def launch_traffic(workload: str, kernel: str):
     """DRAM bytes (read + write) of one timed launch from the workload's ncu capture, or None."""
-    cnt = ncu_counts(workload)
+    cnt = ncu_counts(workload, kernel)
     return None if cnt is None else cnt[3]
 
 
-def issue_roofline(workload: str, steps_per_s: float, sm_mhz: float, polls_per_step=None):
+def issue_roofline(workload: str, kernel: str, steps_per_s: float, sm_mhz: float, polls_per_step=None):
     """Issue-rate view: warp instructions per second against 4 per SM cycle x
     the SMs x the SM clock.  Gross counts every instruction, halo polls
     included; net leaves out the poll iterations (busy-waiting, not work).
     With polls_per_step (this run's own count) the gross figure uses it, else
     the capture's."""
     import torch
-    cnt = ncu_counts(workload)
-    if cnt is None or INST_PER_POLL is None:
+    cnt = ncu_counts(workload, kernel)
+    ipp = INST_PER_POLL.get(kernel)
+    if cnt is None or ipp is None:
         return None
     inst, steps, polls, _ = cnt
     if polls is None and polls_per_step is None:
         return None
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak = ISSUE_PER_SM_CYCLE * sms * sm_mhz * 1e6
-    ipp = INST_PER_POLL["threads" if workload == "batched" else "warp"]
     # the capture's polls where it counted them, else this run's
     work = inst / steps - (polls / steps if polls is not None else polls_per_step) * ipp
     pps = polls / steps if polls_per_step is None else polls_per_step
@@ -328,7 +333,7 @@ def kernel_source_sha256() -> str:
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("kmc_kernels.cuh", "kmc_tpd.cuh"):
+    for name in ("kmc_kernels.cuh", "kmc_tpd.cuh", "kmc_tpdr.cuh"):
         with open(os.path.join(ROOT, "paper_1403_4674_gb300", "csrc", name)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -420,10 +425,11 @@ def variant_batched(args, peaks, flush, stream):
            "groups": [{"replicas": len(ch.replicas), "L_d": ch.L_d, "k": ch.k, "plan": list(ch.plan),
                        "tuned_events_per_s": ch.events_per_s} for ch in choices],
            "tune_s": tune_s, "events_per_step": ev, "polls_per_launch": polls,
-           "roofline": roofline(by, dev_s / args.steps, peaks, launch_traffic("batched") if one_thread_group else None),
+           "roofline": roofline(by, dev_s / args.steps, peaks,
+                                launch_traffic("batched", "tpd_kernel") if one_thread_group else None),
            "cpu_baseline": cpu}
     out["roofline"]["note"] = "step-level: the groups' run kernels overlap on concurrent streams"
-    iss = issue_roofline("batched", ev * args.steps / dev_s, float(peaks.get("sm_max_mhz", 2070.0))) \
+    iss = issue_roofline("batched", "tpd_kernel", ev * args.steps / dev_s, float(peaks.get("sm_max_mhz", 2070.0))) \
         if one_thread_group else None
     if iss is not None:
         iss["note"] = "counts of the single-context configuration of the same batch; steps/s of the whole step"
@@ -478,8 +484,9 @@ def variant_grad(args, peaks, flush, stream):
            "plan": list(plan), "launch": list(lat.launch()),
            "lr_grad_e_beta_h": [float(ge[0]), float(ge[1])], "lr_grad_m_beta_h": [float(gm[0]), float(gm[1])],
            "events_per_step": ev, "cpu_baseline": cpu, "polls_per_launch": polls / max(run_n, 1),
-           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks, launch_traffic("grad"))}
-    iss = issue_roofline("grad", ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0,
+           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks,
+                                launch_traffic("grad", run_kernel_name(lat)))}
+    iss = issue_roofline("grad", run_kernel_name(lat), ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0,
                          float(peaks.get("sm_max_mhz", 2070.0)), polls / max(ev * max(run_n, 1), 1))
     if iss is not None:
         out["roofline"]["issue"] = iss
@@ -526,9 +533,11 @@ def variant_lattice8192(args, peaks, flush, stream):
                        "schedules" % n,
            "plan": list(plan), "launch": list(lat.launch()), "events_per_step": ev, "cpu_baseline": cpu,
            "polls_per_launch": polls / max(run_n, 1),
-           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks, launch_traffic("lattice8192"))}
-    iss = issue_roofline("lattice8192", ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0,
-                         float(peaks.get("sm_max_mhz", 2070.0)), polls / max(ev * max(run_n, 1), 1))
+           "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks,
+                                launch_traffic("lattice8192", run_kernel_name(lat)))}
+    rate = ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0
+    iss = issue_roofline("lattice8192", run_kernel_name(lat), rate, float(peaks.get("sm_max_mhz", 2070.0)),
+                         polls / max(ev * max(run_n, 1), 1))
     if iss is not None:
         out["roofline"]["issue"] = iss
     lat.close()
@@ -679,9 +688,22 @@ def variant_pollcost(args, peaks, flush, stream):
     lat.sync()
     out = {"workload": desc, "plan": list(plan), "launch": list(lat.launch()), "limit_ns": limit_ns,
            "status_after_timeout": status, "polls": polls}
-    lat.close()
     if status != -5:
         raise RuntimeError("expected KMC_ETIMEOUT from the waits that run out, got %d" % status)
+    # the same workload on the shared-memory thread-per-domain kernel (its
+    # count is per warp poll round)
+    lat.set_launch(3, 0, 1)
+    kmc.kmc_debug_barrier(lat.ctx, 1, limit_ns)
+    lat.profile_polls()
+    lat.run(1)
+    try:
+        lat.sync()
+        status = 0
+    except kmc.KmcError as e:
+        status = e.status
+    out["thread_rows"] = {"launch": list(lat.launch()), "status_after_timeout": status, "polls": lat.profile_polls()}
+    kmc.kmc_debug_barrier(lat.ctx, 0, 0)
+    lat.close()
     # the same for the thread-per-domain kernel (its count is per thread): the
     # batched workload's 512 replicas at L_d = 8, k = 16 on the library's plan
     from paper_1403_4674_gb300 import workloads as wl
@@ -860,16 +882,17 @@ def main():
                 ((host_obs[..., 3] - do[..., 3]).abs() / do[..., 3].abs().clamp_min(1e-300)).max().item())
 
     full = args.schedules == 0
-    traffic = launch_traffic(args.workload) if full else None
+    kern = run_kernel_name(lat)
+    traffic = launch_traffic(args.workload, kern) if full else None
     avg_run_s = (run_ms / 1000.0) / max(run_n, 1)
     roof = roofline(bytes_step, avg_run_s, peaks, traffic)
-    roof.update({"kernel": "kmcdev::run_kernel", "run_kernel_ms_avg": 1000 * avg_run_s,
+    roof.update({"kernel": "kmcdev::" + kern, "run_kernel_ms_avg": 1000 * avg_run_s,
                  "run_kernel_launches": run_n, "algorithmic_bytes_per_launch": bytes_step,
                  "step_level_achieved": bytes_step * args.steps / dev_s / 1e9,
                  "polls_per_launch": polls / max(run_n, 1)})
     # the bound this kernel actually meets: instruction issue
     if full and clk.get("sm_mhz") and avg_run_s > 0:
-        iss = issue_roofline(args.workload, events_step / avg_run_s, clk["sm_mhz"],
+        iss = issue_roofline(args.workload, kern, events_step / avg_run_s, clk["sm_mhz"],
                              polls / max(events_step * max(run_n, 1), 1))
         if iss is not None:
             roof["issue"] = iss
@@ -894,8 +917,10 @@ def main():
                            "parallelism": ("replicas only, %d ranks" % world if world > 1 else "1 GPU") +
                                           ", one run-kernel launch per step",
                            "plan": list(plan), "launch": list(lat.launch()), "tune_s": tune_s,
-                           "threads_per_domain": "one warp per 32x32 domain (not a tuner knob; 8x8 domains of "
-                                                 "other workloads run one thread per domain)",
+                           "threads_per_domain": (("one thread per domain, 32 domains per warp, state in shared "
+                                                   "memory" if kern == "tpdr_kernel" else "one thread per domain")
+                                                  if kern != "run_kernel" else "one warp per domain") +
+                                                 " (the tuner's choice between thread and warp plans)",
                            "wall_s": wall},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "bit_exact": bit_exact,
                 "clocks": clk, "variants": variants}

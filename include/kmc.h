@@ -329,11 +329,14 @@ kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, ui
 kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
 
 /* Launch plan of the persistent run kernel.
- *   KMC_LAUNCH_AUTO: the library's choice: CLUSTER when every replica fits
- *     one cluster of at most 16 CTAs at one visit per warp and phase, else a
- *     cooperative GRID (the shape with the most resident warps per SM that
- *     fits: three CTAs of 8 warps, two of 12 or 10, one of 16, ...), else
- *     16-CTA clusters with several visits per warp; size and warps ignored.
+ *   KMC_LAUNCH_AUTO: the library's choice: KMC_LAUNCH_THREADS while scores
+ *     are off and L_d is 8, 16 or 32 (for 16 and 32 when the domains' state
+ *     fits the GPU's shared memory); otherwise CLUSTER when every replica
+ *     fits one cluster of at most 16 CTAs at one visit per warp and phase,
+ *     else a cooperative GRID (the shape with the most resident warps per SM
+ *     that fits: three CTAs of 8 warps, two of 12 or 10, one of 16, ...),
+ *     else 16-CTA clusters with several visits per warp; size and warps
+ *     ignored.
  *   KMC_LAUNCH_CLUSTER: every replica resident in one thread-block cluster of
  *     `size` CTAs (1, 2, 4, 8 or 16); halos and visit counters read through
  *     distributed shared memory; no device-wide synchronisation.
@@ -342,19 +345,27 @@ kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
  *     neighbour domain is in the same CTA.  The run kernels hold 80 to 128
  *     registers per thread (by domain side and scores), so two or three CTAs
  *     of 8-12 warps can share an SM.
- *   KMC_LAUNCH_THREADS (L_d = 8 only): one thread per domain visit; a
- *     cooperative grid of `size` CTAs (0: as many as spread each colour's
- *     domains evenly over at most three 4-warp CTAs per SM) of warps_per_cta
- *     (1..4) warps, thread t
- *     visiting the t-th, (t+T)-th, ... domain of each colour's list (T the
- *     grid's threads).  An 8x8 domain is one 64-bit word, so a thread runs a
- *     whole domain process in registers and a warp 32 of them at once, with
- *     state, edge words and counters in global memory (L2).  It covers the
- *     palindromic and fixed schedules with the exponential or expected
- *     clock and no scores; a run that needs scores, fixed-time visits or
- *     random colour orders first replaces the plan by the library's choice
- *     among the others (KMC_EINVAL while the stream is capturing).  This is
- *     the library's choice for L_d = 8 while scores are off.
+ *   KMC_LAUNCH_THREADS (L_d = 8, 16 or 32): one thread runs a whole domain
+ *     process and a warp 32 of them at once, with no warp collective on the
+ *     step path; warps_per_cta 1..4.
+ *     L_d = 8: a cooperative grid of `size` CTAs (0: as many as spread each
+ *     colour's domains evenly over at most three 4-warp CTAs per SM), thread
+ *     t visiting the t-th, (t+T)-th, ... domain of each colour's list (T the
+ *     grid's threads); an 8x8 domain is one 64-bit word, so the domain
+ *     process runs in registers, with state, edge words and counters in
+ *     global memory (L2).
+ *     L_d = 16, 32: one domain per thread for the whole launch, a warp
+ *     holding 32 domains of one colour; the domain's rows, the class counts
+ *     of every row, of every block of 8 rows and of the domain, and its
+ *     counters stay in the CTA's shared memory (about 1.5 KB per 32x32
+ *     domain, 1.2 KB per 16x16 one); `size` is ignored (the grid follows
+ *     from the domain count) and KMC_EINVAL is returned when the domains do
+ *     not fit the GPU at once.
+ *     Both cover the palindromic and fixed schedules with the exponential or
+ *     expected clock and no scores; a run that needs scores, fixed-time
+ *     visits or random colour orders first replaces the plan by the
+ *     library's choice among the others (KMC_EINVAL while the stream is
+ *     capturing).
  * In all plans a visit starts as soon as its four neighbours have finished
  * their visits of earlier colour phases (per-domain dataflow instead of a
  * barrier per phase; Sec. 2.2 lets non-interacting domains run at once); observation records are built from per-visit changes,
@@ -395,7 +406,8 @@ kmc_status kmc_profile_read(kmc_ctx *ctx, double *run_kernel_ms, int64_t *run_ke
  * warps of the times a warp re-read a neighbour's edge word because the
  * neighbour had not finished its earlier visit yet (the first read of a halo
  * is not counted; a warp polling several neighbours at once counts its
- * slowest lane; under KMC_LAUNCH_THREADS the sum over threads).  With instructions per poll iteration this separates
+ * slowest lane; under KMC_LAUNCH_THREADS at L_d = 8 the sum over threads,
+ * at 16 and 32 the sum over warps of their poll rounds).  With instructions per poll iteration this separates
  * busy-waiting from the visits' own instructions.  *polls is a host int64;
  * reading synchronises the context's stream and clears the count.  0 when
  * profiling was never enabled.  KMC_EINVAL for null arguments.  No

@@ -54,8 +54,11 @@ def plan_candidates(sm_count: int) -> List[Plan]:
             (KMC_LAUNCH_GRID, 2 * sm_count, 10), (KMC_LAUNCH_GRID, 2 * sm_count, 12),
             (KMC_LAUNCH_GRID, 3 * sm_count, 8), (KMC_LAUNCH_GRID, 4 * sm_count, 5),
             (KMC_LAUNCH_GRID, 5 * sm_count, 4), (KMC_LAUNCH_GRID, 6 * sm_count, 4)]
-    # one thread per domain (8x8 domains only; the library refuses it otherwise)
-    out += [(KMC_LAUNCH_THREADS, 0, 4)]  # the library's balanced thread grid
+    # one thread per domain (L_d = 8, 16, 32; the library refuses it
+    # otherwise): the library's balanced grid, and for 8x8 domains grids of
+    # fixed size (16x16 and 32x32 ones take one domain per thread whatever
+    # the size, so those entries repeat the first at other CTA widths)
+    out += [(KMC_LAUNCH_THREADS, 0, 4), (KMC_LAUNCH_THREADS, 0, 1)]
     out += [(KMC_LAUNCH_THREADS, m * sm_count, w) for m, w in ((3, 4), (2, 4), (4, 4), (6, 2))]
     return out
 

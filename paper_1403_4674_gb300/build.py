@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkmc_gb300.so")
 SOURCES = [os.path.join(CSRC, "kmc_api.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "kmc_kernels.cuh"), os.path.join(CSRC, "kmc_ring.cuh"),
-        os.path.join(CSRC, "kmc_part.cuh"), os.path.join(CSRC, "kmc_tpd.cuh"),
+        os.path.join(CSRC, "kmc_part.cuh"), os.path.join(CSRC, "kmc_tpd.cuh"), os.path.join(CSRC, "kmc_tpdr.cuh"),
         os.path.join(ROOT, "include", "kmc.h")]
 
 

@@ -10,6 +10,7 @@
 #include "kmc_ring.cuh"
 #include "kmc_part.cuh"
 #include "kmc_tpd.cuh"
+#include "kmc_tpdr.cuh"
 
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
@@ -555,7 +556,45 @@ kmc_status plan_threads(kmc_ctx *c, int n_cta, int wpb, Plan &pl)
 }
 
 using TpdKernel = void (*)(const RunParams);
-TpdKernel tpd_kernel_for(bool expo) { return expo ? tpd_kernel<true> : tpd_kernel<false>; }
+// the thread-per-domain kernel of the context's domain side
+TpdKernel tpd_kernel_for(int LD, bool expo)
+{
+    if (LD == 16) return expo ? tpdr_kernel<16, true> : tpdr_kernel<16, false>;
+    if (LD == 32) return expo ? tpdr_kernel<32, true> : tpdr_kernel<32, false>;
+    return expo ? tpd_kernel<true> : tpd_kernel<false>;
+}
+size_t tpdr_warp_bytes_for(int LD) { return LD == 16 ? tpdr_warp_bytes<16>() : tpdr_warp_bytes<32>(); }
+
+// THREADS plan for L_d = 16, 32: warps of 32 domains of one colour, one per
+// thread and consecutive in the colour list (a colour's last warp may be
+// partly empty), the colours' warps interleaved so that a CTA holds
+// neighbouring groups of every colour; slot_g holds 32 entries per warp of
+// the grid, 0xFFFFFFFF for an empty lane or warp.  The domains stay in the
+// CTA's shared memory for the whole launch.
+kmc_status plan_thread_rows(kmc_ctx *c, int wpb, Plan &pl)
+{
+    if (c->LD != 16 && c->LD != 32) return fail(c, KMC_EINVAL, "no thread-row kernel for L_d = %d", c->LD);
+    if (wpb < 1 || wpb > 4) return fail(c, KMC_EINVAL, "thread plans take 1..4 warps per CTA");
+    pl = Plan();
+    pl.mode = KMC_LAUNCH_THREADS;
+    pl.wpb = wpb;
+    std::vector<std::vector<uint32_t>> lists(4);
+    for (uint32_t g = 0; g < (uint32_t)c->n_dom; ++g) lists[domain_colour(c, g)].push_back(g);
+    size_t most = 0;
+    for (const auto &lq : lists) most = std::max(most, (lq.size() + 31) / 32);
+    for (size_t i = 0; i < most; ++i) {
+        for (int q = 0; q < 4; ++q) {
+            const std::vector<uint32_t> &lq = lists[q];
+            if (i * 32 >= lq.size()) continue;
+            for (size_t l = 0; l < 32; ++l) pl.slot_g.push_back(i * 32 + l < lq.size() ? lq[i * 32 + l] : 0xFFFFFFFFu);
+        }
+    }
+    const int n_warps = (int)(pl.slot_g.size() / 32);
+    pl.n_cta = (n_warps + wpb - 1) / wpb;
+    pl.slot_g.resize((size_t)pl.n_cta * wpb * 32, 0xFFFFFFFFu);
+    pl.smem = (size_t)wpb * tpdr_warp_bytes_for(c->LD);
+    return KMC_OK;
+}
 
 // CTAs of `wpb` warps for a thread plan: a phase takes as many rounds as its
 // busiest thread has domains, so the threads are the domains of a colour
@@ -581,12 +620,22 @@ kmc_status check_plan(kmc_ctx *c, const Plan &pl)
     if (pl.mode == KMC_LAUNCH_THREADS) {
         if (c->grad) return fail(c, KMC_EINVAL, "the thread-per-domain plan has no score kernel");
         for (int e = 0; e < 2; ++e) {
+            const void *kern = (const void *)tpd_kernel_for(c->LD, e == 0);
+            if (pl.smem > 0) {
+                if (pl.smem > (size_t)c->smem_optin)
+                    return fail(c, KMC_EINVAL, "thread plan needs %zu bytes of shared memory per CTA (%d available)",
+                                pl.smem, c->smem_optin);
+                cudaFuncAttributes fa;
+                CUDA_TRY(c, cudaFuncGetAttributes(&fa, kern));
+                if ((size_t)fa.maxDynamicSharedSizeBytes < pl.smem)
+                    CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+            }
             int nb = 0;
-            CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)tpd_kernel_for(e == 0),
-                                                                      pl.wpb * 32, 0));
+            CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, pl.wpb * 32, pl.smem));
             if ((int64_t)nb * c->sm_count < pl.n_cta)
                 return fail(c, KMC_EINVAL, "%d CTAs of %d warps cannot be co-resident (%d per SM)", pl.n_cta, pl.wpb, nb);
         }
+        if (c->LD != 8) return KMC_OK;
         if (!c->d_obs_dom) {
             kmc_status st = dev_alloc(c, &c->d_obs_dom, (size_t)c->n_dom * TPD_OBS_WORDS);
             if (st != KMC_OK) return st;
@@ -656,14 +705,17 @@ kmc_status install_plan(kmc_ctx *c, Plan &pl)
 
 kmc_status default_warp_plan(kmc_ctx *c);
 
-// The library's plan: one thread per domain visit for 8x8 domains while
-// scores are off (a warp then runs 32 domain processes), else the warp
-// plans below.
+// The library's plan: one thread per domain while scores are off (a warp
+// then runs 32 domain processes): for 8x8 domains with state in L2, for
+// 16x16 and 32x32 domains with state in shared memory when it fits the
+// GPU; else the warp plans below.
 kmc_status default_plan(kmc_ctx *c)
 {
-    if (c->LD == 8 && !c->grad) {
+    if (!c->grad && (c->LD == 8 || c->LD == 16 || c->LD == 32)) {
         Plan pl;
-        if (plan_threads(c, balanced_thread_ctas(c, 4), 4, pl) == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
+        const kmc_status st = (c->LD == 8) ? plan_threads(c, balanced_thread_ctas(c, 4), 4, pl)
+                                           : plan_thread_rows(c, 1, pl);
+        if (st == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
         cudaGetLastError();
     }
     return default_warp_plan(c);
@@ -1295,9 +1347,14 @@ kmc_status kmc_set_launch(kmc_ctx *c, int32_t mode, int32_t size, int32_t warps_
         if ((s = plan_grid(c, size, warps_per_cta, pl)) != KMC_OK) return s;
     } else if (mode == KMC_LAUNCH_THREADS) {
         if (warps_per_cta > 4) return fail(c, KMC_EINVAL, "thread plans take 1..4 warps per CTA");
-        // size 0: the balanced grid of the library's choice
-        if ((s = plan_threads(c, size > 0 ? size : balanced_thread_ctas(c, warps_per_cta), warps_per_cta, pl)) != KMC_OK)
+        if (c->LD == 16 || c->LD == 32) {
+            // one domain per thread: the grid follows from the domains
+            if ((s = plan_thread_rows(c, warps_per_cta, pl)) != KMC_OK) return s;
+        } else if ((s = plan_threads(c, size > 0 ? size : balanced_thread_ctas(c, warps_per_cta), warps_per_cta, pl)) !=
+                   KMC_OK) {
+            // size 0: the balanced grid of the library's choice
             return s;
+        }
     } else {
         return fail(c, KMC_EINVAL, "bad launch mode %d", mode);
     }
@@ -1472,7 +1529,7 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     const Plan &pl = c->plan;
     const bool cluster = pl.mode == KMC_LAUNCH_CLUSTER;
     const bool threads = pl.mode == KMC_LAUNCH_THREADS;
-    RunKernel kern = threads ? tpd_kernel_for(time_mode == KMC_TIME_EXPONENTIAL)
+    RunKernel kern = threads ? tpd_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL)
                              : run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad, cluster);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool prof = c->prof && !cap;

@@ -26,15 +26,21 @@ def _sm():
     return torch.cuda.get_device_properties(0).multi_processor_count
 
 
-def test_default_plan_for_8x8_domains():
+def test_default_plans():
+    """One thread per domain for 8x8, 16x16 and 32x32 domains while scores
+    are off; 64x64 domains and runs with scores take a warp plan."""
     import paper_1403_4674_gb300 as kmc
-    lat = kmc.Lattice([64, 32], 8, 4, [1, 2])
-    assert lat.launch()[0] == THREADS
-    lat.close()
-    lat = kmc.Lattice([64], 16, 4, [1])
+    for Ld in (8, 16, 32):
+        lat = kmc.Lattice([4 * Ld, 2 * Ld], Ld, 4, [1, 2])
+        assert lat.launch()[0] == THREADS
+        lat.enable_grad(True)
+        assert lat.launch()[0] != THREADS
+        lat.close()
+    lat = kmc.Lattice([128], 64, 4, [1])
     assert lat.launch()[0] != THREADS
     with pytest.raises(kmc.KmcError):
-        lat.set_launch(THREADS, _sm(), 4)  # 16x16 domains: refused, previous plan kept
+        lat.set_launch(THREADS, _sm(), 4)  # 64x64 domains: refused, previous plan kept
+    assert lat.launch()[0] != THREADS
     lat.close()
 
 
