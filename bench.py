@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the batched and gradient variants")
     ap.add_argument("--plan", default="", help="launch plan mode,size,warps (skips the plan tuning)")
     ap.add_argument("--only", default="", choices=["", "batched", "grad", "lattice8192", "ring8", "partitions2d",
-                                                    "pollcost"],
+                                                    "pollcost", "chain"],
                     help="time one variant alone and print its JSON object (profiling runs; not the contract line)")
     return ap.parse_args()
 
@@ -267,12 +267,17 @@ def reference_arm(args):
 # thread iteration for the thread-per-domain kernel).  They hold for the
 # kernel sources with this SHA-256 and are left out of the line once the
 # sources change.
-NCU_KERNEL_SHA256 = None
+NCU_KERNEL_SHA256 = "9fd4c6568cbc78efb87e729f7a13e8c87fa5431690938c3388a0a7c4869e730e"
 # instructions of one poll iteration: per warp iteration for the warp kernels
 # and the shared-memory thread kernel, per thread re-read for the 8x8 one
-INST_PER_POLL = {"run_kernel": 22.24, "tpd_kernel": 0.85, "tpdr_kernel": None}
+INST_PER_POLL = {"run_kernel": 22.24, "tpd_kernel": 0.85, "tpdr_kernel": 27.28}
 NCU_COUNTS = {
     # (workload, kernel): (warp instructions, steps, poll iterations or None, DRAM bytes) of one launch
+    ("ising1024", "run_kernel"): (424601387407, 2580480000, 1572303118, 6401280),
+    ("ising1024", "tpdr_kernel"): (51462792856, 2580480000, 226211721, 7025152),
+    ("grad", "run_kernel"): (281949602755, 1310720000, 1232445050, 4996352),
+    ("lattice8192", "run_kernel"): (144446437556, 524288000, 435496368, 10969600),
+    ("batched", "tpd_kernel"): (38908958794, 2636876800, 168298809, 7615934464),
 }
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 
@@ -651,6 +656,41 @@ def variant_part(args, peaks, flush, stream):
     return out
 
 
+def variant_chain(args, peaks, flush, stream):
+    """Latency of one domain's chain: a 64^2 lattice at L_d = 32 (four
+    domains, one per colour) at beta = 0, where every uniformised step is a
+    real event (Metropolis), so that one palindromic schedule is a chain of
+    6k events and four colour hand-offs (colours 1 and 2 run side by side).
+    Launch times at k = 4 and k = 16 give the time per event (their
+    difference over 72 events) and per hand-off, for the thread plan and a
+    warp plan.  This is the floor under the 1024^2 workload's launch time:
+    its k = 16, T = 3 replicas run about 70 real events per schedule on
+    their critical path."""
+    import paper_1403_4674_gb300 as kmc
+    n = 2000
+    out = {"workload": "64x64, L_d = 32, beta = 0, k in {4, 16}, %d palindromic schedules per launch" % n}
+    for name, plan in (("thread", (3, 0, 1)), ("warp", (2, 4, 4))):
+        per = {}
+        for k in (4, 16):
+            lat = kmc.Lattice([64], 32, k, [7])
+            lat.set_launch(*plan)
+            lat.set_rates([0.0], [0.0])
+            lat.run(2)
+            lat.sync()
+            lat.profile(True)
+            lat.profile_read()
+            lat.run(n)
+            lat.sync()
+            ms, runs = lat.profile_read()
+            per[k] = ms * 1e6 / max(runs, 1) / n  # ns per schedule
+            lat.close()
+        ev = (per[16] - per[4]) / (6 * 12)
+        hop = (per[4] - 6 * 4 * ev) / 4
+        out[name] = {"plan": list(plan), "ns_per_schedule": {str(k): v for k, v in per.items()},
+                     "ns_per_event": ev, "ns_per_handoff": hop}
+    return out
+
+
 def variant_pollcost(args, peaks, flush, stream):
     """Instructions of one halo-poll iteration, for the net issue rate: one
     launch of the default workload's context and plan in which every visit
@@ -728,7 +768,8 @@ def variant_pollcost(args, peaks, flush, stream):
 
 
 VARIANTS = {"batched": "variant_batched", "grad": "variant_grad", "lattice8192": "variant_lattice8192",
-            "ring8": "variant_ring", "partitions2d": "variant_part", "pollcost": "variant_pollcost"}
+            "ring8": "variant_ring", "partitions2d": "variant_part", "pollcost": "variant_pollcost",
+            "chain": "variant_chain"}
 
 
 def only_variant(args):
