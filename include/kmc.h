@@ -329,9 +329,9 @@ kmc_status kmc_get_rate_table(const kmc_ctx *ctx, int32_t replica, double *a, ui
 kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
 
 /* Launch plan of the persistent run kernel.
- *   KMC_LAUNCH_AUTO: the library's choice: KMC_LAUNCH_THREADS while scores
- *     are off and L_d is 8, 16 or 32 (for 16 and 32 when the domains' state
- *     fits the GPU's shared memory); otherwise CLUSTER when every replica
+ *   KMC_LAUNCH_AUTO: the library's choice: KMC_LAUNCH_THREADS for L_d = 16
+ *     and 32 when the domains' state fits the GPU's shared memory, and for
+ *     L_d = 8 while scores are off; otherwise CLUSTER when every replica
  *     fits one cluster of at most 16 CTAs at one visit per warp and phase,
  *     else a cooperative GRID (the shape with the most resident warps per SM
  *     that fits: three CTAs of 8 warps, two of 12 or 10, one of 16, ...),
@@ -362,10 +362,11 @@ kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
  *     from the domain count) and KMC_EINVAL is returned when the domains do
  *     not fit the GPU at once.
  *     Both cover the palindromic and fixed schedules with the exponential or
- *     expected clock and no scores; a run that needs scores, fixed-time
- *     visits or random colour orders first replaces the plan by the
- *     library's choice among the others (KMC_EINVAL while the stream is
- *     capturing).
+ *     expected clock, and the L_d = 16, 32 kernel also path scores
+ *     (kmc_enable_grad; each thread forms its own domain's FP64 score
+ *     terms); a run that needs fixed-time visits, random colour orders or,
+ *     at L_d = 8, scores first replaces the plan by the library's choice
+ *     among the others (KMC_EINVAL while the stream is capturing).
  * In all plans a visit starts as soon as its four neighbours have finished
  * their visits of earlier colour phases (per-domain dataflow instead of a
  * barrier per phase; Sec. 2.2 lets non-interacting domains run at once); observation records are built from per-visit changes,
@@ -374,7 +375,8 @@ kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
  * or the state does not fit in shared memory; the previous plan then stays.
  * Results do not depend on the plan, except the last bits of the FP64 domain
  * clocks: the thread plan multiplies a visit's clock variates in step order,
- * the others in pairs (both within 1e-12 of the oracle). */
+ * the others in pairs (both within 1e-12 of the oracle).  Path scores are
+ * the same on every plan (the same terms in the same order per domain). */
 enum { KMC_LAUNCH_AUTO = 0, KMC_LAUNCH_CLUSTER = 1, KMC_LAUNCH_GRID = 2, KMC_LAUNCH_THREADS = 3 };
 kmc_status kmc_set_launch(kmc_ctx *ctx, int32_t mode, int32_t size, int32_t warps_per_cta);
 /* Current plan: mode, size (cluster size or CTA count), CTAs, warps per CTA,

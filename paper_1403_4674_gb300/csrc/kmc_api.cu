@@ -556,11 +556,16 @@ kmc_status plan_threads(kmc_ctx *c, int n_cta, int wpb, Plan &pl)
 }
 
 using TpdKernel = void (*)(const RunParams);
-// the thread-per-domain kernel of the context's domain side
-TpdKernel tpd_kernel_for(int LD, bool expo)
+// the thread-per-domain kernel of the context's domain side (scores: the
+// shared-memory kernel of 16x16 and 32x32 domains only)
+TpdKernel tpd_kernel_for(int LD, bool expo, bool grad)
 {
-    if (LD == 16) return expo ? tpdr_kernel<16, true> : tpdr_kernel<16, false>;
-    if (LD == 32) return expo ? tpdr_kernel<32, true> : tpdr_kernel<32, false>;
+    if (LD == 16)
+        return grad ? (expo ? tpdr_kernel<16, true, true> : tpdr_kernel<16, false, true>)
+                    : (expo ? tpdr_kernel<16, true, false> : tpdr_kernel<16, false, false>);
+    if (LD == 32)
+        return grad ? (expo ? tpdr_kernel<32, true, true> : tpdr_kernel<32, false, true>)
+                    : (expo ? tpdr_kernel<32, true, false> : tpdr_kernel<32, false, false>);
     return expo ? tpd_kernel<true> : tpd_kernel<false>;
 }
 size_t tpdr_warp_bytes_for(int LD) { return LD == 16 ? tpdr_warp_bytes<16>() : tpdr_warp_bytes<32>(); }
@@ -618,9 +623,9 @@ int balanced_thread_ctas(const kmc_ctx *c, int wpb)
 kmc_status check_plan(kmc_ctx *c, const Plan &pl)
 {
     if (pl.mode == KMC_LAUNCH_THREADS) {
-        if (c->grad) return fail(c, KMC_EINVAL, "the thread-per-domain plan has no score kernel");
+        if (c->grad && c->LD == 8) return fail(c, KMC_EINVAL, "the thread-per-domain plan of L_d = 8 has no score kernel");
         for (int e = 0; e < 2; ++e) {
-            const void *kern = (const void *)tpd_kernel_for(c->LD, e == 0);
+            const void *kern = (const void *)tpd_kernel_for(c->LD, e == 0, c->grad);
             if (pl.smem > 0) {
                 if (pl.smem > (size_t)c->smem_optin)
                     return fail(c, KMC_EINVAL, "thread plan needs %zu bytes of shared memory per CTA (%d available)",
@@ -705,13 +710,13 @@ kmc_status install_plan(kmc_ctx *c, Plan &pl)
 
 kmc_status default_warp_plan(kmc_ctx *c);
 
-// The library's plan: one thread per domain while scores are off (a warp
-// then runs 32 domain processes): for 8x8 domains with state in L2, for
+// The library's plan: one thread per domain (a warp then runs 32 domain
+// processes): for 8x8 domains with state in L2 while scores are off, for
 // 16x16 and 32x32 domains with state in shared memory when it fits the
 // GPU; else the warp plans below.
 kmc_status default_plan(kmc_ctx *c)
 {
-    if (!c->grad && (c->LD == 8 || c->LD == 16 || c->LD == 32)) {
+    if ((!c->grad && c->LD == 8) || c->LD == 16 || c->LD == 32) {
         Plan pl;
         const kmc_status st = (c->LD == 8) ? plan_threads(c, balanced_thread_ctas(c, 4), 4, pl)
                                            : plan_thread_rows(c, 1, pl);
@@ -1484,10 +1489,10 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     const int64_t units = pass_obs ? n_schedules * (schedule == KMC_SCHEDULE_PALINDROME ? 8 : 4) : n_schedules;
     const int64_t n_obs = want_obs ? units / obs_every : 0;
     const bool cap = capturing(c);
-    if (c->plan.mode == KMC_LAUNCH_THREADS &&
-        (c->grad || time_mode == KMC_TIME_HORIZON || schedule == KMC_SCHEDULE_RANDOM_PERM)) {
-        // the thread kernel covers fixed-length visits of the palindromic
-        // and fixed schedules without scores: this run takes a warp plan
+    if (c->plan.mode == KMC_LAUNCH_THREADS && ((c->grad && c->LD == 8) || time_mode == KMC_TIME_HORIZON ||
+                                               schedule == KMC_SCHEDULE_RANDOM_PERM)) {
+        // the thread kernels cover fixed-length visits of the palindromic
+        // and fixed schedules (with scores at L_d = 16, 32): this run takes a warp plan
         // (installed once the stream has drained: earlier launches read the
         // plan buffer)
         if (cap) return fail(c, KMC_EINVAL, "this run needs a warp launch plan; set one before capturing");
@@ -1529,7 +1534,7 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     const Plan &pl = c->plan;
     const bool cluster = pl.mode == KMC_LAUNCH_CLUSTER;
     const bool threads = pl.mode == KMC_LAUNCH_THREADS;
-    RunKernel kern = threads ? tpd_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL)
+    RunKernel kern = threads ? tpd_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad)
                              : run_kernel_for(c->LD, time_mode == KMC_TIME_EXPONENTIAL, c->grad, cluster);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool prof = c->prof && !cap;

@@ -29,8 +29,10 @@
 // as in the other plans.
 //
 // Scope: palindromic and fixed colour schedules, exponential and expected
-// clocks, per-replica k, records at schedule endpoints or every colour pass.
-// Scores, fixed-time visits and random colour orders use the warp kernel.
+// clocks, per-replica k, records at schedule endpoints or every colour pass,
+// path scores (GRAD: every lane forms its own domain's FP64 score terms, so
+// one FP64 instruction serves up to 32 domains).  Fixed-time visits and
+// random colour orders use the warp kernel.
 #pragma once
 
 #include "kmc_kernels.cuh"
@@ -46,13 +48,16 @@ template <int LD> struct TpdrLayout {
     // spare block each, the target of updates that have no second block),
     // domain counts lo / hi, event hash, real flips, steps, clock mantissa and
     // exponent, open record (record | steps << 32, bonds | mag << 32, clock
-    // product mantissa, exponent), 0 and the cumulative class rates C_c,
-    // acceptances A_c, their reciprocals floor((2^64 - 1) / A_c), the step targets of the current chunk (four spare words past its
-    // end hold ~0, a target no rate sum reaches)
+    // product mantissa, exponent), the domain's scores d/dbeta, d/dh and
+    // those of the open record (FP64 bits), 0 and the cumulative class rates
+    // C_c, acceptances A_c, their reciprocals floor((2^64 - 1) / A_c), the
+    // step targets of the current chunk (four spare words past its end hold
+    // ~0, a target no rate sum reaches)
     static constexpr int ROWLO = 0, ROWHI = LD, BLKLO = 2 * LD, BLKHI = BLKLO + NB + 1, TOTLO = BLKHI + NB + 1,
                          TOTHI = TOTLO + 1, CH = TOTLO + 2, CFL = CH + 1, CST = CH + 2, CCM = CH + 3, CCE = CH + 4,
-                         OB0 = CH + 5, OB1 = OB0 + 1, OBM = OB0 + 2, OBE = OB0 + 3, CC = OB0 + 4, AT = CC + 11,
-                         MR = AT + 10, TG = MR + 10, N64 = TG + CHUNK + 4;
+                         OB0 = CH + 5, OB1 = OB0 + 1, OBM = OB0 + 2, OBE = OB0 + 3, CSB = OB0 + 4, CSH = CSB + 1,
+                         OSB = CSB + 2, OSH = CSB + 3, CC = CSB + 4, AT = CC + 11, MR = AT + 10, TG = MR + 10,
+                         N64 = TG + CHUNK + 4;
     // 32-bit words per lane: spin rows, the halo the counts hold (N row, S
     // row, W column, E column), the domain's W and E columns, neighbour ids,
     // phase offset f << 16 | step j of each step of the chunk
@@ -132,7 +137,7 @@ __device__ __forceinline__ int tpdr_select(uint32_t w, uint32_t rr)
 // Persistent kernel.  P.slot_g holds 32 domain ids per warp of the grid (one
 // colour per warp, 0xFFFFFFFF for an empty lane); the dynamic shared memory
 // holds a TpdrLayout region per warp.
-template <int LD, bool EXPO>
+template <int LD, bool EXPO, bool GRAD>
 __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
 {
     using Lay = TpdrLayout<LD>;
@@ -179,6 +184,28 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
 #pragma unroll
     for (int i = CHUNK; i < CHUNK + 4; ++i) at(Lay::TG + i) = ~0ull;
     at(Lay::CC) = 0;
+    // Score constants of the lane's replica (scores only; registers): the
+    // two fixed-point words X_c (2^-Q) and Y_c (2^-(Q+18)) of a_c dlog a_c /
+    // d(beta, h), and 2^-(Q+4) 2^P, the scale of a state's rounded sum over
+    // 2^P (n_d - R).  The per-event terms dlog a_c are read where an event
+    // needs them.
+    constexpr int PBITS = 63 - 2 * (LD == 16 ? 4 : 5);
+    int64_t Xb[10], Xh[10];
+    int32_t Yb[10], Yh[10];
+    double scaleP = 0.0;
+    const double *gr = P.rep_grad + (size_t)r * 32;
+    if (GRAD) {
+        const int64_t *gf = P.rep_gfix + (size_t)r * GFIX_WORDS;
+        const int32_t *gl32 = reinterpret_cast<const int32_t *>(gf);
+#pragma unroll
+        for (int c = 0; c < 10; ++c) {
+            Xb[c] = __ldg(gf + c);
+            Xh[c] = __ldg(gf + 10 + c);
+            Yb[c] = __ldg(gl32 + 2 * GFIX_YB + c);
+            Yh[c] = __ldg(gl32 + 2 * GFIX_YH + c);
+        }
+        scaleP = __longlong_as_double(__ldg(gf + 20)) * (double)(1ull << PBITS);
+    }
 
     // ---- stage the domain: spins, row / block / domain counts with an all-down halo ----
     if (has) {
@@ -233,6 +260,10 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
         at(Lay::OB1) = 0;
         at(Lay::OBM) = 1ull << 63;
         at(Lay::OBE) = 0;
+        at(Lay::CSB) = ctr[DCTR_SB];
+        at(Lay::CSH) = ctr[DCTR_SH];
+        at(Lay::OSB) = 0; // +0.0
+        at(Lay::OSH) = 0;
     }
 
     // the open record of this lane's domain to its replica's record (records
@@ -249,6 +280,10 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
         const double dt = EXPO ? domain_time(true, at(Lay::OBM), (int64_t)at(Lay::OBE), 0, P.lambda)
                                : __ddiv_rn((double)steps, P.lambda);
         atomicAdd(reinterpret_cast<double *>(&acc[2]), dt);
+        if (GRAD) {
+            atomicAdd(reinterpret_cast<double *>(&acc[3]), __longlong_as_double((long long)at(Lay::OSB)));
+            atomicAdd(reinterpret_cast<double *>(&acc[4]), __longlong_as_double((long long)at(Lay::OSH)));
+        }
     };
 
     const int nph = (P.schedule == SCHED_PALINDROME) ? 8 : 4;
@@ -422,12 +457,50 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                 uint64_t flips = 0;
                 int dbonds = 0, dmag = 0;
 
+                // Path score of the visit (scores only): a real event of class c
+                // adds dlog a_c, a null step dlog(1 - R/n_d) = -sum_c n_c a_c
+                // dlog a_c / (n_d - R) (App. A, Eq. Glauber_TM), one value per
+                // state, formed only for states that have null steps.  The
+                // numerator is an exact integer sum of the two fixed-point words
+                // of every class, rounded once to 2^-(Q+4); n_d - R comes from
+                // the exact rate sum as (2^63 - R') 2^-P; its reciprocal from the
+                // FP32 one x0 = (1 - e)/g by x0 (1 + e + e^2) = (1 - e^3)/g
+                // (|e| < 2^-21: truncation 2^-63).  Terms are added in step
+                // order, a null run split at the 32-step chunk boundaries.
+                double sb = 0.0, sh = 0.0, nbo = 0.0, nho = 0.0;
+                bool scored = false;
+                auto grad_state = [&]() {
+                    int64_t xb = 0, xh = 0;
+                    int yb = 0, yh = 0;
+#pragma unroll
+                    for (int c = 0; c < 10; ++c) {
+                        const uint32_t n = tpdr_field(c < 5 ? tlo : thi, 12 * (c % 5));
+                        xb += (int64_t)n * Xb[c];
+                        xh += (int64_t)n * Xh[c];
+                        yb += (int)n * Yb[c];
+                        yh += (int)n * Yh[c];
+                    }
+                    constexpr int SH = GFIX_LO_BITS - GFIX_T_BITS;
+                    const int64_t tb = xb * (1ll << GFIX_T_BITS) + (int64_t)((yb + (1 << (SH - 1))) >> SH);
+                    const int64_t th = xh * (1ll << GFIX_T_BITS) + (int64_t)((yh + (1 << (SH - 1))) >> SH);
+                    const uint64_t gap = (1ull << 63) - C[9];
+                    const double gd = __ull2double_rn(gap);
+                    const double x0 = (double)__frcp_rn(u64_to_float_rz(gap));
+                    const double e = __fma_rn(-gd, x0, 1.0);
+                    const double inv = gap ? __fma_rn(x0, __fma_rn(e, e, e), x0) : 0.0;
+                    const double w = inv * scaleP;
+                    nbo = (double)tb * w;
+                    nho = (double)th * w;
+                    scored = true;
+                };
+
                 for (int base = 0; base < smax; base += CHUNK) {
                     if (base > 0) draw(base);
                     // Each lane jumps from real event to real event of its own
                     // domain (the steps between are null: App. A, the diagonal
                     // 1 - R/n_d); the warp runs as many rounds as its busiest lane.
-                    int i = 0; // this lane's next step, relative to the chunk
+                    int i = 0;   // this lane's next step, relative to the chunk
+                    int pos = 0; // first step of the current run of null steps (scores)
                     while (true) {
                         // the lane's next step with target < R' (targets past its
                         // last step are ~0), four at a time
@@ -442,6 +515,18 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                             i += 4;
                         }
                         const bool ev = i < CHUNK;
+                        if (GRAD) {
+                            // the null steps before this event, or up to the chunk's
+                            // (or the visit's) end, all in the current state
+                            const int end = ev ? i : min(CHUNK, total - base);
+                            if (end > pos) {
+                                if (!scored) grad_state();
+                                const double q = (double)(end - pos);
+                                sb -= q * nbo;
+                                sh -= q * nho;
+                            }
+                            pos = ev ? i + 1 : CHUNK;
+                        }
                         if (!__any_sync(FULL_WARP, ev)) break;
                         if (!ev) continue;
                         const uint64_t tgt = at(Lay::TG + i);
@@ -453,6 +538,11 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                         int c = 0;
 #pragma unroll
                         for (int cc = 0; cc < 9; ++cc) c += (tgt >= C[cc]) ? 1 : 0;
+                        if (GRAD) {
+                            // dlog a_c / d(beta, h) of the chosen class
+                            sb += __ldg(gr + 10 + c);
+                            sh += __ldg(gr + 20 + c);
+                        }
                         const uint64_t Cprev = at(Lay::CC + c); // C_{c-1}, 0 for c = 0
                         const uint64_t Ac = at(Lay::AT + c);
                         const uint64_t Mc = at(Lay::MR + c);
@@ -597,6 +687,7 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                         dbonds -= 2 * sgn * (2 * qc - 4);
                         dmag -= 2 * sgn;
                         rates();
+                        scored = false;
                         if (bad) {
                             atomicCAS(P.err, 0, ERR_INTERNAL);
                             i = CHUNK;
@@ -618,6 +709,10 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                     at(Lay::CH) = H;
                     at(Lay::CFL) += flips;
                     at(Lay::CST) += (uint64_t)total;
+                    if (GRAD) {
+                        at(Lay::CSB) = (uint64_t)__double_as_longlong(__longlong_as_double((long long)at(Lay::CSB)) + sb);
+                        at(Lay::CSH) = (uint64_t)__double_as_longlong(__longlong_as_double((long long)at(Lay::CSH)) + sh);
+                    }
                     if (EXPO) {
                         // the domain clock takes the visit's product
                         uint64_t m = at(Lay::CCM);
@@ -635,6 +730,8 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                             at(Lay::OB1) = 0;
                             at(Lay::OBM) = 1ull << 63;
                             at(Lay::OBE) = 0;
+                            at(Lay::OSB) = 0;
+                            at(Lay::OSH) = 0;
                         }
                         const uint64_t o0 = at(Lay::OB0), o1 = at(Lay::OB1);
                         const uint32_t steps = (uint32_t)(o0 >> 32) + (uint32_t)total;
@@ -647,6 +744,10 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                             mant_mul(m, e, vM, vE);
                             at(Lay::OBM) = m;
                             at(Lay::OBE) = (uint64_t)e;
+                        }
+                        if (GRAD) {
+                            at(Lay::OSB) = (uint64_t)__double_as_longlong(__longlong_as_double((long long)at(Lay::OSB)) + sb);
+                            at(Lay::OSH) = (uint64_t)__double_as_longlong(__longlong_as_double((long long)at(Lay::OSH)) + sh);
                         }
                     }
                 }
@@ -672,6 +773,10 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
         ctr[DCTR_STEPS] = at(Lay::CST);
         ctr[DCTR_CLKM] = at(Lay::CCM);
         ctr[DCTR_CLKE] = at(Lay::CCE);
+        if (GRAD) {
+            ctr[DCTR_SB] = at(Lay::CSB);
+            ctr[DCTR_SH] = at(Lay::CSH);
+        }
         if (P.n_obs > 0) flush();
     }
 }

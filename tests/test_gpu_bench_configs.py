@@ -161,10 +161,11 @@ def _oracle_grad_replica(args):
 
 def test_grad_full_timed_length_sampled_replicas():
     """The gradient benchmark's timed launch at its full length: 256 x 256^2
-    with scores on the 16-warp grid, 5000 schedules (5.1e6 steps per
-    replica), one record at the end; four replicas' spins, records and
-    scores checked against the oracle (run in parallel worker processes),
-    the scores to 1e-12 relative."""
+    with scores, 5000 schedules (5.1e6 steps per replica), one record at the
+    end, on both plans the tuner chooses between (the 16-warp grid of the
+    warp kernel and the thread kernel, one domain per lane); four replicas'
+    spins, records and scores checked against the oracle (run in parallel
+    worker processes), the scores to 1e-12 relative."""
     import multiprocessing as mp
     import paper_1403_4674_gb300 as kmc
     from paper_1403_4674_gb300 import workloads as wl
@@ -174,21 +175,25 @@ def test_grad_full_timed_length_sampled_replicas():
     # the oracle workers start before this test's first GPU call, by spawn
     with mp.get_context("spawn").Pool(len(jobs)) as pool:
         pending = pool.map_async(_oracle_grad_replica, jobs)
-        lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
-        lat.set_rates(w.beta, w.h)
-        lat.enable_grad(True)
-        lat.set_launch(2, _sm(), 16)
-        obs = lat.run(w.schedules, obs_every=w.schedules).cpu().numpy()
-        scores = lat.score().cpu().numpy()
-        spins = [lat.replica_spins(r).cpu().numpy() for r in idx]
-        lat.close()
+        runs = []
+        for plan in ((2, _sm(), 16), (3, 0, 1)):
+            lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
+            lat.set_rates(w.beta, w.h)
+            lat.enable_grad(True)
+            lat.set_launch(*plan)
+            obs = lat.run(w.schedules, obs_every=w.schedules).cpu().numpy()
+            assert lat.launch()[0] == plan[0]
+            runs.append((plan, obs, lat.score().cpu().numpy(), [lat.replica_spins(r).cpu().numpy() for r in idx]))
+            lat.close()
         results = pending.get()
-    for r, sp, (rspins, robs, rscore) in zip(idx, spins, results):
-        assert np.array_equal(sp, rspins), "replica %d: spins differ" % r
-        assert np.array_equal(obs[:, r, :3], robs[:, :3]), "replica %d: e, m, e*m differ" % r
-        np.testing.assert_allclose(obs[:, r, 3], robs[:, 3], rtol=1e-12, atol=0)
-        np.testing.assert_allclose(scores[r], rscore, rtol=1e-12, atol=1e-12, err_msg="replica %d" % r)
-        np.testing.assert_allclose(obs[:, r, 4:6], robs[:, 4:6], rtol=1e-12, atol=1e-12, err_msg="replica %d" % r)
+    for plan, obs, scores, spins in runs:
+        for r, sp, (rspins, robs, rscore) in zip(idx, spins, results):
+            msg = "plan %s replica %d" % (plan, r)
+            assert np.array_equal(sp, rspins), msg + ": spins differ"
+            assert np.array_equal(obs[:, r, :3], robs[:, :3]), msg + ": e, m, e*m differ"
+            np.testing.assert_allclose(obs[:, r, 3], robs[:, 3], rtol=1e-12, atol=0)
+            np.testing.assert_allclose(scores[r], rscore, rtol=1e-12, atol=1e-12, err_msg=msg)
+            np.testing.assert_allclose(obs[:, r, 4:6], robs[:, 4:6], rtol=1e-12, atol=1e-12, err_msg=msg)
 
 
 def test_batched_512_full_step_sample():
