@@ -358,9 +358,13 @@ kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
  *     holding 32 domains of one colour; the domain's rows, the class counts
  *     of every row, of every block of 8 rows and of the domain, and its
  *     counters stay in the CTA's shared memory (about 1.5 KB per 32x32
- *     domain, 1.2 KB per 16x16 one); `size` is ignored (the grid follows
- *     from the domain count) and KMC_EINVAL is returned when the domains do
- *     not fit the GPU at once.
+ *     domain, 1.2 KB per 16x16 one); the grid follows from the domain
+ *     count and KMC_EINVAL is returned when the domains do not fit the GPU
+ *     at once.  `size` orders each colour's domains over the warps: 0 or 1
+ *     replica after replica, 2 round-robin over the replicas (each warp then
+ *     holds domains of many replicas; faster when the replicas differ in
+ *     steps per visit or temperature, slower on a batch of alike replicas);
+ *     other values KMC_EINVAL.
  *     Both cover the palindromic and fixed schedules with the exponential or
  *     expected clock, and the L_d = 16, 32 kernel also path scores
  *     (kmc_enable_grad; each thread forms its own domain's FP64 score

@@ -40,13 +40,13 @@ def max_domain_side(L: int, candidates: Sequence[int] = DOMAIN_SIDES) -> int:
     return best
 
 
-def plan_candidates(sm_count: int) -> List[Plan]:
+def plan_candidates(sm_count: int, L_d: Optional[int] = None) -> List[Plan]:
     """Launch plans worth measuring: the library default, clusters of every
     size (the library packs as many replicas per cluster as fit), and
     cooperative grids of one to six CTAs per SM with 20-24 resident warps
     where the kernel's registers allow (small CTAs spread the cost-balanced
     colour chunks over more, shorter lists; the library rejects shapes that
-    do not fit)."""
+    do not fit), and the thread-per-domain plans of the domain side."""
     out: List[Plan] = [(KMC_LAUNCH_AUTO, 0, 16)]
     out += [(KMC_LAUNCH_CLUSTER, c, 16) for c in (1, 2, 4, 8, 16)]
     out += [(KMC_LAUNCH_CLUSTER, c, 8) for c in (4, 16)]
@@ -55,11 +55,15 @@ def plan_candidates(sm_count: int) -> List[Plan]:
             (KMC_LAUNCH_GRID, 3 * sm_count, 8), (KMC_LAUNCH_GRID, 4 * sm_count, 5),
             (KMC_LAUNCH_GRID, 5 * sm_count, 4), (KMC_LAUNCH_GRID, 6 * sm_count, 4)]
     # one thread per domain (L_d = 8, 16, 32; the library refuses it
-    # otherwise): the library's balanced grid, and for 8x8 domains grids of
-    # fixed size (16x16 and 32x32 ones take one domain per thread whatever
-    # the size, so those entries repeat the first at other CTA widths)
-    out += [(KMC_LAUNCH_THREADS, 0, 4), (KMC_LAUNCH_THREADS, 0, 1)]
-    out += [(KMC_LAUNCH_THREADS, m * sm_count, w) for m, w in ((3, 4), (2, 4), (4, 4), (6, 2))]
+    # otherwise): for 8x8 domains the library's balanced grid and grids of
+    # fixed size; 16x16 and 32x32 ones take one domain per thread, their size
+    # choosing the order of the domains over the warps (1: replica after
+    # replica, 2: round-robin over the replicas)
+    if L_d in (16, 32):
+        out += [(KMC_LAUNCH_THREADS, o, w) for o in (1, 2) for w in (4, 1)]
+    elif L_d in (None, 8):
+        out += [(KMC_LAUNCH_THREADS, 0, 4), (KMC_LAUNCH_THREADS, 0, 1)]
+        out += [(KMC_LAUNCH_THREADS, m * sm_count, w) for m, w in ((3, 4), (2, 4), (4, 4), (6, 2))]
     return out
 
 
@@ -126,7 +130,7 @@ def tune_plan(lat: Lattice, beta: Sequence[float], h: Sequence[float], plans: Op
     """Measure the plans on a scratch copy of `lat`'s geometry and install
     the fastest on `lat`."""
     if plans is None:
-        plans = plan_candidates(torch.cuda.get_device_properties(lat.spins.device).multi_processor_count)
+        plans = plan_candidates(torch.cuda.get_device_properties(lat.spins.device).multi_processor_count, lat.L_d)
     trials = measure(lat.L, lat.L_d, lat.ks, lat.seeds, beta, h, plans, trial_schedules, law,
                      grad=lat.grad_enabled)
     ok = [t for t in trials if t.error is None]
@@ -153,8 +157,10 @@ def tune_batch(L: Sequence[int], beta: Sequence[float], h: Sequence[float], seed
                law: int = 0) -> List[GroupChoice]:
     """Group replicas by their largest valid domain side, then pick (L_d, k,
     plan) per group by measured events/s."""
-    if plans is None:
-        plans = plan_candidates(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+    def plans_for(Ld: int) -> Sequence[Plan]:
+        return plans if plans is not None else plan_candidates(sm, Ld)
     groups: Dict[int, List[int]] = {}
     for i, x in enumerate(L):
         groups.setdefault(max_domain_side(x, Ld_candidates), []).append(i)
@@ -166,7 +172,7 @@ def tune_batch(L: Sequence[int], beta: Sequence[float], h: Sequence[float], seed
         for Ld in sides:
             for k in k_candidates:
                 trials += measure(Lg, Ld, [k] * len(idx), [seeds[i] for i in idx], [beta[i] for i in idx],
-                                  [h[i] for i in idx], plans, trial_schedules, law)
+                                  [h[i] for i in idx], plans_for(Ld), trial_schedules, law)
         ok = [t for t in trials if t.error is None]
         if not ok:
             errs = sorted({str(t.error) for t in trials})[:3]
@@ -188,7 +194,7 @@ def tune_batch(L: Sequence[int], beta: Sequence[float], h: Sequence[float], seed
                 continue
             idx = sorted(i for ch in chs for i in ch.replicas)
             trials = measure([L[i] for i in idx], Ld, [k] * len(idx), [seeds[i] for i in idx],
-                             [beta[i] for i in idx], [h[i] for i in idx], plans, trial_schedules, law)
+                             [beta[i] for i in idx], [h[i] for i in idx], plans_for(Ld), trial_schedules, law)
             okm = [t for t in trials if t.error is None]
             if not okm:
                 merged = []

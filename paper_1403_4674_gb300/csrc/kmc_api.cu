@@ -575,8 +575,16 @@ size_t tpdr_warp_bytes_for(int LD) { return LD == 16 ? tpdr_warp_bytes<16>() : t
 // partly empty), the colours' warps interleaved so that a CTA holds
 // neighbouring groups of every colour; slot_g holds 32 entries per warp of
 // the grid, 0xFFFFFFFF for an empty lane or warp.  The domains stay in the
-// CTA's shared memory for the whole launch.
-kmc_status plan_thread_rows(kmc_ctx *c, int wpb, Plan &pl)
+// CTA's shared memory for the whole launch.  The colour list holds the
+// replicas one after another, or with `interleave` their domains dealt
+// round-robin (the first of each replica, then the second, ...), so that a
+// warp's 32 domains come from many replicas: a warp's visit lasts as long as
+// its busiest lane, and a replica's chain of visits then waits on fewer of
+// its own busiest domains at a time.  That pays when the replicas differ in
+// cost (steps per visit, temperature): 1024^2 x 18 workload 661 -> 598 ms;
+// on a batch of alike replicas it couples the replicas' dataflow for
+// nothing (256 x 256^2 with scores: 278 -> 322 ms).
+kmc_status plan_thread_rows(kmc_ctx *c, int wpb, Plan &pl, bool interleave)
 {
     if (c->LD != 16 && c->LD != 32) return fail(c, KMC_EINVAL, "no thread-row kernel for L_d = %d", c->LD);
     if (wpb < 1 || wpb > 4) return fail(c, KMC_EINVAL, "thread plans take 1..4 warps per CTA");
@@ -584,7 +592,19 @@ kmc_status plan_thread_rows(kmc_ctx *c, int wpb, Plan &pl)
     pl.mode = KMC_LAUNCH_THREADS;
     pl.wpb = wpb;
     std::vector<std::vector<uint32_t>> lists(4);
-    for (uint32_t g = 0; g < (uint32_t)c->n_dom; ++g) lists[domain_colour(c, g)].push_back(g);
+    if (!interleave) {
+        for (uint32_t g = 0; g < (uint32_t)c->n_dom; ++g) lists[domain_colour(c, g)].push_back(g);
+    } else {
+        std::vector<std::vector<std::vector<uint32_t>>> per(4, std::vector<std::vector<uint32_t>>(c->n_rep));
+        for (uint32_t g = 0; g < (uint32_t)c->n_dom; ++g) per[domain_colour(c, g)][c->dom_rep[g]].push_back(g);
+        for (int q = 0; q < 4; ++q) {
+            size_t longest = 0;
+            for (const auto &v : per[q]) longest = std::max(longest, v.size());
+            for (size_t j = 0; j < longest; ++j)
+                for (const auto &v : per[q])
+                    if (j < v.size()) lists[q].push_back(v[j]);
+        }
+    }
     size_t most = 0;
     for (const auto &lq : lists) most = std::max(most, (lq.size() + 31) / 32);
     for (size_t i = 0; i < most; ++i) {
@@ -719,7 +739,7 @@ kmc_status default_plan(kmc_ctx *c)
     if ((!c->grad && c->LD == 8) || c->LD == 16 || c->LD == 32) {
         Plan pl;
         const kmc_status st = (c->LD == 8) ? plan_threads(c, balanced_thread_ctas(c, 4), 4, pl)
-                                           : plan_thread_rows(c, 1, pl);
+                                           : plan_thread_rows(c, 1, pl, false);
         if (st == KMC_OK && install_plan(c, pl) == KMC_OK) return KMC_OK;
         cudaGetLastError();
     }
@@ -1353,8 +1373,10 @@ kmc_status kmc_set_launch(kmc_ctx *c, int32_t mode, int32_t size, int32_t warps_
     } else if (mode == KMC_LAUNCH_THREADS) {
         if (warps_per_cta > 4) return fail(c, KMC_EINVAL, "thread plans take 1..4 warps per CTA");
         if (c->LD == 16 || c->LD == 32) {
-            // one domain per thread: the grid follows from the domains
-            if ((s = plan_thread_rows(c, warps_per_cta, pl)) != KMC_OK) return s;
+            // one domain per thread: the grid follows from the domains; size
+            // 0 or 1: the replicas one after another, 2: round-robin
+            if (size < 0 || size > 2) return fail(c, KMC_EINVAL, "thread plans of L_d = %d take size 0, 1 or 2", c->LD);
+            if ((s = plan_thread_rows(c, warps_per_cta, pl, size == 2)) != KMC_OK) return s;
         } else if ((s = plan_threads(c, size > 0 ? size : balanced_thread_ctas(c, warps_per_cta), warps_per_cta, pl)) !=
                    KMC_OK) {
             // size 0: the balanced grid of the library's choice

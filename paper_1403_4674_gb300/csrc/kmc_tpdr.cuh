@@ -57,7 +57,7 @@ template <int LD> struct TpdrLayout {
                          TOTHI = TOTLO + 1, CH = TOTLO + 2, CFL = CH + 1, CST = CH + 2, CCM = CH + 3, CCE = CH + 4,
                          OB0 = CH + 5, OB1 = OB0 + 1, OBM = OB0 + 2, OBE = OB0 + 3, CSB = OB0 + 4, CSH = CSB + 1,
                          OSB = CSB + 2, OSH = CSB + 3, CC = CSB + 4, AT = CC + 11, MR = AT + 10, TG = MR + 10,
-                         N64 = TG + CHUNK + 4;
+                         N64 = TG + CHUNK + 8;
     // 32-bit words per lane: spin rows, the halo the counts hold (N row, S
     // row, W column, E column), the domain's W and E columns, neighbour ids,
     // phase offset f << 16 | step j of each step of the chunk
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
         at(Lay::MR + c) = A[c] ? ~0ull / A[c] : 0ull;
     }
 #pragma unroll
-    for (int i = CHUNK; i < CHUNK + 4; ++i) at(Lay::TG + i) = ~0ull;
+    for (int i = CHUNK; i < CHUNK + 8; ++i) at(Lay::TG + i) = ~0ull;
     at(Lay::CC) = 0;
     // Score constants of the lane's replica (scores only; registers): the
     // two fixed-point words X_c (2^-Q) and Y_c (2^-(Q+18)) of a_c dlog a_c /
@@ -409,19 +409,32 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                     at32(Lay::HW) = hW;
                     at32(Lay::HE) = hE;
                 }
+                // two rows per round; re-counting a row is idempotent (its counts
+                // follow from the current spins and halo), so a lane with one row
+                // or none left re-counts row 0 in the free place
                 while (__any_sync(FULL_WARP, todo != 0)) {
-                    if (todo) {
-                        const int y = __ffs(todo) - 1;
+                    int yy[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        yy[u] = todo ? __ffs(todo) - 1 : 0;
                         todo &= todo - 1;
+                    }
+                    uint64_t lo[2], hi[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int y = yy[u];
                         const uint32_t Sy = at32(Lay::SP + y);
                         const uint32_t U = (y > 0) ? at32(Lay::SP + (y > 0 ? y - 1 : 0)) : hN;
                         const uint32_t D = (y < LD - 1) ? at32(Lay::SP + (y < LD - 1 ? y + 1 : 0)) : hS;
-                        uint64_t lo, hi;
-                        tpdr_row_counts<LD>(Sy, U, D, (hW >> y) & 1u, (hE >> y) & 1u, lo, hi);
+                        tpdr_row_counts<LD>(Sy, U, D, (hW >> y) & 1u, (hE >> y) & 1u, lo[u], hi[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int y = yy[u];
                         // differences of packed counts: exact once added to words that hold the old row
-                        const uint64_t dlo = lo - at(Lay::ROWLO + y), dhi = hi - at(Lay::ROWHI + y);
-                        at(Lay::ROWLO + y) = lo;
-                        at(Lay::ROWHI + y) = hi;
+                        const uint64_t dlo = lo[u] - at(Lay::ROWLO + y), dhi = hi[u] - at(Lay::ROWHI + y);
+                        at(Lay::ROWLO + y) = lo[u];
+                        at(Lay::ROWHI + y) = hi[u];
                         at(Lay::BLKLO + (y >> 3)) += dlo;
                         at(Lay::BLKHI + (y >> 3)) += dhi;
                         tlo += dlo;
@@ -494,6 +507,7 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                     scored = true;
                 };
 
+                bool corrupt = false; // counts and spins disagreed at some event
                 for (int base = 0; base < smax; base += CHUNK) {
                     if (base > 0) draw(base);
                     // Each lane jumps from real event to real event of its own
@@ -504,15 +518,31 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                     while (true) {
                         // the lane's next step with target < R' (targets past its
                         // last step are ~0), four at a time
+                        uint64_t tgt = 0;
                         while (i < CHUNK) {
                             const uint64_t R = C[9];
-                            const unsigned m = (at(Lay::TG + i) < R ? 1u : 0u) | (at(Lay::TG + i + 1) < R ? 2u : 0u) |
-                                               (at(Lay::TG + i + 2) < R ? 4u : 0u) | (at(Lay::TG + i + 3) < R ? 8u : 0u);
+                            uint64_t t[8];
+                            unsigned m = 0;
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                t[u] = at(Lay::TG + i + u);
+                                m |= (t[u] < R ? 1u : 0u) << u;
+                            }
                             if (m) {
-                                i += __ffs(m) - 1;
+                                const int f = __ffs(m) - 1;
+                                i += f;
+                                // t[f] by selection (no indexed registers)
+                                uint64_t q[4];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) q[u] = (f & 1) ? t[2 * u + 1] : t[2 * u];
+#pragma unroll
+                                for (int w = 4, bit = 2; w > 1; w >>= 1, bit <<= 1)
+#pragma unroll
+                                    for (int u = 0; u < w / 2; ++u) q[u] = (f & bit) ? q[2 * u + 1] : q[2 * u];
+                                tgt = q[0];
                                 break;
                             }
-                            i += 4;
+                            i += 8;
                         }
                         const bool ev = i < CHUNK;
                         if (GRAD) {
@@ -529,7 +559,6 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                         }
                         if (!__any_sync(FULL_WARP, ev)) break;
                         if (!ev) continue;
-                        const uint64_t tgt = at(Lay::TG + i);
                         const uint32_t eb = at32(Lay::EB + i);
                         ++i;
                         const uint64_t np = np0 + (eb >> 16);
@@ -661,16 +690,15 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                         const uint64_t kYlo = at(Lay::BLKLO + by), kYhi = at(Lay::BLKHI + by);
                         const uint64_t kOlo = at(Lay::BLKLO + bo), kOhi = at(Lay::BLKHI + bo);
                         at32(Lay::SP + y) = Sy ^ bit;
+                        // the neighbour rows first: without one (yN or yS = y) its
+                        // store writes row y's old words, which row y's store then
+                        // replaces
+                        at(Lay::ROWLO + yN) = rNlo + dNlo;
+                        at(Lay::ROWHI + yN) = rNhi + dNhi;
+                        at(Lay::ROWLO + yS) = rSlo + dSlo;
+                        at(Lay::ROWHI + yS) = rShi + dShi;
                         at(Lay::ROWLO + y) = rYlo + dYlo;
                         at(Lay::ROWHI + y) = rYhi + dYhi;
-                        if (hasN) {
-                            at(Lay::ROWLO + yN) = rNlo + dNlo;
-                            at(Lay::ROWHI + yN) = rNhi + dNhi;
-                        }
-                        if (hasS) {
-                            at(Lay::ROWLO + yS) = rSlo + dSlo;
-                            at(Lay::ROWHI + yS) = rShi + dShi;
-                        }
                         at(Lay::BLKLO + by) = kYlo + bYlo;
                         at(Lay::BLKHI + by) = kYhi + bYhi;
                         at(Lay::BLKLO + bo) = kOlo + bOlo;
@@ -688,12 +716,10 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                         dmag -= 2 * sgn;
                         rates();
                         scored = false;
-                        if (bad) {
-                            atomicCAS(P.err, 0, ERR_INTERNAL);
-                            i = CHUNK;
-                        }
+                        corrupt |= bad;
                     }
                 }
+                if (corrupt) atomicCAS(P.err, 0, ERR_INTERNAL);
                 if (has) {
                     // edges first (neighbours wait for them), then counters and record
                     uint64_t *ew = P.edges + (size_t)gl * EDGE_WORDS;

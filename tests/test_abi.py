@@ -56,6 +56,9 @@ def test_autotune_host_logic():
         autotune.max_domain_side(24)
     plans = autotune.plan_candidates(152)
     assert plans[0][0] == 0 and (2, 152, 16) in plans and (1, 16, 16) in plans
+    # 16x16 and 32x32 domains: thread plans in both domain orders, no CTA counts
+    rows = [p for p in autotune.plan_candidates(152, 32) if p[0] == 3]
+    assert (3, 1, 4) in rows and (3, 2, 4) in rows and all(p[1] in (1, 2) for p in rows)
     for name in ("run", "step", "capture", "sync", "close", "events_per_schedule"):
         assert callable(getattr(autotune.Batch, name, None)), name
     assert callable(getattr(autotune.BatchGraph, "replay", None))

@@ -37,7 +37,8 @@ def _check(spins_of, obs, idx, n, L, Ld, ks, seeds, beta, h, inits, scores=None,
                 np.testing.assert_allclose(obs[:, r, 4:6], robs[:, 4:6], rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("plan", ["grid_5x4", "grid_2x10", "grid_3x8", "grid_1x16", "cluster_16"])
+@pytest.mark.parametrize("plan", ["grid_5x4", "grid_2x10", "grid_3x8", "grid_1x16", "cluster_16", "threads_1",
+                                  "threads_rr_1", "threads_rr_4"])
 def test_ising1024_all_replicas(plan):
     """The 18 replicas of 1024^2 (T x start x k) in one context and launch,
     per-replica k and start, profiling on, as the benchmark runs them."""
@@ -53,7 +54,8 @@ def test_ising1024_all_replicas(plan):
     lat.set_rates(w.beta, w.h)
     sm = _sm()
     lat.set_launch(*{"grid_5x4": (2, 5 * sm, 4), "grid_2x10": (2, 2 * sm, 10), "grid_3x8": (2, 3 * sm, 8),
-                     "grid_1x16": (2, sm, 16), "cluster_16": (1, 16, 16)}[plan])
+                     "grid_1x16": (2, sm, 16), "cluster_16": (1, 16, 16), "threads_1": (3, 1, 1),
+                     "threads_rr_1": (3, 2, 1), "threads_rr_4": (3, 2, 4)}[plan])
     lat.profile(True)
     obs = lat.run(3, obs_every=1).cpu().numpy()
     lat.sync()
@@ -128,26 +130,35 @@ def test_lattice8192_one_schedule():
 
 def test_ising1024_full_timed_length_sampled_replica():
     """The benchmark's timed launch itself: all 18 replicas of 1024^2 in one
-    context on the grid the tuner picks for it (five CTAs of 4 warps per SM)
-    for the full 1e4 schedules with records every 10; replica 2 (k = 1, T = 3.0, random start: the most real events
-    per step) checked against the oracle over the whole run (about a minute
-    of CPU)."""
+    context for the full 1e4 schedules with records every 10, on the plans
+    the tuner chooses between (the warp kernel's grid of five CTAs of 4
+    warps per SM, and the thread kernel with the replicas dealt round-robin
+    over the warps); all 18 replicas' spins and records identical on both;
+    replica 2 (k = 1, T = 3.0, random start: the most real events per step)
+    checked against the oracle over the whole run (about a minute of CPU)."""
     import paper_1403_4674_gb300 as kmc
     from paper_1403_4674_gb300 import workloads as wl
     w = wl.ising1024_all()
     n = len(w.L)
     ks = [w.k_of(r) for r in range(n)]
     inits = [w.init_of(r) for r in range(n)]
-    lat = kmc.Lattice(w.L, w.L_d, ks[0], w.seeds, init=inits[0])
-    lat.set_replica_params(k=ks, init=inits)
-    lat.reset(kmc.KMC_INIT_PER_REPLICA)
-    lat.set_rates(w.beta, w.h)
-    lat.set_launch(2, 5 * _sm(), 4)
-    obs = lat.run(w.schedules, obs_every=w.obs_every).cpu().numpy()
-    lat.sync()
-    _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [2], w.schedules, w.L, w.L_d, ks, w.seeds, w.beta,
-           w.h, inits, obs_every=w.obs_every)
-    lat.close()
+    runs = []
+    for plan in ((2, 5 * _sm(), 4), (3, 2, 1)):
+        lat = kmc.Lattice(w.L, w.L_d, ks[0], w.seeds, init=inits[0])
+        lat.set_replica_params(k=ks, init=inits)
+        lat.reset(kmc.KMC_INIT_PER_REPLICA)
+        lat.set_rates(w.beta, w.h)
+        lat.set_launch(*plan)
+        obs = lat.run(w.schedules, obs_every=w.obs_every).cpu().numpy()
+        lat.sync()
+        assert lat.launch()[0] == plan[0]
+        runs.append((lat.spins.cpu().numpy(), obs, lat.replica_spins(2).cpu().numpy()))
+        lat.close()
+    (s0, o0, r0), (s1, o1, r1) = runs
+    assert np.array_equal(s0, s1), "the plans' final spins differ"
+    assert np.array_equal(o0[..., :3], o1[..., :3]), "the plans' records differ"
+    np.testing.assert_allclose(o0[..., 3], o1[..., 3], rtol=1e-12, atol=0)
+    _check(lambda r: r1, o1, [2], w.schedules, w.L, w.L_d, ks, w.seeds, w.beta, w.h, inits, obs_every=w.obs_every)
 
 
 def _oracle_grad_replica(args):

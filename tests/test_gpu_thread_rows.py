@@ -34,7 +34,21 @@ def test_plan_one_domain_per_thread(Ld):
         assert ctas * wpb >= 4 and smem > 0
     with pytest.raises(kmc.KmcError):
         lat.set_launch(THREADS, 0, 5)
+    with pytest.raises(kmc.KmcError):
+        lat.set_launch(THREADS, 3, 1)  # domain orders are 0/1 and 2
     lat.close()
+
+
+@pytest.mark.parametrize("Ld", [16, 32])
+@pytest.mark.parametrize("wpb", [1, 4])
+def test_parity_replicas_dealt_round_robin(Ld, wpb):
+    """Size 2: each colour's domains dealt round-robin over the replicas, so
+    that warps hold domains of replicas with different k, temperatures,
+    fields, starts and sizes: the same trajectories as the oracle's."""
+    L = [4 * Ld, 2 * Ld, 6 * Ld, 4 * Ld]
+    gpu, ref = run_both(L, Ld, [1, 16, 4, 40], [51, 52, 53, 54], [0.3, 0.45, 0.6, 0.4], [0.0, 0.05, -0.1, 0.02], 4,
+                        init=[0, 1, 0, 1], obs_every=1, launch=(THREADS, 2, wpb))
+    assert_parity(gpu, ref, len(L))
 
 
 @pytest.mark.parametrize("Ld", [16, 32])
