@@ -285,7 +285,7 @@ ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four sch
 def run_kernel_name(lat) -> str:
     """The persistent kernel a lattice's plan launches."""
     if lat.launch()[0] == 3:
-        return "tpd_kernel" if lat.L_d == 8 else "tpdr_kernel"
+        return {8: "tpd_kernel", 64: "tpdr64_kernel"}.get(lat.L_d, "tpdr_kernel")
     return "run_kernel"
 
 

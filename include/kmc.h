@@ -330,8 +330,9 @@ kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
 
 /* Launch plan of the persistent run kernel.
  *   KMC_LAUNCH_AUTO: the library's choice: KMC_LAUNCH_THREADS for L_d = 16
- *     and 32 when the domains' state fits the GPU's shared memory, and for
- *     L_d = 8 while scores are off; otherwise CLUSTER when every replica
+ *     and 32 when the domains' state fits the GPU's shared memory, for L_d =
+ *     64 when it fits and scores are off, and for L_d = 8 while scores are
+ *     off; otherwise CLUSTER when every replica
  *     fits one cluster of at most 16 CTAs at one visit per warp and phase,
  *     else a cooperative GRID (the shape with the most resident warps per SM
  *     that fits: three CTAs of 8 warps, two of 12 or 10, one of 16, ...),
@@ -345,32 +346,34 @@ kmc_status kmc_rate_table_error(const kmc_ctx *ctx, double *max_rel_err);
  *     neighbour domain is in the same CTA.  The run kernels hold 80 to 128
  *     registers per thread (by domain side and scores), so two or three CTAs
  *     of 8-12 warps can share an SM.
- *   KMC_LAUNCH_THREADS (L_d = 8, 16 or 32): one thread runs a whole domain
- *     process and a warp 32 of them at once, with no warp collective on the
- *     step path; warps_per_cta 1..4.
+ *   KMC_LAUNCH_THREADS (L_d = 8, 16, 32 or 64): one thread runs a whole
+ *     domain process and a warp 32 of them at once, with no warp collective
+ *     on the step path; warps_per_cta 1..4.
  *     L_d = 8: a cooperative grid of `size` CTAs (0: as many as spread each
  *     colour's domains evenly over at most three 4-warp CTAs per SM), thread
  *     t visiting the t-th, (t+T)-th, ... domain of each colour's list (T the
  *     grid's threads); an 8x8 domain is one 64-bit word, so the domain
  *     process runs in registers, with state, edge words and counters in
  *     global memory (L2).
- *     L_d = 16, 32: one domain per thread for the whole launch, a warp
+ *     L_d = 16, 32, 64: one domain per thread for the whole launch, a warp
  *     holding 32 domains of one colour; the domain's rows, the class counts
- *     of every row, of every block of 8 rows and of the domain, and its
- *     counters stay in the CTA's shared memory (about 1.5 KB per 32x32
- *     domain, 1.2 KB per 16x16 one); the grid follows from the domain
+ *     of every row (not at L_d = 64, where an event counts the 8 rows of
+ *     its block from their spins), of every block of 8 rows and of the
+ *     domain, and its counters stay in the CTA's shared memory (about
+ *     1.5 KB per 32x32 domain, 1.2 KB per 16x16 one, 1.5 KB per 64x64 one,
+ *     so 16,384 64x64 domains fit a GPU at once); the grid follows from the domain
  *     count and KMC_EINVAL is returned when the domains do not fit the GPU
  *     at once.  `size` orders each colour's domains over the warps: 0 or 1
  *     replica after replica, 2 round-robin over the replicas (each warp then
  *     holds domains of many replicas; faster when the replicas differ in
  *     steps per visit or temperature, slower on a batch of alike replicas);
  *     other values KMC_EINVAL.
- *     Both cover the palindromic and fixed schedules with the exponential or
+ *     All cover the palindromic and fixed schedules with the exponential or
  *     expected clock, and the L_d = 16, 32 kernel also path scores
  *     (kmc_enable_grad; each thread forms its own domain's FP64 score
  *     terms); a run that needs fixed-time visits, random colour orders or,
- *     at L_d = 8, scores first replaces the plan by the library's choice
- *     among the others (KMC_EINVAL while the stream is capturing).
+ *     at L_d = 8 or 64, scores first replaces the plan by the library's
+ *     choice among the others (KMC_EINVAL while the stream is capturing).
  * In all plans a visit starts as soon as its four neighbours have finished
  * their visits of earlier colour phases (per-domain dataflow instead of a
  * barrier per phase; Sec. 2.2 lets non-interacting domains run at once); observation records are built from per-visit changes,

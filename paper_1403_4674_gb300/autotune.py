@@ -54,12 +54,11 @@ def plan_candidates(sm_count: int, L_d: Optional[int] = None) -> List[Plan]:
             (KMC_LAUNCH_GRID, 2 * sm_count, 10), (KMC_LAUNCH_GRID, 2 * sm_count, 12),
             (KMC_LAUNCH_GRID, 3 * sm_count, 8), (KMC_LAUNCH_GRID, 4 * sm_count, 5),
             (KMC_LAUNCH_GRID, 5 * sm_count, 4), (KMC_LAUNCH_GRID, 6 * sm_count, 4)]
-    # one thread per domain (L_d = 8, 16, 32; the library refuses it
-    # otherwise): for 8x8 domains the library's balanced grid and grids of
-    # fixed size; 16x16 and 32x32 ones take one domain per thread, their size
-    # choosing the order of the domains over the warps (1: replica after
-    # replica, 2: round-robin over the replicas)
-    if L_d in (16, 32):
+    # one thread per domain: for 8x8 domains the library's balanced grid and
+    # grids of fixed size; 16x16, 32x32 and 64x64 ones take one domain per
+    # thread, their size choosing the order of the domains over the warps (1:
+    # replica after replica, 2: round-robin over the replicas)
+    if L_d in (16, 32, 64):
         out += [(KMC_LAUNCH_THREADS, o, w) for o in (1, 2) for w in (4, 1)]
     elif L_d in (None, 8):
         out += [(KMC_LAUNCH_THREADS, 0, 4), (KMC_LAUNCH_THREADS, 0, 1)]

@@ -20,9 +20,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkmc_gb300.so")
 SOURCES = [os.path.join(CSRC, "kmc_api.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "kmc_kernels.cuh"), os.path.join(CSRC, "kmc_ring.cuh"),
-        os.path.join(CSRC, "kmc_part.cuh"), os.path.join(CSRC, "kmc_tpd.cuh"), os.path.join(CSRC, "kmc_tpdr.cuh"),
-        os.path.join(ROOT, "include", "kmc.h")]
+DEPS = SOURCES + [os.path.join(CSRC, name) for name in ("kmc_kernels.cuh", "kmc_ring.cuh", "kmc_part.cuh",
+                                                          "kmc_tpd.cuh", "kmc_tpdr.cuh", "kmc_tpdr64.cuh")] + \
+    [os.path.join(ROOT, "include", "kmc.h")]
 
 
 def nvcc() -> str:

@@ -11,6 +11,7 @@
 #include "kmc_part.cuh"
 #include "kmc_tpd.cuh"
 #include "kmc_tpdr.cuh"
+#include "kmc_tpdr64.cuh"
 
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
@@ -560,6 +561,7 @@ using TpdKernel = void (*)(const RunParams);
 // shared-memory kernel of 16x16 and 32x32 domains only)
 TpdKernel tpd_kernel_for(int LD, bool expo, bool grad)
 {
+    if (LD == 64) return expo ? tpdr64_kernel<true> : tpdr64_kernel<false>;
     if (LD == 16)
         return grad ? (expo ? tpdr_kernel<16, true, true> : tpdr_kernel<16, false, true>)
                     : (expo ? tpdr_kernel<16, true, false> : tpdr_kernel<16, false, false>);
@@ -568,7 +570,10 @@ TpdKernel tpd_kernel_for(int LD, bool expo, bool grad)
                     : (expo ? tpdr_kernel<32, true, false> : tpdr_kernel<32, false, false>);
     return expo ? tpd_kernel<true> : tpd_kernel<false>;
 }
-size_t tpdr_warp_bytes_for(int LD) { return LD == 16 ? tpdr_warp_bytes<16>() : tpdr_warp_bytes<32>(); }
+size_t tpdr_warp_bytes_for(int LD)
+{
+    return LD == 16 ? tpdr_warp_bytes<16>() : LD == 32 ? tpdr_warp_bytes<32>() : tpdr64_warp_bytes();
+}
 
 // THREADS plan for L_d = 16, 32: warps of 32 domains of one colour, one per
 // thread and consecutive in the colour list (a colour's last warp may be
@@ -586,7 +591,7 @@ size_t tpdr_warp_bytes_for(int LD) { return LD == 16 ? tpdr_warp_bytes<16>() : t
 // nothing (256 x 256^2 with scores: 278 -> 322 ms).
 kmc_status plan_thread_rows(kmc_ctx *c, int wpb, Plan &pl, bool interleave)
 {
-    if (c->LD != 16 && c->LD != 32) return fail(c, KMC_EINVAL, "no thread-row kernel for L_d = %d", c->LD);
+    if (c->LD != 16 && c->LD != 32 && c->LD != 64) return fail(c, KMC_EINVAL, "no thread-row kernel for L_d = %d", c->LD);
     if (wpb < 1 || wpb > 4) return fail(c, KMC_EINVAL, "thread plans take 1..4 warps per CTA");
     pl = Plan();
     pl.mode = KMC_LAUNCH_THREADS;
@@ -643,7 +648,8 @@ int balanced_thread_ctas(const kmc_ctx *c, int wpb)
 kmc_status check_plan(kmc_ctx *c, const Plan &pl)
 {
     if (pl.mode == KMC_LAUNCH_THREADS) {
-        if (c->grad && c->LD == 8) return fail(c, KMC_EINVAL, "the thread-per-domain plan of L_d = 8 has no score kernel");
+        if (c->grad && (c->LD == 8 || c->LD == 64))
+            return fail(c, KMC_EINVAL, "the thread-per-domain plan of L_d = %d has no score kernel", c->LD);
         for (int e = 0; e < 2; ++e) {
             const void *kern = (const void *)tpd_kernel_for(c->LD, e == 0, c->grad);
             if (pl.smem > 0) {
@@ -731,12 +737,13 @@ kmc_status install_plan(kmc_ctx *c, Plan &pl)
 kmc_status default_warp_plan(kmc_ctx *c);
 
 // The library's plan: one thread per domain (a warp then runs 32 domain
-// processes): for 8x8 domains with state in L2 while scores are off, for
-// 16x16 and 32x32 domains with state in shared memory when it fits the
-// GPU; else the warp plans below.
+// processes): for 8x8 domains with state in L2 and for 64x64 domains with
+// state in shared memory while scores are off, for 16x16 and 32x32 domains
+// with state in shared memory with or without scores, when it fits the GPU;
+// else the warp plans below.
 kmc_status default_plan(kmc_ctx *c)
 {
-    if ((!c->grad && c->LD == 8) || c->LD == 16 || c->LD == 32) {
+    if ((!c->grad && (c->LD == 8 || c->LD == 64)) || c->LD == 16 || c->LD == 32) {
         Plan pl;
         const kmc_status st = (c->LD == 8) ? plan_threads(c, balanced_thread_ctas(c, 4), 4, pl)
                                            : plan_thread_rows(c, 1, pl, false);
@@ -1372,7 +1379,7 @@ kmc_status kmc_set_launch(kmc_ctx *c, int32_t mode, int32_t size, int32_t warps_
         if ((s = plan_grid(c, size, warps_per_cta, pl)) != KMC_OK) return s;
     } else if (mode == KMC_LAUNCH_THREADS) {
         if (warps_per_cta > 4) return fail(c, KMC_EINVAL, "thread plans take 1..4 warps per CTA");
-        if (c->LD == 16 || c->LD == 32) {
+        if (c->LD == 16 || c->LD == 32 || c->LD == 64) {
             // one domain per thread: the grid follows from the domains; size
             // 0 or 1: the replicas one after another, 2: round-robin
             if (size < 0 || size > 2) return fail(c, KMC_EINVAL, "thread plans of L_d = %d take size 0, 1 or 2", c->LD);
@@ -1511,8 +1518,8 @@ kmc_status kmc_run_schedule(kmc_ctx *c, int64_t n_schedules, int32_t schedule, i
     const int64_t units = pass_obs ? n_schedules * (schedule == KMC_SCHEDULE_PALINDROME ? 8 : 4) : n_schedules;
     const int64_t n_obs = want_obs ? units / obs_every : 0;
     const bool cap = capturing(c);
-    if (c->plan.mode == KMC_LAUNCH_THREADS && ((c->grad && c->LD == 8) || time_mode == KMC_TIME_HORIZON ||
-                                               schedule == KMC_SCHEDULE_RANDOM_PERM)) {
+    if (c->plan.mode == KMC_LAUNCH_THREADS && ((c->grad && (c->LD == 8 || c->LD == 64)) ||
+                                               time_mode == KMC_TIME_HORIZON || schedule == KMC_SCHEDULE_RANDOM_PERM)) {
         // the thread kernels cover fixed-length visits of the palindromic
         // and fixed schedules (with scores at L_d = 16, 32): this run takes a warp plan
         // (installed once the stream has drained: earlier launches read the

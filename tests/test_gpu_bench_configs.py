@@ -111,16 +111,18 @@ def test_grad_256_replicas_sample():
     lat.close()
 
 
-def test_lattice8192_one_schedule():
-    """8192^2 at L_d = 64, k = 8 on the 16-warp grid: one schedule, checked
-    on every site against the oracle (one replica; the C oracle runs it in
-    seconds)."""
+@pytest.mark.parametrize("plan", [(2, 0, 16), (3, 1, 4), (3, 1, 1)])
+def test_lattice8192_one_schedule(plan):
+    """8192^2 at L_d = 64, k = 8 on the 16-warp grid and on the thread plan:
+    one schedule, checked on every site against the oracle (one replica; the
+    C oracle runs it in seconds)."""
     import paper_1403_4674_gb300 as kmc
     from paper_1403_4674_gb300 import workloads as wl
     w = wl.lattice_8192()
     lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
     lat.set_rates(w.beta, w.h)
-    lat.set_launch(2, _sm(), 16)
+    lat.set_launch(plan[0], plan[1] or _sm(), plan[2])
+    assert lat.launch()[0] == plan[0]
     obs = lat.run(1, obs_every=1).cpu().numpy()
     lat.sync()
     _check(lambda r: lat.replica_spins(r).cpu().numpy(), obs, [0], 1, w.L, w.L_d, [w.k], w.seeds, w.beta, w.h,
@@ -233,7 +235,8 @@ def test_batched_512_full_step_sample():
     batch.close()
 
 
-def test_lattice8192_full_length_properties():
+@pytest.mark.parametrize("plan", [(2, 0, 16), (3, 1, 4)])
+def test_lattice8192_full_length_properties(plan):
     """The 8192^2 benchmark launch at its full 2000 schedules (too long for
     the oracle), checked by properties that hold at any size: the records,
     built on the device from per-visit changes, equal e and m recomputed from
@@ -246,7 +249,8 @@ def test_lattice8192_full_length_properties():
     L, n = w.L[0], w.schedules
     lat = kmc.Lattice(w.L, w.L_d, w.k, w.seeds)
     lat.set_rates(w.beta, w.h)
-    lat.set_launch(2, _sm(), 16)
+    lat.set_launch(plan[0], plan[1] or _sm(), plan[2])
+    assert lat.launch()[0] == plan[0]
     obs = lat.run(n, obs_every=n // 2).cpu().numpy()
     s = lat.spins.view(L, L).to(torch.int32)
     bonds = int((s * (torch.roll(s, -1, 1) + torch.roll(s, -1, 0))).sum().item())

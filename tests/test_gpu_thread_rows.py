@@ -1,6 +1,7 @@
-"""The thread-per-domain plan at L_d = 16 and 32 (KMC_LAUNCH_THREADS): one
-thread runs a whole domain process (Sec. 2.2) with the domain's rows and
-class counts in shared memory.  Checked against the oracle element by
+"""The thread-per-domain plan at L_d = 16, 32 and 64 (KMC_LAUNCH_THREADS):
+one thread runs a whole domain process (Sec. 2.2) with the domain's rows and
+class counts in shared memory (at L_d = 64 the counts of blocks of 8 rows,
+a row's counted from its spins when an event needs it).  Checked against the oracle element by
 element, as the warp plans are: spins, per-domain real-event counts and event
 hashes bit-exact, e, m, e*m bit-exact, clocks to 1e-12; and against a warp
 plan on the same seeds."""
@@ -22,7 +23,7 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("Ld", [16, 32])
+@pytest.mark.parametrize("Ld", [16, 32, 64])
 def test_plan_one_domain_per_thread(Ld):
     import paper_1403_4674_gb300 as kmc
     lat = kmc.Lattice([4 * Ld, 8 * Ld], Ld, 4, [1, 2])
@@ -39,7 +40,7 @@ def test_plan_one_domain_per_thread(Ld):
     lat.close()
 
 
-@pytest.mark.parametrize("Ld", [16, 32])
+@pytest.mark.parametrize("Ld", [16, 32, 64])
 @pytest.mark.parametrize("wpb", [1, 4])
 def test_parity_replicas_dealt_round_robin(Ld, wpb):
     """Size 2: each colour's domains dealt round-robin over the replicas, so
@@ -51,7 +52,7 @@ def test_parity_replicas_dealt_round_robin(Ld, wpb):
     assert_parity(gpu, ref, len(L))
 
 
-@pytest.mark.parametrize("Ld", [16, 32])
+@pytest.mark.parametrize("Ld", [16, 32, 64])
 @pytest.mark.parametrize("k", [1, 5, 16, 40])
 @pytest.mark.parametrize("time_mode", [0, 1])
 def test_parity_steps_and_clocks(Ld, k, time_mode):
@@ -64,7 +65,7 @@ def test_parity_steps_and_clocks(Ld, k, time_mode):
     assert_parity(gpu, ref, 3)
 
 
-@pytest.mark.parametrize("Ld", [16, 32])
+@pytest.mark.parametrize("Ld", [16, 32, 64])
 @pytest.mark.parametrize("law", [orc.RATE_METROPOLIS, orc.RATE_BARKER])
 @pytest.mark.parametrize("schedule", [0, 1])
 def test_laws_and_schedules(Ld, law, schedule):
@@ -73,7 +74,7 @@ def test_laws_and_schedules(Ld, law, schedule):
     assert_parity(gpu, ref, 1)
 
 
-@pytest.mark.parametrize("Ld", [16, 32])
+@pytest.mark.parametrize("Ld", [16, 32, 64])
 @pytest.mark.parametrize("every", [1, 3])
 def test_colour_pass_records(Ld, every):
     gpu, ref = run_both([4 * Ld, 2 * Ld], Ld, 4, [5, 6], [0.4, 0.5], [0.0, 0.03], 3, obs_every=every,
@@ -81,7 +82,7 @@ def test_colour_pass_records(Ld, every):
     assert_parity(gpu, ref, 2)
 
 
-@pytest.mark.parametrize("Ld", [16, 32])
+@pytest.mark.parametrize("Ld", [16, 32, 64])
 def test_extreme_temperatures(Ld):
     """beta = 0 (every step a real event for Metropolis) and a cold all-up
     start at beta = 4.5 (almost every step null; the rows hold one class)."""
@@ -104,7 +105,7 @@ def test_uneven_batch_per_replica_k_and_start():
     assert_parity(gpu, ref, len(L))
 
 
-@pytest.mark.parametrize("Ld", [16, 32])
+@pytest.mark.parametrize("Ld", [16, 32, 64])
 def test_thread_and_warp_plans_agree(Ld):
     """Same seeds under the thread plan and a warp grid plan: identical
     trajectories and records, clocks to 1e-12 (they multiply the clock
@@ -208,10 +209,30 @@ def test_scores_equal_the_warp_kernels(Ld):
     np.testing.assert_allclose(o0[..., 4:6], o1[..., 4:6], rtol=1e-13, atol=1e-13)
 
 
-def test_bounded_waits_give_up_and_context_survives():
+def test_scores_at_64_take_a_warp_plan():
+    """The 64x64 thread kernel carries no scores: a run with scores installs
+    a warp plan and follows the oracle."""
+    import paper_1403_4674_gb300 as kmc
+    lat = kmc.Lattice([128], 64, 4, [3])
+    lat.set_launch(THREADS, 0, 4)
+    assert lat.launch()[0] == THREADS
+    lat.set_rates([0.4], [0.02])
+    lat.enable_grad(True)
+    ref = orc.Replica(L=128, Ld=64, k=4, seed=3, beta=0.4, h=0.02)
+    ref.enable_score()
+    lat.run(3)
+    ref.run(3)
+    assert lat.launch()[0] != THREADS
+    np.testing.assert_allclose(lat.score().cpu().numpy()[0], ref.score.sum(axis=0), rtol=1e-12, atol=1e-12)
+    assert np.array_equal(lat.replica_spins(0).cpu().numpy(), ref.spins)
+    lat.close()
+
+
+@pytest.mark.parametrize("Ld", [32, 64])
+def test_bounded_waits_give_up_and_context_survives(Ld):
     """Waits for neighbour visits that never come end in KMC_ETIMEOUT."""
     import paper_1403_4674_gb300 as kmc
-    lat = kmc.Lattice([128], 32, 2, [5])
+    lat = kmc.Lattice([128], Ld, 2, [5])
     lat.set_launch(THREADS, 0, 4)
     kmc.kmc_debug_barrier(lat.ctx, 1, 20_000_000)  # 20 ms
     lat.run(3)
@@ -223,7 +244,7 @@ def test_bounded_waits_give_up_and_context_survives():
     lat.set_rates([0.4], [0.0])
     lat.run(3)
     lat.sync()
-    ref = orc.Replica(L=128, Ld=32, k=2, seed=5, beta=0.4)
+    ref = orc.Replica(L=128, Ld=Ld, k=2, seed=5, beta=0.4)
     ref.run(3)
     assert np.array_equal(lat.replica_spins(0).cpu().numpy(), ref.spins)
     lat.close()

@@ -27,22 +27,21 @@ def _sm():
 
 
 def test_default_plans():
-    """One thread per domain for 8x8, 16x16 and 32x32 domains; with scores
-    on, 16x16 and 32x32 domains keep it (their thread kernel carries
-    scores) and 8x8 domains take a warp plan; 64x64 domains always take a
-    warp plan."""
+    """One thread per domain for every domain side; with scores on, 16x16
+    and 32x32 domains keep it (their thread kernel carries scores) and 8x8
+    and 64x64 domains take a warp plan."""
     import paper_1403_4674_gb300 as kmc
-    for Ld in (8, 16, 32):
+    for Ld in (8, 16, 32, 64):
         lat = kmc.Lattice([4 * Ld, 2 * Ld], Ld, 4, [1, 2])
         assert lat.launch()[0] == THREADS
         lat.enable_grad(True)
-        assert (lat.launch()[0] == THREADS) == (Ld != 8)
+        assert (lat.launch()[0] == THREADS) == (Ld in (16, 32))
         lat.close()
     lat = kmc.Lattice([128], 64, 4, [1])
-    assert lat.launch()[0] != THREADS
+    lat.set_launch(2, _sm(), 8)
     with pytest.raises(kmc.KmcError):
-        lat.set_launch(THREADS, _sm(), 4)  # 64x64 domains: refused, previous plan kept
-    assert lat.launch()[0] != THREADS
+        lat.set_launch(THREADS, _sm(), 4)  # a CTA count is no domain order: refused, previous plan kept
+    assert lat.launch()[0] == 2
     lat.close()
 
 
