@@ -338,7 +338,7 @@ def kernel_source_sha256() -> str:
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("kmc_kernels.cuh", "kmc_tpd.cuh", "kmc_tpdr.cuh"):
+    for name in ("kmc_kernels.cuh", "kmc_tpd.cuh", "kmc_tpdr.cuh", "kmc_tpdr64.cuh"):
         with open(os.path.join(ROOT, "paper_1403_4674_gb300", "csrc", name)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -517,7 +517,7 @@ def variant_lattice8192(args, peaks, flush, stream):
     else:
         plan, _ = autotune.tune_plan(lat, w.beta, w.h, trial_schedules=20)
     lat.profile(True)
-    n = w.schedules
+    n = args.schedules if args.schedules > 0 else w.schedules  # a shorter run only for profiling captures
 
     def step():
         lat.reset(kmc.KMC_INIT_RANDOM)
@@ -702,6 +702,7 @@ def variant_pollcost(args, peaks, flush, stream):
     iteration.  The context is checked to be usable afterwards."""
     import torch
     import paper_1403_4674_gb300 as kmc
+    from paper_1403_4674_gb300 import workloads as wl
     w, desc = main_workload("ising1024", 0, 0)
     ks = [w.k_of(r) for r in range(len(w.L))]
     inits = [w.init_of(r) for r in range(len(w.L))]
@@ -744,9 +745,27 @@ def variant_pollcost(args, peaks, flush, stream):
     out["thread_rows"] = {"launch": list(lat.launch()), "status_after_timeout": status, "polls": lat.profile_polls()}
     kmc.kmc_debug_barrier(lat.ctx, 0, 0)
     lat.close()
+    # the 64x64 thread kernel (count per warp poll round): the 8192^2 lattice
+    w64 = wl.lattice_8192(seed=8192)
+    lat = kmc.Lattice(w64.L, w64.L_d, w64.k, w64.seeds)
+    lat.set_rates(w64.beta, w64.h)
+    lat.set_launch(3, 1, 4)
+    kmc.kmc_debug_barrier(lat.ctx, 1, limit_ns)
+    lat.profile(True)
+    lat.run(1)
+    try:
+        lat.sync()
+        status = 0
+    except kmc.KmcError as e:
+        status = e.status
+    out["thread_rows64"] = {"workload": "8192^2, L_d = 64, k = 8", "launch": list(lat.launch()),
+                            "status_after_timeout": status, "polls": lat.profile_polls()}
+    kmc.kmc_debug_barrier(lat.ctx, 0, 0)
+    lat.close()
+    if status != -5:
+        raise RuntimeError("expected KMC_ETIMEOUT from the 64x64 thread plan's waits, got %d" % status)
     # the same for the thread-per-domain kernel (its count is per thread): the
     # batched workload's 512 replicas at L_d = 8, k = 16 on the library's plan
-    from paper_1403_4674_gb300 import workloads as wl
     wb = wl.batched_replicas(512, master=512)
     lat = kmc.Lattice(wb.L, 8, 16, wb.seeds)
     lat.set_rates(wb.beta, wb.h)
