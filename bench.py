@@ -267,17 +267,17 @@ def reference_arm(args):
 # thread iteration for the thread-per-domain kernel).  They hold for the
 # kernel sources with this SHA-256 and are left out of the line once the
 # sources change.
-NCU_KERNEL_SHA256 = "9fd4c6568cbc78efb87e729f7a13e8c87fa5431690938c3388a0a7c4869e730e"
+NCU_KERNEL_SHA256 = "9bf7358672f81ece489232e17a5e6b7fd981688f6f5255ee636b1be899f4837c"
 # instructions of one poll iteration: per warp iteration for the warp kernels
 # and the shared-memory thread kernel, per thread re-read for the 8x8 one
-INST_PER_POLL = {"run_kernel": 22.24, "tpd_kernel": 0.85, "tpdr_kernel": 27.28}
+INST_PER_POLL = {"run_kernel": 22.24, "tpd_kernel": 0.85, "tpdr_kernel": 28.38, "tpdr64_kernel": 32.44}
 NCU_COUNTS = {
     # (workload, kernel): (warp instructions, steps, poll iterations or None, DRAM bytes) of one launch
-    ("ising1024", "run_kernel"): (424601387407, 2580480000, 1572303118, 6401280),
-    ("ising1024", "tpdr_kernel"): (51462792856, 2580480000, 226211721, 7025152),
-    ("grad", "run_kernel"): (281949602755, 1310720000, 1232445050, 4996352),
-    ("lattice8192", "run_kernel"): (144446437556, 524288000, 435496368, 10969600),
-    ("batched", "tpd_kernel"): (38908958794, 2636876800, 168298809, 7615934464),
+    ("ising1024", "tpdr_kernel"): (105701953345, 2580480000, 359845347, 6919936),
+    ("ising1024", "run_kernel"): (424586232478, 2580480000, 1572988655, 6585856),
+    ("grad", "tpdr_kernel"): (38819166107, 1310720000, 238780472, 5571840),
+    ("lattice8192", "tpdr64_kernel"): (18400662534, 524288000, 59494537, 11306240),
+    ("batched", "tpd_kernel"): (38915595659, 2636876800, 170153118, 7601300224),
 }
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 
