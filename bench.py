@@ -273,7 +273,7 @@ NCU_KERNEL_SHA256 = "9bf7358672f81ece489232e17a5e6b7fd981688f6f5255ee636b1be899f
 INST_PER_POLL = {"run_kernel": 22.24, "tpd_kernel": 0.85, "tpdr_kernel": 28.38, "tpdr64_kernel": 32.44}
 NCU_COUNTS = {
     # (workload, kernel): (warp instructions, steps, poll iterations or None, DRAM bytes) of one launch
-    ("ising1024", "tpdr_kernel"): (105701953345, 2580480000, 359845347, 6919936),
+    ("ising1024", "tpdr_kernel/rr"): (105701953345, 2580480000, 359845347, 6919936),
     ("ising1024", "run_kernel"): (424586232478, 2580480000, 1572988655, 6585856),
     ("grad", "tpdr_kernel"): (38819166107, 1310720000, 238780472, 5571840),
     ("lattice8192", "tpdr64_kernel"): (18400662534, 524288000, 59494537, 11306240),
@@ -287,6 +287,17 @@ def run_kernel_name(lat) -> str:
     if lat.launch()[0] == 3:
         return {8: "tpd_kernel", 64: "tpdr64_kernel"}.get(lat.L_d, "tpdr_kernel")
     return "run_kernel"
+
+
+def counts_kernel(lat, plan) -> str:
+    """The name the ncu counts of a launch are keyed by: the kernel, marked
+    "/rr" on a thread plan that deals several replicas round-robin over the
+    warps (the same kernel on another domain order, with other counts)."""
+    k = run_kernel_name(lat)
+    if k in ("tpdr_kernel", "tpdr64_kernel") and plan is not None and len(plan) > 1 and plan[0] == 3 \
+            and plan[1] == 2 and lat.n_replicas > 1:
+        k += "/rr"
+    return k
 
 
 def ncu_counts(workload: str, kernel: str):
@@ -310,7 +321,7 @@ def issue_roofline(workload: str, kernel: str, steps_per_s: float, sm_mhz: float
     the capture's."""
     import torch
     cnt = ncu_counts(workload, kernel)
-    ipp = INST_PER_POLL.get(kernel)
+    ipp = INST_PER_POLL.get(kernel.split("/")[0])
     if cnt is None or ipp is None:
         return None
     inst, steps, polls, _ = cnt
@@ -490,8 +501,8 @@ def variant_grad(args, peaks, flush, stream):
            "lr_grad_e_beta_h": [float(ge[0]), float(ge[1])], "lr_grad_m_beta_h": [float(gm[0]), float(gm[1])],
            "events_per_step": ev, "cpu_baseline": cpu, "polls_per_launch": polls / max(run_n, 1),
            "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks,
-                                launch_traffic("grad", run_kernel_name(lat)))}
-    iss = issue_roofline("grad", run_kernel_name(lat), ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0,
+                                launch_traffic("grad", counts_kernel(lat, plan)))}
+    iss = issue_roofline("grad", counts_kernel(lat, plan), ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0,
                          float(peaks.get("sm_max_mhz", 2070.0)), polls / max(ev * max(run_n, 1), 1))
     if iss is not None:
         out["roofline"]["issue"] = iss
@@ -539,9 +550,9 @@ def variant_lattice8192(args, peaks, flush, stream):
            "plan": list(plan), "launch": list(lat.launch()), "events_per_step": ev, "cpu_baseline": cpu,
            "polls_per_launch": polls / max(run_n, 1),
            "roofline": roofline(by, (run_ms / 1000.0) / max(run_n, 1), peaks,
-                                launch_traffic("lattice8192", run_kernel_name(lat)))}
+                                launch_traffic("lattice8192", counts_kernel(lat, plan)))}
     rate = ev * max(run_n, 1) / (run_ms / 1000.0) if run_ms > 0 else 0.0
-    iss = issue_roofline("lattice8192", run_kernel_name(lat), rate, float(peaks.get("sm_max_mhz", 2070.0)),
+    iss = issue_roofline("lattice8192", counts_kernel(lat, plan), rate, float(peaks.get("sm_max_mhz", 2070.0)),
                          polls / max(ev * max(run_n, 1), 1))
     if iss is not None:
         out["roofline"]["issue"] = iss
@@ -943,7 +954,8 @@ def main():
 
     full = args.schedules == 0
     kern = run_kernel_name(lat)
-    traffic = launch_traffic(args.workload, kern) if full else None
+    ckern = counts_kernel(lat, plan)
+    traffic = launch_traffic(args.workload, ckern) if full else None
     avg_run_s = (run_ms / 1000.0) / max(run_n, 1)
     roof = roofline(bytes_step, avg_run_s, peaks, traffic)
     roof.update({"kernel": "kmcdev::" + kern, "run_kernel_ms_avg": 1000 * avg_run_s,
@@ -952,7 +964,7 @@ def main():
                  "polls_per_launch": polls / max(run_n, 1)})
     # the bound this kernel actually meets: instruction issue
     if full and clk.get("sm_mhz") and avg_run_s > 0:
-        iss = issue_roofline(args.workload, kern, events_step / avg_run_s, clk["sm_mhz"],
+        iss = issue_roofline(args.workload, ckern, events_step / avg_run_s, clk["sm_mhz"],
                              polls / max(events_step * max(run_n, 1), 1))
         if iss is not None:
             roof["issue"] = iss
