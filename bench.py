@@ -264,10 +264,18 @@ def reference_arm(args):
 # (kmc_profile_polls) of one launch, DRAM bytes read + written, and the
 # instructions of one poll iteration (a launch whose every wait runs out:
 # `bench.py --only pollcost`; per warp iteration for the warp kernels, per
-# thread iteration for the thread-per-domain kernel).  They hold for the
-# kernel sources with this SHA-256 and are left out of the line once the
-# sources change.
-NCU_KERNEL_SHA256 = "9bf7358672f81ece489232e17a5e6b7fd981688f6f5255ee636b1be899f4837c"
+# thread iteration for the thread-per-domain kernel).  Each kernel's counts
+# hold for the sources it is compiled from with these SHA-256 values and are
+# left out of the line once those sources change.
+KERNEL_SOURCES = {"run_kernel": ("kmc_kernels.cuh",), "tpd_kernel": ("kmc_kernels.cuh", "kmc_tpd.cuh"),
+                  "tpdr_kernel": ("kmc_kernels.cuh", "kmc_tpdr.cuh"),
+                  "tpdr64_kernel": ("kmc_kernels.cuh", "kmc_tpdr.cuh", "kmc_tpdr64.cuh")}
+NCU_KERNEL_SHA256 = {
+    "run_kernel": "90af89946413baa798ef8f01d0c7ce7e5b89bd1e0fd3acf67e20162380c30ad6",
+    "tpd_kernel": "c6082338e7624860ab0f10a762086cc1e094e0e123ff3223d4087b046854577d",
+    "tpdr_kernel": "1c3f3576cd4a8b8ff68d0f0762f1031a3aaaa29eaceace994b1a14a8ede61ed8",
+    "tpdr64_kernel": "6b404b82601f0094f4f12fc6fe54ed1788cea73a5585c71dbbe6715c588f5699",
+}
 # instructions of one poll iteration: per warp iteration for the warp kernels
 # and the shared-memory thread kernel, per thread re-read for the 8x8 one
 INST_PER_POLL = {"run_kernel": 22.24, "tpd_kernel": 0.85, "tpdr_kernel": 28.38, "tpdr64_kernel": 32.44}
@@ -302,7 +310,9 @@ def counts_kernel(lat, plan) -> str:
 
 def ncu_counts(workload: str, kernel: str):
     """The workload's ncu counters on that kernel, if taken on the current kernel source."""
-    if NCU_KERNEL_SHA256 is None or NCU_KERNEL_SHA256 != kernel_source_sha256():
+    base = kernel.split("/")[0]
+    want = NCU_KERNEL_SHA256.get(base)
+    if want is None or want != kernel_source_sha256(base):
         return None
     return NCU_COUNTS.get((workload, kernel))
 
@@ -342,14 +352,15 @@ def issue_roofline(workload: str, kernel: str, steps_per_s: float, sm_mhz: float
                       "per poll iteration; peak = 4 warp instructions per SM cycle x %d SMs x %.0f MHz" % (sms, sm_mhz)}
 
 
-def kernel_source_sha256() -> str:
-    """SHA-256 over the device code of the run kernels (warp and thread plans),
-    comments and blank lines left out, so that a comment edit keeps counters
-    taken on the same code."""
+def kernel_source_sha256(kernel: str = "") -> str:
+    """SHA-256 over the device code of one run kernel (its sources in
+    KERNEL_SOURCES), or of all of them, comments and blank lines left out, so
+    that a comment edit keeps counters taken on the same code."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("kmc_kernels.cuh", "kmc_tpd.cuh", "kmc_tpdr.cuh", "kmc_tpdr64.cuh"):
+    names = KERNEL_SOURCES[kernel] if kernel else ("kmc_kernels.cuh", "kmc_tpd.cuh", "kmc_tpdr.cuh", "kmc_tpdr64.cuh")
+    for name in names:
         with open(os.path.join(ROOT, "paper_1403_4674_gb300", "csrc", name)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
