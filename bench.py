@@ -272,7 +272,7 @@ KERNEL_SOURCES = {"run_kernel": ("kmc_kernels.cuh",), "tpd_kernel": ("kmc_kernel
                   "tpdr64_kernel": ("kmc_kernels.cuh", "kmc_tpdr.cuh", "kmc_tpdr64.cuh")}
 NCU_KERNEL_SHA256 = {
     "run_kernel": "90af89946413baa798ef8f01d0c7ce7e5b89bd1e0fd3acf67e20162380c30ad6",
-    "tpd_kernel": "c6082338e7624860ab0f10a762086cc1e094e0e123ff3223d4087b046854577d",
+    "tpd_kernel": "5ab1c616b84c8ddd0b73b5d36543cc05ac331f4a3fd1470c4adebfb01c54cb6b",
     "tpdr_kernel": "1c3f3576cd4a8b8ff68d0f0762f1031a3aaaa29eaceace994b1a14a8ede61ed8",
     "tpdr64_kernel": "6b404b82601f0094f4f12fc6fe54ed1788cea73a5585c71dbbe6715c588f5699",
 }
@@ -285,7 +285,7 @@ NCU_COUNTS = {
     ("ising1024", "run_kernel"): (424586232478, 2580480000, 1572988655, 6585856),
     ("grad", "tpdr_kernel"): (38819166107, 1310720000, 238780472, 5571840),
     ("lattice8192", "tpdr64_kernel"): (18400662534, 524288000, 59494537, 11306240),
-    ("batched", "tpd_kernel"): (38915595659, 2636876800, 170153118, 7601300224),
+    ("batched", "tpd_kernel"): (37003135232, 2636876800, 160081004, 7619467264),
 }
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 

@@ -92,7 +92,7 @@ def test_thread_and_warp_plans_agree():
     import paper_1403_4674_gb300 as kmc
     L, seeds = [64, 128, 256], [31, 32, 33]
     out = []
-    for plan in ((THREADS, 4 * _sm(), 4), (2, 2 * _sm(), 8)):
+    for plan in ((THREADS, 3 * _sm(), 4), (2, 2 * _sm(), 8)):
         lat = kmc.Lattice(L, 8, 16, seeds)
         lat.set_launch(*plan)
         lat.set_rates([0.42, 0.35, 0.5], [0.0, 0.01, -0.02])
