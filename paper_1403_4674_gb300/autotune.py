@@ -62,7 +62,7 @@ def plan_candidates(sm_count: int, L_d: Optional[int] = None) -> List[Plan]:
         out += [(KMC_LAUNCH_THREADS, o, w) for o in (1, 2) for w in (4, 1)]
     elif L_d in (None, 8):
         out += [(KMC_LAUNCH_THREADS, 0, 4), (KMC_LAUNCH_THREADS, 0, 1)]
-        out += [(KMC_LAUNCH_THREADS, m * sm_count, w) for m, w in ((3, 4), (2, 4), (4, 4), (6, 2))]
+        out += [(KMC_LAUNCH_THREADS, m * sm_count, w) for m, w in ((3, 4), (2, 4), (4, 2), (6, 2))]
     return out
 
 
