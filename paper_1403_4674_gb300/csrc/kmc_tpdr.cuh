@@ -51,8 +51,9 @@ template <int LD> struct TpdrLayout {
     // product mantissa, exponent), the domain's scores d/dbeta, d/dh and
     // those of the open record (FP64 bits), 0 and the cumulative class rates
     // C_c, acceptances A_c, their reciprocals floor((2^64 - 1) / A_c), the
-    // step targets of the current chunk (four spare words past its end hold
-    // ~0, a target no rate sum reaches)
+    // step targets of the current chunk (eight spare words past its end hold
+    // ~0, a target no rate sum reaches, so that a scan of eight never reads
+    // past them)
     static constexpr int ROWLO = 0, ROWHI = LD, BLKLO = 2 * LD, BLKHI = BLKLO + NB + 1, TOTLO = BLKHI + NB + 1,
                          TOTHI = TOTLO + 1, CH = TOTLO + 2, CFL = CH + 1, CST = CH + 2, CCM = CH + 3, CCE = CH + 4,
                          OB0 = CH + 5, OB1 = OB0 + 1, OBM = OB0 + 2, OBE = OB0 + 3, CSB = OB0 + 4, CSH = CSB + 1,
@@ -639,8 +640,8 @@ __global__ void __launch_bounds__(128) tpdr_kernel(const RunParams P)
                         tpdr_planes<LD>(Sy, Su, Sd, (hW >> y) & 1u, (hE >> y) & 1u, b0, b1, b2);
                         const uint32_t mask = tpdr_eq(b0, b1, b2, qc) & (up ? Sy : ~Sy) & FULL;
                         // counts and spins disagree (never, unless the state is
-                        // corrupt): the launch stops after this event, whose
-                        // shared-memory writes stay within the domain's rows
+                        // corrupt): recorded, reported after the visit; every
+                        // index below stays within the domain's rows
                         const bool bad = rr >= (uint32_t)__popc(mask);
                         const int col = tpdr_select(mask, rr) & 31;
                         const uint32_t bit = 1u << col;
