@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the batched and gradient variants")
     ap.add_argument("--plan", default="", help="launch plan mode,size,warps (skips the plan tuning)")
+    ap.add_argument("--batch-k", type=int, default=32, help="steps per visit of the batch with --plan (profiling)")
     ap.add_argument("--only", default="", choices=["", "batched", "grad", "lattice8192", "ring8", "partitions2d",
                                                     "pollcost", "chain"],
                     help="time one variant alone and print its JSON object (profiling runs; not the contract line)")
@@ -285,7 +286,8 @@ NCU_COUNTS = {
     ("ising1024", "run_kernel"): (424586232478, 2580480000, 1572988655, 6585856),
     ("grad", "tpdr_kernel"): (38819166107, 1310720000, 238780472, 5571840),
     ("lattice8192", "tpdr64_kernel"): (18400662534, 524288000, 59494537, 11306240),
-    ("batched", "tpd_kernel"): (37003135232, 2636876800, 160081004, 7619467264),
+    ("batched", "tpd_kernel/k16"): (37003135232, 2636876800, 160081004, 7619467264),
+    ("batched", "tpd_kernel/k32"): (73589388272, 5273753600, 637452521, 6709346304),
 }
 ISSUE_PER_SM_CYCLE = 4  # one warp instruction per scheduler per cycle, four schedulers
 
@@ -410,13 +412,13 @@ def variant_batched(args, peaks, flush, stream):
     t0 = time.perf_counter()
     sm = torch.cuda.get_device_properties(0).multi_processor_count
     if args.plan:
-        # profiling runs: the whole batch as one group at L_d = 8, k = 16 on the given plan
-        choices = [autotune.GroupChoice(replicas=list(range(len(w.L))), L_d=8, k=16,
+        # profiling runs: the whole batch as one group at L_d = 8 and k = --batch-k on the given plan
+        choices = [autotune.GroupChoice(replicas=list(range(len(w.L))), L_d=8, k=args.batch_k,
                                         plan=tuple(int(x) for x in args.plan.split(",")), events_per_s=0.0)]
     else:
         plans = [(0, 0, 16), (3, 0, 4), (3, 3 * sm, 4), (3, 6 * sm, 2), (1, 4, 16), (1, 16, 16), (1, 16, 8),
                  (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
-        choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
+        choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16, 32),
                                       Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=20)
     tune_s = time.perf_counter() - t0
     # oracle on a 64-replica subset, each with its group's domain side and k
@@ -432,9 +434,11 @@ def variant_batched(args, peaks, flush, stream):
     graph = batch.capture(n_sched, obs_every, reset=0)
     ms = device_time(graph.replay, args.steps, args.warmup, flush, stream)
     ev = batch.events_per_schedule() * n_sched
-    # the ncu counters were taken on the whole batch as one group at L_d = 8,
-    # k = 16 on a thread-per-domain plan (its state stays in L2 on any such plan)
-    one_thread_group = len(choices) == 1 and choices[0].L_d == 8 and choices[0].k == 16 and choices[0].plan[0] == 3
+    # the ncu counters were taken on the whole batch as one group at L_d = 8
+    # on a thread-per-domain plan (its state stays in L2 on any such plan),
+    # per k
+    one_thread_group = len(choices) == 1 and choices[0].L_d == 8 and choices[0].plan[0] == 3
+    ckern = "tpd_kernel/k%d" % choices[0].k
     polls = None
     if args.plan:
         # profiling runs: one more step outside the graph, profiled, for its halo-poll count
@@ -453,10 +457,10 @@ def variant_batched(args, peaks, flush, stream):
                        "tuned_events_per_s": ch.events_per_s} for ch in choices],
            "tune_s": tune_s, "events_per_step": ev, "polls_per_launch": polls,
            "roofline": roofline(by, dev_s / args.steps, peaks,
-                                launch_traffic("batched", "tpd_kernel") if one_thread_group else None),
+                                launch_traffic("batched", ckern) if one_thread_group else None),
            "cpu_baseline": cpu}
     out["roofline"]["note"] = "step-level: the groups' run kernels overlap on concurrent streams"
-    iss = issue_roofline("batched", "tpd_kernel", ev * args.steps / dev_s, float(peaks.get("sm_max_mhz", 2070.0))) \
+    iss = issue_roofline("batched", ckern, ev * args.steps / dev_s, float(peaks.get("sm_max_mhz", 2070.0))) \
         if one_thread_group else None
     if iss is not None:
         iss["note"] = "counts of the single-context configuration of the same batch; steps/s of the whole step"

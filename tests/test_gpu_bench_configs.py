@@ -74,7 +74,7 @@ def test_batched_512_autotuned_graph_sample():
     w = wl.batched_replicas(512, master=512)
     sm = _sm()
     plans = [(0, 0, 16), (1, 4, 16), (1, 16, 16), (1, 16, 8), (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
-    choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
+    choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16, 32),
                                   Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=4)
     assert sorted(i for ch in choices for i in ch.replicas) == list(range(len(w.L)))
     batch = autotune.Batch(w.L, w.beta, w.h, w.seeds, choices)
@@ -219,7 +219,7 @@ def test_batched_512_full_step_sample():
     w = wl.batched_replicas(512, master=512)
     sm = _sm()
     plans = [(0, 0, 16), (1, 4, 16), (1, 16, 16), (1, 16, 8), (2, sm, 16), (2, 2 * sm, 12), (2, 3 * sm, 8)]
-    choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16),
+    choices = autotune.tune_batch(w.L, w.beta, w.h, w.seeds, k_candidates=(4, 8, 16, 32),
                                   Ld_candidates=(8, 16, 32, 64), plans=plans, trial_schedules=20)
     batch = autotune.Batch(w.L, w.beta, w.h, w.seeds, choices)
     graph = batch.capture(200, 10, reset=0)
