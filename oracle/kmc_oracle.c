@@ -52,9 +52,9 @@
  * the ring against its transfer-matrix equilibrium, the textbook
  * random-site kernel, its enumerated final-state distribution and
  * time-dependent spin averages, and the beta = 0 closed form.
- * Parity unpinned: the per-domain event hash (a fingerprint this build
+ * Parity unpinned: the per-domain event hash (a fingerprint this library
  * defines for CPU/GPU event-sequence parity, not a quantity of the paper)
- * and the Philox counter layout (likewise a definition of this build).
+ * and the Philox counter layout (likewise a definition of this library).
  *
  * Build: gcc -O2 -std=gnu11 -ffp-contract=off -fPIC -shared -lm.
  */

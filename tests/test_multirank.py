@@ -60,7 +60,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
 
 def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
     """Rank 0 of the reference arm times the oracle and prints one JSON line
-    with the contract's keys (the driver computes the arms' ratio from it)."""
+    with the benchmark contract's keys (the arms' ratio is computed from it)."""
     import json
     import bench
     monkeypatch.setenv("RANK", "0")
