@@ -209,11 +209,12 @@ def test_scores_equal_the_warp_kernels(Ld):
     np.testing.assert_allclose(o0[..., 4:6], o1[..., 4:6], rtol=1e-13, atol=1e-13)
 
 
-@pytest.mark.parametrize("L,Ld", [(8192, 32), (16384, 64)])
+@pytest.mark.parametrize("L,Ld", [(8192, 32), (10240, 64)])
 def test_too_many_domains_for_shared_memory_take_a_warp_plan(L, Ld):
-    """65,536 domains do not fit the GPU's shared memory at once: the thread
-    plan is refused (the previous plan stays) and the library's default is a
-    warp plan."""
+    """More domains than the thread plan holds in the GPU's shared memory at
+    once (65,536 of 32x32, 25,600 of 64x64; it holds about 19,000): the
+    thread plan is refused (the previous plan stays) and the library's
+    default is a warp plan."""
     import paper_1403_4674_gb300 as kmc
     lat = kmc.Lattice([L], Ld, 4, [9])
     assert lat.launch()[0] != THREADS
