@@ -1005,8 +1005,11 @@ def main():
                                           ", one run-kernel launch per step",
                            "plan": list(plan), "launch": list(lat.launch()), "tune_s": tune_s,
                            "threads_per_domain": (("one thread per domain, 32 domains per warp, state in shared "
-                                                   "memory" if kern == "tpdr_kernel" else "one thread per domain")
+                                                   "memory" if kern in ("tpdr_kernel", "tpdr64_kernel")
+                                                   else "one thread per domain")
                                                   if kern != "run_kernel" else "one warp per domain") +
+                                                 (", replicas dealt round-robin over the warps"
+                                                  if ckern.endswith("/rr") else "") +
                                                  " (the tuner's choice between thread and warp plans)",
                            "wall_s": wall},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "bit_exact": bit_exact,
