@@ -386,6 +386,9 @@ class Lattice:
         return int(sum(visits * (x // self.L_d) ** 2 * k for x, k in zip(self.L, self.ks)))
 
     def set_launch(self, mode: int = KMC_LAUNCH_AUTO, size: int = 0, warps_per_cta: int = 16):
+        """Launch plan (kmc_set_launch): size is the cluster size, the grid's
+        CTA count, or for the thread plans of L_d = 16, 32, 64 the domain
+        order over the warps (0 or 1 replica after replica, 2 round-robin)."""
         kmc_set_launch(self.ctx, mode, size, warps_per_cta)
 
     def launch(self):
