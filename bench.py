@@ -654,11 +654,15 @@ def variant_part(args, peaks, flush, stream):
                           dtype=torch.float64, device="cuda")
         runs.append((g, n_sched, obs_every, obs, torch.cuda.Stream(), n_traj * S))
 
+    # the longest chains first: the 100^2 settings' trajectories (1.6e5 steps
+    # each) start at once, the short 12^2 ones fill the SMs around them
+    order = sorted(range(len(runs)), key=lambda i: -settings[i][2])
+
     def step():
         main = torch.cuda.current_stream()
         start = torch.cuda.Event()
         start.record(main)
-        for g, n_sched, obs_every, obs, st, _ in runs:
+        for g, n_sched, obs_every, obs, st, _ in (runs[i] for i in order):
             st.wait_event(start)
             with torch.cuda.stream(st):
                 g.run(n_sched, schedule=kmc.KMC_SCHEDULE_RANDOM_PERM, obs_every=obs_every, out=obs)
