@@ -343,6 +343,8 @@ __global__ void __launch_bounds__(PART_WARPS * 32) part_kernel(const PartParams 
             H = (H ^ ev) * HASH_PRIME;
             ++flips;
             pos = jx + 1;
+            // the classes are needed again only if a step of this visit remains
+            if (pos >= hi) break;
             n_c = (lane < 10) ? (uint32_t)dcount[d * 10 + lane] : 0u;
             Wc = (uint64_t)n_c * A;
             Cinc = kmcdev::prefix16(Wc, lane);
