@@ -664,7 +664,11 @@ def variant_part(args, peaks, flush, stream):
     # warps least: 124.7 ms per step against 126.8 on two streams and 129.9
     # with all twelve at once
     S_max = max(s[2] for s in settings)
-    long_ = [i for i in range(len(runs)) if settings[i][2] == S_max]
+    # the 100^2 settings by expected length: smallest N_I first, then blocks
+    # before stripes and more domains first, so that the longest chains take
+    # SMs of their own before the shorter ones double up on SMs
+    long_ = sorted((i for i in range(len(runs)) if settings[i][2] == S_max),
+                   key=lambda i: (settings[i][5], settings[i][3] != B_, -settings[i][4]))
     short = sorted((i for i in range(len(runs)) if settings[i][2] < S_max), key=lambda i: settings[i][5])
     n_sh = min(args.part_streams, len(short)) if args.part_streams > 0 else len(short)
     groups = [(runs[i][4], [i]) for i in long_] + [(runs[short[c]][4], short[c::n_sh]) for c in range(n_sh)]
