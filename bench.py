@@ -629,6 +629,40 @@ def variant_ring(args, peaks, flush, stream):
     return out
 
 
+def part_settings(stripes, blocks):
+    """The 28 settings (L, n_traj, S, kind, N_D, N_I) of the paper's 2D
+    experiments (Sec. 3.2), S the steps per trajectory of one timed step."""
+    settings = []
+    for L, n_traj, S, parts in [(12, 500, 16000, [(stripes, 2), (stripes, 4), (blocks, 4)]),
+                                (100, 50, 160000, [(stripes, 2), (stripes, 4), (blocks, 4), (blocks, 16)])]:
+        for kind, ND in parts:
+            for NI in (1, 2, 5, 10):
+                settings.append((L, n_traj, S, kind, ND, NI))
+    return settings
+
+
+def part_launch_groups(settings, blocks, n_streams):
+    """Launch groups of the 2D experiments' settings (L, n_traj, S, kind, N_D,
+    N_I): each group is a list of setting indices run one after another on
+    one stream, the groups launched in list order.
+
+    The longest chains first: the settings with the most steps per trajectory
+    (100^2: 1.6e5) start at once, one stream each, ordered by expected length
+    (smallest N_I first, then blocks before stripes and more domains first) so
+    that the longest chains take SMs of their own before the shorter ones
+    double up on SMs.  The shorter settings (12^2) follow, smallest N_I first,
+    dealt round-robin over `n_streams` streams (0: one stream each).  One
+    stream (500 trajectories at a time beside the 800 of 100^2) crowds the
+    100^2 warps least: 124.7 ms per step against 126.8 on two streams and
+    129.9 with all twelve at once."""
+    S_max = max(s[2] for s in settings)
+    long_ = sorted((i for i in range(len(settings)) if settings[i][2] == S_max),
+                   key=lambda i: (settings[i][5], settings[i][3] != blocks, -settings[i][4]))
+    short = sorted((i for i in range(len(settings)) if settings[i][2] < S_max), key=lambda i: settings[i][5])
+    n_sh = min(n_streams, len(short)) if n_streams > 0 else len(short)
+    return [[i] for i in long_] + [short[c::n_sh] for c in range(n_sh)]
+
+
 def variant_part(args, peaks, flush, stream):
     """The paper's 2D experiments (Sec. 3.2) as one step: 12^2 x 500 and
     100^2 x 50 trajectories at T = 2.4, Barker, from the all-up state, in
@@ -639,13 +673,8 @@ def variant_part(args, peaks, flush, stream):
     import torch
     import paper_1403_4674_gb300 as kmc
     from paper_1403_4674_gb300 import workloads as wl
-    S_, B_ = kmc.KMC_PART_STRIPES, kmc.KMC_PART_BLOCKS
-    settings = []
-    for L, n_traj, S, parts in [(12, 500, 16000, [(S_, 2), (S_, 4), (B_, 4)]),
-                                (100, 50, 160000, [(S_, 2), (S_, 4), (B_, 4), (B_, 16)])]:
-        for kind, ND in parts:
-            for NI in (1, 2, 5, 10):
-                settings.append((L, n_traj, S, kind, ND, NI))
+    B_ = kmc.KMC_PART_BLOCKS
+    settings = part_settings(kmc.KMC_PART_STRIPES, B_)
     runs = []
     for i, (L, n_traj, S, kind, ND, NI) in enumerate(settings):
         g = kmc.Partitioned(L, kind, ND, NI, wl.replica_seeds(1200 + i, n_traj))
@@ -656,22 +685,7 @@ def variant_part(args, peaks, flush, stream):
                           dtype=torch.float64, device="cuda")
         runs.append((g, n_sched, obs_every, obs, torch.cuda.Stream(), n_traj * S))
 
-    # the longest chains first: the 100^2 settings' trajectories (1.6e5 steps
-    # each) start at once, each on its own stream; the short 12^2 settings
-    # follow, longest (smallest N_I) first, dealt round-robin over
-    # `--part-streams` streams and run one after another on each.  One stream
-    # (500 trajectories at a time beside the 800 of 100^2) crowds the 100^2
-    # warps least: 124.7 ms per step against 126.8 on two streams and 129.9
-    # with all twelve at once
-    S_max = max(s[2] for s in settings)
-    # the 100^2 settings by expected length: smallest N_I first, then blocks
-    # before stripes and more domains first, so that the longest chains take
-    # SMs of their own before the shorter ones double up on SMs
-    long_ = sorted((i for i in range(len(runs)) if settings[i][2] == S_max),
-                   key=lambda i: (settings[i][5], settings[i][3] != B_, -settings[i][4]))
-    short = sorted((i for i in range(len(runs)) if settings[i][2] < S_max), key=lambda i: settings[i][5])
-    n_sh = min(args.part_streams, len(short)) if args.part_streams > 0 else len(short)
-    groups = [(runs[i][4], [i]) for i in long_] + [(runs[short[c]][4], short[c::n_sh]) for c in range(n_sh)]
+    groups = [(runs[members[0]][4], members) for members in part_launch_groups(settings, B_, args.part_streams)]
 
     def step():
         main = torch.cuda.current_stream()

@@ -33,3 +33,28 @@ def test_counts_follow_their_kernel_sources(monkeypatch):
     monkeypatch.setitem(bench.NCU_KERNEL_SHA256, base, "0" * 64)
     assert bench.ncu_counts(*key) is None
     assert bench.launch_traffic(*key) is None
+
+
+def test_part_launch_groups():
+    """The 2D experiments' launch groups: every setting once; the 100^2
+    settings first, one stream each, longest expected chain (N_I = 1, blocks
+    of 16) first; the 12^2 ones dealt over the requested streams, smallest
+    N_I first on each."""
+    STRIPES, BLOCKS = 1, 0
+    settings = bench.part_settings(STRIPES, BLOCKS)
+    assert len(settings) == 28
+    for n_streams, n_short_groups in ((0, 12), (1, 1), (2, 2), (3, 3), (40, 12)):
+        groups = bench.part_launch_groups(settings, BLOCKS, n_streams)
+        flat = [i for g in groups for i in g]
+        assert sorted(flat) == list(range(28))
+        long_, short = groups[:16], groups[16:]
+        assert all(len(g) == 1 and settings[g[0]][0] == 100 for g in long_)
+        assert len(short) == n_short_groups
+        assert all(settings[i][0] == 12 for g in short for i in g)
+        for g in short:
+            NI = [settings[i][5] for i in g]
+            assert NI == sorted(NI)
+        first = settings[long_[0][0]]
+        assert (first[3], first[4], first[5]) == (BLOCKS, 16, 1)
+        NI_long = [settings[g[0]][5] for g in long_]
+        assert NI_long == sorted(NI_long)
