@@ -58,3 +58,15 @@ def test_part_launch_groups():
         assert (first[3], first[4], first[5]) == (BLOCKS, 16, 1)
         NI_long = [settings[g[0]][5] for g in long_]
         assert NI_long == sorted(NI_long)
+
+
+def test_algorithmic_bytes_of_the_headline():
+    """Per-visit bytes (L_d + 2)^2 - 4 + 32 k + 4 L_d at L_d = 32 and the
+    headline's bytes per launch: 18 replicas of 1024^2, k in {1, 4, 16} six
+    replicas each, two visits per domain and schedule, 1e4 schedules."""
+    assert [bench.visit_bytes(32, k) for k in (1, 4, 16)] == [1312, 1408, 1792]
+    L = [1024] * 18
+    ks = [1, 4, 16] * 6
+    per_schedule = bench.schedule_bytes(L, 32, ks)
+    assert per_schedule == 2 * 1024 * 6 * (1312 + 1408 + 1792)
+    assert per_schedule * 10000 == 554434560000
